@@ -1,0 +1,366 @@
+"""FP64 CPU oracle of the NVGS render pass — TEST INFRASTRUCTURE, not part of the product.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the bench's CPU-baseline / reference leg may
+import this package.  The CUDA library never calls it and shares no code with it; both only read
+the seeded inputs drawn by the ``scenes`` package.
+
+The arithmetic lives in ``nvgs_oracle.c`` (plain C, double precision, OpenMP over pixel rows);
+this module only marshals numpy arrays into it.  Each wrapper names the part of the paper it
+restates:
+
+* ``distance_bound``         Sec. 3.1, Eq. 1
+* ``prepare``                Sec. 3.1 (bounding box of the means, near / far distances)
+* ``frustum``                Sec. 3.3 (frustum culling on the Gaussian mean)
+* ``visibility``/``features``/``mlp_forward``  Sec. 3.2-3.3 and Eq. 2 (MLP inputs, forward)
+* ``project``                Sec. 3.3 -> original 3DGS preprocessing (EWA splat, SH colour)
+* ``composite``/``render``   Sec. 4.1 blending rules, exact per-pixel depth-sorted compositing
+* ``labels``                 Sec. 3.1 (contribution alpha * T; visible iff it blends)
+
+Parity status: every function here is pinned by ``tests/test_oracle_*.py`` against closed
+forms, invariants, brute force or independent library routines.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nvgs_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no CUDA involved)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-Wall", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OrAsset(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("pad_", C.c_int32),
+                ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p),
+                ("bbox_min", C.c_double * 3), ("bbox_max", C.c_double * 3),
+                ("d_min", C.c_double), ("d_max", C.c_double), ("train_focal", C.c_double)]
+
+
+class OrInstance(C.Structure):
+    _fields_ = [("asset_id", C.c_int32), ("pad_", C.c_int32), ("R", C.c_double * 9),
+                ("t", C.c_double * 3), ("s", C.c_double)]
+
+
+class OrCamera(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3), ("fx", C.c_double),
+                ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("width", C.c_int32), ("height", C.c_int32), ("z_near", C.c_double)]
+
+
+class OrOpts(C.Structure):
+    _fields_ = [("alpha_min", C.c_double), ("alpha_max", C.c_double), ("t_stop", C.c_double),
+                ("dilation", C.c_double), ("guard_band", C.c_double), ("bg", C.c_double * 3),
+                ("tile_size", C.c_int32), ("pad_", C.c_int32), ("eps_alpha", C.c_double),
+                ("eps_t", C.c_double), ("eps_depth", C.c_double), ("eps_frustum", C.c_double),
+                ("eps_px", C.c_double), ("swap_tol", C.c_double)]
+
+
+SPLAT_DTYPE = np.dtype([
+    ("valid", np.int32), ("ambiguous", np.int32), ("instance", np.int32), ("gaussian", np.int32),
+    ("u", np.float64), ("v", np.float64), ("depth", np.float64), ("cov", np.float64, 3),
+    ("conic", np.float64, 3), ("opacity", np.float64), ("rgb", np.float64, 3),
+    ("x_ext", np.float64), ("y_ext", np.float64), ("px_min", np.int32, 2),
+    ("px_max", np.int32, 2), ("tile_min", np.int32, 2), ("tile_max", np.int32, 2)], align=True)
+assert SPLAT_DTYPE.itemsize == 168
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            P = C.POINTER
+            vp = C.c_void_p
+            L.or_distance_bound.restype = C.c_double
+            L.or_distance_bound.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.or_asset_prepare.argtypes = [P(OrAsset), C.c_double, C.c_double, C.c_double,
+                                           C.c_double, C.c_double]
+            L.or_frustum.argtypes = [P(OrAsset), P(OrInstance), C.c_int, P(OrCamera), P(OrOpts),
+                                     vp, vp]
+            L.or_normalised_distance.restype = C.c_double
+            L.or_normalised_distance.argtypes = [C.c_double] * 5
+            L.or_mlp_features.argtypes = [P(OrAsset), vp, vp, C.c_double, vp]
+            L.or_mlp_forward.argtypes = [vp, C.c_int64, vp, vp]
+            L.or_visibility.argtypes = [P(OrAsset), P(OrInstance), C.c_int, P(OrCamera), vp,
+                                        C.c_int, vp, vp, vp]
+            L.or_sh_basis.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, vp]
+            L.or_quat_to_rot.argtypes = [vp, vp]
+            L.or_cov3d.argtypes = [vp, vp, vp]
+            L.or_project.argtypes = [P(OrAsset), P(OrInstance), C.c_int, P(OrCamera), P(OrOpts),
+                                     vp, vp, vp]
+            L.or_composite.argtypes = [vp, C.c_int64, P(OrCamera), P(OrOpts), vp, C.c_int, vp, vp,
+                                       vp, vp, C.c_int]
+            L.or_pixel_weights.restype = C.c_int
+            L.or_pixel_weights.argtypes = [vp, C.c_int64, P(OrCamera), P(OrOpts), C.c_int,
+                                           C.c_int, vp, C.c_int, P(C.c_double)]
+            L.or_num_threads.restype = C.c_int
+            L.or_set_num_threads.argtypes = [C.c_int]
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+# ----------------------------------------------------------------------------- options
+def opts(alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4, dilation=0.3, guard_band=1.3,
+         bg=(0.0, 0.0, 0.0), tile_size=16, eps_alpha=2e-4, eps_t=2e-4, eps_depth=1e-6,
+         eps_frustum=1e-6, eps_px=1e-3, swap_tol=1e-4) -> OrOpts:
+    """Blending constants of Sec. 4.1 and the 3DGS conventions, plus ambiguity-band widths."""
+    o = OrOpts()
+    o.alpha_min, o.alpha_max, o.t_stop = alpha_min, alpha_max, t_stop
+    o.dilation, o.guard_band = dilation, guard_band
+    o.bg[:] = [float(b) for b in bg]
+    o.tile_size = int(tile_size)
+    o.eps_alpha, o.eps_t, o.eps_depth = eps_alpha, eps_t, eps_depth
+    o.eps_frustum, o.eps_px, o.swap_tol = eps_frustum, eps_px, swap_tol
+    return o
+
+
+# ----------------------------------------------------------------------------- scene marshalling
+class OracleScene:
+    """FP64 copy of a ``scenes.Scene`` plus the per-asset constants of Sec. 3.1."""
+
+    def __init__(self, scene, theta_t=None, p_near=0.9, p_far=0.05, d_min=0.0, d_max=0.0):
+        L = lib()
+        self.scene = scene
+        self._keep = []
+        self.assets = (OrAsset * len(scene.assets))()
+        for k, a in enumerate(scene.assets):
+            arrs = [np.ascontiguousarray(x, np.float64) for x in
+                    (a.means, a.log_scales, a.quats, a.opacity_logits, a.sh)]
+            self._keep.append(arrs)
+            s = self.assets[k]
+            s.n, s.sh_degree = a.n, a.sh_degree
+            s.means, s.log_scales, s.quats, s.opacity_logits, s.sh = [x.ctypes.data for x in arrs]
+            th = a.train_fov_x if theta_t is None else theta_t
+            L.or_asset_prepare(C.byref(s), th, p_near, p_far, d_min, d_max)
+        self.instances = (OrInstance * len(scene.instances))()
+        for k, i in enumerate(scene.instances):
+            d = self.instances[k]
+            d.asset_id = i.asset_id
+            d.R[:] = [float(x) for x in np.asarray(i.R, np.float64).ravel()]
+            d.t[:] = [float(x) for x in np.asarray(i.t, np.float64)]
+            d.s = float(i.s)
+        self.n_inst = len(scene.instances)
+        self.n_instanced = scene.n_instanced
+
+    def asset_constants(self, k):
+        s = self.assets[k]
+        return dict(bbox_min=np.array(s.bbox_min[:]), bbox_max=np.array(s.bbox_max[:]),
+                    d_min=s.d_min, d_max=s.d_max, train_focal=s.train_focal)
+
+
+def camera(cam) -> OrCamera:
+    c = OrCamera()
+    c.R[:] = [float(x) for x in np.asarray(cam.R, np.float64).ravel()]
+    c.t[:] = [float(x) for x in np.asarray(cam.t, np.float64)]
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height, c.z_near = int(cam.width), int(cam.height), float(cam.z_near)
+    return c
+
+
+def flat_weights(w: dict) -> np.ndarray:
+    parts = []
+    for li in range(1, 5):
+        parts += [np.asarray(w[f"W{li}"], np.float64).ravel(), np.asarray(w[f"b{li}"], np.float64).ravel()]
+    out = np.concatenate(parts)
+    assert out.size == 10497
+    return out
+
+
+# ----------------------------------------------------------------------------- wrappers
+def distance_bound(r, theta, p):
+    """Eq. 1: d = r / (tan(theta / 2) p)."""
+    return lib().or_distance_bound(float(r), float(theta), float(p))
+
+
+def normalised_distance(d_local, f_t, f_r, d_min, d_max):
+    """Eq. 2 then the min-max map of Sec. 3.3 on log distance, clamped to [-1, 1]."""
+    return lib().or_normalised_distance(float(d_local), float(f_t), float(f_r), float(d_min), float(d_max))
+
+
+def frustum(osc: OracleScene, cam, o=None):
+    o = o or opts()
+    n = osc.n_instanced
+    inside = np.zeros(n, np.uint8)
+    amb = np.zeros(n, np.uint8)
+    lib().or_frustum(osc.assets, osc.instances, osc.n_inst, C.byref(camera(cam)), C.byref(o),
+                     _ptr(inside), _ptr(amb))
+    return inside.astype(bool), amb.astype(bool)
+
+
+def visibility(osc: OracleScene, cam, weights=None, gate=False, return_features=False):
+    """Per instanced Gaussian: MLP logit, whether the instance bypasses the MLP, and features."""
+    n = osc.n_instanced
+    logits = np.zeros(n, np.float64)
+    gated = np.zeros(n, np.uint8)
+    feats = np.zeros((n, 32), np.float64) if return_features else None
+    w = flat_weights(weights) if weights is not None else None
+    lib().or_visibility(osc.assets, osc.instances, osc.n_inst, C.byref(camera(cam)), _ptr(w),
+                        int(bool(gate)), _ptr(logits), _ptr(gated), _ptr(feats))
+    out = dict(logits=logits, gated=gated.astype(bool))
+    if return_features:
+        out["features"] = feats
+    return out
+
+
+def features(osc: OracleScene, asset_k: int, mu, cam_local, f_r):
+    f = np.zeros(32, np.float64)
+    mu = np.ascontiguousarray(mu, np.float64)
+    cl = np.ascontiguousarray(cam_local, np.float64)
+    lib().or_mlp_features(C.byref(osc.assets[asset_k]), _ptr(mu), _ptr(cl), float(f_r), _ptr(f))
+    return f
+
+
+def mlp_forward(weights: dict, feats: np.ndarray) -> np.ndarray:
+    feats = np.ascontiguousarray(feats, np.float64).reshape(-1, 32)
+    out = np.zeros(feats.shape[0], np.float64)
+    w = flat_weights(weights)
+    lib().or_mlp_forward(_ptr(w), feats.shape[0], _ptr(feats), _ptr(out))
+    return out
+
+
+def sh_basis(degree: int, dirs: np.ndarray) -> np.ndarray:
+    dirs = np.asarray(dirs, np.float64).reshape(-1, 3)
+    out = np.zeros((dirs.shape[0], 16), np.float64)
+    y = np.zeros(16, np.float64)
+    for i, (a, b, c) in enumerate(dirs):
+        lib().or_sh_basis(int(degree), float(a), float(b), float(c), _ptr(y))
+        out[i] = y
+    return out[:, :(degree + 1) ** 2]
+
+
+def quat_to_rot(q) -> np.ndarray:
+    q = np.ascontiguousarray(q, np.float64)
+    R = np.zeros(9, np.float64)
+    lib().or_quat_to_rot(_ptr(q), _ptr(R))
+    return R.reshape(3, 3)
+
+
+def cov3d(log_scale, quat) -> np.ndarray:
+    ls = np.ascontiguousarray(log_scale, np.float64)
+    q = np.ascontiguousarray(quat, np.float64)
+    S = np.zeros(9, np.float64)
+    lib().or_cov3d(_ptr(ls), _ptr(q), _ptr(S))
+    return S.reshape(3, 3)
+
+
+def project(osc: OracleScene, cam, o=None, keep=None, keep_amb=None) -> np.ndarray:
+    o = o or opts()
+    out = np.zeros(osc.n_instanced, SPLAT_DTYPE)
+    k = None if keep is None else np.ascontiguousarray(keep, np.uint8)
+    ka = None if keep_amb is None else np.ascontiguousarray(keep_amb, np.uint8)
+    lib().or_project(osc.assets, osc.instances, osc.n_inst, C.byref(camera(cam)), C.byref(o),
+                     _ptr(k), _ptr(ka), _ptr(out))
+    return out
+
+
+def composite(splats: np.ndarray, cam, o=None, rows=None, brute_force=False,
+              want_contrib=False):
+    o = o or opts()
+    splats = np.ascontiguousarray(splats, SPLAT_DTYPE)
+    H, W = int(cam.height), int(cam.width)
+    r = None if rows is None else np.ascontiguousarray(rows, np.int32)
+    nr = H if r is None else r.size
+    image = np.zeros((nr, W, 3), np.float64)
+    T = np.zeros((nr, W), np.float64)
+    amb = np.zeros((nr, W), np.uint8)
+    contrib = np.zeros(splats.shape[0], np.int32) if want_contrib else None
+    lib().or_composite(_ptr(splats), splats.shape[0], C.byref(camera(cam)), C.byref(o), _ptr(r),
+                       nr, _ptr(image), _ptr(T), _ptr(contrib), _ptr(amb), int(bool(brute_force)))
+    out = dict(image=image, T=T, ambiguous=amb.astype(bool))
+    if want_contrib:
+        out["n_contrib"] = contrib
+    return out
+
+
+def render(osc: OracleScene, cam, o=None, keep=None, keep_amb=None, rows=None,
+           want_contrib=False):
+    """Exact FP64 render: frustum, optional culling decision, projection, compositing."""
+    o = o or opts()
+    sp = project(osc, cam, o, keep, keep_amb)
+    out = composite(sp, cam, o, rows=rows, want_contrib=want_contrib)
+    out["splats"] = sp
+    return out
+
+
+def pixel_weights(splats, cam, o, x, y, cap=4096):
+    """Contributions alpha_k T_k of the blended fragments at pixel (x, y) and the final T."""
+    splats = np.ascontiguousarray(splats, SPLAT_DTYPE)
+    w = np.zeros(cap, np.float64)
+    T = C.c_double(0.0)
+    n = lib().or_pixel_weights(_ptr(splats), splats.shape[0], C.byref(camera(cam)), C.byref(o),
+                               int(x), int(y), _ptr(w), cap, C.byref(T))
+    return w[:min(n, cap)], T.value
+
+
+def cull_decision(vis: dict, inside: np.ndarray, threshold=0.0, band=0.0):
+    """Keep mask after the MLP (Sec. 3.3): in the frustum and (bypassed or logit > threshold).
+    Also returns where |logit - threshold| <= band (ambiguous decision)."""
+    keep = inside & (vis["gated"] | (vis["logits"] > threshold))
+    amb = (~vis["gated"]) & (np.abs(vis["logits"] - threshold) <= band)
+    return keep, amb
+
+
+def labels(osc: OracleScene, cams, o=None):
+    """Sec. 3.1: per view, per instanced Gaussian, whether it is blended at some pixel."""
+    o = o or opts()
+    out = []
+    for cam in cams:
+        r = render(osc, cam, o, want_contrib=True)
+        out.append(r["n_contrib"] > 0)
+    return np.stack(out, 0)
+
+
+def tile_lists(splats: np.ndarray, cam, tile_size: int):
+    """Per tile (row-major tile index): the valid splats whose tile rect covers it, in blend order
+    (depth, instance, gaussian).  Returns (tile ids, instance ids, gaussian ids) sorted by tile,
+    then blend order, and the set of ambiguous (footprint or decision) splats."""
+    tw = (int(cam.width) + tile_size - 1) // tile_size
+    v = splats[splats["valid"] != 0]
+    tiles, inst, gs, depth = [], [], [], []
+    for s in v:
+        for ty in range(s["tile_min"][1], s["tile_max"][1] + 1):
+            for tx in range(s["tile_min"][0], s["tile_max"][0] + 1):
+                tiles.append(ty * tw + tx)
+                inst.append(s["instance"])
+                gs.append(s["gaussian"])
+                depth.append(s["depth"])
+    tiles, inst, gs, depth = map(np.asarray, (tiles, inst, gs, depth))
+    if tiles.size == 0:
+        return tiles, inst, gs
+    order = np.lexsort((gs, inst, depth, tiles))
+    return tiles[order], inst[order], gs[order]
+
+
+def num_threads() -> int:
+    return lib().or_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    lib().or_set_num_threads(int(n))
+
+
+def psnr(a: np.ndarray, b: np.ndarray, peak: float = 1.0) -> float:
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return math.inf if mse == 0.0 else 10.0 * math.log10(peak * peak / mse)
