@@ -1,0 +1,216 @@
+/*
+ * nvgs.h — C ABI of the NVGS per-frame render pass on one NVIDIA B300 (sm_103a).
+ *
+ * The library renders composed scenes of instanced 3D Gaussian Splatting assets with the
+ * occlusion culling of "NVGS: Neural Visibility for Occlusion Culling in 3D Gaussian Splatting":
+ *
+ *   S1  frustum culling of every instanced Gaussian on its mean            (Sec. 3.3)
+ *   S2  the per-asset visibility MLP, queried for in-frustum Gaussians     (Sec. 3.2, 3.3, Eq. 2)
+ *   S3  stream compaction: a Gaussian is instantiated only if it survives  (Sec. 3.3)
+ *   S4  EWA projection to 2D conics and SH colour                          (Sec. 3.3 -> 3DGS)
+ *   S5  tile binning and a radix sort on (tile, depth) keys                (Sec. 3.3 -> 3DGS)
+ *   S6  front-to-back alpha compositing with the blending rules of         (Sec. 4.1)
+ *       alpha < 1/255 skipped and T < 1e-4 stopping the pixel
+ *
+ * Every call is asynchronous on the context's CUDA stream unless stated otherwise.  Device
+ * pointers passed in are borrowed for the duration of the enqueued work; the caller keeps
+ * ownership of everything it passes.  No C++ exception crosses this boundary: each call returns
+ * an nvgs_status and the text of the last error is kept per context (nvgs_last_error).
+ *
+ * Conventions (the same as the test-side oracle's):
+ *   - instance: a local point mu lands at R (s mu) + t in the world (R orthonormal, s > 0);
+ *   - camera: x_c = R x_w + t, x right / y down / z forward; pixel (i, j) is sampled at its centre
+ *     (i + 0.5, j + 0.5); u = fx x_c / z_c + cx, v = fy y_c / z_c + cy;
+ *   - images are row-major H x W x 3 float32 (RGB innermost);
+ *   - "instanced index" of Gaussian g of instance i = sum_{k<i} N(asset of k) + g.
+ */
+#ifndef NVGS_H
+#define NVGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NVGS_ABI_VERSION 1
+
+typedef enum {
+    NVGS_OK = 0,
+    NVGS_ERR_INVALID_ARG = 1,  /* a pointer, size or enum is out of range; nothing was enqueued */
+    NVGS_ERR_OOM = 2,          /* device allocation failed */
+    NVGS_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    NVGS_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    NVGS_ERR_CAPACITY = 5,     /* a fixed-capacity buffer would overflow */
+    NVGS_ERR_UNSUPPORTED = 6   /* valid request this build cannot serve */
+} nvgs_status;
+
+typedef enum { NVGS_MEM_HOST = 0, NVGS_MEM_DEVICE = 1 } nvgs_memory;
+
+/* Arithmetic of the visibility MLP (Sec. 3.2): FP32 on CUDA cores, or BF16 operands with FP32
+ * accumulation on the tcgen05 tensor cores. */
+typedef enum { NVGS_PREC_FP32 = 0, NVGS_PREC_BF16 = 1 } nvgs_precision;
+
+typedef struct nvgs_ctx nvgs_ctx;
+
+/* One 3DGS asset (Sec. 3.3: "each unique asset is stored once").  Arrays are read during the
+ * call and copied into the library's own layout. */
+typedef struct {
+    int64_t n;                   /* Gaussians, >= 1 */
+    int32_t sh_degree;           /* 0..3 */
+    int32_t memory;              /* nvgs_memory of the five arrays below */
+    const float* means;          /* n x 3 */
+    const float* log_scales;     /* n x 3 */
+    const float* quats;          /* n x 4, (w, x, y, z), need not be normalised */
+    const float* opacity_logits; /* n; opacity = sigmoid(logit) */
+    const float* sh;             /* n x (deg+1)^2 x 3, coefficient-major, RGB innermost */
+    float train_fov_x;           /* training field of view theta_t in radians (Eq. 1, Eq. 2) */
+    float d_min, d_max;          /* camera distance bounds; <= 0 selects Eq. 1 on the means' box */
+    float p_near, p_far;         /* Eq. 1 coverage fractions; <= 0 selects 0.9 / 0.05 (Sec. 3.1) */
+} nvgs_asset_desc;
+
+/* A rigid, uniformly scaled placement of an asset (Sec. 3.3: "list of instance transforms"). */
+typedef struct {
+    int32_t asset_id;
+    float R[9];                  /* row-major rotation */
+    float t[3];
+    float s;                     /* uniform scale > 0 (the s of Eq. 2) */
+} nvgs_instance;
+
+/* Pinhole camera.  The field of view is fixed by fx, fy and the image size. */
+typedef struct {
+    float R[9];                  /* world -> camera rotation, row-major */
+    float t[3];
+    float fx, fy, cx, cy;        /* pixels */
+    int32_t width, height;       /* 1 .. 16384 */
+    float z_near;                /* > 0 */
+} nvgs_camera;
+
+/* Per-frame switches.  nvgs_default_flags() fills the paper's values. */
+typedef struct {
+    int32_t use_mlp;             /* 0: unculled plain path (S1, S4-S6); 1: MLP culling (S1-S6) */
+    int32_t mlp_gate;            /* 1: bypass the MLP for instances closer than d_min (Sec. 3.3) */
+    float logit_threshold;       /* keep iff logit > threshold (default 0) */
+    float alpha_min;             /* 1/255 (Sec. 4.1) */
+    float alpha_max;             /* 0.99 (3DGS) */
+    float t_stop;                /* 1e-4 (Sec. 4.1) */
+    float dilation;              /* 0.3 px^2 added to the 2D covariance (3DGS) */
+    float guard_band;            /* 1.3: frustum half-width multiplier */
+    float bg[3];                 /* background colour */
+    int32_t tile_size;           /* 8, 16 or 32 */
+    int32_t image_memory;        /* nvgs_memory of the output image */
+    int32_t profile;             /* 1: time each stage with CUDA events (nvgs_frame_stats) */
+    const float* logits_override;/* nullable DEVICE array of per-instanced-Gaussian logits used
+                                    instead of the MLP (tests inject fixed decisions with it) */
+    int32_t keep_outputs;        /* 1: keep final T and the contributor count per pixel for
+                                    nvgs_render_backward and the labeller */
+    int32_t reserved[7];
+} nvgs_render_flags;
+
+#define NVGS_NUM_STAGES 8
+/* Stage indices of nvgs_frame_stats.stage_ms */
+enum { NVGS_STAGE_SETUP = 0, NVGS_STAGE_CULL = 1, NVGS_STAGE_MLP = 2, NVGS_STAGE_COMPACT = 3,
+       NVGS_STAGE_PROJECT = 4, NVGS_STAGE_BIN = 5, NVGS_STAGE_SORT = 6, NVGS_STAGE_BLEND = 7 };
+
+typedef struct {
+    uint64_t n_instanced;        /* instanced Gaussians before culling */
+    uint64_t n_in_frustum;       /* after S1 */
+    uint64_t n_mlp_queries;      /* Gaussians the MLP evaluated (in frustum, not gated) */
+    uint64_t n_survivors;        /* after S2/S3 = instantiated Gaussians */
+    uint64_t n_pairs;            /* (tile, Gaussian) pairs sorted in S5 */
+    uint32_t n_instances_visible;/* instances whose bounding sphere meets the frustum */
+    uint32_t sort_passes;        /* radix passes run in S5 */
+    float stage_ms[NVGS_NUM_STAGES]; /* filled when flags.profile = 1 (synchronises) */
+    uint64_t kernel_launches;    /* kernels this frame enqueued */
+} nvgs_frame_stats;
+
+/* ------------------------------------------------------------------ context */
+/* Creates a context on CUDA device `device`; `cuda_stream` is a cudaStream_t to enqueue on,
+ * or NULL for a stream the context creates and owns. */
+nvgs_status nvgs_create(nvgs_ctx** out, int device, void* cuda_stream);
+nvgs_status nvgs_destroy(nvgs_ctx* ctx);
+/* Text of the last error on this context ("" if none).  Owned by the context. */
+const char* nvgs_last_error(const nvgs_ctx* ctx);
+/* The cudaStream_t the context enqueues on. */
+void* nvgs_get_stream(const nvgs_ctx* ctx);
+/* Fills the paper's defaults: MLP on, gate on, threshold 0, alpha in [1/255, 0.99],
+ * T stop 1e-4, dilation 0.3, guard band 1.3, black background, 16x16 tiles, device image. */
+void nvgs_default_flags(nvgs_render_flags* flags);
+int nvgs_abi_version(void);
+
+/* ------------------------------------------------------------------ scene */
+/* Copies an asset into device memory (structure-of-arrays, 16-byte vectors), computes its
+ * means' bounding box and the Eq. 1 distance bounds (Sec. 3.1).  Synchronous.  *asset_id
+ * receives the new asset's index (0, 1, ...). */
+nvgs_status nvgs_load_asset(nvgs_ctx* ctx, const nvgs_asset_desc* desc, int* asset_id);
+
+/* Sets the asset's visibility MLP (Sec. 3.2): 32 -> 64 -> 64 -> 64 -> 1 with ReLU.  `weights`
+ * is a HOST array of 10497 floats: W1 (64x32, row = output), b1 (64), W2 (64x64), b2, W3 (64x64),
+ * b3, W4 (1x64), b4 (1).  The library keeps an FP32 copy and, for NVGS_PREC_BF16, BF16 operand
+ * tiles in the tcgen05 shared-memory layout.  Synchronous. */
+nvgs_status nvgs_set_mlp(nvgs_ctx* ctx, int asset_id, const float* weights, int precision);
+
+/* Replaces the instance list (HOST array).  Every asset_id must name a loaded asset. */
+nvgs_status nvgs_set_instances(nvgs_ctx* ctx, const nvgs_instance* instances, int count);
+
+/* Totals of the current scene. */
+nvgs_status nvgs_scene_info(const nvgs_ctx* ctx, int64_t* n_instanced, int* n_assets,
+                            int* n_instances);
+
+/* ------------------------------------------------------------------ per frame */
+/* S1 + S2 only (Sec. 3.3): per instanced Gaussian, the MLP logit (NaN outside the frustum,
+ * +inf where the instance bypasses the MLP) and the keep decision (0/1 bytes: in frustum and
+ * kept).  Both outputs are nullable DEVICE arrays of n_instanced entries.  stats (HOST,
+ * nullable) is written after the call synchronises. */
+nvgs_status nvgs_query_visibility(nvgs_ctx* ctx, const nvgs_camera* cam,
+                                  const nvgs_render_flags* flags, float* logits,
+                                  uint8_t* keep, nvgs_frame_stats* stats);
+
+/* The whole pass S1-S6 for one camera into `image` (H x W x 3 float32 in flags.image_memory;
+ * a HOST image is copied back inside the call).  stats (HOST, nullable) is filled after the
+ * call synchronises. */
+nvgs_status nvgs_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_render_flags* flags,
+                        float* image, nvgs_frame_stats* stats);
+
+/* ------------------------------------------------------------------ per-kernel timing */
+/* Device time of each kernel, accumulated over every nvgs_render call made with
+ * flags.profile = 1 since the last reset (CUDA events bracket each launch on the context's
+ * stream).  Writes up to `cap` entries and the number of distinct kernels to *n. */
+typedef struct {
+    char name[40];
+    uint64_t launches;
+    double total_ms;
+} nvgs_kernel_stat;
+nvgs_status nvgs_kernel_stats(const nvgs_ctx* ctx, nvgs_kernel_stat* out, int cap, int* n);
+nvgs_status nvgs_reset_kernel_stats(nvgs_ctx* ctx);
+
+/* ------------------------------------------------------------------ internals of the last frame */
+/* Device pointers into the library's buffers after the last nvgs_render (valid until the next
+ * call on this context).  For tests and debugging: the survivor list (S3), projected records
+ * (S4), sorted pair values and per-tile ranges (S5). */
+typedef struct {
+    const uint32_t* survivors;   /* 2 x n_survivors: (instance, gaussian) */
+    const float* records;        /* 12 x n_survivors: u, v, conic a, b, c, opacity, depth, -,
+                                    r, g, b, - */
+    const int32_t* tile_rects;   /* 4 x n_survivors: tile x0, y0, x1, y1 (inclusive) */
+    const uint32_t* pair_values; /* n_pairs survivor indices in (tile, depth) order */
+    const uint64_t* pair_keys;   /* n_pairs sorted keys: tile << depth_bits | depth offset */
+    const uint32_t* tile_ranges; /* 2 x n_tiles: [start, end) into pair_values */
+    const float* final_T;        /* W x H, when flags.keep_outputs */
+    const int32_t* n_contrib;    /* W x H, when flags.keep_outputs: fragments blended */
+    uint64_t n_survivors, n_pairs;
+    int32_t tiles_x, tiles_y, tile_size, depth_bits;
+} nvgs_frame_view;
+nvgs_status nvgs_last_frame(const nvgs_ctx* ctx, nvgs_frame_view* out);
+
+/* ------------------------------------------------------------------ building blocks */
+/* Stable LSD radix sort of n (key, value) pairs on the low `key_bits` bits of the keys, in
+ * place, on DEVICE arrays (the library's scratch is used for the ping-pong buffers).  The S5
+ * sort of nvgs_render is this routine. */
+nvgs_status nvgs_sort_pairs(nvgs_ctx* ctx, uint64_t* keys, uint32_t* values, int64_t n,
+                            int key_bits);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NVGS_H */

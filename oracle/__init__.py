@@ -108,6 +108,9 @@ def lib():
                                      vp, vp, vp]
             L.or_composite.argtypes = [vp, C.c_int64, P(OrCamera), P(OrOpts), vp, C.c_int, vp, vp,
                                        vp, vp, C.c_int]
+            L.or_render_rows.restype = C.c_int64
+            L.or_render_rows.argtypes = [P(OrAsset), P(OrInstance), C.c_int, P(OrCamera), P(OrOpts),
+                                         vp, vp, vp, C.c_int, vp, vp, vp]
             L.or_pixel_weights.restype = C.c_int
             L.or_pixel_weights.argtypes = [vp, C.c_int64, P(OrCamera), P(OrOpts), C.c_int,
                                            C.c_int, vp, C.c_int, P(C.c_double)]
@@ -123,8 +126,8 @@ def _ptr(a):
 
 # ----------------------------------------------------------------------------- options
 def opts(alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4, dilation=0.3, guard_band=1.3,
-         bg=(0.0, 0.0, 0.0), tile_size=16, eps_alpha=2e-4, eps_t=2e-4, eps_depth=1e-6,
-         eps_frustum=1e-6, eps_px=1e-3, swap_tol=1e-4) -> OrOpts:
+         bg=(0.0, 0.0, 0.0), tile_size=16, eps_alpha=2e-4, eps_t=2e-4, eps_depth=4e-7,
+         eps_frustum=1e-6, eps_px=1e-3, swap_tol=5e-4) -> OrOpts:
     """Blending constants of Sec. 4.1 and the 3DGS conventions, plus ambiguity-band widths."""
     o = OrOpts()
     o.alpha_min, o.alpha_max, o.t_stop = alpha_min, alpha_max, t_stop
@@ -302,6 +305,24 @@ def render(osc: OracleScene, cam, o=None, keep=None, keep_amb=None, rows=None,
     out = composite(sp, cam, o, rows=rows, want_contrib=want_contrib)
     out["splats"] = sp
     return out
+
+
+def render_rows(osc: OracleScene, cam, rows, o=None, keep=None, keep_amb=None):
+    """Exact FP64 render of the given pixel rows only (memory-light: splats that reach no
+    requested row are projected and dropped)."""
+    o = o or opts()
+    r = np.ascontiguousarray(rows, np.int32)
+    W = int(cam.width)
+    image = np.zeros((r.size, W, 3), np.float64)
+    T = np.zeros((r.size, W), np.float64)
+    amb = np.zeros((r.size, W), np.uint8)
+    k = None if keep is None else np.ascontiguousarray(keep, np.uint8)
+    ka = None if keep_amb is None else np.ascontiguousarray(keep_amb, np.uint8)
+    n = lib().or_render_rows(osc.assets, osc.instances, osc.n_inst, C.byref(camera(cam)), C.byref(o),
+                             _ptr(k), _ptr(ka), _ptr(r), r.size, _ptr(image), _ptr(T), _ptr(amb))
+    if n < 0:
+        raise MemoryError("oracle row render: allocation failed")
+    return dict(image=image, T=T, ambiguous=amb.astype(bool), n_splats=int(n))
 
 
 def pixel_weights(splats, cam, o, x, y, cap=4096):

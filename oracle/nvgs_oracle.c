@@ -498,7 +498,8 @@ typedef struct {
     int32_t inst, g;
     int64_t idx;      /* index into the splat array */
     double alpha;
-    int amb;          /* the splat's own ambiguity (frustum / cull / opacity) */
+    int ghost;        /* not blended (alpha just below alpha_min, or a culled ambiguous splat) */
+    int amb;          /* reaching this fragment makes the pixel ambiguous */
 } fragment;
 
 static int frag_cmp(const void* pa, const void* pb) {
@@ -521,19 +522,77 @@ static double splat_alpha(const or_splat* sp, const or_opts* o, int px, int py, 
     return al < o->alpha_max ? al : o->alpha_max;
 }
 
+/* Front-to-back compositing of one pixel's fragments (Sec. 4.1).  Returns whether a decision
+ * that FP32 could take the other way was reached before the pixel stopped. */
+static int blend_pixel(fragment* fr, size_t nf, const or_splat* splats, const or_opts* o,
+                       double* C, double* T_io, int32_t* n_contrib) {
+    qsort(fr, nf, sizeof(fragment), frag_cmp);
+    double T = 1.0;
+    int amb = 0;
+    for (size_t k = 0; k < nf; k++) {
+        if (fr[k].amb) amb = 1;
+        if (fr[k].ghost) continue;
+        double al = fr[k].alpha;
+        /* next blended neighbour in depth order */
+        size_t k2 = k + 1;
+        while (k2 < nf && fr[k2].ghost) k2++;
+        if (k2 < nf && fr[k2].z - fr[k].z <= o->eps_depth * fr[k].z) {
+            /* FP32 depths may order this pair the other way: blend the pair both ways from the
+             * current T (stop rule included) and count the pixel as ambiguous only if the
+             * colour or the transmittance handed on differs by more than swap_tol. */
+            const double* ca = splats[fr[k].idx].rgb;
+            const double* cb = splats[fr[k2].idx].rgb;
+            double ab[2] = {al, fr[k2].alpha};
+            const double* cc[2] = {ca, cb};
+            double res[2][4];
+            for (int ord = 0; ord < 2; ord++) {
+                double t = T, c3[3] = {0.0, 0.0, 0.0};
+                for (int q = 0; q < 2; q++) {
+                    int e = ord ? 1 - q : q;
+                    double ntq = t * (1.0 - ab[e]);
+                    if (ntq < o->t_stop) { t = 0.0; break; }  /* stopped: nothing passes on */
+                    for (int ch = 0; ch < 3; ch++) c3[ch] += ab[e] * t * cc[e][ch];
+                    t = ntq;
+                }
+                res[ord][0] = c3[0]; res[ord][1] = c3[1]; res[ord][2] = c3[2]; res[ord][3] = t;
+            }
+            double d = 0.0;
+            for (int ch = 0; ch < 4; ch++) d = fmax(d, fabs(res[0][ch] - res[1][ch]));
+            if (d > o->swap_tol) amb = 1;
+        }
+        double nt = T * (1.0 - al);
+        if (fabs(nt - o->t_stop) <= o->eps_t * o->t_stop) amb = 1;
+        if (nt < o->t_stop) break;
+        const double* c = splats[fr[k].idx].rgb;
+        for (int ch = 0; ch < 3; ch++) C[ch] += al * T * c[ch];
+        T = nt;
+        if (n_contrib) {
+#pragma omp atomic
+            n_contrib[fr[k].idx]++;
+        }
+    }
+    *T_io = T;
+    return amb;
+}
+
 /* Composite the listed splats front to back at every requested pixel row.
  *   splats, n_splats : candidates (valid or merely ambiguous); only valid ones are blended
  *   rows, n_rows     : the image rows to produce (all rows if rows == NULL)
  *   image            : n_rows * W * 3 (bg applied)
  *   T_final          : nullable, n_rows * W
  *   n_contrib        : nullable, per splat: number of pixels where it was blended (Sec. 3.1)
- *   amb_px           : nullable, n_rows * W, 1 where a decision sits in an ambiguity band
- *   brute_force      : 1 = ignore the support bbox and test every splat at every pixel */
+ *   amb_px           : nullable, n_rows * W, 1 where a decision that FP32 arithmetic could take
+ *                      the other way is reached before the pixel stops
+ *   brute_force      : 1 = ignore the support bbox and test every splat at every pixel
+ * Candidates are bucketed by row and, inside a row, by 16-pixel column; both only skip pixels
+ * outside a splat's exact-support bounding box (pinned against brute force). */
 void or_composite(const or_splat* splats, int64_t n_splats, const or_camera* cam,
                   const or_opts* o, const int32_t* rows, int n_rows, double* image,
                   double* T_final, int32_t* n_contrib, uint8_t* amb_px, int brute_force) {
     int W = cam->width;
     int nr = rows ? n_rows : cam->height;
+    const int CW = 16;
+    int ncol = (W + CW - 1) / CW;
     /* row buckets: which splats have a (possibly ambiguous) footprint on row y */
     int32_t* row_of = (int32_t*)malloc(sizeof(int32_t) * (size_t)cam->height);
     for (int y = 0; y < cam->height; y++) row_of[y] = -1;
@@ -562,64 +621,108 @@ void or_composite(const or_splat* splats, int64_t n_splats, const or_camera* cam
     {
         size_t cap = 256;
         fragment* fr = (fragment*)malloc(sizeof(fragment) * cap);
+        int64_t* ccnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ncol + 1));
+        int64_t* cfill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ncol + 1));
+        size_t clist_cap = 1024;
+        int64_t* clist = (int64_t*)malloc(sizeof(int64_t) * clist_cap);
 #pragma omp for schedule(dynamic, 1)
         for (int r = 0; r < nr; r++) {
             int y = rows ? rows[r] : r;
+            /* column buckets of this row's candidates */
+            for (int c = 0; c <= ncol; c++) ccnt[c] = 0;
+            for (int64_t q = cnt[r]; q < cnt[r + 1]; q++) {
+                const or_splat* sp = &splats[list[q]];
+                int c0 = brute_force ? 0 : sp->px_min[0] / CW;
+                int c1 = brute_force ? ncol - 1 : sp->px_max[0] / CW;
+                for (int c = c0; c <= c1; c++) ccnt[c + 1]++;
+            }
+            for (int c = 0; c < ncol; c++) ccnt[c + 1] += ccnt[c];
+            if ((size_t)ccnt[ncol] > clist_cap) {
+                clist_cap = (size_t)ccnt[ncol];
+                clist = (int64_t*)realloc(clist, sizeof(int64_t) * clist_cap);
+            }
+            for (int c = 0; c < ncol; c++) cfill[c] = ccnt[c];
+            for (int64_t q = cnt[r]; q < cnt[r + 1]; q++) {
+                const or_splat* sp = &splats[list[q]];
+                int c0 = brute_force ? 0 : sp->px_min[0] / CW;
+                int c1 = brute_force ? ncol - 1 : sp->px_max[0] / CW;
+                for (int c = c0; c <= c1; c++) clist[cfill[c]++] = list[q];
+            }
             for (int x = 0; x < W; x++) {
                 size_t nf = 0;
-                int amb = 0;
-                for (int64_t q = cnt[r]; q < cnt[r + 1]; q++) {
-                    const or_splat* sp = &splats[list[q]];
+                int col = x / CW;
+                for (int64_t q = ccnt[col]; q < ccnt[col + 1]; q++) {
+                    const or_splat* sp = &splats[clist[q]];
                     if (!brute_force && (x < sp->px_min[0] || x > sp->px_max[0])) continue;
                     double power;
                     double al = splat_alpha(sp, o, x, y, &power);
-                    int near_thr = fabs(al - o->alpha_min) <= o->eps_alpha * o->alpha_min;
-                    if (near_thr) amb = 1;
-                    if (power > 0.0 || al < o->alpha_min) continue;
-                    if (sp->ambiguous & 1) amb = 1;
-                    if (!sp->valid) continue;
+                    int near_thr = (sp->valid || (sp->ambiguous & 1)) &&
+                                   fabs(al - o->alpha_min) <= o->eps_alpha * o->alpha_min;
+                    int blend = sp->valid && power <= 0.0 && al >= o->alpha_min;
+                    if (!blend && !near_thr && !((sp->ambiguous & 1) && al >= o->alpha_min)) continue;
                     if (nf == cap) { cap *= 2; fr = (fragment*)realloc(fr, sizeof(fragment) * cap); }
                     fr[nf].z = sp->depth; fr[nf].inst = sp->instance; fr[nf].g = sp->gaussian;
-                    fr[nf].idx = list[q]; fr[nf].alpha = al; fr[nf].amb = 0;
+                    fr[nf].idx = clist[q]; fr[nf].alpha = al;
+                    fr[nf].ghost = !blend;
+                    fr[nf].amb = near_thr || (sp->ambiguous & 1);
                     nf++;
                 }
-                qsort(fr, nf, sizeof(fragment), frag_cmp);
                 double T = 1.0, C[3] = {0.0, 0.0, 0.0};
-                for (size_t k = 0; k < nf; k++) {
-                    double al = fr[k].alpha;
-                    if (k + 1 < nf && fr[k + 1].z - fr[k].z <= o->eps_depth * fr[k].z) {
-                        /* FP32 depths may order this pair the other way.  Swapping two
-                         * neighbours changes the pixel by alpha_a alpha_b T (c_a - c_b) and
-                         * leaves the T after both unchanged, so only a visible change counts. */
-                        const double* ca = splats[fr[k].idx].rgb;
-                        const double* cb = splats[fr[k + 1].idx].rgb;
-                        double dc = 0.0;
-                        for (int ch = 0; ch < 3; ch++)
-                            dc = fabs(ca[ch] - cb[ch]) > dc ? fabs(ca[ch] - cb[ch]) : dc;
-                        double t2 = T * (1.0 - al) * (1.0 - fr[k + 1].alpha);
-                        if (al * fr[k + 1].alpha * T * dc > o->swap_tol || t2 < 10.0 * o->t_stop)
-                            amb = 1;
-                    }
-                    double nt = T * (1.0 - al);
-                    if (fabs(nt - o->t_stop) <= o->eps_t * o->t_stop) amb = 1;
-                    if (nt < o->t_stop) break;
-                    const or_splat* sp = &splats[fr[k].idx];
-                    for (int ch = 0; ch < 3; ch++) C[ch] += al * T * sp->rgb[ch];
-                    T = nt;
-                    if (n_contrib) {
-#pragma omp atomic
-                        n_contrib[fr[k].idx]++;
-                    }
-                }
+                int amb = blend_pixel(fr, nf, splats, o, C, &T, n_contrib);
                 int64_t p = (int64_t)r * W + x;
                 for (int ch = 0; ch < 3; ch++) image[3 * p + ch] = C[ch] + T * o->bg[ch];
                 if (T_final) T_final[p] = T;
                 if (amb_px) amb_px[p] = (uint8_t)amb;
             }
         }
-        free(fr);
+        free(fr); free(ccnt); free(cfill); free(clist);
     }
     free(row_of); free(cnt); free(list); free(fill);
+}
+
+/* Exact render of selected pixel rows of a large scene without materialising every splat:
+ * each instanced Gaussian is projected (in parallel); only those whose footprint reaches one of
+ * the rows are kept, then composited as in or_composite.  Returns the number of kept splats, or
+ * -1 on allocation failure.  keep / keep_amb are nullable per-instanced culling decisions. */
+int64_t or_render_rows(const or_asset* assets, const or_instance* inst, int n_inst,
+                       const or_camera* cam, const or_opts* o, const uint8_t* keep,
+                       const uint8_t* keep_amb, const int32_t* rows, int n_rows, double* image,
+                       double* T_final, uint8_t* amb_px) {
+    uint8_t* on_row = (uint8_t*)calloc((size_t)cam->height, 1);
+    for (int r = 0; r < n_rows; r++) on_row[rows[r]] = 1;
+    int64_t total = 0;
+    for (int i = 0; i < n_inst; i++) total += assets[inst[i].asset_id].n;
+    uint8_t* hit = (uint8_t*)calloc((size_t)(total > 0 ? total : 1), 1);
+    if (!hit) { free(on_row); return -1; }
+    for (int i = 0; i < n_inst; i++) {
+        const or_asset* a = &assets[inst[i].asset_id];
+        int64_t off = instance_offset(assets, inst, i);
+#pragma omp parallel for schedule(dynamic, 4096)
+        for (int64_t g = 0; g < a->n; g++) {
+            or_splat sp;
+            project_one(a, &inst[i], cam, o, i, g, keep ? keep[off + g] : 1,
+                        keep_amb ? keep_amb[off + g] : 0, &sp);
+            if (!sp.valid && !(sp.ambiguous & 1)) continue;
+            for (int y = sp.px_min[1]; y <= sp.px_max[1]; y++)
+                if (on_row[y]) { hit[off + g] = 1; break; }
+        }
+    }
+    int64_t n_hit = 0;
+    for (int64_t k = 0; k < total; k++) n_hit += hit[k];
+    or_splat* sp = (or_splat*)malloc(sizeof(or_splat) * (size_t)(n_hit > 0 ? n_hit : 1));
+    if (!sp) { free(on_row); free(hit); return -1; }
+    int64_t w = 0;
+    for (int i = 0; i < n_inst; i++) {
+        const or_asset* a = &assets[inst[i].asset_id];
+        int64_t off = instance_offset(assets, inst, i);
+        for (int64_t g = 0; g < a->n; g++)
+            if (hit[off + g])
+                project_one(a, &inst[i], cam, o, i, g, keep ? keep[off + g] : 1,
+                            keep_amb ? keep_amb[off + g] : 0, &sp[w++]);
+    }
+    or_composite(sp, n_hit, cam, o, rows, n_rows, image, T_final, NULL, amb_px, 0);
+    free(sp); free(hit); free(on_row);
+    return n_hit;
 }
 
 /* Contributions alpha_k T_k of every blended fragment at one pixel, in blend order, plus the
@@ -636,7 +739,7 @@ int or_pixel_weights(const or_splat* splats, int64_t n_splats, const or_camera* 
         double al = splat_alpha(sp, o, x, y, &power);
         if (power > 0.0 || al < o->alpha_min) continue;
         fr[nf].z = sp->depth; fr[nf].inst = sp->instance; fr[nf].g = sp->gaussian;
-        fr[nf].idx = s; fr[nf].alpha = al; fr[nf].amb = 0;
+        fr[nf].idx = s; fr[nf].alpha = al; fr[nf].amb = 0; fr[nf].ghost = 0;
         nf++;
     }
     qsort(fr, nf, sizeof(fragment), frag_cmp);

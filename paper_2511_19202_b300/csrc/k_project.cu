@@ -1,0 +1,172 @@
+// S4: EWA projection of the surviving instanced Gaussians to 2D conics plus SH colour
+// (NVGS Sec. 3.3 hands the survivors to the original 3DGS tiled pipeline).
+//
+// One thread per survivor.  Per survivor it reads 16 B mean/opacity + 16 B log-scale + 16 B
+// quaternion + 16..192 B of SH (all 16-byte vector loads) and writes one 48-byte record, a
+// 16-byte tile rectangle and a 4-byte tile count.
+//
+// Conventions (3DGS):  Sigma = R(q) diag(e^{2 ls}) R(q)^T;  Sigma_cam = s^2 W Sigma W^T with
+// W = R_cam R_inst;  J is the pinhole Jacobian at the mean with x/z, y/z clamped to the guard
+// band;  Sigma_2D = J Sigma_cam J^T + dilation I.  The support is the exact ellipse where
+// opacity * exp(power) >= alpha_min, i.e. d^T Sigma_2D^{-1} d <= 2 ln(opacity / alpha_min); its
+// axis-aligned half-extents are sqrt(k Sigma_2D,xx) and sqrt(k Sigma_2D,yy), so a splat is
+// binned to exactly the tiles whose pixel centres it can reach.
+#include "nvgs_internal.cuh"
+
+namespace nvgs {
+
+// Real spherical harmonics up to degree 3 (the 3DGS sign convention), Y[(l+1)^2].
+// Constants: 1/(2 sqrt pi); sqrt(3/(4 pi)); sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4;
+// sqrt(35/(2 pi))/4, sqrt(105/pi)/2, sqrt(21/(2 pi))/4, sqrt(7/pi)/4, sqrt(105/pi)/4.
+__device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, float* Y) {
+    Y[0] = 0.28209479177387814f;
+    if (deg < 1) return;
+    Y[1] = -0.4886025119029199f * y;
+    Y[2] = 0.4886025119029199f * z;
+    Y[3] = -0.4886025119029199f * x;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = 1.0925484305920792f * x * y;
+    Y[5] = -1.0925484305920792f * y * z;
+    Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+    Y[7] = -1.0925484305920792f * x * z;
+    Y[8] = 0.5462742152960396f * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = -0.5900435899266435f * y * (3.0f * xx - yy);
+    Y[10] = 2.890611442640554f * x * y * z;
+    Y[11] = -0.4570457994644658f * y * (4.0f * zz - xx - yy);
+    Y[12] = 0.3731763325901154f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -0.4570457994644658f * x * (4.0f * zz - xx - yy);
+    Y[14] = 1.445305721320277f * z * (xx - yy);
+    Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
+}
+
+__global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv, uint32_t n,
+                                                 const FrameInst* __restrict__ fis,
+                                                 const AssetDev* __restrict__ assets, CamParams cam,
+                                                 float4* __restrict__ rec, int4* __restrict__ rects,
+                                                 uint32_t* __restrict__ counts,
+                                                 uint32_t* __restrict__ depth_minmax) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = false;
+    float depth = 0.0f;
+    if (i < n) {
+        const uint2 e = surv[i];
+        const FrameInst& fi = fis[e.x];
+        const AssetDev& a = assets[fi.asset];
+        const uint32_t g = e.y;
+        const float4 m = __ldg(&a.mean_op[g]);
+        const float4 ls = __ldg(&a.scale[g]);
+        const float4 qr = __ldg(&a.quat[g]);
+
+        const float3 pc = cam_point(fi, m.x, m.y, m.z);
+        const float x = pc.x, y = pc.y, z = pc.z;
+        const float iz = 1.0f / z;
+        const float tx = fminf(cam.lim_x, fmaxf(-cam.lim_x, x * iz));
+        const float ty = fminf(cam.lim_y, fmaxf(-cam.lim_y, y * iz));
+        // A = J W (2 x 3)
+        const float jx = cam.fx * iz, jy = cam.fy * iz;
+        float A0[3], A1[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            A0[k] = jx * fmaf(-tx, fi.W[6 + k], fi.W[k]);
+            A1[k] = jy * fmaf(-ty, fi.W[6 + k], fi.W[3 + k]);
+        }
+        // R(q) with q normalised
+        const float qn = rsqrtf(qr.x * qr.x + qr.y * qr.y + qr.z * qr.z + qr.w * qr.w);
+        const float qw = qr.x * qn, qx = qr.y * qn, qy = qr.z * qn, qz = qr.w * qn;
+        const float Rq[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                             2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                             2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+        const float sc[3] = {fi.s * expf(ls.x), fi.s * expf(ls.y), fi.s * expf(ls.z)};
+        // B = A R(q) diag(s e^ls);  Sigma_2D = B B^T + dilation I
+        float B0[3], B1[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            B0[k] = (A0[0] * Rq[k] + A0[1] * Rq[3 + k] + A0[2] * Rq[6 + k]) * sc[k];
+            B1[k] = (A1[0] * Rq[k] + A1[1] * Rq[3 + k] + A1[2] * Rq[6 + k]) * sc[k];
+        }
+        const float ca = fmaf(B0[0], B0[0], fmaf(B0[1], B0[1], B0[2] * B0[2])) + cam.dilation;
+        const float cb = fmaf(B0[0], B1[0], fmaf(B0[1], B1[1], B0[2] * B1[2]));
+        const float cc = fmaf(B1[0], B1[0], fmaf(B1[1], B1[1], B1[2] * B1[2])) + cam.dilation;
+        float det = ca * cc - cb * cb;
+        if (!(det > 1e-3f * ca * cc))   // near-degenerate: cancellation guard in FP64
+            det = (float)((double)ca * (double)cc - (double)cb * (double)cb);
+
+        const float op = 1.0f / (1.0f + expf(-m.w));
+        const float kk = 2.0f * (logf(op) - logf(cam.alpha_min));
+        int4 r = make_int4(1, 1, 0, 0);
+        uint32_t cnt = 0;
+        const float u = fmaf(cam.fx, x * iz, cam.cx);
+        const float v = fmaf(cam.fy, y * iz, cam.cy);
+        const float xe = sqrtf(kk * ca), ye = sqrtf(kk * cc);
+        // non-finite geometry (degenerate input) is never binned
+        if (kk > 0.0f && det > 0.0f && isfinite(u) && isfinite(v) && isfinite(xe) &&
+            isfinite(ye) && isfinite(det)) {
+            float x0 = fmaxf(ceilf(u - xe - 0.5f), 0.0f);
+            float x1 = fminf(floorf(u + xe - 0.5f), (float)(cam.W - 1));
+            float y0 = fmaxf(ceilf(v - ye - 0.5f), 0.0f);
+            float y1 = fminf(floorf(v + ye - 0.5f), (float)(cam.H - 1));
+            if (x0 <= x1 && y0 <= y1) {
+                const int ts = cam.tile_size;
+                r = make_int4((int)x0 / ts, (int)y0 / ts, (int)x1 / ts, (int)y1 / ts);
+                cnt = (uint32_t)((r.z - r.x + 1) * (r.w - r.y + 1));
+                valid = true;
+                depth = z;
+            }
+        }
+        rects[i] = r;
+        counts[i] = cnt;
+
+        // colour at the local-frame direction from the camera to the mean
+        float dx = m.x - fi.cam_local[0], dy = m.y - fi.cam_local[1], dz = m.z - fi.cam_local[2];
+        const float dn = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        dx *= dn; dy *= dn; dz *= dn;
+        float Y[16];
+        sh_eval(a.sh_degree, dx, dy, dz, Y);
+        const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
+        const float4* __restrict__ shp = reinterpret_cast<const float4*>(a.sh + (size_t)g * a.sh_stride);
+        float col[3] = {0.5f, 0.5f, 0.5f};
+        float buf[48];
+        const int nv = (3 * K + 3) / 4;
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            if (k < nv) {
+                float4 t = __ldg(&shp[k]);
+                buf[4 * k] = t.x; buf[4 * k + 1] = t.y; buf[4 * k + 2] = t.z; buf[4 * k + 3] = t.w;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            if (k < K) {
+                col[0] = fmaf(Y[k], buf[3 * k], col[0]);
+                col[1] = fmaf(Y[k], buf[3 * k + 1], col[1]);
+                col[2] = fmaf(Y[k], buf[3 * k + 2], col[2]);
+            }
+        }
+        rec[3 * (size_t)i] = make_float4(u, v, cc / det, -cb / det);
+        rec[3 * (size_t)i + 1] = make_float4(ca / det, op, z, 0.0f);
+        rec[3 * (size_t)i + 2] = make_float4(fmaxf(col[0], 0.0f), fmaxf(col[1], 0.0f),
+                                             fmaxf(col[2], 0.0f), 0.0f);
+    }
+    // depth range of the binned splats (positive floats order like their bit patterns)
+    uint32_t lo = valid ? __float_as_uint(depth) : 0xffffffffu;
+    uint32_t hi = valid ? __float_as_uint(depth) : 0u;
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((threadIdx.x & 31) == 0 && hi != 0u) {
+        atomicMin(&depth_minmax[0], lo);
+        atomicMax(&depth_minmax[1], hi);
+    }
+}
+
+cudaError_t launch_project(const uint2* surv, uint32_t n, const FrameInst* fi,
+                           const AssetDev* assets, CamParams cam, float4* rec, int4* rects,
+                           uint32_t* tile_counts, uint32_t* depth_minmax, cudaStream_t s,
+                           LaunchLog* log) {
+    if (n == 0) return cudaSuccess;
+    NVGS_LAUNCH(log, s, "k_project", k_project<<<(n + 255) / 256, 256, 0, s>>>(surv, n, fi, assets, cam, rec, rects, tile_counts, depth_minmax));
+    return cudaGetLastError();
+}
+
+}  // namespace nvgs

@@ -1,0 +1,329 @@
+// Device-wide exclusive scan and the stable LSD radix sort of S5 (NVGS Sec. 3.3 -> 3DGS sorts
+// (tile, depth) keys).  Both are reduce-then-scan designs: no CTA ever waits on another, so
+// there is no inter-CTA spin of any kind.
+//
+// Radix sort, per 8-bit digit pass over tiles of 8192 pairs (512 threads x 16):
+//   1. k_rs_hist:    per-tile digit histogram, stored digit-major: hist[d * n_tiles + tile]
+//   2. exclusive scan of hist -> global start of every (digit, tile) bucket
+//   3. k_rs_scatter: stable rank of every pair inside its tile (warp match + per-warp running
+//      digit counters, each warp owning a contiguous 512-pair slice), a local counting sort in
+//      shared memory, then runs of equal digits written to consecutive global addresses.
+#include "nvgs_internal.cuh"
+
+namespace nvgs {
+
+// ================================================================== exclusive scan (uint32)
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 4096
+
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t* s_warp,
+                                                             uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < 8 ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < 8) s_warp[8 + lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    const uint32_t warp_excl = warp ? s_warp[8 + warp - 1] : 0u;
+    if (total) *total = s_warp[15];
+    return warp_excl + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in,
+                                                              uint64_t n,
+                                                              uint32_t* __restrict__ sums) {
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; j++) {
+        uint64_t i = base + j * kScanThreads + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ uint32_t w[8];
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int k = 0; k < 8; k++) t += w[k];
+        sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile(const uint32_t* __restrict__ in,
+                                                            uint32_t* __restrict__ out, uint64_t n,
+                                                            const uint32_t* __restrict__ offsets,
+                                                            uint32_t* __restrict__ total) {
+    __shared__ uint32_t s[kScanTile + kScanTile / 32];
+    __shared__ uint32_t s_warp[16];
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    // striped, coalesced load; padded index p + p/32 avoids bank conflicts on the blocked read
+#pragma unroll
+    for (int j = 0; j < kScanItems; j++) {
+        const int p = j * kScanThreads + threadIdx.x;
+        const uint64_t i = base + p;
+        s[p + (p >> 5)] = i < n ? in[i] : 0u;
+    }
+    __syncthreads();
+    uint32_t v[kScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; j++) {
+        const int p = threadIdx.x * kScanItems + j;
+        v[j] = s[p + (p >> 5)];
+        sum += v[j];
+    }
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan_256(sum, s_warp, &tot);
+    if (offsets) run += offsets[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < kScanItems; j++) {
+        const int p = threadIdx.x * kScanItems + j;
+        s[p + (p >> 5)] = run;
+        run += v[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kScanItems; j++) {
+        const int p = j * kScanThreads + threadIdx.x;
+        const uint64_t i = base + p;
+        if (i < n) out[i] = s[p + (p >> 5)];
+    }
+    if (total && threadIdx.x == 0) *total = tot;
+}
+
+static uint64_t scan_levels_bytes(uint64_t n) {
+    uint64_t bytes = 0;
+    while (n > (uint64_t)kScanTile) {
+        uint64_t nb = (n + kScanTile - 1) / kScanTile;
+        bytes += 2 * ((nb * 4 + 255) / 256 * 256);
+        n = nb;
+    }
+    return bytes;
+}
+
+size_t scan_scratch_bytes(uint64_t n) { return (size_t)scan_levels_bytes(n) + 256; }
+
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* total,
+                               void* scratch, cudaStream_t s, LaunchLog* log) {
+    if (n == 0) {
+        if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
+        return cudaSuccess;
+    }
+    if (n <= (uint64_t)kScanTile) {
+        NVGS_LAUNCH(log, s, "k_scan_tile", k_scan_tile<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total));
+        return cudaGetLastError();
+    }
+    const uint64_t nb = (n + kScanTile - 1) / kScanTile;
+    const uint64_t seg = (nb * 4 + 255) / 256 * 256;
+    uint32_t* sums = (uint32_t*)scratch;
+    uint32_t* sums_scan = (uint32_t*)((char*)scratch + seg);
+    void* rest = (char*)scratch + 2 * seg;
+    NVGS_LAUNCH(log, s, "k_scan_reduce", k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = exclusive_scan_u32(sums, sums_scan, nb, total, rest, s, log);
+    if (e != cudaSuccess) return e;
+    NVGS_LAUNCH(log, s, "k_scan_tile", k_scan_tile<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums_scan, nullptr));
+    return cudaGetLastError();
+}
+
+// ================================================================== radix sort
+constexpr int kRsThreads = 512;
+constexpr int kRsItems = 16;
+constexpr int kRsTile = kRsThreads * kRsItems;  // 8192
+constexpr int kRsWarps = kRsThreads / 32;       // 16
+constexpr int kRsSmem = kRsWarps * 256 * 4 + kRsTile * 8 + kRsTile * 4 + 2 * 256 * 4;
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const unsigned long long* __restrict__ keys,
+                                                        uint64_t n, int shift, uint32_t n_tiles,
+                                                        uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[kRsWarps][256];
+    const int warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) (&h[0][0])[k] = 0u;
+    __syncthreads();
+    const uint64_t base = (uint64_t)blockIdx.x * kRsTile;
+#pragma unroll 4
+    for (int j = 0; j < kRsItems; j++) {
+        const uint64_t i = base + (uint64_t)j * kRsThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kRsWarps; w++) s += h[w][threadIdx.x];
+        hist[(uint64_t)threadIdx.x * n_tiles + blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(
+    const unsigned long long* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+    unsigned long long* __restrict__ keys_out, uint32_t* __restrict__ vals_out, uint64_t n,
+    int shift, uint32_t n_tiles, const uint32_t* __restrict__ hist_scan) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* cnt = (uint32_t*)smem;                                   // [16 warps][256]
+    unsigned long long* s_keys = (unsigned long long*)(smem + kRsWarps * 256 * 4);
+    uint32_t* s_vals = (uint32_t*)(smem + kRsWarps * 256 * 4 + kRsTile * 8);
+    uint32_t* d_local = s_vals + kRsTile;                              // [256] tile-local start
+    uint32_t* d_global = d_local + 256;                                // [256] global start
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) cnt[k] = 0u;
+    __syncthreads();
+
+    const uint64_t base = (uint64_t)blockIdx.x * kRsTile;
+    const uint64_t tile_n64 = n - base < (uint64_t)kRsTile ? n - base : (uint64_t)kRsTile;
+    const int tile_n = (int)tile_n64;
+    unsigned long long key[kRsItems];
+    uint32_t val[kRsItems];
+    uint32_t digit[kRsItems];
+    uint32_t rank[kRsItems];
+    // each warp ranks its own contiguous slice [warp*512, warp*512 + 512) in order
+#pragma unroll
+    for (int r = 0; r < kRsItems; r++) {
+        const int p = warp * (kRsItems * 32) + r * 32 + lane;
+        const bool ok = p < tile_n;
+        key[r] = ok ? keys_in[base + p] : 0ull;
+        val[r] = ok ? vals_in[base + p] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kRsItems; r++) {
+        const int p = warp * (kRsItems * 32) + r * 32 + lane;
+        const bool ok = p < tile_n;
+        const uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u + lane;  // unmatched
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = ok ? cnt[warp * 256 + d] : 0u;
+        __syncwarp();
+        if (ok && (peers & lt) == 0u) cnt[warp * 256 + d] = before + __popc(peers);
+        __syncwarp();
+        digit[r] = d;
+        rank[r] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, then over digits (tile-local bucket starts)
+    if (threadIdx.x < 256) {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kRsWarps; w++) {
+            const uint32_t c = cnt[w * 256 + d];
+            cnt[w * 256 + d] = run;
+            run += c;
+        }
+        d_local[d] = run;   // digit total for now
+        d_global[d] = hist_scan[(uint64_t)d * n_tiles + blockIdx.x];
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of the 256 digit totals by one warp
+        uint32_t v[8], s = 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) { v[k] = d_local[lane * 8 + k]; s += v[k]; }
+        uint32_t x = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        uint32_t run = x - s;
+#pragma unroll
+        for (int k = 0; k < 8; k++) { d_local[lane * 8 + k] = run; run += v[k]; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRsItems; r++) {
+        const int p = warp * (kRsItems * 32) + r * 32 + lane;
+        if (p < tile_n) {
+            const uint32_t d = digit[r];
+            const uint32_t lp = d_local[d] + cnt[warp * 256 + d] + rank[r];
+            s_keys[lp] = key[r];
+            s_vals[lp] = val[r];
+        }
+    }
+    __syncthreads();
+    // the tile is now sorted by digit in shared memory; stream it out in order
+#pragma unroll 4
+    for (int j = 0; j < kRsItems; j++) {
+        const int p = j * kRsThreads + threadIdx.x;
+        if (p < tile_n) {
+            const unsigned long long k = s_keys[p];
+            const uint32_t d = (uint32_t)(k >> shift) & 255u;
+            const uint64_t g = (uint64_t)d_global[d] + (uint32_t)(p - d_local[d]);
+            keys_out[g] = k;
+            vals_out[g] = s_vals[p];
+        }
+    }
+}
+
+size_t radix_scratch_bytes(uint64_t n) {
+    const uint64_t tiles = (n + kRsTile - 1) / kRsTile;
+    const uint64_t h = (256 * tiles * 4 + 255) / 256 * 256;
+    return (size_t)(2 * h + scan_scratch_bytes(256 * tiles));
+}
+
+cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* values,
+                             unsigned long long* keys_alt, uint32_t* values_alt, uint64_t n,
+                             int key_bits, void* scratch, cudaStream_t s, LaunchLog* log,
+                             int* passes_out, int copy_back, int* result_in_alt) {
+    int passes = key_bits <= 0 ? 0 : (key_bits + 7) / 8;
+    if (n <= 1) passes = 0;
+    if (passes_out) *passes_out = passes;
+    if (result_in_alt) *result_in_alt = 0;
+    if (passes == 0) return cudaSuccess;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kRsSmem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const uint64_t tiles = (n + kRsTile - 1) / kRsTile;
+    const uint64_t h = (256 * tiles * 4 + 255) / 256 * 256;
+    uint32_t* hist = (uint32_t*)scratch;
+    uint32_t* hist_scan = (uint32_t*)((char*)scratch + h);
+    void* scan_scratch = (char*)scratch + 2 * h;
+    unsigned long long* kin = keys;
+    uint32_t* vin = values;
+    unsigned long long* kout = keys_alt;
+    uint32_t* vout = values_alt;
+    for (int p = 0; p < passes; p++) {
+        const int shift = 8 * p;
+        NVGS_LAUNCH(log, s, "k_rs_hist", k_rs_hist<<<(unsigned)tiles, kRsThreads, 0, s>>>(kin, n, shift, (uint32_t)tiles, hist));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = exclusive_scan_u32(hist, hist_scan, 256 * tiles, nullptr, scan_scratch, s, log);
+        if (e != cudaSuccess) return e;
+        NVGS_LAUNCH(log, s, "k_rs_scatter", k_rs_scatter<<<(unsigned)tiles, kRsThreads, kRsSmem, s>>>(kin, vin, kout, vout, n, shift, (uint32_t)tiles, hist_scan));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        unsigned long long* tk = kin; kin = kout; kout = tk;
+        uint32_t* tv = vin; vin = vout; vout = tv;
+    }
+    if (kin != keys) {  // odd number of passes: the result sits in the alternate buffers
+        if (!copy_back) {
+            if (result_in_alt) *result_in_alt = 1;
+            return cudaSuccess;
+        }
+        cudaError_t e = cudaMemcpyAsync(keys, kin, n * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(values, vin, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace nvgs

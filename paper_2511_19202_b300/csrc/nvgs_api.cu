@@ -1,0 +1,751 @@
+// C ABI of libnvgs: context, scene upload and the per-frame orchestration of S1-S6 (NVGS
+// Sec. 3.3).  Host code here only validates arguments, sizes buffers and enqueues kernels; every
+// step of the pass itself runs in the kernels of the k_*.cu files.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "nvgs_internal.cuh"
+
+using namespace nvgs;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+struct AssetStore {
+    DevBuf mean_op, scale, quat, sh, w_fp32, w_tc;
+    AssetDev dev{};
+    int precision = -1;  // -1: no MLP
+};
+
+}  // namespace
+
+struct nvgs_ctx {
+    int device = 0;
+    int num_sms = 148;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+
+    std::vector<AssetStore> assets;
+    DevBuf assets_dev;
+    bool assets_dirty = true;
+
+    std::vector<nvgs_instance> instances;
+    std::vector<int64_t> inst_offset_h;
+    DevBuf inst_raw, inst_offset, chunks;
+    int n_chunks = 0;
+    int64_t n_instanced = 0;
+
+    // per-frame buffers
+    DevBuf frame_inst, bits, chunk_counts, chunk_offsets, vis_list, keep_bits, logits_tmp,
+        block_counts, block_offsets, surv, rec, rects, tile_counts, tile_offsets, keys, vals,
+        keys_alt, vals_alt, ranges, scratch, counters, image_tmp, final_T, n_contrib;
+    uint32_t* h_counters = nullptr;  // pinned mirror of counters
+
+    cudaEvent_t ev[NVGS_NUM_STAGES + 1] = {};
+    bool events_ready = false;
+
+    // last frame
+    nvgs_frame_view last{};
+    LaunchLog log;
+    // per-kernel device time accumulated over profiled frames
+    std::vector<std::string> kname;
+    std::vector<uint64_t> kcount;
+    std::vector<double> kms;
+};
+
+namespace {
+
+nvgs_status fail(nvgs_ctx* c, nvgs_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? NVGS_ERR_OOM : NVGS_ERR_CUDA,   \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,      \
+                        __LINE__);                                                            \
+    } while (0)
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.cap >= bytes) return cudaSuccess;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        if (e != cudaSuccess) return e;
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    size_t want = bytes + bytes / 4;
+    want = (want + 255) / 256 * 256;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return e;
+    }
+    b.cap = want;
+    return cudaSuccess;
+}
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+template <class T>
+T* P(DevBuf& b) { return reinterpret_cast<T*>(b.p); }
+
+int bit_width(uint64_t v) {
+    int b = 0;
+    while (v) { b++; v >>= 1; }
+    return b;
+}
+
+nvgs_status validate_flags(nvgs_ctx* ctx, const nvgs_render_flags* f) {
+    if (!f) return fail(ctx, NVGS_ERR_INVALID_ARG, "flags is NULL");
+    if (f->tile_size != 8 && f->tile_size != 16 && f->tile_size != 32)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "tile_size must be 8, 16 or 32 (got %d)", f->tile_size);
+    if (!(f->alpha_min > 0.f && f->alpha_min < 1.f) || !(f->alpha_max > 0.f && f->alpha_max <= 1.f) ||
+        !(f->t_stop >= 0.f && f->t_stop < 1.f) || !(f->dilation >= 0.f) || !(f->guard_band > 0.f))
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "blending constants out of range");
+    if (f->image_memory != NVGS_MEM_HOST && f->image_memory != NVGS_MEM_DEVICE)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "image_memory must be NVGS_MEM_HOST or NVGS_MEM_DEVICE");
+    return NVGS_OK;
+}
+
+nvgs_status make_cam(nvgs_ctx* ctx, const nvgs_camera* c, const nvgs_render_flags* f, CamParams* cp) {
+    if (!c) return fail(ctx, NVGS_ERR_INVALID_ARG, "camera is NULL");
+    if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "image size %dx%d out of range", c->width, c->height);
+    if (!(c->fx > 0.f) || !(c->fy > 0.f) || !(c->z_near > 0.f) || !std::isfinite(c->cx) ||
+        !std::isfinite(c->cy))
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "camera intrinsics out of range");
+    for (int k = 0; k < 9; k++)
+        if (!std::isfinite(c->R[k])) return fail(ctx, NVGS_ERR_INVALID_ARG, "camera R not finite");
+    for (int k = 0; k < 3; k++)
+        if (!std::isfinite(c->t[k])) return fail(ctx, NVGS_ERR_INVALID_ARG, "camera t not finite");
+    CamParams p{};
+    memcpy(p.R, c->R, sizeof p.R);
+    memcpy(p.t, c->t, sizeof p.t);
+    p.fx = c->fx; p.fy = c->fy; p.cx = c->cx; p.cy = c->cy;
+    p.W = c->width; p.H = c->height; p.z_near = c->z_near;
+    p.lim_x = (float)(f->guard_band * (double)c->width / (2.0 * c->fx));
+    p.lim_y = (float)(f->guard_band * (double)c->height / (2.0 * c->fy));
+    p.f_r = (float)(2.0 * c->fx / c->width);
+    p.alpha_min = f->alpha_min; p.alpha_max = f->alpha_max; p.t_stop = f->t_stop;
+    p.dilation = f->dilation;
+    for (int k = 0; k < 3; k++) p.bg[k] = f->bg[k];
+    p.tile_size = f->tile_size;
+    p.tiles_x = (c->width + f->tile_size - 1) / f->tile_size;
+    p.tiles_y = (c->height + f->tile_size - 1) / f->tile_size;
+    p.mlp_gate = f->mlp_gate ? 1 : 0;
+    *cp = p;
+    return NVGS_OK;
+}
+
+nvgs_status upload_assets(nvgs_ctx* ctx) {
+    if (!ctx->assets_dirty) return NVGS_OK;
+    std::vector<AssetDev> h(ctx->assets.size());
+    for (size_t k = 0; k < ctx->assets.size(); k++) h[k] = ctx->assets[k].dev;
+    CK(ensure(ctx->assets_dev, h.size() * sizeof(AssetDev)));
+    CK(cudaMemcpy(ctx->assets_dev.p, h.data(), h.size() * sizeof(AssetDev), cudaMemcpyHostToDevice));
+    ctx->assets_dirty = false;
+    return NVGS_OK;
+}
+
+struct StageTimer {
+    nvgs_ctx* ctx;
+    bool on;
+    void mark(int k) {
+        if (on) cudaEventRecord(ctx->ev[k], ctx->stream);
+    }
+};
+
+// S1 (+ S2 when use_mlp, + S3): fills ctx->vis_list / surv and the counts.  `query` keeps the
+// per-entry logits for nvgs_query_visibility.
+nvgs_status run_cull(nvgs_ctx* ctx, const CamParams& cp, const nvgs_render_flags* f,
+                     StageTimer& tm, uint32_t* n_vis_out, uint32_t* n_mlp_out, bool want_logits,
+                     bool compact) {
+    cudaStream_t s = ctx->stream;
+    const int n_inst = (int)ctx->instances.size();
+    tm.mark(NVGS_STAGE_SETUP);
+    CK(ensure(ctx->frame_inst, n_inst * sizeof(FrameInst)));
+    CK(launch_instance_setup(P<InstanceRaw>(ctx->inst_raw), n_inst, P<AssetDev>(ctx->assets_dev), cp,
+                             P<FrameInst>(ctx->frame_inst), s, &ctx->log));
+    tm.mark(NVGS_STAGE_CULL);
+    const uint64_t cap = (uint64_t)ctx->n_instanced;
+    CK(ensure(ctx->bits, (size_t)ctx->n_chunks * kChunkWords * 4));
+    CK(ensure(ctx->chunk_counts, (size_t)ctx->n_chunks * 4));
+    CK(ensure(ctx->chunk_offsets, (size_t)ctx->n_chunks * 4));
+    CK(ensure(ctx->vis_list, cap * sizeof(uint2)));
+    CK(ensure(ctx->scratch, std::max(scan_scratch_bytes(ctx->n_chunks), scan_scratch_bytes(cap / kChunk + 1))));
+    CK(launch_frustum(P<Chunk>(ctx->chunks), ctx->n_chunks, P<FrameInst>(ctx->frame_inst),
+                      P<AssetDev>(ctx->assets_dev), cp, P<uint32_t>(ctx->bits),
+                      P<uint32_t>(ctx->chunk_counts), s, &ctx->log));
+    uint32_t* counters = P<uint32_t>(ctx->counters);
+    CK(exclusive_scan_u32(P<uint32_t>(ctx->chunk_counts), P<uint32_t>(ctx->chunk_offsets), ctx->n_chunks,
+                          &counters[0], ctx->scratch.p, s, &ctx->log));
+    CK(launch_expand_chunks(P<Chunk>(ctx->chunks), ctx->n_chunks, P<uint32_t>(ctx->bits),
+                            P<uint32_t>(ctx->chunk_offsets), P<uint2>(ctx->vis_list), s, &ctx->log));
+    CK(cudaMemcpyAsync(ctx->h_counters, counters, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint32_t n_vis = ctx->h_counters[0];
+    *n_vis_out = n_vis;
+    *n_mlp_out = 0;
+    tm.mark(NVGS_STAGE_MLP);
+    if (!f->use_mlp) {
+        tm.mark(NVGS_STAGE_COMPACT);
+        return NVGS_OK;
+    }
+    CK(ensure(ctx->keep_bits, ((size_t)cap / 32 + 2) * 4));
+    if (want_logits) CK(ensure(ctx->logits_tmp, (size_t)cap * 4 + 16));
+    // precision: BF16 tensor-core path only when every asset has BF16 tiles and no override
+    bool tc = f->logits_override == nullptr;
+    for (auto& a : ctx->assets) tc = tc && (a.precision == NVGS_PREC_BF16 || a.precision < 0);
+    bool any_mlp = false;
+    for (auto& a : ctx->assets) any_mlp = any_mlp || a.precision >= 0;
+    tc = tc && any_mlp;
+    if (tc) {
+        CK(launch_mlp_tc(P<uint2>(ctx->vis_list), n_vis, P<FrameInst>(ctx->frame_inst),
+                         P<AssetDev>(ctx->assets_dev), P<int64_t>(ctx->inst_offset),
+                         f->logit_threshold, P<uint32_t>(ctx->keep_bits),
+                         want_logits ? P<float>(ctx->logits_tmp) : nullptr, ctx->num_sms, s,
+                         &ctx->log));
+    } else {
+        CK(launch_mlp_fp32(P<uint2>(ctx->vis_list), n_vis, P<FrameInst>(ctx->frame_inst),
+                           P<AssetDev>(ctx->assets_dev), f->logits_override, P<int64_t>(ctx->inst_offset),
+                           f->logit_threshold, P<uint32_t>(ctx->keep_bits),
+                           want_logits ? P<float>(ctx->logits_tmp) : nullptr, s, &ctx->log));
+    }
+    *n_mlp_out = n_vis;
+    tm.mark(NVGS_STAGE_COMPACT);
+    if (!compact) return NVGS_OK;
+    const uint32_t nb = (n_vis + kChunk - 1) / kChunk;
+    CK(ensure(ctx->block_counts, (size_t)nb * 4 + 16));
+    CK(ensure(ctx->block_offsets, (size_t)nb * 4 + 16));
+    CK(ensure(ctx->surv, cap * sizeof(uint2)));
+    if (n_vis > 0) {
+        CK(launch_bit_counts(P<uint32_t>(ctx->keep_bits), n_vis, P<uint32_t>(ctx->block_counts), s,
+                             &ctx->log));
+        CK(exclusive_scan_u32(P<uint32_t>(ctx->block_counts), P<uint32_t>(ctx->block_offsets), nb,
+                              &counters[1], ctx->scratch.p, s, &ctx->log));
+        CK(launch_compact_list(P<uint2>(ctx->vis_list), n_vis, P<uint32_t>(ctx->keep_bits),
+                               P<uint32_t>(ctx->block_offsets), P<uint2>(ctx->surv), s, &ctx->log));
+    } else {
+        CK(cudaMemsetAsync(&counters[1], 0, 4, s));
+    }
+    return NVGS_OK;
+}
+
+nvgs_status begin_frame(nvgs_ctx* ctx, bool record) {
+    ctx->log.count = 0;
+    ctx->log.n = 0;
+    ctx->log.record = record;
+    if (record && !ctx->log.ready) {
+        for (int k = 0; k < 2 * LaunchLog::kMax; k++) CK(cudaEventCreate(&ctx->log.ev[k]));
+        ctx->log.ready = true;
+    }
+    return NVGS_OK;
+}
+
+// After the frame's final synchronisation: fold the bracketed launches into per-kernel totals.
+void end_frame(nvgs_ctx* ctx) {
+    LaunchLog& L = ctx->log;
+    if (!L.record) return;
+    for (int k = 0; k < L.n; k++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, L.ev[2 * k], L.ev[2 * k + 1]) != cudaSuccess) continue;
+        size_t j = 0;
+        while (j < ctx->kname.size() && ctx->kname[j] != L.names[k]) j++;
+        if (j == ctx->kname.size()) {
+            ctx->kname.emplace_back(L.names[k]);
+            ctx->kcount.push_back(0);
+            ctx->kms.push_back(0.0);
+        }
+        ctx->kcount[j]++;
+        ctx->kms[j] += ms;
+    }
+    L.n = 0;
+}
+
+nvgs_status check_scene(nvgs_ctx* ctx) {
+    if (ctx->instances.empty()) return fail(ctx, NVGS_ERR_INVALID_ARG, "no instances set");
+    return upload_assets(ctx);
+}
+
+}  // namespace
+
+// ============================================================================ context
+extern "C" int nvgs_abi_version(void) { return NVGS_ABI_VERSION; }
+
+extern "C" void nvgs_default_flags(nvgs_render_flags* f) {
+    if (!f) return;
+    memset(f, 0, sizeof *f);
+    f->use_mlp = 1;
+    f->mlp_gate = 1;
+    f->logit_threshold = 0.0f;
+    f->alpha_min = 1.0f / 255.0f;
+    f->alpha_max = 0.99f;
+    f->t_stop = 1e-4f;
+    f->dilation = 0.3f;
+    f->guard_band = 1.3f;
+    f->tile_size = 16;
+    f->image_memory = NVGS_MEM_DEVICE;
+}
+
+extern "C" nvgs_status nvgs_create(nvgs_ctx** out, int device, void* cuda_stream) {
+    if (!out) return NVGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    nvgs_ctx* ctx = new (std::nothrow) nvgs_ctx();
+    if (!ctx) return NVGS_ERR_OOM;
+    int n_dev = 0;
+    cudaError_t e = cudaGetDeviceCount(&n_dev);
+    if (e != cudaSuccess || device < 0 || device >= n_dev) {
+        delete ctx;
+        return e != cudaSuccess ? NVGS_ERR_CUDA : NVGS_ERR_INVALID_ARG;
+    }
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return NVGS_ERR_CUDA; }
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return NVGS_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (ensure(ctx->counters, 64) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_counters, 64) != cudaSuccess) {
+        delete ctx;
+        return NVGS_ERR_OOM;
+    }
+    *out = ctx;
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_destroy(nvgs_ctx* ctx) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& a : ctx->assets) {
+        release(a.mean_op); release(a.scale); release(a.quat); release(a.sh);
+        release(a.w_fp32); release(a.w_tc);
+    }
+    DevBuf* bufs[] = {&ctx->assets_dev, &ctx->inst_raw, &ctx->inst_offset, &ctx->chunks,
+                      &ctx->frame_inst, &ctx->bits, &ctx->chunk_counts, &ctx->chunk_offsets,
+                      &ctx->vis_list, &ctx->keep_bits, &ctx->logits_tmp, &ctx->block_counts,
+                      &ctx->block_offsets, &ctx->surv, &ctx->rec, &ctx->rects, &ctx->tile_counts,
+                      &ctx->tile_offsets, &ctx->keys, &ctx->vals, &ctx->keys_alt, &ctx->vals_alt,
+                      &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
+                      &ctx->n_contrib};
+    for (DevBuf* b : bufs) release(*b);
+    if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+    if (ctx->events_ready)
+        for (auto& ev : ctx->ev) cudaEventDestroy(ev);
+    if (ctx->log.ready)
+        for (int k = 0; k < 2 * LaunchLog::kMax; k++) cudaEventDestroy(ctx->log.ev[k]);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return NVGS_OK;
+}
+
+extern "C" const char* nvgs_last_error(const nvgs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" void* nvgs_get_stream(const nvgs_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+// ============================================================================ scene
+extern "C" nvgs_status nvgs_load_asset(nvgs_ctx* ctx, const nvgs_asset_desc* d, int* asset_id) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (!d || !asset_id) return fail(ctx, NVGS_ERR_INVALID_ARG, "desc / asset_id is NULL");
+    if (d->n < 1 || d->n > (int64_t)1 << 31) return fail(ctx, NVGS_ERR_INVALID_ARG, "asset size %lld out of range", (long long)d->n);
+    if (d->sh_degree < 0 || d->sh_degree > 3) return fail(ctx, NVGS_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    if (!d->means || !d->log_scales || !d->quats || !d->opacity_logits || !d->sh)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "asset array is NULL");
+    if (d->memory != NVGS_MEM_HOST && d->memory != NVGS_MEM_DEVICE)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "asset memory kind invalid");
+    if (!(d->train_fov_x > 0.f && d->train_fov_x < 3.14159f))
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "train_fov_x must be in (0, pi)");
+    CK(cudaSetDevice(ctx->device));
+    const int64_t n = d->n;
+    const int K = (d->sh_degree + 1) * (d->sh_degree + 1);
+    const int stride = (3 * K + 3) / 4 * 4;
+    // stage the five arrays on the host (device inputs are copied down once at load time)
+    std::vector<float> mh(n * 3), lh(n * 3), qh(n * 4), oh(n), sh(n * 3 * K);
+    auto fetch = [&](std::vector<float>& dst, const float* src) -> cudaError_t {
+        if (d->memory == NVGS_MEM_HOST) {
+            memcpy(dst.data(), src, dst.size() * 4);
+            return cudaSuccess;
+        }
+        return cudaMemcpy(dst.data(), src, dst.size() * 4, cudaMemcpyDeviceToHost);
+    };
+    CK(fetch(mh, d->means)); CK(fetch(lh, d->log_scales)); CK(fetch(qh, d->quats));
+    CK(fetch(oh, d->opacity_logits)); CK(fetch(sh, d->sh));
+    std::vector<float4> m4(n), s4(n), q4(n);
+    std::vector<float> shp((size_t)n * stride, 0.0f);
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t g = 0; g < n; g++) {
+        for (int k = 0; k < 3; k++) {
+            double v = mh[3 * g + k];
+            if (!std::isfinite(v)) return fail(ctx, NVGS_ERR_INVALID_ARG, "non-finite mean at %lld", (long long)g);
+            lo[k] = std::min(lo[k], v);
+            hi[k] = std::max(hi[k], v);
+        }
+        m4[g] = make_float4(mh[3 * g], mh[3 * g + 1], mh[3 * g + 2], oh[g]);
+        s4[g] = make_float4(lh[3 * g], lh[3 * g + 1], lh[3 * g + 2], 0.0f);
+        q4[g] = make_float4(qh[4 * g], qh[4 * g + 1], qh[4 * g + 2], qh[4 * g + 3]);
+        memcpy(&shp[(size_t)g * stride], &sh[(size_t)g * 3 * K], 3 * K * sizeof(float));
+    }
+    AssetStore as;
+    CK(ensure(as.mean_op, n * 16)); CK(ensure(as.scale, n * 16)); CK(ensure(as.quat, n * 16));
+    CK(ensure(as.sh, (size_t)n * stride * 4));
+    CK(cudaMemcpy(as.mean_op.p, m4.data(), n * 16, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(as.scale.p, s4.data(), n * 16, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(as.quat.p, q4.data(), n * 16, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(as.sh.p, shp.data(), (size_t)n * stride * 4, cudaMemcpyHostToDevice));
+    AssetDev& a = as.dev;
+    a.mean_op = P<float4>(as.mean_op); a.scale = P<float4>(as.scale); a.quat = P<float4>(as.quat);
+    a.sh = P<float>(as.sh);
+    a.w_fp32 = nullptr; a.w_tc = nullptr;
+    a.n = n; a.sh_degree = d->sh_degree; a.sh_stride = stride;
+    double dd = 0.0;
+    for (int k = 0; k < 3; k++) {
+        double e = hi[k] - lo[k];
+        a.bbox_c[k] = (float)(0.5 * (lo[k] + hi[k]));
+        a.bbox_scale[k] = (float)(e > 0.0 ? 2.0 / e : 2.0);
+        dd += e * e;
+    }
+    // half the box diagonal; a single point (zero box) keeps a tiny positive radius
+    const double r = std::max(0.5 * std::sqrt(dd), 1e-6);
+    // Eq. 1 (Sec. 3.1): d = r / (tan(theta_t / 2) p), p = 0.9 (near) and 0.05 (far)
+    const double th = d->train_fov_x;
+    const double pn = d->p_near > 0.f ? d->p_near : 0.9, pf = d->p_far > 0.f ? d->p_far : 0.05;
+    const double dmin = d->d_min > 0.f ? d->d_min : r / (std::tan(th / 2.0) * pn);
+    const double dmax = d->d_max > 0.f ? d->d_max : r / (std::tan(th / 2.0) * pf);
+    if (!(dmax > dmin && dmin > 0.0)) return fail(ctx, NVGS_ERR_INVALID_ARG, "need 0 < d_min < d_max");
+    a.bbox_r = (float)r;
+    a.d_min = (float)dmin; a.d_max = (float)dmax;
+    a.log_dmin = (float)std::log(dmin);
+    a.inv_log_range = (float)(1.0 / (std::log(dmax) - std::log(dmin)));
+    a.train_focal = (float)(1.0 / std::tan(th / 2.0));
+    ctx->assets.push_back(as);
+    ctx->assets_dirty = true;
+    *asset_id = (int)ctx->assets.size() - 1;
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_set_mlp(nvgs_ctx* ctx, int asset_id, const float* w, int precision) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (asset_id < 0 || asset_id >= (int)ctx->assets.size())
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "asset_id %d out of range", asset_id);
+    if (!w) return fail(ctx, NVGS_ERR_INVALID_ARG, "weights is NULL");
+    if (precision != NVGS_PREC_FP32 && precision != NVGS_PREC_BF16)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "precision must be NVGS_PREC_FP32 or NVGS_PREC_BF16");
+    for (int k = 0; k < kMlpWeights; k++)
+        if (!std::isfinite(w[k])) return fail(ctx, NVGS_ERR_INVALID_ARG, "non-finite weight %d", k);
+    CK(cudaSetDevice(ctx->device));
+    AssetStore& as = ctx->assets[asset_id];
+    CK(ensure(as.w_fp32, kMlpWeights * 4));
+    CK(cudaMemcpy(as.w_fp32.p, w, kMlpWeights * 4, cudaMemcpyHostToDevice));
+    as.dev.w_fp32 = P<float>(as.w_fp32);
+    as.precision = NVGS_PREC_FP32;
+    if (precision == NVGS_PREC_BF16) {
+        const size_t nb = mlp_tc_weight_bytes();
+        std::vector<uint8_t> packed(nb);
+        mlp_tc_pack_weights(w, packed.data());
+        CK(ensure(as.w_tc, nb));
+        CK(cudaMemcpy(as.w_tc.p, packed.data(), nb, cudaMemcpyHostToDevice));
+        as.dev.w_tc = P<uint8_t>(as.w_tc);
+        as.precision = NVGS_PREC_BF16;
+    }
+    ctx->assets_dirty = true;
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_set_instances(nvgs_ctx* ctx, const nvgs_instance* inst, int count) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (count < 1 || !inst) return fail(ctx, NVGS_ERR_INVALID_ARG, "need at least one instance");
+    std::vector<InstanceRaw> raw(count);
+    std::vector<int64_t> off(count);
+    std::vector<Chunk> chunks;
+    int64_t total = 0;
+    for (int i = 0; i < count; i++) {
+        const nvgs_instance& x = inst[i];
+        if (x.asset_id < 0 || x.asset_id >= (int)ctx->assets.size())
+            return fail(ctx, NVGS_ERR_INVALID_ARG, "instance %d: asset_id %d not loaded", i, x.asset_id);
+        if (!(x.s > 0.f) || !std::isfinite(x.s))
+            return fail(ctx, NVGS_ERR_INVALID_ARG, "instance %d: scale must be > 0", i);
+        for (int k = 0; k < 9; k++)
+            if (!std::isfinite(x.R[k])) return fail(ctx, NVGS_ERR_INVALID_ARG, "instance %d: R not finite", i);
+        memcpy(raw[i].R, x.R, sizeof raw[i].R);
+        memcpy(raw[i].t, x.t, sizeof raw[i].t);
+        raw[i].s = x.s;
+        raw[i].asset = x.asset_id;
+        off[i] = total;
+        const int64_t n = ctx->assets[x.asset_id].dev.n;
+        for (int64_t g0 = 0; g0 < n; g0 += kChunk)
+            chunks.push_back(Chunk{i, (int)g0, (int)std::min<int64_t>(kChunk, n - g0), 0});
+        total += n;
+    }
+    if (total >= ((int64_t)1 << 32) - 1)
+        return fail(ctx, NVGS_ERR_CAPACITY, "more than 2^32 instanced Gaussians");
+    CK(cudaSetDevice(ctx->device));
+    CK(ensure(ctx->inst_raw, raw.size() * sizeof(InstanceRaw)));
+    CK(ensure(ctx->inst_offset, off.size() * sizeof(int64_t)));
+    CK(ensure(ctx->chunks, chunks.size() * sizeof(Chunk)));
+    CK(cudaMemcpy(ctx->inst_raw.p, raw.data(), raw.size() * sizeof(InstanceRaw), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->inst_offset.p, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->chunks.p, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+    ctx->instances.assign(inst, inst + count);
+    ctx->inst_offset_h = off;
+    ctx->n_chunks = (int)chunks.size();
+    ctx->n_instanced = total;
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_scene_info(const nvgs_ctx* ctx, int64_t* n_instanced, int* n_assets,
+                                       int* n_instances) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (n_instanced) *n_instanced = ctx->n_instanced;
+    if (n_assets) *n_assets = (int)ctx->assets.size();
+    if (n_instances) *n_instances = (int)ctx->instances.size();
+    return NVGS_OK;
+}
+
+// ============================================================================ per frame
+extern "C" nvgs_status nvgs_query_visibility(nvgs_ctx* ctx, const nvgs_camera* cam,
+                                             const nvgs_render_flags* f, float* logits,
+                                             uint8_t* keep, nvgs_frame_stats* stats) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    nvgs_status st = validate_flags(ctx, f);
+    if (st != NVGS_OK) return st;
+    CamParams cp;
+    if ((st = make_cam(ctx, cam, f, &cp)) != NVGS_OK) return st;
+    CK(cudaSetDevice(ctx->device));
+    if ((st = check_scene(ctx)) != NVGS_OK) return st;
+    begin_frame(ctx, false);
+    StageTimer tm{ctx, false};
+    uint32_t n_vis = 0, n_mlp = 0;
+    if ((st = run_cull(ctx, cp, f, tm, &n_vis, &n_mlp, true, false)) != NVGS_OK) return st;
+    cudaStream_t s = ctx->stream;
+    const uint64_t N = (uint64_t)ctx->n_instanced;
+    if (keep) CK(cudaMemsetAsync(keep, 0, N, s));
+    if (logits) CK(cudaMemsetAsync(logits, 0xff, N * 4, s));  // NaN pattern
+    if (!f->use_mlp) {
+        // keep = in frustum; no logits
+        CK(ensure(ctx->keep_bits, (N / 32 + 2) * 4));
+        CK(cudaMemsetAsync(ctx->keep_bits.p, 0xff, ((size_t)n_vis + 31) / 32 * 4, s));
+    }
+    CK(launch_scatter_visibility(P<uint2>(ctx->vis_list), n_vis, P<uint32_t>(ctx->keep_bits),
+                                 f->use_mlp ? P<float>(ctx->logits_tmp) : nullptr,
+                                 P<int64_t>(ctx->inst_offset), P<FrameInst>(ctx->frame_inst),
+                                 f->use_mlp ? logits : nullptr, keep, s, &ctx->log));
+    CK(cudaStreamSynchronize(s));
+    if (stats) {
+        memset(stats, 0, sizeof *stats);
+        stats->n_instanced = N;
+        stats->n_in_frustum = n_vis;
+        stats->n_mlp_queries = n_mlp;
+        stats->kernel_launches = ctx->log.count;
+    }
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_render_flags* f,
+                                   float* image, nvgs_frame_stats* stats) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    nvgs_status st = validate_flags(ctx, f);
+    if (st != NVGS_OK) return st;
+    if (!image) return fail(ctx, NVGS_ERR_INVALID_ARG, "image is NULL");
+    CamParams cp;
+    if ((st = make_cam(ctx, cam, f, &cp)) != NVGS_OK) return st;
+    CK(cudaSetDevice(ctx->device));
+    if ((st = check_scene(ctx)) != NVGS_OK) return st;
+    cudaStream_t s = ctx->stream;
+    if ((st = begin_frame(ctx, f->profile != 0)) != NVGS_OK) return st;
+    if (f->profile && !ctx->events_ready) {
+        for (auto& ev : ctx->ev) CK(cudaEventCreate(&ev));
+        ctx->events_ready = true;
+    }
+    StageTimer tm{ctx, f->profile != 0};
+
+    uint32_t n_vis = 0, n_mlp = 0;
+    if ((st = run_cull(ctx, cp, f, tm, &n_vis, &n_mlp, false, true)) != NVGS_OK) return st;
+    uint32_t* counters = P<uint32_t>(ctx->counters);
+    uint32_t n_surv = n_vis;
+    const uint2* surv = P<uint2>(ctx->vis_list);
+    if (f->use_mlp) {
+        CK(cudaMemcpyAsync(ctx->h_counters + 1, counters + 1, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        n_surv = ctx->h_counters[1];
+        surv = P<uint2>(ctx->surv);
+    }
+
+    // ---- S4
+    tm.mark(NVGS_STAGE_PROJECT);
+    const uint64_t cap = (uint64_t)ctx->n_instanced;
+    CK(ensure(ctx->rec, cap * 48 + 48));
+    CK(ensure(ctx->rects, cap * 16 + 16));
+    CK(ensure(ctx->tile_counts, cap * 4 + 16));
+    CK(ensure(ctx->tile_offsets, cap * 4 + 16));
+    CK(ensure(ctx->scratch, std::max({scan_scratch_bytes(ctx->n_chunks), scan_scratch_bytes(cap + 1)})));
+    CK(cudaMemsetAsync(counters + 3, 0xff, 4, s));   // depth min bits
+    CK(cudaMemsetAsync(counters + 4, 0x00, 4, s));   // depth max bits
+    CK(launch_project(surv, n_surv, P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev), cp,
+                      P<float4>(ctx->rec), P<int4>(ctx->rects), P<uint32_t>(ctx->tile_counts),
+                      counters + 3, s, &ctx->log));
+
+    // ---- S5: scan of tile counts, binning, sort, ranges
+    tm.mark(NVGS_STAGE_BIN);
+    CK(exclusive_scan_u32(P<uint32_t>(ctx->tile_counts), P<uint32_t>(ctx->tile_offsets), n_surv,
+                          counters + 2, ctx->scratch.p, s, &ctx->log));
+    CK(cudaMemcpyAsync(ctx->h_counters + 2, counters + 2, 12, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint32_t n_pairs = n_surv ? ctx->h_counters[2] : 0u;
+    const uint32_t dlo = ctx->h_counters[3], dhi = ctx->h_counters[4];
+    const int depth_bits = (n_pairs > 0 && dhi >= dlo) ? std::max(1, bit_width(dhi - dlo)) : 1;
+    const int n_tiles = cp.tiles_x * cp.tiles_y;
+    const int tile_bits = std::max(1, bit_width((uint64_t)n_tiles - 1));
+    CK(ensure(ctx->keys, (size_t)n_pairs * 8 + 16));
+    CK(ensure(ctx->vals, (size_t)n_pairs * 4 + 16));
+    CK(ensure(ctx->keys_alt, (size_t)n_pairs * 8 + 16));
+    CK(ensure(ctx->vals_alt, (size_t)n_pairs * 4 + 16));
+    CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
+    if (radix_scratch_bytes(n_pairs) > ctx->scratch.cap) CK(ensure(ctx->scratch, radix_scratch_bytes(n_pairs)));
+    CK(launch_duplicate(P<int4>(ctx->rects), P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets), n_surv,
+                        cp.tiles_x, depth_bits, counters + 3, P<unsigned long long>(ctx->keys),
+                        P<uint32_t>(ctx->vals), s, &ctx->log));
+    tm.mark(NVGS_STAGE_SORT);
+    int passes = 0, in_alt = 0;
+    CK(radix_sort_pairs(P<unsigned long long>(ctx->keys), P<uint32_t>(ctx->vals),
+                        P<unsigned long long>(ctx->keys_alt), P<uint32_t>(ctx->vals_alt), n_pairs,
+                        tile_bits + depth_bits, ctx->scratch.p, s, &ctx->log, &passes, 0, &in_alt));
+    unsigned long long* skeys = in_alt ? P<unsigned long long>(ctx->keys_alt) : P<unsigned long long>(ctx->keys);
+    uint32_t* svals = in_alt ? P<uint32_t>(ctx->vals_alt) : P<uint32_t>(ctx->vals);
+    CK(cudaMemsetAsync(ctx->ranges.p, 0, (size_t)n_tiles * 8, s));
+    CK(launch_tile_ranges(skeys, n_pairs, depth_bits, P<uint32_t>(ctx->ranges), s, &ctx->log));
+
+    // ---- S6
+    tm.mark(NVGS_STAGE_BLEND);
+    const size_t npx = (size_t)cp.W * cp.H;
+    float* img_dev = image;
+    if (f->image_memory == NVGS_MEM_HOST) {
+        CK(ensure(ctx->image_tmp, npx * 12));
+        img_dev = P<float>(ctx->image_tmp);
+    }
+    float* fT = nullptr;
+    int32_t* nc = nullptr;
+    if (f->keep_outputs) {
+        CK(ensure(ctx->final_T, npx * 4));
+        CK(ensure(ctx->n_contrib, npx * 4));
+        fT = P<float>(ctx->final_T);
+        nc = P<int32_t>(ctx->n_contrib);
+    }
+    CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, img_dev, fT, nc, s,
+                    &ctx->log));
+    tm.mark(NVGS_NUM_STAGES);
+    if (f->image_memory == NVGS_MEM_HOST)
+        CK(cudaMemcpyAsync(image, img_dev, npx * 12, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    end_frame(ctx);
+
+    nvgs_frame_view& L = ctx->last;
+    L.survivors = reinterpret_cast<const uint32_t*>(surv);
+    L.records = P<float>(ctx->rec);
+    L.tile_rects = P<int32_t>(ctx->rects);
+    L.pair_values = svals;
+    L.pair_keys = reinterpret_cast<const uint64_t*>(skeys);
+    L.tile_ranges = P<uint32_t>(ctx->ranges);
+    L.final_T = fT;
+    L.n_contrib = nc;
+    L.n_survivors = n_surv;
+    L.n_pairs = n_pairs;
+    L.tiles_x = cp.tiles_x; L.tiles_y = cp.tiles_y; L.tile_size = cp.tile_size;
+    L.depth_bits = depth_bits;
+    if (stats) {
+        memset(stats, 0, sizeof *stats);
+        stats->n_instanced = (uint64_t)ctx->n_instanced;
+        stats->n_in_frustum = n_vis;
+        stats->n_mlp_queries = n_mlp;
+        stats->n_survivors = n_surv;
+        stats->n_pairs = n_pairs;
+        stats->sort_passes = (uint32_t)passes;
+        stats->kernel_launches = ctx->log.count;
+        if (f->profile) {
+            for (int k = 0; k < NVGS_NUM_STAGES; k++) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ctx->ev[k], ctx->ev[k + 1]);
+                stats->stage_ms[k] = ms;
+            }
+        }
+    }
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_last_frame(const nvgs_ctx* ctx, nvgs_frame_view* out) {
+    if (!ctx || !out) return NVGS_ERR_INVALID_ARG;
+    *out = ctx->last;
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_sort_pairs(nvgs_ctx* ctx, uint64_t* keys, uint32_t* values, int64_t n,
+                                       int key_bits) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (n < 0 || n > 0xffffffffLL) return fail(ctx, NVGS_ERR_INVALID_ARG, "n out of range");
+    if (key_bits < 0 || key_bits > 64) return fail(ctx, NVGS_ERR_INVALID_ARG, "key_bits must be 0..64");
+    if (n > 0 && (!keys || !values)) return fail(ctx, NVGS_ERR_INVALID_ARG, "keys / values NULL");
+    CK(cudaSetDevice(ctx->device));
+    if (n <= 1 || key_bits == 0) return NVGS_OK;
+    CK(ensure(ctx->keys_alt, (size_t)n * 8));
+    CK(ensure(ctx->vals_alt, (size_t)n * 4));
+    CK(ensure(ctx->scratch, radix_scratch_bytes((uint64_t)n)));
+    int passes = 0, in_alt = 0;
+    begin_frame(ctx, false);
+    CK(radix_sort_pairs(reinterpret_cast<unsigned long long*>(keys), values,
+                        P<unsigned long long>(ctx->keys_alt), P<uint32_t>(ctx->vals_alt), (uint64_t)n,
+                        key_bits, ctx->scratch.p, ctx->stream, &ctx->log, &passes, 1, &in_alt));
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_kernel_stats(const nvgs_ctx* ctx, nvgs_kernel_stat* out, int cap,
+                                         int* n_out) {
+    if (!ctx || !n_out || cap < 0 || (cap > 0 && !out)) return NVGS_ERR_INVALID_ARG;
+    const int n = (int)ctx->kname.size();
+    for (int k = 0; k < n && k < cap; k++) {
+        memset(out[k].name, 0, sizeof out[k].name);
+        strncpy(out[k].name, ctx->kname[k].c_str(), sizeof out[k].name - 1);
+        out[k].launches = ctx->kcount[k];
+        out[k].total_ms = ctx->kms[k];
+    }
+    *n_out = n;
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_reset_kernel_stats(nvgs_ctx* ctx) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    ctx->kname.clear();
+    ctx->kcount.clear();
+    ctx->kms.clear();
+    return NVGS_OK;
+}

@@ -1,0 +1,198 @@
+// Internal declarations shared by the CUDA translation units of libnvgs (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nvgs.h"
+
+namespace nvgs {
+
+constexpr int kMlpIn = 32;
+constexpr int kMlpHidden = 64;
+constexpr int kMlpWeights = 64 * 32 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 64 + 1;  // 10497
+constexpr int kChunk = 2048;          // Gaussians per S1 work item (64 bitmask words)
+constexpr int kChunkWords = kChunk / 32;
+
+// One asset in device memory (structure of arrays of 16-byte vectors).
+struct AssetDev {
+    const float4* mean_op;    // (x, y, z, opacity logit)
+    const float4* scale;      // (log sx, log sy, log sz, 0)
+    const float4* quat;       // (w, x, y, z)
+    const float* sh;          // n * sh_stride floats, coefficient-major, RGB innermost
+    const float* w_fp32;      // visibility MLP, kMlpWeights floats (nullptr: no MLP)
+    const uint8_t* w_tc;      // BF16 operand tiles for the tcgen05 MLP (nullptr: none)
+    int64_t n;
+    int sh_degree;
+    int sh_stride;            // floats per Gaussian, multiple of 4
+    float bbox_c[3];          // centre of the means' bounding box
+    float bbox_scale[3];      // 2 / extent: p = (mu - c) * scale lies in [-1, 1]
+    float bbox_r;             // half the box diagonal
+    float log_dmin;           // ln d_min
+    float inv_log_range;      // 1 / (ln d_max - ln d_min)
+    float d_min, d_max;
+    float train_focal;        // f_t = 1 / tan(theta_t / 2)
+};
+
+// Per frame, per instance: transforms composed in FP64 on the device, rounded to FP32.
+struct FrameInst {
+    float M[9];               // s * Rc * Ri: local point -> camera frame (linear part)
+    float b[3];               // Rc * t_i + t_c
+    float W[9];               // Rc * Ri (rotation part; covariance uses s^2 W S W^T)
+    float cam_local[3];       // camera centre in the instance's local frame
+    float s;
+    float dist_scale;         // f_t / f_r (Eq. 2; the 1/s is inside cam_local)
+    int asset;
+    int visible;              // bounding sphere meets the guard-band frustum
+    int gated;                // instance closer than d_min: bypass the MLP (Sec. 3.3)
+    int no_mlp;               // the asset has no visibility MLP: rendered unculled
+};
+
+// Camera-space position of a local mean: the small terms M mu first, the instance offset b last,
+// so that points of one instance keep their relative depth to about one FP32 ulp.
+__device__ __forceinline__ float3 cam_point(const FrameInst& f, float mx, float my, float mz) {
+    float x = fmaf(f.M[0], mx, fmaf(f.M[1], my, f.M[2] * mz)) + f.b[0];
+    float y = fmaf(f.M[3], mx, fmaf(f.M[4], my, f.M[5] * mz)) + f.b[1];
+    float z = fmaf(f.M[6], mx, fmaf(f.M[7], my, f.M[8] * mz)) + f.b[2];
+    return make_float3(x, y, z);
+}
+
+// Camera plus blending constants, passed by value to kernels.
+struct CamParams {
+    float R[9], t[3];
+    float fx, fy, cx, cy;
+    int W, H;
+    float z_near;
+    float lim_x, lim_y;       // guard_band * W / (2 fx), guard_band * H / (2 fy)
+    float f_r;                // 2 fx / W
+    float alpha_min, alpha_max, t_stop, dilation;
+    float bg[3];
+    int tile_size, tiles_x, tiles_y;
+    int mlp_gate;             // 1: instances closer than d_min bypass the MLP
+};
+
+// Raw instance as uploaded by nvgs_set_instances.
+struct InstanceRaw {
+    float R[9], t[3], s;
+    int asset;
+};
+
+// S1 work item: up to kChunk consecutive Gaussians of one instance.
+struct Chunk {
+    int inst;
+    int g0;
+    int count;
+    int pad_;
+};
+
+// ------------------------------------------------------------------ launch log
+// Counts kernel launches and, when `record` is set, brackets each launch with CUDA events on
+// its stream so that per-kernel device time can be read back after the frame.
+struct LaunchLog {
+    static constexpr int kMax = 1024;
+    uint64_t count = 0;
+    bool record = false;
+    bool ready = false;
+    int n = 0;
+    cudaEvent_t ev[2 * kMax];
+    const char* names[kMax];
+    void begin(cudaStream_t s, const char* name) {
+        if (record && ready && n < kMax) {
+            names[n] = name;
+            cudaEventRecord(ev[2 * n], s);
+        }
+    }
+    void end(cudaStream_t s) {
+        count++;
+        if (record && ready && n < kMax) {
+            cudaEventRecord(ev[2 * n + 1], s);
+            n++;
+        }
+    }
+};
+#define NVGS_LAUNCH(log, stream, name, ...) \
+    do {                                   \
+        (log)->begin(stream, name);        \
+        __VA_ARGS__;                       \
+        (log)->end(stream);                \
+    } while (0)
+
+// ------------------------------------------------------------------ launchers (stream-ordered)
+// Each returns cudaGetLastError() after its launches and logs them in *log.
+cudaError_t launch_instance_setup(const InstanceRaw* inst, int n_inst, const AssetDev* assets,
+                                  CamParams cam, FrameInst* out, cudaStream_t s, LaunchLog* log);
+
+cudaError_t launch_frustum(const Chunk* chunks, int n_chunks, const FrameInst* fi,
+                           const AssetDev* assets, CamParams cam, uint32_t* bits,
+                           uint32_t* chunk_counts, cudaStream_t s, LaunchLog* log);
+
+// Writes (instance, gaussian) of every set bit, in bit order, at out[chunk_offsets[c] + rank].
+cudaError_t launch_expand_chunks(const Chunk* chunks, int n_chunks, const uint32_t* bits,
+                                 const uint32_t* chunk_offsets, uint2* out, cudaStream_t s,
+                                 LaunchLog* log);
+
+// S2: keep bits over a list of (instance, gaussian) entries.
+cudaError_t launch_mlp_fp32(const uint2* list, uint32_t n, const FrameInst* fi,
+                            const AssetDev* assets, const float* logits_override,
+                            const int64_t* inst_offset, float threshold, uint32_t* keep_bits,
+                            float* logits_out, cudaStream_t s, LaunchLog* log);
+cudaError_t launch_mlp_tc(const uint2* list, uint32_t n, const FrameInst* fi,
+                          const AssetDev* assets, const int64_t* inst_offset, float threshold,
+                          uint32_t* keep_bits, float* logits_out, int num_sms, cudaStream_t s,
+                          LaunchLog* log);
+
+// BF16 operand tiles of one asset's MLP in the tcgen05 shared-memory layout (host-side packing).
+size_t mlp_tc_weight_bytes();
+void mlp_tc_pack_weights(const float* w, uint8_t* out);
+
+// Per-block popcounts of a bitmask over n items (blocks of kChunk items).
+cudaError_t launch_bit_counts(const uint32_t* bits, uint32_t n, uint32_t* block_counts,
+                              cudaStream_t s, LaunchLog* log);
+// Stable compaction of list[i] for set bits i, using block offsets from the scan.
+cudaError_t launch_compact_list(const uint2* list, uint32_t n, const uint32_t* bits,
+                                const uint32_t* block_offsets, uint2* out, cudaStream_t s,
+                                LaunchLog* log);
+
+// Scatter of per-instanced-Gaussian outputs of nvgs_query_visibility.
+cudaError_t launch_scatter_visibility(const uint2* list, uint32_t n, const uint32_t* keep_bits,
+                                      const float* logits, const int64_t* inst_offset,
+                                      const FrameInst* fi, float* out_logits, uint8_t* out_keep,
+                                      cudaStream_t s, LaunchLog* log);
+
+// S4
+cudaError_t launch_project(const uint2* surv, uint32_t n, const FrameInst* fi,
+                           const AssetDev* assets, CamParams cam, float4* rec,
+                           int4* rects, uint32_t* tile_counts, uint32_t* depth_minmax,
+                           cudaStream_t s, LaunchLog* log);
+
+// S5
+cudaError_t launch_duplicate(const int4* rects, const float4* rec, const uint32_t* offsets,
+                             uint32_t n, int tiles_x, int depth_bits, const uint32_t* depth_minmax,
+                             unsigned long long* keys, uint32_t* values, cudaStream_t s,
+                             LaunchLog* log);
+cudaError_t launch_tile_ranges(const unsigned long long* keys, uint32_t n, int depth_bits,
+                               uint32_t* ranges, cudaStream_t s, LaunchLog* log);
+
+// S6
+cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const float4* rec,
+                         CamParams cam, float* image, float* final_T, int32_t* n_contrib,
+                         cudaStream_t s, LaunchLog* log);
+
+// ------------------------------------------------------------------ generic device primitives
+// Exclusive scan of n uint32 values; total (nullable, device) receives the sum.  Needs
+// scan_scratch_bytes(n) bytes of scratch.
+size_t scan_scratch_bytes(uint64_t n);
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* total,
+                               void* scratch, cudaStream_t s, LaunchLog* log);
+
+// Stable LSD radix sort (8-bit digits) of n (key, value) pairs on bits [0, key_bits).
+// keys/values hold the input; the alt buffers must hold n entries each.  With copy_back the
+// result always lands in keys/values; otherwise *result_in_alt tells where it is.
+// Scratch: radix_scratch_bytes(n).
+size_t radix_scratch_bytes(uint64_t n);
+cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* values,
+                             unsigned long long* keys_alt, uint32_t* values_alt, uint64_t n,
+                             int key_bits, void* scratch, cudaStream_t s, LaunchLog* log,
+                             int* passes_out, int copy_back, int* result_in_alt);
+
+}  // namespace nvgs

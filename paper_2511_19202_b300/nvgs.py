@@ -1,0 +1,275 @@
+"""Thin ctypes binding of libnvgs (include/nvgs.h): argument marshalling only.
+
+Every function below has the name of the C entry point it calls.  Pointers may be given as
+torch tensors (their ``data_ptr()``; CUDA tensors for device arguments), numpy arrays (host
+arguments) or ``None`` for NULL.  PyTorch only provides device memory and the stream; all work is
+done by the library's CUDA kernels.  Importing this module raises if the library is missing: there
+is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnvgs.so")
+
+NVGS_OK, NVGS_ERR_INVALID_ARG, NVGS_ERR_OOM, NVGS_ERR_CUDA = 0, 1, 2, 3
+NVGS_ERR_TIMEOUT, NVGS_ERR_CAPACITY, NVGS_ERR_UNSUPPORTED = 4, 5, 6
+NVGS_MEM_HOST, NVGS_MEM_DEVICE = 0, 1
+NVGS_PREC_FP32, NVGS_PREC_BF16 = 0, 1
+NVGS_NUM_STAGES = 8
+STAGE_NAMES = ("setup", "cull", "mlp", "compact", "project", "bin", "sort", "blend")
+MLP_WEIGHTS = 10497
+
+
+class NvgsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"nvgs status {status}: {msg}")
+        self.status = status
+
+
+class AssetDesc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("memory", C.c_int32),
+                ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("train_fov_x", C.c_float),
+                ("d_min", C.c_float), ("d_max", C.c_float), ("p_near", C.c_float),
+                ("p_far", C.c_float)]
+
+
+class Instance(C.Structure):
+    _fields_ = [("asset_id", C.c_int32), ("R", C.c_float * 9), ("t", C.c_float * 3),
+                ("s", C.c_float)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("z_near", C.c_float)]
+
+
+class RenderFlags(C.Structure):
+    _fields_ = [("use_mlp", C.c_int32), ("mlp_gate", C.c_int32), ("logit_threshold", C.c_float),
+                ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_stop", C.c_float),
+                ("dilation", C.c_float), ("guard_band", C.c_float), ("bg", C.c_float * 3),
+                ("tile_size", C.c_int32), ("image_memory", C.c_int32), ("profile", C.c_int32),
+                ("logits_override", C.c_void_p), ("keep_outputs", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
+
+
+class FrameStats(C.Structure):
+    _fields_ = [("n_instanced", C.c_uint64), ("n_in_frustum", C.c_uint64),
+                ("n_mlp_queries", C.c_uint64), ("n_survivors", C.c_uint64),
+                ("n_pairs", C.c_uint64), ("n_instances_visible", C.c_uint32),
+                ("sort_passes", C.c_uint32), ("stage_ms", C.c_float * NVGS_NUM_STAGES),
+                ("kernel_launches", C.c_uint64)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "stage_ms"}
+        d["stage_ms"] = dict(zip(STAGE_NAMES, list(self.stage_ms)))
+        return d
+
+
+class FrameView(C.Structure):
+    _fields_ = [("survivors", C.c_void_p), ("records", C.c_void_p), ("tile_rects", C.c_void_p),
+                ("pair_values", C.c_void_p), ("pair_keys", C.c_void_p), ("tile_ranges", C.c_void_p),
+                ("final_T", C.c_void_p), ("n_contrib", C.c_void_p), ("n_survivors", C.c_uint64),
+                ("n_pairs", C.c_uint64), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
+                ("tile_size", C.c_int32), ("depth_bits", C.c_int32)]
+
+
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 40), ("launches", C.c_uint64), ("total_ms", C.c_double)]
+
+
+EXPORTS = ("nvgs_create", "nvgs_destroy", "nvgs_last_error", "nvgs_get_stream", "nvgs_default_flags",
+           "nvgs_abi_version", "nvgs_load_asset", "nvgs_set_mlp", "nvgs_set_instances",
+           "nvgs_scene_info", "nvgs_query_visibility", "nvgs_render", "nvgs_last_frame",
+           "nvgs_sort_pairs", "nvgs_kernel_stats", "nvgs_reset_kernel_stats")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_2511_19202_b300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, P = C.c_void_p, C.POINTER
+    L.nvgs_create.argtypes = [P(vp), C.c_int, vp]
+    L.nvgs_destroy.argtypes = [vp]
+    L.nvgs_last_error.argtypes = [vp]
+    L.nvgs_last_error.restype = C.c_char_p
+    L.nvgs_get_stream.argtypes = [vp]
+    L.nvgs_get_stream.restype = vp
+    L.nvgs_default_flags.argtypes = [P(RenderFlags)]
+    L.nvgs_default_flags.restype = None
+    L.nvgs_abi_version.restype = C.c_int
+    L.nvgs_load_asset.argtypes = [vp, P(AssetDesc), P(C.c_int)]
+    L.nvgs_set_mlp.argtypes = [vp, C.c_int, vp, C.c_int]
+    L.nvgs_set_instances.argtypes = [vp, vp, C.c_int]
+    L.nvgs_scene_info.argtypes = [vp, P(C.c_int64), P(C.c_int), P(C.c_int)]
+    L.nvgs_query_visibility.argtypes = [vp, P(Camera), P(RenderFlags), vp, vp, P(FrameStats)]
+    L.nvgs_render.argtypes = [vp, P(Camera), P(RenderFlags), vp, P(FrameStats)]
+    L.nvgs_last_frame.argtypes = [vp, P(FrameView)]
+    L.nvgs_sort_pairs.argtypes = [vp, vp, vp, C.c_int64, C.c_int]
+    L.nvgs_kernel_stats.argtypes = [vp, vp, C.c_int, P(C.c_int)]
+    L.nvgs_reset_kernel_stats.argtypes = [vp]
+    for name in EXPORTS:
+        if name not in ("nvgs_default_flags", "nvgs_abi_version", "nvgs_last_error", "nvgs_get_stream"):
+            getattr(L, name).restype = C.c_int
+    return L
+
+
+lib = _load()
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _check(ctx, st):
+    if st != NVGS_OK:
+        msg = lib.nvgs_last_error(ctx).decode() if ctx else ""
+        raise NvgsError(st, msg)
+
+
+# ----------------------------------------------------------------------------- C entry points
+def nvgs_create(device: int = 0, stream=None):
+    h = C.c_void_p()
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(None, lib.nvgs_create(C.byref(h), int(device), s))
+    return h
+
+
+def nvgs_destroy(ctx):
+    _check(None, lib.nvgs_destroy(ctx))
+
+
+def nvgs_last_error(ctx) -> str:
+    return lib.nvgs_last_error(ctx).decode()
+
+
+def nvgs_get_stream(ctx) -> int:
+    return lib.nvgs_get_stream(ctx)
+
+
+def nvgs_default_flags(**overrides) -> RenderFlags:
+    f = RenderFlags()
+    lib.nvgs_default_flags(C.byref(f))
+    for k, v in overrides.items():
+        if k == "bg":
+            f.bg[:] = [float(x) for x in v]
+        elif k == "logits_override":
+            f.logits_override = _ptr(v)
+        else:
+            setattr(f, k, v)
+    return f
+
+
+def nvgs_abi_version() -> int:
+    return lib.nvgs_abi_version()
+
+
+def nvgs_load_asset(ctx, asset, d_min=0.0, d_max=0.0, p_near=0.0, p_far=0.0) -> int:
+    """``asset`` has means, log_scales, quats, opacity_logits, sh (numpy float32, host) and
+    sh_degree, train_fov_x attributes."""
+    arrs = [np.ascontiguousarray(getattr(asset, k), np.float32)
+            for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+    d = AssetDesc()
+    d.n = int(arrs[0].shape[0])
+    d.sh_degree = int(asset.sh_degree)
+    d.memory = NVGS_MEM_HOST
+    d.means, d.log_scales, d.quats, d.opacity_logits, d.sh = [a.ctypes.data for a in arrs]
+    d.train_fov_x = float(asset.train_fov_x)
+    d.d_min, d.d_max, d.p_near, d.p_far = float(d_min), float(d_max), float(p_near), float(p_far)
+    out = C.c_int(-1)
+    _check(ctx, lib.nvgs_load_asset(ctx, C.byref(d), C.byref(out)))
+    return out.value
+
+
+def flat_weights(w) -> np.ndarray:
+    if isinstance(w, dict):
+        parts = []
+        for k in range(1, 5):
+            parts += [np.asarray(w[f"W{k}"], np.float32).ravel(), np.asarray(w[f"b{k}"], np.float32).ravel()]
+        w = np.concatenate(parts)
+    w = np.ascontiguousarray(w, np.float32)
+    assert w.size == MLP_WEIGHTS
+    return w
+
+
+def nvgs_set_mlp(ctx, asset_id: int, weights, precision: int = NVGS_PREC_FP32):
+    w = flat_weights(weights)
+    _check(ctx, lib.nvgs_set_mlp(ctx, int(asset_id), w.ctypes.data, int(precision)))
+
+
+def nvgs_set_instances(ctx, instances):
+    arr = (Instance * len(instances))()
+    for k, i in enumerate(instances):
+        arr[k].asset_id = int(i.asset_id)
+        arr[k].R[:] = [float(x) for x in np.asarray(i.R, np.float32).ravel()]
+        arr[k].t[:] = [float(x) for x in np.asarray(i.t, np.float32).ravel()]
+        arr[k].s = float(i.s)
+    _check(ctx, lib.nvgs_set_instances(ctx, C.cast(arr, C.c_void_p), len(instances)))
+
+
+def nvgs_scene_info(ctx):
+    n = C.c_int64()
+    a = C.c_int()
+    i = C.c_int()
+    _check(ctx, lib.nvgs_scene_info(ctx, C.byref(n), C.byref(a), C.byref(i)))
+    return n.value, a.value, i.value
+
+
+def camera(cam) -> Camera:
+    c = Camera()
+    c.R[:] = [float(x) for x in np.asarray(cam.R, np.float32).ravel()]
+    c.t[:] = [float(x) for x in np.asarray(cam.t, np.float32).ravel()]
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height, c.z_near = int(cam.width), int(cam.height), float(cam.z_near)
+    return c
+
+
+def nvgs_query_visibility(ctx, cam, flags: RenderFlags, logits=None, keep=None) -> FrameStats:
+    st = FrameStats()
+    _check(ctx, lib.nvgs_query_visibility(ctx, C.byref(camera(cam)), C.byref(flags), _ptr(logits),
+                                          _ptr(keep), C.byref(st)))
+    return st
+
+
+def nvgs_render(ctx, cam, flags: RenderFlags, image) -> FrameStats:
+    st = FrameStats()
+    _check(ctx, lib.nvgs_render(ctx, C.byref(camera(cam)), C.byref(flags), _ptr(image), C.byref(st)))
+    return st
+
+
+def nvgs_last_frame(ctx) -> FrameView:
+    v = FrameView()
+    _check(ctx, lib.nvgs_last_frame(ctx, C.byref(v)))
+    return v
+
+
+def nvgs_sort_pairs(ctx, keys, values, n: int, key_bits: int):
+    _check(ctx, lib.nvgs_sort_pairs(ctx, _ptr(keys), _ptr(values), int(n), int(key_bits)))
+
+
+def nvgs_kernel_stats(ctx):
+    """{kernel name: (launches, total device ms)} over the profiled frames since the last reset."""
+    n = C.c_int(0)
+    _check(ctx, lib.nvgs_kernel_stats(ctx, None, 0, C.byref(n)))
+    arr = (KernelStat * max(1, n.value))()
+    _check(ctx, lib.nvgs_kernel_stats(ctx, C.cast(arr, C.c_void_p), n.value, C.byref(n)))
+    return {arr[k].name.decode(): (int(arr[k].launches), float(arr[k].total_ms)) for k in range(n.value)}
+
+
+def nvgs_reset_kernel_stats(ctx):
+    _check(ctx, lib.nvgs_reset_kernel_stats(ctx))

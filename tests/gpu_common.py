@@ -1,0 +1,65 @@
+"""Shared helpers of the GPU parity tests: build the library, run the CUDA path through the
+C ABI, and compare with the FP64 oracle on the same seeded inputs."""
+import numpy as np
+
+import oracle
+
+
+def renderer_for(scene, weights=None, precision=0, **kw):
+    from paper_2511_19202_b300 import build
+    build.build()
+    from paper_2511_19202_b300.render import Renderer
+    r = Renderer(0)
+    r.load_scene(scene, weights, precision, **kw)
+    return r
+
+
+def gpu_image(r, cam, **flags):
+    img, st = r.render(cam, r.flags(**flags))
+    return img.cpu().numpy().astype(np.float64), st
+
+
+def oracle_opts_for(flags: dict, **eps):
+    return oracle.opts(alpha_min=flags.get("alpha_min", 1 / 255), alpha_max=flags.get("alpha_max", 0.99),
+                       t_stop=flags.get("t_stop", 1e-4), bg=flags.get("bg", (0, 0, 0)),
+                       tile_size=flags.get("tile_size", 16), **eps)
+
+
+def compare_images(gpu, ora, amb, tol=1e-3, max_amb_frac=0.02):
+    """Max-abs error over pixels outside the ambiguity band; returns (err, n_ambiguous)."""
+    ok = ~amb
+    err = float(np.max(np.abs(gpu[ok] - ora[ok]))) if ok.any() else 0.0
+    frac = float(amb.mean())
+    assert frac <= max_amb_frac, f"ambiguous fraction {frac:.4f} too large"
+    assert err <= tol, f"max abs error {err:.3e} > {tol}"
+    return err, int(amb.sum())
+
+
+def survivors_set(lf):
+    s = lf["survivors"].cpu().numpy()
+    return s
+
+
+def check_tile_lists(gpu_tiles, gpu_inst, gpu_g, ora_tiles, ora_inst, ora_g, depth_of, drop,
+                     eps=1e-6):
+    """Per tile: the same (instance, gaussian) multiset on both sides once the ambiguous splats in
+    ``drop`` are removed, and the GPU order non-decreasing in the oracle's FP64 depth except where
+    two depths are within ``eps`` (relative) of each other, which FP32 cannot order."""
+    def split(t, i, g):
+        d = {}
+        for a, b, c in zip(t.tolist(), i.tolist(), g.tolist()):
+            if (b, c) in drop:
+                continue
+            d.setdefault(a, []).append((b, c))
+        return d
+    G = split(gpu_tiles, gpu_inst, gpu_g)
+    O = split(ora_tiles, ora_inst, ora_g)
+    assert set(G) == set(O), "different sets of non-empty tiles"
+    n_pairs = 0
+    for t in O:
+        assert sorted(G[t]) == sorted(O[t]), f"tile {t}: different Gaussians"
+        ds = [depth_of[e] for e in G[t]]
+        for k in range(len(ds) - 1):
+            assert ds[k + 1] >= ds[k] - eps * abs(ds[k]), f"tile {t}: order broken at {k}"
+        n_pairs += len(O[t])
+    return n_pairs

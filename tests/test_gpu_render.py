@@ -1,0 +1,239 @@
+"""GPU parity of the CUDA render pass (through the C ABI) against the FP64 oracle on the same seeded
+inputs: images within 1e-3 max-abs outside the ambiguity band, culled sets / survivor order /
+tile lists bit-exact from fixed logits, MLP logits and decisions, the radix sort, and edge cases.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from gpu_common import (check_tile_lists, compare_images, gpu_image, oracle_opts_for,
+                        renderer_for)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def cfg1_setup():
+    sc, cam = scenes.config1_scene(), scenes.config1_camera()
+    r = renderer_for(sc)
+    yield sc, cam, r, oracle.OracleScene(sc)
+    r.close()
+
+
+def _random_weights(seed=42, bias_std=0.3):
+    w = scenes.mlp_weights(seed)
+    rng = np.random.default_rng(seed + 1)
+    for k in range(1, 5):
+        w[f"b{k}"] = rng.normal(0, bias_std, w[f"b{k}"].shape).astype(np.float32)
+    return w
+
+
+# ----------------------------------------------------------------------------- unculled path
+@pytest.mark.parametrize("tile", [16])
+def test_cfg1_unculled_image_matches_oracle(cfg1_setup, tile):
+    sc, cam, r, osc = cfg1_setup
+    img, st = gpu_image(r, cam, use_mlp=0, tile_size=tile)
+    o = oracle_opts_for(dict(tile_size=tile))
+    ref = oracle.render(osc, cam, o)
+    err, n_amb = compare_images(img, ref["image"], ref["ambiguous"])
+    assert st["n_survivors"] == st["n_in_frustum"] > 0
+    print(f"max err {err:.2e}, ambiguous px {n_amb}")
+
+
+def test_tile_size_does_not_change_the_image(cfg1_setup):
+    sc, cam, r, osc = cfg1_setup
+    imgs = [gpu_image(r, cam, use_mlp=0, tile_size=t)[0] for t in (8, 16, 32)]
+    np.testing.assert_array_equal(imgs[0], imgs[1])
+    np.testing.assert_array_equal(imgs[1], imgs[2])
+
+
+def test_background_and_host_output(cfg1_setup):
+    sc, cam, r, osc = cfg1_setup
+    bg = (0.2, 0.5, 0.9)
+    dev, _ = gpu_image(r, cam, use_mlp=0, bg=bg)
+    host = np.zeros((cam.height, cam.width, 3), np.float32)
+    r.render_host(cam, r.flags(use_mlp=0, bg=bg), host)
+    np.testing.assert_array_equal(dev, host.astype(np.float64))
+    ref = oracle.render(osc, cam, oracle_opts_for(dict(bg=bg)))
+    compare_images(dev, ref["image"], ref["ambiguous"])
+
+
+def test_render_is_deterministic(cfg1_setup):
+    sc, cam, r, osc = cfg1_setup
+    a, _ = gpu_image(r, cam, use_mlp=0)
+    b, _ = gpu_image(r, cam, use_mlp=0)
+    np.testing.assert_array_equal(a, b)
+
+
+# ----------------------------------------------------------------------------- S1-S3 bit-exact
+def test_fixed_logits_culled_set_and_order_are_exact(cfg1_setup):
+    sc, cam, r, osc = cfg1_setup
+    rng = np.random.default_rng(123)
+    logits = rng.normal(0, 1, sc.n_instanced).astype(np.float32)
+    d_logits = torch.from_numpy(logits).cuda()
+    flags = dict(use_mlp=1, mlp_gate=0, logits_override=d_logits)
+    img, st = gpu_image(r, cam, **flags)
+    lf = r.last_frame()
+    surv = lf["survivors"].cpu().numpy()
+    inside, f_amb = oracle.frustum(osc, cam)
+    keep = inside & (logits > 0)
+    ora = np.nonzero(keep)[0]                    # instance-major order, one instance here
+    gpu = surv[:, 1].astype(np.int64)
+    amb = set(np.nonzero(f_amb)[0].tolist())
+    assert np.all(np.diff(gpu) > 0), "survivors must keep (instance, gaussian) order"
+    sym = set(gpu.tolist()) ^ set(ora.tolist())
+    assert sym <= amb, f"{len(sym - amb)} non-ambiguous differences"
+    # the culled image equals the oracle render with the same decisions
+    ref = oracle.render(osc, cam, oracle_opts_for({}), keep=keep.astype(np.uint8))
+    compare_images(img, ref["image"], ref["ambiguous"])
+    # nvgs_query_visibility reports the same decisions
+    lg, kp, _ = r.query_visibility(cam, r.flags(**flags))
+    kp = kp.cpu().numpy().astype(bool)
+    assert set(np.nonzero(kp != keep)[0].tolist()) <= amb
+
+
+def test_tile_lists_are_exact(cfg1_setup):
+    sc, cam, r, osc = cfg1_setup
+    o = oracle_opts_for(dict(tile_size=16))
+    _, st = gpu_image(r, cam, use_mlp=0, tile_size=16)
+    lf = r.last_frame()
+    vals = lf["pair_values"].cpu().numpy().astype(np.int64)
+    keys = lf["pair_keys"].cpu().numpy().view(np.uint64)
+    surv = lf["survivors"].cpu().numpy()
+    gpu_tiles = (keys >> np.uint64(lf["depth_bits"])).astype(np.int64)
+    assert np.all(np.diff(gpu_tiles) >= 0)
+    sp = oracle.project(osc, cam, o)
+    ot, oi, og = oracle.tile_lists(sp, cam, 16)
+    drop = set(zip(sp["instance"][sp["ambiguous"] != 0].tolist(), sp["gaussian"][sp["ambiguous"] != 0].tolist()))
+    depth_of = dict(zip(zip(sp["instance"].tolist(), sp["gaussian"].tolist()), sp["depth"].tolist()))
+    n = check_tile_lists(gpu_tiles, surv[vals, 0], surv[vals, 1], ot, oi, og, depth_of, drop)
+    assert n > 10000
+    # ranges cover exactly the sorted pairs of each tile
+    rng_ = lf["tile_ranges"].cpu().numpy()
+    for t in np.unique(gpu_tiles)[:50]:
+        idx = np.nonzero(gpu_tiles == t)[0]
+        assert rng_[t, 0] == idx[0] and rng_[t, 1] == idx[-1] + 1
+
+
+# ----------------------------------------------------------------------------- S2 (FP32)
+def test_fp32_mlp_logits_and_decisions_match_oracle():
+    sc, cam = scenes.config1_scene(), scenes.config1_camera()
+    w = _random_weights()
+    r = renderer_for(sc, w, precision=0)
+    try:
+        lg, kp, st = r.query_visibility(cam, r.flags(use_mlp=1, mlp_gate=0))
+        lg = lg.cpu().numpy().astype(np.float64)
+        osc = oracle.OracleScene(sc)
+        vis = oracle.visibility(osc, cam, w, gate=False)
+        inside, _ = oracle.frustum(osc, cam)
+        m = inside & np.isfinite(lg)
+        assert m.sum() == inside.sum() > 0
+        err = np.abs(lg[m] - vis["logits"][m])
+        scale = np.abs(vis["logits"][m]).max()
+        assert err.max() <= 1e-4 * max(1.0, scale), err.max()
+        big = np.abs(vis["logits"][m]) > 0.05
+        agree = ((lg[m] > 0) == (vis["logits"][m] > 0))[big].mean()
+        assert agree == 1.0
+        # culled render with the MLP's own decisions, threshold at the median logit
+        thr = float(np.float32(np.median(vis["logits"][inside])))
+        img, st = gpu_image(r, cam, use_mlp=1, mlp_gate=0, logit_threshold=thr)
+        # decisions within 3x the measured FP32 logit error of the threshold may flip
+        keep, kamb = oracle.cull_decision(vis, inside, thr, band=3.0 * float(err.max()) + 1e-7)
+        ref = oracle.render(osc, cam, oracle_opts_for({}), keep=keep.astype(np.uint8),
+                            keep_amb=kamb.astype(np.uint8))
+        compare_images(img, ref["image"], ref["ambiguous"])
+        assert st["n_survivors"] < st["n_in_frustum"]
+    finally:
+        r.close()
+
+
+# ----------------------------------------------------------------------------- several instances, SH
+@pytest.mark.parametrize("deg", [1, 2, 3])
+def test_instances_and_sh_degrees_match_oracle(deg):
+    sc = scenes.tiny_scene(300, 10 + deg, spread=0.6, log_scale_mean=-3.0, sh_degree=deg, n_instances=4)
+    cam = scenes.look_at_camera((0.6, 0.9, 2.8), (0, 0, 0), 97, 61, 55.0)   # ragged tiles
+    r = renderer_for(sc)
+    try:
+        img, st = gpu_image(r, cam, use_mlp=0)
+        osc = oracle.OracleScene(sc)
+        ref = oracle.render(osc, cam, oracle_opts_for({}))
+        compare_images(img, ref["image"], ref["ambiguous"])
+        assert st["n_instanced"] == 1200
+    finally:
+        r.close()
+
+
+# ----------------------------------------------------------------------------- edge cases
+def test_empty_frustum_gives_background():
+    sc = scenes.config1_scene(2000)
+    cam = scenes.look_at_camera((0, 0, 3), (0, 0, 10), 64, 48, 50.0)   # looking away
+    r = renderer_for(sc)
+    try:
+        img, st = gpu_image(r, cam, use_mlp=0, bg=(0.1, 0.2, 0.3))
+        assert st["n_in_frustum"] == 0 and st["n_pairs"] == 0
+        np.testing.assert_array_equal(img, np.broadcast_to(np.float32([0.1, 0.2, 0.3]), img.shape))
+    finally:
+        r.close()
+
+
+def test_everything_culled_gives_background(cfg1_setup):
+    sc, cam, r, osc = cfg1_setup
+    d_logits = torch.full((sc.n_instanced,), -1.0, device="cuda")
+    img, st = gpu_image(r, cam, use_mlp=1, mlp_gate=0, logits_override=d_logits)
+    assert st["n_survivors"] == 0
+    assert np.all(img == 0.0)
+
+
+def test_single_gaussian_peak_alpha():
+    from helpers import axis_camera, identity_instance, logit, one_asset
+    cam = axis_camera(32, 32, fx=32.0)
+    a = one_asset([[(10.5 - 16) * 2 / 32, (13.5 - 16) * 2 / 32, 2.0]], [[-3.0] * 3], None,
+                  [logit(0.7)], np.full((1, 1, 3), 1.0))
+    r = renderer_for(scenes.Scene([a], [identity_instance()]))
+    try:
+        img, _ = gpu_image(r, cam, use_mlp=0)
+        o = 1 / (1 + math.exp(-float(np.float32(logit(0.7)))))
+        rgb = 0.5 + 0.28209479177387814 * 1.0
+        np.testing.assert_allclose(img[13, 10], o * rgb, rtol=2e-6)
+    finally:
+        r.close()
+
+
+def test_invalid_arguments_are_rejected(cfg1_setup):
+    from paper_2511_19202_b300.nvgs import NvgsError
+    sc, cam, r, osc = cfg1_setup
+    with pytest.raises(NvgsError):
+        r.render(cam, r.flags(tile_size=12))
+    bad = scenes.Camera(cam.R, cam.t, -1.0, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    with pytest.raises(NvgsError):
+        r.render(bad)
+
+
+# ----------------------------------------------------------------------------- radix sort
+@pytest.mark.parametrize("n,bits,spread", [(0, 8, 0), (1, 8, 0), (2, 3, 2), (1000, 7, 100),
+                                           (8191, 13, 1 << 13), (8192, 45, 1 << 45),
+                                           (8193, 16, 5), (100_003, 40, 1 << 40),
+                                           (1_000_003, 64, 0), (777_777, 20, 3)])
+def test_radix_sort_is_a_stable_sort(cfg1_setup, n, bits, spread):
+    sc, cam, r, osc = cfg1_setup
+    rng = np.random.default_rng(n + bits)
+    if spread:
+        keys = rng.integers(0, spread, n, dtype=np.uint64)
+    else:
+        keys = rng.integers(0, np.iinfo(np.uint64).max, n, dtype=np.uint64, endpoint=True)
+    mask = np.uint64((1 << bits) - 1) if bits < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+    keys = keys & mask
+    vals = np.arange(n, dtype=np.uint32)
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    dv = torch.from_numpy(vals.view(np.int32)).cuda()
+    r.sort_pairs(dk, dv, bits)
+    torch.cuda.synchronize()
+    order = np.argsort(keys, kind="stable")
+    np.testing.assert_array_equal(dk.cpu().numpy().view(np.uint64), keys[order])
+    np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), vals[order])

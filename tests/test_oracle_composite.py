@@ -218,6 +218,18 @@ def test_row_subset_equals_full_frame(cfg1):
     np.testing.assert_array_equal(sub, full[rows])
 
 
+def test_memory_light_row_render_equals_full_frame():
+    sc = scenes.tiny_scene(400, 21, spread=0.7, log_scale_mean=-3.0, sh_degree=1, n_instances=3)
+    cam = scenes.look_at_camera((0.4, 0.7, 3.0), (0, 0, 0), 80, 60, 50.0)
+    osc = oracle.OracleScene(sc)
+    full = oracle.render(osc, cam)
+    rows = np.array([0, 17, 30, 31, 59], np.int32)
+    sub = oracle.render_rows(osc, cam, rows)
+    np.testing.assert_array_equal(sub["image"], full["image"][rows])
+    np.testing.assert_array_equal(sub["ambiguous"], full["ambiguous"][rows])
+    assert 0 < sub["n_splats"] < sc.n_instanced
+
+
 def test_tile_lists_cover_every_blended_pixel(cfg1):
     scene, cam = cfg1
     osc = oracle.OracleScene(scene)
