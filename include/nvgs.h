@@ -210,6 +210,24 @@ nvgs_status nvgs_last_frame(const nvgs_ctx* ctx, nvgs_frame_view* out);
 nvgs_status nvgs_sort_pairs(nvgs_ctx* ctx, uint64_t* keys, uint32_t* values, int64_t n,
                             int key_bits);
 
+/* Allocation-free variant of nvgs_sort_pairs (the paper has no counterpart: this is a library
+ * service).  For callers that cannot call cudaMalloc -- a plugin whose host application owns all
+ * device memory, a real-time loop that cannot afford cudaMalloc's implicit synchronisation, or
+ * code that must leave the allocator alone while its stream is recorded.  It takes no context
+ * and allocates nothing: its scratch is a fixed array of about 13 MB compiled into the library,
+ * held on every GPU that loads the library until the process exits.
+ *   keys, values : DEVICE arrays of n pairs, sorted in place (stable, low key_bits bits)
+ *   n            : 0 .. NVGS_SORT_NOALLOC_MAX_PAIRS; larger n returns NVGS_ERR_CAPACITY and
+ *                  enqueues nothing
+ *   cuda_stream  : cudaStream_t to enqueue on (NULL = the legacy default stream)
+ * The first call on a device looks up the scratch array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  All calls share
+ * the one array and leave their data in it; calls that overlap on the GPU race, so serialise
+ * them.  Returns NVGS_ERR_INVALID_ARG for bad arguments and NVGS_ERR_CUDA if a launch fails. */
+#define NVGS_SORT_NOALLOC_MAX_PAIRS (1u << 20)
+nvgs_status nvgs_sort_pairs_noalloc(uint64_t* keys, uint32_t* values, int64_t n, int key_bits,
+                                    void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,7 +87,9 @@ class KernelStat(C.Structure):
 EXPORTS = ("nvgs_create", "nvgs_destroy", "nvgs_last_error", "nvgs_get_stream", "nvgs_default_flags",
            "nvgs_abi_version", "nvgs_load_asset", "nvgs_set_mlp", "nvgs_set_instances",
            "nvgs_scene_info", "nvgs_query_visibility", "nvgs_render", "nvgs_last_frame",
-           "nvgs_sort_pairs", "nvgs_kernel_stats", "nvgs_reset_kernel_stats")
+           "nvgs_sort_pairs", "nvgs_kernel_stats", "nvgs_reset_kernel_stats",
+           "nvgs_sort_pairs_noalloc")
+NVGS_SORT_NOALLOC_MAX_PAIRS = 1 << 20
 
 
 def _load():
@@ -114,6 +116,7 @@ def _load():
     L.nvgs_sort_pairs.argtypes = [vp, vp, vp, C.c_int64, C.c_int]
     L.nvgs_kernel_stats.argtypes = [vp, vp, C.c_int, P(C.c_int)]
     L.nvgs_reset_kernel_stats.argtypes = [vp]
+    L.nvgs_sort_pairs_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int, vp]
     for name in EXPORTS:
         if name not in ("nvgs_default_flags", "nvgs_abi_version", "nvgs_last_error", "nvgs_get_stream"):
             getattr(L, name).restype = C.c_int
@@ -273,3 +276,11 @@ def nvgs_kernel_stats(ctx):
 
 def nvgs_reset_kernel_stats(ctx):
     _check(ctx, lib.nvgs_reset_kernel_stats(ctx))
+
+
+def nvgs_sort_pairs_noalloc(keys, values, n: int, key_bits: int, stream=None) -> int:
+    """Allocation-free sort (fixed scratch inside the library, at most
+    NVGS_SORT_NOALLOC_MAX_PAIRS pairs).  Returns the nvgs status code; raises nothing, so that
+    callers can test the capacity error."""
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    return lib.nvgs_sort_pairs_noalloc(_ptr(keys), _ptr(values), int(n), int(key_bits), s)
