@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--config", choices=["composed", "small"], default="composed")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--mlp", choices=["random"], default="random")
+    p.add_argument("--precision", choices=["bf16", "fp32"], default="bf16",
+                   help="visibility-MLP arithmetic: BF16 tensor cores (tcgen05) or FP32 CUDA cores")
     return p.parse_args()
 
 
@@ -185,7 +187,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     sc, cams, weights, desc = workload(args.config)
     r = Renderer(dev)
-    r.load_scene(sc, weights, N.NVGS_PREC_FP32)
+    prec = N.NVGS_PREC_BF16 if args.precision == "bf16" else N.NVGS_PREC_FP32
+    r.load_scene(sc, weights, prec)
     sh_stride = (3 * (sc.assets[0].sh_degree + 1) ** 2 + 3) // 4 * 4
     W, H = cams[0].width, cams[0].height
     tile = 16
@@ -286,7 +289,10 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": desc, "mlp": "random-init N(0,1/fan_in) weights, FP32 CUDA-core path",
+        "config": {"workload": desc,
+                   "mlp": ("random-init N(0,1/fan_in) weights, " +
+                           ("BF16 tcgen05 tensor cores, FP32 accumulate" if args.precision == "bf16"
+                            else "FP32 CUDA cores")),
                    "l2": "no flush: the assets (1.9 GB) and per-frame buffers exceed the 126 MB L2",
                    "unculled_ms_per_frame": plain_ms,
                    "speedup_culled_vs_unculled": plain_ms / value,

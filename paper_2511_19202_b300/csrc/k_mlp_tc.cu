@@ -1,14 +1,378 @@
-// S2, BF16 tensor-core variant (placeholder until the tcgen05 kernel lands).
-#include "nvgs_internal.cuh"
+// S2, BF16 tensor-core variant: the per-asset visibility MLP (32 -> 64 -> 64 -> 64 -> 1, ReLU;
+// NVGS Sec. 3.2, queried per in-frustum Gaussian as in Sec. 3.3) on the 5th-generation tensor
+// cores (tcgen05), BF16 operands with FP32 accumulation in tensor memory (TMEM).
+//
+// One CTA = one warpgroup (128 threads) walking 128-Gaussian tiles of the in-frustum list:
+//   1. thread r builds the 32 inputs of row r (Eq. 2 distance, frequency encoding) and writes
+//      them as BF16 into the A tile in shared memory;
+//   2. thread 0 issues tcgen05.mma (M = 128, N = 64, K = 16 per instruction) for layer 1 with the
+//      accumulator in TMEM columns [0, 64) and commits to an mbarrier;
+//   3. after the mbarrier completes, each warp reads its 32 TMEM lanes (tcgen05.ld 32x32b),
+//      adds the FP32 bias, applies ReLU while converting to BF16, and writes the activations back
+//      to shared memory as the next layer's A operand; layers 2 and 3 repeat steps 2-3;
+//   4. the 64 -> 1 output layer runs in FP32 on the CUDA cores straight from the TMEM values.
+// Four CTAs share an SM (64 TMEM columns each), so one CTA's epilogue overlaps another's MMAs.
+//
+// Operand layout (both operands K-major, no swizzle): 8 x 16-byte "core matrices"; element
+// (row, k) of a tile with K columns sits at (row / 8) * SBO + (k / 8) * 128 + (row % 8) * 16
+// + (k % 8) * 2 with SBO = 16 * K bytes.  The weights are packed on the host into exactly this
+// byte layout (mlp_tc_pack_weights) and copied to shared memory with 16-byte loads.
+//
+// Every mbarrier wait is bounded; on a timeout the CTA sets the error flag, frees its TMEM and
+// returns.
+#include <climits>
+#include <cstring>
+
+#include "mlp_common.cuh"
 
 namespace nvgs {
 
-size_t mlp_tc_weight_bytes() { return 16; }
-void mlp_tc_pack_weights(const float*, uint8_t* out) { for (int k = 0; k < 16; k++) out[k] = 0; }
+namespace {
 
-cudaError_t launch_mlp_tc(const uint2*, uint32_t, const FrameInst*, const AssetDev*, const int64_t*,
-                          float, uint32_t*, float*, int, cudaStream_t, LaunchLog*) {
-    return cudaErrorNotSupported;
+constexpr int kThreads = 128;
+constexpr int kRows = 128;
+constexpr int kTmemCols = 64;
+// shared-memory map (bytes)
+constexpr int kOffW1 = 0;            // 64 x 32 BF16
+constexpr int kOffW2 = 4096;         // 64 x 64 BF16
+constexpr int kOffW3 = 12288;        // 64 x 64 BF16
+constexpr int kOffVec = 20480;       // FP32: b1[64] b2[64] b3[64] w4[64] b4 pad[3]
+constexpr int kVecFloats = 260;
+constexpr int kBlobBytes = kOffVec + kVecFloats * 4;   // 21520, a multiple of 16
+constexpr int kOffA = 21760;         // 128 x 32 BF16
+constexpr int kOffH = kOffA + 8192;  // 128 x 64 BF16
+constexpr int kOffMisc = kOffH + 16384;
+constexpr int kSmemBytes = kOffMisc + 64;
+constexpr uint32_t kSboK32 = 512;    // 16 * 32
+constexpr uint32_t kSboK64 = 1024;   // 16 * 64
+constexpr uint32_t kLbo = 128;
+constexpr uint32_t kWaitIters = 1u << 20;   // x ~1 us suspend hint: about a second at most
+
+// kind::f16 instruction descriptor: D = F32 (bit 4), A = B = BF16 (bits 7, 10), both K-major,
+// N / 8 at bit 17, M / 16 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// tcgen05 shared-memory matrix descriptor, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(const void* p, uint32_t lbo, uint32_t sbo) {
+    const uint32_t a = smem_u32(p);
+    return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+           ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kWaitIters; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.  The load and its wait sit in one asm
+// statement so that no use of the registers can be scheduled before the data has arrived.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+// (lo, hi) -> BF16x2 with ReLU, lo in the low half (the lower address).
+__device__ __forceinline__ uint32_t bf16x2_relu(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+__device__ __forceinline__ void st_chunk(uint8_t* tile, uint32_t sbo, int row, int chunk, uint4 v) {
+    *reinterpret_cast<uint4*>(tile + (row >> 3) * sbo + chunk * kLbo + (row & 7) * 16) = v;
+}
+
+// TMEM accumulator (this lane, 64 columns) + bias -> ReLU -> BF16 row of the next A operand.
+__device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, const float* bias, uint8_t* sH, int row) {
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+        uint32_t r[32];
+        tmem_ld32(t_lane + half * 32, r);
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            uint32_t p[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int col = half * 32 + c * 8 + 2 * q;
+                p[q] = bf16x2_relu(__uint_as_float(r[c * 8 + 2 * q]) + bias[col],
+                                   __uint_as_float(r[c * 8 + 2 * q + 1]) + bias[col + 1]);
+            }
+            st_chunk(sH, kSboK64, row, half * 4 + c, make_uint4(p[0], p[1], p[2], p[3]));
+        }
+    }
+}
+
+// Output layer in FP32: logit = b4 + w4 . ReLU(acc + b3).
+__device__ __forceinline__ float epilogue_logit(uint32_t t_lane, const float* b3, const float* w4, float b4) {
+    float lg = b4;
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+        uint32_t r[32];
+        tmem_ld32(t_lane + half * 32, r);
+#pragma unroll
+        for (int k = 0; k < 32; k++) {
+            const int col = half * 32 + k;
+            lg = fmaf(w4[col], fmaxf(__uint_as_float(r[k]) + b3[col], 0.0f), lg);
+        }
+    }
+    return lg;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads, 4)
+k_mlp_tc(const uint2* __restrict__ list, uint32_t n, const FrameInst* __restrict__ fis,
+         const AssetDev* __restrict__ assets, float threshold, uint32_t* __restrict__ keep_bits,
+         float* __restrict__ logits_out, uint32_t* __restrict__ err_flag) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t* sA = sm + kOffA;
+    uint8_t* sH = sm + kOffH;
+    const float* sVec = reinterpret_cast<const float*>(sm + kOffVec);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kOffMisc);
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + kOffMisc + 8);
+    int* s_red = reinterpret_cast<int*>(sm + kOffMisc + 16);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(s_tmem)), "r"((uint32_t)kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+    const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
+
+    uint32_t phase = 0;
+    int loaded = -1;
+    bool abort = false;
+    const uint32_t n_tiles = (n + kRows - 1) / kRows;
+    for (uint32_t tile = blockIdx.x; tile < n_tiles && !abort; tile += gridDim.x) {
+        const uint32_t i = tile * kRows + tid;
+        uint2 e = make_uint2(0, 0);
+        int my_asset = INT_MAX;
+        if (i < n) {
+            e = list[i];
+            my_asset = fis[e.x].asset;
+        }
+        bool pending = i < n, keep = false;
+        float logit = 0.0f;
+        // a tile holds consecutive in-frustum Gaussians; rows of different assets (at instance
+        // boundaries) are evaluated in separate passes with each asset's own weights
+        for (;;) {
+            int cand = __reduce_min_sync(0xffffffffu, pending ? my_asset : INT_MAX);
+            if (lane == 0) s_red[warp] = cand;
+            __syncthreads();
+            const int cur = min(min(s_red[0], s_red[1]), min(s_red[2], s_red[3]));
+            __syncthreads();
+            if (cur == INT_MAX) break;
+            const AssetDev& a = assets[cur];
+            const bool mine = pending && my_asset == cur;
+            if (a.w_tc == nullptr) {   // asset without an MLP: rendered unculled
+                if (mine) { keep = true; logit = __int_as_float(0x7f800000); pending = false; }
+                continue;
+            }
+            if (cur != loaded) {
+                const uint4* src = reinterpret_cast<const uint4*>(a.w_tc);
+                uint4* dst = reinterpret_cast<uint4*>(sm);
+                for (int k = tid; k < kBlobBytes / 16; k += kThreads) dst[k] = __ldg(&src[k]);
+                loaded = cur;
+            }
+            // ---- inputs -> A (BF16)
+            uint32_t p[16];
+            if (mine) {
+                float f[32];
+                mlp_features(a, fis[e.x], __ldg(&a.mean_op[e.y]), f);
+#pragma unroll
+                for (int k = 0; k < 16; k++) p[k] = bf16x2(f[2 * k], f[2 * k + 1]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; k++) p[k] = 0u;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++)
+                st_chunk(sA, kSboK32, tid, c, make_uint4(p[4 * c], p[4 * c + 1], p[4 * c + 2], p[4 * c + 3]));
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+
+            // ---- three tensor-core layers
+            bool ok = true;
+#pragma unroll 1
+            for (int layer = 0; layer < 3 && ok; layer++) {
+                if (tid == 0) {
+                    tc_fence_after();
+                    if (layer == 0) {
+#pragma unroll
+                        for (int s = 0; s < 2; s++)
+                            mma_bf16(tmem, sdesc(sA + 256 * s, kLbo, kSboK32),
+                                     sdesc(sm + kOffW1 + 256 * s, kLbo, kSboK32), s > 0);
+                    } else {
+                        const uint8_t* W = sm + (layer == 1 ? kOffW2 : kOffW3);
+#pragma unroll
+                        for (int s = 0; s < 4; s++)
+                            mma_bf16(tmem, sdesc(sH + 256 * s, kLbo, kSboK64),
+                                     sdesc(W + 256 * s, kLbo, kSboK64), s > 0);
+                    }
+                    mma_commit(mbar);
+                }
+                const bool done = mbar_wait(mbar, phase);
+                if (__syncthreads_or(!done)) { ok = false; break; }
+                phase ^= 1u;
+                tc_fence_after();
+                if (layer < 2) {
+                    epilogue_hidden(t_lane, sVec + 64 * layer, sH, tid);
+                    fence_async_smem();
+                    tc_fence_before();
+                    __syncthreads();
+                } else {
+                    const float lg = epilogue_logit(t_lane, sVec + 128, sVec + 192, sVec[256]);
+                    tc_fence_before();
+                    if (mine) {
+                        logit = lg;
+                        keep = fis[e.x].gated || (lg > threshold);
+                        pending = false;
+                    }
+                }
+            }
+            if (!ok) {
+                if (tid == 0) atomicExch(err_flag, 1u);
+                abort = true;
+                break;
+            }
+        }
+        if (abort) break;
+        const uint32_t w = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0 && tile * kRows + warp * 32 < n) keep_bits[tile * 4 + warp] = w;
+        if (logits_out && i < n) logits_out[i] = logit;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     ::"r"(tmem), "r"((uint32_t)kTmemCols) : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ host side
+size_t mlp_tc_weight_bytes() { return (size_t)kBlobBytes; }
+
+static uint16_t f32_to_bf16_rne(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);   // inf / nan kept
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+// Packs W1 (64x32), W2, W3 (64x64) as BF16 core-matrix tiles (row = output neuron, K-major) and
+// b1, b2, b3, w4, b4 as FP32, in the shared-memory byte layout k_mlp_tc reads.
+void mlp_tc_pack_weights(const float* w, uint8_t* out) {
+    memset(out, 0, kBlobBytes);
+    const float* W1 = w;
+    const float* b1 = W1 + 64 * 32;
+    const float* W2 = b1 + 64;
+    const float* b2 = W2 + 64 * 64;
+    const float* W3 = b2 + 64;
+    const float* b3 = W3 + 64 * 64;
+    const float* W4 = b3 + 64;
+    const float* b4 = W4 + 64;
+    auto put = [&](int off, int K, const float* Wm) {
+        const int sbo = 16 * K;
+        for (int nrow = 0; nrow < 64; nrow++)
+            for (int k = 0; k < K; k++) {
+                const uint16_t v = f32_to_bf16_rne(Wm[nrow * K + k]);
+                const int b = off + (nrow / 8) * sbo + (k / 8) * 128 + (nrow % 8) * 16 + (k % 8) * 2;
+                memcpy(out + b, &v, 2);
+            }
+    };
+    put(kOffW1, 32, W1);
+    put(kOffW2, 64, W2);
+    put(kOffW3, 64, W3);
+    float* vec = reinterpret_cast<float*>(out + kOffVec);
+    for (int k = 0; k < 64; k++) {
+        vec[k] = b1[k];
+        vec[64 + k] = b2[k];
+        vec[128 + k] = b3[k];
+        vec[192 + k] = W4[k];
+    }
+    vec[256] = b4[0];
+}
+
+cudaError_t launch_mlp_tc(const uint2* list, uint32_t n, const FrameInst* fi, const AssetDev* assets,
+                          float threshold, uint32_t* keep_bits, float* logits_out, uint32_t* err_flag,
+                          int num_sms, cudaStream_t s, LaunchLog* log) {
+    if (n == 0) return cudaSuccess;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const uint32_t tiles = (n + kRows - 1) / kRows;
+    const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)num_sms * 4u);
+    NVGS_LAUNCH(log, s, "k_mlp_tc", k_mlp_tc<<<grid, kThreads, kSmemBytes, s>>>(list, n, fi, assets, threshold, keep_bits, logits_out, err_flag));
+    return cudaGetLastError();
 }
 
 }  // namespace nvgs

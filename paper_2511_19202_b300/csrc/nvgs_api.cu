@@ -226,11 +226,15 @@ nvgs_status run_cull(nvgs_ctx* ctx, const CamParams& cp, const nvgs_render_flags
     for (auto& a : ctx->assets) any_mlp = any_mlp || a.precision >= 0;
     tc = tc && any_mlp;
     if (tc) {
+        CK(cudaMemsetAsync(&counters[8], 0, 4, s));
         CK(launch_mlp_tc(P<uint2>(ctx->vis_list), n_vis, P<FrameInst>(ctx->frame_inst),
-                         P<AssetDev>(ctx->assets_dev), P<int64_t>(ctx->inst_offset),
-                         f->logit_threshold, P<uint32_t>(ctx->keep_bits),
-                         want_logits ? P<float>(ctx->logits_tmp) : nullptr, ctx->num_sms, s,
-                         &ctx->log));
+                         P<AssetDev>(ctx->assets_dev), f->logit_threshold, P<uint32_t>(ctx->keep_bits),
+                         want_logits ? P<float>(ctx->logits_tmp) : nullptr, &counters[8],
+                         ctx->num_sms, s, &ctx->log));
+        CK(cudaMemcpyAsync(ctx->h_counters + 8, &counters[8], 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (ctx->h_counters[8])
+            return fail(ctx, NVGS_ERR_TIMEOUT, "tensor-core MLP: a bounded mbarrier wait gave up");
     } else {
         CK(launch_mlp_fp32(P<uint2>(ctx->vis_list), n_vis, P<FrameInst>(ctx->frame_inst),
                            P<AssetDev>(ctx->assets_dev), f->logits_override, P<int64_t>(ctx->inst_offset),

@@ -136,9 +136,10 @@ cudaError_t launch_mlp_fp32(const uint2* list, uint32_t n, const FrameInst* fi,
                             const AssetDev* assets, const float* logits_override,
                             const int64_t* inst_offset, float threshold, uint32_t* keep_bits,
                             float* logits_out, cudaStream_t s, LaunchLog* log);
+// err_flag (device) is set to 1 if a bounded wait on the tensor-core pipeline gave up.
 cudaError_t launch_mlp_tc(const uint2* list, uint32_t n, const FrameInst* fi,
-                          const AssetDev* assets, const int64_t* inst_offset, float threshold,
-                          uint32_t* keep_bits, float* logits_out, int num_sms, cudaStream_t s,
+                          const AssetDev* assets, float threshold, uint32_t* keep_bits,
+                          float* logits_out, uint32_t* err_flag, int num_sms, cudaStream_t s,
                           LaunchLog* log);
 
 // BF16 operand tiles of one asset's MLP in the tcgen05 shared-memory layout (host-side packing).

@@ -1,0 +1,123 @@
+"""GPU parity of the BF16 tensor-core visibility MLP (tcgen05) against the FP64 oracle: logits
+within the BF16 error budget, decisions agreeing on >= 99.9% of Gaussians with |logit| > 0.05,
+multi-asset tiles, and the culled image against the oracle render with the same decisions."""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from gpu_common import compare_images, gpu_image, oracle_opts_for, renderer_for
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+BF16 = 1
+
+
+def _weights(seed, bias_std=0.3):
+    w = scenes.mlp_weights(seed)
+    rng = np.random.default_rng(seed + 7)
+    for k in range(1, 5):
+        w[f"b{k}"] = rng.normal(0, bias_std, w[f"b{k}"].shape).astype(np.float32)
+    return w
+
+
+def _check_logits(lg_gpu, lg_ora, mask):
+    lg_gpu = lg_gpu[mask].astype(np.float64)
+    lg_ora = lg_ora[mask]
+    err = np.abs(lg_gpu - lg_ora)
+    big = np.abs(lg_ora) > 0.05
+    agree = float(((lg_gpu > 0) == (lg_ora > 0))[big].mean())
+    # BF16 operands (8-bit mantissa) through three 64-wide layers: a few 1e-2 of the logit scale
+    scale = float(np.percentile(np.abs(lg_ora), 99))
+    assert np.percentile(err, 99) <= 0.02 * max(1.0, scale), (np.percentile(err, 99), scale)
+    assert agree >= 0.999, agree
+    return err, agree
+
+
+def test_bf16_logits_match_oracle_cfg1():
+    sc, cam = scenes.config1_scene(), scenes.config1_camera()
+    w = _weights(42)
+    r = renderer_for(sc, w, precision=BF16)
+    try:
+        lg, kp, st = r.query_visibility(cam, r.flags(use_mlp=1, mlp_gate=0))
+        lg = lg.cpu().numpy()
+        osc = oracle.OracleScene(sc)
+        vis = oracle.visibility(osc, cam, w, gate=False)
+        inside, _ = oracle.frustum(osc, cam)
+        assert np.isfinite(lg[inside]).all()
+        err, agree = _check_logits(lg, vis["logits"], inside)
+        print(f"bf16 logits: max err {err.max():.3e}, p99 {np.percentile(err, 99):.3e}, agree {agree:.5f}")
+        kp = kp.cpu().numpy().astype(bool)
+        np.testing.assert_array_equal(kp, inside & (lg > 0))
+    finally:
+        r.close()
+
+
+def test_bf16_multi_asset_tiles():
+    """Three assets, nine instances: tiles straddle instance and asset boundaries."""
+    assets = [scenes.torus_asset(3001, seed=1, sh_degree=0), scenes.sphere_asset(2500, 2, sh_degree=0),
+              scenes.box_asset(1999, 3, sh_degree=0)]
+    rng = np.random.default_rng(5)
+    insts = []
+    for k in range(9):
+        q, rr = np.linalg.qr(rng.standard_normal((3, 3)))
+        q = q * np.sign(np.diag(rr))
+        if np.linalg.det(q) < 0:
+            q[:, 0] *= -1
+        insts.append(scenes.Instance(k % 3, q.astype(np.float32),
+                                     np.array([(k % 3 - 1) * 2.5, (k // 3 - 1) * 2.5, 0], np.float32),
+                                     float(np.float32(rng.uniform(0.6, 1.2)))))
+    sc = scenes.Scene(assets, insts)
+    cam = scenes.look_at_camera((0.5, 1.0, 9.0), (0, 0, 0), 320, 240, 60.0)
+    ws = [_weights(100 + k) for k in range(3)]
+    r = renderer_for(sc, ws, precision=BF16)
+    try:
+        lg, kp, st = r.query_visibility(cam, r.flags(use_mlp=1, mlp_gate=0))
+        osc = oracle.OracleScene(sc)
+        inside, _ = oracle.frustum(osc, cam)
+        # oracle logits per asset's own weights (one instance at a time)
+        ora = np.zeros(sc.n_instanced)
+        off = 0
+        for k, inst in enumerate(insts):
+            n = assets[inst.asset_id].n
+            sub = oracle.OracleScene(scenes.Scene(assets, [inst]))
+            ora[off:off + n] = oracle.visibility(sub, cam, ws[inst.asset_id], gate=False)["logits"]
+            off += n
+        _check_logits(lg.cpu().numpy(), ora, inside)
+    finally:
+        r.close()
+
+
+def test_bf16_culled_render_matches_oracle_with_same_decisions():
+    sc, cam = scenes.config1_scene(), scenes.config1_camera()
+    w = _weights(7)
+    # a wider logit spread keeps few decisions inside the +-0.05 band, and an output bias at the
+    # median FP64 logit culls about half of the in-frustum Gaussians
+    w["W4"] = (w["W4"] * 10.0).astype(np.float32)
+    w["b4"] = np.zeros(1, np.float32)
+    osc0 = oracle.OracleScene(sc)
+    inside0, _ = oracle.frustum(osc0, cam)
+    med = np.median(oracle.visibility(osc0, cam, w, gate=False)["logits"][inside0])
+    w["b4"] = np.array([-med], np.float32)
+    r = renderer_for(sc, w, precision=BF16)
+    try:
+        lg, kp, _ = r.query_visibility(cam, r.flags(use_mlp=1, mlp_gate=0))
+        lg = lg.cpu().numpy().astype(np.float64)
+        img, st = gpu_image(r, cam, use_mlp=1, mlp_gate=0)
+        osc = oracle.OracleScene(sc)
+        vis = oracle.visibility(osc, cam, w, gate=False)
+        inside, _ = oracle.frustum(osc, cam)
+        keep = inside & (vis["logits"] > 0)
+        # decisions inside the 0.05 band, or the (<= 0.1%) ones that disagree, are ambiguous
+        amb = inside & ((np.abs(vis["logits"]) <= 0.05) | ((lg > 0) != (vis["logits"] > 0)))
+        assert (amb & inside).sum() <= 0.02 * inside.sum()
+        assert 0.05 * inside.sum() < (keep.sum()) < 0.95 * inside.sum()
+        ref = oracle.render(osc, cam, oracle_opts_for({}), keep=keep.astype(np.uint8),
+                            keep_amb=amb.astype(np.uint8))
+        compare_images(img, ref["image"], ref["ambiguous"], max_amb_frac=0.05)
+        assert st["n_mlp_queries"] == st["n_in_frustum"]
+    finally:
+        r.close()
