@@ -172,6 +172,71 @@ nvgs_status nvgs_query_visibility(nvgs_ctx* ctx, const nvgs_camera* cam,
 nvgs_status nvgs_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_render_flags* flags,
                         float* image, nvgs_frame_stats* stats);
 
+/* ------------------------------------------------------------------ visibility MLP: labels, training */
+/* GPU labeller (Sec. 3.1): renders asset `asset_id` alone (identity transform, no culling) from
+ * each of the n_views HOST cameras and writes labels[(v / group) * N + g] = 1 for every Gaussian g
+ * that is blended at one or more pixels of view v (contribution alpha * T > 0), else 0.  Views are
+ * taken in groups of `group` consecutive cameras whose labels are OR-ed: a main view followed by
+ * its auxiliary cone views (Sec. 3.1).  labels is a DEVICE array of (n_views / group) * N bytes.
+ * flags supplies the blending constants and tile size (use_mlp is ignored).  The caller's scene
+ * (instances) is restored afterwards.  Synchronous. */
+nvgs_status nvgs_label_visibility(nvgs_ctx* ctx, int asset_id, const nvgs_camera* views, int n_views,
+                                  int group, const nvgs_render_flags* flags, uint8_t* labels);
+
+/* Per-asset constants computed at load (Sec. 3.1). */
+typedef struct {
+    int64_t n;
+    int32_t sh_degree;
+    int32_t has_mlp;             /* -1 none, else the nvgs_precision set */
+    float bbox_center[3];        /* centre of the means' bounding box */
+    float bbox_half_extent[3];
+    float d_min, d_max;          /* Eq. 1 camera distance bounds */
+    float train_fov_x;           /* theta_t */
+} nvgs_asset_info;
+nvgs_status nvgs_get_asset_info(const nvgs_ctx* ctx, int asset_id, nvgs_asset_info* out);
+
+/* Training views (Sec. 3.1, 4.1): n_dirs Fibonacci-sphere directions around the asset's box
+ * centre, each at n_dist distances log-spaced from d_min to d_max (n_dist = 3 gives d_min, their
+ * geometric mean and d_max), looking at the centre with the asset's training field of view, at
+ * width x height pixels.  out: HOST array of n_dirs * n_dist cameras, direction-major. */
+nvgs_status nvgs_training_views(const nvgs_ctx* ctx, int asset_id, int n_dirs, int n_dist, int width,
+                                int height, nvgs_camera* out);
+
+/* Starts training the MLP of `asset_id` (Sec. 3.2, 4.1): FP32 master weights from `w0` (HOST,
+ * 10497 floats, the nvgs_set_mlp layout), zero Adam moments, and the n_views HOST cameras the
+ * label rows refer to (one per label row; their centre and focal length give each sample's view
+ * direction and Eq. 2 distance). */
+nvgs_status nvgs_train_init(nvgs_ctx* ctx, int asset_id, const float* w0, const nvgs_camera* views,
+                            int n_views);
+
+typedef struct {
+    const uint8_t* labels;       /* DEVICE, n_views x N bytes from nvgs_label_visibility */
+    int32_t batch;               /* samples per step (B) */
+    int32_t pad_;
+    const int32_t* sample_view;  /* nullable DEVICE [B]: explicit (view, gaussian) samples; NULL */
+    const int32_t* sample_gauss; /*   draws them on the device from seed and step (SplitMix64) */
+    uint64_t seed;
+} nvgs_train_batch;
+
+typedef struct {
+    float lr, beta1, beta2, eps; /* Adam (Sec. 4.1: Adam, lr 2e-3 decaying to 2e-4) */
+    int32_t step;                /* 0-based step index (bias correction, sample stream) */
+} nvgs_adam_cfg;
+
+/* One Adam step on the class-balanced binary cross-entropy of B samples (a sample of class c
+ * weighs B / (2 N_c), N_c = its class count in the batch; Sec. 4.1 "weights each occurrence by
+ * its frequency in the batch").  loss_out (HOST, nullable) receives the batch loss; reading it
+ * synchronises. */
+nvgs_status nvgs_train_visibility_step(nvgs_ctx* ctx, int asset_id, const nvgs_train_batch* batch,
+                                       const nvgs_adam_cfg* adam, float* loss_out);
+
+/* Copies the FP32 master weights (HOST, 10497 floats).  Pass them to nvgs_set_mlp to use them. */
+nvgs_status nvgs_train_get_weights(nvgs_ctx* ctx, int asset_id, float* w_out);
+
+/* Learning rate at `step` of `total` (Sec. 4.1): cosine warm-up from 0 to lr0 over the first
+ * warmup_frac of the steps, then exponential decay to lr1 at the last step. */
+float nvgs_lr_schedule(int step, int total, float lr0, float lr1, float warmup_frac);
+
 /* ------------------------------------------------------------------ per-kernel timing */
 /* Device time of each kernel, accumulated over every nvgs_render call made with
  * flags.profile = 1 since the last reset (CUDA events bracket each launch on the context's

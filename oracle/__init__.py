@@ -114,6 +114,11 @@ def lib():
             L.or_pixel_weights.restype = C.c_int
             L.or_pixel_weights.argtypes = [vp, C.c_int64, P(OrCamera), P(OrOpts), C.c_int,
                                            C.c_int, vp, C.c_int, P(C.c_double)]
+            L.or_train_loss_grad.restype = C.c_double
+            L.or_train_loss_grad.argtypes = [P(OrAsset), vp, vp, C.c_int64, vp, vp, C.c_int64, vp, vp]
+            L.or_train_step.restype = C.c_double
+            L.or_train_step.argtypes = [P(OrAsset), vp, vp, C.c_int64, vp, vp, C.c_int64, vp, vp, vp,
+                                        C.c_double, C.c_double, C.c_double, C.c_double, C.c_int]
             L.or_num_threads.restype = C.c_int
             L.or_set_num_threads.argtypes = [C.c_int]
             _lib = L
@@ -372,6 +377,45 @@ def tile_lists(splats: np.ndarray, cam, tile_size: int):
         return tiles, inst, gs
     order = np.lexsort((gs, inst, depth, tiles))
     return tiles[order], inst[order], gs[order]
+
+
+def training_views_table(cams, train_fov_x=None):
+    """Per training camera: its centre (asset frame) and normalised focal 2 fx / W."""
+    out = np.zeros((len(cams), 4), np.float64)
+    for k, c in enumerate(cams):
+        R = np.asarray(c.R, np.float64).reshape(3, 3)
+        out[k, :3] = -R.T @ np.asarray(c.t, np.float64)
+        out[k, 3] = 2.0 * float(c.fx) / int(c.width)
+    return out
+
+
+def train_loss_grad(osc: OracleScene, asset_k: int, views, labels, sv, sg, weights):
+    """Sec. 3.2 / 4.1: class-balanced BCE of a batch and its gradient (flat weight layout)."""
+    w = flat_weights(weights) if isinstance(weights, dict) else np.ascontiguousarray(weights, np.float64)
+    g = np.zeros(10497, np.float64)
+    vt = np.ascontiguousarray(views, np.float64)
+    lab = np.ascontiguousarray(labels, np.uint8)
+    sv = np.ascontiguousarray(sv, np.int32)
+    sg = np.ascontiguousarray(sg, np.int32)
+    n_gauss = lab.size // vt.shape[0]
+    loss = lib().or_train_loss_grad(C.byref(osc.assets[asset_k]), _ptr(vt), _ptr(lab), n_gauss,
+                                    _ptr(sv), _ptr(sg), sv.size, _ptr(w), _ptr(g))
+    return loss, g
+
+
+def train_step(osc: OracleScene, asset_k: int, views, labels, sv, sg, w, m, v, lr, beta1, beta2, eps,
+               step):
+    """One Adam step in FP64; w, m, v (float64 arrays) are updated in place; returns the loss."""
+    vt = np.ascontiguousarray(views, np.float64)
+    lab = np.ascontiguousarray(labels, np.uint8)
+    sv = np.ascontiguousarray(sv, np.int32)
+    sg = np.ascontiguousarray(sg, np.int32)
+    n_gauss = lab.size // vt.shape[0]
+    for x in (w, m, v):
+        assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"] and x.size == 10497
+    return lib().or_train_step(C.byref(osc.assets[asset_k]), _ptr(vt), _ptr(lab), n_gauss, _ptr(sv),
+                               _ptr(sg), sv.size, _ptr(w), _ptr(m), _ptr(v), lr, beta1, beta2, eps,
+                               int(step))
 
 
 def num_threads() -> int:

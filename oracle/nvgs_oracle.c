@@ -757,6 +757,88 @@ int or_pixel_weights(const or_splat* splats, int64_t n_splats, const or_camera* 
     return n;
 }
 
+/* ------------------------------------------------------------------ MLP training (Sec. 3.2, 4.1) */
+/* Batch loss of the class-balanced binary cross-entropy and (if grad != NULL) its gradient with
+ * respect to the flat weights.  Sample k is Gaussian sg[k] seen from training view sv[k]; views
+ * holds, per view, the camera centre in the asset frame and its normalised focal length f_view.
+ * A sample of class c weighs B / (2 N_c), N_c = the batch count of class c ("each occurrence
+ * weighted by its frequency in the batch"); the loss is the weighted mean over the batch. */
+double or_train_loss_grad(const or_asset* a, const double* views, const uint8_t* labels,
+                          int64_t n_gauss, const int32_t* sv, const int32_t* sg, int64_t B,
+                          const double* w, double* grad) {
+    const double *W1 = w, *b1 = W1 + 64 * 32, *W2 = b1 + 64, *b2 = W2 + 64 * 64,
+                 *W3 = b2 + 64, *b3 = W3 + 64 * 64, *W4 = b3 + 64, *b4 = W4 + 64;
+    int64_t n_pos = 0;
+    for (int64_t k = 0; k < B; k++) n_pos += labels[(int64_t)sv[k] * n_gauss + sg[k]] != 0;
+    double w_pos = 1.0, w_neg = 1.0;
+    if (n_pos > 0 && n_pos < B) { w_pos = (double)B / (2.0 * n_pos); w_neg = (double)B / (2.0 * (B - n_pos)); }
+    if (grad) memset(grad, 0, sizeof(double) * OR_MLP_NW);
+    double loss = 0.0;
+    for (int64_t k = 0; k < B; k++) {
+        const double* vw = &views[4 * sv[k]];
+        double f[32], h1[64], h2[64], h3[64], z;
+        or_mlp_features(a, &a->means[3 * (int64_t)sg[k]], vw, vw[3], f);
+        dense(W1, b1, f, 32, 64, 1, h1);
+        dense(W2, b2, h1, 64, 64, 1, h2);
+        dense(W3, b3, h2, 64, 64, 1, h3);
+        dense(W4, b4, h3, 64, 1, 0, &z);
+        const int y = labels[(int64_t)sv[k] * n_gauss + sg[k]] != 0;
+        const double wy = y ? w_pos : w_neg;
+        const double p = 1.0 / (1.0 + exp(-z));
+        /* -[y log p + (1 - y) log(1 - p)], written stably */
+        loss += wy * ((z > 0 ? z : 0.0) - (y ? z : 0.0) + log1p(exp(-fabs(z)))) / (double)B;
+        if (!grad) continue;
+        double *gW1 = grad, *gb1 = gW1 + 64 * 32, *gW2 = gb1 + 64, *gb2 = gW2 + 64 * 64,
+               *gW3 = gb2 + 64, *gb3 = gW3 + 64 * 64, *gW4 = gb3 + 64, *gb4 = gW4 + 64;
+        const double dz = wy * (p - y) / (double)B;
+        double d3[64], d2[64], d1[64];
+        gb4[0] += dz;
+        for (int j = 0; j < 64; j++) {
+            gW4[j] += dz * h3[j];
+            d3[j] = h3[j] > 0.0 ? dz * W4[j] : 0.0;
+        }
+        for (int j = 0; j < 64; j++) {
+            gb3[j] += d3[j];
+            for (int i = 0; i < 64; i++) gW3[64 * j + i] += d3[j] * h2[i];
+        }
+        for (int i = 0; i < 64; i++) {
+            double s = 0.0;
+            for (int j = 0; j < 64; j++) s += d3[j] * W3[64 * j + i];
+            d2[i] = h2[i] > 0.0 ? s : 0.0;
+        }
+        for (int j = 0; j < 64; j++) {
+            gb2[j] += d2[j];
+            for (int i = 0; i < 64; i++) gW2[64 * j + i] += d2[j] * h1[i];
+        }
+        for (int i = 0; i < 64; i++) {
+            double s = 0.0;
+            for (int j = 0; j < 64; j++) s += d2[j] * W2[64 * j + i];
+            d1[i] = h1[i] > 0.0 ? s : 0.0;
+        }
+        for (int j = 0; j < 64; j++) {
+            gb1[j] += d1[j];
+            for (int i = 0; i < 32; i++) gW1[32 * j + i] += d1[j] * f[i];
+        }
+    }
+    return loss;
+}
+
+/* One Adam step (bias-corrected moments; step is 0-based) on the batch gradient above. */
+double or_train_step(const or_asset* a, const double* views, const uint8_t* labels, int64_t n_gauss,
+                     const int32_t* sv, const int32_t* sg, int64_t B, double* w, double* m,
+                     double* v, double lr, double beta1, double beta2, double eps, int step) {
+    double* g = (double*)malloc(sizeof(double) * OR_MLP_NW);
+    double loss = or_train_loss_grad(a, views, labels, n_gauss, sv, sg, B, w, g);
+    const double bc1 = 1.0 - pow(beta1, step + 1), bc2 = 1.0 - pow(beta2, step + 1);
+    for (int i = 0; i < OR_MLP_NW; i++) {
+        m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
+        v[i] = beta2 * v[i] + (1.0 - beta2) * g[i] * g[i];
+        w[i] -= lr * (m[i] / bc1) / (sqrt(v[i] / bc2) + eps);
+    }
+    free(g);
+    return loss;
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -8,6 +8,7 @@
 //   skip if power > 0;  alpha = min(alpha_max, opacity e^power);  skip if alpha < alpha_min;
 //   stop (without blending) if T (1 - alpha) < t_stop;  C += alpha T rgb;  T *= 1 - alpha.
 // The CTA leaves the range as soon as every pixel has stopped (a block-wide vote per batch).
+// With `mark` set, every blended fragment also flags its survivor (the visibility labeller).
 #include "nvgs_internal.cuh"
 
 namespace nvgs {
@@ -17,7 +18,8 @@ __global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ r
                                                   const uint32_t* __restrict__ values,
                                                   const float4* __restrict__ rec, CamParams cam,
                                                   float* __restrict__ image, float* __restrict__ final_T,
-                                                  int32_t* __restrict__ n_contrib) {
+                                                  int32_t* __restrict__ n_contrib,
+                                                  uint8_t* __restrict__ mark) {
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
@@ -55,6 +57,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ r
             if (nt < cam.t_stop) { done = true; break; }
             const float4 c = s_c[j];
             const float w = alpha * T;
+            if (mark) mark[values[base + j]] = 1;   // contribution alpha * T > 0 (Sec. 3.1)
             C0 = fmaf(w, c.x, C0);
             C1 = fmaf(w, c.y, C1);
             C2 = fmaf(w, c.z, C2);
@@ -74,15 +77,29 @@ __global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ r
 
 cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const float4* rec,
                          CamParams cam, float* image, float* final_T, int32_t* n_contrib,
-                         cudaStream_t s, LaunchLog* log) {
+                         uint8_t* mark, cudaStream_t s, LaunchLog* log) {
     const int n_tiles = cam.tiles_x * cam.tiles_y;
     if (n_tiles <= 0) return cudaSuccess;
     switch (cam.tile_size) {
-        case 8: NVGS_LAUNCH(log, s, "k_blend<8>", k_blend<8><<<n_tiles, 64, 0, s>>>(ranges, values, rec, cam, image, final_T, n_contrib)); break;
-        case 16: NVGS_LAUNCH(log, s, "k_blend<16>", k_blend<16><<<n_tiles, 256, 0, s>>>(ranges, values, rec, cam, image, final_T, n_contrib)); break;
-        case 32: NVGS_LAUNCH(log, s, "k_blend<32>", k_blend<32><<<n_tiles, 1024, 0, s>>>(ranges, values, rec, cam, image, final_T, n_contrib)); break;
+        case 8: NVGS_LAUNCH(log, s, "k_blend<8>", k_blend<8><<<n_tiles, 64, 0, s>>>(ranges, values, rec, cam, image, final_T, n_contrib, mark)); break;
+        case 16: NVGS_LAUNCH(log, s, "k_blend<16>", k_blend<16><<<n_tiles, 256, 0, s>>>(ranges, values, rec, cam, image, final_T, n_contrib, mark)); break;
+        case 32: NVGS_LAUNCH(log, s, "k_blend<32>", k_blend<32><<<n_tiles, 1024, 0, s>>>(ranges, values, rec, cam, image, final_T, n_contrib, mark)); break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_mark_labels(const uint2* __restrict__ surv, uint32_t n,
+                                                     const uint8_t* __restrict__ mark,
+                                                     uint8_t* __restrict__ labels_row) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && mark[i]) labels_row[surv[i].y] = 1;
+}
+
+cudaError_t launch_mark_labels(const uint2* surv, uint32_t n_surv, const uint8_t* mark,
+                               uint8_t* labels_row, cudaStream_t s, LaunchLog* log) {
+    if (n_surv == 0) return cudaSuccess;
+    NVGS_LAUNCH(log, s, "k_mark_labels", k_mark_labels<<<(n_surv + 255) / 256, 256, 0, s>>>(surv, n_surv, mark, labels_row));
     return cudaGetLastError();
 }
 

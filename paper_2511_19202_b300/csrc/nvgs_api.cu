@@ -50,7 +50,14 @@ struct nvgs_ctx {
     // per-frame buffers
     DevBuf frame_inst, bits, chunk_counts, chunk_offsets, vis_list, keep_bits, logits_tmp,
         block_counts, block_offsets, surv, rec, rects, tile_counts, tile_offsets, keys, vals,
-        keys_alt, vals_alt, ranges, scratch, counters, image_tmp, final_T, n_contrib;
+        keys_alt, vals_alt, ranges, scratch, counters, image_tmp, final_T, n_contrib, mark;
+    // visibility-MLP training state, per asset (FP32 master weights, Adam moments, views)
+    struct Train {
+        DevBuf w, m, v, views;
+        int n_views = 0;
+    };
+    std::vector<Train> train;
+    DevBuf tr_sv, tr_sg, tr_partial;
     uint32_t* h_counters = nullptr;  // pinned mirror of counters
 
     cudaEvent_t ev[NVGS_NUM_STAGES + 1] = {};
@@ -363,7 +370,8 @@ extern "C" nvgs_status nvgs_destroy(nvgs_ctx* ctx) {
                       &ctx->block_offsets, &ctx->surv, &ctx->rec, &ctx->rects, &ctx->tile_counts,
                       &ctx->tile_offsets, &ctx->keys, &ctx->vals, &ctx->keys_alt, &ctx->vals_alt,
                       &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
-                      &ctx->n_contrib};
+                      &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial};
+    for (auto& t : ctx->train) { release(t.w); release(t.m); release(t.v); release(t.views); }
     for (DevBuf* b : bufs) release(*b);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     if (ctx->events_ready)
@@ -576,8 +584,10 @@ extern "C" nvgs_status nvgs_query_visibility(nvgs_ctx* ctx, const nvgs_camera* c
     return NVGS_OK;
 }
 
-extern "C" nvgs_status nvgs_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_render_flags* f,
-                                   float* image, nvgs_frame_stats* stats) {
+// The whole pass for one camera.  labels_row (nullable, device, one byte per Gaussian of the
+// scene's single instance) receives 1 for every Gaussian blended at some pixel (the labeller).
+static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_render_flags* f,
+                             float* image, nvgs_frame_stats* stats, uint8_t* labels_row) {
     if (!ctx) return NVGS_ERR_INVALID_ARG;
     nvgs_status st = validate_flags(ctx, f);
     if (st != NVGS_OK) return st;
@@ -666,8 +676,15 @@ extern "C" nvgs_status nvgs_render(nvgs_ctx* ctx, const nvgs_camera* cam, const 
         fT = P<float>(ctx->final_T);
         nc = P<int32_t>(ctx->n_contrib);
     }
-    CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, img_dev, fT, nc, s,
+    uint8_t* mark = nullptr;
+    if (labels_row) {
+        CK(ensure(ctx->mark, (size_t)n_surv + 16));
+        mark = P<uint8_t>(ctx->mark);
+        CK(cudaMemsetAsync(mark, 0, (size_t)n_surv + 1, s));
+    }
+    CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, img_dev, fT, nc, mark, s,
                     &ctx->log));
+    if (labels_row) CK(launch_mark_labels(surv, n_surv, mark, labels_row, s, &ctx->log));
     tm.mark(NVGS_NUM_STAGES);
     if (f->image_memory == NVGS_MEM_HOST)
         CK(cudaMemcpyAsync(image, img_dev, npx * 12, cudaMemcpyDeviceToHost, s));
@@ -705,6 +722,201 @@ extern "C" nvgs_status nvgs_render(nvgs_ctx* ctx, const nvgs_camera* cam, const 
         }
     }
     return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_render_flags* f,
+                                   float* image, nvgs_frame_stats* stats) {
+    return do_render(ctx, cam, f, image, stats, nullptr);
+}
+
+// ============================================================================ N1: labeller + trainer
+extern "C" nvgs_status nvgs_label_visibility(nvgs_ctx* ctx, int asset_id, const nvgs_camera* views,
+                                             int n_views, int group, const nvgs_render_flags* flags,
+                                             uint8_t* labels) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (asset_id < 0 || asset_id >= (int)ctx->assets.size())
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "asset_id %d out of range", asset_id);
+    if (!views || n_views < 1 || group < 1 || n_views % group != 0 || !labels)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "need views, n_views >= 1 divisible by group >= 1, labels");
+    nvgs_status st = validate_flags(ctx, flags);
+    if (st != NVGS_OK) return st;
+    CK(cudaSetDevice(ctx->device));
+    // render the asset alone (identity instance, no MLP), then restore the caller's scene
+    const std::vector<nvgs_instance> saved = ctx->instances;
+    nvgs_instance one{};
+    one.asset_id = asset_id;
+    one.R[0] = one.R[4] = one.R[8] = 1.0f;
+    one.s = 1.0f;
+    if ((st = nvgs_set_instances(ctx, &one, 1)) != NVGS_OK) return st;
+    nvgs_render_flags fl = *flags;
+    fl.use_mlp = 0;
+    fl.image_memory = NVGS_MEM_DEVICE;
+    fl.logits_override = nullptr;
+    fl.keep_outputs = 0;
+    const int64_t n = ctx->assets[asset_id].dev.n;
+    CK(cudaMemsetAsync(labels, 0, (size_t)(n_views / group) * n, ctx->stream));
+    for (int v = 0; v < n_views && st == NVGS_OK; v++) {
+        const size_t npx = (size_t)views[v].width * views[v].height;
+        if (ensure(ctx->image_tmp, npx * 12) != cudaSuccess) { st = fail(ctx, NVGS_ERR_OOM, "labeller image"); break; }
+        st = do_render(ctx, &views[v], &fl, P<float>(ctx->image_tmp), nullptr,
+                       labels + (size_t)(v / group) * n);
+    }
+    nvgs_status st2 = saved.empty() ? NVGS_OK : nvgs_set_instances(ctx, saved.data(), (int)saved.size());
+    if (saved.empty()) { ctx->instances.clear(); ctx->n_instanced = 0; ctx->n_chunks = 0; }
+    return st != NVGS_OK ? st : st2;
+}
+
+extern "C" nvgs_status nvgs_train_init(nvgs_ctx* ctx, int asset_id, const float* w0,
+                                       const nvgs_camera* views, int n_views) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (asset_id < 0 || asset_id >= (int)ctx->assets.size())
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "asset_id %d out of range", asset_id);
+    if (!w0 || !views || n_views < 1) return fail(ctx, NVGS_ERR_INVALID_ARG, "weights / views missing");
+    CK(cudaSetDevice(ctx->device));
+    if (ctx->train.size() < ctx->assets.size()) ctx->train.resize(ctx->assets.size());
+    auto& T = ctx->train[asset_id];
+    CK(ensure(T.w, kMlpWeights * 4));
+    CK(ensure(T.m, kMlpWeights * 4));
+    CK(ensure(T.v, kMlpWeights * 4));
+    CK(ensure(T.views, (size_t)n_views * 16));
+    CK(cudaMemcpy(T.w.p, w0, kMlpWeights * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemset(T.m.p, 0, kMlpWeights * 4));
+    CK(cudaMemset(T.v.p, 0, kMlpWeights * 4));
+    const float f_t = ctx->assets[asset_id].dev.train_focal;
+    std::vector<float4> vt(n_views);
+    for (int v = 0; v < n_views; v++) {
+        const nvgs_camera& c = views[v];
+        if (!(c.fx > 0.f) || c.width < 1) return fail(ctx, NVGS_ERR_INVALID_ARG, "view %d invalid", v);
+        double cc[3];
+        for (int q = 0; q < 3; q++)   // camera centre -R^T t (the asset frame is the world frame)
+            cc[q] = -((double)c.R[q] * c.t[0] + (double)c.R[3 + q] * c.t[1] + (double)c.R[6 + q] * c.t[2]);
+        const double f_view = 2.0 * c.fx / c.width;
+        vt[v] = make_float4((float)cc[0], (float)cc[1], (float)cc[2], (float)(f_t / f_view));
+    }
+    CK(cudaMemcpy(T.views.p, vt.data(), (size_t)n_views * 16, cudaMemcpyHostToDevice));
+    T.n_views = n_views;
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_train_visibility_step(nvgs_ctx* ctx, int asset_id, const nvgs_train_batch* b,
+                                                  const nvgs_adam_cfg* adam, float* loss_out) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (asset_id < 0 || asset_id >= (int)ctx->train.size() || !ctx->train[asset_id].n_views)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "asset %d has no training state (nvgs_train_init)", asset_id);
+    if (!b || !adam || !b->labels || b->batch < 1 || (!b->sample_view) != (!b->sample_gauss))
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "bad batch");
+    if (!(adam->lr >= 0.f) || !(adam->beta1 >= 0.f && adam->beta1 < 1.f) ||
+        !(adam->beta2 >= 0.f && adam->beta2 < 1.f) || !(adam->eps > 0.f) || adam->step < 0)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "bad Adam configuration");
+    CK(cudaSetDevice(ctx->device));
+    auto& T = ctx->train[asset_id];
+    const uint32_t B = (uint32_t)b->batch;
+    const bool expl = b->sample_view != nullptr;
+    CK(ensure(ctx->tr_sv, (size_t)B * 4));
+    CK(ensure(ctx->tr_sg, (size_t)B * 4));
+    CK(ensure(ctx->tr_partial, train_partial_bytes(B)));
+    cudaStream_t s = ctx->stream;
+    if (expl) {
+        CK(cudaMemcpyAsync(ctx->tr_sv.p, b->sample_view, (size_t)B * 4, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->tr_sg.p, b->sample_gauss, (size_t)B * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    {
+        const nvgs_status ust = upload_assets(ctx);
+        if (ust != NVGS_OK) return ust;
+    }
+    uint32_t* counters = P<uint32_t>(ctx->counters);
+    ctx->log.count = 0;
+    CK(launch_train_step(P<AssetDev>(ctx->assets_dev) + asset_id, (uint32_t)ctx->assets[asset_id].dev.n,
+                         P<float4>(T.views), (uint32_t)T.n_views, b->labels, B, b->seed,
+                         (uint32_t)adam->step, P<int32_t>(ctx->tr_sv), P<int32_t>(ctx->tr_sg), expl ? 1 : 0,
+                         &counters[10], reinterpret_cast<float*>(&counters[11]), P<float>(ctx->tr_partial),
+                         P<float>(T.w), P<float>(T.m), P<float>(T.v), adam->lr, adam->beta1, adam->beta2,
+                         adam->eps, s, &ctx->log));
+    if (loss_out) {
+        CK(cudaMemcpyAsync(ctx->h_counters + 11, &counters[11], 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        memcpy(loss_out, ctx->h_counters + 11, 4);
+    }
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_train_get_weights(nvgs_ctx* ctx, int asset_id, float* w_out) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (asset_id < 0 || asset_id >= (int)ctx->train.size() || !ctx->train[asset_id].n_views || !w_out)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "asset %d has no training state", asset_id);
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(w_out, ctx->train[asset_id].w.p, kMlpWeights * 4, cudaMemcpyDeviceToHost));
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_get_asset_info(const nvgs_ctx* ctx, int asset_id, nvgs_asset_info* out) {
+    if (!ctx || !out || asset_id < 0 || asset_id >= (int)ctx->assets.size()) return NVGS_ERR_INVALID_ARG;
+    const AssetDev& a = ctx->assets[asset_id].dev;
+    out->n = a.n;
+    out->sh_degree = a.sh_degree;
+    for (int k = 0; k < 3; k++) {
+        out->bbox_center[k] = a.bbox_c[k];
+        out->bbox_half_extent[k] = 1.0f / a.bbox_scale[k];
+    }
+    out->d_min = a.d_min;
+    out->d_max = a.d_max;
+    out->train_fov_x = (float)(2.0 * std::atan(1.0 / a.train_focal));
+    out->has_mlp = ctx->assets[asset_id].precision;
+    return NVGS_OK;
+}
+
+// Training cameras of Sec. 3.1 / 4.1: n_dirs directions on a Fibonacci sphere around the box
+// centre, each at n_dist distances log-spaced from d_min to d_max (one distance: d_min), looking
+// at the centre with the asset's training field of view.  Direction-major order.
+extern "C" nvgs_status nvgs_training_views(const nvgs_ctx* ctx, int asset_id, int n_dirs, int n_dist,
+                                           int width, int height, nvgs_camera* out) {
+    if (!ctx || !out || asset_id < 0 || asset_id >= (int)ctx->assets.size() || n_dirs < 1 ||
+        n_dist < 1 || width < 1 || height < 1)
+        return NVGS_ERR_INVALID_ARG;
+    const AssetDev& a = ctx->assets[asset_id].dev;
+    const double golden = M_PI * (3.0 - std::sqrt(5.0));
+    const double fx = (width / 2.0) * a.train_focal;   // (W/2) / tan(theta_t / 2)
+    for (int k = 0; k < n_dirs; k++) {
+        const double y = 1.0 - 2.0 * (k + 0.5) / n_dirs;
+        const double rad = std::sqrt(std::max(0.0, 1.0 - y * y));
+        const double ph = golden * k;
+        const double dir[3] = {rad * std::cos(ph), y, rad * std::sin(ph)};
+        for (int j = 0; j < n_dist; j++) {
+            const double u = n_dist > 1 ? (double)j / (n_dist - 1) : 0.0;
+            const double d = a.d_min * std::pow((double)a.d_max / a.d_min, u);
+            double eye[3], f[3], r[3], dn[3];
+            for (int q = 0; q < 3; q++) { eye[q] = a.bbox_c[q] + d * dir[q]; f[q] = -dir[q]; }
+            // right = f x up (up = +y, or +z when looking along y), down = f x right
+            double up[3] = {0.0, 1.0, 0.0};
+            if (std::fabs(f[1]) > 0.999) { up[1] = 0.0; up[2] = 1.0; }
+            r[0] = f[1] * up[2] - f[2] * up[1]; r[1] = f[2] * up[0] - f[0] * up[2]; r[2] = f[0] * up[1] - f[1] * up[0];
+            const double rn = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+            for (int q = 0; q < 3; q++) r[q] /= rn;
+            dn[0] = f[1] * r[2] - f[2] * r[1]; dn[1] = f[2] * r[0] - f[0] * r[2]; dn[2] = f[0] * r[1] - f[1] * r[0];
+            nvgs_camera& c = out[k * n_dist + j];
+            const double* rows[3] = {r, dn, f};
+            for (int p = 0; p < 3; p++) {
+                for (int q = 0; q < 3; q++) c.R[3 * p + q] = (float)rows[p][q];
+                c.t[p] = (float)(-(rows[p][0] * eye[0] + rows[p][1] * eye[1] + rows[p][2] * eye[2]));
+            }
+            c.fx = c.fy = (float)fx;
+            c.cx = width / 2.0f;
+            c.cy = height / 2.0f;
+            c.width = width;
+            c.height = height;
+            c.z_near = 0.2f;
+        }
+    }
+    return NVGS_OK;
+}
+
+extern "C" float nvgs_lr_schedule(int step, int total, float lr0, float lr1, float warmup_frac) {
+    if (total <= 0) return lr0;
+    const double tw = std::max(1.0, (double)warmup_frac * total);
+    if (step < tw) return (float)(lr0 * 0.5 * (1.0 - std::cos(M_PI * (step + 1) / tw)));
+    const double u = std::min(1.0, (step - tw) / std::max(1.0, total - tw));
+    return (float)(lr0 * std::pow((double)lr1 / lr0, u));
 }
 
 extern "C" nvgs_status nvgs_last_frame(const nvgs_ctx* ctx, nvgs_frame_view* out) {

@@ -146,6 +146,15 @@ cudaError_t launch_mlp_tc(const uint2* list, uint32_t n, const FrameInst* fi,
 size_t mlp_tc_weight_bytes();
 void mlp_tc_pack_weights(const float* w, uint8_t* out);
 
+// One training step of the visibility MLP (k_train.cu); partial needs train_partial_bytes(B).
+size_t train_partial_bytes(uint32_t B);
+cudaError_t launch_train_step(const AssetDev* asset_dev, uint32_t n_gauss, const float4* views,
+                              uint32_t n_views, const uint8_t* labels, uint32_t B, uint64_t seed,
+                              uint32_t step, int32_t* sv, int32_t* sg, int explicit_samples,
+                              uint32_t* n_pos, float* loss_sum, float* partial, float* w, float* m,
+                              float* v, float lr, float beta1, float beta2, float eps,
+                              cudaStream_t s, LaunchLog* log);
+
 // Per-block popcounts of a bitmask over n items (blocks of kChunk items).
 cudaError_t launch_bit_counts(const uint32_t* bits, uint32_t n, uint32_t* block_counts,
                               cudaStream_t s, LaunchLog* log);
@@ -175,9 +184,13 @@ cudaError_t launch_tile_ranges(const unsigned long long* keys, uint32_t n, int d
                                uint32_t* ranges, cudaStream_t s, LaunchLog* log);
 
 // S6
+// mark (nullable, per survivor): set to 1 when the survivor is blended at some pixel.
 cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const float4* rec,
                          CamParams cam, float* image, float* final_T, int32_t* n_contrib,
-                         cudaStream_t s, LaunchLog* log);
+                         uint8_t* mark, cudaStream_t s, LaunchLog* log);
+// labels[row * n_gauss + g] |= mark[s] for survivor s = (instance, g)
+cudaError_t launch_mark_labels(const uint2* surv, uint32_t n_surv, const uint8_t* mark,
+                               uint8_t* labels_row, cudaStream_t s, LaunchLog* log);
 
 // ------------------------------------------------------------------ generic device primitives
 // Exclusive scan of n uint32 values; total (nullable, device) receives the sum.  Needs

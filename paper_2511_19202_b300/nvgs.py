@@ -80,6 +80,22 @@ class FrameView(C.Structure):
                 ("tile_size", C.c_int32), ("depth_bits", C.c_int32)]
 
 
+class AssetInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("has_mlp", C.c_int32),
+                ("bbox_center", C.c_float * 3), ("bbox_half_extent", C.c_float * 3),
+                ("d_min", C.c_float), ("d_max", C.c_float), ("train_fov_x", C.c_float)]
+
+
+class TrainBatch(C.Structure):
+    _fields_ = [("labels", C.c_void_p), ("batch", C.c_int32), ("pad_", C.c_int32),
+                ("sample_view", C.c_void_p), ("sample_gauss", C.c_void_p), ("seed", C.c_uint64)]
+
+
+class AdamCfg(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("step", C.c_int32)]
+
+
 class KernelStat(C.Structure):
     _fields_ = [("name", C.c_char * 40), ("launches", C.c_uint64), ("total_ms", C.c_double)]
 
@@ -88,7 +104,9 @@ EXPORTS = ("nvgs_create", "nvgs_destroy", "nvgs_last_error", "nvgs_get_stream", 
            "nvgs_abi_version", "nvgs_load_asset", "nvgs_set_mlp", "nvgs_set_instances",
            "nvgs_scene_info", "nvgs_query_visibility", "nvgs_render", "nvgs_last_frame",
            "nvgs_sort_pairs", "nvgs_kernel_stats", "nvgs_reset_kernel_stats",
-           "nvgs_sort_pairs_noalloc")
+           "nvgs_sort_pairs_noalloc", "nvgs_label_visibility", "nvgs_train_init",
+           "nvgs_train_visibility_step", "nvgs_train_get_weights", "nvgs_lr_schedule",
+           "nvgs_get_asset_info", "nvgs_training_views")
 NVGS_SORT_NOALLOC_MAX_PAIRS = 1 << 20
 
 
@@ -117,8 +135,17 @@ def _load():
     L.nvgs_kernel_stats.argtypes = [vp, vp, C.c_int, P(C.c_int)]
     L.nvgs_reset_kernel_stats.argtypes = [vp]
     L.nvgs_sort_pairs_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int, vp]
+    L.nvgs_label_visibility.argtypes = [vp, C.c_int, vp, C.c_int, C.c_int, P(RenderFlags), vp]
+    L.nvgs_train_init.argtypes = [vp, C.c_int, vp, vp, C.c_int]
+    L.nvgs_train_visibility_step.argtypes = [vp, C.c_int, P(TrainBatch), P(AdamCfg), P(C.c_float)]
+    L.nvgs_train_get_weights.argtypes = [vp, C.c_int, vp]
+    L.nvgs_lr_schedule.argtypes = [C.c_int, C.c_int, C.c_float, C.c_float, C.c_float]
+    L.nvgs_lr_schedule.restype = C.c_float
+    L.nvgs_get_asset_info.argtypes = [vp, C.c_int, P(AssetInfo)]
+    L.nvgs_training_views.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
     for name in EXPORTS:
-        if name not in ("nvgs_default_flags", "nvgs_abi_version", "nvgs_last_error", "nvgs_get_stream"):
+        if name not in ("nvgs_default_flags", "nvgs_abi_version", "nvgs_last_error", "nvgs_get_stream",
+                        "nvgs_lr_schedule"):
             getattr(L, name).restype = C.c_int
     return L
 
@@ -284,3 +311,64 @@ def nvgs_sort_pairs_noalloc(keys, values, n: int, key_bits: int, stream=None) ->
     callers can test the capacity error."""
     s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
     return lib.nvgs_sort_pairs_noalloc(_ptr(keys), _ptr(values), int(n), int(key_bits), s)
+
+
+def _cam_array(cams):
+    if isinstance(cams, C.Array):
+        return cams
+    arr = (Camera * len(cams))()
+    for k, c in enumerate(cams):
+        arr[k] = c if isinstance(c, Camera) else camera(c)
+    return arr
+
+
+def nvgs_label_visibility(ctx, asset_id: int, views, flags: RenderFlags, labels, group: int = 1):
+    arr = _cam_array(views)
+    _check(ctx, lib.nvgs_label_visibility(ctx, int(asset_id), C.cast(arr, C.c_void_p), len(arr),
+                                          int(group), C.byref(flags), _ptr(labels)))
+
+
+def nvgs_train_init(ctx, asset_id: int, w0, views):
+    w = flat_weights(w0)
+    arr = _cam_array(views)
+    _check(ctx, lib.nvgs_train_init(ctx, int(asset_id), w.ctypes.data, C.cast(arr, C.c_void_p), len(arr)))
+
+
+def nvgs_train_visibility_step(ctx, asset_id: int, labels, batch: int, step: int, lr: float,
+                               seed: int = 0, sample_view=None, sample_gauss=None,
+                               beta1=0.9, beta2=0.999, eps=1e-8, want_loss=False):
+    b = TrainBatch()
+    b.labels = _ptr(labels)
+    b.batch = int(batch)
+    b.sample_view = _ptr(sample_view)
+    b.sample_gauss = _ptr(sample_gauss)
+    b.seed = int(seed)
+    a = AdamCfg()
+    a.lr, a.beta1, a.beta2, a.eps, a.step = float(lr), float(beta1), float(beta2), float(eps), int(step)
+    loss = C.c_float(float("nan"))
+    _check(ctx, lib.nvgs_train_visibility_step(ctx, int(asset_id), C.byref(b), C.byref(a),
+                                               C.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def nvgs_train_get_weights(ctx, asset_id: int) -> np.ndarray:
+    w = np.zeros(MLP_WEIGHTS, np.float32)
+    _check(ctx, lib.nvgs_train_get_weights(ctx, int(asset_id), w.ctypes.data))
+    return w
+
+
+def nvgs_lr_schedule(step: int, total: int, lr0: float, lr1: float, warmup_frac: float) -> float:
+    return lib.nvgs_lr_schedule(int(step), int(total), float(lr0), float(lr1), float(warmup_frac))
+
+
+def nvgs_get_asset_info(ctx, asset_id: int) -> AssetInfo:
+    out = AssetInfo()
+    _check(ctx, lib.nvgs_get_asset_info(ctx, int(asset_id), C.byref(out)))
+    return out
+
+
+def nvgs_training_views(ctx, asset_id: int, n_dirs: int, n_dist: int, width: int, height: int):
+    arr = (Camera * (n_dirs * n_dist))()
+    _check(ctx, lib.nvgs_training_views(ctx, int(asset_id), int(n_dirs), int(n_dist), int(width),
+                                        int(height), C.cast(arr, C.c_void_p)))
+    return arr

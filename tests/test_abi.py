@@ -42,7 +42,8 @@ def test_struct_layouts_match_the_c_compiler(N):
     structs = {"nvgs_asset_desc": N.AssetDesc, "nvgs_instance": N.Instance,
                "nvgs_camera": N.Camera, "nvgs_render_flags": N.RenderFlags,
                "nvgs_frame_stats": N.FrameStats, "nvgs_frame_view": N.FrameView,
-               "nvgs_kernel_stat": N.KernelStat}
+               "nvgs_kernel_stat": N.KernelStat, "nvgs_asset_info": N.AssetInfo,
+               "nvgs_train_batch": N.TrainBatch, "nvgs_adam_cfg": N.AdamCfg}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void){']
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

@@ -1,0 +1,111 @@
+"""GPU parity of the visibility labeller and the MLP training step (N1) against the FP64 oracle,
+and an end-to-end check that training on GPU labels learns the occlusion it is shown."""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from gpu_common import renderer_for
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def test_labeller_matches_oracle_contributions():
+    sc = scenes.config1_scene(6000)
+    cams = [scenes.look_at_camera(3.0 * d, (0, 0, 0), 160, 120, 50.0) for d in scenes.fibonacci_directions(5)]
+    r = renderer_for(sc)
+    try:
+        from paper_2511_19202_b300 import nvgs as N
+        n = sc.n_instanced
+        labels = torch.zeros(len(cams) * n, dtype=torch.uint8, device="cuda")
+        N.nvgs_label_visibility(r.ctx, 0, cams, N.nvgs_default_flags(use_mlp=0), labels)
+        gpu = labels.cpu().numpy().reshape(len(cams), n).astype(bool)
+        osc = oracle.OracleScene(sc)
+        ora = oracle.labels(osc, cams)
+        agree = (gpu == ora).mean()
+        print(f"labels: agree {agree:.5f}, visible {ora.mean():.3f}, differ {(gpu != ora).sum()}")
+        assert agree >= 0.999
+        assert 0.05 < ora.mean() < 0.95
+        # the user's scene is back in place after labelling
+        img, st = r.render(scenes.config1_camera(), r.flags(use_mlp=0))
+        assert st["n_instanced"] == n
+    finally:
+        r.close()
+
+
+def test_train_step_matches_oracle_gradient():
+    """With beta1 = beta2 = 0 and lr = eps = 1e6 one Adam step moves each weight by
+    g / (1 + |g| / 1e6) ~ g, so the updated weights expose the batch gradient."""
+    from paper_2511_19202_b300 import nvgs as N
+    sc = scenes.config1_scene(3000)
+    cams = [scenes.look_at_camera(3.0 * d, (0, 0, 0), 128, 128, 50.0) for d in scenes.fibonacci_directions(6)]
+    rng = np.random.default_rng(0)
+    labels = (rng.random((6, 3000)) < 0.4).astype(np.uint8)
+    B = 1000
+    sv = rng.integers(0, 6, B).astype(np.int32)
+    sg = rng.integers(0, 3000, B).astype(np.int32)
+    w = scenes.mlp_weights(3)
+    for k in range(1, 5):
+        w[f"b{k}"] = rng.normal(0, 0.2, w[f"b{k}"].shape).astype(np.float32)
+    w0 = N.flat_weights(w)
+    r = renderer_for(sc)
+    try:
+        N.nvgs_train_init(r.ctx, 0, w0, cams)
+        d_lab = torch.from_numpy(labels.ravel()).cuda()
+        loss = N.nvgs_train_visibility_step(r.ctx, 0, d_lab, B, 0, 1e6, sample_view=torch.from_numpy(sv).cuda(),
+                                            sample_gauss=torch.from_numpy(sg).cuda(), beta1=0.0, beta2=0.0,
+                                            eps=1e6, want_loss=True)
+        w1 = N.nvgs_train_get_weights(r.ctx, 0).astype(np.float64)
+    finally:
+        r.close()
+    osc = oracle.OracleScene(sc)
+    views = oracle.training_views_table(cams)
+    ref_loss, g = oracle.train_loss_grad(osc, 0, views, labels, sv, sg, w0.astype(np.float64))
+    assert loss == pytest.approx(ref_loss, rel=1e-4)
+    step_gpu = w0.astype(np.float64) - w1
+    step_ref = g / (1.0 + np.abs(g) / 1e6)
+    scale = np.abs(step_ref).max()
+    err = np.abs(step_gpu - step_ref).max()
+    print(f"train step: loss {loss:.6f} vs {ref_loss:.6f}, max grad err {err:.2e} (scale {scale:.2e})")
+    assert err <= 1e-4 * scale + 2e-7
+
+
+def test_training_learns_back_face_occlusion():
+    """A dense sphere hides its far side: after training on GPU labels, the MLP predicts fresh
+    labels of held-out views clearly better than the majority class, and a conservative threshold
+    keeps nearly every visible Gaussian while still culling."""
+    from paper_2511_19202_b300 import nvgs as N
+    from paper_2511_19202_b300.train import train_visibility
+    a = scenes.sphere_asset(40000, seed=5, sh_degree=0)
+    sc = scenes.Scene([a], [scenes.Instance(0, np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 1.0)])
+    r = renderer_for(sc)
+    try:
+        w, info = train_visibility(r.ctx, 0, n_dirs=96, n_dist=3, res=256, steps=500, batch=32768,
+                                   precision=N.NVGS_PREC_BF16, log_every=100)
+        print({k: info[k] for k in ("label_s", "total_s", "visible_fraction", "losses")})
+        assert info["losses"][-1][1] < 0.7 * info["losses"][0][1]
+        dirs = scenes.fibonacci_directions(9)[1::2]
+        held = [scenes.look_at_camera(d * dirv, (0, 0, 0), 256, 256, 50.0) for dirv in dirs for d in (8.0, 20.0)]
+        n = a.n
+        labels = torch.zeros(len(held) * n, dtype=torch.uint8, device="cuda")
+        N.nvgs_label_visibility(r.ctx, 0, held, N.nvgs_default_flags(use_mlp=0, tile_size=16), labels)
+        lab = labels.cpu().numpy().reshape(len(held), n).astype(bool)
+        gain, recall, culled = [], [], []
+        for k, cam in enumerate(held):
+            lg, kp, _ = r.query_visibility(cam, r.flags(use_mlp=1, mlp_gate=0))
+            kp = kp.cpu().numpy().astype(bool)
+            lg = lg.cpu().numpy()
+            majority = max(lab[k].mean(), 1.0 - lab[k].mean())
+            gain.append((kp == lab[k]).mean() - majority)
+            keep = lg > -2.0
+            recall.append((keep & lab[k]).sum() / max(1, lab[k].sum()))
+            culled.append(1.0 - keep.mean())
+        print("accuracy over majority", np.round(gain, 3), "recall at -2", np.round(recall, 4),
+              "culled at -2", np.round(culled, 3))
+        assert np.mean(gain) > 0.05
+        assert np.mean(recall) > 0.97 and np.mean(culled) > 0.05
+    finally:
+        r.close()
