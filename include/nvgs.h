@@ -104,7 +104,9 @@ typedef struct {
                                     instead of the MLP (tests inject fixed decisions with it) */
     int32_t keep_outputs;        /* 1: keep final T and the contributor count per pixel for
                                     nvgs_render_backward and the labeller */
-    int32_t reserved[7];
+    int32_t blend_split_len;     /* tiles with more pairs are composited in chunks of this many
+                                    pairs on separate CTAs (0: 4096; < 0: never; else >= 256) */
+    int32_t reserved[6];
 } nvgs_render_flags;
 
 #define NVGS_NUM_STAGES 8
@@ -259,12 +261,12 @@ typedef struct {
                                     r, g, b, - */
     const int32_t* tile_rects;   /* 4 x n_survivors: tile x0, y0, x1, y1 (inclusive) */
     const uint32_t* pair_values; /* n_pairs survivor indices in (tile, depth) order */
-    const uint64_t* pair_keys;   /* n_pairs sorted keys: tile << depth_bits | depth offset */
+    const uint32_t* pair_keys;   /* n_pairs tile ids of those pairs (non-decreasing) */
     const uint32_t* tile_ranges; /* 2 x n_tiles: [start, end) into pair_values */
     const float* final_T;        /* W x H, when flags.keep_outputs */
     const int32_t* n_contrib;    /* W x H, when flags.keep_outputs: fragments blended */
     uint64_t n_survivors, n_pairs;
-    int32_t tiles_x, tiles_y, tile_size, depth_bits;
+    int32_t tiles_x, tiles_y, tile_size, depth_bits; /* depth_bits: 0 (pair_keys hold tile ids) */
 } nvgs_frame_view;
 nvgs_status nvgs_last_frame(const nvgs_ctx* ctx, nvgs_frame_view* out);
 

@@ -1,61 +1,75 @@
-// S5 (first and last parts): tile binning and tile ranges (NVGS Sec. 3.3 -> 3DGS tiled pipeline).
+// S5 around the sorts: binning and tile ranges (NVGS Sec. 3.3 -> 3DGS tiled pipeline).
 //
-// Binning writes one (key, value) pair per (survivor, covered tile) at the survivor's exclusive
-// prefix of tile counts, so pairs appear in survivor order (instance-major) before the sort.
-// key = tile << depth_bits | (depth bits - minimum depth bits): camera-space depth is positive,
-// so its IEEE bit pattern orders like the value and only the span of this frame's depths needs
-// key bits.  A stable sort of these keys gives every tile its Gaussians front to back, ties in
-// instance-then-Gaussian order.
+// The (tile, depth) order of the pairs is produced by two stable radix sorts instead of one
+// sort of 64-bit (tile << depth | depth) keys:
+//   1. the survivors are sorted by depth (32-bit IEEE pattern of the positive camera-space z),
+//      stably, so equal depths keep the survivor order (instance-major, Gaussian-minor);
+//   2. k_duplicate walks the survivors in that order and writes one (tile id, survivor) pair per
+//      covered tile at the survivor's prefix of tile counts (also taken in depth order);
+//   3. the pairs are sorted stably by tile id alone.
+// Inside every tile the pairs then come front to back with ties in survivor order, exactly the
+// order of a stable sort on (tile, depth) -- at 32-bit keys and two tile passes instead of five
+// 64-bit passes over the pairs.
 #include "nvgs_internal.cuh"
 
 namespace nvgs {
 
-__global__ void __launch_bounds__(256) k_duplicate(const int4* __restrict__ rects,
-                                                   const float4* __restrict__ rec,
+__global__ void __launch_bounds__(256) k_gather_counts(const uint32_t* __restrict__ order,
+                                                       const uint32_t* __restrict__ counts, uint32_t n,
+                                                       uint32_t* __restrict__ counts_sorted) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) counts_sorted[k] = counts[order[k]];
+}
+
+cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* counts, uint32_t n,
+                                 uint32_t* counts_sorted, cudaStream_t s, LaunchLog* log) {
+    if (n == 0) return cudaSuccess;
+    NVGS_LAUNCH(log, s, "k_gather_counts", k_gather_counts<<<(n + 255) / 256, 256, 0, s>>>(order, counts, n, counts_sorted));
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ order,
+                                                   const int4* __restrict__ rects,
                                                    const uint32_t* __restrict__ offsets, uint32_t n,
-                                                   int tiles_x, int depth_bits,
-                                                   const uint32_t* __restrict__ depth_minmax,
-                                                   unsigned long long* __restrict__ keys,
+                                                   int tiles_x, uint32_t* __restrict__ keys,
                                                    uint32_t* __restrict__ values) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t i = order[k];
     const int4 r = rects[i];
     if (r.x > r.z || r.y > r.w) return;
-    const uint32_t dk = __float_as_uint(rec[3 * (size_t)i + 1].z) - depth_minmax[0];
-    uint32_t o = offsets[i];
+    uint32_t o = offsets[k];
     for (int ty = r.y; ty <= r.w; ty++)
         for (int tx = r.x; tx <= r.z; tx++) {
-            keys[o] = ((unsigned long long)(ty * tiles_x + tx) << depth_bits) | dk;
+            keys[o] = (uint32_t)(ty * tiles_x + tx);
             values[o] = i;
             o++;
         }
 }
 
-cudaError_t launch_duplicate(const int4* rects, const float4* rec, const uint32_t* offsets,
-                             uint32_t n, int tiles_x, int depth_bits, const uint32_t* depth_minmax,
-                             unsigned long long* keys, uint32_t* values, cudaStream_t s,
-                             LaunchLog* log) {
+cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const uint32_t* offsets,
+                             uint32_t n, int tiles_x, uint32_t* keys, uint32_t* values,
+                             cudaStream_t s, LaunchLog* log) {
     if (n == 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<<<(n + 255) / 256, 256, 0, s>>>(rects, rec, offsets, n, tiles_x, depth_bits, depth_minmax, keys, values));
+    NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<<<(n + 255) / 256, 256, 0, s>>>(order, rects, offsets, n, tiles_x, keys, values));
     return cudaGetLastError();
 }
 
 // ranges[2t] / ranges[2t+1] = first / one-past-last index of tile t in the sorted keys.
 // Tiles without pairs keep the zeros the caller wrote.
-__global__ void __launch_bounds__(256) k_tile_ranges(const unsigned long long* __restrict__ keys,
-                                                     uint32_t n, int depth_bits,
+__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ keys, uint32_t n,
                                                      uint32_t* __restrict__ ranges) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t t = (uint32_t)(keys[i] >> depth_bits);
-    if (i == 0 || (uint32_t)(keys[i - 1] >> depth_bits) != t) ranges[2 * t] = i;
-    if (i == n - 1 || (uint32_t)(keys[i + 1] >> depth_bits) != t) ranges[2 * t + 1] = i + 1;
+    const uint32_t t = keys[i];
+    if (i == 0 || keys[i - 1] != t) ranges[2 * t] = i;
+    if (i == n - 1 || keys[i + 1] != t) ranges[2 * t + 1] = i + 1;
 }
 
-cudaError_t launch_tile_ranges(const unsigned long long* keys, uint32_t n, int depth_bits,
-                               uint32_t* ranges, cudaStream_t s, LaunchLog* log) {
+cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, uint32_t* ranges, cudaStream_t s,
+                               LaunchLog* log) {
     if (n == 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_tile_ranges", k_tile_ranges<<<(n + 255) / 256, 256, 0, s>>>(keys, n, depth_bits, ranges));
+    NVGS_LAUNCH(log, s, "k_tile_ranges", k_tile_ranges<<<(n + 255) / 256, 256, 0, s>>>(keys, n, ranges));
     return cudaGetLastError();
 }
 

@@ -7,11 +7,95 @@
 //   power = -1/2 (A dx^2 + C dy^2) - B dx dy      (conic [[A, B], [B, C]], pixel centre - mean)
 //   skip if power > 0;  alpha = min(alpha_max, opacity e^power);  skip if alpha < alpha_min;
 //   stop (without blending) if T (1 - alpha) < t_stop;  C += alpha T rgb;  T *= 1 - alpha.
+// A fragment whose exponent is below ln(alpha_min / opacity) minus a margin of 1e-4 is skipped
+// before the exponential: with that margin the skip never changes an alpha decision.
 // The CTA leaves the range as soon as every pixel has stopped (a block-wide vote per batch).
 // With `mark` set, every blended fragment also flags its survivor (the visibility labeller).
+//
+// Dense tiles (Sec. 4 of the supplement: many Gaussians on few pixels load-balance badly) are
+// split: a tile whose range exceeds `split_len` pairs is cut into chunks of split_len that
+// separate CTAs process in three steps --
+//   k_blend_split_T  the product of (1 - alpha) over each chunk's blended fragments per pixel;
+//   k_blend_split_C  each chunk again, entering with T = the product over the earlier chunks
+//                    (nothing to do once that is below t_stop) and applying the stop rule;
+//   k_blend_split_D  per pixel, the colours of the chunks up to the one that stopped are summed
+//                    and the transmittance left by it composes the background.
+// Only the grouping of the T products differs from the one-CTA order (FP32 rounding).
 #include "nvgs_internal.cuh"
 
 namespace nvgs {
+
+namespace {
+
+constexpr float kPowerMargin = 1e-4f;
+
+struct Frag {
+    float T, C0, C1, C2;
+    int count;
+    bool done;
+};
+
+template <int TS>
+__device__ __forceinline__ void stage(const uint32_t* __restrict__ values, const float4* __restrict__ rec,
+                                      uint32_t k, uint32_t end, float4* s_a, float4* s_b, float4* s_c) {
+    if (k < end) {
+        const size_t idx = 3 * (size_t)values[k];
+        s_a[threadIdx.x] = __ldg(&rec[idx]);
+        s_b[threadIdx.x] = __ldg(&rec[idx + 1]);
+        s_c[threadIdx.x] = __ldg(&rec[idx + 2]);
+    }
+}
+
+// Blend records [base, base + nb) (staged in shared memory) into one pixel.  transmittance_only:
+// no stop rule, no colour -- only the product of (1 - alpha).
+template <bool kTransmittanceOnly>
+__device__ __forceinline__ void blend_batch(const float4* s_a, const float4* s_b, const float4* s_c,
+                                            int nb, float fx, float fy, const CamParams& cam, Frag& f,
+                                            const uint32_t* __restrict__ values, uint32_t base,
+                                            uint8_t* __restrict__ mark) {
+    for (int j = 0; j < nb && !f.done; j++) {
+        const float4 a = s_a[j];
+        const float dx = fx - a.x, dy = fy - a.y;
+        const float4 b = s_b[j];
+        const float power = -0.5f * (a.z * dx * dx + b.x * dy * dy) - a.w * dx * dy;
+        if (power > 0.0f || power < b.w - kPowerMargin) continue;
+        const float alpha = fminf(cam.alpha_max, b.y * __expf(power));
+        if (alpha < cam.alpha_min) continue;
+        const float nt = f.T * (1.0f - alpha);
+        if (kTransmittanceOnly) {
+            f.T = nt;
+            if (nt < cam.t_stop) f.done = true;   // every later chunk is dead already
+            continue;
+        }
+        if (nt < cam.t_stop) { f.done = true; break; }
+        const float4 c = s_c[j];
+        const float w = alpha * f.T;
+        if (mark) mark[values[base + j]] = 1;   // contribution alpha * T > 0 (Sec. 3.1)
+        f.C0 = fmaf(w, c.x, f.C0);
+        f.C1 = fmaf(w, c.y, f.C1);
+        f.C2 = fmaf(w, c.z, f.C2);
+        f.T = nt;
+        f.count++;
+    }
+}
+
+// Walk pairs [start, end) for this thread's pixel with the usual batching and block-wide exit.
+template <int TS, bool kTransmittanceOnly>
+__device__ __forceinline__ void walk(const uint32_t* __restrict__ values, const float4* __restrict__ rec,
+                                     uint32_t start, uint32_t end, float fx, float fy,
+                                     const CamParams& cam, Frag& f, uint8_t* __restrict__ mark,
+                                     float4* s_a, float4* s_b, float4* s_c) {
+    constexpr int B = TS * TS;
+    for (uint32_t base = start; base < end; base += B) {
+        if (__syncthreads_count(f.done) == B) break;   // also: previous batch fully consumed
+        stage<TS>(values, rec, base + threadIdx.x, end, s_a, s_b, s_c);
+        __syncthreads();
+        const int nb = (int)min((uint32_t)B, end - base);
+        blend_batch<kTransmittanceOnly>(s_a, s_b, s_c, nb, fx, fy, cam, f, values, base, mark);
+    }
+}
+
+}  // namespace
 
 template <int TS>
 __global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ ranges,
@@ -19,74 +103,189 @@ __global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ r
                                                   const float4* __restrict__ rec, CamParams cam,
                                                   float* __restrict__ image, float* __restrict__ final_T,
                                                   int32_t* __restrict__ n_contrib,
-                                                  uint8_t* __restrict__ mark) {
+                                                  uint8_t* __restrict__ mark, uint32_t split_len) {
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
     __shared__ float4 s_c[B];
     const int tile = blockIdx.x;
+    const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
+    if (end - start > split_len) return;   // a dense tile: the split kernels own it
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
     const bool inside = px < cam.W && py < cam.H;
-    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-    const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
-
-    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    int count = 0;
-    bool done = !inside;
-    for (uint32_t base = start; base < end; base += B) {
-        if (__syncthreads_count(done) == B) break;   // also: previous batch fully consumed
-        const uint32_t k = base + threadIdx.x;
-        if (k < end) {
-            const size_t idx = 3 * (size_t)values[k];
-            s_a[threadIdx.x] = __ldg(&rec[idx]);
-            s_b[threadIdx.x] = __ldg(&rec[idx + 1]);
-            s_c[threadIdx.x] = __ldg(&rec[idx + 2]);
-        }
-        __syncthreads();
-        const int nb = (int)min((uint32_t)B, end - base);
-        for (int j = 0; j < nb && !done; j++) {
-            const float4 a = s_a[j];
-            const float dx = fx - a.x, dy = fy - a.y;
-            const float4 b = s_b[j];
-            const float power = -0.5f * (a.z * dx * dx + b.x * dy * dy) - a.w * dx * dy;
-            if (power > 0.0f) continue;
-            const float alpha = fminf(cam.alpha_max, b.y * __expf(power));
-            if (alpha < cam.alpha_min) continue;
-            const float nt = T * (1.0f - alpha);
-            if (nt < cam.t_stop) { done = true; break; }
-            const float4 c = s_c[j];
-            const float w = alpha * T;
-            if (mark) mark[values[base + j]] = 1;   // contribution alpha * T > 0 (Sec. 3.1)
-            C0 = fmaf(w, c.x, C0);
-            C1 = fmaf(w, c.y, C1);
-            C2 = fmaf(w, c.z, C2);
-            T = nt;
-            count++;
-        }
-    }
+    Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, !inside};
+    walk<TS, false>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, mark, s_a, s_b, s_c);
     if (inside) {
         const size_t p = (size_t)py * cam.W + px;
-        image[3 * p] = fmaf(T, cam.bg[0], C0);
-        image[3 * p + 1] = fmaf(T, cam.bg[1], C1);
-        image[3 * p + 2] = fmaf(T, cam.bg[2], C2);
-        if (final_T) final_T[p] = T;
-        if (n_contrib) n_contrib[p] = count;
+        image[3 * p] = fmaf(f.T, cam.bg[0], f.C0);
+        image[3 * p + 1] = fmaf(f.T, cam.bg[1], f.C1);
+        image[3 * p + 2] = fmaf(f.T, cam.bg[2], f.C2);
+        if (final_T) final_T[p] = f.T;
+        if (n_contrib) n_contrib[p] = f.count;
     }
+}
+
+// ------------------------------------------------------------------ dense tiles
+__global__ void k_split_count(const uint32_t* __restrict__ ranges, int n_tiles, uint32_t split_len,
+                              uint32_t* __restrict__ n_chunks) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const uint32_t n = ranges[2 * t + 1] - ranges[2 * t];
+    n_chunks[t] = n > split_len ? (n + split_len - 1) / split_len : 0u;
+}
+
+__global__ void k_split_fill(const uint32_t* __restrict__ n_chunks, const uint32_t* __restrict__ first,
+                             int n_tiles, uint2* __restrict__ items) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    for (uint32_t c = 0; c < n_chunks[t]; c++) items[first[t] + c] = make_uint2((uint32_t)t, c);
+}
+
+template <int TS>
+__global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __restrict__ ranges,
+                                                          const uint32_t* __restrict__ values,
+                                                          const float4* __restrict__ rec, CamParams cam,
+                                                          const uint2* __restrict__ items,
+                                                          const uint32_t* __restrict__ n_items,
+                                                          uint32_t split_len, float* __restrict__ Tch) {
+    constexpr int B = TS * TS;
+    __shared__ float4 s_a[B];
+    __shared__ float4 s_b[B];
+    __shared__ float4 s_c[B];
+    const uint32_t item = blockIdx.x;
+    if (item >= *n_items) return;
+    const uint2 it = items[item];
+    const int tile = (int)it.x;
+    const uint32_t start = ranges[2 * tile] + it.y * split_len;
+    const uint32_t end = min(ranges[2 * tile + 1], start + split_len);
+    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
+    Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, !(px < cam.W && py < cam.H)};
+    walk<TS, true>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, nullptr, s_a, s_b, s_c);
+    Tch[(size_t)item * B + threadIdx.x] = f.T;
+}
+
+template <int TS>
+__global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __restrict__ ranges,
+                                                          const uint32_t* __restrict__ values,
+                                                          const float4* __restrict__ rec, CamParams cam,
+                                                          const uint2* __restrict__ items,
+                                                          const uint32_t* __restrict__ n_items,
+                                                          uint32_t split_len, const float* __restrict__ Tch,
+                                                          float4* __restrict__ part, int32_t* __restrict__ pcount,
+                                                          uint8_t* __restrict__ mark) {
+    constexpr int B = TS * TS;
+    __shared__ float4 s_a[B];
+    __shared__ float4 s_b[B];
+    __shared__ float4 s_c[B];
+    const uint32_t item = blockIdx.x;
+    if (item >= *n_items) return;
+    const uint2 it = items[item];
+    const int tile = (int)it.x;
+    const uint32_t start = ranges[2 * tile] + it.y * split_len;
+    const uint32_t end = min(ranges[2 * tile + 1], start + split_len);
+    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
+    // transmittance entering this chunk: product over the earlier chunks of the tile
+    float T_in = 1.0f;
+    for (uint32_t c = 0; c < it.y; c++) T_in *= Tch[(size_t)(item - it.y + c) * B + threadIdx.x];
+    const bool dead = T_in < cam.t_stop;
+    Frag f{T_in, 0.0f, 0.0f, 0.0f, 0, dead || !(px < cam.W && py < cam.H)};
+    walk<TS, false>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, mark, s_a, s_b, s_c);
+    // w < 0 marks "stopped inside this chunk or before"
+    part[(size_t)item * B + threadIdx.x] = make_float4(f.C0, f.C1, f.C2, (f.done || dead) ? -f.T - 1.0f : f.T);
+    pcount[(size_t)item * B + threadIdx.x] = f.count;
+}
+
+template <int TS>
+__global__ void __launch_bounds__(TS* TS) k_blend_split_D(const uint32_t* __restrict__ n_chunks,
+                                                          const uint32_t* __restrict__ first,
+                                                          CamParams cam, const float4* __restrict__ part,
+                                                          const int32_t* __restrict__ pcount,
+                                                          float* __restrict__ image, float* __restrict__ final_T,
+                                                          int32_t* __restrict__ n_contrib) {
+    constexpr int B = TS * TS;
+    const int tile = blockIdx.x;
+    const uint32_t nc = n_chunks[tile];
+    if (nc == 0) return;
+    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
+    if (!(px < cam.W && py < cam.H)) return;
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
+    int count = 0;
+    for (uint32_t c = 0; c < nc; c++) {
+        const size_t q = (size_t)(first[tile] + c) * B + threadIdx.x;
+        const float4 v = part[q];
+        C0 += v.x; C1 += v.y; C2 += v.z;
+        count += pcount[q];
+        if (v.w < 0.0f) { T = -v.w - 1.0f; break; }   // stopped: later chunks add nothing
+        T = v.w;
+    }
+    const size_t p = (size_t)py * cam.W + px;
+    image[3 * p] = fmaf(T, cam.bg[0], C0);
+    image[3 * p + 1] = fmaf(T, cam.bg[1], C1);
+    image[3 * p + 2] = fmaf(T, cam.bg[2], C2);
+    if (final_T) final_T[p] = T;
+    if (n_contrib) n_contrib[p] = count;
+}
+
+static inline uint64_t round256(uint64_t b) { return (b + 255) / 256 * 256; }
+
+size_t blend_split_scratch_bytes(int n_tiles, uint64_t n_pairs, int tile_size, uint32_t split_len) {
+    const uint64_t items = 2 * n_pairs / split_len + 2;
+    const uint64_t B = (uint64_t)tile_size * tile_size;
+    return (size_t)(round256((uint64_t)n_tiles * 8 + 64) + round256(items * 8) + round256(items * B * 4) +
+                    round256(items * B * 16) + round256(items * B * 4));
+}
+
+template <int TS>
+static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, const float4* rec,
+                            CamParams cam, float* image, float* final_T, int32_t* n_contrib,
+                            uint8_t* mark, uint32_t split_len, uint64_t n_pairs, void* scratch,
+                            void* scan_scratch, cudaStream_t s, LaunchLog* log) {
+    constexpr int B = TS * TS;
+    const int n_tiles = cam.tiles_x * cam.tiles_y;
+    NVGS_LAUNCH(log, s, TS == 8 ? "k_blend<8>" : TS == 16 ? "k_blend<16>" : "k_blend<32>",
+                k_blend<TS><<<n_tiles, B, 0, s>>>(ranges, values, rec, cam, image, final_T, n_contrib, mark, split_len));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || n_pairs <= split_len) return e;
+    // carve the scratch
+    char* p = static_cast<char*>(scratch);
+    uint32_t* n_chunks = reinterpret_cast<uint32_t*>(p);
+    uint32_t* first = n_chunks + n_tiles;
+    uint32_t* n_items = first + n_tiles;
+    p += round256((uint64_t)n_tiles * 8 + 64);   // every section starts on a 256-byte boundary
+    const uint64_t max_items = 2 * n_pairs / split_len + 2;
+    uint2* items = reinterpret_cast<uint2*>(p);
+    p += round256(max_items * 8);
+    float* Tch = reinterpret_cast<float*>(p);
+    p += round256(max_items * B * 4);
+    float4* part = reinterpret_cast<float4*>(p);
+    p += round256(max_items * B * 16);
+    int32_t* pcount = reinterpret_cast<int32_t*>(p);
+    NVGS_LAUNCH(log, s, "k_split_count", k_split_count<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, n_tiles, split_len, n_chunks));
+    e = exclusive_scan_u32(n_chunks, first, n_tiles, n_items, scan_scratch, s, log);
+    if (e != cudaSuccess) return e;
+    NVGS_LAUNCH(log, s, "k_split_fill", k_split_fill<<<(n_tiles + 255) / 256, 256, 0, s>>>(n_chunks, first, n_tiles, items));
+    NVGS_LAUNCH(log, s, "k_blend_split_T", k_blend_split_T<TS><<<(unsigned)max_items, B, 0, s>>>(ranges, values, rec, cam, items, n_items, split_len, Tch));
+    NVGS_LAUNCH(log, s, "k_blend_split_C", k_blend_split_C<TS><<<(unsigned)max_items, B, 0, s>>>(ranges, values, rec, cam, items, n_items, split_len, Tch, part, pcount, mark));
+    NVGS_LAUNCH(log, s, "k_blend_split_D", k_blend_split_D<TS><<<n_tiles, B, 0, s>>>(n_chunks, first, cam, part, pcount, image, final_T, n_contrib));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const float4* rec,
                          CamParams cam, float* image, float* final_T, int32_t* n_contrib,
-                         uint8_t* mark, cudaStream_t s, LaunchLog* log) {
+                         uint8_t* mark, uint32_t split_len, uint64_t n_pairs, void* scratch,
+                         void* scan_scratch, cudaStream_t s, LaunchLog* log) {
     const int n_tiles = cam.tiles_x * cam.tiles_y;
     if (n_tiles <= 0) return cudaSuccess;
     switch (cam.tile_size) {
-        case 8: NVGS_LAUNCH(log, s, "k_blend<8>", k_blend<8><<<n_tiles, 64, 0, s>>>(ranges, values, rec, cam, image, final_T, n_contrib, mark)); break;
-        case 16: NVGS_LAUNCH(log, s, "k_blend<16>", k_blend<16><<<n_tiles, 256, 0, s>>>(ranges, values, rec, cam, image, final_T, n_contrib, mark)); break;
-        case 32: NVGS_LAUNCH(log, s, "k_blend<32>", k_blend<32><<<n_tiles, 1024, 0, s>>>(ranges, values, rec, cam, image, final_T, n_contrib, mark)); break;
+        case 8: return blend_ts<8>(ranges, values, rec, cam, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, s, log);
+        case 16: return blend_ts<16>(ranges, values, rec, cam, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, s, log);
+        case 32: return blend_ts<32>(ranges, values, rec, cam, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, s, log);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(256) k_mark_labels(const uint2* __restrict__ surv, uint32_t n,

@@ -46,10 +46,9 @@ __global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv,
                                                  const AssetDev* __restrict__ assets, CamParams cam,
                                                  float4* __restrict__ rec, int4* __restrict__ rects,
                                                  uint32_t* __restrict__ counts,
-                                                 uint32_t* __restrict__ depth_minmax) {
+                                                 uint32_t* __restrict__ dkey,
+                                                 uint32_t* __restrict__ didx) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool valid = false;
-    float depth = 0.0f;
     if (i < n) {
         const uint2 e = surv[i];
         const FrameInst& fi = fis[e.x];
@@ -111,12 +110,12 @@ __global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv,
                 const int ts = cam.tile_size;
                 r = make_int4((int)x0 / ts, (int)y0 / ts, (int)x1 / ts, (int)y1 / ts);
                 cnt = (uint32_t)((r.z - r.x + 1) * (r.w - r.y + 1));
-                valid = true;
-                depth = z;
             }
         }
         rects[i] = r;
         counts[i] = cnt;
+        dkey[i] = __float_as_uint(z);   // z > z_near > 0: the bit pattern orders like the value
+        didx[i] = i;
 
         // colour at the local-frame direction from the camera to the mean
         float dx = m.x - fi.cam_local[0], dy = m.y - fi.cam_local[1], dz = m.z - fi.cam_local[2];
@@ -145,27 +144,19 @@ __global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv,
             }
         }
         rec[3 * (size_t)i] = make_float4(u, v, cc / det, -cb / det);
-        rec[3 * (size_t)i + 1] = make_float4(ca / det, op, z, 0.0f);
+        // w: ln(alpha_min / opacity), the exponent below which a fragment cannot reach alpha_min
+        rec[3 * (size_t)i + 1] = make_float4(ca / det, op, z, -0.5f * kk);
         rec[3 * (size_t)i + 2] = make_float4(fmaxf(col[0], 0.0f), fmaxf(col[1], 0.0f),
                                              fmaxf(col[2], 0.0f), 0.0f);
-    }
-    // depth range of the binned splats (positive floats order like their bit patterns)
-    uint32_t lo = valid ? __float_as_uint(depth) : 0xffffffffu;
-    uint32_t hi = valid ? __float_as_uint(depth) : 0u;
-    lo = __reduce_min_sync(0xffffffffu, lo);
-    hi = __reduce_max_sync(0xffffffffu, hi);
-    if ((threadIdx.x & 31) == 0 && hi != 0u) {
-        atomicMin(&depth_minmax[0], lo);
-        atomicMax(&depth_minmax[1], hi);
     }
 }
 
 cudaError_t launch_project(const uint2* surv, uint32_t n, const FrameInst* fi,
                            const AssetDev* assets, CamParams cam, float4* rec, int4* rects,
-                           uint32_t* tile_counts, uint32_t* depth_minmax, cudaStream_t s,
+                           uint32_t* tile_counts, uint32_t* dkey, uint32_t* didx, cudaStream_t s,
                            LaunchLog* log) {
     if (n == 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_project", k_project<<<(n + 255) / 256, 256, 0, s>>>(surv, n, fi, assets, cam, rec, rects, tile_counts, depth_minmax));
+    NVGS_LAUNCH(log, s, "k_project", k_project<<<(n + 255) / 256, 256, 0, s>>>(surv, n, fi, assets, cam, rec, rects, tile_counts, dkey, didx));
     return cudaGetLastError();
 }
 

@@ -148,11 +148,13 @@ constexpr int kRsThreads = 512;
 constexpr int kRsItems = 16;
 constexpr int kRsTile = kRsThreads * kRsItems;  // 8192
 constexpr int kRsWarps = kRsThreads / 32;       // 16
-constexpr int kRsSmem = kRsWarps * 256 * 4 + kRsTile * 8 + kRsTile * 4 + 2 * 256 * 4;
 
-__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const unsigned long long* __restrict__ keys,
-                                                        uint64_t n, int shift, uint32_t n_tiles,
-                                                        uint32_t* __restrict__ hist) {
+template <typename K>
+constexpr int rs_smem_bytes() { return kRsWarps * 256 * 4 + kRsTile * (int)sizeof(K) + kRsTile * 4 + 2 * 256 * 4; }
+
+template <typename K>
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ keys, uint64_t n, int shift,
+                                                        uint32_t n_tiles, uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[kRsWarps][256];
     const int warp = threadIdx.x >> 5;
     for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) (&h[0][0])[k] = 0u;
@@ -172,14 +174,15 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const unsigned long long
     }
 }
 
+template <typename K>
 __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(
-    const unsigned long long* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-    unsigned long long* __restrict__ keys_out, uint32_t* __restrict__ vals_out, uint64_t n,
-    int shift, uint32_t n_tiles, const uint32_t* __restrict__ hist_scan) {
+    const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, K* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, uint64_t n, int shift, uint32_t n_tiles,
+    const uint32_t* __restrict__ hist_scan) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* cnt = (uint32_t*)smem;                                   // [16 warps][256]
-    unsigned long long* s_keys = (unsigned long long*)(smem + kRsWarps * 256 * 4);
-    uint32_t* s_vals = (uint32_t*)(smem + kRsWarps * 256 * 4 + kRsTile * 8);
+    K* s_keys = (K*)(smem + kRsWarps * 256 * 4);
+    uint32_t* s_vals = (uint32_t*)(smem + kRsWarps * 256 * 4 + kRsTile * sizeof(K));
     uint32_t* d_local = s_vals + kRsTile;                              // [256] tile-local start
     uint32_t* d_global = d_local + 256;                                // [256] global start
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(
     const uint64_t base = (uint64_t)blockIdx.x * kRsTile;
     const uint64_t tile_n64 = n - base < (uint64_t)kRsTile ? n - base : (uint64_t)kRsTile;
     const int tile_n = (int)tile_n64;
-    unsigned long long key[kRsItems];
+    K key[kRsItems];
     uint32_t val[kRsItems];
     uint32_t digit[kRsItems];
     uint32_t rank[kRsItems];
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(
     for (int r = 0; r < kRsItems; r++) {
         const int p = warp * (kRsItems * 32) + r * 32 + lane;
         const bool ok = p < tile_n;
-        key[r] = ok ? keys_in[base + p] : 0ull;
+        key[r] = ok ? keys_in[base + p] : (K)0;
         val[r] = ok ? vals_in[base + p] : 0u;
     }
 #pragma unroll
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(
     for (int j = 0; j < kRsItems; j++) {
         const int p = j * kRsThreads + threadIdx.x;
         if (p < tile_n) {
-            const unsigned long long k = s_keys[p];
+            const K k = s_keys[p];
             const uint32_t d = (uint32_t)(k >> shift) & 255u;
             const uint64_t g = (uint64_t)d_global[d] + (uint32_t)(p - d_local[d]);
             keys_out[g] = k;
@@ -276,10 +279,10 @@ size_t radix_scratch_bytes(uint64_t n) {
     return (size_t)(2 * h + scan_scratch_bytes(256 * tiles));
 }
 
-cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* values,
-                             unsigned long long* keys_alt, uint32_t* values_alt, uint64_t n,
-                             int key_bits, void* scratch, cudaStream_t s, LaunchLog* log,
-                             int* passes_out, int copy_back, int* result_in_alt) {
+template <typename K>
+static cudaError_t radix_sort_impl(K* keys, uint32_t* values, K* keys_alt, uint32_t* values_alt,
+                                   uint64_t n, int key_bits, void* scratch, cudaStream_t s,
+                                   LaunchLog* log, int* passes_out, int copy_back, int* result_in_alt) {
     int passes = key_bits <= 0 ? 0 : (key_bits + 7) / 8;
     if (n <= 1) passes = 0;
     if (passes_out) *passes_out = passes;
@@ -287,7 +290,8 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* values,
     if (passes == 0) return cudaSuccess;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kRsSmem);
+        cudaError_t e = cudaFuncSetAttribute(k_rs_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             rs_smem_bytes<K>());
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
@@ -296,21 +300,23 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* values,
     uint32_t* hist = (uint32_t*)scratch;
     uint32_t* hist_scan = (uint32_t*)((char*)scratch + h);
     void* scan_scratch = (char*)scratch + 2 * h;
-    unsigned long long* kin = keys;
+    K* kin = keys;
     uint32_t* vin = values;
-    unsigned long long* kout = keys_alt;
+    K* kout = keys_alt;
     uint32_t* vout = values_alt;
+    const char* hname = sizeof(K) == 8 ? "k_rs_hist<u64>" : "k_rs_hist<u32>";
+    const char* sname = sizeof(K) == 8 ? "k_rs_scatter<u64>" : "k_rs_scatter<u32>";
     for (int p = 0; p < passes; p++) {
         const int shift = 8 * p;
-        NVGS_LAUNCH(log, s, "k_rs_hist", k_rs_hist<<<(unsigned)tiles, kRsThreads, 0, s>>>(kin, n, shift, (uint32_t)tiles, hist));
+        NVGS_LAUNCH(log, s, hname, k_rs_hist<K><<<(unsigned)tiles, kRsThreads, 0, s>>>(kin, n, shift, (uint32_t)tiles, hist));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = exclusive_scan_u32(hist, hist_scan, 256 * tiles, nullptr, scan_scratch, s, log);
         if (e != cudaSuccess) return e;
-        NVGS_LAUNCH(log, s, "k_rs_scatter", k_rs_scatter<<<(unsigned)tiles, kRsThreads, kRsSmem, s>>>(kin, vin, kout, vout, n, shift, (uint32_t)tiles, hist_scan));
+        NVGS_LAUNCH(log, s, sname, k_rs_scatter<K><<<(unsigned)tiles, kRsThreads, rs_smem_bytes<K>(), s>>>(kin, vin, kout, vout, n, shift, (uint32_t)tiles, hist_scan));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        unsigned long long* tk = kin; kin = kout; kout = tk;
+        K* tk = kin; kin = kout; kout = tk;
         uint32_t* tv = vin; vin = vout; vout = tv;
     }
     if (kin != keys) {  // odd number of passes: the result sits in the alternate buffers
@@ -318,12 +324,28 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* values,
             if (result_in_alt) *result_in_alt = 1;
             return cudaSuccess;
         }
-        cudaError_t e = cudaMemcpyAsync(keys, kin, n * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s);
+        cudaError_t e = cudaMemcpyAsync(keys, kin, n * sizeof(K), cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
         e = cudaMemcpyAsync(values, vin, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* values,
+                             unsigned long long* keys_alt, uint32_t* values_alt, uint64_t n,
+                             int key_bits, void* scratch, cudaStream_t s, LaunchLog* log,
+                             int* passes_out, int copy_back, int* result_in_alt) {
+    return radix_sort_impl<unsigned long long>(keys, values, keys_alt, values_alt, n, key_bits, scratch,
+                                               s, log, passes_out, copy_back, result_in_alt);
+}
+
+cudaError_t radix_sort_pairs_u32(uint32_t* keys, uint32_t* values, uint32_t* keys_alt,
+                                 uint32_t* values_alt, uint64_t n, int key_bits, void* scratch,
+                                 cudaStream_t s, LaunchLog* log, int* passes_out, int copy_back,
+                                 int* result_in_alt) {
+    return radix_sort_impl<uint32_t>(keys, values, keys_alt, values_alt, n, key_bits, scratch, s, log,
+                                     passes_out, copy_back, result_in_alt);
 }
 
 }  // namespace nvgs

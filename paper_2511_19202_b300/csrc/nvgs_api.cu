@@ -50,7 +50,8 @@ struct nvgs_ctx {
     // per-frame buffers
     DevBuf frame_inst, bits, chunk_counts, chunk_offsets, vis_list, keep_bits, logits_tmp,
         block_counts, block_offsets, surv, rec, rects, tile_counts, tile_offsets, keys, vals,
-        keys_alt, vals_alt, ranges, scratch, counters, image_tmp, final_T, n_contrib, mark;
+        keys_alt, vals_alt, ranges, scratch, counters, image_tmp, final_T, n_contrib, mark, dkey,
+        didx, dkey_alt, didx_alt, split_scratch;
     // visibility-MLP training state, per asset (FP32 master weights, Adam moments, views)
     struct Train {
         DevBuf w, m, v, views;
@@ -135,6 +136,8 @@ nvgs_status validate_flags(nvgs_ctx* ctx, const nvgs_render_flags* f) {
     if (!(f->alpha_min > 0.f && f->alpha_min < 1.f) || !(f->alpha_max > 0.f && f->alpha_max <= 1.f) ||
         !(f->t_stop >= 0.f && f->t_stop < 1.f) || !(f->dilation >= 0.f) || !(f->guard_band > 0.f))
         return fail(ctx, NVGS_ERR_INVALID_ARG, "blending constants out of range");
+    if (f->blend_split_len > 0 && f->blend_split_len < 256)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "blend_split_len must be 0, negative or >= 256");
     if (f->image_memory != NVGS_MEM_HOST && f->image_memory != NVGS_MEM_DEVICE)
         return fail(ctx, NVGS_ERR_INVALID_ARG, "image_memory must be NVGS_MEM_HOST or NVGS_MEM_DEVICE");
     return NVGS_OK;
@@ -370,7 +373,8 @@ extern "C" nvgs_status nvgs_destroy(nvgs_ctx* ctx) {
                       &ctx->block_offsets, &ctx->surv, &ctx->rec, &ctx->rects, &ctx->tile_counts,
                       &ctx->tile_offsets, &ctx->keys, &ctx->vals, &ctx->keys_alt, &ctx->vals_alt,
                       &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
-                      &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial};
+                      &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial,
+                      &ctx->dkey, &ctx->didx, &ctx->dkey_alt, &ctx->didx_alt, &ctx->split_scratch};
     for (auto& t : ctx->train) { release(t.w); release(t.m); release(t.v); release(t.views); }
     for (DevBuf* b : bufs) release(*b);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
@@ -623,42 +627,52 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     CK(ensure(ctx->rects, cap * 16 + 16));
     CK(ensure(ctx->tile_counts, cap * 4 + 16));
     CK(ensure(ctx->tile_offsets, cap * 4 + 16));
-    CK(ensure(ctx->scratch, std::max({scan_scratch_bytes(ctx->n_chunks), scan_scratch_bytes(cap + 1)})));
-    CK(cudaMemsetAsync(counters + 3, 0xff, 4, s));   // depth min bits
-    CK(cudaMemsetAsync(counters + 4, 0x00, 4, s));   // depth max bits
+    CK(ensure(ctx->dkey, cap * 4 + 16));
+    CK(ensure(ctx->didx, cap * 4 + 16));
+    CK(ensure(ctx->dkey_alt, cap * 4 + 16));
+    CK(ensure(ctx->didx_alt, cap * 4 + 16));
+    CK(ensure(ctx->scratch, std::max({scan_scratch_bytes(ctx->n_chunks), scan_scratch_bytes(cap + 1),
+                                      radix_scratch_bytes(n_surv)})));
     CK(launch_project(surv, n_surv, P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev), cp,
                       P<float4>(ctx->rec), P<int4>(ctx->rects), P<uint32_t>(ctx->tile_counts),
-                      counters + 3, s, &ctx->log));
+                      P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), s, &ctx->log));
 
-    // ---- S5: scan of tile counts, binning, sort, ranges
+    // ---- S5: survivors by depth, pairs in that order, pairs by tile, tile ranges
     tm.mark(NVGS_STAGE_BIN);
-    CK(exclusive_scan_u32(P<uint32_t>(ctx->tile_counts), P<uint32_t>(ctx->tile_offsets), n_surv,
+    int dpasses = 0, d_alt = 0;
+    CK(radix_sort_pairs_u32(P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), P<uint32_t>(ctx->dkey_alt),
+                            P<uint32_t>(ctx->didx_alt), n_surv, 32, ctx->scratch.p, s, &ctx->log,
+                            &dpasses, 0, &d_alt));
+    const uint32_t* order = d_alt ? P<uint32_t>(ctx->didx_alt) : P<uint32_t>(ctx->didx);
+    if (n_surv <= 1) order = P<uint32_t>(ctx->didx);
+    CK(launch_gather_counts(order, P<uint32_t>(ctx->tile_counts), n_surv, P<uint32_t>(ctx->tile_offsets),
+                            s, &ctx->log));
+    CK(exclusive_scan_u32(P<uint32_t>(ctx->tile_offsets), P<uint32_t>(ctx->tile_offsets), n_surv,
                           counters + 2, ctx->scratch.p, s, &ctx->log));
-    CK(cudaMemcpyAsync(ctx->h_counters + 2, counters + 2, 12, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_counters + 2, counters + 2, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const uint32_t n_pairs = n_surv ? ctx->h_counters[2] : 0u;
-    const uint32_t dlo = ctx->h_counters[3], dhi = ctx->h_counters[4];
-    const int depth_bits = (n_pairs > 0 && dhi >= dlo) ? std::max(1, bit_width(dhi - dlo)) : 1;
     const int n_tiles = cp.tiles_x * cp.tiles_y;
     const int tile_bits = std::max(1, bit_width((uint64_t)n_tiles - 1));
-    CK(ensure(ctx->keys, (size_t)n_pairs * 8 + 16));
+    CK(ensure(ctx->keys, (size_t)n_pairs * 4 + 16));
     CK(ensure(ctx->vals, (size_t)n_pairs * 4 + 16));
-    CK(ensure(ctx->keys_alt, (size_t)n_pairs * 8 + 16));
+    CK(ensure(ctx->keys_alt, (size_t)n_pairs * 4 + 16));
     CK(ensure(ctx->vals_alt, (size_t)n_pairs * 4 + 16));
     CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
     if (radix_scratch_bytes(n_pairs) > ctx->scratch.cap) CK(ensure(ctx->scratch, radix_scratch_bytes(n_pairs)));
-    CK(launch_duplicate(P<int4>(ctx->rects), P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets), n_surv,
-                        cp.tiles_x, depth_bits, counters + 3, P<unsigned long long>(ctx->keys),
-                        P<uint32_t>(ctx->vals), s, &ctx->log));
+    CK(launch_duplicate(order, P<int4>(ctx->rects), P<uint32_t>(ctx->tile_offsets), n_surv, cp.tiles_x,
+                        P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), s, &ctx->log));
     tm.mark(NVGS_STAGE_SORT);
     int passes = 0, in_alt = 0;
-    CK(radix_sort_pairs(P<unsigned long long>(ctx->keys), P<uint32_t>(ctx->vals),
-                        P<unsigned long long>(ctx->keys_alt), P<uint32_t>(ctx->vals_alt), n_pairs,
-                        tile_bits + depth_bits, ctx->scratch.p, s, &ctx->log, &passes, 0, &in_alt));
-    unsigned long long* skeys = in_alt ? P<unsigned long long>(ctx->keys_alt) : P<unsigned long long>(ctx->keys);
+    CK(radix_sort_pairs_u32(P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), P<uint32_t>(ctx->keys_alt),
+                            P<uint32_t>(ctx->vals_alt), n_pairs, tile_bits, ctx->scratch.p, s, &ctx->log,
+                            &passes, 0, &in_alt));
+    uint32_t* skeys = in_alt ? P<uint32_t>(ctx->keys_alt) : P<uint32_t>(ctx->keys);
     uint32_t* svals = in_alt ? P<uint32_t>(ctx->vals_alt) : P<uint32_t>(ctx->vals);
     CK(cudaMemsetAsync(ctx->ranges.p, 0, (size_t)n_tiles * 8, s));
-    CK(launch_tile_ranges(skeys, n_pairs, depth_bits, P<uint32_t>(ctx->ranges), s, &ctx->log));
+    CK(launch_tile_ranges(skeys, n_pairs, P<uint32_t>(ctx->ranges), s, &ctx->log));
+    passes += dpasses;
+    const int depth_bits = 0;
 
     // ---- S6
     tm.mark(NVGS_STAGE_BLEND);
@@ -682,8 +696,16 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
         mark = P<uint8_t>(ctx->mark);
         CK(cudaMemsetAsync(mark, 0, (size_t)n_surv + 1, s));
     }
-    CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, img_dev, fT, nc, mark, s,
-                    &ctx->log));
+    // dense tiles: chunks of split_len pairs on separate CTAs (flags.blend_split_len, 0 = 4096,
+    // < 0 = never split)
+    const uint32_t split_len = f->blend_split_len < 0 ? 0xffffffffu
+                               : (f->blend_split_len == 0 ? 4096u : (uint32_t)f->blend_split_len);
+    if (n_pairs > split_len) {
+        CK(ensure(ctx->split_scratch, blend_split_scratch_bytes(n_tiles, n_pairs, cp.tile_size, split_len)));
+        CK(ensure(ctx->scratch, scan_scratch_bytes(n_tiles)));
+    }
+    CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, img_dev, fT, nc, mark,
+                    split_len, n_pairs, ctx->split_scratch.p, ctx->scratch.p, s, &ctx->log));
     if (labels_row) CK(launch_mark_labels(surv, n_surv, mark, labels_row, s, &ctx->log));
     tm.mark(NVGS_NUM_STAGES);
     if (f->image_memory == NVGS_MEM_HOST)
@@ -696,7 +718,7 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     L.records = P<float>(ctx->rec);
     L.tile_rects = P<int32_t>(ctx->rects);
     L.pair_values = svals;
-    L.pair_keys = reinterpret_cast<const uint64_t*>(skeys);
+    L.pair_keys = skeys;
     L.tile_ranges = P<uint32_t>(ctx->ranges);
     L.final_T = fT;
     L.n_contrib = nc;

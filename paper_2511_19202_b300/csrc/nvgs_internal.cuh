@@ -169,25 +169,31 @@ cudaError_t launch_scatter_visibility(const uint2* list, uint32_t n, const uint3
                                       const FrameInst* fi, float* out_logits, uint8_t* out_keep,
                                       cudaStream_t s, LaunchLog* log);
 
-// S4
+// S4: records, tile rects and counts; dkey / didx receive the depth sort keys (IEEE bits of
+// the camera-space z) and the survivor indices 0..n-1.
 cudaError_t launch_project(const uint2* surv, uint32_t n, const FrameInst* fi,
                            const AssetDev* assets, CamParams cam, float4* rec,
-                           int4* rects, uint32_t* tile_counts, uint32_t* depth_minmax,
+                           int4* rects, uint32_t* tile_counts, uint32_t* dkey, uint32_t* didx,
                            cudaStream_t s, LaunchLog* log);
 
-// S5
-cudaError_t launch_duplicate(const int4* rects, const float4* rec, const uint32_t* offsets,
-                             uint32_t n, int tiles_x, int depth_bits, const uint32_t* depth_minmax,
-                             unsigned long long* keys, uint32_t* values, cudaStream_t s,
-                             LaunchLog* log);
-cudaError_t launch_tile_ranges(const unsigned long long* keys, uint32_t n, int depth_bits,
-                               uint32_t* ranges, cudaStream_t s, LaunchLog* log);
+// S5 (k_bin.cu)
+cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* counts, uint32_t n,
+                                 uint32_t* counts_sorted, cudaStream_t s, LaunchLog* log);
+cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const uint32_t* offsets,
+                             uint32_t n, int tiles_x, uint32_t* keys, uint32_t* values,
+                             cudaStream_t s, LaunchLog* log);
+cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, uint32_t* ranges, cudaStream_t s,
+                               LaunchLog* log);
 
 // S6
 // mark (nullable, per survivor): set to 1 when the survivor is blended at some pixel.
+// Tiles with more than split_len pairs take the chunked path; scratch must hold
+// blend_split_scratch_bytes(...), scan_scratch a scan of n_tiles values.
+size_t blend_split_scratch_bytes(int n_tiles, uint64_t n_pairs, int tile_size, uint32_t split_len);
 cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const float4* rec,
                          CamParams cam, float* image, float* final_T, int32_t* n_contrib,
-                         uint8_t* mark, cudaStream_t s, LaunchLog* log);
+                         uint8_t* mark, uint32_t split_len, uint64_t n_pairs, void* scratch,
+                         void* scan_scratch, cudaStream_t s, LaunchLog* log);
 // labels[row * n_gauss + g] |= mark[s] for survivor s = (instance, g)
 cudaError_t launch_mark_labels(const uint2* surv, uint32_t n_surv, const uint8_t* mark,
                                uint8_t* labels_row, cudaStream_t s, LaunchLog* log);
@@ -208,5 +214,10 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* values,
                              unsigned long long* keys_alt, uint32_t* values_alt, uint64_t n,
                              int key_bits, void* scratch, cudaStream_t s, LaunchLog* log,
                              int* passes_out, int copy_back, int* result_in_alt);
+// The same sort for 32-bit keys.
+cudaError_t radix_sort_pairs_u32(uint32_t* keys, uint32_t* values, uint32_t* keys_alt,
+                                 uint32_t* values_alt, uint64_t n, int key_bits, void* scratch,
+                                 cudaStream_t s, LaunchLog* log, int* passes_out, int copy_back,
+                                 int* result_in_alt);
 
 }  // namespace nvgs

@@ -106,7 +106,7 @@ class Renderer:
             records=grab(v.records, 12 * ns, torch.float32).view(-1, 12),
             tile_rects=grab(v.tile_rects, 4 * ns, torch.int32).view(-1, 4),
             pair_values=grab(v.pair_values, npairs, torch.int32),
-            pair_keys=grab(v.pair_keys, npairs, torch.int64),
+            pair_keys=grab(v.pair_keys, npairs, torch.int32),
             tile_ranges=grab(v.tile_ranges, 2 * n_tiles, torch.int32).view(-1, 2),
             tiles_x=int(v.tiles_x), tiles_y=int(v.tiles_y), tile_size=int(v.tile_size),
             depth_bits=int(v.depth_bits))

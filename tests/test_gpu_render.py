@@ -104,9 +104,8 @@ def test_tile_lists_are_exact(cfg1_setup):
     _, st = gpu_image(r, cam, use_mlp=0, tile_size=16)
     lf = r.last_frame()
     vals = lf["pair_values"].cpu().numpy().astype(np.int64)
-    keys = lf["pair_keys"].cpu().numpy().view(np.uint64)
     surv = lf["survivors"].cpu().numpy()
-    gpu_tiles = (keys >> np.uint64(lf["depth_bits"])).astype(np.int64)
+    gpu_tiles = lf["pair_keys"].cpu().numpy().astype(np.int64)
     assert np.all(np.diff(gpu_tiles) >= 0)
     sp = oracle.project(osc, cam, o)
     ot, oi, og = oracle.tile_lists(sp, cam, 16)
@@ -237,3 +236,36 @@ def test_radix_sort_is_a_stable_sort(cfg1_setup, n, bits, spread):
     order = np.argsort(keys, kind="stable")
     np.testing.assert_array_equal(dk.cpu().numpy().view(np.uint64), keys[order])
     np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), vals[order])
+
+
+# ----------------------------------------------------------------------------- dense-tile split
+@pytest.mark.parametrize("tile", [8, 16])
+def test_split_compositing_matches_one_cta_per_tile(cfg1_setup, tile):
+    """Cutting every tile into 256-pair chunks (separate CTAs) changes only the grouping of the
+    transmittance products: the image equals the one-CTA-per-tile image to FP32 rounding and the
+    oracle within the parity tolerance."""
+    sc, cam, r, osc = cfg1_setup
+    one, st = gpu_image(r, cam, use_mlp=0, tile_size=tile, blend_split_len=-1)
+    split, st2 = gpu_image(r, cam, use_mlp=0, tile_size=tile, blend_split_len=256)
+    assert st["n_pairs"] > 256 * 4
+    np.testing.assert_allclose(split, one, atol=2e-6)
+    ref = oracle.render(osc, cam, oracle_opts_for(dict(tile_size=tile)))
+    compare_images(split, ref["image"], ref["ambiguous"])
+
+
+def test_labeller_unchanged_by_split():
+    from paper_2511_19202_b300 import nvgs as N
+    sc = scenes.config1_scene(20000)
+    cams = [scenes.look_at_camera(12.0 * d, (0, 0, 0), 128, 128, 50.0) for d in scenes.fibonacci_directions(3)]
+    r = renderer_for(sc)
+    try:
+        n = sc.n_instanced
+        out = []
+        for split in (-1, 256):
+            lab = torch.zeros(len(cams) * n, dtype=torch.uint8, device="cuda")
+            N.nvgs_label_visibility(r.ctx, 0, cams, N.nvgs_default_flags(use_mlp=0, blend_split_len=split), lab)
+            out.append(lab.cpu().numpy())
+        assert (out[0] == out[1]).mean() >= 0.9999
+        assert 0.02 < out[0].mean() < 0.98
+    finally:
+        r.close()
