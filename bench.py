@@ -245,7 +245,7 @@ def run_ours(args, rank, world):
     def frame(k):
         return cams[(rank + k * world) % len(cams)]
 
-    def timed(flags, K, profile):
+    def timed(flags, K, profile, label):
         flags.profile = 1 if profile else 0
         out = torch.empty((H, W, 3), dtype=torch.float32, device=f"cuda:{dev}")
         stats = []
@@ -254,11 +254,13 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(label)   # lets ncu --nvtx-include select the timed frames
         e0.record(stream)
         for k in range(K):
             _, st = r.render(frame(k), flags, out)
             stats.append(st)
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -271,9 +273,9 @@ def run_ours(args, rank, world):
     clocks = ClockSampler(dev)
     clocks.start()
     N.nvgs_reset_kernel_stats(r.ctx)
-    ms_culled, st_culled = timed(culled, args.steps, True)
+    ms_culled, st_culled = timed(culled, args.steps, True, "nvgs_timed_culled")
     kstats = N.nvgs_kernel_stats(r.ctx)
-    ms_plain, st_plain = timed(plain, args.steps, False)
+    ms_plain, st_plain = timed(plain, args.steps, False, "nvgs_timed_unculled")
     clk = clocks.stop()
 
     if world > 1:

@@ -12,14 +12,15 @@
 // The CTA leaves the range as soon as every pixel has stopped (a block-wide vote per batch).
 // With `mark` set, every blended fragment also flags its survivor (the visibility labeller).
 //
-// Dense tiles (Sec. 4 of the supplement: many Gaussians on few pixels load-balance badly) are
-// split: a tile whose range exceeds `split_len` pairs is cut into chunks of split_len that
-// separate CTAs process in three steps --
+// Dense tiles (the supplement's "Gaussian/Asset Density": many Gaussians on few pixels balance
+// badly): k_blend walks at most `split_len` pairs of a tile.  If some pixel of a longer tile is
+// still unsaturated after them, its state (colour, T, count) is saved and the rest of the range
+// is cut into chunks of split_len that separate CTAs process in three steps --
 //   k_blend_split_T  the product of (1 - alpha) over each chunk's blended fragments per pixel;
-//   k_blend_split_C  each chunk again, entering with T = the product over the earlier chunks
-//                    (nothing to do once that is below t_stop) and applying the stop rule;
-//   k_blend_split_D  per pixel, the colours of the chunks up to the one that stopped are summed
-//                    and the transmittance left by it composes the background.
+//   k_blend_split_C  each chunk again, entering with T = the saved T times the products of the
+//                    earlier chunks (nothing to do once that is below t_stop), stop rule applied;
+//   k_blend_split_D  per pixel, the saved colour plus the chunks' colours up to the one that
+//                    stopped, and the transmittance left by it composing the background.
 // Only the grouping of the T products differs from the one-CTA order (FP32 rounding).
 #include "nvgs_internal.cuh"
 
@@ -103,19 +104,33 @@ __global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ r
                                                   const float4* __restrict__ rec, CamParams cam,
                                                   float* __restrict__ image, float* __restrict__ final_T,
                                                   int32_t* __restrict__ n_contrib,
-                                                  uint8_t* __restrict__ mark, uint32_t split_len) {
+                                                  uint8_t* __restrict__ mark, uint32_t split_len,
+                                                  float4* __restrict__ state_tc,
+                                                  int32_t* __restrict__ state_cnt,
+                                                  uint32_t* __restrict__ alive) {
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
     __shared__ float4 s_c[B];
     const int tile = blockIdx.x;
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
-    if (end - start > split_len) return;   // a dense tile: the split kernels own it
+    const bool longer = end - start > split_len;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
     const bool inside = px < cam.W && py < cam.H;
     Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, !inside};
-    walk<TS, false>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, mark, s_a, s_b, s_c);
+    walk<TS, false>(values, rec, start, longer ? start + split_len : end, (float)px + 0.5f,
+                    (float)py + 0.5f, cam, f, mark, s_a, s_b, s_c);
+    if (longer) {
+        const bool all_done = __syncthreads_count(f.done) == B;
+        if (threadIdx.x == 0) alive[tile] = all_done ? 0u : 1u;
+        if (!all_done) {   // the chunked kernels finish this tile
+            state_tc[(size_t)tile * B + threadIdx.x] =
+                make_float4(f.C0, f.C1, f.C2, f.done ? -f.T - 1.0f : f.T);
+            state_cnt[(size_t)tile * B + threadIdx.x] = f.count;
+            return;
+        }
+    }
     if (inside) {
         const size_t p = (size_t)py * cam.W + px;
         image[3 * p] = fmaf(f.T, cam.bg[0], f.C0);
@@ -127,12 +142,12 @@ __global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ r
 }
 
 // ------------------------------------------------------------------ dense tiles
-__global__ void k_split_count(const uint32_t* __restrict__ ranges, int n_tiles, uint32_t split_len,
-                              uint32_t* __restrict__ n_chunks) {
+__global__ void k_split_count(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ alive,
+                              int n_tiles, uint32_t split_len, uint32_t* __restrict__ n_chunks) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
     const uint32_t n = ranges[2 * t + 1] - ranges[2 * t];
-    n_chunks[t] = n > split_len ? (n + split_len - 1) / split_len : 0u;
+    n_chunks[t] = (n > split_len && alive[t]) ? (n - split_len + split_len - 1) / split_len : 0u;
 }
 
 __global__ void k_split_fill(const uint32_t* __restrict__ n_chunks, const uint32_t* __restrict__ first,
@@ -142,13 +157,22 @@ __global__ void k_split_fill(const uint32_t* __restrict__ n_chunks, const uint32
     for (uint32_t c = 0; c < n_chunks[t]; c++) items[first[t] + c] = make_uint2((uint32_t)t, c);
 }
 
+// [start, end) of chunk c of a continued tile (the first split_len pairs were k_blend's)
+__device__ __forceinline__ void chunk_range(const uint32_t* __restrict__ ranges, uint2 it,
+                                            uint32_t split_len, uint32_t& start, uint32_t& end) {
+    start = ranges[2 * it.x] + (it.y + 1) * split_len;
+    end = min(ranges[2 * it.x + 1], start + split_len);
+}
+
 template <int TS>
 __global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __restrict__ ranges,
                                                           const uint32_t* __restrict__ values,
                                                           const float4* __restrict__ rec, CamParams cam,
                                                           const uint2* __restrict__ items,
                                                           const uint32_t* __restrict__ n_items,
-                                                          uint32_t split_len, float* __restrict__ Tch) {
+                                                          uint32_t split_len,
+                                                          const float4* __restrict__ state_tc,
+                                                          float* __restrict__ Tch) {
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
@@ -157,11 +181,12 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __rest
     if (item >= *n_items) return;
     const uint2 it = items[item];
     const int tile = (int)it.x;
-    const uint32_t start = ranges[2 * tile] + it.y * split_len;
-    const uint32_t end = min(ranges[2 * tile + 1], start + split_len);
+    uint32_t start, end;
+    chunk_range(ranges, it, split_len, start, end);
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
-    Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, !(px < cam.W && py < cam.H)};
+    const bool stopped = state_tc[(size_t)tile * B + threadIdx.x].w < 0.0f;
+    Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, stopped || !(px < cam.W && py < cam.H)};
     walk<TS, true>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, nullptr, s_a, s_b, s_c);
     Tch[(size_t)item * B + threadIdx.x] = f.T;
 }
@@ -172,7 +197,9 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
                                                           const float4* __restrict__ rec, CamParams cam,
                                                           const uint2* __restrict__ items,
                                                           const uint32_t* __restrict__ n_items,
-                                                          uint32_t split_len, const float* __restrict__ Tch,
+                                                          uint32_t split_len,
+                                                          const float4* __restrict__ state_tc,
+                                                          const float* __restrict__ Tch,
                                                           float4* __restrict__ part, int32_t* __restrict__ pcount,
                                                           uint8_t* __restrict__ mark) {
     constexpr int B = TS * TS;
@@ -183,14 +210,15 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
     if (item >= *n_items) return;
     const uint2 it = items[item];
     const int tile = (int)it.x;
-    const uint32_t start = ranges[2 * tile] + it.y * split_len;
-    const uint32_t end = min(ranges[2 * tile + 1], start + split_len);
+    uint32_t start, end;
+    chunk_range(ranges, it, split_len, start, end);
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
-    // transmittance entering this chunk: product over the earlier chunks of the tile
-    float T_in = 1.0f;
+    // transmittance entering this chunk: after k_blend's pairs, times the earlier chunks
+    const float sw = state_tc[(size_t)tile * B + threadIdx.x].w;
+    float T_in = sw < 0.0f ? 0.0f : sw;
     for (uint32_t c = 0; c < it.y; c++) T_in *= Tch[(size_t)(item - it.y + c) * B + threadIdx.x];
-    const bool dead = T_in < cam.t_stop;
+    const bool dead = sw < 0.0f || T_in < cam.t_stop;
     Frag f{T_in, 0.0f, 0.0f, 0.0f, 0, dead || !(px < cam.W && py < cam.H)};
     walk<TS, false>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, mark, s_a, s_b, s_c);
     // w < 0 marks "stopped inside this chunk or before"
@@ -201,7 +229,9 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
 template <int TS>
 __global__ void __launch_bounds__(TS* TS) k_blend_split_D(const uint32_t* __restrict__ n_chunks,
                                                           const uint32_t* __restrict__ first,
-                                                          CamParams cam, const float4* __restrict__ part,
+                                                          CamParams cam, const float4* __restrict__ state_tc,
+                                                          const int32_t* __restrict__ state_cnt,
+                                                          const float4* __restrict__ part,
                                                           const int32_t* __restrict__ pcount,
                                                           float* __restrict__ image, float* __restrict__ final_T,
                                                           int32_t* __restrict__ n_contrib) {
@@ -212,15 +242,21 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_D(const uint32_t* __rest
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
     if (!(px < cam.W && py < cam.H)) return;
-    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
-    int count = 0;
-    for (uint32_t c = 0; c < nc; c++) {
-        const size_t q = (size_t)(first[tile] + c) * B + threadIdx.x;
-        const float4 v = part[q];
-        C0 += v.x; C1 += v.y; C2 += v.z;
-        count += pcount[q];
-        if (v.w < 0.0f) { T = -v.w - 1.0f; break; }   // stopped: later chunks add nothing
-        T = v.w;
+    const float4 st = state_tc[(size_t)tile * B + threadIdx.x];
+    float C0 = st.x, C1 = st.y, C2 = st.z, T;
+    int count = state_cnt[(size_t)tile * B + threadIdx.x];
+    if (st.w < 0.0f) {
+        T = -st.w - 1.0f;   // stopped inside k_blend's pairs
+    } else {
+        T = st.w;
+        for (uint32_t c = 0; c < nc; c++) {
+            const size_t q = (size_t)(first[tile] + c) * B + threadIdx.x;
+            const float4 v = part[q];
+            C0 += v.x; C1 += v.y; C2 += v.z;
+            count += pcount[q];
+            if (v.w < 0.0f) { T = -v.w - 1.0f; break; }   // stopped: later chunks add nothing
+            T = v.w;
+        }
     }
     const size_t p = (size_t)py * cam.W + px;
     image[3 * p] = fmaf(T, cam.bg[0], C0);
@@ -233,9 +269,10 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_D(const uint32_t* __rest
 static inline uint64_t round256(uint64_t b) { return (b + 255) / 256 * 256; }
 
 size_t blend_split_scratch_bytes(int n_tiles, uint64_t n_pairs, int tile_size, uint32_t split_len) {
-    const uint64_t items = 2 * n_pairs / split_len + 2;
+    const uint64_t items = n_pairs / split_len + 2;
     const uint64_t B = (uint64_t)tile_size * tile_size;
-    return (size_t)(round256((uint64_t)n_tiles * 8 + 64) + round256(items * 8) + round256(items * B * 4) +
+    return (size_t)(round256((uint64_t)n_tiles * 12 + 64) + round256((uint64_t)n_tiles * B * 16) +
+                    round256((uint64_t)n_tiles * B * 4) + round256(items * 8) + round256(items * B * 4) +
                     round256(items * B * 16) + round256(items * B * 4));
 }
 
@@ -246,31 +283,47 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
                             void* scan_scratch, cudaStream_t s, LaunchLog* log) {
     constexpr int B = TS * TS;
     const int n_tiles = cam.tiles_x * cam.tiles_y;
-    NVGS_LAUNCH(log, s, TS == 8 ? "k_blend<8>" : TS == 16 ? "k_blend<16>" : "k_blend<32>",
-                k_blend<TS><<<n_tiles, B, 0, s>>>(ranges, values, rec, cam, image, final_T, n_contrib, mark, split_len));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || n_pairs <= split_len) return e;
-    // carve the scratch
+    const bool may_split = n_pairs > split_len;
+    // carve the scratch; every section starts on a 256-byte boundary
     char* p = static_cast<char*>(scratch);
-    uint32_t* n_chunks = reinterpret_cast<uint32_t*>(p);
-    uint32_t* first = n_chunks + n_tiles;
-    uint32_t* n_items = first + n_tiles;
-    p += round256((uint64_t)n_tiles * 8 + 64);   // every section starts on a 256-byte boundary
-    const uint64_t max_items = 2 * n_pairs / split_len + 2;
-    uint2* items = reinterpret_cast<uint2*>(p);
-    p += round256(max_items * 8);
-    float* Tch = reinterpret_cast<float*>(p);
-    p += round256(max_items * B * 4);
-    float4* part = reinterpret_cast<float4*>(p);
-    p += round256(max_items * B * 16);
-    int32_t* pcount = reinterpret_cast<int32_t*>(p);
-    NVGS_LAUNCH(log, s, "k_split_count", k_split_count<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, n_tiles, split_len, n_chunks));
+    uint32_t *n_chunks = nullptr, *first = nullptr, *n_items = nullptr, *alive = nullptr;
+    float4* state_tc = nullptr;
+    int32_t* state_cnt = nullptr;
+    uint2* items = nullptr;
+    float* Tch = nullptr;
+    float4* part = nullptr;
+    int32_t* pcount = nullptr;
+    const uint64_t max_items = n_pairs / split_len + 2;
+    if (may_split) {
+        n_chunks = reinterpret_cast<uint32_t*>(p);
+        first = n_chunks + n_tiles;
+        alive = first + n_tiles;
+        n_items = alive + n_tiles;
+        p += round256((uint64_t)n_tiles * 12 + 64);
+        state_tc = reinterpret_cast<float4*>(p);
+        p += round256((uint64_t)n_tiles * B * 16);
+        state_cnt = reinterpret_cast<int32_t*>(p);
+        p += round256((uint64_t)n_tiles * B * 4);
+        items = reinterpret_cast<uint2*>(p);
+        p += round256(max_items * 8);
+        Tch = reinterpret_cast<float*>(p);
+        p += round256(max_items * B * 4);
+        part = reinterpret_cast<float4*>(p);
+        p += round256(max_items * B * 16);
+        pcount = reinterpret_cast<int32_t*>(p);
+    }
+    NVGS_LAUNCH(log, s, TS == 8 ? "k_blend<8>" : TS == 16 ? "k_blend<16>" : "k_blend<32>",
+                k_blend<TS><<<n_tiles, B, 0, s>>>(ranges, values, rec, cam, image, final_T, n_contrib, mark,
+                                                  split_len, state_tc, state_cnt, alive));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !may_split) return e;
+    NVGS_LAUNCH(log, s, "k_split_count", k_split_count<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, alive, n_tiles, split_len, n_chunks));
     e = exclusive_scan_u32(n_chunks, first, n_tiles, n_items, scan_scratch, s, log);
     if (e != cudaSuccess) return e;
     NVGS_LAUNCH(log, s, "k_split_fill", k_split_fill<<<(n_tiles + 255) / 256, 256, 0, s>>>(n_chunks, first, n_tiles, items));
-    NVGS_LAUNCH(log, s, "k_blend_split_T", k_blend_split_T<TS><<<(unsigned)max_items, B, 0, s>>>(ranges, values, rec, cam, items, n_items, split_len, Tch));
-    NVGS_LAUNCH(log, s, "k_blend_split_C", k_blend_split_C<TS><<<(unsigned)max_items, B, 0, s>>>(ranges, values, rec, cam, items, n_items, split_len, Tch, part, pcount, mark));
-    NVGS_LAUNCH(log, s, "k_blend_split_D", k_blend_split_D<TS><<<n_tiles, B, 0, s>>>(n_chunks, first, cam, part, pcount, image, final_T, n_contrib));
+    NVGS_LAUNCH(log, s, "k_blend_split_T", k_blend_split_T<TS><<<(unsigned)max_items, B, 0, s>>>(ranges, values, rec, cam, items, n_items, split_len, state_tc, Tch));
+    NVGS_LAUNCH(log, s, "k_blend_split_C", k_blend_split_C<TS><<<(unsigned)max_items, B, 0, s>>>(ranges, values, rec, cam, items, n_items, split_len, state_tc, Tch, part, pcount, mark));
+    NVGS_LAUNCH(log, s, "k_blend_split_D", k_blend_split_D<TS><<<n_tiles, B, 0, s>>>(n_chunks, first, cam, state_tc, state_cnt, part, pcount, image, final_T, n_contrib));
     return cudaGetLastError();
 }
 
