@@ -147,7 +147,7 @@ def kernel_frame_work(name, fr, sh_stride_floats, W, H, tile):
     if name == "k_duplicate":
         return "hbm", ns * (4 + 16 + 4) + npairs * 8
     if name == "k_tile_ranges":
-        return "hbm", npairs * 4 + n_tiles * 8
+        return "hbm", n_tiles * 8
     if name == "k_frustum":
         return "hbm", fr["n_instanced"] * 16
     if name in ("k_mlp_fp32", "k_mlp_tc"):

@@ -106,7 +106,9 @@ typedef struct {
                                     nvgs_render_backward and the labeller */
     int32_t blend_split_len;     /* tiles with more pairs are composited in chunks of this many
                                     pairs on separate CTAs (0: 4096; < 0: never; else >= 256) */
-    int32_t reserved[6];
+    int32_t mlp_ctas_per_sm;     /* resident CTAs per SM of the tensor-core MLP (0: default 4;
+                                    1..4) -- a tuning knob, results do not depend on it */
+    int32_t reserved[5];
 } nvgs_render_flags;
 
 #define NVGS_NUM_STAGES 8

@@ -55,21 +55,30 @@ cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const uin
     return cudaGetLastError();
 }
 
-// ranges[2t] / ranges[2t+1] = first / one-past-last index of tile t in the sorted keys.
-// Tiles without pairs keep the zeros the caller wrote.
-__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ keys, uint32_t n,
-                                                     uint32_t* __restrict__ ranges) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t t = keys[i];
-    if (i == 0 || keys[i - 1] != t) ranges[2 * t] = i;
-    if (i == n - 1 || keys[i + 1] != t) ranges[2 * t + 1] = i + 1;
+// ranges[2t] / ranges[2t+1] = first / one-past-last index of tile t in the sorted keys: one
+// thread per tile, two binary searches (lower bounds of t and t + 1) instead of a pass over the
+// pairs.
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ a, uint32_t n, uint32_t v) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(&a[mid]) < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
 }
 
-cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, uint32_t* ranges, cudaStream_t s,
-                               LaunchLog* log) {
-    if (n == 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_tile_ranges", k_tile_ranges<<<(n + 255) / 256, 256, 0, s>>>(keys, n, ranges));
+__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ keys, uint32_t n,
+                                                     uint32_t n_tiles, uint32_t* __restrict__ ranges) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    ranges[2 * t] = lower_bound_u32(keys, n, t);
+    ranges[2 * t + 1] = lower_bound_u32(keys, n, t + 1);
+}
+
+cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, uint32_t n_tiles, uint32_t* ranges,
+                               cudaStream_t s, LaunchLog* log) {
+    if (n_tiles == 0) return cudaSuccess;
+    NVGS_LAUNCH(log, s, "k_tile_ranges", k_tile_ranges<<<(n_tiles + 255) / 256, 256, 0, s>>>(keys, n, n_tiles, ranges));
     return cudaGetLastError();
 }
 

@@ -160,7 +160,10 @@ __device__ __forceinline__ void chunk_word_prefix(const uint32_t* __restrict__ w
 __global__ void __launch_bounds__(256) k_expand_chunks(const Chunk* __restrict__ chunks,
                                                        const uint32_t* __restrict__ bits,
                                                        const uint32_t* __restrict__ chunk_offsets,
-                                                       uint2* __restrict__ out) {
+                                                       uint2* __restrict__ out,
+                                                       const FrameInst* __restrict__ fi,
+                                                       const AssetDev* __restrict__ assets,
+                                                       float4* __restrict__ out_mean) {
     __shared__ uint32_t s_word[64];
     __shared__ uint32_t s_pref[128];
     const int c = blockIdx.x;
@@ -175,16 +178,20 @@ __global__ void __launch_bounds__(256) k_expand_chunks(const Chunk* __restrict__
         uint32_t word = s_word[w];
         if ((word >> lane) & 1u) {
             uint32_t pos = base + s_pref[64 + w] + __popc(word & lt);
-            out[pos] = make_uint2((uint32_t)ch.inst, (uint32_t)(ch.g0 + w * 32 + lane));
+            const uint32_t g = (uint32_t)(ch.g0 + w * 32 + lane);
+            out[pos] = make_uint2((uint32_t)ch.inst, g);
+            // the MLP reads the mean next to the entry instead of through instance -> asset
+            if (out_mean) out_mean[pos] = __ldg(&assets[fi[ch.inst].asset].mean_op[g]);
         }
     }
 }
 
 cudaError_t launch_expand_chunks(const Chunk* chunks, int n_chunks, const uint32_t* bits,
-                                 const uint32_t* chunk_offsets, uint2* out, cudaStream_t s,
+                                 const uint32_t* chunk_offsets, uint2* out, const FrameInst* fi,
+                                 const AssetDev* assets, float4* out_mean, cudaStream_t s,
                                  LaunchLog* log) {
     if (n_chunks <= 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_expand_chunks", k_expand_chunks<<<n_chunks, 256, 0, s>>>(chunks, bits, chunk_offsets, out));
+    NVGS_LAUNCH(log, s, "k_expand_chunks", k_expand_chunks<<<n_chunks, 256, 0, s>>>(chunks, bits, chunk_offsets, out, fi, assets, out_mean));
     return cudaGetLastError();
 }
 

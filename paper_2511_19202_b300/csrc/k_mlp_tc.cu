@@ -2,7 +2,8 @@
 // NVGS Sec. 3.2, queried per in-frustum Gaussian as in Sec. 3.3) on the 5th-generation tensor
 // cores (tcgen05), BF16 operands with FP32 accumulation in tensor memory (TMEM).
 //
-// One CTA = one warpgroup (128 threads) walking 128-Gaussian tiles of the in-frustum list:
+// One CTA = one warpgroup (128 threads) walking 256-Gaussian steps of the in-frustum list, as
+// two 128-row tiles that share every MMA round trip (thread r owns rows r and 128 + r):
 //   1. thread r builds the 32 inputs of row r (Eq. 2 distance, frequency encoding) and writes
 //      them as BF16 into the A tile in shared memory;
 //   2. thread 0 issues tcgen05.mma (M = 128, N = 64, K = 16 per instruction) for layer 1 with the
@@ -11,7 +12,8 @@
 //      adds the FP32 bias, applies ReLU while converting to BF16, and writes the activations back
 //      to shared memory as the next layer's A operand; layers 2 and 3 repeat steps 2-3;
 //   4. the 64 -> 1 output layer runs in FP32 on the CUDA cores straight from the TMEM values.
-// Four CTAs share an SM (64 TMEM columns each), so one CTA's epilogue overlaps another's MMAs.
+// Four CTAs share an SM (128 TMEM columns and 54 KB of shared memory each), so the epilogues of
+// some overlap the MMAs of others.
 //
 // Operand layout (both operands K-major, no swizzle): 8 x 16-byte "core matrices"; element
 // (row, k) of a tile with K columns sits at (row / 8) * SBO + (k / 8) * 128 + (row % 8) * 16
@@ -30,8 +32,9 @@ namespace nvgs {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kRows = 128;
-constexpr int kTmemCols = 64;
+constexpr int kHalves = 2;                 // each CTA carries two 128-row tiles through a layer
+constexpr int kRows = 128 * kHalves;       // rows per CTA step
+constexpr int kTmemCols = 64 * kHalves;
 // shared-memory map (bytes)
 constexpr int kOffW1 = 0;            // 64 x 32 BF16
 constexpr int kOffW2 = 4096;         // 64 x 64 BF16
@@ -39,9 +42,12 @@ constexpr int kOffW3 = 12288;        // 64 x 64 BF16
 constexpr int kOffVec = 20480;       // FP32: b1[64] b2[64] b3[64] w4[64] b4 pad[3]
 constexpr int kVecFloats = 260;
 constexpr int kBlobBytes = kOffVec + kVecFloats * 4;   // 21520, a multiple of 16
-constexpr int kOffA = 21760;         // 128 x 32 BF16
-constexpr int kOffH = kOffA + 8192;  // 128 x 64 BF16
-constexpr int kOffMisc = kOffH + 16384;
+// Per half, the input tile A (128 x 32) overlays the first half of the hidden tile H (128 x 64):
+// layer 1's MMA has finished reading A before its epilogue writes H, and the next step's inputs
+// are written only after layer 3's MMA has finished reading H.
+constexpr int kOffH = 21760;         // kHalves x (128 x 64 BF16)
+constexpr int kHBytes = 16384;
+constexpr int kOffMisc = kOffH + kHalves * kHBytes;
 constexpr int kSmemBytes = kOffMisc + 64;
 constexpr uint32_t kSboK32 = 512;    // 16 * 32
 constexpr uint32_t kSboK64 = 1024;   // 16 * 64
@@ -79,10 +85,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Lane 0 of each warp polls (bounded); the rest of the warp waits at __syncwarp.  The warp's
+// verdict is broadcast so that a timeout is seen by every thread.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kWaitIters; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    uint32_t ok = 0;
+    if ((threadIdx.x & 31) == 0) {
+        for (uint32_t it = 0; it < kWaitIters; ++it)
+            if (mbar_try_wait(bar, parity)) { ok = 1; break; }
+    }
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -175,12 +186,11 @@ __device__ __forceinline__ float epilogue_logit(uint32_t t_lane, const float* b3
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 4)
-k_mlp_tc(const uint2* __restrict__ list, uint32_t n, const FrameInst* __restrict__ fis,
+k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, uint32_t n,
+         const FrameInst* __restrict__ fis,
          const AssetDev* __restrict__ assets, float threshold, uint32_t* __restrict__ keep_bits,
          float* __restrict__ logits_out, uint32_t* __restrict__ err_flag) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t* sA = sm + kOffA;
-    uint8_t* sH = sm + kOffH;
     const float* sVec = reinterpret_cast<const float*>(sm + kOffVec);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kOffMisc);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + kOffMisc + 8);
@@ -205,30 +215,60 @@ k_mlp_tc(const uint2* __restrict__ list, uint32_t n, const FrameInst* __restrict
     uint32_t phase = 0;
     int loaded = -1;
     bool abort = false;
-    const uint32_t n_tiles = (n + kRows - 1) / kRows;
-    for (uint32_t tile = blockIdx.x; tile < n_tiles && !abort; tile += gridDim.x) {
-        const uint32_t i = tile * kRows + tid;
-        uint2 e = make_uint2(0, 0);
-        int my_asset = INT_MAX;
-        if (i < n) {
-            e = list[i];
-            my_asset = fis[e.x].asset;
+    const uint32_t n_steps = (n + kRows - 1) / kRows;
+    // row inputs of the next step are loaded one step ahead, so their latency overlaps the
+    // current step's tensor-core chain
+    uint2 e_next[kHalves];
+    float4 m_next[kHalves];
+#pragma unroll
+    for (int h = 0; h < kHalves; h++) {
+        const uint32_t i = blockIdx.x * kRows + h * 128 + tid;
+        e_next[h] = make_uint2(0, 0);
+        m_next[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (blockIdx.x < n_steps && i < n) {
+            e_next[h] = __ldg(&list[i]);
+            m_next[h] = __ldg(&list_mean[i]);
         }
-        bool pending = i < n, keep = false;
-        float logit = 0.0f;
-        // a tile holds consecutive in-frustum Gaussians; rows of different assets (at instance
-        // boundaries) are evaluated in separate passes with each asset's own weights
+    }
+    for (uint32_t step = blockIdx.x; step < n_steps && !abort; step += gridDim.x) {
+        uint2 e[kHalves];
+        float4 m[kHalves];
+        int my_asset[kHalves];
+        bool pending[kHalves], keep[kHalves];
+        float logit[kHalves];
+#pragma unroll
+        for (int h = 0; h < kHalves; h++) {
+            const uint32_t i = step * kRows + h * 128 + tid;
+            e[h] = e_next[h];
+            m[h] = m_next[h];
+            const uint32_t i_next = (step + gridDim.x) * kRows + h * 128 + tid;
+            if (step + gridDim.x < n_steps && i_next < n) {
+                e_next[h] = __ldg(&list[i_next]);
+                m_next[h] = __ldg(&list_mean[i_next]);
+            }
+            my_asset[h] = i < n ? fis[e[h].x].asset : INT_MAX;
+            pending[h] = i < n;
+            keep[h] = false;
+            logit[h] = 0.0f;
+        }
+        // rows of different assets (at instance boundaries) are evaluated in separate passes,
+        // each with that asset's weights
         for (;;) {
-            int cand = __reduce_min_sync(0xffffffffu, pending ? my_asset : INT_MAX);
+            int cand = min(pending[0] ? my_asset[0] : INT_MAX, pending[1] ? my_asset[1] : INT_MAX);
+            cand = __reduce_min_sync(0xffffffffu, cand);
             if (lane == 0) s_red[warp] = cand;
             __syncthreads();
             const int cur = min(min(s_red[0], s_red[1]), min(s_red[2], s_red[3]));
             __syncthreads();
             if (cur == INT_MAX) break;
             const AssetDev& a = assets[cur];
-            const bool mine = pending && my_asset == cur;
+            bool mine[kHalves];
+#pragma unroll
+            for (int h = 0; h < kHalves; h++) mine[h] = pending[h] && my_asset[h] == cur;
             if (a.w_tc == nullptr) {   // asset without an MLP: rendered unculled
-                if (mine) { keep = true; logit = __int_as_float(0x7f800000); pending = false; }
+#pragma unroll
+                for (int h = 0; h < kHalves; h++)
+                    if (mine[h]) { keep[h] = true; logit[h] = __int_as_float(0x7f800000); pending[h] = false; }
                 continue;
             }
             if (cur != loaded) {
@@ -237,41 +277,50 @@ k_mlp_tc(const uint2* __restrict__ list, uint32_t n, const FrameInst* __restrict
                 for (int k = tid; k < kBlobBytes / 16; k += kThreads) dst[k] = __ldg(&src[k]);
                 loaded = cur;
             }
-            // ---- inputs -> A (BF16)
-            uint32_t p[16];
-            if (mine) {
-                float f[32];
-                mlp_features(a, fis[e.x], __ldg(&a.mean_op[e.y]), f);
+            // ---- inputs -> A (BF16), one row per half
 #pragma unroll
-                for (int k = 0; k < 16; k++) p[k] = bf16x2(f[2 * k], f[2 * k + 1]);
-            } else {
+            for (int h = 0; h < kHalves; h++) {
+                uint32_t p[16];
+                if (mine[h]) {
+                    float f[32];
+                    mlp_features(a, fis[e[h].x], m[h], f);
 #pragma unroll
-                for (int k = 0; k < 16; k++) p[k] = 0u;
+                    for (int k = 0; k < 16; k++) p[k] = bf16x2(f[2 * k], f[2 * k + 1]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 16; k++) p[k] = 0u;
+                }
+                uint8_t* sA = sm + kOffH + h * kHBytes;
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    st_chunk(sA, kSboK32, tid, c, make_uint4(p[4 * c], p[4 * c + 1], p[4 * c + 2], p[4 * c + 3]));
             }
-#pragma unroll
-            for (int c = 0; c < 4; c++)
-                st_chunk(sA, kSboK32, tid, c, make_uint4(p[4 * c], p[4 * c + 1], p[4 * c + 2], p[4 * c + 3]));
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
 
-            // ---- three tensor-core layers
+            // ---- three tensor-core layers, both halves per round trip
             bool ok = true;
 #pragma unroll 1
             for (int layer = 0; layer < 3 && ok; layer++) {
                 if (tid == 0) {
                     tc_fence_after();
-                    if (layer == 0) {
 #pragma unroll
-                        for (int s = 0; s < 2; s++)
-                            mma_bf16(tmem, sdesc(sA + 256 * s, kLbo, kSboK32),
-                                     sdesc(sm + kOffW1 + 256 * s, kLbo, kSboK32), s > 0);
-                    } else {
-                        const uint8_t* W = sm + (layer == 1 ? kOffW2 : kOffW3);
+                    for (int h = 0; h < kHalves; h++) {
+                        const uint8_t* sH = sm + kOffH + h * kHBytes;
+                        const uint32_t d = tmem + 64 * h;
+                        if (layer == 0) {
 #pragma unroll
-                        for (int s = 0; s < 4; s++)
-                            mma_bf16(tmem, sdesc(sH + 256 * s, kLbo, kSboK64),
-                                     sdesc(W + 256 * s, kLbo, kSboK64), s > 0);
+                            for (int k = 0; k < 2; k++)
+                                mma_bf16(d, sdesc(sH + 256 * k, kLbo, kSboK32),
+                                         sdesc(sm + kOffW1 + 256 * k, kLbo, kSboK32), k > 0);
+                        } else {
+                            const uint8_t* W = sm + (layer == 1 ? kOffW2 : kOffW3);
+#pragma unroll
+                            for (int k = 0; k < 4; k++)
+                                mma_bf16(d, sdesc(sH + 256 * k, kLbo, kSboK64),
+                                         sdesc(W + 256 * k, kLbo, kSboK64), k > 0);
+                        }
                     }
                     mma_commit(mbar);
                 }
@@ -280,18 +329,23 @@ k_mlp_tc(const uint2* __restrict__ list, uint32_t n, const FrameInst* __restrict
                 phase ^= 1u;
                 tc_fence_after();
                 if (layer < 2) {
-                    epilogue_hidden(t_lane, sVec + 64 * layer, sH, tid);
+#pragma unroll
+                    for (int h = 0; h < kHalves; h++)
+                        epilogue_hidden(t_lane + 64 * h, sVec + 64 * layer, sm + kOffH + h * kHBytes, tid);
                     fence_async_smem();
                     tc_fence_before();
                     __syncthreads();
                 } else {
-                    const float lg = epilogue_logit(t_lane, sVec + 128, sVec + 192, sVec[256]);
-                    tc_fence_before();
-                    if (mine) {
-                        logit = lg;
-                        keep = fis[e.x].gated || (lg > threshold);
-                        pending = false;
+#pragma unroll
+                    for (int h = 0; h < kHalves; h++) {
+                        const float lg = epilogue_logit(t_lane + 64 * h, sVec + 128, sVec + 192, sVec[256]);
+                        if (mine[h]) {
+                            logit[h] = lg;
+                            keep[h] = fis[e[h].x].gated || (lg > threshold);
+                            pending[h] = false;
+                        }
                     }
+                    tc_fence_before();
                 }
             }
             if (!ok) {
@@ -301,9 +355,13 @@ k_mlp_tc(const uint2* __restrict__ list, uint32_t n, const FrameInst* __restrict
             }
         }
         if (abort) break;
-        const uint32_t w = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0 && tile * kRows + warp * 32 < n) keep_bits[tile * 4 + warp] = w;
-        if (logits_out && i < n) logits_out[i] = logit;
+#pragma unroll
+        for (int h = 0; h < kHalves; h++) {
+            const uint32_t row0 = step * kRows + h * 128;
+            const uint32_t w = __ballot_sync(0xffffffffu, keep[h]);
+            if (lane == 0 && row0 + warp * 32 < n) keep_bits[(row0 >> 5) + warp] = w;
+            if (logits_out && row0 + tid < n) logits_out[row0 + tid] = logit[h];
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -359,9 +417,10 @@ void mlp_tc_pack_weights(const float* w, uint8_t* out) {
     vec[256] = b4[0];
 }
 
-cudaError_t launch_mlp_tc(const uint2* list, uint32_t n, const FrameInst* fi, const AssetDev* assets,
+cudaError_t launch_mlp_tc(const uint2* list, const float4* list_mean, uint32_t n, const FrameInst* fi,
+                          const AssetDev* assets,
                           float threshold, uint32_t* keep_bits, float* logits_out, uint32_t* err_flag,
-                          int num_sms, cudaStream_t s, LaunchLog* log) {
+                          int num_sms, int ctas_per_sm, cudaStream_t s, LaunchLog* log) {
     if (n == 0) return cudaSuccess;
     static bool attr_done = false;
     if (!attr_done) {
@@ -369,9 +428,10 @@ cudaError_t launch_mlp_tc(const uint2* list, uint32_t n, const FrameInst* fi, co
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    const uint32_t tiles = (n + kRows - 1) / kRows;
-    const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)num_sms * 4u);
-    NVGS_LAUNCH(log, s, "k_mlp_tc", k_mlp_tc<<<grid, kThreads, kSmemBytes, s>>>(list, n, fi, assets, threshold, keep_bits, logits_out, err_flag));
+    const uint32_t steps = (n + kRows - 1) / kRows;
+    const uint32_t per_sm = ctas_per_sm >= 1 && ctas_per_sm <= 4 ? (uint32_t)ctas_per_sm : 4u;
+    const uint32_t grid = std::min<uint32_t>(steps, (uint32_t)num_sms * per_sm);
+    NVGS_LAUNCH(log, s, "k_mlp_tc", k_mlp_tc<<<grid, kThreads, kSmemBytes, s>>>(list, list_mean, n, fi, assets, threshold, keep_bits, logits_out, err_flag));
     return cudaGetLastError();
 }
 

@@ -51,7 +51,7 @@ struct nvgs_ctx {
     DevBuf frame_inst, bits, chunk_counts, chunk_offsets, vis_list, keep_bits, logits_tmp,
         block_counts, block_offsets, surv, rec, rects, tile_counts, tile_offsets, keys, vals,
         keys_alt, vals_alt, ranges, scratch, counters, image_tmp, final_T, n_contrib, mark, dkey,
-        didx, dkey_alt, didx_alt, split_scratch;
+        didx, dkey_alt, didx_alt, split_scratch, vis_mean;
     // visibility-MLP training state, per asset (FP32 master weights, Adam moments, views)
     struct Train {
         DevBuf w, m, v, views;
@@ -136,6 +136,8 @@ nvgs_status validate_flags(nvgs_ctx* ctx, const nvgs_render_flags* f) {
     if (!(f->alpha_min > 0.f && f->alpha_min < 1.f) || !(f->alpha_max > 0.f && f->alpha_max <= 1.f) ||
         !(f->t_stop >= 0.f && f->t_stop < 1.f) || !(f->dilation >= 0.f) || !(f->guard_band > 0.f))
         return fail(ctx, NVGS_ERR_INVALID_ARG, "blending constants out of range");
+    if (f->mlp_ctas_per_sm < 0 || f->mlp_ctas_per_sm > 4)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "mlp_ctas_per_sm must be 0..4");
     if (f->blend_split_len > 0 && f->blend_split_len < 256)
         return fail(ctx, NVGS_ERR_INVALID_ARG, "blend_split_len must be 0, negative or >= 256");
     if (f->image_memory != NVGS_MEM_HOST && f->image_memory != NVGS_MEM_DEVICE)
@@ -191,6 +193,18 @@ struct StageTimer {
     }
 };
 
+// BF16 tensor-core MLP only when every asset with an MLP has BF16 tiles and no logits are
+// injected.
+bool uses_tc_mlp(const nvgs_ctx* ctx, const nvgs_render_flags* f) {
+    bool tc = f->logits_override == nullptr;
+    bool any_mlp = false;
+    for (auto& a : ctx->assets) {
+        tc = tc && (a.precision == NVGS_PREC_BF16 || a.precision < 0);
+        any_mlp = any_mlp || a.precision >= 0;
+    }
+    return tc && any_mlp;
+}
+
 // S1 (+ S2 when use_mlp, + S3): fills ctx->vis_list / surv and the counts.  `query` keeps the
 // per-entry logits for nvgs_query_visibility.
 nvgs_status run_cull(nvgs_ctx* ctx, const CamParams& cp, const nvgs_render_flags* f,
@@ -215,8 +229,12 @@ nvgs_status run_cull(nvgs_ctx* ctx, const CamParams& cp, const nvgs_render_flags
     uint32_t* counters = P<uint32_t>(ctx->counters);
     CK(exclusive_scan_u32(P<uint32_t>(ctx->chunk_counts), P<uint32_t>(ctx->chunk_offsets), ctx->n_chunks,
                           &counters[0], ctx->scratch.p, s, &ctx->log));
+    const bool tc_mlp = f->use_mlp && uses_tc_mlp(ctx, f);
+    if (tc_mlp) CK(ensure(ctx->vis_mean, cap * 16 + 16));
     CK(launch_expand_chunks(P<Chunk>(ctx->chunks), ctx->n_chunks, P<uint32_t>(ctx->bits),
-                            P<uint32_t>(ctx->chunk_offsets), P<uint2>(ctx->vis_list), s, &ctx->log));
+                            P<uint32_t>(ctx->chunk_offsets), P<uint2>(ctx->vis_list),
+                            P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev),
+                            tc_mlp ? P<float4>(ctx->vis_mean) : nullptr, s, &ctx->log));
     CK(cudaMemcpyAsync(ctx->h_counters, counters, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const uint32_t n_vis = ctx->h_counters[0];
@@ -229,18 +247,12 @@ nvgs_status run_cull(nvgs_ctx* ctx, const CamParams& cp, const nvgs_render_flags
     }
     CK(ensure(ctx->keep_bits, ((size_t)cap / 32 + 2) * 4));
     if (want_logits) CK(ensure(ctx->logits_tmp, (size_t)cap * 4 + 16));
-    // precision: BF16 tensor-core path only when every asset has BF16 tiles and no override
-    bool tc = f->logits_override == nullptr;
-    for (auto& a : ctx->assets) tc = tc && (a.precision == NVGS_PREC_BF16 || a.precision < 0);
-    bool any_mlp = false;
-    for (auto& a : ctx->assets) any_mlp = any_mlp || a.precision >= 0;
-    tc = tc && any_mlp;
-    if (tc) {
+    if (tc_mlp) {
         CK(cudaMemsetAsync(&counters[8], 0, 4, s));
-        CK(launch_mlp_tc(P<uint2>(ctx->vis_list), n_vis, P<FrameInst>(ctx->frame_inst),
+        CK(launch_mlp_tc(P<uint2>(ctx->vis_list), P<float4>(ctx->vis_mean), n_vis, P<FrameInst>(ctx->frame_inst),
                          P<AssetDev>(ctx->assets_dev), f->logit_threshold, P<uint32_t>(ctx->keep_bits),
                          want_logits ? P<float>(ctx->logits_tmp) : nullptr, &counters[8],
-                         ctx->num_sms, s, &ctx->log));
+                         ctx->num_sms, f->mlp_ctas_per_sm, s, &ctx->log));
         CK(cudaMemcpyAsync(ctx->h_counters + 8, &counters[8], 4, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (ctx->h_counters[8])
@@ -374,7 +386,8 @@ extern "C" nvgs_status nvgs_destroy(nvgs_ctx* ctx) {
                       &ctx->tile_offsets, &ctx->keys, &ctx->vals, &ctx->keys_alt, &ctx->vals_alt,
                       &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
                       &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial,
-                      &ctx->dkey, &ctx->didx, &ctx->dkey_alt, &ctx->didx_alt, &ctx->split_scratch};
+                      &ctx->dkey, &ctx->didx, &ctx->dkey_alt, &ctx->didx_alt, &ctx->split_scratch,
+                      &ctx->vis_mean};
     for (auto& t : ctx->train) { release(t.w); release(t.m); release(t.v); release(t.views); }
     for (DevBuf* b : bufs) release(*b);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
@@ -669,8 +682,7 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
                             &passes, 0, &in_alt));
     uint32_t* skeys = in_alt ? P<uint32_t>(ctx->keys_alt) : P<uint32_t>(ctx->keys);
     uint32_t* svals = in_alt ? P<uint32_t>(ctx->vals_alt) : P<uint32_t>(ctx->vals);
-    CK(cudaMemsetAsync(ctx->ranges.p, 0, (size_t)n_tiles * 8, s));
-    CK(launch_tile_ranges(skeys, n_pairs, P<uint32_t>(ctx->ranges), s, &ctx->log));
+    CK(launch_tile_ranges(skeys, n_pairs, (uint32_t)n_tiles, P<uint32_t>(ctx->ranges), s, &ctx->log));
     passes += dpasses;
     const int depth_bits = 0;
 

@@ -126,9 +126,11 @@ cudaError_t launch_frustum(const Chunk* chunks, int n_chunks, const FrameInst* f
                            const AssetDev* assets, CamParams cam, uint32_t* bits,
                            uint32_t* chunk_counts, cudaStream_t s, LaunchLog* log);
 
-// Writes (instance, gaussian) of every set bit, in bit order, at out[chunk_offsets[c] + rank].
+// Writes (instance, gaussian) of every set bit, in bit order, at out[chunk_offsets[c] + rank],
+// and (out_mean nullable) the Gaussian's (mean, opacity logit) at the same position.
 cudaError_t launch_expand_chunks(const Chunk* chunks, int n_chunks, const uint32_t* bits,
-                                 const uint32_t* chunk_offsets, uint2* out, cudaStream_t s,
+                                 const uint32_t* chunk_offsets, uint2* out, const FrameInst* fi,
+                                 const AssetDev* assets, float4* out_mean, cudaStream_t s,
                                  LaunchLog* log);
 
 // S2: keep bits over a list of (instance, gaussian) entries.
@@ -137,10 +139,10 @@ cudaError_t launch_mlp_fp32(const uint2* list, uint32_t n, const FrameInst* fi,
                             const int64_t* inst_offset, float threshold, uint32_t* keep_bits,
                             float* logits_out, cudaStream_t s, LaunchLog* log);
 // err_flag (device) is set to 1 if a bounded wait on the tensor-core pipeline gave up.
-cudaError_t launch_mlp_tc(const uint2* list, uint32_t n, const FrameInst* fi,
+cudaError_t launch_mlp_tc(const uint2* list, const float4* list_mean, uint32_t n, const FrameInst* fi,
                           const AssetDev* assets, float threshold, uint32_t* keep_bits,
-                          float* logits_out, uint32_t* err_flag, int num_sms, cudaStream_t s,
-                          LaunchLog* log);
+                          float* logits_out, uint32_t* err_flag, int num_sms, int ctas_per_sm,
+                          cudaStream_t s, LaunchLog* log);
 
 // BF16 operand tiles of one asset's MLP in the tcgen05 shared-memory layout (host-side packing).
 size_t mlp_tc_weight_bytes();
@@ -182,8 +184,8 @@ cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* counts, 
 cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const uint32_t* offsets,
                              uint32_t n, int tiles_x, uint32_t* keys, uint32_t* values,
                              cudaStream_t s, LaunchLog* log);
-cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, uint32_t* ranges, cudaStream_t s,
-                               LaunchLog* log);
+cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, uint32_t n_tiles, uint32_t* ranges,
+                               cudaStream_t s, LaunchLog* log);
 
 // S6
 // mark (nullable, per survivor): set to 1 when the survivor is blended at some pixel.

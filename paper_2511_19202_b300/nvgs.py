@@ -56,7 +56,8 @@ class RenderFlags(C.Structure):
                 ("dilation", C.c_float), ("guard_band", C.c_float), ("bg", C.c_float * 3),
                 ("tile_size", C.c_int32), ("image_memory", C.c_int32), ("profile", C.c_int32),
                 ("logits_override", C.c_void_p), ("keep_outputs", C.c_int32),
-                ("blend_split_len", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("blend_split_len", C.c_int32), ("mlp_ctas_per_sm", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class FrameStats(C.Structure):
