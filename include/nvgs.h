@@ -253,6 +253,37 @@ typedef struct {
 nvgs_status nvgs_kernel_stats(const nvgs_ctx* ctx, nvgs_kernel_stat* out, int cap, int* n);
 nvgs_status nvgs_reset_kernel_stats(nvgs_ctx* ctx);
 
+/* ------------------------------------------------------------------ gradients of the render */
+/* Derivatives of a loss L(image) of the last rendered frame with respect to one asset's
+ * parameters: the backward pass of the 3DGS rasteriser that Sec. 3.3 hands the survivors to
+ * (compositing of Sec. 4.1, EWA projection, SH colour).  Culled Gaussians (frustum, MLP) and
+ * fragments the forward skipped or cut off receive nothing; the alpha clamp, the 1/255 skip, the
+ * stop rule and the support cut-off are treated as constants (piecewise-smooth derivative).
+ * Every array is DEVICE float32 in the layout of nvgs_asset_desc; the call ADDS into them (zero
+ * them first), so several instances of the asset accumulate. */
+typedef struct {
+    float* means;            /* n x 3 */
+    float* log_scales;       /* n x 3 */
+    float* quats;            /* n x 4, with respect to the stored (unnormalised) quaternion */
+    float* opacity_logits;   /* n */
+    float* sh;               /* n x (sh_degree+1)^2 x 3 */
+} nvgs_asset_grads;
+
+/* dL_dimage: DEVICE H x W x 3 float32, dL/d(image) of the most recent nvgs_render on this
+ * context.  That render must have used keep_outputs = 1, and no render, query or labelling call
+ * may come between the two (the backward reuses its survivors, records, sorted pairs, final
+ * transmittance and last-fragment indices).  Returns NVGS_ERR_INVALID_ARG for a bad asset id or
+ * NULL pointer and NVGS_ERR_UNSUPPORTED when no kept frame is available. */
+nvgs_status nvgs_render_backward(nvgs_ctx* ctx, const float* dL_dimage, int asset_id,
+                                 const nvgs_asset_grads* grads);
+
+/* Replace the parameters of an asset in place from DEVICE arrays (layout of nvgs_asset_desc,
+ * same n and sh_degree) -- the update step of an optimiser.  The bounding box and the distance
+ * range of Sec. 3.1 (the MLP's input normalisation) are those computed at load time. */
+nvgs_status nvgs_update_asset(nvgs_ctx* ctx, int asset_id, const float* means,
+                              const float* log_scales, const float* quats,
+                              const float* opacity_logits, const float* sh);
+
 /* ------------------------------------------------------------------ internals of the last frame */
 /* Device pointers into the library's buffers after the last nvgs_render (valid until the next
  * call on this context).  For tests and debugging: the survivor list (S3), projected records
@@ -266,7 +297,8 @@ typedef struct {
     const uint32_t* pair_keys;   /* n_pairs tile ids of those pairs (non-decreasing) */
     const uint32_t* tile_ranges; /* 2 x n_tiles: [start, end) into pair_values */
     const float* final_T;        /* W x H, when flags.keep_outputs */
-    const int32_t* n_contrib;    /* W x H, when flags.keep_outputs: fragments blended */
+    const int32_t* n_contrib;    /* W x H, when flags.keep_outputs: 1 + index (into the sorted
+                                    pairs) of the last fragment blended at the pixel, 0 if none */
     uint64_t n_survivors, n_pairs;
     int32_t tiles_x, tiles_y, tile_size, depth_bits; /* depth_bits: 0 (pair_keys hold tile ids) */
 } nvgs_frame_view;

@@ -32,7 +32,7 @@ constexpr float kPowerMargin = 1e-4f;
 
 struct Frag {
     float T, C0, C1, C2;
-    int count;
+    uint32_t last;   // global index + 1 of the last pair blended at the pixel (0: none)
     bool done;
 };
 
@@ -58,9 +58,9 @@ __device__ __forceinline__ void blend_batch(const float4* s_a, const float4* s_b
         const float4 a = s_a[j];
         const float dx = fx - a.x, dy = fy - a.y;
         const float4 b = s_b[j];
-        const float power = -0.5f * (a.z * dx * dx + b.x * dy * dy) - a.w * dx * dy;
+        const float power = splat_power(a, b, dx, dy);
         if (power > 0.0f || power < b.w - kPowerMargin) continue;
-        const float alpha = fminf(cam.alpha_max, b.y * __expf(power));
+        const float alpha = fminf(cam.alpha_max, __fmul_rn(b.y, __expf(power)));
         if (alpha < cam.alpha_min) continue;
         const float nt = f.T * (1.0f - alpha);
         if (kTransmittanceOnly) {
@@ -76,7 +76,7 @@ __device__ __forceinline__ void blend_batch(const float4* s_a, const float4* s_b
         f.C1 = fmaf(w, c.y, f.C1);
         f.C2 = fmaf(w, c.z, f.C2);
         f.T = nt;
-        f.count++;
+        f.last = base + j + 1;
     }
 }
 
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ r
         if (!all_done) {   // the chunked kernels finish this tile
             state_tc[(size_t)tile * B + threadIdx.x] =
                 make_float4(f.C0, f.C1, f.C2, f.done ? -f.T - 1.0f : f.T);
-            state_cnt[(size_t)tile * B + threadIdx.x] = f.count;
+            state_cnt[(size_t)tile * B + threadIdx.x] = (int32_t)f.last;
             return;
         }
     }
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ r
         image[3 * p + 1] = fmaf(f.T, cam.bg[1], f.C1);
         image[3 * p + 2] = fmaf(f.T, cam.bg[2], f.C2);
         if (final_T) final_T[p] = f.T;
-        if (n_contrib) n_contrib[p] = f.count;
+        if (n_contrib) n_contrib[p] = (int32_t)f.last;
     }
 }
 
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
     walk<TS, false>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, mark, s_a, s_b, s_c);
     // w < 0 marks "stopped inside this chunk or before"
     part[(size_t)item * B + threadIdx.x] = make_float4(f.C0, f.C1, f.C2, (f.done || dead) ? -f.T - 1.0f : f.T);
-    pcount[(size_t)item * B + threadIdx.x] = f.count;
+    pcount[(size_t)item * B + threadIdx.x] = (int32_t)f.last;
 }
 
 template <int TS>
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_D(const uint32_t* __rest
     if (!(px < cam.W && py < cam.H)) return;
     const float4 st = state_tc[(size_t)tile * B + threadIdx.x];
     float C0 = st.x, C1 = st.y, C2 = st.z, T;
-    int count = state_cnt[(size_t)tile * B + threadIdx.x];
+    int32_t last = state_cnt[(size_t)tile * B + threadIdx.x];
     if (st.w < 0.0f) {
         T = -st.w - 1.0f;   // stopped inside k_blend's pairs
     } else {
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_D(const uint32_t* __rest
             const size_t q = (size_t)(first[tile] + c) * B + threadIdx.x;
             const float4 v = part[q];
             C0 += v.x; C1 += v.y; C2 += v.z;
-            count += pcount[q];
+            if (pcount[q] > 0) last = pcount[q];
             if (v.w < 0.0f) { T = -v.w - 1.0f; break; }   // stopped: later chunks add nothing
             T = v.w;
         }
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_D(const uint32_t* __rest
     image[3 * p + 1] = fmaf(T, cam.bg[1], C1);
     image[3 * p + 2] = fmaf(T, cam.bg[2], C2);
     if (final_T) final_T[p] = T;
-    if (n_contrib) n_contrib[p] = count;
+    if (n_contrib) n_contrib[p] = last;
 }
 
 static inline uint64_t round256(uint64_t b) { return (b + 255) / 256 * 256; }

@@ -15,32 +15,6 @@
 
 namespace nvgs {
 
-// Real spherical harmonics up to degree 3 (the 3DGS sign convention), Y[(l+1)^2].
-// Constants: 1/(2 sqrt pi); sqrt(3/(4 pi)); sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4;
-// sqrt(35/(2 pi))/4, sqrt(105/pi)/2, sqrt(21/(2 pi))/4, sqrt(7/pi)/4, sqrt(105/pi)/4.
-__device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, float* Y) {
-    Y[0] = 0.28209479177387814f;
-    if (deg < 1) return;
-    Y[1] = -0.4886025119029199f * y;
-    Y[2] = 0.4886025119029199f * z;
-    Y[3] = -0.4886025119029199f * x;
-    if (deg < 2) return;
-    const float xx = x * x, yy = y * y, zz = z * z;
-    Y[4] = 1.0925484305920792f * x * y;
-    Y[5] = -1.0925484305920792f * y * z;
-    Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
-    Y[7] = -1.0925484305920792f * x * z;
-    Y[8] = 0.5462742152960396f * (xx - yy);
-    if (deg < 3) return;
-    Y[9] = -0.5900435899266435f * y * (3.0f * xx - yy);
-    Y[10] = 2.890611442640554f * x * y * z;
-    Y[11] = -0.4570457994644658f * y * (4.0f * zz - xx - yy);
-    Y[12] = 0.3731763325901154f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
-    Y[13] = -0.4570457994644658f * x * (4.0f * zz - xx - yy);
-    Y[14] = 1.445305721320277f * z * (xx - yy);
-    Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
-}
-
 __global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv, uint32_t n,
                                                  const FrameInst* __restrict__ fis,
                                                  const AssetDev* __restrict__ assets, CamParams cam,

@@ -51,7 +51,7 @@ struct nvgs_ctx {
     DevBuf frame_inst, bits, chunk_counts, chunk_offsets, vis_list, keep_bits, logits_tmp,
         block_counts, block_offsets, surv, rec, rects, tile_counts, tile_offsets, keys, vals,
         keys_alt, vals_alt, ranges, scratch, counters, image_tmp, final_T, n_contrib, mark, dkey,
-        didx, dkey_alt, didx_alt, split_scratch, vis_mean;
+        didx, dkey_alt, didx_alt, split_scratch, vis_mean, grad_surv;
     // visibility-MLP training state, per asset (FP32 master weights, Adam moments, views)
     struct Train {
         DevBuf w, m, v, views;
@@ -64,8 +64,11 @@ struct nvgs_ctx {
     cudaEvent_t ev[NVGS_NUM_STAGES + 1] = {};
     bool events_ready = false;
 
-    // last frame
+    // last frame (kept_frame: it kept final T and last-fragment indices and nothing has
+    // overwritten its buffers since -- what nvgs_render_backward needs)
     nvgs_frame_view last{};
+    CamParams last_cp{};
+    bool kept_frame = false;
     LaunchLog log;
     // per-kernel device time accumulated over profiled frames
     std::vector<std::string> kname;
@@ -284,6 +287,7 @@ nvgs_status run_cull(nvgs_ctx* ctx, const CamParams& cp, const nvgs_render_flags
 }
 
 nvgs_status begin_frame(nvgs_ctx* ctx, bool record) {
+    ctx->kept_frame = false;
     ctx->log.count = 0;
     ctx->log.n = 0;
     ctx->log.record = record;
@@ -292,6 +296,13 @@ nvgs_status begin_frame(nvgs_ctx* ctx, bool record) {
         ctx->log.ready = true;
     }
     return NVGS_OK;
+}
+
+// Launch-log reset for calls that enqueue work outside a frame (no timing, kept frame untouched).
+void begin_frame_log_only(nvgs_ctx* ctx) {
+    ctx->log.count = 0;
+    ctx->log.n = 0;
+    ctx->log.record = false;
 }
 
 // After the frame's final synchronisation: fold the bracketed launches into per-kernel totals.
@@ -387,7 +398,7 @@ extern "C" nvgs_status nvgs_destroy(nvgs_ctx* ctx) {
                       &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
                       &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial,
                       &ctx->dkey, &ctx->didx, &ctx->dkey_alt, &ctx->didx_alt, &ctx->split_scratch,
-                      &ctx->vis_mean};
+                      &ctx->vis_mean, &ctx->grad_surv};
     for (auto& t : ctx->train) { release(t.w); release(t.m); release(t.v); release(t.views); }
     for (DevBuf* b : bufs) release(*b);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
@@ -546,6 +557,7 @@ extern "C" nvgs_status nvgs_set_instances(nvgs_ctx* ctx, const nvgs_instance* in
     CK(cudaMemcpy(ctx->inst_raw.p, raw.data(), raw.size() * sizeof(InstanceRaw), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->inst_offset.p, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->chunks.p, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+    ctx->kept_frame = false;
     ctx->instances.assign(inst, inst + count);
     ctx->inst_offset_h = off;
     ctx->n_chunks = (int)chunks.size();
@@ -738,6 +750,8 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     L.n_pairs = n_pairs;
     L.tiles_x = cp.tiles_x; L.tiles_y = cp.tiles_y; L.tile_size = cp.tile_size;
     L.depth_bits = depth_bits;
+    ctx->last_cp = cp;
+    ctx->kept_frame = f->keep_outputs != 0 && !labels_row;
     if (stats) {
         memset(stats, 0, sizeof *stats);
         stats->n_instanced = (uint64_t)ctx->n_instanced;
@@ -951,6 +965,50 @@ extern "C" float nvgs_lr_schedule(int step, int total, float lr0, float lr1, flo
     if (step < tw) return (float)(lr0 * 0.5 * (1.0 - std::cos(M_PI * (step + 1) / tw)));
     const double u = std::min(1.0, (step - tw) / std::max(1.0, total - tw));
     return (float)(lr0 * std::pow((double)lr1 / lr0, u));
+}
+
+// ============================================================================ gradients
+extern "C" nvgs_status nvgs_render_backward(nvgs_ctx* ctx, const float* dL_dimage, int asset_id,
+                                            const nvgs_asset_grads* g) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (asset_id < 0 || asset_id >= (int)ctx->assets.size())
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "asset_id %d not loaded", asset_id);
+    if (!dL_dimage || !g || !g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "dL_dimage / gradient array is NULL");
+    if (!ctx->kept_frame)
+        return fail(ctx, NVGS_ERR_UNSUPPORTED,
+                    "no kept frame: render with keep_outputs = 1 right before the backward");
+    CK(cudaSetDevice(ctx->device));
+    const nvgs_frame_view& L = ctx->last;
+    const uint32_t n_surv = (uint32_t)L.n_survivors;
+    CK(ensure(ctx->grad_surv, render_backward_scratch_bytes(n_surv)));
+    begin_frame_log_only(ctx);
+    CK(launch_render_backward(L.tile_ranges, L.pair_values, reinterpret_cast<const float4*>(L.records),
+                              ctx->last_cp, L.final_T, L.n_contrib, dL_dimage, P<float>(ctx->grad_surv),
+                              reinterpret_cast<const uint2*>(L.survivors), n_surv,
+                              P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev), asset_id,
+                              g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, ctx->stream,
+                              &ctx->log));
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_update_asset(nvgs_ctx* ctx, int asset_id, const float* means,
+                                         const float* log_scales, const float* quats,
+                                         const float* opacity_logits, const float* sh) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (asset_id < 0 || asset_id >= (int)ctx->assets.size())
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "asset_id %d not loaded", asset_id);
+    if (!means || !log_scales || !quats || !opacity_logits || !sh)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "asset array is NULL");
+    CK(cudaSetDevice(ctx->device));
+    AssetStore& a = ctx->assets[asset_id];
+    const int K = (a.dev.sh_degree + 1) * (a.dev.sh_degree + 1);
+    ctx->kept_frame = false;
+    begin_frame_log_only(ctx);
+    CK(launch_pack_asset((uint32_t)a.dev.n, K, a.dev.sh_stride, means, log_scales, quats, opacity_logits,
+                         sh, P<float4>(a.mean_op), P<float4>(a.scale), P<float4>(a.quat), P<float>(a.sh),
+                         ctx->stream, &ctx->log));
+    return NVGS_OK;
 }
 
 extern "C" nvgs_status nvgs_last_frame(const nvgs_ctx* ctx, nvgs_frame_view* out) {

@@ -71,6 +71,41 @@ struct CamParams {
     int mlp_gate;             // 1: instances closer than d_min bypass the MLP
 };
 
+// Real spherical harmonics up to degree 3 (the 3DGS sign convention), Y[(l+1)^2].
+// Constants: 1/(2 sqrt pi); sqrt(3/(4 pi)); sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4;
+// sqrt(35/(2 pi))/4, sqrt(105/pi)/2, sqrt(21/(2 pi))/4, sqrt(7/pi)/4, sqrt(105/pi)/4.
+__device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, float* Y) {
+    Y[0] = 0.28209479177387814f;
+    if (deg < 1) return;
+    Y[1] = -0.4886025119029199f * y;
+    Y[2] = 0.4886025119029199f * z;
+    Y[3] = -0.4886025119029199f * x;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = 1.0925484305920792f * x * y;
+    Y[5] = -1.0925484305920792f * y * z;
+    Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+    Y[7] = -1.0925484305920792f * x * z;
+    Y[8] = 0.5462742152960396f * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = -0.5900435899266435f * y * (3.0f * xx - yy);
+    Y[10] = 2.890611442640554f * x * y * z;
+    Y[11] = -0.4570457994644658f * y * (4.0f * zz - xx - yy);
+    Y[12] = 0.3731763325901154f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -0.4570457994644658f * x * (4.0f * zz - xx - yy);
+    Y[14] = 1.445305721320277f * z * (xx - yy);
+    Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
+}
+
+// Exponent of a splat at a pixel offset (dx, dy) = pixel centre - mean:
+//   power = -1/2 (A dx^2 + C dy^2) - B dx dy,  a = (u, v, A, B), b = (C, opacity, ...).
+// Every rounding step is explicit (no contraction left to the compiler), so the compositing and
+// its derivative recompute bit-identical exponents and take the same alpha decisions.
+__device__ __forceinline__ float splat_power(const float4& a, const float4& b, float dx, float dy) {
+    const float q = __fmaf_rn(__fmul_rn(a.z, dx), dx, __fmul_rn(__fmul_rn(b.x, dy), dy));
+    return __fmaf_rn(-0.5f, q, -__fmul_rn(__fmul_rn(a.w, dx), dy));
+}
+
 // Raw instance as uploaded by nvgs_set_instances.
 struct InstanceRaw {
     float R[9], t[3], s;
@@ -221,5 +256,18 @@ cudaError_t radix_sort_pairs_u32(uint32_t* keys, uint32_t* values, uint32_t* key
                                  uint32_t* values_alt, uint64_t n, int key_bits, void* scratch,
                                  cudaStream_t s, LaunchLog* log, int* passes_out, int copy_back,
                                  int* result_in_alt);
+
+// N2: gradients of the render (k_backward.cu).  gsurv: render_backward_scratch_bytes(n_surv).
+size_t render_backward_scratch_bytes(uint64_t n_surv);
+cudaError_t launch_render_backward(const uint32_t* ranges, const uint32_t* values, const float4* rec,
+                                   CamParams cam, const float* final_T, const int32_t* last_pair,
+                                   const float* dL_dimg, float* gsurv, const uint2* surv, uint32_t n_surv,
+                                   const FrameInst* fi, const AssetDev* assets, int asset_id,
+                                   float* g_means, float* g_ls, float* g_quat, float* g_op, float* g_sh,
+                                   cudaStream_t s, LaunchLog* log);
+cudaError_t launch_pack_asset(uint32_t n, int K, int stride, const float* means, const float* log_scales,
+                              const float* quats, const float* opacity_logits, const float* sh,
+                              float4* mean_op, float4* scale, float4* quat, float* sh_out,
+                              cudaStream_t s, LaunchLog* log);
 
 }  // namespace nvgs

@@ -97,6 +97,11 @@ class AdamCfg(C.Structure):
                 ("step", C.c_int32)]
 
 
+class AssetGrads(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
+
+
 class KernelStat(C.Structure):
     _fields_ = [("name", C.c_char * 40), ("launches", C.c_uint64), ("total_ms", C.c_double)]
 
@@ -107,7 +112,8 @@ EXPORTS = ("nvgs_create", "nvgs_destroy", "nvgs_last_error", "nvgs_get_stream", 
            "nvgs_sort_pairs", "nvgs_kernel_stats", "nvgs_reset_kernel_stats",
            "nvgs_sort_pairs_noalloc", "nvgs_label_visibility", "nvgs_train_init",
            "nvgs_train_visibility_step", "nvgs_train_get_weights", "nvgs_lr_schedule",
-           "nvgs_get_asset_info", "nvgs_training_views")
+           "nvgs_get_asset_info", "nvgs_training_views", "nvgs_render_backward",
+           "nvgs_update_asset")
 NVGS_SORT_NOALLOC_MAX_PAIRS = 1 << 20
 
 
@@ -144,6 +150,8 @@ def _load():
     L.nvgs_lr_schedule.restype = C.c_float
     L.nvgs_get_asset_info.argtypes = [vp, C.c_int, P(AssetInfo)]
     L.nvgs_training_views.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+    L.nvgs_render_backward.argtypes = [vp, vp, C.c_int, P(AssetGrads)]
+    L.nvgs_update_asset.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("nvgs_default_flags", "nvgs_abi_version", "nvgs_last_error", "nvgs_get_stream",
                         "nvgs_lr_schedule"):
@@ -373,3 +381,15 @@ def nvgs_training_views(ctx, asset_id: int, n_dirs: int, n_dist: int, width: int
     _check(ctx, lib.nvgs_training_views(ctx, int(asset_id), int(n_dirs), int(n_dist), int(width),
                                         int(height), C.cast(arr, C.c_void_p)))
     return arr
+
+
+def nvgs_render_backward(ctx, dL_dimage, asset_id: int, means, log_scales, quats, opacity_logits, sh):
+    """Adds dL/d(parameters) of asset `asset_id` into the five device arrays, for dL/d(image) of
+    the last render (which must have kept its outputs)."""
+    g = AssetGrads(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh))
+    _check(ctx, lib.nvgs_render_backward(ctx, _ptr(dL_dimage), int(asset_id), C.byref(g)))
+
+
+def nvgs_update_asset(ctx, asset_id: int, means, log_scales, quats, opacity_logits, sh):
+    _check(ctx, lib.nvgs_update_asset(ctx, int(asset_id), _ptr(means), _ptr(log_scales), _ptr(quats),
+                                      _ptr(opacity_logits), _ptr(sh)))

@@ -43,7 +43,8 @@ def test_struct_layouts_match_the_c_compiler(N):
                "nvgs_camera": N.Camera, "nvgs_render_flags": N.RenderFlags,
                "nvgs_frame_stats": N.FrameStats, "nvgs_frame_view": N.FrameView,
                "nvgs_kernel_stat": N.KernelStat, "nvgs_asset_info": N.AssetInfo,
-               "nvgs_train_batch": N.TrainBatch, "nvgs_adam_cfg": N.AdamCfg}
+               "nvgs_train_batch": N.TrainBatch, "nvgs_adam_cfg": N.AdamCfg,
+               "nvgs_asset_grads": N.AssetGrads}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void){']
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -81,3 +82,6 @@ def test_create_fails_cleanly_on_a_bad_device(N):
     assert st != N.NVGS_OK and not h.value
     assert N.lib.nvgs_create(None, 0, None) == N.NVGS_ERR_INVALID_ARG
     assert N.lib.nvgs_destroy(None) == N.NVGS_ERR_INVALID_ARG
+    g = N.AssetGrads()
+    assert N.lib.nvgs_render_backward(None, None, 0, C.byref(g)) == N.NVGS_ERR_INVALID_ARG
+    assert N.lib.nvgs_update_asset(None, 0, None, None, None, None, None) == N.NVGS_ERR_INVALID_ARG
