@@ -290,8 +290,8 @@ nvgs_status nvgs_update_asset(nvgs_ctx* ctx, int asset_id, const float* means,
  * (S4), sorted pair values and per-tile ranges (S5). */
 typedef struct {
     const uint32_t* survivors;   /* 2 x n_survivors: (instance, gaussian) */
-    const float* records;        /* 12 x n_survivors: u, v, conic a, b, c, opacity, depth, -,
-                                    r, g, b, - */
+    const float* records;        /* 12 x n_survivors: u, v, conic a, b, c, opacity, depth,
+                                    ln(alpha_min / opacity), r, g, b, det Sigma_2D */
     const int32_t* tile_rects;   /* 4 x n_survivors: tile x0, y0, x1, y1 (inclusive) */
     const uint32_t* pair_values; /* n_pairs survivor indices in (tile, depth) order */
     const uint32_t* pair_keys;   /* n_pairs tile ids of those pairs (non-decreasing) */

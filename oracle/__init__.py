@@ -358,20 +358,41 @@ def labels(osc: OracleScene, cams, o=None):
     return np.stack(out, 0)
 
 
-def tile_lists(splats: np.ndarray, cam, tile_size: int):
-    """Per tile (row-major tile index): the valid splats whose tile rect covers it, in blend order
-    (depth, instance, gaussian).  Returns (tile ids, instance ids, gaussian ids) sorted by tile,
-    then blend order, and the set of ambiguous (footprint or decision) splats."""
+def tile_lists(splats: np.ndarray, cam, tile_size: int, mode: str = "rect", alpha_min=1.0 / 255.0):
+    """Per tile (row-major tile index): the valid splats binned to it, in blend order (depth,
+    instance, gaussian).  Returns (tile ids, instance ids, gaussian ids) sorted by tile, then
+    blend order.
+
+    mode "rect":    every tile of the splat's tile rectangle (the box of its support, R3);
+    mode "support": only tiles holding a pixel centre where the splat reaches alpha_min, i.e.
+                    q(d) = d^T conic d <= 2 ln(opacity / alpha_min) (Sec. 4.1's 1/255 rule),
+                    checked pixel by pixel over the splat's pixel box."""
     tw = (int(cam.width) + tile_size - 1) // tile_size
     v = splats[splats["valid"] != 0]
     tiles, inst, gs, depth = [], [], [], []
     for s in v:
-        for ty in range(s["tile_min"][1], s["tile_max"][1] + 1):
-            for tx in range(s["tile_min"][0], s["tile_max"][0] + 1):
-                tiles.append(ty * tw + tx)
-                inst.append(s["instance"])
-                gs.append(s["gaussian"])
-                depth.append(s["depth"])
+        if mode == "rect":
+            cover = [(tx, ty) for ty in range(s["tile_min"][1], s["tile_max"][1] + 1)
+                     for tx in range(s["tile_min"][0], s["tile_max"][0] + 1)]
+        elif mode == "support":
+            xs = np.arange(s["px_min"][0], s["px_max"][0] + 1)
+            ys = np.arange(s["px_min"][1], s["px_max"][1] + 1)
+            if xs.size == 0 or ys.size == 0:
+                continue
+            dx = (xs + 0.5 - s["u"])[None, :]
+            dy = (ys + 0.5 - s["v"])[:, None]
+            a, b, c = s["conic"]
+            q = a * dx * dx + 2.0 * b * dx * dy + c * dy * dy
+            kk = 2.0 * math.log(s["opacity"] / alpha_min)
+            yy, xx = np.nonzero(q <= kk)
+            cover = sorted(set(zip((xs[xx] // tile_size).tolist(), (ys[yy] // tile_size).tolist())))
+        else:
+            raise ValueError(mode)
+        for tx, ty in cover:
+            tiles.append(ty * tw + tx)
+            inst.append(s["instance"])
+            gs.append(s["gaussian"])
+            depth.append(s["depth"])
     tiles, inst, gs, depth = map(np.asarray, (tiles, inst, gs, depth))
     if tiles.size == 0:
         return tiles, inst, gs

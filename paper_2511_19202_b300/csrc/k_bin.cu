@@ -28,30 +28,68 @@ cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* counts, 
     return cudaGetLastError();
 }
 
+// One warp per 32 consecutive survivors (depth order).  Their pairs form one contiguous run of
+// the output starting at the first survivor's offset, so the warp walks the concatenation of the
+// 32 tile rectangles 32 candidates at a time: each lane finds its candidate's survivor by a
+// binary search over the lanes' rectangle prefix sums, tests the tile (as the projection counted
+// it), and the passing candidates are written at the running offset plus their rank in the
+// ballot -- balanced over the warp whatever the rectangle sizes, and coalesced.
 __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ order,
                                                    const int4* __restrict__ rects,
+                                                   const float4* __restrict__ rec,
                                                    const uint32_t* __restrict__ offsets, uint32_t n,
-                                                   int tiles_x, uint32_t* __restrict__ keys,
+                                                   CamParams cam, const uint32_t* __restrict__ n_pairs,
+                                                   uint32_t* __restrict__ keys,
                                                    uint32_t* __restrict__ values) {
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const uint32_t i = order[k];
-    const int4 r = rects[i];
-    if (r.x > r.z || r.y > r.w) return;
-    uint32_t o = offsets[k];
-    for (int ty = r.y; ty <= r.w; ty++)
-        for (int tx = r.x; tx <= r.z; tx++) {
-            keys[o] = (uint32_t)(ty * tiles_x + tx);
-            values[o] = i;
-            o++;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t base = warp * 32u;
+    if (base >= n) return;   // whole warps only
+    const uint32_t k = base + lane;
+    uint32_t i = 0;
+    SplatTiles st{};
+    st.w = 1;
+    if (k < n) {
+        i = order[k];
+        const int4 r = rects[i];
+        if (r.x <= r.z && r.y <= r.w) {
+            st.w = (uint32_t)(r.z - r.x + 1);
+            st.area = st.w * (uint32_t)(r.w - r.y + 1);
+            st.rx = r.x; st.ry = r.y;
+            st.test = st.area > 1u;
+            if (st.test) {
+                const float4 a = rec[3 * (size_t)i];
+                const float4 b = rec[3 * (size_t)i + 1];
+                st.u = a.x; st.v = a.y; st.A = a.z; st.B = a.w; st.C = b.x; st.kk = -2.0f * b.w;
+                st.det = rec[3 * (size_t)i + 2].w;
+            }
         }
+    }
+    const uint32_t total = warp_prefix(st.area, st.pre);
+    uint32_t out = __shfl_sync(0xffffffffu, k < n ? offsets[k] : 0u, 0);
+    const uint32_t limit = *n_pairs;
+    for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+        int j, tx = 0, ty = 0;
+        const bool pass = warp_tile_candidate(st, c0 + lane, total, cam, j, tx, ty);
+        const uint32_t ij = __shfl_sync(0xffffffffu, i, j);
+        const uint32_t bal = __ballot_sync(0xffffffffu, pass);
+        if (pass) {
+            const uint32_t pos = out + __popc(bal & ((1u << lane) - 1u));
+            if (pos < limit) {
+                keys[pos] = (uint32_t)(ty * cam.tiles_x + tx);
+                values[pos] = ij;
+            }
+        }
+        out += __popc(bal);
+    }
 }
 
-cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const uint32_t* offsets,
-                             uint32_t n, int tiles_x, uint32_t* keys, uint32_t* values,
-                             cudaStream_t s, LaunchLog* log) {
+cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const float4* rec,
+                             const uint32_t* offsets, uint32_t n, CamParams cam, const uint32_t* n_pairs,
+                             uint32_t* keys, uint32_t* values, cudaStream_t s, LaunchLog* log) {
     if (n == 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<<<(n + 255) / 256, 256, 0, s>>>(order, rects, offsets, n, tiles_x, keys, values));
+    const uint32_t warps = (n + 31) / 32;
+    NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<<<(warps + 7) / 8, 256, 0, s>>>(order, rects, rec, offsets, n, cam, n_pairs, keys, values));
     return cudaGetLastError();
 }
 

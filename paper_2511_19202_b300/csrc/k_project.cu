@@ -73,6 +73,8 @@ __global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv,
         const float u = fmaf(cam.fx, x * iz, cam.cx);
         const float v = fmaf(cam.fy, y * iz, cam.cy);
         const float xe = sqrtf(kk * ca), ye = sqrtf(kk * cc);
+        const float cA = cc / det, cB = -cb / det, cC = ca / det;   // conic, as stored
+        const float kw = -0.5f * kk;                                  // stored ln(alpha_min / o)
         // non-finite geometry (degenerate input) is never binned
         if (kk > 0.0f && det > 0.0f && isfinite(u) && isfinite(v) && isfinite(xe) &&
             isfinite(ye) && isfinite(det)) {
@@ -84,6 +86,18 @@ __global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv,
                 const int ts = cam.tile_size;
                 r = make_int4((int)x0 / ts, (int)y0 / ts, (int)x1 / ts, (int)y1 / ts);
                 cnt = (uint32_t)((r.z - r.x + 1) * (r.w - r.y + 1));
+                if (cnt > 1) {
+                    // row by row, from the values the record stores (as k_duplicate reads them)
+                    const SplatEllipse el = splat_ellipse(u, v, cA, cB, cC, det, -2.0f * kw);
+                    cnt = 0;
+                    for (int ty = r.y; ty <= r.w; ty++) {
+                        int t0, t1;
+                        row_tile_span(el, ty, ts, t0, t1);
+                        t0 = max(t0, r.x);
+                        t1 = min(t1, r.z);
+                        if (t0 <= t1) cnt += (uint32_t)(t1 - t0 + 1);
+                    }
+                }
             }
         }
         rects[i] = r;
@@ -117,11 +131,12 @@ __global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv,
                 col[2] = fmaf(Y[k], buf[3 * k + 2], col[2]);
             }
         }
-        rec[3 * (size_t)i] = make_float4(u, v, cc / det, -cb / det);
+        rec[3 * (size_t)i] = make_float4(u, v, cA, cB);
         // w: ln(alpha_min / opacity), the exponent below which a fragment cannot reach alpha_min
-        rec[3 * (size_t)i + 1] = make_float4(ca / det, op, z, -0.5f * kk);
+        rec[3 * (size_t)i + 1] = make_float4(cC, op, z, kw);
+        // w: det Sigma_2D (the binning's row spans recover Sigma_2D from it and the conic)
         rec[3 * (size_t)i + 2] = make_float4(fmaxf(col[0], 0.0f), fmaxf(col[1], 0.0f),
-                                             fmaxf(col[2], 0.0f), 0.0f);
+                                             fmaxf(col[2], 0.0f), det);
     }
 }
 

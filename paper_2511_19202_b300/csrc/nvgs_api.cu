@@ -685,8 +685,9 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     CK(ensure(ctx->vals_alt, (size_t)n_pairs * 4 + 16));
     CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
     if (radix_scratch_bytes(n_pairs) > ctx->scratch.cap) CK(ensure(ctx->scratch, radix_scratch_bytes(n_pairs)));
-    CK(launch_duplicate(order, P<int4>(ctx->rects), P<uint32_t>(ctx->tile_offsets), n_surv, cp.tiles_x,
-                        P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), s, &ctx->log));
+    CK(launch_duplicate(order, P<int4>(ctx->rects), P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
+                        n_surv, cp, counters + 2, P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), s,
+                        &ctx->log));
     tm.mark(NVGS_STAGE_SORT);
     int passes = 0, in_alt = 0;
     CK(radix_sort_pairs_u32(P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), P<uint32_t>(ctx->keys_alt),

@@ -106,6 +106,112 @@ __device__ __forceinline__ float splat_power(const float4& a, const float4& b, f
     return __fmaf_rn(-0.5f, q, -__fmul_rn(__fmul_rn(a.w, dx), dy));
 }
 
+// S5 binning refinement.  A splat's tile rectangle (the box of its support ellipse) is pruned,
+// row by row, to the tiles whose pixel-centre box meets the ellipse q(d) <= kk.  Within a tile
+// row (a horizontal band of pixel-centre offsets y in [y0, y1]) the ellipse is convex, so the
+// tiles it meets are those whose pixel-centre columns meet the interval of x it covers over the
+// band: [min x_left(y), max x_right(y)] with
+//   x_right/left(y) = (cb y +- sqrt(det (cc kk - y^2))) / cc,   |y| <= sqrt(cc kk),
+// (Sigma_2D = [[ca, cb], [cb, cc]], det its determinant); x_right is concave with its maximum at
+// the ellipse's rightmost point y = cb x_max / ca, x_max = sqrt(ca kk), so its maximum over the
+// band is at that y clamped to the band (and symmetrically for x_left).  The projection counts
+// with this function and the duplication writes with it, on the same stored record values
+// (conic and det), with every rounding step explicit, so both agree.  It is conservative: kk is
+// inflated by 1e-4 relative plus 1e-3 and the interval widened by 1e-3 px plus 1e-5 relative --
+// more than the compositing's exponent pre-test margin -- so a pruned tile holds no pixel the
+// compositing could blend.
+struct SplatEllipse {
+    float u, v;          // mean (pixels)
+    float ca, cb, cc;    // Sigma_2D recovered from the stored conic and det
+    float det, kq;       // det Sigma_2D, inflated support level
+    float xmax, ymax, yr;
+};
+
+__device__ __forceinline__ SplatEllipse splat_ellipse(float u, float v, float A, float B, float C, float det,
+                                                      float kk) {
+    SplatEllipse e;
+    e.u = u; e.v = v;
+    e.ca = __fmul_rn(C, det);
+    e.cb = __fmul_rn(-B, det);
+    e.cc = __fmul_rn(A, det);
+    e.det = det;
+    e.kq = __fadd_rn(__fmul_rn(kk, 1.0001f), 1e-3f);
+    e.xmax = __fsqrt_rn(__fmul_rn(e.ca, e.kq));
+    e.ymax = __fsqrt_rn(__fmul_rn(e.cc, e.kq));
+    e.yr = __fdiv_rn(__fmul_rn(e.cb, e.xmax), e.ca);
+    return e;
+}
+
+// Tile columns [t0, t1] of tile row ty that the ellipse reaches (t0 > t1: none).
+__device__ __forceinline__ void row_tile_span(const SplatEllipse& e, int ty, int ts, int& t0, int& t1) {
+    const float y0 = __fsub_rn(__fadd_rn((float)(ty * ts), 0.5f), e.v);
+    const float y1 = __fsub_rn(__fadd_rn((float)((ty + 1) * ts), -0.5f), e.v);
+    const float ya = fmaxf(y0, -e.ymax), yb = fminf(y1, e.ymax);
+    if (!(ya <= yb)) { t0 = 1; t1 = 0; return; }
+    const float ys = fminf(yb, fmaxf(ya, e.yr));     // band point of the rightmost x
+    const float yl = fminf(yb, fmaxf(ya, -e.yr));    // band point of the leftmost x
+    const float hr = __fsqrt_rn(fmaxf(0.0f, __fmul_rn(e.det, __fsub_rn(__fmul_rn(e.cc, e.kq), __fmul_rn(ys, ys)))));
+    const float hl = __fsqrt_rn(fmaxf(0.0f, __fmul_rn(e.det, __fsub_rn(__fmul_rn(e.cc, e.kq), __fmul_rn(yl, yl)))));
+    float xr = __fdiv_rn(__fadd_rn(__fmul_rn(e.cb, ys), hr), e.cc);
+    float xl = __fdiv_rn(__fsub_rn(__fmul_rn(e.cb, yl), hl), e.cc);
+    const float pad = __fadd_rn(1e-3f, __fmul_rn(1e-5f, __fadd_rn(fabsf(xl), fabsf(xr))));
+    xr = __fadd_rn(__fadd_rn(xr, pad), e.u);    // absolute pixel coordinates
+    xl = __fsub_rn(__fadd_rn(xl, e.u), pad);
+    // tile tx's pixel centres span [tx ts + 0.5, tx ts + ts - 0.5]
+    t1 = (int)floorf(__fdiv_rn(__fsub_rn(xr, 0.5f), (float)ts));
+    t0 = (int)ceilf(__fdiv_rn(__fadd_rn(xl, 0.5f - (float)ts), (float)ts));
+}
+
+// One splat's view of the warp-cooperative walk over the concatenated tile rectangles of the
+// warp's 32 splats (the duplication writes the kept tiles of every rectangle).
+struct SplatTiles {
+    uint32_t pre, area, w;   // exclusive prefix of the areas, rect area and width
+    int rx, ry;
+    float u, v, A, B, C, det, kk;
+    bool test;               // rect of more than one tile: pruned row by row
+};
+
+// Candidate c (< total) of the walk: the lane's owning splat j (the last lane whose prefix is
+// <= c), its tile and whether that tile is kept.  Every lane of the warp must call this.
+__device__ __forceinline__ bool warp_tile_candidate(const SplatTiles& s, uint32_t c, uint32_t total,
+                                                    const CamParams& cam, int& j, int& tx, int& ty) {
+    j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t pj = __shfl_sync(0xffffffffu, s.pre, j + step);
+        if (pj <= c) j += step;
+    }
+    const uint32_t pj = __shfl_sync(0xffffffffu, s.pre, j);
+    const uint32_t wj = __shfl_sync(0xffffffffu, s.w, j);
+    const int rx = __shfl_sync(0xffffffffu, s.rx, j), ry = __shfl_sync(0xffffffffu, s.ry, j);
+    const float uj = __shfl_sync(0xffffffffu, s.u, j), vj = __shfl_sync(0xffffffffu, s.v, j);
+    const float Aj = __shfl_sync(0xffffffffu, s.A, j), Bj = __shfl_sync(0xffffffffu, s.B, j);
+    const float Cj = __shfl_sync(0xffffffffu, s.C, j), dj = __shfl_sync(0xffffffffu, s.det, j);
+    const float kj = __shfl_sync(0xffffffffu, s.kk, j);
+    const bool tj = __shfl_sync(0xffffffffu, (int)s.test, j) != 0;
+    if (c >= total) return false;
+    const uint32_t t = c - pj;
+    tx = rx + (int)(t % wj);
+    ty = ry + (int)(t / wj);
+    if (!tj) return true;
+    int t0, t1;
+    row_tile_span(splat_ellipse(uj, vj, Aj, Bj, Cj, dj, kj), ty, cam.tile_size, t0, t1);
+    return tx >= t0 && tx <= t1;
+}
+
+// Exclusive warp prefix of the areas; returns the warp total.
+__device__ __forceinline__ uint32_t warp_prefix(uint32_t area, uint32_t& pre) {
+    const int lane = threadIdx.x & 31;
+    uint32_t p = area;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, p, o);
+        if (lane >= o) p += t;
+    }
+    pre = p - area;
+    return __shfl_sync(0xffffffffu, p, 31);
+}
+
 // Raw instance as uploaded by nvgs_set_instances.
 struct InstanceRaw {
     float R[9], t[3], s;
@@ -216,9 +322,11 @@ cudaError_t launch_project(const uint2* surv, uint32_t n, const FrameInst* fi,
 // S5 (k_bin.cu)
 cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* counts, uint32_t n,
                                  uint32_t* counts_sorted, cudaStream_t s, LaunchLog* log);
-cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const uint32_t* offsets,
-                             uint32_t n, int tiles_x, uint32_t* keys, uint32_t* values,
-                             cudaStream_t s, LaunchLog* log);
+// Pairs of the survivors in depth order: the tiles of each rectangle that row_tile_span keeps,
+// as the projection counted them.  n_pairs (device) bounds the writes.
+cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const float4* rec,
+                             const uint32_t* offsets, uint32_t n, CamParams cam, const uint32_t* n_pairs,
+                             uint32_t* keys, uint32_t* values, cudaStream_t s, LaunchLog* log);
 cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, uint32_t n_tiles, uint32_t* ranges,
                                cudaStream_t s, LaunchLog* log);
 

@@ -40,11 +40,11 @@ def survivors_set(lf):
     return s
 
 
-def check_tile_lists(gpu_tiles, gpu_inst, gpu_g, ora_tiles, ora_inst, ora_g, depth_of, drop,
-                     eps=1e-6):
-    """Per tile: the same (instance, gaussian) multiset on both sides once the ambiguous splats in
-    ``drop`` are removed, and the GPU order non-decreasing in the oracle's FP64 depth except where
-    two depths are within ``eps`` (relative) of each other, which FP32 cannot order."""
+def check_pruned_tile_lists(gpu_tiles, gpu_inst, gpu_g, support, rect, depth_of, drop, eps=1e-6):
+    """Per tile, with the ambiguous splats in ``drop`` removed: the oracle's support list (tiles
+    holding a pixel the splat reaches at alpha >= 1/255) is contained in the GPU list, which is
+    contained in the rect list, and the GPU order is non-decreasing in the oracle's FP64 depth
+    except within ``eps`` (relative).  Returns (GPU pairs, support pairs, rect pairs)."""
     def split(t, i, g):
         d = {}
         for a, b, c in zip(t.tolist(), i.tolist(), g.tolist()):
@@ -52,14 +52,14 @@ def check_tile_lists(gpu_tiles, gpu_inst, gpu_g, ora_tiles, ora_inst, ora_g, dep
                 continue
             d.setdefault(a, []).append((b, c))
         return d
-    G = split(gpu_tiles, gpu_inst, gpu_g)
-    O = split(ora_tiles, ora_inst, ora_g)
-    assert set(G) == set(O), "different sets of non-empty tiles"
-    n_pairs = 0
-    for t in O:
-        assert sorted(G[t]) == sorted(O[t]), f"tile {t}: different Gaussians"
-        ds = [depth_of[e] for e in G[t]]
+    G, S, R = split(gpu_tiles, gpu_inst, gpu_g), split(*support), split(*rect)
+    for t, lst in S.items():
+        assert set(lst) <= set(G.get(t, [])), f"tile {t}: a reachable Gaussian is missing"
+    for t, lst in G.items():
+        assert len(set(lst)) == len(lst), f"tile {t}: duplicate pair"
+        assert set(lst) <= set(R.get(t, [])), f"tile {t}: a Gaussian outside its rectangle"
+        ds = [depth_of[e] for e in lst]
         for k in range(len(ds) - 1):
             assert ds[k + 1] >= ds[k] - eps * abs(ds[k]), f"tile {t}: order broken at {k}"
-        n_pairs += len(O[t])
-    return n_pairs
+    count = lambda d: sum(len(v) for v in d.values())
+    return count(G), count(S), count(R)

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import scenes
-from gpu_common import (check_tile_lists, compare_images, gpu_image, oracle_opts_for,
+from gpu_common import (check_pruned_tile_lists, compare_images, gpu_image, oracle_opts_for,
                         renderer_for)
 
 pytestmark = pytest.mark.gpu
@@ -99,6 +99,8 @@ def test_fixed_logits_culled_set_and_order_are_exact(cfg1_setup):
 
 
 def test_tile_lists_are_exact(cfg1_setup):
+    """Every tile holding a pixel a splat can blend at lists it (front to back); pruned tiles are
+    only ever tiles of its rectangle."""
     sc, cam, r, osc = cfg1_setup
     o = oracle_opts_for(dict(tile_size=16))
     _, st = gpu_image(r, cam, use_mlp=0, tile_size=16)
@@ -108,11 +110,14 @@ def test_tile_lists_are_exact(cfg1_setup):
     gpu_tiles = lf["pair_keys"].cpu().numpy().astype(np.int64)
     assert np.all(np.diff(gpu_tiles) >= 0)
     sp = oracle.project(osc, cam, o)
-    ot, oi, og = oracle.tile_lists(sp, cam, 16)
+    support = oracle.tile_lists(sp, cam, 16, mode="support")
+    rect = oracle.tile_lists(sp, cam, 16, mode="rect")
     drop = set(zip(sp["instance"][sp["ambiguous"] != 0].tolist(), sp["gaussian"][sp["ambiguous"] != 0].tolist()))
     depth_of = dict(zip(zip(sp["instance"].tolist(), sp["gaussian"].tolist()), sp["depth"].tolist()))
-    n = check_tile_lists(gpu_tiles, surv[vals, 0], surv[vals, 1], ot, oi, og, depth_of, drop)
-    assert n > 10000
+    n_gpu, n_sup, n_rect = check_pruned_tile_lists(gpu_tiles, surv[vals, 0], surv[vals, 1], support, rect,
+                                                   depth_of, drop)
+    print(f"pairs: gpu {n_gpu}, support {n_sup}, rect {n_rect}")
+    assert n_sup > 10000 and n_gpu < n_rect
     # ranges cover exactly the sorted pairs of each tile
     rng_ = lf["tile_ranges"].cpu().numpy()
     for t in np.unique(gpu_tiles)[:50]:

@@ -251,3 +251,48 @@ def test_tile_lists_cover_every_blended_pixel(cfg1):
     d = np.array([depth[g] for g in gs.tolist()])
     same = tiles[1:] == tiles[:-1]
     assert np.all(d[1:][same] >= d[:-1][same])
+
+
+def test_support_tile_lists_are_the_tiles_of_blendable_pixels(cfg1):
+    """Support mode lists exactly the tiles holding a pixel with alpha >= 1/255 (brute force over
+    the whole image, through the exponential rather than the quadratic form), inside the rect
+    lists."""
+    scene, cam = cfg1
+    osc = oracle.OracleScene(scene)
+    o = oracle.opts(tile_size=16)
+    sp = oracle.project(osc, cam, o)
+    v = sp[sp["valid"] != 0][:300]
+    tiles, inst, gs = oracle.tile_lists(v, cam, 16, mode="support")
+    rt, ri, rg = oracle.tile_lists(v, cam, 16, mode="rect")
+    member = set(zip(tiles.tolist(), gs.tolist()))
+    assert member <= set(zip(rt.tolist(), rg.tolist()))
+    tw = cam.width // 16
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+    brute = set()
+    for s in v:
+        dx, dy = xs + 0.5 - s["u"], ys + 0.5 - s["v"]
+        p = -0.5 * (s["conic"][0] * dx * dx + s["conic"][2] * dy * dy) - s["conic"][1] * dx * dy
+        yy, xx = np.nonzero(s["opacity"] * np.exp(p) >= o.alpha_min)
+        brute |= {(t, int(s["gaussian"])) for t in set(((yy // 16) * tw + xx // 16).tolist())}
+    assert member == brute
+
+
+def test_support_tile_list_of_a_circle_off_a_tile_corner():
+    """Closed form: a circular support of radius 5 px centred at (20, 20) has a 2 x 2 tile rectangle
+    (pixels 15 ... 24) but misses tile (0, 0), whose nearest pixel centre (15.5, 15.5) lies 6.4 px
+    away; tiles (1, 0) and (0, 1) are reached at (19.5, 15.5) and (15.5, 19.5), 4.5 px away."""
+    cam = axis_camera(64, 64, fx=64.0)
+    sp = np.zeros(1, oracle.SPLAT_DTYPE)
+    op, am = 0.8, 1.0 / 255.0
+    kk = 2.0 * math.log(op / am)
+    sigma2 = 25.0 / kk                   # q = r^2 / sigma^2 = kk at r = 5
+    sp["valid"], sp["u"], sp["v"], sp["opacity"] = 1, 20.0, 20.0, op
+    sp["conic"] = [[1.0 / sigma2, 0.0, 1.0 / sigma2]]
+    sp["px_min"], sp["px_max"] = [[15, 15]], [[24, 24]]
+    sp["tile_min"], sp["tile_max"] = [[0, 0]], [[1, 1]]
+    rect = oracle.tile_lists(sp, cam, 16, mode="rect")[0]
+    supp = oracle.tile_lists(sp, cam, 16, mode="support")[0]
+    assert rect.tolist() == [0, 1, 4, 5] and supp.tolist() == [1, 4, 5]
+    sp["u"], sp["v"] = 16.0, 16.0        # on the corner: all four tiles are reached
+    sp["px_min"], sp["px_max"] = [[11, 11]], [[20, 20]]
+    assert oracle.tile_lists(sp, cam, 16, mode="support")[0].tolist() == [0, 1, 4, 5]
