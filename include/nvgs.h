@@ -102,12 +102,12 @@ typedef struct {
     int32_t profile;             /* 1: time each stage with CUDA events (nvgs_frame_stats) */
     const float* logits_override;/* nullable DEVICE array of per-instanced-Gaussian logits used
                                     instead of the MLP (tests inject fixed decisions with it) */
-    int32_t keep_outputs;        /* 1: keep final T and the contributor count per pixel for
-                                    nvgs_render_backward and the labeller */
+    int32_t keep_outputs;        /* 1: keep final T and the last blended pair per pixel for
+                                    nvgs_render_backward */
     int32_t blend_split_len;     /* tiles with more pairs are composited in chunks of this many
                                     pairs on separate CTAs (0: 4096; < 0: never; else >= 256) */
-    int32_t mlp_ctas_per_sm;     /* resident CTAs per SM of the tensor-core MLP (0: default 4;
-                                    1..4) -- a tuning knob, results do not depend on it */
+    int32_t mlp_ctas_per_sm;     /* resident CTAs per SM of the tensor-core MLP (0: default 3;
+                                    1..3) -- a tuning knob, results do not depend on it */
     int32_t reserved[5];
 } nvgs_render_flags;
 

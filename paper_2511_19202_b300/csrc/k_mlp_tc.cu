@@ -6,13 +6,18 @@
 // two 128-row tiles that share every MMA round trip (thread r owns rows r and 128 + r):
 //   1. thread r builds the 32 inputs of row r (Eq. 2 distance, frequency encoding) and writes
 //      them as BF16 into the A tile in shared memory;
-//   2. thread 0 issues tcgen05.mma (M = 128, N = 64, K = 16 per instruction) for layer 1 with the
-//      accumulator in TMEM columns [0, 64) and commits to an mbarrier;
+//   2. thread 0 issues tcgen05.mma (M = 128, K = 16 per instruction) for the layer with the
+//      accumulator in TMEM and commits to an mbarrier;
 //   3. after the mbarrier completes, each warp reads its 32 TMEM lanes (tcgen05.ld 32x32b),
-//      adds the FP32 bias, applies ReLU while converting to BF16, and writes the activations back
-//      to shared memory as the next layer's A operand; layers 2 and 3 repeat steps 2-3;
-//   4. the 64 -> 1 output layer runs in FP32 on the CUDA cores straight from the TMEM values.
-// Four CTAs share an SM (128 TMEM columns and 54 KB of shared memory each), so the epilogues of
+//      applies ReLU while converting to BF16 and writes the activations back to shared memory as
+//      the next layer's A operand.
+// All four layers run on the tensor cores, the output layer as an N = 16 MMA whose first two
+// columns hold w4 split into BF16 high and low parts (the logit is their sum).  Biases cost no
+// CUDA-core work: every layer ends with one more K = 16 MMA step of a constant A tile whose
+// first two columns are 1 against a B tile holding the bias split into BF16 high and low parts,
+// so the accumulator already contains W h + b (to about 2^-16 of b).  The epilogue of a hidden
+// layer is thus tcgen05.ld -> cvt.rn.relu.bf16x2 -> st.shared.
+// Three CTAs share an SM (128 TMEM columns and 65 KB of shared memory each), so the epilogues of
 // some overlap the MMAs of others.
 //
 // Operand layout (both operands K-major, no swizzle): 8 x 16-byte "core matrices"; element
@@ -32,31 +37,39 @@ namespace nvgs {
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kCtasPerSm = 3;
 constexpr int kHalves = 2;                 // each CTA carries two 128-row tiles through a layer
 constexpr int kRows = 128 * kHalves;       // rows per CTA step
 constexpr int kTmemCols = 64 * kHalves;
-// shared-memory map (bytes)
+// shared-memory map (bytes); the weight blob [0, kBlobBytes) is packed on the host
 constexpr int kOffW1 = 0;            // 64 x 32 BF16
 constexpr int kOffW2 = 4096;         // 64 x 64 BF16
 constexpr int kOffW3 = 12288;        // 64 x 64 BF16
-constexpr int kOffVec = 20480;       // FP32: b1[64] b2[64] b3[64] w4[64] b4 pad[3]
-constexpr int kVecFloats = 260;
-constexpr int kBlobBytes = kOffVec + kVecFloats * 4;   // 21520, a multiple of 16
+constexpr int kOffW4 = 20480;        // 16 x 64 BF16: row 0 = w4 high part, row 1 = low part
+constexpr int kOffB1 = 22528;        // bias tiles, N x 16 BF16: column 0 = high, 1 = low part
+constexpr int kOffB2 = 24576;
+constexpr int kOffB3 = 26624;
+constexpr int kOffB4 = 28672;        // 16 x 16: row 0 = b4
+constexpr int kBlobBytes = 29184;
+constexpr int kOffOnes = kBlobBytes; // 128 x 16 BF16, columns 0 and 1 = 1 (written in the kernel)
 // Per half, the input tile A (128 x 32) overlays the first half of the hidden tile H (128 x 64):
 // layer 1's MMA has finished reading A before its epilogue writes H, and the next step's inputs
-// are written only after layer 3's MMA has finished reading H.
-constexpr int kOffH = 21760;         // kHalves x (128 x 64 BF16)
+// are written only after the output layer's MMA has finished reading H.
+constexpr int kOffH = kOffOnes + 4096;
 constexpr int kHBytes = 16384;
 constexpr int kOffMisc = kOffH + kHalves * kHBytes;
 constexpr int kSmemBytes = kOffMisc + 64;
+constexpr uint32_t kSboK16 = 256;    // 16 * 16
 constexpr uint32_t kSboK32 = 512;    // 16 * 32
 constexpr uint32_t kSboK64 = 1024;   // 16 * 64
 constexpr uint32_t kLbo = 128;
 constexpr uint32_t kWaitIters = 1u << 20;   // x ~1 us suspend hint: about a second at most
 
-// kind::f16 instruction descriptor: D = F32 (bit 4), A = B = BF16 (bits 7, 10), both K-major,
+// kind::f16 instruction descriptors: D = F32 (bit 4), A = B = BF16 (bits 7, 10), both K-major,
 // N / 8 at bit 17, M / 16 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t idesc(uint32_t n) { return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24); }
+constexpr uint32_t kIdescN64 = idesc(64);
+constexpr uint32_t kIdescN16 = idesc(16);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -100,12 +113,13 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc_,
+                                         uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-        ::"r"(d_tmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc_), "r"(accumulate)
         : "memory");
 }
 
@@ -131,6 +145,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
         : "memory");
 }
 
+// The first two FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1])
+        : "r"(taddr)
+        : "memory");
+}
+
 // (lo, hi) -> BF16x2 with ReLU, lo in the low half (the lower address).
 __device__ __forceinline__ uint32_t bf16x2_relu(float lo, float hi) {
     uint32_t d;
@@ -147,8 +171,9 @@ __device__ __forceinline__ void st_chunk(uint8_t* tile, uint32_t sbo, int row, i
     *reinterpret_cast<uint4*>(tile + (row >> 3) * sbo + chunk * kLbo + (row & 7) * 16) = v;
 }
 
-// TMEM accumulator (this lane, 64 columns) + bias -> ReLU -> BF16 row of the next A operand.
-__device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, const float* bias, uint8_t* sH, int row) {
+// TMEM accumulator (this lane, 64 columns, bias included) -> ReLU -> BF16 row of the next A
+// operand.
+__device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, uint8_t* sH, int row) {
 #pragma unroll
     for (int half = 0; half < 2; half++) {
         uint32_t r[32];
@@ -157,41 +182,31 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, const float* bi
         for (int c = 0; c < 4; c++) {
             uint32_t p[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int col = half * 32 + c * 8 + 2 * q;
-                p[q] = bf16x2_relu(__uint_as_float(r[c * 8 + 2 * q]) + bias[col],
-                                   __uint_as_float(r[c * 8 + 2 * q + 1]) + bias[col + 1]);
-            }
+            for (int q = 0; q < 4; q++)
+                p[q] = bf16x2_relu(__uint_as_float(r[c * 8 + 2 * q]), __uint_as_float(r[c * 8 + 2 * q + 1]));
             st_chunk(sH, kSboK64, row, half * 4 + c, make_uint4(p[0], p[1], p[2], p[3]));
         }
     }
 }
 
-// Output layer in FP32: logit = b4 + w4 . ReLU(acc + b3).
-__device__ __forceinline__ float epilogue_logit(uint32_t t_lane, const float* b3, const float* w4, float b4) {
-    float lg = b4;
-#pragma unroll
-    for (int half = 0; half < 2; half++) {
-        uint32_t r[32];
-        tmem_ld32(t_lane + half * 32, r);
-#pragma unroll
-        for (int k = 0; k < 32; k++) {
-            const int col = half * 32 + k;
-            lg = fmaf(w4[col], fmaxf(__uint_as_float(r[k]) + b3[col], 0.0f), lg);
-        }
-    }
-    return lg;
+// Issue one layer for one 128-row tile: K / 16 steps of A x B plus the bias step.
+__device__ __forceinline__ void issue_layer(uint32_t d, const uint8_t* sA, uint32_t sbo_a, int k_steps,
+                                            const uint8_t* sW, uint32_t sbo_w, const uint8_t* sBias,
+                                            const uint8_t* sOnes, uint32_t idesc_) {
+#pragma unroll 4
+    for (int k = 0; k < k_steps; k++)
+        mma_bf16(d, sdesc(sA + 256 * k, kLbo, sbo_a), sdesc(sW + 256 * k, kLbo, sbo_w), idesc_, k > 0);
+    mma_bf16(d, sdesc(sOnes, kLbo, kSboK16), sdesc(sBias, kLbo, kSboK16), idesc_, 1);
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
 k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, uint32_t n,
          const FrameInst* __restrict__ fis,
          const AssetDev* __restrict__ assets, float threshold, uint32_t* __restrict__ keep_bits,
          float* __restrict__ logits_out, uint32_t* __restrict__ err_flag) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    const float* sVec = reinterpret_cast<const float*>(sm + kOffVec);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kOffMisc);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + kOffMisc + 8);
     int* s_red = reinterpret_cast<int*>(sm + kOffMisc + 16);
@@ -205,6 +220,14 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
     if (tid == 0) {
         mbar_init(mbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // constant A tile of the bias steps: row r = (1, 1, 0, ..., 0); core-matrix chunk 0 of row r
+    // holds k = 0..7, chunk 1 k = 8..15
+    {
+        uint8_t* sOnes = sm + kOffOnes;
+        st_chunk(sOnes, kSboK16, tid, 0, make_uint4(0x3F803F80u, 0u, 0u, 0u));
+        st_chunk(sOnes, kSboK16, tid, 1, make_uint4(0u, 0u, 0u, 0u));
+        fence_async_smem();
     }
     tc_fence_before();
     __syncthreads();
@@ -299,28 +322,24 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
             tc_fence_before();
             __syncthreads();
 
-            // ---- three tensor-core layers, both halves per round trip
+            // ---- four tensor-core layers, both halves per round trip
             bool ok = true;
 #pragma unroll 1
-            for (int layer = 0; layer < 3 && ok; layer++) {
+            for (int layer = 0; layer < 4 && ok; layer++) {
                 if (tid == 0) {
                     tc_fence_after();
 #pragma unroll
                     for (int h = 0; h < kHalves; h++) {
                         const uint8_t* sH = sm + kOffH + h * kHBytes;
                         const uint32_t d = tmem + 64 * h;
-                        if (layer == 0) {
-#pragma unroll
-                            for (int k = 0; k < 2; k++)
-                                mma_bf16(d, sdesc(sH + 256 * k, kLbo, kSboK32),
-                                         sdesc(sm + kOffW1 + 256 * k, kLbo, kSboK32), k > 0);
-                        } else {
-                            const uint8_t* W = sm + (layer == 1 ? kOffW2 : kOffW3);
-#pragma unroll
-                            for (int k = 0; k < 4; k++)
-                                mma_bf16(d, sdesc(sH + 256 * k, kLbo, kSboK64),
-                                         sdesc(W + 256 * k, kLbo, kSboK64), k > 0);
-                        }
+                        if (layer == 0)
+                            issue_layer(d, sH, kSboK32, 2, sm + kOffW1, kSboK32, sm + kOffB1, sm + kOffOnes, kIdescN64);
+                        else if (layer < 3)
+                            issue_layer(d, sH, kSboK64, 4, sm + (layer == 1 ? kOffW2 : kOffW3), kSboK64,
+                                        sm + (layer == 1 ? kOffB2 : kOffB3), sm + kOffOnes, kIdescN64);
+                        else
+                            issue_layer(d, sH, kSboK64, 4, sm + kOffW4, kSboK64, sm + kOffB4, sm + kOffOnes,
+                                        kIdescN16);
                     }
                     mma_commit(mbar);
                 }
@@ -328,17 +347,19 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
                 if (__syncthreads_or(!done)) { ok = false; break; }
                 phase ^= 1u;
                 tc_fence_after();
-                if (layer < 2) {
+                if (layer < 3) {
 #pragma unroll
                     for (int h = 0; h < kHalves; h++)
-                        epilogue_hidden(t_lane + 64 * h, sVec + 64 * layer, sm + kOffH + h * kHBytes, tid);
+                        epilogue_hidden(t_lane + 64 * h, sm + kOffH + h * kHBytes, tid);
                     fence_async_smem();
                     tc_fence_before();
                     __syncthreads();
                 } else {
 #pragma unroll
                     for (int h = 0; h < kHalves; h++) {
-                        const float lg = epilogue_logit(t_lane + 64 * h, sVec + 128, sVec + 192, sVec[256]);
+                        uint32_t r[2];
+                        tmem_ld2(t_lane + 64 * h, r);
+                        const float lg = __uint_as_float(r[0]) + __uint_as_float(r[1]);
                         if (mine[h]) {
                             logit[h] = lg;
                             keep[h] = fis[e[h].x].gated || (lg > threshold);
@@ -383,8 +404,17 @@ static uint16_t f32_to_bf16_rne(float x) {
     return (uint16_t)(u >> 16);
 }
 
-// Packs W1 (64x32), W2, W3 (64x64) as BF16 core-matrix tiles (row = output neuron, K-major) and
-// b1, b2, b3, w4, b4 as FP32, in the shared-memory byte layout k_mlp_tc reads.
+static float bf16_to_f32(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+// Packs W1 (64x32), W2, W3 (64x64) as BF16 core-matrix tiles (row = output neuron, K-major), w4
+// as rows 0 (high part) and 1 (low part) of a 16 x 64 tile, and every bias as an N x 16 tile
+// with the high part in column 0 and the low part (bias - high, rounded) in column 1, in the
+// shared-memory byte layout k_mlp_tc reads.
 void mlp_tc_pack_weights(const float* w, uint8_t* out) {
     memset(out, 0, kBlobBytes);
     const float* W1 = w;
@@ -395,26 +425,33 @@ void mlp_tc_pack_weights(const float* w, uint8_t* out) {
     const float* b3 = W3 + 64 * 64;
     const float* W4 = b3 + 64;
     const float* b4 = W4 + 64;
-    auto put = [&](int off, int K, const float* Wm) {
-        const int sbo = 16 * K;
-        for (int nrow = 0; nrow < 64; nrow++)
-            for (int k = 0; k < K; k++) {
-                const uint16_t v = f32_to_bf16_rne(Wm[nrow * K + k]);
-                const int b = off + (nrow / 8) * sbo + (k / 8) * 128 + (nrow % 8) * 16 + (k % 8) * 2;
-                memcpy(out + b, &v, 2);
-            }
+    auto put1 = [&](int off, int K, int nrow, int k, uint16_t v) {
+        const int b = off + (nrow / 8) * 16 * K + (k / 8) * 128 + (nrow % 8) * 16 + (k % 8) * 2;
+        memcpy(out + b, &v, 2);
     };
-    put(kOffW1, 32, W1);
-    put(kOffW2, 64, W2);
-    put(kOffW3, 64, W3);
-    float* vec = reinterpret_cast<float*>(out + kOffVec);
-    for (int k = 0; k < 64; k++) {
-        vec[k] = b1[k];
-        vec[64 + k] = b2[k];
-        vec[128 + k] = b3[k];
-        vec[192 + k] = W4[k];
+    auto put = [&](int off, int K, int rows, const float* Wm) {
+        for (int nrow = 0; nrow < rows; nrow++)
+            for (int k = 0; k < K; k++) put1(off, K, nrow, k, f32_to_bf16_rne(Wm[nrow * K + k]));
+    };
+    auto split = [&](int off, int K, int nrow, int k0, float x) {   // x = high + low
+        const uint16_t hi = f32_to_bf16_rne(x);
+        put1(off, K, nrow, k0, hi);
+        put1(off, K, nrow, k0 + 1, f32_to_bf16_rne(x - bf16_to_f32(hi)));
+    };
+    put(kOffW1, 32, 64, W1);
+    put(kOffW2, 64, 64, W2);
+    put(kOffW3, 64, 64, W3);
+    for (int k = 0; k < 64; k++) {   // w4: rows 0 and 1 of the 16 x 64 tile
+        const uint16_t hi = f32_to_bf16_rne(W4[k]);
+        put1(kOffW4, 64, 0, k, hi);
+        put1(kOffW4, 64, 1, k, f32_to_bf16_rne(W4[k] - bf16_to_f32(hi)));
     }
-    vec[256] = b4[0];
+    for (int nrow = 0; nrow < 64; nrow++) {
+        split(kOffB1, 16, nrow, 0, b1[nrow]);
+        split(kOffB2, 16, nrow, 0, b2[nrow]);
+        split(kOffB3, 16, nrow, 0, b3[nrow]);
+    }
+    split(kOffB4, 16, 0, 0, b4[0]);
 }
 
 cudaError_t launch_mlp_tc(const uint2* list, const float4* list_mean, uint32_t n, const FrameInst* fi,
@@ -429,7 +466,8 @@ cudaError_t launch_mlp_tc(const uint2* list, const float4* list_mean, uint32_t n
         attr_done = true;
     }
     const uint32_t steps = (n + kRows - 1) / kRows;
-    const uint32_t per_sm = ctas_per_sm >= 1 && ctas_per_sm <= 4 ? (uint32_t)ctas_per_sm : 4u;
+    const uint32_t per_sm = ctas_per_sm >= 1 && ctas_per_sm <= kCtasPerSm ? (uint32_t)ctas_per_sm
+                                                                           : (uint32_t)kCtasPerSm;
     const uint32_t grid = std::min<uint32_t>(steps, (uint32_t)num_sms * per_sm);
     NVGS_LAUNCH(log, s, "k_mlp_tc", k_mlp_tc<<<grid, kThreads, kSmemBytes, s>>>(list, list_mean, n, fi, assets, threshold, keep_bits, logits_out, err_flag));
     return cudaGetLastError();

@@ -174,8 +174,10 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ ke
     }
 }
 
+// Registers hold the tile's keys and one packed (digit << 16 | rank-in-warp) word per item;
+// values are read only when they are placed in shared memory, so two CTAs fit on an SM.
 template <typename K>
-__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(
+__global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 2 : 1) k_rs_scatter(
     const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, K* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, uint64_t n, int shift, uint32_t n_tiles,
     const uint32_t* __restrict__ hist_scan) {
@@ -194,16 +196,12 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(
     const uint64_t tile_n64 = n - base < (uint64_t)kRsTile ? n - base : (uint64_t)kRsTile;
     const int tile_n = (int)tile_n64;
     K key[kRsItems];
-    uint32_t val[kRsItems];
-    uint32_t digit[kRsItems];
-    uint32_t rank[kRsItems];
+    uint32_t pk[kRsItems];   // digit << 16 | rank among the warp's earlier items of that digit
     // each warp ranks its own contiguous slice [warp*512, warp*512 + 512) in order
 #pragma unroll
     for (int r = 0; r < kRsItems; r++) {
         const int p = warp * (kRsItems * 32) + r * 32 + lane;
-        const bool ok = p < tile_n;
-        key[r] = ok ? keys_in[base + p] : (K)0;
-        val[r] = ok ? vals_in[base + p] : 0u;
+        key[r] = p < tile_n ? keys_in[base + p] : (K)0;
     }
 #pragma unroll
     for (int r = 0; r < kRsItems; r++) {
@@ -215,8 +213,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(
         __syncwarp();
         if (ok && (peers & lt) == 0u) cnt[warp * 256 + d] = before + __popc(peers);
         __syncwarp();
-        digit[r] = d;
-        rank[r] = before + __popc(peers & lt);
+        pk[r] = (d << 16) | (before + __popc(peers & lt));
     }
     __syncthreads();
     // per digit: exclusive prefix over warps, then over digits (tile-local bucket starts)
@@ -252,10 +249,10 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(
     for (int r = 0; r < kRsItems; r++) {
         const int p = warp * (kRsItems * 32) + r * 32 + lane;
         if (p < tile_n) {
-            const uint32_t d = digit[r];
-            const uint32_t lp = d_local[d] + cnt[warp * 256 + d] + rank[r];
+            const uint32_t d = pk[r] >> 16;
+            const uint32_t lp = d_local[d] + cnt[warp * 256 + d] + (pk[r] & 0xffffu);
             s_keys[lp] = key[r];
-            s_vals[lp] = val[r];
+            s_vals[lp] = vals_in[base + p];
         }
     }
     __syncthreads();

@@ -139,8 +139,8 @@ nvgs_status validate_flags(nvgs_ctx* ctx, const nvgs_render_flags* f) {
     if (!(f->alpha_min > 0.f && f->alpha_min < 1.f) || !(f->alpha_max > 0.f && f->alpha_max <= 1.f) ||
         !(f->t_stop >= 0.f && f->t_stop < 1.f) || !(f->dilation >= 0.f) || !(f->guard_band > 0.f))
         return fail(ctx, NVGS_ERR_INVALID_ARG, "blending constants out of range");
-    if (f->mlp_ctas_per_sm < 0 || f->mlp_ctas_per_sm > 4)
-        return fail(ctx, NVGS_ERR_INVALID_ARG, "mlp_ctas_per_sm must be 0..4");
+    if (f->mlp_ctas_per_sm < 0 || f->mlp_ctas_per_sm > 3)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "mlp_ctas_per_sm must be 0..3");
     if (f->blend_split_len > 0 && f->blend_split_len < 256)
         return fail(ctx, NVGS_ERR_INVALID_ARG, "blend_split_len must be 0, negative or >= 256");
     if (f->image_memory != NVGS_MEM_HOST && f->image_memory != NVGS_MEM_DEVICE)
