@@ -105,7 +105,8 @@ typedef struct {
     int32_t keep_outputs;        /* 1: keep final T and the last blended pair per pixel for
                                     nvgs_render_backward */
     int32_t blend_split_len;     /* tiles with more pairs are composited in chunks of this many
-                                    pairs on separate CTAs (0: 4096; < 0: never; else >= 256) */
+                                    pairs on separate CTAs (0: automatic, max(4096, 4 x the
+                                    mean pairs per tile); < 0: never; else >= 256) */
     int32_t mlp_ctas_per_sm;     /* resident CTAs per SM of the tensor-core MLP (0: default 3;
                                     1..3) -- a tuning knob, results do not depend on it */
     int32_t reserved[5];

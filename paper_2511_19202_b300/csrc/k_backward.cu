@@ -28,11 +28,12 @@ constexpr int kG = 9;   // per-survivor accumulators: u, v, conic A, B, C, opaci
 template <int TS>
 __global__ void __launch_bounds__(TS* TS) k_blend_bwd(const uint32_t* __restrict__ ranges,
                                                       const uint32_t* __restrict__ values,
-                                                      const float4* __restrict__ rec, CamParams cam,
+                                                      const float4* __restrict__ rec, const CamParams* __restrict__ camp,
                                                       const float* __restrict__ final_T,
                                                       const int32_t* __restrict__ last_pair,
                                                       const float* __restrict__ dL_dimg,
                                                       float* __restrict__ gsurv) {
+    const CamParams cam = *camp;
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
@@ -164,11 +165,12 @@ __device__ __forceinline__ float3 sh_dir_grad(int deg, float x, float y, float z
 
 __global__ void __launch_bounds__(128) k_project_bwd(const uint2* __restrict__ surv, uint32_t n,
                                                      const FrameInst* __restrict__ fis,
-                                                     const AssetDev* __restrict__ assets, CamParams cam,
+                                                     const AssetDev* __restrict__ assets, const CamParams* __restrict__ camp,
                                                      const float* __restrict__ gsurv, int asset_id,
                                                      float* __restrict__ g_means, float* __restrict__ g_ls,
                                                      float* __restrict__ g_quat, float* __restrict__ g_op,
                                                      float* __restrict__ g_sh) {
+    const CamParams cam = *camp;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint2 e = surv[i];
@@ -300,7 +302,8 @@ __global__ void __launch_bounds__(128) k_project_bwd(const uint2* __restrict__ s
 }
 
 cudaError_t launch_render_backward(const uint32_t* ranges, const uint32_t* values, const float4* rec,
-                                   CamParams cam, const float* final_T, const int32_t* last_pair,
+                                   const CamParams& cam, const CamParams* cam_dev, const float* final_T,
+                                   const int32_t* last_pair,
                                    const float* dL_dimg, float* gsurv, const uint2* surv, uint32_t n_surv,
                                    const FrameInst* fi, const AssetDev* assets, int asset_id,
                                    float* g_means, float* g_ls, float* g_quat, float* g_op, float* g_sh,
@@ -309,14 +312,14 @@ cudaError_t launch_render_backward(const uint32_t* ranges, const uint32_t* value
     cudaError_t e = cudaMemsetAsync(gsurv, 0, (size_t)n_surv * kG * 4 + 4, s);
     if (e != cudaSuccess) return e;
     switch (cam.tile_size) {
-        case 8: NVGS_LAUNCH(log, s, "k_blend_bwd<8>", k_blend_bwd<8><<<n_tiles, 64, 0, s>>>(ranges, values, rec, cam, final_T, last_pair, dL_dimg, gsurv)); break;
-        case 16: NVGS_LAUNCH(log, s, "k_blend_bwd<16>", k_blend_bwd<16><<<n_tiles, 256, 0, s>>>(ranges, values, rec, cam, final_T, last_pair, dL_dimg, gsurv)); break;
-        case 32: NVGS_LAUNCH(log, s, "k_blend_bwd<32>", k_blend_bwd<32><<<n_tiles, 1024, 0, s>>>(ranges, values, rec, cam, final_T, last_pair, dL_dimg, gsurv)); break;
+        case 8: NVGS_LAUNCH(log, s, "k_blend_bwd<8>", k_blend_bwd<8><<<n_tiles, 64, 0, s>>>(ranges, values, rec, cam_dev, final_T, last_pair, dL_dimg, gsurv)); break;
+        case 16: NVGS_LAUNCH(log, s, "k_blend_bwd<16>", k_blend_bwd<16><<<n_tiles, 256, 0, s>>>(ranges, values, rec, cam_dev, final_T, last_pair, dL_dimg, gsurv)); break;
+        case 32: NVGS_LAUNCH(log, s, "k_blend_bwd<32>", k_blend_bwd<32><<<n_tiles, 1024, 0, s>>>(ranges, values, rec, cam_dev, final_T, last_pair, dL_dimg, gsurv)); break;
         default: return cudaErrorInvalidValue;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess || n_surv == 0) return e;
-    NVGS_LAUNCH(log, s, "k_project_bwd", k_project_bwd<<<(n_surv + 127) / 128, 128, 0, s>>>(surv, n_surv, fi, assets, cam, gsurv, asset_id, g_means, g_ls, g_quat, g_op, g_sh));
+    NVGS_LAUNCH(log, s, "k_project_bwd", k_project_bwd<<<(n_surv + 127) / 128, 128, 0, s>>>(surv, n_surv, fi, assets, cam_dev, gsurv, asset_id, g_means, g_ls, g_quat, g_op, g_sh));
     return cudaGetLastError();
 }
 

@@ -38,9 +38,10 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
                                                    const int4* __restrict__ rects,
                                                    const float4* __restrict__ rec,
                                                    const uint32_t* __restrict__ offsets, uint32_t n,
-                                                   CamParams cam, const uint32_t* __restrict__ n_pairs,
+                                                   const CamParams* __restrict__ camp, const uint32_t* __restrict__ n_pairs,
                                                    uint32_t* __restrict__ keys,
                                                    uint32_t* __restrict__ values) {
+    const CamParams cam = *camp;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const uint32_t base = warp * 32u;
@@ -85,11 +86,11 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
 }
 
 cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const float4* rec,
-                             const uint32_t* offsets, uint32_t n, CamParams cam, const uint32_t* n_pairs,
+                             const uint32_t* offsets, uint32_t n, const CamParams* cam_dev, const uint32_t* n_pairs,
                              uint32_t* keys, uint32_t* values, cudaStream_t s, LaunchLog* log) {
     if (n == 0) return cudaSuccess;
     const uint32_t warps = (n + 31) / 32;
-    NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<<<(warps + 7) / 8, 256, 0, s>>>(order, rects, rec, offsets, n, cam, n_pairs, keys, values));
+    NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<<<(warps + 7) / 8, 256, 0, s>>>(order, rects, rec, offsets, n, cam_dev, n_pairs, keys, values));
     return cudaGetLastError();
 }
 

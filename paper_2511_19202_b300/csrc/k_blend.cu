@@ -22,6 +22,8 @@
 //   k_blend_split_D  per pixel, the saved colour plus the chunks' colours up to the one that
 //                    stopped, and the transmittance left by it composing the background.
 // Only the grouping of the T products differs from the one-CTA order (FP32 rounding).
+#include <algorithm>
+
 #include "nvgs_internal.cuh"
 
 namespace nvgs {
@@ -101,13 +103,14 @@ __device__ __forceinline__ void walk(const uint32_t* __restrict__ values, const 
 template <int TS>
 __global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ ranges,
                                                   const uint32_t* __restrict__ values,
-                                                  const float4* __restrict__ rec, CamParams cam,
+                                                  const float4* __restrict__ rec, const CamParams* __restrict__ camp,
                                                   float* __restrict__ image, float* __restrict__ final_T,
                                                   int32_t* __restrict__ n_contrib,
                                                   uint8_t* __restrict__ mark, uint32_t split_len,
                                                   float4* __restrict__ state_tc,
                                                   int32_t* __restrict__ state_cnt,
                                                   uint32_t* __restrict__ alive) {
+    const CamParams cam = *camp;
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
@@ -167,34 +170,38 @@ __device__ __forceinline__ void chunk_range(const uint32_t* __restrict__ ranges,
 template <int TS>
 __global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __restrict__ ranges,
                                                           const uint32_t* __restrict__ values,
-                                                          const float4* __restrict__ rec, CamParams cam,
+                                                          const float4* __restrict__ rec, const CamParams* __restrict__ camp,
                                                           const uint2* __restrict__ items,
                                                           const uint32_t* __restrict__ n_items,
                                                           uint32_t split_len,
                                                           const float4* __restrict__ state_tc,
                                                           float* __restrict__ Tch) {
+    const CamParams cam = *camp;
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
     __shared__ float4 s_c[B];
-    const uint32_t item = blockIdx.x;
-    if (item >= *n_items) return;
-    const uint2 it = items[item];
-    const int tile = (int)it.x;
-    uint32_t start, end;
-    chunk_range(ranges, it, split_len, start, end);
-    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
-    const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
-    const bool stopped = state_tc[(size_t)tile * B + threadIdx.x].w < 0.0f;
-    Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, stopped || !(px < cam.W && py < cam.H)};
-    walk<TS, true>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, nullptr, s_a, s_b, s_c);
-    Tch[(size_t)item * B + threadIdx.x] = f.T;
+    // persistent: the grid is sized for the GPU, not for the worst-case item count
+    const uint32_t n_it = *n_items;
+    for (uint32_t item = blockIdx.x; item < n_it; item += gridDim.x) {
+        const uint2 it = items[item];
+        const int tile = (int)it.x;
+        uint32_t start, end;
+        chunk_range(ranges, it, split_len, start, end);
+        const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+        const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
+        const bool stopped = state_tc[(size_t)tile * B + threadIdx.x].w < 0.0f;
+        Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, stopped || !(px < cam.W && py < cam.H)};
+        __syncthreads();   // the previous item's last batch is fully consumed
+        walk<TS, true>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, nullptr, s_a, s_b, s_c);
+        Tch[(size_t)item * B + threadIdx.x] = f.T;
+    }
 }
 
 template <int TS>
 __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __restrict__ ranges,
                                                           const uint32_t* __restrict__ values,
-                                                          const float4* __restrict__ rec, CamParams cam,
+                                                          const float4* __restrict__ rec, const CamParams* __restrict__ camp,
                                                           const uint2* __restrict__ items,
                                                           const uint32_t* __restrict__ n_items,
                                                           uint32_t split_len,
@@ -202,39 +209,43 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
                                                           const float* __restrict__ Tch,
                                                           float4* __restrict__ part, int32_t* __restrict__ pcount,
                                                           uint8_t* __restrict__ mark) {
+    const CamParams cam = *camp;
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
     __shared__ float4 s_c[B];
-    const uint32_t item = blockIdx.x;
-    if (item >= *n_items) return;
-    const uint2 it = items[item];
-    const int tile = (int)it.x;
-    uint32_t start, end;
-    chunk_range(ranges, it, split_len, start, end);
-    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
-    const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
-    // transmittance entering this chunk: after k_blend's pairs, times the earlier chunks
-    const float sw = state_tc[(size_t)tile * B + threadIdx.x].w;
-    float T_in = sw < 0.0f ? 0.0f : sw;
-    for (uint32_t c = 0; c < it.y; c++) T_in *= Tch[(size_t)(item - it.y + c) * B + threadIdx.x];
-    const bool dead = sw < 0.0f || T_in < cam.t_stop;
-    Frag f{T_in, 0.0f, 0.0f, 0.0f, 0, dead || !(px < cam.W && py < cam.H)};
-    walk<TS, false>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, mark, s_a, s_b, s_c);
-    // w < 0 marks "stopped inside this chunk or before"
-    part[(size_t)item * B + threadIdx.x] = make_float4(f.C0, f.C1, f.C2, (f.done || dead) ? -f.T - 1.0f : f.T);
-    pcount[(size_t)item * B + threadIdx.x] = (int32_t)f.last;
+    const uint32_t n_it = *n_items;
+    for (uint32_t item = blockIdx.x; item < n_it; item += gridDim.x) {
+        const uint2 it = items[item];
+        const int tile = (int)it.x;
+        uint32_t start, end;
+        chunk_range(ranges, it, split_len, start, end);
+        const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+        const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
+        // transmittance entering this chunk: after k_blend's pairs, times the earlier chunks
+        const float sw = state_tc[(size_t)tile * B + threadIdx.x].w;
+        float T_in = sw < 0.0f ? 0.0f : sw;
+        for (uint32_t c = 0; c < it.y; c++) T_in *= Tch[(size_t)(item - it.y + c) * B + threadIdx.x];
+        const bool dead = sw < 0.0f || T_in < cam.t_stop;
+        Frag f{T_in, 0.0f, 0.0f, 0.0f, 0, dead || !(px < cam.W && py < cam.H)};
+        __syncthreads();   // the previous item's last batch is fully consumed
+        walk<TS, false>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, mark, s_a, s_b, s_c);
+        // w < 0 marks "stopped inside this chunk or before"
+        part[(size_t)item * B + threadIdx.x] = make_float4(f.C0, f.C1, f.C2, (f.done || dead) ? -f.T - 1.0f : f.T);
+        pcount[(size_t)item * B + threadIdx.x] = (int32_t)f.last;
+    }
 }
 
 template <int TS>
 __global__ void __launch_bounds__(TS* TS) k_blend_split_D(const uint32_t* __restrict__ n_chunks,
                                                           const uint32_t* __restrict__ first,
-                                                          CamParams cam, const float4* __restrict__ state_tc,
+                                                          const CamParams* __restrict__ camp, const float4* __restrict__ state_tc,
                                                           const int32_t* __restrict__ state_cnt,
                                                           const float4* __restrict__ part,
                                                           const int32_t* __restrict__ pcount,
                                                           float* __restrict__ image, float* __restrict__ final_T,
                                                           int32_t* __restrict__ n_contrib) {
+    const CamParams cam = *camp;
     constexpr int B = TS * TS;
     const int tile = blockIdx.x;
     const uint32_t nc = n_chunks[tile];
@@ -278,9 +289,9 @@ size_t blend_split_scratch_bytes(int n_tiles, uint64_t n_pairs, int tile_size, u
 
 template <int TS>
 static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, const float4* rec,
-                            CamParams cam, float* image, float* final_T, int32_t* n_contrib,
-                            uint8_t* mark, uint32_t split_len, uint64_t n_pairs, void* scratch,
-                            void* scan_scratch, cudaStream_t s, LaunchLog* log) {
+                            const CamParams& cam, const CamParams* cam_dev, float* image, float* final_T,
+                            int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
+                            void* scratch, void* scan_scratch, int num_sms, cudaStream_t s, LaunchLog* log) {
     constexpr int B = TS * TS;
     const int n_tiles = cam.tiles_x * cam.tiles_y;
     const bool may_split = n_pairs > split_len;
@@ -313,7 +324,7 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
         pcount = reinterpret_cast<int32_t*>(p);
     }
     NVGS_LAUNCH(log, s, TS == 8 ? "k_blend<8>" : TS == 16 ? "k_blend<16>" : "k_blend<32>",
-                k_blend<TS><<<n_tiles, B, 0, s>>>(ranges, values, rec, cam, image, final_T, n_contrib, mark,
+                k_blend<TS><<<n_tiles, B, 0, s>>>(ranges, values, rec, cam_dev, image, final_T, n_contrib, mark,
                                                   split_len, state_tc, state_cnt, alive));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !may_split) return e;
@@ -321,22 +332,24 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
     e = exclusive_scan_u32(n_chunks, first, n_tiles, n_items, scan_scratch, s, log);
     if (e != cudaSuccess) return e;
     NVGS_LAUNCH(log, s, "k_split_fill", k_split_fill<<<(n_tiles + 255) / 256, 256, 0, s>>>(n_chunks, first, n_tiles, items));
-    NVGS_LAUNCH(log, s, "k_blend_split_T", k_blend_split_T<TS><<<(unsigned)max_items, B, 0, s>>>(ranges, values, rec, cam, items, n_items, split_len, state_tc, Tch));
-    NVGS_LAUNCH(log, s, "k_blend_split_C", k_blend_split_C<TS><<<(unsigned)max_items, B, 0, s>>>(ranges, values, rec, cam, items, n_items, split_len, state_tc, Tch, part, pcount, mark));
-    NVGS_LAUNCH(log, s, "k_blend_split_D", k_blend_split_D<TS><<<n_tiles, B, 0, s>>>(n_chunks, first, cam, state_tc, state_cnt, part, pcount, image, final_T, n_contrib));
+    // persistent grids: enough CTAs to fill the GPU (the item count lives on the device)
+    const unsigned pgrid = (unsigned)std::min<uint64_t>(max_items, (uint64_t)num_sms * (2048 / B));
+    NVGS_LAUNCH(log, s, "k_blend_split_T", k_blend_split_T<TS><<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, state_tc, Tch));
+    NVGS_LAUNCH(log, s, "k_blend_split_C", k_blend_split_C<TS><<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, state_tc, Tch, part, pcount, mark));
+    NVGS_LAUNCH(log, s, "k_blend_split_D", k_blend_split_D<TS><<<n_tiles, B, 0, s>>>(n_chunks, first, cam_dev, state_tc, state_cnt, part, pcount, image, final_T, n_contrib));
     return cudaGetLastError();
 }
 
 cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const float4* rec,
-                         CamParams cam, float* image, float* final_T, int32_t* n_contrib,
-                         uint8_t* mark, uint32_t split_len, uint64_t n_pairs, void* scratch,
-                         void* scan_scratch, cudaStream_t s, LaunchLog* log) {
+                         const CamParams& cam, const CamParams* cam_dev, float* image, float* final_T,
+                         int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
+                         void* scratch, void* scan_scratch, int num_sms, cudaStream_t s, LaunchLog* log) {
     const int n_tiles = cam.tiles_x * cam.tiles_y;
     if (n_tiles <= 0) return cudaSuccess;
     switch (cam.tile_size) {
-        case 8: return blend_ts<8>(ranges, values, rec, cam, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, s, log);
-        case 16: return blend_ts<16>(ranges, values, rec, cam, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, s, log);
-        case 32: return blend_ts<32>(ranges, values, rec, cam, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, s, log);
+        case 8: return blend_ts<8>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, num_sms, s, log);
+        case 16: return blend_ts<16>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, num_sms, s, log);
+        case 32: return blend_ts<32>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, num_sms, s, log);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -15,8 +15,9 @@ namespace nvgs {
 // FP64 composition of camera and instance transforms (one thread per instance), rounded once to
 // FP32 so that the per-Gaussian camera-space position is three FMAs per coordinate.
 __global__ void k_instance_setup(const InstanceRaw* __restrict__ inst, int n_inst,
-                                 const AssetDev* __restrict__ assets, CamParams cam,
+                                 const AssetDev* __restrict__ assets, const CamParams* __restrict__ camp,
                                  FrameInst* __restrict__ out) {
+    const CamParams cam = *camp;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_inst) return;
     InstanceRaw r = inst[i];
@@ -70,9 +71,9 @@ __global__ void k_instance_setup(const InstanceRaw* __restrict__ inst, int n_ins
 }
 
 cudaError_t launch_instance_setup(const InstanceRaw* inst, int n_inst, const AssetDev* assets,
-                                  CamParams cam, FrameInst* out, cudaStream_t s, LaunchLog* log) {
+                                  const CamParams* cam_dev, FrameInst* out, cudaStream_t s, LaunchLog* log) {
     if (n_inst <= 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_instance_setup", k_instance_setup<<<(n_inst + 127) / 128, 128, 0, s>>>(inst, n_inst, assets, cam, out));
+    NVGS_LAUNCH(log, s, "k_instance_setup", k_instance_setup<<<(n_inst + 127) / 128, 128, 0, s>>>(inst, n_inst, assets, cam_dev, out));
     return cudaGetLastError();
 }
 
@@ -84,9 +85,10 @@ __device__ __forceinline__ bool in_frustum(const FrameInst& f, const CamParams& 
 
 __global__ void __launch_bounds__(256) k_frustum(const Chunk* __restrict__ chunks,
                                                  const FrameInst* __restrict__ fi,
-                                                 const AssetDev* __restrict__ assets, CamParams cam,
+                                                 const AssetDev* __restrict__ assets, const CamParams* __restrict__ camp,
                                                  uint32_t* __restrict__ bits,
                                                  uint32_t* __restrict__ chunk_counts) {
+    const CamParams cam = *camp;
     __shared__ uint32_t warp_tot[8];
     const int c = blockIdx.x;
     const Chunk ch = chunks[c];
@@ -124,10 +126,10 @@ __global__ void __launch_bounds__(256) k_frustum(const Chunk* __restrict__ chunk
 }
 
 cudaError_t launch_frustum(const Chunk* chunks, int n_chunks, const FrameInst* fi,
-                           const AssetDev* assets, CamParams cam, uint32_t* bits,
+                           const AssetDev* assets, const CamParams* cam_dev, uint32_t* bits,
                            uint32_t* chunk_counts, cudaStream_t s, LaunchLog* log) {
     if (n_chunks <= 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_frustum", k_frustum<<<n_chunks, 256, 0, s>>>(chunks, fi, assets, cam, bits, chunk_counts));
+    NVGS_LAUNCH(log, s, "k_frustum", k_frustum<<<n_chunks, 256, 0, s>>>(chunks, fi, assets, cam_dev, bits, chunk_counts));
     return cudaGetLastError();
 }
 

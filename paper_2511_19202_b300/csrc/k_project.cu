@@ -17,11 +17,12 @@ namespace nvgs {
 
 __global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv, uint32_t n,
                                                  const FrameInst* __restrict__ fis,
-                                                 const AssetDev* __restrict__ assets, CamParams cam,
+                                                 const AssetDev* __restrict__ assets, const CamParams* __restrict__ camp,
                                                  float4* __restrict__ rec, int4* __restrict__ rects,
                                                  uint32_t* __restrict__ counts,
                                                  uint32_t* __restrict__ dkey,
                                                  uint32_t* __restrict__ didx) {
+    const CamParams cam = *camp;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         const uint2 e = surv[i];
@@ -141,11 +142,11 @@ __global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv,
 }
 
 cudaError_t launch_project(const uint2* surv, uint32_t n, const FrameInst* fi,
-                           const AssetDev* assets, CamParams cam, float4* rec, int4* rects,
+                           const AssetDev* assets, const CamParams* cam_dev, float4* rec, int4* rects,
                            uint32_t* tile_counts, uint32_t* dkey, uint32_t* didx, cudaStream_t s,
                            LaunchLog* log) {
     if (n == 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_project", k_project<<<(n + 255) / 256, 256, 0, s>>>(surv, n, fi, assets, cam, rec, rects, tile_counts, dkey, didx));
+    NVGS_LAUNCH(log, s, "k_project", k_project<<<(n + 255) / 256, 256, 0, s>>>(surv, n, fi, assets, cam_dev, rec, rects, tile_counts, dkey, didx));
     return cudaGetLastError();
 }
 

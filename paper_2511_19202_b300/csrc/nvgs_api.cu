@@ -60,6 +60,13 @@ struct nvgs_ctx {
     std::vector<Train> train;
     DevBuf tr_sv, tr_sg, tr_partial;
     uint32_t* h_counters = nullptr;  // pinned mirror of counters
+    // camera parameters of the frame(s) in flight: kernels read them from device memory (so that
+    // a captured graph replays with new cameras); staged through pinned host memory
+    DevBuf cam_dev;
+    CamParams* h_cam = nullptr;
+    int h_cam_cap = 0;
+    cudaEvent_t cam_ev = nullptr;
+    bool cam_ev_pending = false;
 
     cudaEvent_t ev[NVGS_NUM_STAGES + 1] = {};
     bool events_ready = false;
@@ -210,14 +217,14 @@ bool uses_tc_mlp(const nvgs_ctx* ctx, const nvgs_render_flags* f) {
 
 // S1 (+ S2 when use_mlp, + S3): fills ctx->vis_list / surv and the counts.  `query` keeps the
 // per-entry logits for nvgs_query_visibility.
-nvgs_status run_cull(nvgs_ctx* ctx, const CamParams& cp, const nvgs_render_flags* f,
+nvgs_status run_cull(nvgs_ctx* ctx, const CamParams* cam_dev, const nvgs_render_flags* f,
                      StageTimer& tm, uint32_t* n_vis_out, uint32_t* n_mlp_out, bool want_logits,
                      bool compact) {
     cudaStream_t s = ctx->stream;
     const int n_inst = (int)ctx->instances.size();
     tm.mark(NVGS_STAGE_SETUP);
     CK(ensure(ctx->frame_inst, n_inst * sizeof(FrameInst)));
-    CK(launch_instance_setup(P<InstanceRaw>(ctx->inst_raw), n_inst, P<AssetDev>(ctx->assets_dev), cp,
+    CK(launch_instance_setup(P<InstanceRaw>(ctx->inst_raw), n_inst, P<AssetDev>(ctx->assets_dev), cam_dev,
                              P<FrameInst>(ctx->frame_inst), s, &ctx->log));
     tm.mark(NVGS_STAGE_CULL);
     const uint64_t cap = (uint64_t)ctx->n_instanced;
@@ -227,7 +234,7 @@ nvgs_status run_cull(nvgs_ctx* ctx, const CamParams& cp, const nvgs_render_flags
     CK(ensure(ctx->vis_list, cap * sizeof(uint2)));
     CK(ensure(ctx->scratch, std::max(scan_scratch_bytes(ctx->n_chunks), scan_scratch_bytes(cap / kChunk + 1))));
     CK(launch_frustum(P<Chunk>(ctx->chunks), ctx->n_chunks, P<FrameInst>(ctx->frame_inst),
-                      P<AssetDev>(ctx->assets_dev), cp, P<uint32_t>(ctx->bits),
+                      P<AssetDev>(ctx->assets_dev), cam_dev, P<uint32_t>(ctx->bits),
                       P<uint32_t>(ctx->chunk_counts), s, &ctx->log));
     uint32_t* counters = P<uint32_t>(ctx->counters);
     CK(exclusive_scan_u32(P<uint32_t>(ctx->chunk_counts), P<uint32_t>(ctx->chunk_offsets), ctx->n_chunks,
@@ -325,6 +332,29 @@ void end_frame(nvgs_ctx* ctx) {
     L.n = 0;
 }
 
+// Stage n camera records and copy them to ctx->cam_dev on the stream (the staging buffer is
+// reused only after the previous copy has completed).
+nvgs_status upload_cams(nvgs_ctx* ctx, const CamParams* cps, int n) {
+    if (n > ctx->h_cam_cap) {
+        if (ctx->cam_ev_pending) CK(cudaEventSynchronize(ctx->cam_ev));
+        ctx->cam_ev_pending = false;
+        if (ctx->h_cam) CK(cudaFreeHost(ctx->h_cam));
+        ctx->h_cam = nullptr;
+        const int cap = std::max(n, 64);
+        CK(cudaMallocHost(&ctx->h_cam, (size_t)cap * sizeof(CamParams)));
+        ctx->h_cam_cap = cap;
+        CK(ensure(ctx->cam_dev, (size_t)cap * sizeof(CamParams)));
+    }
+    if (!ctx->cam_ev) CK(cudaEventCreateWithFlags(&ctx->cam_ev, cudaEventDisableTiming));
+    if (ctx->cam_ev_pending) CK(cudaEventSynchronize(ctx->cam_ev));
+    memcpy(ctx->h_cam, cps, (size_t)n * sizeof(CamParams));
+    CK(cudaMemcpyAsync(ctx->cam_dev.p, ctx->h_cam, (size_t)n * sizeof(CamParams), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaEventRecord(ctx->cam_ev, ctx->stream));
+    ctx->cam_ev_pending = true;
+    return NVGS_OK;
+}
+
 nvgs_status check_scene(nvgs_ctx* ctx) {
     if (ctx->instances.empty()) return fail(ctx, NVGS_ERR_INVALID_ARG, "no instances set");
     return upload_assets(ctx);
@@ -398,10 +428,12 @@ extern "C" nvgs_status nvgs_destroy(nvgs_ctx* ctx) {
                       &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
                       &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial,
                       &ctx->dkey, &ctx->didx, &ctx->dkey_alt, &ctx->didx_alt, &ctx->split_scratch,
-                      &ctx->vis_mean, &ctx->grad_surv};
+                      &ctx->vis_mean, &ctx->grad_surv, &ctx->cam_dev};
     for (auto& t : ctx->train) { release(t.w); release(t.m); release(t.v); release(t.views); }
     for (DevBuf* b : bufs) release(*b);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+    if (ctx->h_cam) cudaFreeHost(ctx->h_cam);
+    if (ctx->cam_ev) cudaEventDestroy(ctx->cam_ev);
     if (ctx->events_ready)
         for (auto& ev : ctx->ev) cudaEventDestroy(ev);
     if (ctx->log.ready)
@@ -588,7 +620,9 @@ extern "C" nvgs_status nvgs_query_visibility(nvgs_ctx* ctx, const nvgs_camera* c
     begin_frame(ctx, false);
     StageTimer tm{ctx, false};
     uint32_t n_vis = 0, n_mlp = 0;
-    if ((st = run_cull(ctx, cp, f, tm, &n_vis, &n_mlp, true, false)) != NVGS_OK) return st;
+    if ((st = upload_cams(ctx, &cp, 1)) != NVGS_OK) return st;
+    if ((st = run_cull(ctx, P<CamParams>(ctx->cam_dev), f, tm, &n_vis, &n_mlp, true, false)) != NVGS_OK)
+        return st;
     cudaStream_t s = ctx->stream;
     const uint64_t N = (uint64_t)ctx->n_instanced;
     if (keep) CK(cudaMemsetAsync(keep, 0, N, s));
@@ -634,7 +668,9 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     StageTimer tm{ctx, f->profile != 0};
 
     uint32_t n_vis = 0, n_mlp = 0;
-    if ((st = run_cull(ctx, cp, f, tm, &n_vis, &n_mlp, false, true)) != NVGS_OK) return st;
+    if ((st = upload_cams(ctx, &cp, 1)) != NVGS_OK) return st;
+    const CamParams* cam_dev = P<CamParams>(ctx->cam_dev);
+    if ((st = run_cull(ctx, cam_dev, f, tm, &n_vis, &n_mlp, false, true)) != NVGS_OK) return st;
     uint32_t* counters = P<uint32_t>(ctx->counters);
     uint32_t n_surv = n_vis;
     const uint2* surv = P<uint2>(ctx->vis_list);
@@ -658,7 +694,7 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     CK(ensure(ctx->didx_alt, cap * 4 + 16));
     CK(ensure(ctx->scratch, std::max({scan_scratch_bytes(ctx->n_chunks), scan_scratch_bytes(cap + 1),
                                       radix_scratch_bytes(n_surv)})));
-    CK(launch_project(surv, n_surv, P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev), cp,
+    CK(launch_project(surv, n_surv, P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev), cam_dev,
                       P<float4>(ctx->rec), P<int4>(ctx->rects), P<uint32_t>(ctx->tile_counts),
                       P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), s, &ctx->log));
 
@@ -686,7 +722,7 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
     if (radix_scratch_bytes(n_pairs) > ctx->scratch.cap) CK(ensure(ctx->scratch, radix_scratch_bytes(n_pairs)));
     CK(launch_duplicate(order, P<int4>(ctx->rects), P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
-                        n_surv, cp, counters + 2, P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), s,
+                        n_surv, cam_dev, counters + 2, P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), s,
                         &ctx->log));
     tm.mark(NVGS_STAGE_SORT);
     int passes = 0, in_alt = 0;
@@ -721,16 +757,19 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
         mark = P<uint8_t>(ctx->mark);
         CK(cudaMemsetAsync(mark, 0, (size_t)n_surv + 1, s));
     }
-    // dense tiles: chunks of split_len pairs on separate CTAs (flags.blend_split_len, 0 = 4096,
-    // < 0 = never split)
+    // dense tiles: chunks of split_len pairs on separate CTAs (flags.blend_split_len; < 0 = never
+    // split; 0 = automatic: tiles longer than four times the mean, and at least 4096 pairs --
+    // splitting pays only where a few tiles would otherwise hold up the whole grid)
+    const uint64_t auto_len = std::max<uint64_t>(4096, 4 * ((uint64_t)n_pairs / (uint64_t)n_tiles + 1));
     const uint32_t split_len = f->blend_split_len < 0 ? 0xffffffffu
-                               : (f->blend_split_len == 0 ? 4096u : (uint32_t)f->blend_split_len);
+                               : (f->blend_split_len == 0 ? (uint32_t)std::min<uint64_t>(auto_len, 0x7fffffffu)
+                                                          : (uint32_t)f->blend_split_len);
     if (n_pairs > split_len) {
         CK(ensure(ctx->split_scratch, blend_split_scratch_bytes(n_tiles, n_pairs, cp.tile_size, split_len)));
         CK(ensure(ctx->scratch, scan_scratch_bytes(n_tiles)));
     }
-    CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, img_dev, fT, nc, mark,
-                    split_len, n_pairs, ctx->split_scratch.p, ctx->scratch.p, s, &ctx->log));
+    CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, cam_dev, img_dev, fT, nc, mark,
+                    split_len, n_pairs, ctx->split_scratch.p, ctx->scratch.p, ctx->num_sms, s, &ctx->log));
     if (labels_row) CK(launch_mark_labels(surv, n_surv, mark, labels_row, s, &ctx->log));
     tm.mark(NVGS_NUM_STAGES);
     if (f->image_memory == NVGS_MEM_HOST)
@@ -985,7 +1024,8 @@ extern "C" nvgs_status nvgs_render_backward(nvgs_ctx* ctx, const float* dL_dimag
     CK(ensure(ctx->grad_surv, render_backward_scratch_bytes(n_surv)));
     begin_frame_log_only(ctx);
     CK(launch_render_backward(L.tile_ranges, L.pair_values, reinterpret_cast<const float4*>(L.records),
-                              ctx->last_cp, L.final_T, L.n_contrib, dL_dimage, P<float>(ctx->grad_surv),
+                              ctx->last_cp, P<CamParams>(ctx->cam_dev), L.final_T, L.n_contrib, dL_dimage,
+                              P<float>(ctx->grad_surv),
                               reinterpret_cast<const uint2*>(L.survivors), n_surv,
                               P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev), asset_id,
                               g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, ctx->stream,

@@ -261,10 +261,10 @@ struct LaunchLog {
 // ------------------------------------------------------------------ launchers (stream-ordered)
 // Each returns cudaGetLastError() after its launches and logs them in *log.
 cudaError_t launch_instance_setup(const InstanceRaw* inst, int n_inst, const AssetDev* assets,
-                                  CamParams cam, FrameInst* out, cudaStream_t s, LaunchLog* log);
+                                  const CamParams* cam_dev, FrameInst* out, cudaStream_t s, LaunchLog* log);
 
 cudaError_t launch_frustum(const Chunk* chunks, int n_chunks, const FrameInst* fi,
-                           const AssetDev* assets, CamParams cam, uint32_t* bits,
+                           const AssetDev* assets, const CamParams* cam_dev, uint32_t* bits,
                            uint32_t* chunk_counts, cudaStream_t s, LaunchLog* log);
 
 // Writes (instance, gaussian) of every set bit, in bit order, at out[chunk_offsets[c] + rank],
@@ -315,7 +315,7 @@ cudaError_t launch_scatter_visibility(const uint2* list, uint32_t n, const uint3
 // S4: records, tile rects and counts; dkey / didx receive the depth sort keys (IEEE bits of
 // the camera-space z) and the survivor indices 0..n-1.
 cudaError_t launch_project(const uint2* surv, uint32_t n, const FrameInst* fi,
-                           const AssetDev* assets, CamParams cam, float4* rec,
+                           const AssetDev* assets, const CamParams* cam_dev, float4* rec,
                            int4* rects, uint32_t* tile_counts, uint32_t* dkey, uint32_t* didx,
                            cudaStream_t s, LaunchLog* log);
 
@@ -325,7 +325,7 @@ cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* counts, 
 // Pairs of the survivors in depth order: the tiles of each rectangle that row_tile_span keeps,
 // as the projection counted them.  n_pairs (device) bounds the writes.
 cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const float4* rec,
-                             const uint32_t* offsets, uint32_t n, CamParams cam, const uint32_t* n_pairs,
+                             const uint32_t* offsets, uint32_t n, const CamParams* cam_dev, const uint32_t* n_pairs,
                              uint32_t* keys, uint32_t* values, cudaStream_t s, LaunchLog* log);
 cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, uint32_t n_tiles, uint32_t* ranges,
                                cudaStream_t s, LaunchLog* log);
@@ -336,9 +336,9 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, uint32_t n_tile
 // blend_split_scratch_bytes(...), scan_scratch a scan of n_tiles values.
 size_t blend_split_scratch_bytes(int n_tiles, uint64_t n_pairs, int tile_size, uint32_t split_len);
 cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const float4* rec,
-                         CamParams cam, float* image, float* final_T, int32_t* n_contrib,
-                         uint8_t* mark, uint32_t split_len, uint64_t n_pairs, void* scratch,
-                         void* scan_scratch, cudaStream_t s, LaunchLog* log);
+                         const CamParams& cam, const CamParams* cam_dev, float* image, float* final_T,
+                         int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
+                         void* scratch, void* scan_scratch, int num_sms, cudaStream_t s, LaunchLog* log);
 // labels[row * n_gauss + g] |= mark[s] for survivor s = (instance, g)
 cudaError_t launch_mark_labels(const uint2* surv, uint32_t n_surv, const uint8_t* mark,
                                uint8_t* labels_row, cudaStream_t s, LaunchLog* log);
@@ -368,7 +368,8 @@ cudaError_t radix_sort_pairs_u32(uint32_t* keys, uint32_t* values, uint32_t* key
 // N2: gradients of the render (k_backward.cu).  gsurv: render_backward_scratch_bytes(n_surv).
 size_t render_backward_scratch_bytes(uint64_t n_surv);
 cudaError_t launch_render_backward(const uint32_t* ranges, const uint32_t* values, const float4* rec,
-                                   CamParams cam, const float* final_T, const int32_t* last_pair,
+                                   const CamParams& cam, const CamParams* cam_dev, const float* final_T,
+                                   const int32_t* last_pair,
                                    const float* dL_dimg, float* gsurv, const uint2* surv, uint32_t n_surv,
                                    const FrameInst* fi, const AssetDev* assets, int asset_id,
                                    float* g_means, float* g_ls, float* g_quat, float* g_op, float* g_sh,
