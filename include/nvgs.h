@@ -254,6 +254,34 @@ typedef struct {
 nvgs_status nvgs_kernel_stats(const nvgs_ctx* ctx, nvgs_kernel_stat* out, int cap, int* n);
 nvgs_status nvgs_reset_kernel_stats(nvgs_ctx* ctx);
 
+/* ------------------------------------------------------------------ batched, sync-free rendering */
+/* Several views in one call with no host synchronisation between (or inside) them: every count
+ * (in-frustum, survivors, pairs) stays on the device and each kernel reads it there, buffers are
+ * sized for capacities instead of the counts, and the camera records are copied to the device on
+ * the stream.  The whole batch can therefore be captured into a CUDA graph: with use_graph = 1
+ * the first call renders the batch and captures it; later calls with the same number of views,
+ * the same view sizes, flags and options replay the graph with the new cameras (one graph launch
+ * per batch).  The paper runs one view per frame (Sec. 3.3); batching serves multi-view use such
+ * as training-view rendering or several cameras per frame. */
+typedef struct {
+    int64_t max_pairs;           /* capacity of (tile, Gaussian) pairs per view; 0: 8 x the
+                                    instanced Gaussians */
+    int32_t use_graph;           /* 1: capture on first use, replay on later calls */
+    int32_t reserved[5];
+} nvgs_batch_opts;
+
+/* cams: n_views cameras (host); images: n_views DEVICE pointers to H x W x 3 float32 (each the
+ * size of its camera); flags as for nvgs_render except that image_memory must be DEVICE and
+ * keep_outputs, profile and labelling are not available (NVGS_ERR_INVALID_ARG).  With
+ * blend_split_len = 0 the split length is max(4096, 4 x max_pairs / tiles).  opts: nullable
+ * (defaults).  stats: NULL (the call returns without waiting for the GPU; capacity overflows are
+ * then not reported) or n_views records, in which case the call waits for the batch and returns
+ * NVGS_ERR_CAPACITY if some view needed more than max_pairs pairs (that view's image is
+ * incomplete) or NVGS_ERR_TIMEOUT if the tensor-core MLP gave up a wait. */
+nvgs_status nvgs_render_batch(nvgs_ctx* ctx, const nvgs_camera* cams, int n_views,
+                              float* const* images, const nvgs_render_flags* flags,
+                              const nvgs_batch_opts* opts, nvgs_frame_stats* stats);
+
 /* ------------------------------------------------------------------ gradients of the render */
 /* Derivatives of a loss L(image) of the last rendered frame with respect to one asset's
  * parameters: the backward pass of the 3DGS rasteriser that Sec. 3.3 hands the survivors to

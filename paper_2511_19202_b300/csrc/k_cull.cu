@@ -199,7 +199,9 @@ cudaError_t launch_expand_chunks(const Chunk* chunks, int n_chunks, const uint32
 
 // ------------------------------------------------------------------ S3 on a list
 __global__ void __launch_bounds__(64) k_bit_counts(const uint32_t* __restrict__ bits, uint32_t n,
+                                                   const uint32_t* __restrict__ n_dev,
                                                    uint32_t* __restrict__ block_counts) {
+    if (n_dev) n = min(n, *n_dev);   // blocks past the device count write 0
     const uint32_t n_words = (n + 31) / 32;
     const uint32_t w = blockIdx.x * kChunkWords + threadIdx.x;
     uint32_t c = w < n_words ? __popc(bits[w]) : 0u;
@@ -211,22 +213,25 @@ __global__ void __launch_bounds__(64) k_bit_counts(const uint32_t* __restrict__ 
     if (threadIdx.x == 0) block_counts[blockIdx.x] = s[0] + s[1];
 }
 
-cudaError_t launch_bit_counts(const uint32_t* bits, uint32_t n, uint32_t* block_counts,
-                              cudaStream_t s, LaunchLog* log) {
+cudaError_t launch_bit_counts(const uint32_t* bits, uint32_t n, const uint32_t* n_dev,
+                              uint32_t* block_counts, cudaStream_t s, LaunchLog* log) {
     if (n == 0) return cudaSuccess;
     uint32_t nb = (n + kChunk - 1) / kChunk;
-    NVGS_LAUNCH(log, s, "k_bit_counts", k_bit_counts<<<nb, 64, 0, s>>>(bits, n, block_counts));
+    NVGS_LAUNCH(log, s, "k_bit_counts", k_bit_counts<<<nb, 64, 0, s>>>(bits, n, n_dev, block_counts));
     return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(256) k_compact_list(const uint2* __restrict__ list, uint32_t n,
+                                                      const uint32_t* __restrict__ n_dev,
                                                       const uint32_t* __restrict__ bits,
                                                       const uint32_t* __restrict__ block_offsets,
                                                       uint2* __restrict__ out) {
     __shared__ uint32_t s_word[64];
     __shared__ uint32_t s_pref[128];
+    if (n_dev) n = min(n, *n_dev);
     const uint32_t n_words = (n + 31) / 32;
     const uint32_t w0 = blockIdx.x * kChunkWords;
+    if (w0 >= n_words) return;
     int nw = (int)min((uint32_t)kChunkWords, n_words - w0);
     chunk_word_prefix(bits + w0, nw, s_word, s_pref);
     const uint32_t base = block_offsets[blockIdx.x];
@@ -243,12 +248,12 @@ __global__ void __launch_bounds__(256) k_compact_list(const uint2* __restrict__ 
     }
 }
 
-cudaError_t launch_compact_list(const uint2* list, uint32_t n, const uint32_t* bits,
+cudaError_t launch_compact_list(const uint2* list, uint32_t n, const uint32_t* n_dev, const uint32_t* bits,
                                 const uint32_t* block_offsets, uint2* out, cudaStream_t s,
                                 LaunchLog* log) {
     if (n == 0) return cudaSuccess;
     uint32_t nb = (n + kChunk - 1) / kChunk;
-    NVGS_LAUNCH(log, s, "k_compact_list", k_compact_list<<<nb, 256, 0, s>>>(list, n, bits, block_offsets, out));
+    NVGS_LAUNCH(log, s, "k_compact_list", k_compact_list<<<nb, 256, 0, s>>>(list, n, n_dev, bits, block_offsets, out));
     return cudaGetLastError();
 }
 

@@ -10,12 +10,15 @@
 namespace nvgs {
 
 __global__ void __launch_bounds__(128) k_mlp_fp32(const uint2* __restrict__ list, uint32_t n,
+                                                  const uint32_t* __restrict__ n_dev,
                                                   const FrameInst* __restrict__ fis,
                                                   const AssetDev* __restrict__ assets,
                                                   const float* __restrict__ logits_override,
                                                   const int64_t* __restrict__ inst_offset,
                                                   float threshold, uint32_t* __restrict__ keep_bits,
                                                   float* __restrict__ logits_out) {
+    if (n_dev) n = min(n, *n_dev);   // device-side count (n is then the capacity)
+    if (blockIdx.x * blockDim.x >= n) return;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     bool keep = false;
     if (i < n) {
@@ -71,12 +74,12 @@ __global__ void __launch_bounds__(128) k_mlp_fp32(const uint2* __restrict__ list
     if ((threadIdx.x & 31) == 0 && (i & ~31u) < n) keep_bits[i >> 5] = w;
 }
 
-cudaError_t launch_mlp_fp32(const uint2* list, uint32_t n, const FrameInst* fi,
+cudaError_t launch_mlp_fp32(const uint2* list, uint32_t n, const uint32_t* n_dev, const FrameInst* fi,
                             const AssetDev* assets, const float* logits_override,
                             const int64_t* inst_offset, float threshold, uint32_t* keep_bits,
                             float* logits_out, cudaStream_t s, LaunchLog* log) {
     if (n == 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_mlp_fp32", k_mlp_fp32<<<(n + 127) / 128, 128, 0, s>>>(list, n, fi, assets, logits_override, inst_offset, threshold, keep_bits, logits_out));
+    NVGS_LAUNCH(log, s, "k_mlp_fp32", k_mlp_fp32<<<(n + 127) / 128, 128, 0, s>>>(list, n, n_dev, fi, assets, logits_override, inst_offset, threshold, keep_bits, logits_out));
     return cudaGetLastError();
 }
 

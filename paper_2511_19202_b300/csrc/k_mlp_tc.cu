@@ -203,10 +203,11 @@ __device__ __forceinline__ void issue_layer(uint32_t d, const uint8_t* sA, uint3
 
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, uint32_t n,
-         const FrameInst* __restrict__ fis,
+         const uint32_t* __restrict__ n_dev, const FrameInst* __restrict__ fis,
          const AssetDev* __restrict__ assets, float threshold, uint32_t* __restrict__ keep_bits,
          float* __restrict__ logits_out, uint32_t* __restrict__ err_flag) {
     extern __shared__ __align__(1024) uint8_t sm[];
+    if (n_dev) n = min(n, *n_dev);   // device-side count (n is then the capacity)
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kOffMisc);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + kOffMisc + 8);
     int* s_red = reinterpret_cast<int*>(sm + kOffMisc + 16);
@@ -454,7 +455,8 @@ void mlp_tc_pack_weights(const float* w, uint8_t* out) {
     split(kOffB4, 16, 0, 0, b4[0]);
 }
 
-cudaError_t launch_mlp_tc(const uint2* list, const float4* list_mean, uint32_t n, const FrameInst* fi,
+cudaError_t launch_mlp_tc(const uint2* list, const float4* list_mean, uint32_t n, const uint32_t* n_dev,
+                          const FrameInst* fi,
                           const AssetDev* assets,
                           float threshold, uint32_t* keep_bits, float* logits_out, uint32_t* err_flag,
                           int num_sms, int ctas_per_sm, cudaStream_t s, LaunchLog* log) {
@@ -469,7 +471,7 @@ cudaError_t launch_mlp_tc(const uint2* list, const float4* list_mean, uint32_t n
     const uint32_t per_sm = ctas_per_sm >= 1 && ctas_per_sm <= kCtasPerSm ? (uint32_t)ctas_per_sm
                                                                            : (uint32_t)kCtasPerSm;
     const uint32_t grid = std::min<uint32_t>(steps, (uint32_t)num_sms * per_sm);
-    NVGS_LAUNCH(log, s, "k_mlp_tc", k_mlp_tc<<<grid, kThreads, kSmemBytes, s>>>(list, list_mean, n, fi, assets, threshold, keep_bits, logits_out, err_flag));
+    NVGS_LAUNCH(log, s, "k_mlp_tc", k_mlp_tc<<<grid, kThreads, kSmemBytes, s>>>(list, list_mean, n, n_dev, fi, assets, threshold, keep_bits, logits_out, err_flag));
     return cudaGetLastError();
 }
 

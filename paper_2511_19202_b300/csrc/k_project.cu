@@ -11,11 +11,14 @@
 // opacity * exp(power) >= alpha_min, i.e. d^T Sigma_2D^{-1} d <= 2 ln(opacity / alpha_min); its
 // axis-aligned half-extents are sqrt(k Sigma_2D,xx) and sqrt(k Sigma_2D,yy), so a splat is
 // binned to exactly the tiles whose pixel centres it can reach.
+#include <algorithm>
+
 #include "nvgs_internal.cuh"
 
 namespace nvgs {
 
 __global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv, uint32_t n,
+                                                 const uint32_t* __restrict__ n_dev,
                                                  const FrameInst* __restrict__ fis,
                                                  const AssetDev* __restrict__ assets, const CamParams* __restrict__ camp,
                                                  float4* __restrict__ rec, int4* __restrict__ rects,
@@ -23,8 +26,8 @@ __global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv,
                                                  uint32_t* __restrict__ dkey,
                                                  uint32_t* __restrict__ didx) {
     const CamParams cam = *camp;
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
+    if (n_dev) n = min(n, *n_dev);   // device-side count (n is then the capacity)
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint2 e = surv[i];
         const FrameInst& fi = fis[e.x];
         const AssetDev& a = assets[fi.asset];
@@ -141,12 +144,14 @@ __global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv,
     }
 }
 
-cudaError_t launch_project(const uint2* surv, uint32_t n, const FrameInst* fi,
+cudaError_t launch_project(const uint2* surv, uint32_t n, const uint32_t* n_dev, const FrameInst* fi,
                            const AssetDev* assets, const CamParams* cam_dev, float4* rec, int4* rects,
-                           uint32_t* tile_counts, uint32_t* dkey, uint32_t* didx, cudaStream_t s,
-                           LaunchLog* log) {
+                           uint32_t* tile_counts, uint32_t* dkey, uint32_t* didx, int num_sms,
+                           cudaStream_t s, LaunchLog* log) {
     if (n == 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_project", k_project<<<(n + 255) / 256, 256, 0, s>>>(surv, n, fi, assets, cam_dev, rec, rects, tile_counts, dkey, didx));
+    // grid-stride: at most 3 resident CTAs per SM at this kernel's register count
+    const uint32_t grid = std::min<uint32_t>((n + 255) / 256, (uint32_t)num_sms * 3 * 4);
+    NVGS_LAUNCH(log, s, "k_project", k_project<<<grid, 256, 0, s>>>(surv, n, n_dev, fi, assets, cam_dev, rec, rects, tile_counts, dkey, didx));
     return cudaGetLastError();
 }
 

@@ -8,6 +8,8 @@
 //   3. k_rs_scatter: stable rank of every pair inside its tile (warp match + per-warp running
 //      digit counters, each warp owning a contiguous 512-pair slice), a local counting sort in
 //      shared memory, then runs of equal digits written to consecutive global addresses.
+#include <algorithm>
+
 #include "nvgs_internal.cuh"
 
 namespace nvgs {
@@ -44,8 +46,9 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in,
-                                                              uint64_t n,
+                                                              uint64_t n, const uint32_t* __restrict__ n_dev,
                                                               uint32_t* __restrict__ sums) {
+    if (n_dev) n = min(n, (uint64_t)*n_dev);   // elements past the device count read as 0
     const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
     uint32_t s = 0;
 #pragma unroll
@@ -67,10 +70,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_tile(const uint32_t* __restrict__ in,
                                                             uint32_t* __restrict__ out, uint64_t n,
+                                                            const uint32_t* __restrict__ n_dev,
                                                             const uint32_t* __restrict__ offsets,
                                                             uint32_t* __restrict__ total) {
     __shared__ uint32_t s[kScanTile + kScanTile / 32];
     __shared__ uint32_t s_warp[16];
+    const uint64_t n_out = n;   // outputs are written over the whole (capacity) range
+    if (n_dev) n = min(n, (uint64_t)*n_dev);
     const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
     // striped, coalesced load; padded index p + p/32 avoids bank conflicts on the blocked read
 #pragma unroll
@@ -102,7 +108,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tile(const uint32_t* __re
     for (int j = 0; j < kScanItems; j++) {
         const int p = j * kScanThreads + threadIdx.x;
         const uint64_t i = base + p;
-        if (i < n) out[i] = s[p + (p >> 5)];
+        if (i < n_out) out[i] = s[p + (p >> 5)];
     }
     if (total && threadIdx.x == 0) *total = tot;
 }
@@ -120,13 +126,13 @@ static uint64_t scan_levels_bytes(uint64_t n) {
 size_t scan_scratch_bytes(uint64_t n) { return (size_t)scan_levels_bytes(n) + 256; }
 
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* total,
-                               void* scratch, cudaStream_t s, LaunchLog* log) {
+                               void* scratch, cudaStream_t s, LaunchLog* log, const uint32_t* n_dev) {
     if (n == 0) {
         if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
         return cudaSuccess;
     }
     if (n <= (uint64_t)kScanTile) {
-        NVGS_LAUNCH(log, s, "k_scan_tile", k_scan_tile<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total));
+        NVGS_LAUNCH(log, s, "k_scan_tile", k_scan_tile<<<1, kScanThreads, 0, s>>>(in, out, n, n_dev, nullptr, total));
         return cudaGetLastError();
     }
     const uint64_t nb = (n + kScanTile - 1) / kScanTile;
@@ -134,12 +140,12 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, ui
     uint32_t* sums = (uint32_t*)scratch;
     uint32_t* sums_scan = (uint32_t*)((char*)scratch + seg);
     void* rest = (char*)scratch + 2 * seg;
-    NVGS_LAUNCH(log, s, "k_scan_reduce", k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums));
+    NVGS_LAUNCH(log, s, "k_scan_reduce", k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, n_dev, sums));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = exclusive_scan_u32(sums, sums_scan, nb, total, rest, s, log);
     if (e != cudaSuccess) return e;
-    NVGS_LAUNCH(log, s, "k_scan_tile", k_scan_tile<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums_scan, nullptr));
+    NVGS_LAUNCH(log, s, "k_scan_tile", k_scan_tile<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, n_dev, sums_scan, nullptr));
     return cudaGetLastError();
 }
 
@@ -152,25 +158,36 @@ constexpr int kRsWarps = kRsThreads / 32;       // 16
 template <typename K>
 constexpr int rs_smem_bytes() { return kRsWarps * 256 * 4 + kRsTile * (int)sizeof(K) + kRsTile * 4 + 2 * 256 * 4; }
 
+// Persistent over tiles: tiles at or past the (device-side) element count write zero counts, so
+// the digit-major layout always spans n_tiles (the capacity's tile count).
 template <typename K>
-__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ keys, uint64_t n, int shift,
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ keys, uint64_t n,
+                                                        const uint32_t* __restrict__ n_dev, int shift,
                                                         uint32_t n_tiles, uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[kRsWarps][256];
+    if (n_dev) n = min(n, (uint64_t)*n_dev);
     const int warp = threadIdx.x >> 5;
-    for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) (&h[0][0])[k] = 0u;
-    __syncthreads();
-    const uint64_t base = (uint64_t)blockIdx.x * kRsTile;
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const uint64_t base = (uint64_t)tile * kRsTile;
+        if (base >= n) {
+            if (threadIdx.x < 256) hist[(uint64_t)threadIdx.x * n_tiles + tile] = 0u;
+            continue;
+        }
+        for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) (&h[0][0])[k] = 0u;
+        __syncthreads();
 #pragma unroll 4
-    for (int j = 0; j < kRsItems; j++) {
-        const uint64_t i = base + (uint64_t)j * kRsThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x < 256) {
-        uint32_t s = 0;
+        for (int j = 0; j < kRsItems; j++) {
+            const uint64_t i = base + (uint64_t)j * kRsThreads + threadIdx.x;
+            if (i < n) atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            uint32_t sum = 0;
 #pragma unroll
-        for (int w = 0; w < kRsWarps; w++) s += h[w][threadIdx.x];
-        hist[(uint64_t)threadIdx.x * n_tiles + blockIdx.x] = s;
+            for (int w = 0; w < kRsWarps; w++) sum += h[w][threadIdx.x];
+            hist[(uint64_t)threadIdx.x * n_tiles + tile] = sum;
+        }
+        __syncthreads();
     }
 }
 
@@ -179,8 +196,8 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ ke
 template <typename K>
 __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 2 : 1) k_rs_scatter(
     const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, K* __restrict__ keys_out,
-    uint32_t* __restrict__ vals_out, uint64_t n, int shift, uint32_t n_tiles,
-    const uint32_t* __restrict__ hist_scan) {
+    uint32_t* __restrict__ vals_out, uint64_t n, const uint32_t* __restrict__ n_dev, int shift,
+    uint32_t n_tiles, const uint32_t* __restrict__ hist_scan) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* cnt = (uint32_t*)smem;                                   // [16 warps][256]
     K* s_keys = (K*)(smem + kRsWarps * 256 * 4);
@@ -189,84 +206,89 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 2 : 1) k_rs_scatt
     uint32_t* d_global = d_local + 256;                                // [256] global start
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) cnt[k] = 0u;
-    __syncthreads();
+    if (n_dev) n = min(n, (uint64_t)*n_dev);
+    const uint32_t tiles_used = (uint32_t)((n + kRsTile - 1) / kRsTile);
+    for (uint32_t tile = blockIdx.x; tile < tiles_used; tile += gridDim.x) {
+        for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) cnt[k] = 0u;
+        __syncthreads();
 
-    const uint64_t base = (uint64_t)blockIdx.x * kRsTile;
-    const uint64_t tile_n64 = n - base < (uint64_t)kRsTile ? n - base : (uint64_t)kRsTile;
-    const int tile_n = (int)tile_n64;
-    K key[kRsItems];
-    uint32_t pk[kRsItems];   // digit << 16 | rank among the warp's earlier items of that digit
-    // each warp ranks its own contiguous slice [warp*512, warp*512 + 512) in order
+        const uint64_t base = (uint64_t)tile * kRsTile;
+        const uint64_t tile_n64 = n - base < (uint64_t)kRsTile ? n - base : (uint64_t)kRsTile;
+        const int tile_n = (int)tile_n64;
+        K key[kRsItems];
+        uint32_t pk[kRsItems];   // digit << 16 | rank among the warp's earlier items of that digit
+        // each warp ranks its own contiguous slice [warp*512, warp*512 + 512) in order
 #pragma unroll
-    for (int r = 0; r < kRsItems; r++) {
-        const int p = warp * (kRsItems * 32) + r * 32 + lane;
-        key[r] = p < tile_n ? keys_in[base + p] : (K)0;
-    }
-#pragma unroll
-    for (int r = 0; r < kRsItems; r++) {
-        const int p = warp * (kRsItems * 32) + r * 32 + lane;
-        const bool ok = p < tile_n;
-        const uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u + lane;  // unmatched
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t before = ok ? cnt[warp * 256 + d] : 0u;
-        __syncwarp();
-        if (ok && (peers & lt) == 0u) cnt[warp * 256 + d] = before + __popc(peers);
-        __syncwarp();
-        pk[r] = (d << 16) | (before + __popc(peers & lt));
-    }
-    __syncthreads();
-    // per digit: exclusive prefix over warps, then over digits (tile-local bucket starts)
-    if (threadIdx.x < 256) {
-        const int d = threadIdx.x;
-        uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < kRsWarps; w++) {
-            const uint32_t c = cnt[w * 256 + d];
-            cnt[w * 256 + d] = run;
-            run += c;
+        for (int r = 0; r < kRsItems; r++) {
+            const int p = warp * (kRsItems * 32) + r * 32 + lane;
+            key[r] = p < tile_n ? keys_in[base + p] : (K)0;
         }
-        d_local[d] = run;   // digit total for now
-        d_global[d] = hist_scan[(uint64_t)d * n_tiles + blockIdx.x];
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {  // exclusive scan of the 256 digit totals by one warp
-        uint32_t v[8], s = 0;
 #pragma unroll
-        for (int k = 0; k < 8; k++) { v[k] = d_local[lane * 8 + k]; s += v[k]; }
-        uint32_t x = s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += t;
+        for (int r = 0; r < kRsItems; r++) {
+            const int p = warp * (kRsItems * 32) + r * 32 + lane;
+            const bool ok = p < tile_n;
+            const uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u + lane;  // unmatched
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t before = ok ? cnt[warp * 256 + d] : 0u;
+            __syncwarp();
+            if (ok && (peers & lt) == 0u) cnt[warp * 256 + d] = before + __popc(peers);
+            __syncwarp();
+            pk[r] = (d << 16) | (before + __popc(peers & lt));
         }
-        uint32_t run = x - s;
+        __syncthreads();
+        // per digit: exclusive prefix over warps, then over digits (tile-local bucket starts)
+        if (threadIdx.x < 256) {
+            const int d = threadIdx.x;
+            uint32_t run = 0;
 #pragma unroll
-        for (int k = 0; k < 8; k++) { d_local[lane * 8 + k] = run; run += v[k]; }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kRsItems; r++) {
-        const int p = warp * (kRsItems * 32) + r * 32 + lane;
-        if (p < tile_n) {
-            const uint32_t d = pk[r] >> 16;
-            const uint32_t lp = d_local[d] + cnt[warp * 256 + d] + (pk[r] & 0xffffu);
-            s_keys[lp] = key[r];
-            s_vals[lp] = vals_in[base + p];
+            for (int w = 0; w < kRsWarps; w++) {
+                const uint32_t c = cnt[w * 256 + d];
+                cnt[w * 256 + d] = run;
+                run += c;
+            }
+            d_local[d] = run;   // digit total for now
+            d_global[d] = hist_scan[(uint64_t)d * n_tiles + tile];
         }
-    }
-    __syncthreads();
-    // the tile is now sorted by digit in shared memory; stream it out in order
+        __syncthreads();
+        if (threadIdx.x < 32) {  // exclusive scan of the 256 digit totals by one warp
+            uint32_t v[8], s = 0;
+#pragma unroll
+            for (int k = 0; k < 8; k++) { v[k] = d_local[lane * 8 + k]; s += v[k]; }
+            uint32_t x = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += t;
+            }
+            uint32_t run = x - s;
+#pragma unroll
+            for (int k = 0; k < 8; k++) { d_local[lane * 8 + k] = run; run += v[k]; }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kRsItems; r++) {
+            const int p = warp * (kRsItems * 32) + r * 32 + lane;
+            if (p < tile_n) {
+                const uint32_t d = pk[r] >> 16;
+                const uint32_t lp = d_local[d] + cnt[warp * 256 + d] + (pk[r] & 0xffffu);
+                s_keys[lp] = key[r];
+                s_vals[lp] = vals_in[base + p];
+            }
+        }
+        __syncthreads();
+        // the tile is now sorted by digit in shared memory; stream it out in order
 #pragma unroll 4
-    for (int j = 0; j < kRsItems; j++) {
-        const int p = j * kRsThreads + threadIdx.x;
-        if (p < tile_n) {
-            const K k = s_keys[p];
-            const uint32_t d = (uint32_t)(k >> shift) & 255u;
-            const uint64_t g = (uint64_t)d_global[d] + (uint32_t)(p - d_local[d]);
-            keys_out[g] = k;
-            vals_out[g] = s_vals[p];
+        for (int j = 0; j < kRsItems; j++) {
+            const int p = j * kRsThreads + threadIdx.x;
+            if (p < tile_n) {
+                const K k = s_keys[p];
+                const uint32_t d = (uint32_t)(k >> shift) & 255u;
+                const uint64_t g = (uint64_t)d_global[d] + (uint32_t)(p - d_local[d]);
+                keys_out[g] = k;
+                vals_out[g] = s_vals[p];
+            }
         }
+        __syncthreads();   // shared memory is reused by the next tile
     }
 }
 
@@ -276,12 +298,27 @@ size_t radix_scratch_bytes(uint64_t n) {
     return (size_t)(2 * h + scan_scratch_bytes(256 * tiles));
 }
 
+static int device_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 148;
+    }
+    return sms;
+}
+
+// n is the element count, or with n_dev the capacity (the count then lives on the device and
+// every kernel reads it; nothing here waits for it).
 template <typename K>
 static cudaError_t radix_sort_impl(K* keys, uint32_t* values, K* keys_alt, uint32_t* values_alt,
                                    uint64_t n, int key_bits, void* scratch, cudaStream_t s,
-                                   LaunchLog* log, int* passes_out, int copy_back, int* result_in_alt) {
+                                   LaunchLog* log, int* passes_out, int copy_back, int* result_in_alt,
+                                   const uint32_t* n_dev) {
     int passes = key_bits <= 0 ? 0 : (key_bits + 7) / 8;
-    if (n <= 1) passes = 0;
+    if (n <= 1 && !n_dev) passes = 0;
+    if (n == 0) passes = 0;
     if (passes_out) *passes_out = passes;
     if (result_in_alt) *result_in_alt = 0;
     if (passes == 0) return cudaSuccess;
@@ -303,14 +340,17 @@ static cudaError_t radix_sort_impl(K* keys, uint32_t* values, K* keys_alt, uint3
     uint32_t* vout = values_alt;
     const char* hname = sizeof(K) == 8 ? "k_rs_hist<u64>" : "k_rs_hist<u32>";
     const char* sname = sizeof(K) == 8 ? "k_rs_scatter<u64>" : "k_rs_scatter<u32>";
+    // persistent grids: the tile loops cover the rest
+    const unsigned hgrid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)device_sms() * 4);
+    const unsigned sgrid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)device_sms() * (sizeof(K) == 4 ? 2 : 1));
     for (int p = 0; p < passes; p++) {
         const int shift = 8 * p;
-        NVGS_LAUNCH(log, s, hname, k_rs_hist<K><<<(unsigned)tiles, kRsThreads, 0, s>>>(kin, n, shift, (uint32_t)tiles, hist));
+        NVGS_LAUNCH(log, s, hname, k_rs_hist<K><<<hgrid, kRsThreads, 0, s>>>(kin, n, n_dev, shift, (uint32_t)tiles, hist));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = exclusive_scan_u32(hist, hist_scan, 256 * tiles, nullptr, scan_scratch, s, log);
         if (e != cudaSuccess) return e;
-        NVGS_LAUNCH(log, s, sname, k_rs_scatter<K><<<(unsigned)tiles, kRsThreads, rs_smem_bytes<K>(), s>>>(kin, vin, kout, vout, n, shift, (uint32_t)tiles, hist_scan));
+        NVGS_LAUNCH(log, s, sname, k_rs_scatter<K><<<sgrid, kRsThreads, rs_smem_bytes<K>(), s>>>(kin, vin, kout, vout, n, n_dev, shift, (uint32_t)tiles, hist_scan));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         K* tk = kin; kin = kout; kout = tk;
@@ -334,15 +374,15 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* values,
                              int key_bits, void* scratch, cudaStream_t s, LaunchLog* log,
                              int* passes_out, int copy_back, int* result_in_alt) {
     return radix_sort_impl<unsigned long long>(keys, values, keys_alt, values_alt, n, key_bits, scratch,
-                                               s, log, passes_out, copy_back, result_in_alt);
+                                               s, log, passes_out, copy_back, result_in_alt, nullptr);
 }
 
 cudaError_t radix_sort_pairs_u32(uint32_t* keys, uint32_t* values, uint32_t* keys_alt,
                                  uint32_t* values_alt, uint64_t n, int key_bits, void* scratch,
                                  cudaStream_t s, LaunchLog* log, int* passes_out, int copy_back,
-                                 int* result_in_alt) {
+                                 int* result_in_alt, const uint32_t* n_dev) {
     return radix_sort_impl<uint32_t>(keys, values, keys_alt, values_alt, n, key_bits, scratch, s, log,
-                                     passes_out, copy_back, result_in_alt);
+                                     passes_out, copy_back, result_in_alt, n_dev);
 }
 
 }  // namespace nvgs

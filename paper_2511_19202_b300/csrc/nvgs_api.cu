@@ -76,6 +76,10 @@ struct nvgs_ctx {
     nvgs_frame_view last{};
     CamParams last_cp{};
     bool kept_frame = false;
+    // batched rendering: per-view counts (in frustum, survivors, pairs, pad) and the cached graph
+    DevBuf view_stats;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<uint8_t> graph_key;
     LaunchLog log;
     // per-kernel device time accumulated over profiled frames
     std::vector<std::string> kname;
@@ -215,11 +219,15 @@ bool uses_tc_mlp(const nvgs_ctx* ctx, const nvgs_render_flags* f) {
     return tc && any_mlp;
 }
 
-// S1 (+ S2 when use_mlp, + S3): fills ctx->vis_list / surv and the counts.  `query` keeps the
-// per-entry logits for nvgs_query_visibility.
+// S1 (+ S2 when use_mlp, + S3): fills ctx->vis_list / surv and the counts (counters[0] = in
+// frustum, counters[1] = survivors).  `query` keeps the per-entry logits for
+// nvgs_query_visibility.  Synchronous mode reads the counts back to size what follows; in
+// device-count mode (`async`) nothing waits: every later kernel reads the count from the counters
+// and the instanced-Gaussian count is the capacity (the MLP's timeout flag is read at the end of
+// the batch).
 nvgs_status run_cull(nvgs_ctx* ctx, const CamParams* cam_dev, const nvgs_render_flags* f,
                      StageTimer& tm, uint32_t* n_vis_out, uint32_t* n_mlp_out, bool want_logits,
-                     bool compact) {
+                     bool compact, bool async = false) {
     cudaStream_t s = ctx->stream;
     const int n_inst = (int)ctx->instances.size();
     tm.mark(NVGS_STAGE_SETUP);
@@ -245,10 +253,15 @@ nvgs_status run_cull(nvgs_ctx* ctx, const CamParams* cam_dev, const nvgs_render_
                             P<uint32_t>(ctx->chunk_offsets), P<uint2>(ctx->vis_list),
                             P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev),
                             tc_mlp ? P<float4>(ctx->vis_mean) : nullptr, s, &ctx->log));
-    CK(cudaMemcpyAsync(ctx->h_counters, counters, 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const uint32_t n_vis = ctx->h_counters[0];
-    *n_vis_out = n_vis;
+    uint32_t n_vis_cap = (uint32_t)cap;
+    const uint32_t* n_vis_dev = &counters[0];
+    if (!async) {
+        CK(cudaMemcpyAsync(ctx->h_counters, counters, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        n_vis_cap = ctx->h_counters[0];
+        n_vis_dev = nullptr;
+    }
+    *n_vis_out = n_vis_cap;
     *n_mlp_out = 0;
     tm.mark(NVGS_STAGE_MLP);
     if (!f->use_mlp) {
@@ -258,34 +271,37 @@ nvgs_status run_cull(nvgs_ctx* ctx, const CamParams* cam_dev, const nvgs_render_
     CK(ensure(ctx->keep_bits, ((size_t)cap / 32 + 2) * 4));
     if (want_logits) CK(ensure(ctx->logits_tmp, (size_t)cap * 4 + 16));
     if (tc_mlp) {
-        CK(cudaMemsetAsync(&counters[8], 0, 4, s));
-        CK(launch_mlp_tc(P<uint2>(ctx->vis_list), P<float4>(ctx->vis_mean), n_vis, P<FrameInst>(ctx->frame_inst),
+        if (!async) CK(cudaMemsetAsync(&counters[8], 0, 4, s));
+        CK(launch_mlp_tc(P<uint2>(ctx->vis_list), P<float4>(ctx->vis_mean), n_vis_cap, n_vis_dev,
+                         P<FrameInst>(ctx->frame_inst),
                          P<AssetDev>(ctx->assets_dev), f->logit_threshold, P<uint32_t>(ctx->keep_bits),
                          want_logits ? P<float>(ctx->logits_tmp) : nullptr, &counters[8],
                          ctx->num_sms, f->mlp_ctas_per_sm, s, &ctx->log));
-        CK(cudaMemcpyAsync(ctx->h_counters + 8, &counters[8], 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (ctx->h_counters[8])
-            return fail(ctx, NVGS_ERR_TIMEOUT, "tensor-core MLP: a bounded mbarrier wait gave up");
+        if (!async) {
+            CK(cudaMemcpyAsync(ctx->h_counters + 8, &counters[8], 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (ctx->h_counters[8])
+                return fail(ctx, NVGS_ERR_TIMEOUT, "tensor-core MLP: a bounded mbarrier wait gave up");
+        }
     } else {
-        CK(launch_mlp_fp32(P<uint2>(ctx->vis_list), n_vis, P<FrameInst>(ctx->frame_inst),
+        CK(launch_mlp_fp32(P<uint2>(ctx->vis_list), n_vis_cap, n_vis_dev, P<FrameInst>(ctx->frame_inst),
                            P<AssetDev>(ctx->assets_dev), f->logits_override, P<int64_t>(ctx->inst_offset),
                            f->logit_threshold, P<uint32_t>(ctx->keep_bits),
                            want_logits ? P<float>(ctx->logits_tmp) : nullptr, s, &ctx->log));
     }
-    *n_mlp_out = n_vis;
+    *n_mlp_out = n_vis_cap;
     tm.mark(NVGS_STAGE_COMPACT);
     if (!compact) return NVGS_OK;
-    const uint32_t nb = (n_vis + kChunk - 1) / kChunk;
+    const uint32_t nb = (n_vis_cap + kChunk - 1) / kChunk;
     CK(ensure(ctx->block_counts, (size_t)nb * 4 + 16));
     CK(ensure(ctx->block_offsets, (size_t)nb * 4 + 16));
     CK(ensure(ctx->surv, cap * sizeof(uint2)));
-    if (n_vis > 0) {
-        CK(launch_bit_counts(P<uint32_t>(ctx->keep_bits), n_vis, P<uint32_t>(ctx->block_counts), s,
+    if (n_vis_cap > 0) {
+        CK(launch_bit_counts(P<uint32_t>(ctx->keep_bits), n_vis_cap, n_vis_dev, P<uint32_t>(ctx->block_counts), s,
                              &ctx->log));
         CK(exclusive_scan_u32(P<uint32_t>(ctx->block_counts), P<uint32_t>(ctx->block_offsets), nb,
                               &counters[1], ctx->scratch.p, s, &ctx->log));
-        CK(launch_compact_list(P<uint2>(ctx->vis_list), n_vis, P<uint32_t>(ctx->keep_bits),
+        CK(launch_compact_list(P<uint2>(ctx->vis_list), n_vis_cap, n_vis_dev, P<uint32_t>(ctx->keep_bits),
                                P<uint32_t>(ctx->block_offsets), P<uint2>(ctx->surv), s, &ctx->log));
     } else {
         CK(cudaMemsetAsync(&counters[1], 0, 4, s));
@@ -428,11 +444,12 @@ extern "C" nvgs_status nvgs_destroy(nvgs_ctx* ctx) {
                       &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
                       &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial,
                       &ctx->dkey, &ctx->didx, &ctx->dkey_alt, &ctx->didx_alt, &ctx->split_scratch,
-                      &ctx->vis_mean, &ctx->grad_surv, &ctx->cam_dev};
+                      &ctx->vis_mean, &ctx->grad_surv, &ctx->cam_dev, &ctx->view_stats};
     for (auto& t : ctx->train) { release(t.w); release(t.m); release(t.v); release(t.views); }
     for (DevBuf* b : bufs) release(*b);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     if (ctx->h_cam) cudaFreeHost(ctx->h_cam);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->cam_ev) cudaEventDestroy(ctx->cam_ev);
     if (ctx->events_ready)
         for (auto& ev : ctx->ev) cudaEventDestroy(ev);
@@ -694,9 +711,9 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     CK(ensure(ctx->didx_alt, cap * 4 + 16));
     CK(ensure(ctx->scratch, std::max({scan_scratch_bytes(ctx->n_chunks), scan_scratch_bytes(cap + 1),
                                       radix_scratch_bytes(n_surv)})));
-    CK(launch_project(surv, n_surv, P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev), cam_dev,
+    CK(launch_project(surv, n_surv, nullptr, P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev), cam_dev,
                       P<float4>(ctx->rec), P<int4>(ctx->rects), P<uint32_t>(ctx->tile_counts),
-                      P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), s, &ctx->log));
+                      P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), ctx->num_sms, s, &ctx->log));
 
     // ---- S5: survivors by depth, pairs in that order, pairs by tile, tile ranges
     tm.mark(NVGS_STAGE_BIN);
@@ -706,8 +723,8 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
                             &dpasses, 0, &d_alt));
     const uint32_t* order = d_alt ? P<uint32_t>(ctx->didx_alt) : P<uint32_t>(ctx->didx);
     if (n_surv <= 1) order = P<uint32_t>(ctx->didx);
-    CK(launch_gather_counts(order, P<uint32_t>(ctx->tile_counts), n_surv, P<uint32_t>(ctx->tile_offsets),
-                            s, &ctx->log));
+    CK(launch_gather_counts(order, P<uint32_t>(ctx->tile_counts), n_surv, nullptr, P<uint32_t>(ctx->tile_offsets),
+                            ctx->num_sms, s, &ctx->log));
     CK(exclusive_scan_u32(P<uint32_t>(ctx->tile_offsets), P<uint32_t>(ctx->tile_offsets), n_surv,
                           counters + 2, ctx->scratch.p, s, &ctx->log));
     CK(cudaMemcpyAsync(ctx->h_counters + 2, counters + 2, 4, cudaMemcpyDeviceToHost, s));
@@ -722,8 +739,8 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
     if (radix_scratch_bytes(n_pairs) > ctx->scratch.cap) CK(ensure(ctx->scratch, radix_scratch_bytes(n_pairs)));
     CK(launch_duplicate(order, P<int4>(ctx->rects), P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
-                        n_surv, cam_dev, counters + 2, P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), s,
-                        &ctx->log));
+                        n_surv, nullptr, cam_dev, counters + 2, n_pairs, nullptr, P<uint32_t>(ctx->keys),
+                        P<uint32_t>(ctx->vals), ctx->num_sms, s, &ctx->log));
     tm.mark(NVGS_STAGE_SORT);
     int passes = 0, in_alt = 0;
     CK(radix_sort_pairs_u32(P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), P<uint32_t>(ctx->keys_alt),
@@ -731,7 +748,7 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
                             &passes, 0, &in_alt));
     uint32_t* skeys = in_alt ? P<uint32_t>(ctx->keys_alt) : P<uint32_t>(ctx->keys);
     uint32_t* svals = in_alt ? P<uint32_t>(ctx->vals_alt) : P<uint32_t>(ctx->vals);
-    CK(launch_tile_ranges(skeys, n_pairs, (uint32_t)n_tiles, P<uint32_t>(ctx->ranges), s, &ctx->log));
+    CK(launch_tile_ranges(skeys, n_pairs, nullptr, (uint32_t)n_tiles, P<uint32_t>(ctx->ranges), s, &ctx->log));
     passes += dpasses;
     const int depth_bits = 0;
 
@@ -1005,6 +1022,184 @@ extern "C" float nvgs_lr_schedule(int step, int total, float lr0, float lr1, flo
     if (step < tw) return (float)(lr0 * 0.5 * (1.0 - std::cos(M_PI * (step + 1) / tw)));
     const double u = std::min(1.0, (step - tw) / std::max(1.0, total - tw));
     return (float)(lr0 * std::pow((double)lr1 / lr0, u));
+}
+
+// ============================================================================ batched views
+// One view of a batch in device-count mode: the S1-S6 pass of do_render with every count read on
+// the device (counters) and every size a capacity, so that nothing here waits for the GPU.
+static nvgs_status enqueue_view_async(nvgs_ctx* ctx, const CamParams& cp, const CamParams* cam_dev,
+                                      const nvgs_render_flags* f, float* image, uint64_t pair_cap,
+                                      uint32_t* view_counts) {
+    cudaStream_t s = ctx->stream;
+    StageTimer tm{ctx, false};
+    uint32_t n_vis = 0, n_mlp = 0;
+    nvgs_status st = run_cull(ctx, cam_dev, f, tm, &n_vis, &n_mlp, false, true, true);
+    if (st != NVGS_OK) return st;
+    uint32_t* counters = P<uint32_t>(ctx->counters);
+    const uint64_t cap = (uint64_t)ctx->n_instanced;
+    const uint2* surv = f->use_mlp ? P<uint2>(ctx->surv) : P<uint2>(ctx->vis_list);
+    const uint32_t* n_surv_dev = f->use_mlp ? &counters[1] : &counters[0];
+    // S4
+    CK(ensure(ctx->rec, cap * 48 + 48));
+    CK(ensure(ctx->rects, cap * 16 + 16));
+    CK(ensure(ctx->tile_counts, cap * 4 + 16));
+    CK(ensure(ctx->tile_offsets, cap * 4 + 16));
+    CK(ensure(ctx->dkey, cap * 4 + 16));
+    CK(ensure(ctx->didx, cap * 4 + 16));
+    CK(ensure(ctx->dkey_alt, cap * 4 + 16));
+    CK(ensure(ctx->didx_alt, cap * 4 + 16));
+    CK(ensure(ctx->scratch, std::max({scan_scratch_bytes(ctx->n_chunks), scan_scratch_bytes(cap + 1),
+                                      radix_scratch_bytes(cap), radix_scratch_bytes(pair_cap)})));
+    CK(launch_project(surv, (uint32_t)cap, n_surv_dev, P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev),
+                      cam_dev, P<float4>(ctx->rec), P<int4>(ctx->rects), P<uint32_t>(ctx->tile_counts),
+                      P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), ctx->num_sms, s, &ctx->log));
+    // S5
+    int dpasses = 0, d_alt = 0;
+    CK(radix_sort_pairs_u32(P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), P<uint32_t>(ctx->dkey_alt),
+                            P<uint32_t>(ctx->didx_alt), cap, 32, ctx->scratch.p, s, &ctx->log, &dpasses, 0,
+                            &d_alt, n_surv_dev));
+    const uint32_t* order = d_alt ? P<uint32_t>(ctx->didx_alt) : P<uint32_t>(ctx->didx);
+    CK(launch_gather_counts(order, P<uint32_t>(ctx->tile_counts), (uint32_t)cap, n_surv_dev,
+                            P<uint32_t>(ctx->tile_offsets), ctx->num_sms, s, &ctx->log));
+    CK(exclusive_scan_u32(P<uint32_t>(ctx->tile_offsets), P<uint32_t>(ctx->tile_offsets), cap, counters + 2,
+                          ctx->scratch.p, s, &ctx->log, n_surv_dev));
+    const int n_tiles = cp.tiles_x * cp.tiles_y;
+    const int tile_bits = std::max(1, bit_width((uint64_t)n_tiles - 1));
+    CK(ensure(ctx->keys, (size_t)pair_cap * 4 + 16));
+    CK(ensure(ctx->vals, (size_t)pair_cap * 4 + 16));
+    CK(ensure(ctx->keys_alt, (size_t)pair_cap * 4 + 16));
+    CK(ensure(ctx->vals_alt, (size_t)pair_cap * 4 + 16));
+    CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
+    CK(launch_duplicate(order, P<int4>(ctx->rects), P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
+                        (uint32_t)cap, n_surv_dev, cam_dev, counters + 2, (uint32_t)pair_cap, counters + 9,
+                        P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), ctx->num_sms, s, &ctx->log));
+    int passes = 0, in_alt = 0;
+    CK(radix_sort_pairs_u32(P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), P<uint32_t>(ctx->keys_alt),
+                            P<uint32_t>(ctx->vals_alt), pair_cap, tile_bits, ctx->scratch.p, s, &ctx->log,
+                            &passes, 0, &in_alt, counters + 2));
+    uint32_t* skeys = in_alt ? P<uint32_t>(ctx->keys_alt) : P<uint32_t>(ctx->keys);
+    uint32_t* svals = in_alt ? P<uint32_t>(ctx->vals_alt) : P<uint32_t>(ctx->vals);
+    CK(launch_tile_ranges(skeys, (uint32_t)pair_cap, counters + 2, (uint32_t)n_tiles, P<uint32_t>(ctx->ranges),
+                          s, &ctx->log));
+    // S6
+    const uint64_t auto_len = std::max<uint64_t>(4096, 4 * (pair_cap / (uint64_t)n_tiles + 1));
+    const uint32_t split_len = f->blend_split_len < 0 ? 0xffffffffu
+                               : (f->blend_split_len == 0 ? (uint32_t)std::min<uint64_t>(auto_len, 0x7fffffffu)
+                                                          : (uint32_t)f->blend_split_len);
+    if (pair_cap > split_len) {
+        CK(ensure(ctx->split_scratch, blend_split_scratch_bytes(n_tiles, pair_cap, cp.tile_size, split_len)));
+        CK(ensure(ctx->scratch, scan_scratch_bytes(n_tiles)));
+    }
+    CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, cam_dev, image, nullptr, nullptr,
+                    nullptr, split_len, pair_cap, ctx->split_scratch.p, ctx->scratch.p, ctx->num_sms, s,
+                    &ctx->log));
+    // this view's counts
+    CK(cudaMemcpyAsync(view_counts, counters, 3 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    return NVGS_OK;
+}
+
+static nvgs_status enqueue_batch(nvgs_ctx* ctx, const std::vector<CamParams>& cps, float* const* images,
+                                 const nvgs_render_flags* f, uint64_t pair_cap) {
+    cudaStream_t s = ctx->stream;
+    uint32_t* counters = P<uint32_t>(ctx->counters);
+    CK(cudaMemsetAsync(&counters[8], 0, 8, s));   // MLP timeout flag, pair overflow flag
+    for (size_t v = 0; v < cps.size(); v++) {
+        nvgs_status st = enqueue_view_async(ctx, cps[v], P<CamParams>(ctx->cam_dev) + v, f, images[v], pair_cap,
+                                            P<uint32_t>(ctx->view_stats) + 4 * v);
+        if (st != NVGS_OK) return st;
+    }
+    CK(cudaMemcpyAsync(P<uint32_t>(ctx->view_stats) + 4 * cps.size(), &counters[8], 8, cudaMemcpyDeviceToDevice, s));
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_render_batch(nvgs_ctx* ctx, const nvgs_camera* cams, int n_views,
+                                         float* const* images, const nvgs_render_flags* f,
+                                         const nvgs_batch_opts* opts, nvgs_frame_stats* stats) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    nvgs_status st = validate_flags(ctx, f);
+    if (st != NVGS_OK) return st;
+    if (!cams || !images || n_views < 1 || n_views > 4096)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "need 1..4096 cameras and image pointers");
+    if (f->image_memory != NVGS_MEM_DEVICE || f->keep_outputs || f->profile)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "batched views need device images, no kept outputs, no profiling");
+    for (int v = 0; v < n_views; v++)
+        if (!images[v]) return fail(ctx, NVGS_ERR_INVALID_ARG, "image %d is NULL", v);
+    nvgs_batch_opts o{};
+    if (opts) o = *opts;
+    if (o.max_pairs < 0) return fail(ctx, NVGS_ERR_INVALID_ARG, "max_pairs must be >= 0");
+    std::vector<CamParams> cps(n_views);
+    for (int v = 0; v < n_views; v++)
+        if ((st = make_cam(ctx, &cams[v], f, &cps[v])) != NVGS_OK) return st;
+    CK(cudaSetDevice(ctx->device));
+    if ((st = check_scene(ctx)) != NVGS_OK) return st;
+    const uint64_t pair_cap = std::min<uint64_t>(o.max_pairs > 0 ? (uint64_t)o.max_pairs
+                                                                 : 8ull * (uint64_t)ctx->n_instanced,
+                                                 0xffffffffull - 16);
+    if (ctx->n_instanced >= ((int64_t)1 << 31))
+        return fail(ctx, NVGS_ERR_CAPACITY, "batched views take at most 2^31 instanced Gaussians");
+    begin_frame(ctx, false);
+    cudaStream_t s = ctx->stream;
+    CK(ensure(ctx->view_stats, (size_t)(n_views + 1) * 16));
+    // graph key: view sizes, flags, options and capacities
+    std::vector<uint8_t> key;
+    auto put = [&](const void* p, size_t n) { key.insert(key.end(), (const uint8_t*)p, (const uint8_t*)p + n); };
+    put(&n_views, sizeof n_views);
+    for (auto& c : cps) { put(&c.W, sizeof c.W); put(&c.H, sizeof c.H); }
+    put(f, sizeof *f);
+    put(&o, sizeof o);
+    put(&pair_cap, sizeof pair_cap);
+    for (int v = 0; v < n_views; v++) put(&images[v], sizeof(float*));
+    const bool replay = o.use_graph && ctx->graph_exec && key == ctx->graph_key;
+    if (replay) {
+        // the graph's first node copies the staged cameras; restage them once the last copy is done
+        if (ctx->cam_ev_pending) CK(cudaEventSynchronize(ctx->cam_ev));
+        memcpy(ctx->h_cam, cps.data(), cps.size() * sizeof(CamParams));
+        CK(cudaGraphLaunch(ctx->graph_exec, s));
+        CK(cudaEventRecord(ctx->cam_ev, s));
+        ctx->cam_ev_pending = true;
+    } else {
+        if ((st = upload_cams(ctx, cps.data(), n_views)) != NVGS_OK) return st;
+        if ((st = enqueue_batch(ctx, cps, images, f, pair_cap)) != NVGS_OK) return st;
+        if (o.use_graph) {
+            // every buffer now has its size: capture the same work (cameras copied inside)
+            CK(cudaStreamSynchronize(s));
+            if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+            ctx->graph_key.clear();
+            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            cudaError_t ce = cudaMemcpyAsync(ctx->cam_dev.p, ctx->h_cam, cps.size() * sizeof(CamParams),
+                                             cudaMemcpyHostToDevice, s);
+            nvgs_status cs = ce == cudaSuccess ? enqueue_batch(ctx, cps, images, f, pair_cap)
+                                               : fail(ctx, NVGS_ERR_CUDA, "capture: %s", cudaGetErrorString(ce));
+            cudaGraph_t g = nullptr;
+            cudaError_t ee = cudaStreamEndCapture(s, &g);
+            if (cs != NVGS_OK) { if (g) cudaGraphDestroy(g); return cs; }
+            if (ee != cudaSuccess) return fail(ctx, NVGS_ERR_CUDA, "capture: %s", cudaGetErrorString(ee));
+            cudaError_t ie = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) {
+                ctx->graph_exec = nullptr;
+                return fail(ctx, NVGS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+            }
+            ctx->graph_key = key;
+        }
+    }
+    if (!stats) return NVGS_OK;
+    std::vector<uint32_t> h((size_t)(n_views + 1) * 4);
+    CK(cudaMemcpyAsync(h.data(), ctx->view_stats.p, h.size() * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int v = 0; v < n_views; v++) {
+        memset(&stats[v], 0, sizeof stats[v]);
+        stats[v].n_instanced = (uint64_t)ctx->n_instanced;
+        stats[v].n_in_frustum = h[4 * v];
+        stats[v].n_mlp_queries = f->use_mlp ? h[4 * v] : 0;
+        stats[v].n_survivors = f->use_mlp ? h[4 * v + 1] : h[4 * v];
+        stats[v].n_pairs = h[4 * v + 2];
+    }
+    if (h[4 * n_views]) return fail(ctx, NVGS_ERR_TIMEOUT, "tensor-core MLP: a bounded mbarrier wait gave up");
+    if (h[4 * n_views + 1])
+        return fail(ctx, NVGS_ERR_CAPACITY, "a view needed more than max_pairs = %llu pairs",
+                    (unsigned long long)pair_cap);
+    return NVGS_OK;
 }
 
 // ============================================================================ gradients

@@ -275,12 +275,15 @@ cudaError_t launch_expand_chunks(const Chunk* chunks, int n_chunks, const uint32
                                  LaunchLog* log);
 
 // S2: keep bits over a list of (instance, gaussian) entries.
-cudaError_t launch_mlp_fp32(const uint2* list, uint32_t n, const FrameInst* fi,
+// Launchers taking n_dev (nullable): the count is read on the device and n is the capacity
+// (grids are sized from it; nothing waits for the count on the host).
+cudaError_t launch_mlp_fp32(const uint2* list, uint32_t n, const uint32_t* n_dev, const FrameInst* fi,
                             const AssetDev* assets, const float* logits_override,
                             const int64_t* inst_offset, float threshold, uint32_t* keep_bits,
                             float* logits_out, cudaStream_t s, LaunchLog* log);
 // err_flag (device) is set to 1 if a bounded wait on the tensor-core pipeline gave up.
-cudaError_t launch_mlp_tc(const uint2* list, const float4* list_mean, uint32_t n, const FrameInst* fi,
+cudaError_t launch_mlp_tc(const uint2* list, const float4* list_mean, uint32_t n, const uint32_t* n_dev,
+                          const FrameInst* fi,
                           const AssetDev* assets, float threshold, uint32_t* keep_bits,
                           float* logits_out, uint32_t* err_flag, int num_sms, int ctas_per_sm,
                           cudaStream_t s, LaunchLog* log);
@@ -299,10 +302,10 @@ cudaError_t launch_train_step(const AssetDev* asset_dev, uint32_t n_gauss, const
                               cudaStream_t s, LaunchLog* log);
 
 // Per-block popcounts of a bitmask over n items (blocks of kChunk items).
-cudaError_t launch_bit_counts(const uint32_t* bits, uint32_t n, uint32_t* block_counts,
-                              cudaStream_t s, LaunchLog* log);
+cudaError_t launch_bit_counts(const uint32_t* bits, uint32_t n, const uint32_t* n_dev,
+                              uint32_t* block_counts, cudaStream_t s, LaunchLog* log);
 // Stable compaction of list[i] for set bits i, using block offsets from the scan.
-cudaError_t launch_compact_list(const uint2* list, uint32_t n, const uint32_t* bits,
+cudaError_t launch_compact_list(const uint2* list, uint32_t n, const uint32_t* n_dev, const uint32_t* bits,
                                 const uint32_t* block_offsets, uint2* out, cudaStream_t s,
                                 LaunchLog* log);
 
@@ -314,21 +317,25 @@ cudaError_t launch_scatter_visibility(const uint2* list, uint32_t n, const uint3
 
 // S4: records, tile rects and counts; dkey / didx receive the depth sort keys (IEEE bits of
 // the camera-space z) and the survivor indices 0..n-1.
-cudaError_t launch_project(const uint2* surv, uint32_t n, const FrameInst* fi,
-                           const AssetDev* assets, const CamParams* cam_dev, float4* rec,
-                           int4* rects, uint32_t* tile_counts, uint32_t* dkey, uint32_t* didx,
+cudaError_t launch_project(const uint2* surv, uint32_t n, const uint32_t* n_dev, const FrameInst* fi,
+                           const AssetDev* assets, const CamParams* cam_dev, float4* rec, int4* rects,
+                           uint32_t* tile_counts, uint32_t* dkey, uint32_t* didx, int num_sms,
                            cudaStream_t s, LaunchLog* log);
 
 // S5 (k_bin.cu)
 cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* counts, uint32_t n,
-                                 uint32_t* counts_sorted, cudaStream_t s, LaunchLog* log);
+                                 const uint32_t* n_dev, uint32_t* counts_sorted, int num_sms,
+                                 cudaStream_t s, LaunchLog* log);
 // Pairs of the survivors in depth order: the tiles of each rectangle that row_tile_span keeps,
-// as the projection counted them.  n_pairs (device) bounds the writes.
+// as the projection counted them.  n_pairs (device) is the total; writes stop at pair_cap, and
+// overflow (device, nullable) is set when the total exceeds it.
 cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const float4* rec,
-                             const uint32_t* offsets, uint32_t n, const CamParams* cam_dev, const uint32_t* n_pairs,
-                             uint32_t* keys, uint32_t* values, cudaStream_t s, LaunchLog* log);
-cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, uint32_t n_tiles, uint32_t* ranges,
-                               cudaStream_t s, LaunchLog* log);
+                             const uint32_t* offsets, uint32_t n, const uint32_t* n_dev,
+                             const CamParams* cam_dev, const uint32_t* n_pairs, uint32_t pair_cap,
+                             uint32_t* overflow, uint32_t* keys, uint32_t* values, int num_sms,
+                             cudaStream_t s, LaunchLog* log);
+cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, const uint32_t* n_dev, uint32_t n_tiles,
+                               uint32_t* ranges, cudaStream_t s, LaunchLog* log);
 
 // S6
 // mark (nullable, per survivor): set to 1 when the survivor is blended at some pixel.
@@ -347,8 +354,11 @@ cudaError_t launch_mark_labels(const uint2* surv, uint32_t n_surv, const uint8_t
 // Exclusive scan of n uint32 values; total (nullable, device) receives the sum.  Needs
 // scan_scratch_bytes(n) bytes of scratch.
 size_t scan_scratch_bytes(uint64_t n);
+// With n_dev, elements at or past *n_dev read as 0 (n is then the capacity); out is written over
+// all n.
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* total,
-                               void* scratch, cudaStream_t s, LaunchLog* log);
+                               void* scratch, cudaStream_t s, LaunchLog* log,
+                               const uint32_t* n_dev = nullptr);
 
 // Stable LSD radix sort (8-bit digits) of n (key, value) pairs on bits [0, key_bits).
 // keys/values hold the input; the alt buffers must hold n entries each.  With copy_back the
@@ -360,10 +370,11 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* values,
                              int key_bits, void* scratch, cudaStream_t s, LaunchLog* log,
                              int* passes_out, int copy_back, int* result_in_alt);
 // The same sort for 32-bit keys.
+// With n_dev the element count is read on the device (n is the capacity).
 cudaError_t radix_sort_pairs_u32(uint32_t* keys, uint32_t* values, uint32_t* keys_alt,
                                  uint32_t* values_alt, uint64_t n, int key_bits, void* scratch,
                                  cudaStream_t s, LaunchLog* log, int* passes_out, int copy_back,
-                                 int* result_in_alt);
+                                 int* result_in_alt, const uint32_t* n_dev = nullptr);
 
 // N2: gradients of the render (k_backward.cu).  gsurv: render_backward_scratch_bytes(n_surv).
 size_t render_backward_scratch_bytes(uint64_t n_surv);

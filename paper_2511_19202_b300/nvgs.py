@@ -97,6 +97,10 @@ class AdamCfg(C.Structure):
                 ("step", C.c_int32)]
 
 
+class BatchOpts(C.Structure):
+    _fields_ = [("max_pairs", C.c_int64), ("use_graph", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+
 class AssetGrads(C.Structure):
     _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
                 ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
@@ -113,7 +117,7 @@ EXPORTS = ("nvgs_create", "nvgs_destroy", "nvgs_last_error", "nvgs_get_stream", 
            "nvgs_sort_pairs_noalloc", "nvgs_label_visibility", "nvgs_train_init",
            "nvgs_train_visibility_step", "nvgs_train_get_weights", "nvgs_lr_schedule",
            "nvgs_get_asset_info", "nvgs_training_views", "nvgs_render_backward",
-           "nvgs_update_asset")
+           "nvgs_update_asset", "nvgs_render_batch")
 NVGS_SORT_NOALLOC_MAX_PAIRS = 1 << 20
 
 
@@ -151,6 +155,7 @@ def _load():
     L.nvgs_get_asset_info.argtypes = [vp, C.c_int, P(AssetInfo)]
     L.nvgs_training_views.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
     L.nvgs_render_backward.argtypes = [vp, vp, C.c_int, P(AssetGrads)]
+    L.nvgs_render_batch.argtypes = [vp, vp, C.c_int, vp, P(RenderFlags), P(BatchOpts), vp]
     L.nvgs_update_asset.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("nvgs_default_flags", "nvgs_abi_version", "nvgs_last_error", "nvgs_get_stream",
@@ -393,3 +398,17 @@ def nvgs_render_backward(ctx, dL_dimage, asset_id: int, means, log_scales, quats
 def nvgs_update_asset(ctx, asset_id: int, means, log_scales, quats, opacity_logits, sh):
     _check(ctx, lib.nvgs_update_asset(ctx, int(asset_id), _ptr(means), _ptr(log_scales), _ptr(quats),
                                       _ptr(opacity_logits), _ptr(sh)))
+
+
+def nvgs_render_batch(ctx, cams, flags: RenderFlags, images, max_pairs: int = 0, use_graph: bool = False,
+                      want_stats: bool = True):
+    """Renders len(cams) views into the device images (one per camera) without host synchronisation;
+    with want_stats the call waits and returns one stats dict per view."""
+    n = len(cams)
+    arr = (Camera * n)(*[camera(c) for c in cams])
+    ptrs = (C.c_void_p * n)(*[_ptr(im) for im in images])
+    o = BatchOpts(int(max_pairs), 1 if use_graph else 0)
+    st = (FrameStats * n)() if want_stats else None
+    _check(ctx, lib.nvgs_render_batch(ctx, C.cast(arr, C.c_void_p), n, C.cast(ptrs, C.c_void_p), C.byref(flags),
+                                      C.byref(o), C.cast(st, C.c_void_p) if st is not None else None))
+    return [st[k].as_dict() for k in range(n)] if st is not None else None

@@ -72,6 +72,15 @@ class Renderer:
         st = N.nvgs_render(self.ctx, cam, flags, out)
         return out, st.as_dict()
 
+    def render_batch(self, cams, flags: N.RenderFlags | None = None, out=None, max_pairs: int = 0,
+                     use_graph: bool = False, want_stats: bool = True):
+        """Several views in one sync-free call (optionally replayed as a CUDA graph)."""
+        flags = flags or self.flags()
+        if out is None:
+            out = [torch.empty((c.height, c.width, 3), dtype=torch.float32, device=self.device) for c in cams]
+        st = N.nvgs_render_batch(self.ctx, cams, flags, out, max_pairs, use_graph, want_stats)
+        return out, st
+
     def render_host(self, cam, flags: N.RenderFlags, out: np.ndarray | torch.Tensor):
         """Render into HOST memory (the device-to-host copy happens inside the call)."""
         flags.image_memory = N.NVGS_MEM_HOST
