@@ -297,6 +297,45 @@ def run_ours(args, rank, world):
         r.render_host(frame(k), e2e_flags, host)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
 
+    # sync-free path (nvgs_render_batch): one view per call replayed as a CUDA graph with the
+    # frame's camera, and eight views per graph launch; verified equal to the synchronous render
+    max_pairs = int(2 * max(max(s["n_pairs"] for s in st_culled), max(s["n_pairs"] for s in st_plain)))
+
+    def graph_time(make_flags, views_per_call, K):
+        outs = [torch.empty((H, W, 3), dtype=torch.float32, device=f"cuda:{dev}") for _ in range(views_per_call)]
+        calls = max(1, K // views_per_call)
+        group = lambda c: [frame(c * views_per_call + j) for j in range(views_per_call)]
+        r.render_batch(group(0), make_flags(), out=outs, max_pairs=max_pairs, use_graph=True)   # capture
+        ref, _ = r.render(frame(0), make_flags())
+        same = bool(torch.equal(ref, outs[0]))
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for c in range(calls):
+            r.render_batch(group(c), make_flags(), out=outs, max_pairs=max_pairs, use_graph=True,
+                           want_stats=False)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        return g0.elapsed_time(g1) / (calls * views_per_call), same
+
+    mk_culled = lambda: r.flags(use_mlp=1, mlp_gate=1, tile_size=tile, logit_threshold=tau)
+    mk_plain = lambda: r.flags(use_mlp=0, tile_size=tile)
+    graph_culled, same_c = graph_time(mk_culled, 1, args.steps)
+    graph_plain, same_p = graph_time(mk_plain, 1, args.steps)
+    batch8_culled, same_b = graph_time(mk_culled, 8, max(8, args.steps))
+    tune_cams = [cams[f] for f in (64, 72, 80, 88)] if len(cams) >= 120 else cams[:1]
+    tune_out = [torch.empty((c.height, c.width, 3), dtype=torch.float32, device=f"cuda:{dev}") for c in tune_cams]
+    # 8-pixel tiles make about four times the pairs of 16-pixel ones
+    tuned, tune_table = N.nvgs_autotune(r.ctx, tune_cams, mk_culled(), tune_out, 4 * max_pairs)
+    graph_info = {"culled_ms_per_frame_graph": graph_culled, "unculled_ms_per_frame_graph": graph_plain,
+                  "culled_ms_per_view_batch8_graph": batch8_culled,
+                  "graph_images_equal_sync": same_c and same_p and same_b,
+                  "max_pairs": max_pairs,
+                  "autotune": {"best": {"tile_size": tuned.tile_size, "mlp_ctas_per_sm": tuned.mlp_ctas_per_sm,
+                                        "blend_split_len": tuned.blend_split_len},
+                               "candidates": tune_table}}
+
     # image quality: culled vs unculled on the first timed frames
     psnrs, culled_frac = [], []
     for k in range(min(5, args.steps)):
@@ -358,6 +397,7 @@ def run_ours(args, rank, world):
                    "mean_pairs_unculled": mean("n_pairs", st_plain),
                    "gaussians_per_s": st_culled[0]["n_instanced"] / (value * 1e-3),
                    "kernels_ms_per_frame": kernels,
+                   "sync_free": graph_info,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof,
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 76,

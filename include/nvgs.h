@@ -131,7 +131,10 @@ typedef struct {
 
 /* ------------------------------------------------------------------ context */
 /* Creates a context on CUDA device `device`; `cuda_stream` is a cudaStream_t to enqueue on,
- * or NULL for a stream the context creates and owns. */
+ * or NULL for a stream the context creates and owns.  That stream is a blocking one: it orders
+ * itself with the legacy default stream (work enqueued there before a call finishes before the
+ * call's kernels start, and work enqueued there after waits for them), which is how callers
+ * that use the default stream -- such as PyTorch by default -- see the library's results. */
 nvgs_status nvgs_create(nvgs_ctx** out, int device, void* cuda_stream);
 nvgs_status nvgs_destroy(nvgs_ctx* ctx);
 /* Text of the last error on this context ("" if none).  Owned by the context. */
@@ -281,6 +284,23 @@ typedef struct {
 nvgs_status nvgs_render_batch(nvgs_ctx* ctx, const nvgs_camera* cams, int n_views,
                               float* const* images, const nvgs_render_flags* flags,
                               const nvgs_batch_opts* opts, nvgs_frame_stats* stats);
+
+/* Autotuner: times nvgs_render_batch of the given views under every candidate configuration --
+ * tile size {8, 16, 32} x tensor-core MLP CTAs per SM {1, 2, 3} (when flags.use_mlp and every
+ * MLP is BF16) x dense-tile split {automatic, never} -- and returns the fastest flags (all other
+ * fields copied from `flags`).  Images do not depend on these choices.  Each candidate runs one
+ * untimed batch and three timed ones (CUDA events on the context's stream); the call waits.
+ * results (nullable, up to max_results entries) receives every candidate with its time per
+ * view (infinity for a candidate that needs more than max_pairs pairs -- smaller tiles make more
+ * pairs); n_results the number of candidates. */
+typedef struct {
+    int32_t tile_size, mlp_ctas_per_sm, blend_split_len;
+    float ms_per_view;
+} nvgs_tune_result;
+nvgs_status nvgs_autotune(nvgs_ctx* ctx, const nvgs_camera* cams, int n_views, float* const* images,
+                          const nvgs_render_flags* flags, const nvgs_batch_opts* opts,
+                          nvgs_render_flags* best, nvgs_tune_result* results, int max_results,
+                          int* n_results);
 
 /* ------------------------------------------------------------------ gradients of the render */
 /* Derivatives of a loss L(image) of the last rendered frame with respect to one asset's

@@ -413,7 +413,8 @@ extern "C" nvgs_status nvgs_create(nvgs_ctx** out, int device, void* cuda_stream
     if (cuda_stream) {
         ctx->stream = (cudaStream_t)cuda_stream;
     } else {
-        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        // blocking: ordered with the legacy default stream (the default stream of most callers)
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamDefault) != cudaSuccess) {
             delete ctx;
             return NVGS_ERR_CUDA;
         }
@@ -1200,6 +1201,63 @@ extern "C" nvgs_status nvgs_render_batch(nvgs_ctx* ctx, const nvgs_camera* cams,
         return fail(ctx, NVGS_ERR_CAPACITY, "a view needed more than max_pairs = %llu pairs",
                     (unsigned long long)pair_cap);
     return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_autotune(nvgs_ctx* ctx, const nvgs_camera* cams, int n_views,
+                                     float* const* images, const nvgs_render_flags* f,
+                                     const nvgs_batch_opts* opts, nvgs_render_flags* best,
+                                     nvgs_tune_result* results, int max_results, int* n_results) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (!f || !best) return fail(ctx, NVGS_ERR_INVALID_ARG, "flags / best is NULL");
+    nvgs_batch_opts o{};
+    if (opts) o = *opts;
+    o.use_graph = 0;   // plain batches: the graph cache keeps whatever the caller captured
+    const bool tc = f->use_mlp && uses_tc_mlp(ctx, f);
+    const int tiles[3] = {8, 16, 32};
+    const int splits[2] = {0, -1};
+    const int n_ctas = tc ? 3 : 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = INFINITY;
+    int count = 0;
+    nvgs_status st = NVGS_OK;
+    for (int ti = 0; ti < 3 && st == NVGS_OK; ti++)
+        for (int ci = 0; ci < n_ctas && st == NVGS_OK; ci++)
+            for (int si = 0; si < 2 && st == NVGS_OK; si++) {
+                nvgs_render_flags c = *f;
+                c.tile_size = tiles[ti];
+                c.mlp_ctas_per_sm = tc ? ci + 1 : f->mlp_ctas_per_sm;
+                c.blend_split_len = splits[si];
+                std::vector<nvgs_frame_stats> stv(n_views);
+                st = nvgs_render_batch(ctx, cams, n_views, images, &c, &o, stv.data());   // warm-up
+                if (st == NVGS_ERR_CAPACITY) {   // needs more pairs than max_pairs: not a candidate
+                    if (results && count < max_results)
+                        results[count] = nvgs_tune_result{c.tile_size, c.mlp_ctas_per_sm, c.blend_split_len, INFINITY};
+                    count++;
+                    st = NVGS_OK;
+                    continue;
+                }
+                if (st != NVGS_OK) break;
+                cudaEventRecord(e0, ctx->stream);
+                for (int rep = 0; rep < 3 && st == NVGS_OK; rep++)
+                    st = nvgs_render_batch(ctx, cams, n_views, images, &c, &o, nullptr);
+                if (st != NVGS_OK) break;
+                cudaEventRecord(e1, ctx->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= 3.0f * (float)n_views;
+                if (results && count < max_results)
+                    results[count] = nvgs_tune_result{c.tile_size, c.mlp_ctas_per_sm, c.blend_split_len, ms};
+                count++;
+                if (ms < best_ms) { best_ms = ms; *best = c; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_results) *n_results = count;
+    return st;
 }
 
 // ============================================================================ gradients

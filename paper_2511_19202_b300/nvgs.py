@@ -101,6 +101,11 @@ class BatchOpts(C.Structure):
     _fields_ = [("max_pairs", C.c_int64), ("use_graph", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("tile_size", C.c_int32), ("mlp_ctas_per_sm", C.c_int32), ("blend_split_len", C.c_int32),
+                ("ms_per_view", C.c_float)]
+
+
 class AssetGrads(C.Structure):
     _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
                 ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
@@ -117,7 +122,7 @@ EXPORTS = ("nvgs_create", "nvgs_destroy", "nvgs_last_error", "nvgs_get_stream", 
            "nvgs_sort_pairs_noalloc", "nvgs_label_visibility", "nvgs_train_init",
            "nvgs_train_visibility_step", "nvgs_train_get_weights", "nvgs_lr_schedule",
            "nvgs_get_asset_info", "nvgs_training_views", "nvgs_render_backward",
-           "nvgs_update_asset", "nvgs_render_batch")
+           "nvgs_update_asset", "nvgs_render_batch", "nvgs_autotune")
 NVGS_SORT_NOALLOC_MAX_PAIRS = 1 << 20
 
 
@@ -156,6 +161,8 @@ def _load():
     L.nvgs_training_views.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
     L.nvgs_render_backward.argtypes = [vp, vp, C.c_int, P(AssetGrads)]
     L.nvgs_render_batch.argtypes = [vp, vp, C.c_int, vp, P(RenderFlags), P(BatchOpts), vp]
+    L.nvgs_autotune.argtypes = [vp, vp, C.c_int, vp, P(RenderFlags), P(BatchOpts), P(RenderFlags), vp, C.c_int,
+                                P(C.c_int)]
     L.nvgs_update_asset.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("nvgs_default_flags", "nvgs_abi_version", "nvgs_last_error", "nvgs_get_stream",
@@ -412,3 +419,20 @@ def nvgs_render_batch(ctx, cams, flags: RenderFlags, images, max_pairs: int = 0,
     _check(ctx, lib.nvgs_render_batch(ctx, C.cast(arr, C.c_void_p), n, C.cast(ptrs, C.c_void_p), C.byref(flags),
                                       C.byref(o), C.cast(st, C.c_void_p) if st is not None else None))
     return [st[k].as_dict() for k in range(n)] if st is not None else None
+
+
+def nvgs_autotune(ctx, cams, flags: RenderFlags, images, max_pairs: int = 0):
+    """(best flags, [ {tile_size, mlp_ctas_per_sm, blend_split_len, ms_per_view} ... ])."""
+    n = len(cams)
+    arr = (Camera * n)(*[camera(c) for c in cams])
+    ptrs = (C.c_void_p * n)(*[_ptr(im) for im in images])
+    o = BatchOpts(int(max_pairs), 0)
+    best = RenderFlags()
+    res = (TuneResult * 64)()
+    cnt = C.c_int(0)
+    _check(ctx, lib.nvgs_autotune(ctx, C.cast(arr, C.c_void_p), n, C.cast(ptrs, C.c_void_p), C.byref(flags),
+                                  C.byref(o), C.byref(best), C.cast(res, C.c_void_p), 64, C.byref(cnt)))
+    table = [dict(tile_size=res[k].tile_size, mlp_ctas_per_sm=res[k].mlp_ctas_per_sm,
+                  blend_split_len=res[k].blend_split_len, ms_per_view=res[k].ms_per_view)
+             for k in range(min(cnt.value, 64))]
+    return best, table

@@ -102,3 +102,28 @@ def test_batch_rejects_unsupported_flags():
             r.render_batch(_cams()[:1], r.flags(use_mlp=0, profile=1))
     finally:
         r.close()
+
+
+def test_autotuner_times_every_candidate_and_images_do_not_depend_on_the_choice():
+    from paper_2511_19202_b300 import nvgs as N
+    sc = scenes.config1_scene(20000)
+    r = renderer_for(sc, scenes.mlp_weights(3), precision=N.NVGS_PREC_BF16)
+    try:
+        cams = _cams()[:3]
+        out = [torch.zeros((c.height, c.width, 3), device="cuda") for c in cams]
+        base = r.flags(use_mlp=1, mlp_gate=0)
+        best, table = N.nvgs_autotune(r.ctx, cams, base, out)
+        print(table)
+        assert len(table) == 3 * 3 * 2
+        assert {t["tile_size"] for t in table} == {8, 16, 32}
+        fastest = min(table, key=lambda t: t["ms_per_view"])
+        assert best.tile_size == fastest["tile_size"] and best.mlp_ctas_per_sm == fastest["mlp_ctas_per_sm"]
+        assert best.use_mlp == 1 and best.mlp_gate == 0
+        imgs = {}
+        for ts in (8, 16, 32):
+            im, _ = r.render_batch(cams, r.flags(use_mlp=1, mlp_gate=0, tile_size=ts))
+            imgs[ts] = im
+        for k in range(len(cams)):
+            assert torch.equal(imgs[8][k], imgs[16][k]) and torch.equal(imgs[16][k], imgs[32][k])
+    finally:
+        r.close()
