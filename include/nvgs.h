@@ -47,9 +47,11 @@ typedef enum {
 
 typedef enum { NVGS_MEM_HOST = 0, NVGS_MEM_DEVICE = 1 } nvgs_memory;
 
-/* Arithmetic of the visibility MLP (Sec. 3.2): FP32 on CUDA cores, or BF16 operands with FP32
- * accumulation on the tcgen05 tensor cores. */
-typedef enum { NVGS_PREC_FP32 = 0, NVGS_PREC_BF16 = 1 } nvgs_precision;
+/* Arithmetic of the visibility MLP (Sec. 3.2): FP32 on CUDA cores; BF16 operands with FP32
+ * accumulation on the tcgen05 tensor cores; or E4M3 (FP8) operands with FP32 accumulation on
+ * the tensor cores, one scale per tensor: weights max|W| / 448, inputs x 256 (|x| <= 1), hidden
+ * activations (their bound for |x| <= 1) / 448. */
+typedef enum { NVGS_PREC_FP32 = 0, NVGS_PREC_BF16 = 1, NVGS_PREC_FP8 = 2 } nvgs_precision;
 
 typedef struct nvgs_ctx nvgs_ctx;
 

@@ -1,0 +1,376 @@
+// S2, FP8 tensor-core variant: the visibility MLP (32 -> 64 -> 64 -> 64 -> 1, ReLU; NVGS Sec. 3.2,
+// queried as in Sec. 3.3) with E4M3 operands and FP32 accumulation on the tcgen05 tensor cores
+// (kind::f8f6f4, K = 32 per instruction).
+//
+// Quantisation, one scale per tensor ("amax / 448", 448 being the largest finite E4M3):
+//   inputs   q_x = E4M3(256 x)            (|x| <= 1, so 256 |x| <= 448; small features stay normal)
+//   weights  q_W = E4M3(W / s_W),          s_W = max |W| / 448 per layer
+//   hidden   q_h = E4M3(h / s_h),          s_h = (bound of |h| when |x| <= 1) / 448, the bound
+//            propagated layer by layer as max_j (sum_k |W_jk| bound_in + |b_j|)
+// so that the accumulator of layer l holds sum_k q_in q_W and the epilogue is one FMA per value:
+//   q_h = E4M3_sat(max(0, acc alpha_l + beta_j))  with alpha_l = s_in s_W / s_h, beta = b / s_h,
+// and the third layer's h3 = max(0, acc alpha_3 + b3) stays FP32 for the 64 -> 1 output on the
+// CUDA cores.  Conversions saturate (cvt .satfinite), so a value past its bound clamps to 448.
+//
+// Structure as in the BF16 kernel: one warpgroup per CTA, two 128-row tiles per step sharing each
+// MMA round trip, bounded mbarrier waits, multi-asset passes.  Operands are K-major without
+// swizzle; an 8-bit core matrix is 8 rows x 16 elements, element (row, k) of a K-column tile at
+// (row / 8) * SBO + (k / 16) * 128 + (row % 8) * 16 + (k % 16), SBO = 8 K bytes.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "mlp_common.cuh"
+#include "tc_common.cuh"
+
+namespace nvgs {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 128;
+constexpr int kCtasPerSm = 4;
+constexpr int kHalves = 2;
+constexpr int kRows = 128 * kHalves;
+constexpr int kTmemCols = 64 * kHalves;
+// blob (packed on the host): E4M3 weight tiles, then FP32 vectors
+constexpr int kOffW1 = 0;        // 64 x 32 E4M3 (SBO 256)
+constexpr int kOffW2 = 2048;     // 64 x 64 E4M3 (SBO 512)
+constexpr int kOffW3 = 6144;
+constexpr int kOffVec = 10240;   // FP32: beta1[64] beta2[64] b3[64] w4[64] b4 alpha1 alpha2 alpha3
+constexpr int kVecFloats = 260;
+constexpr int kBlobBytes = kOffVec + kVecFloats * 4;   // 11280
+constexpr int kOffH = 11520;     // kHalves x (128 x 64 E4M3); the 128 x 32 input tile overlays it
+constexpr int kHBytes = 8192;
+constexpr int kOffMisc = kOffH + kHalves * kHBytes;
+constexpr int kSmemBytes = kOffMisc + 64;
+constexpr uint32_t kSboK32 = 256;
+constexpr uint32_t kSboK64 = 512;
+constexpr uint32_t kLbo = 128;
+constexpr float kInScale = 256.0f;
+
+// kind::f8f6f4 descriptor: D = F32 (bit 4), A = B = E4M3 (format 0 at bits 7 and 10), K-major,
+// N / 8 at bit 17, M / 16 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+// (lo, hi) -> two saturated E4M3 codes, lo in the low byte (the lower address).
+__device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
+    uint16_t d;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+    return (uint32_t)d;
+}
+
+__device__ __forceinline__ void st_chunk(uint8_t* tile, uint32_t sbo, int row, int chunk, uint4 v) {
+    *reinterpret_cast<uint4*>(tile + (row >> 3) * sbo + chunk * kLbo + (row & 7) * 16) = v;
+}
+
+// 16 consecutive values -> 16 E4M3 bytes
+__device__ __forceinline__ uint4 pack16(const float* v) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        w[q] = e4m3x2(v[4 * q], v[4 * q + 1]) | (e4m3x2(v[4 * q + 2], v[4 * q + 3]) << 16);
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// hidden epilogue: q_h = E4M3_sat(max(0, acc alpha + beta)) into the next layer's A tile
+__device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, float alpha, const float* beta, uint8_t* sH,
+                                                int row) {
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+        uint32_t r[32];
+        tmem_ld32(t_lane + half * 32, r);
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            float v[16];
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                const int col = half * 32 + c * 16 + q;
+                v[q] = fmaxf(fmaf(__uint_as_float(r[c * 16 + q]), alpha, beta[col]), 0.0f);
+            }
+            st_chunk(sH, kSboK64, row, half * 2 + c, pack16(v));
+        }
+    }
+}
+
+__device__ __forceinline__ float epilogue_logit(uint32_t t_lane, float alpha, const float* b3, const float* w4,
+                                                float b4) {
+    float lg = b4;
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+        uint32_t r[32];
+        tmem_ld32(t_lane + half * 32, r);
+#pragma unroll
+        for (int k = 0; k < 32; k++) {
+            const int col = half * 32 + k;
+            lg = fmaf(w4[col], fmaxf(fmaf(__uint_as_float(r[k]), alpha, b3[col]), 0.0f), lg);
+        }
+    }
+    return lg;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
+k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, uint32_t n,
+         const uint32_t* __restrict__ n_dev, const FrameInst* __restrict__ fis,
+         const AssetDev* __restrict__ assets, float threshold, uint32_t* __restrict__ keep_bits,
+         float* __restrict__ logits_out, uint32_t* __restrict__ err_flag) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    if (n_dev) n = min(n, *n_dev);
+    const float* sVec = reinterpret_cast<const float*>(sm + kOffVec);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kOffMisc);
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + kOffMisc + 8);
+    int* s_red = reinterpret_cast<int*>(sm + kOffMisc + 16);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(s_tmem)), "r"((uint32_t)kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+    const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
+
+    uint32_t phase = 0;
+    int loaded = -1;
+    bool abort = false;
+    const uint32_t n_steps = (n + kRows - 1) / kRows;
+    for (uint32_t step = blockIdx.x; step < n_steps && !abort; step += gridDim.x) {
+        uint2 e[kHalves];
+        float4 m[kHalves];
+        int my_asset[kHalves];
+        bool pending[kHalves], keep[kHalves];
+        float logit[kHalves];
+#pragma unroll
+        for (int h = 0; h < kHalves; h++) {
+            const uint32_t i = step * kRows + h * 128 + tid;
+            e[h] = make_uint2(0, 0);
+            m[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < n) { e[h] = __ldg(&list[i]); m[h] = __ldg(&list_mean[i]); }
+            my_asset[h] = i < n ? fis[e[h].x].asset : INT_MAX;
+            pending[h] = i < n;
+            keep[h] = false;
+            logit[h] = 0.0f;
+        }
+        for (;;) {
+            int cand = min(pending[0] ? my_asset[0] : INT_MAX, pending[1] ? my_asset[1] : INT_MAX);
+            cand = __reduce_min_sync(0xffffffffu, cand);
+            if (lane == 0) s_red[warp] = cand;
+            __syncthreads();
+            const int cur = min(min(s_red[0], s_red[1]), min(s_red[2], s_red[3]));
+            __syncthreads();
+            if (cur == INT_MAX) break;
+            const AssetDev& a = assets[cur];
+            bool mine[kHalves];
+#pragma unroll
+            for (int h = 0; h < kHalves; h++) mine[h] = pending[h] && my_asset[h] == cur;
+            if (a.w_f8 == nullptr) {   // asset without an MLP: rendered unculled
+#pragma unroll
+                for (int h = 0; h < kHalves; h++)
+                    if (mine[h]) { keep[h] = true; logit[h] = __int_as_float(0x7f800000); pending[h] = false; }
+                continue;
+            }
+            if (cur != loaded) {
+                const uint4* src = reinterpret_cast<const uint4*>(a.w_f8);
+                uint4* dst = reinterpret_cast<uint4*>(sm);
+                for (int k = tid; k < kBlobBytes / 16; k += kThreads) dst[k] = __ldg(&src[k]);
+                loaded = cur;
+            }
+            // ---- inputs -> A (E4M3, scaled by 256), one row per half
+#pragma unroll
+            for (int h = 0; h < kHalves; h++) {
+                float f[32];
+                if (mine[h]) {
+                    mlp_features(a, fis[e[h].x], m[h], f);
+#pragma unroll
+                    for (int k = 0; k < 32; k++) f[k] *= kInScale;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 32; k++) f[k] = 0.0f;
+                }
+                uint8_t* sA = sm + kOffH + h * kHBytes;
+                st_chunk(sA, kSboK32, tid, 0, pack16(f));
+                st_chunk(sA, kSboK32, tid, 1, pack16(f + 16));
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+
+            bool ok = true;
+#pragma unroll 1
+            for (int layer = 0; layer < 3 && ok; layer++) {
+                if (tid == 0) {
+                    tc_fence_after();
+#pragma unroll
+                    for (int h = 0; h < kHalves; h++) {
+                        const uint8_t* sH = sm + kOffH + h * kHBytes;
+                        const uint32_t d = tmem + 64 * h;
+                        if (layer == 0) {
+                            mma_f8(d, sdesc(sH, kLbo, kSboK32), sdesc(sm + kOffW1, kLbo, kSboK32), kIdesc, 0);
+                        } else {
+                            const uint8_t* W = sm + (layer == 1 ? kOffW2 : kOffW3);
+#pragma unroll
+                            for (int k = 0; k < 2; k++)   // K = 64 in two K = 32 steps (256 bytes apart)
+                                mma_f8(d, sdesc(sH + 256 * k, kLbo, kSboK64), sdesc(W + 256 * k, kLbo, kSboK64),
+                                       kIdesc, k > 0);
+                        }
+                    }
+                    mma_commit(mbar);
+                }
+                const bool done = mbar_wait(mbar, phase);
+                if (__syncthreads_or(!done)) { ok = false; break; }
+                phase ^= 1u;
+                tc_fence_after();
+                if (layer < 2) {
+#pragma unroll
+                    for (int h = 0; h < kHalves; h++)
+                        epilogue_hidden(t_lane + 64 * h, sVec[257 + layer], sVec + 64 * layer, sm + kOffH + h * kHBytes,
+                                        tid);
+                    fence_async_smem();
+                    tc_fence_before();
+                    __syncthreads();
+                } else {
+#pragma unroll
+                    for (int h = 0; h < kHalves; h++) {
+                        const float lg = epilogue_logit(t_lane + 64 * h, sVec[259], sVec + 128, sVec + 192, sVec[256]);
+                        if (mine[h]) {
+                            logit[h] = lg;
+                            keep[h] = fis[e[h].x].gated || (lg > threshold);
+                            pending[h] = false;
+                        }
+                    }
+                    tc_fence_before();
+                }
+            }
+            if (!ok) {
+                if (tid == 0) atomicExch(err_flag, 1u);
+                abort = true;
+                break;
+            }
+        }
+        if (abort) break;
+#pragma unroll
+        for (int h = 0; h < kHalves; h++) {
+            const uint32_t row0 = step * kRows + h * 128;
+            const uint32_t w = __ballot_sync(0xffffffffu, keep[h]);
+            if (lane == 0 && row0 + warp * 32 < n) keep_bits[(row0 >> 5) + warp] = w;
+            if (logits_out && row0 + tid < n) logits_out[row0 + tid] = logit[h];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     ::"r"(tmem), "r"((uint32_t)kTmemCols) : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ host side
+size_t mlp_f8_weight_bytes() { return (size_t)kBlobBytes; }
+
+// E4M3 code of x (round to nearest even, saturating at +-448): 1 sign, 4 exponent (bias 7) and 3
+// mantissa bits, subnormals below 2^-6 with quantum 2^-9.
+static uint8_t f32_to_e4m3(float xf) {
+    const double x = xf;
+    const uint8_t sign = std::signbit(x) ? 0x80 : 0x00;
+    double a = std::fabs(x);
+    if (!(a == a)) return 0x7F;   // NaN (never produced from finite weights)
+    if (a >= 448.0) return sign | 0x7E;
+    if (a < std::ldexp(1.0, -6)) {                       // subnormal: m x 2^-9, m = 0..7
+        const double m = std::nearbyint(a / std::ldexp(1.0, -9));
+        if (m >= 8.0) return sign | 0x08;                // rounds up to the smallest normal
+        return sign | (uint8_t)m;
+    }
+    int e = (int)std::floor(std::log2(a));
+    double q = std::ldexp(1.0, e - 3);
+    double m = std::nearbyint(a / q);                     // 8 .. 16
+    if (m >= 16.0) { e += 1; m = 8.0; }
+    if (e > 8 || (e == 8 && m > 14.0)) return sign | 0x7E;
+    return sign | (uint8_t)(((e + 7) << 3) | ((int)m - 8));
+}
+
+// Packs the weights with the per-tensor scales described at the top of this file.  scales_out
+// (nullable): s_W1, s_W2, s_W3, s_h1, s_h2.
+void mlp_f8_pack_weights(const float* w, uint8_t* out, float* scales_out) {
+    memset(out, 0, kBlobBytes);
+    const float* W1 = w;
+    const float* b1 = W1 + 64 * 32;
+    const float* W2 = b1 + 64;
+    const float* b2 = W2 + 64 * 64;
+    const float* W3 = b2 + 64;
+    const float* b3 = W3 + 64 * 64;
+    const float* W4 = b3 + 64;
+    const float* b4 = W4 + 64;
+    auto amax = [](const float* p, int n) {
+        double m = 0.0;
+        for (int k = 0; k < n; k++) m = std::max(m, (double)std::fabs(p[k]));
+        return m > 0.0 ? m : 1.0;
+    };
+    // |h| bounds for |x| <= 1, layer by layer
+    auto bound = [](const float* W, const float* b, int K, double in) {
+        double m = 0.0;
+        for (int j = 0; j < 64; j++) {
+            double s = std::fabs((double)b[j]);
+            for (int k = 0; k < K; k++) s += std::fabs((double)W[j * K + k]) * in;
+            m = std::max(m, s);
+        }
+        return m > 0.0 ? m : 1.0;
+    };
+    const double sW1 = amax(W1, 64 * 32) / 448.0, sW2 = amax(W2, 64 * 64) / 448.0, sW3 = amax(W3, 64 * 64) / 448.0;
+    const double B1 = bound(W1, b1, 32, 1.0), B2 = bound(W2, b2, 64, B1);
+    const double sh1 = B1 / 448.0, sh2 = B2 / 448.0;
+    auto put = [&](int off, int K, const float* Wm, double sW) {
+        const int sbo = 8 * K;
+        for (int nrow = 0; nrow < 64; nrow++)
+            for (int k = 0; k < K; k++)
+                out[off + (nrow / 8) * sbo + (k / 16) * 128 + (nrow % 8) * 16 + (k % 16)] =
+                    f32_to_e4m3((float)(Wm[nrow * K + k] / sW));
+    };
+    put(kOffW1, 32, W1, sW1);
+    put(kOffW2, 64, W2, sW2);
+    put(kOffW3, 64, W3, sW3);
+    float* vec = reinterpret_cast<float*>(out + kOffVec);
+    for (int k = 0; k < 64; k++) {
+        vec[k] = (float)(b1[k] / sh1);
+        vec[64 + k] = (float)(b2[k] / sh2);
+        vec[128 + k] = b3[k];
+        vec[192 + k] = W4[k];
+    }
+    vec[256] = b4[0];
+    vec[257] = (float)((1.0 / kInScale) * sW1 / sh1);
+    vec[258] = (float)(sh1 * sW2 / sh2);
+    vec[259] = (float)(sh2 * sW3);
+    if (scales_out) {
+        scales_out[0] = (float)sW1; scales_out[1] = (float)sW2; scales_out[2] = (float)sW3;
+        scales_out[3] = (float)sh1; scales_out[4] = (float)sh2;
+    }
+}
+
+cudaError_t launch_mlp_f8(const uint2* list, const float4* list_mean, uint32_t n, const uint32_t* n_dev,
+                          const FrameInst* fi, const AssetDev* assets, float threshold, uint32_t* keep_bits,
+                          float* logits_out, uint32_t* err_flag, int num_sms, cudaStream_t s, LaunchLog* log) {
+    if (n == 0) return cudaSuccess;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_f8, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const uint32_t steps = (n + kRows - 1) / kRows;
+    const uint32_t grid = std::min<uint32_t>(steps, (uint32_t)num_sms * kCtasPerSm);
+    NVGS_LAUNCH(log, s, "k_mlp_f8", k_mlp_f8<<<grid, kThreads, kSmemBytes, s>>>(list, list_mean, n, n_dev, fi, assets, threshold, keep_bits, logits_out, err_flag));
+    return cudaGetLastError();
+}
+
+}  // namespace nvgs

@@ -31,10 +31,13 @@
 #include <cstring>
 
 #include "mlp_common.cuh"
+#include "tc_common.cuh"
 
 namespace nvgs {
 
 namespace {
+
+using namespace tc;
 
 constexpr int kThreads = 128;
 constexpr int kCtasPerSm = 3;
@@ -63,97 +66,12 @@ constexpr uint32_t kSboK16 = 256;    // 16 * 16
 constexpr uint32_t kSboK32 = 512;    // 16 * 32
 constexpr uint32_t kSboK64 = 1024;   // 16 * 64
 constexpr uint32_t kLbo = 128;
-constexpr uint32_t kWaitIters = 1u << 20;   // x ~1 us suspend hint: about a second at most
 
 // kind::f16 instruction descriptors: D = F32 (bit 4), A = B = BF16 (bits 7, 10), both K-major,
 // N / 8 at bit 17, M / 16 at bit 24.
 constexpr uint32_t idesc(uint32_t n) { return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24); }
 constexpr uint32_t kIdescN64 = idesc(64);
 constexpr uint32_t kIdescN16 = idesc(16);
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// tcgen05 shared-memory matrix descriptor, no swizzle.
-__device__ __forceinline__ uint64_t sdesc(const void* p, uint32_t lbo, uint32_t sbo) {
-    const uint32_t a = smem_u32(p);
-    return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
-           ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
-        : "memory");
-    return ok != 0;
-}
-
-// Lane 0 of each warp polls (bounded); the rest of the warp waits at __syncwarp.  The warp's
-// verdict is broadcast so that a timeout is seen by every thread.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok = 0;
-    if ((threadIdx.x & 31) == 0) {
-        for (uint32_t it = 0; it < kWaitIters; ++it)
-            if (mbar_try_wait(bar, parity)) { ok = 1; break; }
-    }
-    return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc_,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc_), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 ::"r"(smem_u32(bar)) : "memory");
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane.  The load and its wait sit in one asm
-// statement so that no use of the registers can be scheduled before the data has arrived.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-}
-
-// The first two FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t* r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1])
-        : "r"(taddr)
-        : "memory");
-}
 
 // (lo, hi) -> BF16x2 with ReLU, lo in the low half (the lower address).
 __device__ __forceinline__ uint32_t bf16x2_relu(float lo, float hi) {
@@ -195,8 +113,8 @@ __device__ __forceinline__ void issue_layer(uint32_t d, const uint8_t* sA, uint3
                                             const uint8_t* sOnes, uint32_t idesc_) {
 #pragma unroll 4
     for (int k = 0; k < k_steps; k++)
-        mma_bf16(d, sdesc(sA + 256 * k, kLbo, sbo_a), sdesc(sW + 256 * k, kLbo, sbo_w), idesc_, k > 0);
-    mma_bf16(d, sdesc(sOnes, kLbo, kSboK16), sdesc(sBias, kLbo, kSboK16), idesc_, 1);
+        mma_f16(d, sdesc(sA + 256 * k, kLbo, sbo_a), sdesc(sW + 256 * k, kLbo, sbo_w), idesc_, k > 0);
+    mma_f16(d, sdesc(sOnes, kLbo, kSboK16), sdesc(sBias, kLbo, kSboK16), idesc_, 1);
 }
 
 }  // namespace

@@ -23,7 +23,7 @@ struct DevBuf {
 };
 
 struct AssetStore {
-    DevBuf mean_op, scale, quat, sh, w_fp32, w_tc;
+    DevBuf mean_op, scale, quat, sh, w_fp32, w_tc, w_f8;
     AssetDev dev{};
     int precision = -1;  // -1: no MLP
 };
@@ -207,17 +207,21 @@ struct StageTimer {
     }
 };
 
-// BF16 tensor-core MLP only when every asset with an MLP has BF16 tiles and no logits are
-// injected.
-bool uses_tc_mlp(const nvgs_ctx* ctx, const nvgs_render_flags* f) {
-    bool tc = f->logits_override == nullptr;
-    bool any_mlp = false;
+// Tensor-core MLP kernel of the frame: BF16 (FP8) when every asset with an MLP has BF16 (FP8)
+// tiles and no logits are injected; otherwise -1 (the FP32 CUDA-core kernel).
+int tc_mlp_precision(const nvgs_ctx* ctx, const nvgs_render_flags* f) {
+    if (f->logits_override) return -1;
+    int prec = -1;
     for (auto& a : ctx->assets) {
-        tc = tc && (a.precision == NVGS_PREC_BF16 || a.precision < 0);
-        any_mlp = any_mlp || a.precision >= 0;
+        if (a.precision < 0) continue;
+        if (a.precision == NVGS_PREC_FP32) return -1;
+        if (prec >= 0 && prec != a.precision) return -1;
+        prec = a.precision;
     }
-    return tc && any_mlp;
+    return prec;
 }
+
+bool uses_tc_mlp(const nvgs_ctx* ctx, const nvgs_render_flags* f) { return tc_mlp_precision(ctx, f) >= 0; }
 
 // S1 (+ S2 when use_mlp, + S3): fills ctx->vis_list / surv and the counts (counters[0] = in
 // frustum, counters[1] = survivors).  `query` keeps the per-entry logits for
@@ -272,11 +276,17 @@ nvgs_status run_cull(nvgs_ctx* ctx, const CamParams* cam_dev, const nvgs_render_
     if (want_logits) CK(ensure(ctx->logits_tmp, (size_t)cap * 4 + 16));
     if (tc_mlp) {
         if (!async) CK(cudaMemsetAsync(&counters[8], 0, 4, s));
-        CK(launch_mlp_tc(P<uint2>(ctx->vis_list), P<float4>(ctx->vis_mean), n_vis_cap, n_vis_dev,
-                         P<FrameInst>(ctx->frame_inst),
-                         P<AssetDev>(ctx->assets_dev), f->logit_threshold, P<uint32_t>(ctx->keep_bits),
-                         want_logits ? P<float>(ctx->logits_tmp) : nullptr, &counters[8],
-                         ctx->num_sms, f->mlp_ctas_per_sm, s, &ctx->log));
+        if (tc_mlp_precision(ctx, f) == NVGS_PREC_FP8)
+            CK(launch_mlp_f8(P<uint2>(ctx->vis_list), P<float4>(ctx->vis_mean), n_vis_cap, n_vis_dev,
+                             P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev), f->logit_threshold,
+                             P<uint32_t>(ctx->keep_bits), want_logits ? P<float>(ctx->logits_tmp) : nullptr,
+                             &counters[8], ctx->num_sms, s, &ctx->log));
+        else
+            CK(launch_mlp_tc(P<uint2>(ctx->vis_list), P<float4>(ctx->vis_mean), n_vis_cap, n_vis_dev,
+                             P<FrameInst>(ctx->frame_inst),
+                             P<AssetDev>(ctx->assets_dev), f->logit_threshold, P<uint32_t>(ctx->keep_bits),
+                             want_logits ? P<float>(ctx->logits_tmp) : nullptr, &counters[8],
+                             ctx->num_sms, f->mlp_ctas_per_sm, s, &ctx->log));
         if (!async) {
             CK(cudaMemcpyAsync(ctx->h_counters + 8, &counters[8], 4, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
@@ -435,7 +445,7 @@ extern "C" nvgs_status nvgs_destroy(nvgs_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto& a : ctx->assets) {
         release(a.mean_op); release(a.scale); release(a.quat); release(a.sh);
-        release(a.w_fp32); release(a.w_tc);
+        release(a.w_fp32); release(a.w_tc); release(a.w_f8);
     }
     DevBuf* bufs[] = {&ctx->assets_dev, &ctx->inst_raw, &ctx->inst_offset, &ctx->chunks,
                       &ctx->frame_inst, &ctx->bits, &ctx->chunk_counts, &ctx->chunk_offsets,
@@ -517,7 +527,7 @@ extern "C" nvgs_status nvgs_load_asset(nvgs_ctx* ctx, const nvgs_asset_desc* d, 
     AssetDev& a = as.dev;
     a.mean_op = P<float4>(as.mean_op); a.scale = P<float4>(as.scale); a.quat = P<float4>(as.quat);
     a.sh = P<float>(as.sh);
-    a.w_fp32 = nullptr; a.w_tc = nullptr;
+    a.w_fp32 = nullptr; a.w_tc = nullptr; a.w_f8 = nullptr;
     a.n = n; a.sh_degree = d->sh_degree; a.sh_stride = stride;
     double dd = 0.0;
     for (int k = 0; k < 3; k++) {
@@ -550,8 +560,8 @@ extern "C" nvgs_status nvgs_set_mlp(nvgs_ctx* ctx, int asset_id, const float* w,
     if (asset_id < 0 || asset_id >= (int)ctx->assets.size())
         return fail(ctx, NVGS_ERR_INVALID_ARG, "asset_id %d out of range", asset_id);
     if (!w) return fail(ctx, NVGS_ERR_INVALID_ARG, "weights is NULL");
-    if (precision != NVGS_PREC_FP32 && precision != NVGS_PREC_BF16)
-        return fail(ctx, NVGS_ERR_INVALID_ARG, "precision must be NVGS_PREC_FP32 or NVGS_PREC_BF16");
+    if (precision != NVGS_PREC_FP32 && precision != NVGS_PREC_BF16 && precision != NVGS_PREC_FP8)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "precision must be NVGS_PREC_FP32, _BF16 or _FP8");
     for (int k = 0; k < kMlpWeights; k++)
         if (!std::isfinite(w[k])) return fail(ctx, NVGS_ERR_INVALID_ARG, "non-finite weight %d", k);
     CK(cudaSetDevice(ctx->device));
@@ -568,6 +578,14 @@ extern "C" nvgs_status nvgs_set_mlp(nvgs_ctx* ctx, int asset_id, const float* w,
         CK(cudaMemcpy(as.w_tc.p, packed.data(), nb, cudaMemcpyHostToDevice));
         as.dev.w_tc = P<uint8_t>(as.w_tc);
         as.precision = NVGS_PREC_BF16;
+    } else if (precision == NVGS_PREC_FP8) {
+        const size_t nb = mlp_f8_weight_bytes();
+        std::vector<uint8_t> packed(nb);
+        mlp_f8_pack_weights(w, packed.data(), nullptr);
+        CK(ensure(as.w_f8, nb));
+        CK(cudaMemcpy(as.w_f8.p, packed.data(), nb, cudaMemcpyHostToDevice));
+        as.dev.w_f8 = P<uint8_t>(as.w_f8);
+        as.precision = NVGS_PREC_FP8;
     }
     ctx->assets_dirty = true;
     return NVGS_OK;

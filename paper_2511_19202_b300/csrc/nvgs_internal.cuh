@@ -22,6 +22,7 @@ struct AssetDev {
     const float* sh;          // n * sh_stride floats, coefficient-major, RGB innermost
     const float* w_fp32;      // visibility MLP, kMlpWeights floats (nullptr: no MLP)
     const uint8_t* w_tc;      // BF16 operand tiles for the tcgen05 MLP (nullptr: none)
+    const uint8_t* w_f8;      // E4M3 operand tiles + FP32 scales for the FP8 tcgen05 MLP (nullptr: none)
     int64_t n;
     int sh_degree;
     int sh_stride;            // floats per Gaussian, multiple of 4
@@ -281,6 +282,13 @@ cudaError_t launch_mlp_fp32(const uint2* list, uint32_t n, const uint32_t* n_dev
                             const AssetDev* assets, const float* logits_override,
                             const int64_t* inst_offset, float threshold, uint32_t* keep_bits,
                             float* logits_out, cudaStream_t s, LaunchLog* log);
+// FP8 (E4M3) variant; weights packed by mlp_f8_pack_weights (scales_out nullable: the five
+// per-tensor scales s_W1, s_W2, s_W3, s_h1, s_h2).
+size_t mlp_f8_weight_bytes();
+void mlp_f8_pack_weights(const float* w, uint8_t* out, float* scales_out);
+cudaError_t launch_mlp_f8(const uint2* list, const float4* list_mean, uint32_t n, const uint32_t* n_dev,
+                          const FrameInst* fi, const AssetDev* assets, float threshold, uint32_t* keep_bits,
+                          float* logits_out, uint32_t* err_flag, int num_sms, cudaStream_t s, LaunchLog* log);
 // err_flag (device) is set to 1 if a bounded wait on the tensor-core pipeline gave up.
 cudaError_t launch_mlp_tc(const uint2* list, const float4* list_mean, uint32_t n, const uint32_t* n_dev,
                           const FrameInst* fi,

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libnvgs.so")
 NVGS_OK, NVGS_ERR_INVALID_ARG, NVGS_ERR_OOM, NVGS_ERR_CUDA = 0, 1, 2, 3
 NVGS_ERR_TIMEOUT, NVGS_ERR_CAPACITY, NVGS_ERR_UNSUPPORTED = 4, 5, 6
 NVGS_MEM_HOST, NVGS_MEM_DEVICE = 0, 1
-NVGS_PREC_FP32, NVGS_PREC_BF16 = 0, 1
+NVGS_PREC_FP32, NVGS_PREC_BF16, NVGS_PREC_FP8 = 0, 1, 2
 NVGS_NUM_STAGES = 8
 STAGE_NAMES = ("setup", "cull", "mlp", "compact", "project", "bin", "sort", "blend")
 MLP_WEIGHTS = 10497
