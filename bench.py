@@ -41,7 +41,10 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", choices=["composed", "small"], default="composed")
+    p.add_argument("--config", choices=["composed", "small", "large"], default="composed",
+                   help="composed: 16 x 500k assets, 64 instances, 1080p (the headline workload); "
+                        "small: one 20k torus at 256^2; large: 8 x 1M assets, 200 instances "
+                        "(200M instanced Gaussians) at 3840x2160")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--mlp", choices=["trained", "random"], default="trained",
                    help="trained: per-asset GPU labels + Adam (Sec. 3.1-3.2) before timing")
@@ -50,7 +53,7 @@ def parse():
     p.add_argument("--train-res", type=int, default=512)
     p.add_argument("--psnr-target", type=float, default=48.0,
                    help="calibration target (dB) for the logit threshold on held-out orbit frames")
-    p.add_argument("--precision", choices=["bf16", "fp32"], default="bf16",
+    p.add_argument("--precision", choices=["bf16", "fp32", "fp8"], default="bf16",
                    help="visibility-MLP arithmetic: BF16 tensor cores (tcgen05) or FP32 CUDA cores")
     return p.parse_args()
 
@@ -63,6 +66,11 @@ def workload(config):
         cams = [scenes.config2_camera(f) for f in range(120)]
         desc = ("composed scene: 16 assets x 500k Gaussians (sphere/torus/box), 64 instances, "
                 "SH degree 3, 1920x1080, 16x16 tiles, 120-frame orbit")
+    elif config == "large":
+        sc = scenes.config5_scene()
+        cams = [scenes.config5_camera(f) for f in range(120)]
+        desc = ("large composed scene: 8 assets x 1M Gaussians (sphere/torus/box), 200 instances "
+                "(200M instanced Gaussians), SH degree 3, 3840x2160, 16x16 tiles, 120-frame orbit")
     else:
         sc = scenes.config1_scene()
         cams = [scenes.config1_camera()]
@@ -198,7 +206,7 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     sc, cams, weights, desc = workload(args.config)
     r = Renderer(dev)
-    prec = N.NVGS_PREC_BF16 if args.precision == "bf16" else N.NVGS_PREC_FP32
+    prec = {"bf16": N.NVGS_PREC_BF16, "fp32": N.NVGS_PREC_FP32, "fp8": N.NVGS_PREC_FP8}[args.precision]
     train_info = None
     if args.mlp == "trained":
         from paper_2511_19202_b300.train import train_visibility
@@ -299,7 +307,7 @@ def run_ours(args, rank, world):
 
     # sync-free path (nvgs_render_batch): one view per call replayed as a CUDA graph with the
     # frame's camera, and eight views per graph launch; verified equal to the synchronous render
-    max_pairs = int(2 * max(max(s["n_pairs"] for s in st_culled), max(s["n_pairs"] for s in st_plain)))
+    max_pairs = int(1.25 * max(max(s["n_pairs"] for s in st_culled), max(s["n_pairs"] for s in st_plain)))
 
     def graph_time(make_flags, views_per_call, K):
         outs = [torch.empty((H, W, 3), dtype=torch.float32, device=f"cuda:{dev}") for _ in range(views_per_call)]
@@ -323,18 +331,21 @@ def run_ours(args, rank, world):
     mk_plain = lambda: r.flags(use_mlp=0, tile_size=tile)
     graph_culled, same_c = graph_time(mk_culled, 1, args.steps)
     graph_plain, same_p = graph_time(mk_plain, 1, args.steps)
-    batch8_culled, same_b = graph_time(mk_culled, 8, max(8, args.steps))
-    tune_cams = [cams[f] for f in (64, 72, 80, 88)] if len(cams) >= 120 else cams[:1]
-    tune_out = [torch.empty((c.height, c.width, 3), dtype=torch.float32, device=f"cuda:{dev}") for c in tune_cams]
-    # 8-pixel tiles make about four times the pairs of 16-pixel ones
-    tuned, tune_table = N.nvgs_autotune(r.ctx, tune_cams, mk_culled(), tune_out, 4 * max_pairs)
     graph_info = {"culled_ms_per_frame_graph": graph_culled, "unculled_ms_per_frame_graph": graph_plain,
-                  "culled_ms_per_view_batch8_graph": batch8_culled,
-                  "graph_images_equal_sync": same_c and same_p and same_b,
-                  "max_pairs": max_pairs,
-                  "autotune": {"best": {"tile_size": tuned.tile_size, "mlp_ctas_per_sm": tuned.mlp_ctas_per_sm,
-                                        "blend_split_len": tuned.blend_split_len},
-                               "candidates": tune_table}}
+                  "graph_images_equal_sync": same_c and same_p, "max_pairs": max_pairs}
+    if args.config != "large":   # eight 4K views or 8-pixel tiles would need tens of GB more pairs
+        batch8_culled, same_b = graph_time(mk_culled, 8, max(8, args.steps))
+        tune_cams = [cams[f] for f in (64, 72, 80, 88)] if len(cams) >= 120 else cams[:1]
+        tune_out = [torch.empty((c.height, c.width, 3), dtype=torch.float32, device=f"cuda:{dev}")
+                    for c in tune_cams]
+        # 8-pixel tiles make about four times the pairs of 16-pixel ones
+        tuned, tune_table = N.nvgs_autotune(r.ctx, tune_cams, mk_culled(), tune_out, 4 * max_pairs)
+        graph_info.update({"culled_ms_per_view_batch8_graph": batch8_culled,
+                           "graph_images_equal_sync": same_c and same_p and same_b,
+                           "autotune": {"best": {"tile_size": tuned.tile_size,
+                                                 "mlp_ctas_per_sm": tuned.mlp_ctas_per_sm,
+                                                 "blend_split_len": tuned.blend_split_len},
+                                        "candidates": tune_table}})
 
     # image quality: culled vs unculled on the first timed frames
     psnrs, culled_frac = [], []
@@ -379,9 +390,10 @@ def run_ours(args, rank, world):
         "config": {"workload": desc,
                    "mlp": (("trained per asset on GPU labels, " if args.mlp == "trained"
                             else "random-init N(0,1/fan_in) weights, ") +
-                           ("BF16 tcgen05 tensor cores, FP32 accumulate" if args.precision == "bf16"
-                            else "FP32 CUDA cores")),
-                   "l2": "no flush: the assets (1.9 GB) and per-frame buffers exceed the 126 MB L2",
+                           {"bf16": "BF16 tcgen05 tensor cores, FP32 accumulate",
+                            "fp8": "FP8 E4M3 tcgen05 tensor cores (per-tensor amax/448 scales), FP32 accumulate",
+                            "fp32": "FP32 CUDA cores"}[args.precision]),
+                   "l2": "no flush: the assets (1.9 GB or more) and per-frame buffers exceed the 126 MB L2",
                    "mlp_training": train_info,
                    "logit_threshold": tau,
                    "threshold_calibration_min_psnr_db": calib,
@@ -398,6 +410,7 @@ def run_ours(args, rank, world):
                    "gaussians_per_s": st_culled[0]["n_instanced"] / (value * 1e-3),
                    "kernels_ms_per_frame": kernels,
                    "sync_free": graph_info,
+                   "library_device_bytes": N.nvgs_device_bytes(r.ctx),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof,
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 76,

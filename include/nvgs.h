@@ -335,6 +335,9 @@ nvgs_status nvgs_update_asset(nvgs_ctx* ctx, int asset_id, const float* means,
                               const float* log_scales, const float* quats,
                               const float* opacity_logits, const float* sh);
 
+/* Device memory the context holds (assets, MLP tiles, per-frame and training buffers), bytes. */
+nvgs_status nvgs_device_bytes(const nvgs_ctx* ctx, uint64_t* bytes);
+
 /* ------------------------------------------------------------------ internals of the last frame */
 /* Device pointers into the library's buffers after the last nvgs_render (valid until the next
  * call on this context).  For tests and debugging: the survivor list (S3), projected records

@@ -1278,6 +1278,26 @@ extern "C" nvgs_status nvgs_autotune(nvgs_ctx* ctx, const nvgs_camera* cams, int
     return st;
 }
 
+extern "C" nvgs_status nvgs_device_bytes(const nvgs_ctx* ctx, uint64_t* bytes) {
+    if (!ctx || !bytes) return NVGS_ERR_INVALID_ARG;
+    uint64_t t = 0;
+    for (auto& a : ctx->assets)
+        for (const DevBuf* b : {&a.mean_op, &a.scale, &a.quat, &a.sh, &a.w_fp32, &a.w_tc, &a.w_f8}) t += b->cap;
+    const DevBuf* bufs[] = {&ctx->assets_dev, &ctx->inst_raw, &ctx->inst_offset, &ctx->chunks,
+                            &ctx->frame_inst, &ctx->bits, &ctx->chunk_counts, &ctx->chunk_offsets,
+                            &ctx->vis_list, &ctx->keep_bits, &ctx->logits_tmp, &ctx->block_counts,
+                            &ctx->block_offsets, &ctx->surv, &ctx->rec, &ctx->rects, &ctx->tile_counts,
+                            &ctx->tile_offsets, &ctx->keys, &ctx->vals, &ctx->keys_alt, &ctx->vals_alt,
+                            &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
+                            &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial,
+                            &ctx->dkey, &ctx->didx, &ctx->dkey_alt, &ctx->didx_alt, &ctx->split_scratch,
+                            &ctx->vis_mean, &ctx->grad_surv, &ctx->cam_dev, &ctx->view_stats};
+    for (const DevBuf* b : bufs) t += b->cap;
+    for (auto& tr : ctx->train) t += tr.w.cap + tr.m.cap + tr.v.cap + tr.views.cap;
+    *bytes = t;
+    return NVGS_OK;
+}
+
 // ============================================================================ gradients
 extern "C" nvgs_status nvgs_render_backward(nvgs_ctx* ctx, const float* dL_dimage, int asset_id,
                                             const nvgs_asset_grads* g) {

@@ -122,7 +122,7 @@ EXPORTS = ("nvgs_create", "nvgs_destroy", "nvgs_last_error", "nvgs_get_stream", 
            "nvgs_sort_pairs_noalloc", "nvgs_label_visibility", "nvgs_train_init",
            "nvgs_train_visibility_step", "nvgs_train_get_weights", "nvgs_lr_schedule",
            "nvgs_get_asset_info", "nvgs_training_views", "nvgs_render_backward",
-           "nvgs_update_asset", "nvgs_render_batch", "nvgs_autotune")
+           "nvgs_update_asset", "nvgs_render_batch", "nvgs_autotune", "nvgs_device_bytes")
 NVGS_SORT_NOALLOC_MAX_PAIRS = 1 << 20
 
 
@@ -160,6 +160,7 @@ def _load():
     L.nvgs_get_asset_info.argtypes = [vp, C.c_int, P(AssetInfo)]
     L.nvgs_training_views.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
     L.nvgs_render_backward.argtypes = [vp, vp, C.c_int, P(AssetGrads)]
+    L.nvgs_device_bytes.argtypes = [vp, P(C.c_uint64)]
     L.nvgs_render_batch.argtypes = [vp, vp, C.c_int, vp, P(RenderFlags), P(BatchOpts), vp]
     L.nvgs_autotune.argtypes = [vp, vp, C.c_int, vp, P(RenderFlags), P(BatchOpts), P(RenderFlags), vp, C.c_int,
                                 P(C.c_int)]
@@ -436,3 +437,9 @@ def nvgs_autotune(ctx, cams, flags: RenderFlags, images, max_pairs: int = 0):
                   blend_split_len=res[k].blend_split_len, ms_per_view=res[k].ms_per_view)
              for k in range(min(cnt.value, 64))]
     return best, table
+
+
+def nvgs_device_bytes(ctx) -> int:
+    b = C.c_uint64(0)
+    _check(ctx, lib.nvgs_device_bytes(ctx, C.byref(b)))
+    return int(b.value)

@@ -22,6 +22,8 @@ from .synth import (  # noqa: F401
     config2_scene,
     config2_camera,
     config2_orbit,
+    config5_scene,
+    config5_camera,
     tiny_scene,
     fibonacci_directions,
 )

@@ -268,6 +268,29 @@ def config2_camera(frame: int = 0, width: int = 1920, height: int = 1080,
     return look_at_camera(eye, (0.0, 0.0, 0.0), width, height, 50.0)
 
 
+def config5_scene(n_assets: int = 8, n_per_asset: int = 1_000_000, n_instances: int = 200,
+                  sh_degree: int = 3) -> Scene:
+    """Large composed scene: ``n_assets`` assets of ``n_per_asset`` Gaussians (sphere / torus / box
+    in turn), ``n_instances`` rigid instances (random rotation, scale U[0.5, 2]) on a 36 x 36
+    ground plane (seed 13): 200M instanced Gaussians by default."""
+    assets = [random_asset(k, n_per_asset, sh_degree) for k in range(n_assets)]
+    rng = np.random.default_rng(13)
+    inst = []
+    for i in range(n_instances):
+        a = int(rng.integers(0, n_assets))
+        R = _random_rotation(rng)
+        s = rng.uniform(0.5, 2.0)
+        xz = rng.uniform(-18.0, 18.0, 2)
+        t = np.array([xz[0], s * 1.0, xz[1]])
+        inst.append(Instance(a, R.astype(np.float32), t.astype(np.float32), float(np.float32(s))))
+    return Scene(assets, inst)
+
+
+def config5_camera(frame: int = 0, width: int = 3840, height: int = 2160, n_frames: int = 120) -> Camera:
+    eye = config2_orbit(n_frames, radius=26.0, height=6.0, seed=17)[frame % n_frames]
+    return look_at_camera(eye, (0.0, 0.0, 0.0), width, height, 50.0)
+
+
 def tiny_scene(n: int, seed: int, spread: float = 0.6, depth: float = 3.0, sh_degree: int = 0,
                log_scale_mean: float = -2.5, n_instances: int = 1) -> Scene:
     """A handful of Gaussians in front of the default camera (for brute-force checks)."""
