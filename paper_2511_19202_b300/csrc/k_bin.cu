@@ -35,11 +35,21 @@ cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* counts, 
 }
 
 // One warp per 32 consecutive survivors (depth order).  Their pairs form one contiguous run of
-// the output starting at the first survivor's offset, so the warp walks the concatenation of the
-// 32 tile rectangles 32 candidates at a time: each lane finds its candidate's survivor by a
-// binary search over the lanes' rectangle prefix sums, tests the tile (as the projection counted
-// it), and the passing candidates are written at the running offset plus their rank in the
-// ballot -- balanced over the warp whatever the rectangle sizes, and coalesced.
+// the output starting at the first survivor's offset.  The warp walks (survivor, tile row) units
+// 32 at a time: each lane finds its unit's survivor by a binary search over the lanes' row
+// prefix sums and computes the row's kept tile span once (as the projection counted it); a
+// second walk over the batch's pairs writes them, each lane finding its unit by a binary search
+// over the span prefix -- balanced whatever the rectangle sizes, and coalesced.
+__device__ __forceinline__ int warp_owner(uint32_t pre, uint32_t c) {
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t pj = __shfl_sync(0xffffffffu, pre, j + step);
+        if (pj <= c) j += step;
+    }
+    return j;
+}
+
 __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ order,
                                                    const int4* __restrict__ rects,
                                                    const float4* __restrict__ rec,
@@ -57,42 +67,70 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
     if (n_pairs_all > pair_cap && blockIdx.x == 0 && threadIdx.x == 0 && overflow) *overflow = 1u;
     const uint32_t n_warps = (blockDim.x * gridDim.x) >> 5;
     for (uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp * 32u < n; warp += n_warps) {
-        const uint32_t base = warp * 32u;
-        const uint32_t k = base + lane;
-        uint32_t i = 0;
-        SplatTiles st{};
-        st.w = 1;
+        const uint32_t k = warp * 32u + lane;
+        // this lane's survivor
+        uint32_t i = 0, rows = 0;
+        int4 r = make_int4(0, 0, -1, -1);
+        float u = 0.f, v = 0.f, A = 0.f, B = 0.f, C = 0.f, det = 0.f, kk = 0.f;
+        bool test = false;
         if (k < n) {
             i = order[k];
-            const int4 r = rects[i];
+            r = rects[i];
             if (r.x <= r.z && r.y <= r.w) {
-                st.w = (uint32_t)(r.z - r.x + 1);
-                st.area = st.w * (uint32_t)(r.w - r.y + 1);
-                st.rx = r.x; st.ry = r.y;
-                st.test = st.area > 1u;
-                if (st.test) {
+                rows = (uint32_t)(r.w - r.y + 1);
+                test = (r.z - r.x + 1) * (int)rows > 1;
+                if (test) {
                     const float4 a = rec[3 * (size_t)i];
                     const float4 b = rec[3 * (size_t)i + 1];
-                    st.u = a.x; st.v = a.y; st.A = a.z; st.B = a.w; st.C = b.x; st.kk = -2.0f * b.w;
-                    st.det = rec[3 * (size_t)i + 2].w;
+                    u = a.x; v = a.y; A = a.z; B = a.w; C = b.x; kk = -2.0f * b.w;
+                    det = rec[3 * (size_t)i + 2].w;
                 }
             }
         }
-        const uint32_t total = warp_prefix(st.area, st.pre);
+        uint32_t row_pre;
+        const uint32_t n_units = warp_prefix(rows, row_pre);
         uint32_t out = __shfl_sync(0xffffffffu, k < n ? offsets[k] : 0u, 0);
-        for (uint32_t c0 = 0; c0 < total; c0 += 32) {
-            int j, tx = 0, ty = 0;
-            const bool pass = warp_tile_candidate(st, c0 + lane, total, cam, j, tx, ty);
-            const uint32_t ij = __shfl_sync(0xffffffffu, i, j);
-            const uint32_t bal = __ballot_sync(0xffffffffu, pass);
-            if (pass) {
-                const uint32_t pos = out + __popc(bal & ((1u << lane) - 1u));
-                if (pos < limit) {
-                    keys[pos] = (uint32_t)(ty * cam.tiles_x + tx);
-                    values[pos] = ij;
+        for (uint32_t c0 = 0; c0 < n_units; c0 += 32) {
+            // ---- unit (survivor j, tile row ty): its kept span [t0, t1]
+            const uint32_t c = c0 + lane;
+            const int j = warp_owner(row_pre, c);
+            const uint32_t pj = __shfl_sync(0xffffffffu, row_pre, j);
+            const int rx = __shfl_sync(0xffffffffu, r.x, j), rz = __shfl_sync(0xffffffffu, r.z, j);
+            const int ry = __shfl_sync(0xffffffffu, r.y, j);
+            const float uj = __shfl_sync(0xffffffffu, u, j), vj = __shfl_sync(0xffffffffu, v, j);
+            const float Aj = __shfl_sync(0xffffffffu, A, j), Bj = __shfl_sync(0xffffffffu, B, j);
+            const float Cj = __shfl_sync(0xffffffffu, C, j), dj = __shfl_sync(0xffffffffu, det, j);
+            const float kj = __shfl_sync(0xffffffffu, kk, j);
+            const bool tj = __shfl_sync(0xffffffffu, (int)test, j) != 0;
+            int ty = 0, t0 = 1, t1 = 0;
+            if (c < n_units) {
+                ty = ry + (int)(c - pj);
+                if (tj) {
+                    row_tile_span(splat_ellipse(uj, vj, Aj, Bj, Cj, dj, kj), ty, cam.tile_size, t0, t1);
+                    t0 = max(t0, rx);
+                    t1 = min(t1, rz);
+                } else {
+                    t0 = rx; t1 = rz;
                 }
             }
-            out += __popc(bal);
+            const uint32_t cnt = t0 <= t1 ? (uint32_t)(t1 - t0 + 1) : 0u;
+            uint32_t cnt_pre;
+            const uint32_t batch = warp_prefix(cnt, cnt_pre);
+            const uint32_t ij = __shfl_sync(0xffffffffu, i, j);
+            // ---- the batch's pairs, 32 at a time
+            for (uint32_t p0 = 0; p0 < batch; p0 += 32) {
+                const uint32_t p = p0 + lane;
+                const int q = warp_owner(cnt_pre, p);
+                const uint32_t pq = __shfl_sync(0xffffffffu, cnt_pre, q);
+                const int tq0 = __shfl_sync(0xffffffffu, t0, q), tyq = __shfl_sync(0xffffffffu, ty, q);
+                const uint32_t iq = __shfl_sync(0xffffffffu, ij, q);
+                const uint32_t pos = out + p;
+                if (p < batch && pos < limit) {
+                    keys[pos] = (uint32_t)(tyq * cam.tiles_x + tq0 + (int)(p - pq));
+                    values[pos] = iq;
+                }
+            }
+            out += batch;
         }
     }
 }

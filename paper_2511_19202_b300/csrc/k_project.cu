@@ -17,7 +17,7 @@
 
 namespace nvgs {
 
-__global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv, uint32_t n,
+__global__ void __launch_bounds__(256, 4) k_project(const uint2* __restrict__ surv, uint32_t n,
                                                  const uint32_t* __restrict__ n_dev,
                                                  const FrameInst* __restrict__ fis,
                                                  const AssetDev* __restrict__ assets, const CamParams* __restrict__ camp,
@@ -108,36 +108,32 @@ __global__ void __launch_bounds__(256) k_project(const uint2* __restrict__ surv,
         counts[i] = cnt;
         dkey[i] = __float_as_uint(z);   // z > z_near > 0: the bit pattern orders like the value
         didx[i] = i;
+        rec[3 * (size_t)i] = make_float4(u, v, cA, cB);
+        // w: ln(alpha_min / opacity), the exponent below which a fragment cannot reach alpha_min
+        rec[3 * (size_t)i + 1] = make_float4(cC, op, z, kw);
 
-        // colour at the local-frame direction from the camera to the mean
+        // colour at the local-frame direction from the camera to the mean; the coefficients are
+        // streamed 16 bytes at a time (coefficient j / 3, channel j % 3 of float j)
         float dx = m.x - fi.cam_local[0], dy = m.y - fi.cam_local[1], dz = m.z - fi.cam_local[2];
         const float dn = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         dx *= dn; dy *= dn; dz *= dn;
         float Y[16];
         sh_eval(a.sh_degree, dx, dy, dz, Y);
-        const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
+        const int n_floats = 3 * (a.sh_degree + 1) * (a.sh_degree + 1);
         const float4* __restrict__ shp = reinterpret_cast<const float4*>(a.sh + (size_t)g * a.sh_stride);
         float col[3] = {0.5f, 0.5f, 0.5f};
-        float buf[48];
-        const int nv = (3 * K + 3) / 4;
 #pragma unroll
-        for (int k = 0; k < 12; k++) {
-            if (k < nv) {
-                float4 t = __ldg(&shp[k]);
-                buf[4 * k] = t.x; buf[4 * k + 1] = t.y; buf[4 * k + 2] = t.z; buf[4 * k + 3] = t.w;
+        for (int q = 0; q < 12; q++) {
+            if (4 * q < n_floats) {
+                const float4 t = __ldg(&shp[q]);
+                const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int j = 4 * q + e;
+                    if (j < n_floats) col[j % 3] = fmaf(Y[j / 3], tv[e], col[j % 3]);
+                }
             }
         }
-#pragma unroll
-        for (int k = 0; k < 16; k++) {
-            if (k < K) {
-                col[0] = fmaf(Y[k], buf[3 * k], col[0]);
-                col[1] = fmaf(Y[k], buf[3 * k + 1], col[1]);
-                col[2] = fmaf(Y[k], buf[3 * k + 2], col[2]);
-            }
-        }
-        rec[3 * (size_t)i] = make_float4(u, v, cA, cB);
-        // w: ln(alpha_min / opacity), the exponent below which a fragment cannot reach alpha_min
-        rec[3 * (size_t)i + 1] = make_float4(cC, op, z, kw);
         // w: det Sigma_2D (the binning's row spans recover Sigma_2D from it and the conic)
         rec[3 * (size_t)i + 2] = make_float4(fmaxf(col[0], 0.0f), fmaxf(col[1], 0.0f),
                                              fmaxf(col[2], 0.0f), det);
@@ -149,8 +145,8 @@ cudaError_t launch_project(const uint2* surv, uint32_t n, const uint32_t* n_dev,
                            uint32_t* tile_counts, uint32_t* dkey, uint32_t* didx, int num_sms,
                            cudaStream_t s, LaunchLog* log) {
     if (n == 0) return cudaSuccess;
-    // grid-stride: at most 3 resident CTAs per SM at this kernel's register count
-    const uint32_t grid = std::min<uint32_t>((n + 255) / 256, (uint32_t)num_sms * 3 * 4);
+    // grid-stride over two waves of the four resident CTAs per SM
+    const uint32_t grid = std::min<uint32_t>((n + 255) / 256, (uint32_t)num_sms * 4 * 2);
     NVGS_LAUNCH(log, s, "k_project", k_project<<<grid, 256, 0, s>>>(surv, n, n_dev, fi, assets, cam_dev, rec, rects, tile_counts, dkey, didx));
     return cudaGetLastError();
 }

@@ -163,44 +163,7 @@ __device__ __forceinline__ void row_tile_span(const SplatEllipse& e, int ty, int
     t0 = (int)ceilf(__fdiv_rn(__fadd_rn(xl, 0.5f - (float)ts), (float)ts));
 }
 
-// One splat's view of the warp-cooperative walk over the concatenated tile rectangles of the
-// warp's 32 splats (the duplication writes the kept tiles of every rectangle).
-struct SplatTiles {
-    uint32_t pre, area, w;   // exclusive prefix of the areas, rect area and width
-    int rx, ry;
-    float u, v, A, B, C, det, kk;
-    bool test;               // rect of more than one tile: pruned row by row
-};
-
-// Candidate c (< total) of the walk: the lane's owning splat j (the last lane whose prefix is
-// <= c), its tile and whether that tile is kept.  Every lane of the warp must call this.
-__device__ __forceinline__ bool warp_tile_candidate(const SplatTiles& s, uint32_t c, uint32_t total,
-                                                    const CamParams& cam, int& j, int& tx, int& ty) {
-    j = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t pj = __shfl_sync(0xffffffffu, s.pre, j + step);
-        if (pj <= c) j += step;
-    }
-    const uint32_t pj = __shfl_sync(0xffffffffu, s.pre, j);
-    const uint32_t wj = __shfl_sync(0xffffffffu, s.w, j);
-    const int rx = __shfl_sync(0xffffffffu, s.rx, j), ry = __shfl_sync(0xffffffffu, s.ry, j);
-    const float uj = __shfl_sync(0xffffffffu, s.u, j), vj = __shfl_sync(0xffffffffu, s.v, j);
-    const float Aj = __shfl_sync(0xffffffffu, s.A, j), Bj = __shfl_sync(0xffffffffu, s.B, j);
-    const float Cj = __shfl_sync(0xffffffffu, s.C, j), dj = __shfl_sync(0xffffffffu, s.det, j);
-    const float kj = __shfl_sync(0xffffffffu, s.kk, j);
-    const bool tj = __shfl_sync(0xffffffffu, (int)s.test, j) != 0;
-    if (c >= total) return false;
-    const uint32_t t = c - pj;
-    tx = rx + (int)(t % wj);
-    ty = ry + (int)(t / wj);
-    if (!tj) return true;
-    int t0, t1;
-    row_tile_span(splat_ellipse(uj, vj, Aj, Bj, Cj, dj, kj), ty, cam.tile_size, t0, t1);
-    return tx >= t0 && tx <= t1;
-}
-
-// Exclusive warp prefix of the areas; returns the warp total.
+// Exclusive warp prefix of one value per lane; returns the warp total.
 __device__ __forceinline__ uint32_t warp_prefix(uint32_t area, uint32_t& pre) {
     const int lane = threadIdx.x & 31;
     uint32_t p = area;
