@@ -158,8 +158,8 @@ constexpr int kRsWarps = kRsThreads / 32;       // 16
 template <typename K>
 constexpr int rs_smem_bytes() { return kRsWarps * 256 * 4 + kRsTile * (int)sizeof(K) + kRsTile * 4 + 2 * 256 * 4; }
 
-// Persistent over tiles: tiles at or past the (device-side) element count write zero counts, so
-// the digit-major layout always spans n_tiles (the capacity's tile count).
+// One CTA per tile; tiles at or past the (device-side) element count write zero counts, so the
+// digit-major layout always spans n_tiles (the capacity's tile count).
 template <typename K>
 __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ keys, uint64_t n,
                                                         const uint32_t* __restrict__ n_dev, int shift,
@@ -167,27 +167,25 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ ke
     __shared__ uint32_t h[kRsWarps][256];
     if (n_dev) n = min(n, (uint64_t)*n_dev);
     const int warp = threadIdx.x >> 5;
-    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const uint64_t base = (uint64_t)tile * kRsTile;
-        if (base >= n) {
-            if (threadIdx.x < 256) hist[(uint64_t)threadIdx.x * n_tiles + tile] = 0u;
-            continue;
-        }
-        for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) (&h[0][0])[k] = 0u;
-        __syncthreads();
+    const uint32_t tile = blockIdx.x;
+    const uint64_t base = (uint64_t)tile * kRsTile;
+    if (base >= n) {
+        if (threadIdx.x < 256) hist[(uint64_t)threadIdx.x * n_tiles + tile] = 0u;
+        return;
+    }
+    for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) (&h[0][0])[k] = 0u;
+    __syncthreads();
 #pragma unroll 4
-        for (int j = 0; j < kRsItems; j++) {
-            const uint64_t i = base + (uint64_t)j * kRsThreads + threadIdx.x;
-            if (i < n) atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & 255u], 1u);
-        }
-        __syncthreads();
-        if (threadIdx.x < 256) {
-            uint32_t sum = 0;
+    for (int j = 0; j < kRsItems; j++) {
+        const uint64_t i = base + (uint64_t)j * kRsThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+        uint32_t sum = 0;
 #pragma unroll
-            for (int w = 0; w < kRsWarps; w++) sum += h[w][threadIdx.x];
-            hist[(uint64_t)threadIdx.x * n_tiles + tile] = sum;
-        }
-        __syncthreads();
+        for (int w = 0; w < kRsWarps; w++) sum += h[w][threadIdx.x];
+        hist[(uint64_t)threadIdx.x * n_tiles + tile] = sum;
     }
 }
 
@@ -207,88 +205,86 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 2 : 1) k_rs_scatt
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     if (n_dev) n = min(n, (uint64_t)*n_dev);
-    const uint32_t tiles_used = (uint32_t)((n + kRsTile - 1) / kRsTile);
-    for (uint32_t tile = blockIdx.x; tile < tiles_used; tile += gridDim.x) {
-        for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) cnt[k] = 0u;
-        __syncthreads();
+    const uint32_t tile = blockIdx.x;   // one CTA per tile; CTAs past the device-side count exit
+    if ((uint64_t)tile * kRsTile >= n) return;
+    for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) cnt[k] = 0u;
+    __syncthreads();
 
-        const uint64_t base = (uint64_t)tile * kRsTile;
-        const uint64_t tile_n64 = n - base < (uint64_t)kRsTile ? n - base : (uint64_t)kRsTile;
-        const int tile_n = (int)tile_n64;
-        K key[kRsItems];
-        uint32_t pk[kRsItems];   // digit << 16 | rank among the warp's earlier items of that digit
-        // each warp ranks its own contiguous slice [warp*512, warp*512 + 512) in order
+    const uint64_t base = (uint64_t)tile * kRsTile;
+    const uint64_t tile_n64 = n - base < (uint64_t)kRsTile ? n - base : (uint64_t)kRsTile;
+    const int tile_n = (int)tile_n64;
+    K key[kRsItems];
+    uint32_t pk[kRsItems];   // digit << 16 | rank among the warp's earlier items of that digit
+    // each warp ranks its own contiguous slice [warp*512, warp*512 + 512) in order
 #pragma unroll
-        for (int r = 0; r < kRsItems; r++) {
-            const int p = warp * (kRsItems * 32) + r * 32 + lane;
-            key[r] = p < tile_n ? keys_in[base + p] : (K)0;
+    for (int r = 0; r < kRsItems; r++) {
+        const int p = warp * (kRsItems * 32) + r * 32 + lane;
+        key[r] = p < tile_n ? keys_in[base + p] : (K)0;
+    }
+#pragma unroll
+    for (int r = 0; r < kRsItems; r++) {
+        const int p = warp * (kRsItems * 32) + r * 32 + lane;
+        const bool ok = p < tile_n;
+        const uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u + lane;  // unmatched
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = ok ? cnt[warp * 256 + d] : 0u;
+        __syncwarp();
+        if (ok && (peers & lt) == 0u) cnt[warp * 256 + d] = before + __popc(peers);
+        __syncwarp();
+        pk[r] = (d << 16) | (before + __popc(peers & lt));
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, then over digits (tile-local bucket starts)
+    if (threadIdx.x < 256) {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kRsWarps; w++) {
+            const uint32_t c = cnt[w * 256 + d];
+            cnt[w * 256 + d] = run;
+            run += c;
         }
+        d_local[d] = run;   // digit total for now
+        d_global[d] = hist_scan[(uint64_t)d * n_tiles + tile];
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of the 256 digit totals by one warp
+        uint32_t v[8], s = 0;
 #pragma unroll
-        for (int r = 0; r < kRsItems; r++) {
-            const int p = warp * (kRsItems * 32) + r * 32 + lane;
-            const bool ok = p < tile_n;
-            const uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u + lane;  // unmatched
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t before = ok ? cnt[warp * 256 + d] : 0u;
-            __syncwarp();
-            if (ok && (peers & lt) == 0u) cnt[warp * 256 + d] = before + __popc(peers);
-            __syncwarp();
-            pk[r] = (d << 16) | (before + __popc(peers & lt));
+        for (int k = 0; k < 8; k++) { v[k] = d_local[lane * 8 + k]; s += v[k]; }
+        uint32_t x = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
         }
-        __syncthreads();
-        // per digit: exclusive prefix over warps, then over digits (tile-local bucket starts)
-        if (threadIdx.x < 256) {
-            const int d = threadIdx.x;
-            uint32_t run = 0;
+        uint32_t run = x - s;
 #pragma unroll
-            for (int w = 0; w < kRsWarps; w++) {
-                const uint32_t c = cnt[w * 256 + d];
-                cnt[w * 256 + d] = run;
-                run += c;
-            }
-            d_local[d] = run;   // digit total for now
-            d_global[d] = hist_scan[(uint64_t)d * n_tiles + tile];
+        for (int k = 0; k < 8; k++) { d_local[lane * 8 + k] = run; run += v[k]; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRsItems; r++) {
+        const int p = warp * (kRsItems * 32) + r * 32 + lane;
+        if (p < tile_n) {
+            const uint32_t d = pk[r] >> 16;
+            const uint32_t lp = d_local[d] + cnt[warp * 256 + d] + (pk[r] & 0xffffu);
+            s_keys[lp] = key[r];
+            s_vals[lp] = vals_in[base + p];
         }
-        __syncthreads();
-        if (threadIdx.x < 32) {  // exclusive scan of the 256 digit totals by one warp
-            uint32_t v[8], s = 0;
-#pragma unroll
-            for (int k = 0; k < 8; k++) { v[k] = d_local[lane * 8 + k]; s += v[k]; }
-            uint32_t x = s;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += t;
-            }
-            uint32_t run = x - s;
-#pragma unroll
-            for (int k = 0; k < 8; k++) { d_local[lane * 8 + k] = run; run += v[k]; }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kRsItems; r++) {
-            const int p = warp * (kRsItems * 32) + r * 32 + lane;
-            if (p < tile_n) {
-                const uint32_t d = pk[r] >> 16;
-                const uint32_t lp = d_local[d] + cnt[warp * 256 + d] + (pk[r] & 0xffffu);
-                s_keys[lp] = key[r];
-                s_vals[lp] = vals_in[base + p];
-            }
-        }
-        __syncthreads();
-        // the tile is now sorted by digit in shared memory; stream it out in order
+    }
+    __syncthreads();
+    // the tile is now sorted by digit in shared memory; stream it out in order
 #pragma unroll 4
-        for (int j = 0; j < kRsItems; j++) {
-            const int p = j * kRsThreads + threadIdx.x;
-            if (p < tile_n) {
-                const K k = s_keys[p];
-                const uint32_t d = (uint32_t)(k >> shift) & 255u;
-                const uint64_t g = (uint64_t)d_global[d] + (uint32_t)(p - d_local[d]);
-                keys_out[g] = k;
-                vals_out[g] = s_vals[p];
-            }
+    for (int j = 0; j < kRsItems; j++) {
+        const int p = j * kRsThreads + threadIdx.x;
+        if (p < tile_n) {
+            const K k = s_keys[p];
+            const uint32_t d = (uint32_t)(k >> shift) & 255u;
+            const uint64_t g = (uint64_t)d_global[d] + (uint32_t)(p - d_local[d]);
+            keys_out[g] = k;
+            vals_out[g] = s_vals[p];
         }
-        __syncthreads();   // shared memory is reused by the next tile
     }
 }
 
@@ -296,17 +292,6 @@ size_t radix_scratch_bytes(uint64_t n) {
     const uint64_t tiles = (n + kRsTile - 1) / kRsTile;
     const uint64_t h = (256 * tiles * 4 + 255) / 256 * 256;
     return (size_t)(2 * h + scan_scratch_bytes(256 * tiles));
-}
-
-static int device_sms() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-            sms = 148;
-    }
-    return sms;
 }
 
 // n is the element count, or with n_dev the capacity (the count then lives on the device and
@@ -340,9 +325,10 @@ static cudaError_t radix_sort_impl(K* keys, uint32_t* values, K* keys_alt, uint3
     uint32_t* vout = values_alt;
     const char* hname = sizeof(K) == 8 ? "k_rs_hist<u64>" : "k_rs_hist<u32>";
     const char* sname = sizeof(K) == 8 ? "k_rs_scatter<u64>" : "k_rs_scatter<u32>";
-    // persistent grids: the tile loops cover the rest
-    const unsigned hgrid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)device_sms() * 4);
-    const unsigned sgrid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)device_sms() * (sizeof(K) == 4 ? 2 : 1));
+    // one CTA per tile; with a device-side count the CTAs past it exit at once (the histogram
+    // ones after writing zero counts)
+    const unsigned hgrid = (unsigned)tiles;
+    const unsigned sgrid = (unsigned)tiles;
     for (int p = 0; p < passes; p++) {
         const int shift = 8 * p;
         NVGS_LAUNCH(log, s, hname, k_rs_hist<K><<<hgrid, kRsThreads, 0, s>>>(kin, n, n_dev, shift, (uint32_t)tiles, hist));
