@@ -196,7 +196,9 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
         // rows of different assets (at instance boundaries) are evaluated in separate passes,
         // each with that asset's weights
         for (;;) {
-            int cand = min(pending[0] ? my_asset[0] : INT_MAX, pending[1] ? my_asset[1] : INT_MAX);
+            int cand = INT_MAX;
+#pragma unroll
+            for (int h = 0; h < kHalves; h++) cand = min(cand, pending[h] ? my_asset[h] : INT_MAX);
             cand = __reduce_min_sync(0xffffffffu, cand);
             if (lane == 0) s_red[warp] = cand;
             __syncthreads();

@@ -6,7 +6,7 @@
 namespace nvgs {
 namespace tc {
 
-constexpr uint32_t kWaitIters = 1u << 20;   // x ~1 us suspend hint: about a second at most
+constexpr uint32_t kWaitIters = 1u << 26;   // polls of an mbarrier before giving up (also <= 1 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -27,21 +27,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+        : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
 }
 
-// Lane 0 of each warp polls (bounded); the rest of the warp waits at __syncwarp.  The warp's
-// verdict is broadcast so that a timeout is seen by every thread.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Lane 0 of each warp polls (bounded by an iteration count and by one second of the global
+// timer, whichever comes first); the rest of the warp waits at the shuffle.  The warp's verdict is
+// broadcast so that a timeout is seen by every thread.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok = 0;
     if ((threadIdx.x & 31) == 0) {
-        for (uint32_t it = 0; it < kWaitIters; ++it)
+        const uint64_t t0 = global_ns();
+        for (uint32_t it = 0; it < kWaitIters; ++it) {
             if (mbar_try_wait(bar, parity)) { ok = 1; break; }
+            if ((it & 255u) == 255u && global_ns() - t0 > 1000000000ull) break;
+        }
     }
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
