@@ -36,7 +36,17 @@ struct Frag {
     float T, C0, C1, C2;
     uint32_t last;   // global index + 1 of the last pair blended at the pixel (0: none)
     bool done;
+    uint32_t evals = 0;   // (pixel, fragment) evaluations -- the compositing's unit of work
 };
+
+// Adds the block's evaluations to *out (profiling only; nullable).
+__device__ __forceinline__ void add_evals(unsigned long long* out, uint32_t evals) {
+    if (!out) return;
+    unsigned long long v = evals;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
 
 template <int TS>
 __device__ __forceinline__ void stage(const uint32_t* __restrict__ values, const float4* __restrict__ rec,
@@ -57,6 +67,7 @@ __device__ __forceinline__ void blend_batch(const float4* s_a, const float4* s_b
                                             const uint32_t* __restrict__ values, uint32_t base,
                                             uint8_t* __restrict__ mark) {
     for (int j = 0; j < nb && !f.done; j++) {
+        f.evals++;
         const float4 a = s_a[j];
         const float dx = fx - a.x, dy = fy - a.y;
         const float4 b = s_b[j];
@@ -109,7 +120,8 @@ __global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ r
                                                   uint8_t* __restrict__ mark, uint32_t split_len,
                                                   float4* __restrict__ state_tc,
                                                   int32_t* __restrict__ state_cnt,
-                                                  uint32_t* __restrict__ alive) {
+                                                  uint32_t* __restrict__ alive,
+                                                  unsigned long long* __restrict__ evals_out) {
     const CamParams cam = *camp;
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
@@ -124,6 +136,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ r
     Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, !inside};
     walk<TS, false>(values, rec, start, longer ? start + split_len : end, (float)px + 0.5f,
                     (float)py + 0.5f, cam, f, mark, s_a, s_b, s_c);
+    add_evals(evals_out, f.evals);
     if (longer) {
         const bool all_done = __syncthreads_count(f.done) == B;
         if (threadIdx.x == 0) alive[tile] = all_done ? 0u : 1u;
@@ -175,7 +188,8 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __rest
                                                           const uint32_t* __restrict__ n_items,
                                                           uint32_t split_len,
                                                           const float4* __restrict__ state_tc,
-                                                          float* __restrict__ Tch) {
+                                                          float* __restrict__ Tch,
+                                                          unsigned long long* __restrict__ evals_out) {
     const CamParams cam = *camp;
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
@@ -195,6 +209,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __rest
         __syncthreads();   // the previous item's last batch is fully consumed
         walk<TS, true>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, nullptr, s_a, s_b, s_c);
         Tch[(size_t)item * B + threadIdx.x] = f.T;
+        add_evals(evals_out, f.evals);
     }
 }
 
@@ -208,7 +223,8 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
                                                           const float4* __restrict__ state_tc,
                                                           const float* __restrict__ Tch,
                                                           float4* __restrict__ part, int32_t* __restrict__ pcount,
-                                                          uint8_t* __restrict__ mark) {
+                                                          uint8_t* __restrict__ mark,
+                                                          unsigned long long* __restrict__ evals_out) {
     const CamParams cam = *camp;
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
@@ -233,6 +249,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
         // w < 0 marks "stopped inside this chunk or before"
         part[(size_t)item * B + threadIdx.x] = make_float4(f.C0, f.C1, f.C2, (f.done || dead) ? -f.T - 1.0f : f.T);
         pcount[(size_t)item * B + threadIdx.x] = (int32_t)f.last;
+        add_evals(evals_out, f.evals);
     }
 }
 
@@ -291,7 +308,8 @@ template <int TS>
 static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, const float4* rec,
                             const CamParams& cam, const CamParams* cam_dev, float* image, float* final_T,
                             int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
-                            void* scratch, void* scan_scratch, int num_sms, cudaStream_t s, LaunchLog* log) {
+                            void* scratch, void* scan_scratch, int num_sms, unsigned long long* evals,
+                            cudaStream_t s, LaunchLog* log) {
     constexpr int B = TS * TS;
     const int n_tiles = cam.tiles_x * cam.tiles_y;
     const bool may_split = n_pairs > split_len;
@@ -325,7 +343,7 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
     }
     NVGS_LAUNCH(log, s, TS == 8 ? "k_blend<8>" : TS == 16 ? "k_blend<16>" : "k_blend<32>",
                 k_blend<TS><<<n_tiles, B, 0, s>>>(ranges, values, rec, cam_dev, image, final_T, n_contrib, mark,
-                                                  split_len, state_tc, state_cnt, alive));
+                                                  split_len, state_tc, state_cnt, alive, evals));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !may_split) return e;
     NVGS_LAUNCH(log, s, "k_split_count", k_split_count<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, alive, n_tiles, split_len, n_chunks));
@@ -334,8 +352,8 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
     NVGS_LAUNCH(log, s, "k_split_fill", k_split_fill<<<(n_tiles + 255) / 256, 256, 0, s>>>(n_chunks, first, n_tiles, items));
     // persistent grids: enough CTAs to fill the GPU (the item count lives on the device)
     const unsigned pgrid = (unsigned)std::min<uint64_t>(max_items, (uint64_t)num_sms * (2048 / B));
-    NVGS_LAUNCH(log, s, "k_blend_split_T", k_blend_split_T<TS><<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, state_tc, Tch));
-    NVGS_LAUNCH(log, s, "k_blend_split_C", k_blend_split_C<TS><<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, state_tc, Tch, part, pcount, mark));
+    NVGS_LAUNCH(log, s, "k_blend_split_T", k_blend_split_T<TS><<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, state_tc, Tch, evals));
+    NVGS_LAUNCH(log, s, "k_blend_split_C", k_blend_split_C<TS><<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, state_tc, Tch, part, pcount, mark, evals));
     NVGS_LAUNCH(log, s, "k_blend_split_D", k_blend_split_D<TS><<<n_tiles, B, 0, s>>>(n_chunks, first, cam_dev, state_tc, state_cnt, part, pcount, image, final_T, n_contrib));
     return cudaGetLastError();
 }
@@ -343,13 +361,14 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
 cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const float4* rec,
                          const CamParams& cam, const CamParams* cam_dev, float* image, float* final_T,
                          int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
-                         void* scratch, void* scan_scratch, int num_sms, cudaStream_t s, LaunchLog* log) {
+                         void* scratch, void* scan_scratch, int num_sms, unsigned long long* evals,
+                         cudaStream_t s, LaunchLog* log) {
     const int n_tiles = cam.tiles_x * cam.tiles_y;
     if (n_tiles <= 0) return cudaSuccess;
     switch (cam.tile_size) {
-        case 8: return blend_ts<8>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, num_sms, s, log);
-        case 16: return blend_ts<16>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, num_sms, s, log);
-        case 32: return blend_ts<32>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, num_sms, s, log);
+        case 8: return blend_ts<8>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, num_sms, evals, s, log);
+        case 16: return blend_ts<16>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, num_sms, evals, s, log);
+        case 32: return blend_ts<32>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, num_sms, evals, s, log);
         default: return cudaErrorInvalidValue;
     }
 }

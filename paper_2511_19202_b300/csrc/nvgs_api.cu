@@ -804,8 +804,12 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
         CK(ensure(ctx->split_scratch, blend_split_scratch_bytes(n_tiles, n_pairs, cp.tile_size, split_len)));
         CK(ensure(ctx->scratch, scan_scratch_bytes(n_tiles)));
     }
+    unsigned long long* evals = f->profile ? reinterpret_cast<unsigned long long*>(counters + 10) : nullptr;
+    if (evals) CK(cudaMemsetAsync(evals, 0, 8, s));
     CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, cam_dev, img_dev, fT, nc, mark,
-                    split_len, n_pairs, ctx->split_scratch.p, ctx->scratch.p, ctx->num_sms, s, &ctx->log));
+                    split_len, n_pairs, ctx->split_scratch.p, ctx->scratch.p, ctx->num_sms, evals, s,
+                    &ctx->log));
+    if (evals) CK(cudaMemcpyAsync(ctx->h_counters + 10, counters + 10, 8, cudaMemcpyDeviceToHost, s));
     if (labels_row) CK(launch_mark_labels(surv, n_surv, mark, labels_row, s, &ctx->log));
     tm.mark(NVGS_NUM_STAGES);
     if (f->image_memory == NVGS_MEM_HOST)
@@ -838,6 +842,9 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
         stats->sort_passes = (uint32_t)passes;
         stats->kernel_launches = ctx->log.count;
         if (f->profile) {
+            uint64_t ev = 0;
+            memcpy(&ev, ctx->h_counters + 10, 8);
+            stats->blend_evaluations = ev;
             for (int k = 0; k < NVGS_NUM_STAGES; k++) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, ctx->ev[k], ctx->ev[k + 1]);
@@ -1110,7 +1117,7 @@ static nvgs_status enqueue_view_async(nvgs_ctx* ctx, const CamParams& cp, const 
         CK(ensure(ctx->scratch, scan_scratch_bytes(n_tiles)));
     }
     CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, cam_dev, image, nullptr, nullptr,
-                    nullptr, split_len, pair_cap, ctx->split_scratch.p, ctx->scratch.p, ctx->num_sms, s,
+                    nullptr, split_len, pair_cap, ctx->split_scratch.p, ctx->scratch.p, ctx->num_sms, nullptr, s,
                     &ctx->log));
     // this view's counts
     CK(cudaMemcpyAsync(view_counts, counters, 3 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
