@@ -81,9 +81,11 @@ __global__ void __launch_bounds__(TS* TS) k_blend_bwd(const uint32_t* __restrict
                 const float4 a = s_a[j];
                 const float4 b = s_b[j];
                 const float dx = fx - a.x, dy = fy - a.y;
-                const float power = splat_power(a, b, dx, dy);
-                if (!(power > 0.0f || power < b.w - 1e-4f)) {   // the forward's pre-test
-                    const float G = __expf(power);
+                float4 sa, sb;
+                stage_splat(a, b, sa, sb);   // the forward's exponent, bit for bit
+                const float p2 = splat_exponent2(sa, sb, dx, dy);
+                if (!(p2 > 0.0f || p2 < sb.z)) {   // the forward's pre-test
+                    const float G = ex2_approx(p2);
                     const float og = __fmul_rn(b.y, G);
                     const float alpha = fminf(cam.alpha_max, og);
                     if (alpha >= cam.alpha_min) {

@@ -30,8 +30,6 @@ namespace nvgs {
 
 namespace {
 
-constexpr float kPowerMargin = 1e-4f;
-
 struct Frag {
     float T, C0, C1, C2;
     uint32_t last;   // global index + 1 of the last pair blended at the pixel (0: none)
@@ -53,27 +51,29 @@ __device__ __forceinline__ void stage(const uint32_t* __restrict__ values, const
                                       uint32_t k, uint32_t end, float4* s_a, float4* s_b, float4* s_c) {
     if (k < end) {
         const size_t idx = 3 * (size_t)values[k];
-        s_a[threadIdx.x] = __ldg(&rec[idx]);
-        s_b[threadIdx.x] = __ldg(&rec[idx + 1]);
+        float4 sa, sb;
+        stage_splat(__ldg(&rec[idx]), __ldg(&rec[idx + 1]), sa, sb);
+        s_a[threadIdx.x] = sa;
+        s_b[threadIdx.x] = sb;
         s_c[threadIdx.x] = __ldg(&rec[idx + 2]);
     }
 }
 
 // Blend records [base, base + nb) (staged in shared memory) into one pixel.  transmittance_only:
 // no stop rule, no colour -- only the product of (1 - alpha).
-template <bool kTransmittanceOnly>
+template <bool kTransmittanceOnly, bool kCount>
 __device__ __forceinline__ void blend_batch(const float4* s_a, const float4* s_b, const float4* s_c,
                                             int nb, float fx, float fy, const CamParams& cam, Frag& f,
                                             const uint32_t* __restrict__ values, uint32_t base,
                                             uint8_t* __restrict__ mark) {
     for (int j = 0; j < nb && !f.done; j++) {
-        f.evals++;
+        if (kCount) f.evals++;
         const float4 a = s_a[j];
         const float dx = fx - a.x, dy = fy - a.y;
         const float4 b = s_b[j];
-        const float power = splat_power(a, b, dx, dy);
-        if (power > 0.0f || power < b.w - kPowerMargin) continue;
-        const float alpha = fminf(cam.alpha_max, __fmul_rn(b.y, __expf(power)));
+        const float p2 = splat_exponent2(a, b, dx, dy);
+        if (p2 > 0.0f || p2 < b.z) continue;
+        const float alpha = fminf(cam.alpha_max, __fmul_rn(b.y, ex2_approx(p2)));
         if (alpha < cam.alpha_min) continue;
         const float nt = f.T * (1.0f - alpha);
         if (kTransmittanceOnly) {
@@ -94,7 +94,7 @@ __device__ __forceinline__ void blend_batch(const float4* s_a, const float4* s_b
 }
 
 // Walk pairs [start, end) for this thread's pixel with the usual batching and block-wide exit.
-template <int TS, bool kTransmittanceOnly>
+template <int TS, bool kTransmittanceOnly, bool kCount>
 __device__ __forceinline__ void walk(const uint32_t* __restrict__ values, const float4* __restrict__ rec,
                                      uint32_t start, uint32_t end, float fx, float fy,
                                      const CamParams& cam, Frag& f, uint8_t* __restrict__ mark,
@@ -105,14 +105,14 @@ __device__ __forceinline__ void walk(const uint32_t* __restrict__ values, const 
         stage<TS>(values, rec, base + threadIdx.x, end, s_a, s_b, s_c);
         __syncthreads();
         const int nb = (int)min((uint32_t)B, end - base);
-        blend_batch<kTransmittanceOnly>(s_a, s_b, s_c, nb, fx, fy, cam, f, values, base, mark);
+        blend_batch<kTransmittanceOnly, kCount>(s_a, s_b, s_c, nb, fx, fy, cam, f, values, base, mark);
     }
 }
 
 }  // namespace
 
-template <int TS>
-__global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ ranges,
+template <int TS, bool kCount>
+__global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS) < 6 ? 1536 / (TS * TS) : 6) k_blend(const uint32_t* __restrict__ ranges,
                                                   const uint32_t* __restrict__ values,
                                                   const float4* __restrict__ rec, const CamParams* __restrict__ camp,
                                                   float* __restrict__ image, float* __restrict__ final_T,
@@ -134,9 +134,9 @@ __global__ void __launch_bounds__(TS* TS) k_blend(const uint32_t* __restrict__ r
     const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
     const bool inside = px < cam.W && py < cam.H;
     Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, !inside};
-    walk<TS, false>(values, rec, start, longer ? start + split_len : end, (float)px + 0.5f,
+    walk<TS, false, kCount>(values, rec, start, longer ? start + split_len : end, (float)px + 0.5f,
                     (float)py + 0.5f, cam, f, mark, s_a, s_b, s_c);
-    add_evals(evals_out, f.evals);
+    if (kCount) add_evals(evals_out, f.evals);
     if (longer) {
         const bool all_done = __syncthreads_count(f.done) == B;
         if (threadIdx.x == 0) alive[tile] = all_done ? 0u : 1u;
@@ -180,7 +180,7 @@ __device__ __forceinline__ void chunk_range(const uint32_t* __restrict__ ranges,
     end = min(ranges[2 * it.x + 1], start + split_len);
 }
 
-template <int TS>
+template <int TS, bool kCount>
 __global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __restrict__ ranges,
                                                           const uint32_t* __restrict__ values,
                                                           const float4* __restrict__ rec, const CamParams* __restrict__ camp,
@@ -207,13 +207,14 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __rest
         const bool stopped = state_tc[(size_t)tile * B + threadIdx.x].w < 0.0f;
         Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, stopped || !(px < cam.W && py < cam.H)};
         __syncthreads();   // the previous item's last batch is fully consumed
-        walk<TS, true>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, nullptr, s_a, s_b, s_c);
+        walk<TS, true, kCount>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, nullptr, s_a, s_b,
+                               s_c);
         Tch[(size_t)item * B + threadIdx.x] = f.T;
-        add_evals(evals_out, f.evals);
+        if (kCount) add_evals(evals_out, f.evals);
     }
 }
 
-template <int TS>
+template <int TS, bool kCount>
 __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __restrict__ ranges,
                                                           const uint32_t* __restrict__ values,
                                                           const float4* __restrict__ rec, const CamParams* __restrict__ camp,
@@ -245,11 +246,12 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
         const bool dead = sw < 0.0f || T_in < cam.t_stop;
         Frag f{T_in, 0.0f, 0.0f, 0.0f, 0, dead || !(px < cam.W && py < cam.H)};
         __syncthreads();   // the previous item's last batch is fully consumed
-        walk<TS, false>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, mark, s_a, s_b, s_c);
+        walk<TS, false, kCount>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, mark, s_a, s_b,
+                                s_c);
         // w < 0 marks "stopped inside this chunk or before"
         part[(size_t)item * B + threadIdx.x] = make_float4(f.C0, f.C1, f.C2, (f.done || dead) ? -f.T - 1.0f : f.T);
         pcount[(size_t)item * B + threadIdx.x] = (int32_t)f.last;
-        add_evals(evals_out, f.evals);
+        if (kCount) add_evals(evals_out, f.evals);
     }
 }
 
@@ -342,7 +344,7 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
         pcount = reinterpret_cast<int32_t*>(p);
     }
     NVGS_LAUNCH(log, s, TS == 8 ? "k_blend<8>" : TS == 16 ? "k_blend<16>" : "k_blend<32>",
-                k_blend<TS><<<n_tiles, B, 0, s>>>(ranges, values, rec, cam_dev, image, final_T, n_contrib, mark,
+                (evals ? k_blend<TS, true> : k_blend<TS, false>)<<<n_tiles, B, 0, s>>>(ranges, values, rec, cam_dev, image, final_T, n_contrib, mark,
                                                   split_len, state_tc, state_cnt, alive, evals));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !may_split) return e;
@@ -352,8 +354,8 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
     NVGS_LAUNCH(log, s, "k_split_fill", k_split_fill<<<(n_tiles + 255) / 256, 256, 0, s>>>(n_chunks, first, n_tiles, items));
     // persistent grids: enough CTAs to fill the GPU (the item count lives on the device)
     const unsigned pgrid = (unsigned)std::min<uint64_t>(max_items, (uint64_t)num_sms * (2048 / B));
-    NVGS_LAUNCH(log, s, "k_blend_split_T", k_blend_split_T<TS><<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, state_tc, Tch, evals));
-    NVGS_LAUNCH(log, s, "k_blend_split_C", k_blend_split_C<TS><<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, state_tc, Tch, part, pcount, mark, evals));
+    NVGS_LAUNCH(log, s, "k_blend_split_T", (evals ? k_blend_split_T<TS, true> : k_blend_split_T<TS, false>)<<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, state_tc, Tch, evals));
+    NVGS_LAUNCH(log, s, "k_blend_split_C", (evals ? k_blend_split_C<TS, true> : k_blend_split_C<TS, false>)<<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, state_tc, Tch, part, pcount, mark, evals));
     NVGS_LAUNCH(log, s, "k_blend_split_D", k_blend_split_D<TS><<<n_tiles, B, 0, s>>>(n_chunks, first, cam_dev, state_tc, state_cnt, part, pcount, image, final_T, n_contrib));
     return cudaGetLastError();
 }

@@ -98,13 +98,29 @@ __device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, floa
     Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
 }
 
-// Exponent of a splat at a pixel offset (dx, dy) = pixel centre - mean:
-//   power = -1/2 (A dx^2 + C dy^2) - B dx dy,  a = (u, v, A, B), b = (C, opacity, ...).
-// Every rounding step is explicit (no contraction left to the compiler), so the compositing and
-// its derivative recompute bit-identical exponents and take the same alpha decisions.
-__device__ __forceinline__ float splat_power(const float4& a, const float4& b, float dx, float dy) {
-    const float q = __fmaf_rn(__fmul_rn(a.z, dx), dx, __fmul_rn(__fmul_rn(b.x, dy), dy));
-    return __fmaf_rn(-0.5f, q, -__fmul_rn(__fmul_rn(a.w, dx), dy));
+// Compositing form of a splat record a = (u, v, A, B), b = (C, opacity, depth, ln(alpha_min/o)):
+// the exponent in base 2, p2 = log2(e) (-1/2 (A dx^2 + C dy^2) - B dx dy), costs five operations
+// per pixel with the per-splat constants kA = -log2(e) A / 2, kB = -log2(e) B, kC = -log2(e) C / 2
+// folded in once, and alpha = opacity 2^p2 needs no further multiply.  The pre-test bound
+// w2 = log2(e) (ln(alpha_min / opacity) - 1e-4) skips a fragment whose exponent is below the
+// alpha_min level by more than 1e-4 (in natural units) before the exponential.  Every rounding
+// step is explicit, so the compositing and its derivative compute bit-identical exponents.
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ void stage_splat(const float4& a, const float4& b, float4& sa, float4& sb) {
+    sa = make_float4(a.x, a.y, __fmul_rn(-0.5f * kLog2e, a.z), __fmul_rn(-kLog2e, a.w));
+    sb = make_float4(__fmul_rn(-0.5f * kLog2e, b.x), b.y, __fmul_rn(kLog2e, __fadd_rn(b.w, -1e-4f)), 0.0f);
+}
+
+__device__ __forceinline__ float splat_exponent2(const float4& sa, const float4& sb, float dx, float dy) {
+    const float t = __fmaf_rn(sa.z, dx, __fmul_rn(sa.w, dy));         // kA dx + kB dy
+    return __fmaf_rn(dx, t, __fmul_rn(__fmul_rn(sb.x, dy), dy));      // dx t + kC dy^2
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // S5 binning refinement.  A splat's tile rectangle (the box of its support ellipse) is pruned,
