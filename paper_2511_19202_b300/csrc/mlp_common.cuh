@@ -15,10 +15,18 @@ namespace nvgs {
 //   [31]     0 (pads K to a multiple of 16 for the tensor cores)
 // The base octave uses the hardware sin/cos (|arg| <= pi); the higher octaves follow from it by
 // the double-angle identities.
-__device__ __forceinline__ void mlp_features(const AssetDev& a, const FrameInst& fi, float4 m,
-                                             float f[32]) {
-    float p[3] = {(m.x - a.bbox_c[0]) * a.bbox_scale[0], (m.y - a.bbox_c[1]) * a.bbox_scale[1],
-                  (m.z - a.bbox_c[2]) * a.bbox_scale[2]};
+// The asset constants the inputs need (loaded once per pass) and the per-row instance values.
+struct MlpAsset {
+    float bc0, bc1, bc2, bs0, bs1, bs2, log_dmin, inv_log_range;
+};
+__device__ __forceinline__ MlpAsset mlp_asset(const AssetDev& a) {
+    return MlpAsset{a.bbox_c[0], a.bbox_c[1], a.bbox_c[2], a.bbox_scale[0], a.bbox_scale[1],
+                    a.bbox_scale[2], a.log_dmin, a.inv_log_range};
+}
+
+__device__ __forceinline__ void mlp_features(const MlpAsset& a, float clx, float cly, float clz,
+                                             float dist_scale, float4 m, float f[32]) {
+    float p[3] = {(m.x - a.bc0) * a.bs0, (m.y - a.bc1) * a.bs1, (m.z - a.bc2) * a.bs2};
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         float s, c;
@@ -34,16 +42,21 @@ __device__ __forceinline__ void mlp_features(const AssetDev& a, const FrameInst&
             c = c2;
         }
     }
-    float dx = m.x - fi.cam_local[0], dy = m.y - fi.cam_local[1], dz = m.z - fi.cam_local[2];
+    float dx = m.x - clx, dy = m.y - cly, dz = m.z - clz;
     float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     float inv = rsqrtf(d2);
     float dist = d2 * inv;
     f[27] = dx * inv;
     f[28] = dy * inv;
     f[29] = dz * inv;
-    float dn = fmaf(2.0f * (logf(dist * fi.dist_scale) - a.log_dmin), a.inv_log_range, -1.0f);
+    float dn = fmaf(2.0f * (logf(dist * dist_scale) - a.log_dmin), a.inv_log_range, -1.0f);
     f[30] = fminf(1.0f, fmaxf(-1.0f, dn));
     f[31] = 0.0f;
+}
+
+__device__ __forceinline__ void mlp_features(const AssetDev& a, const FrameInst& fi, float4 m,
+                                             float f[32]) {
+    mlp_features(mlp_asset(a), fi.cam_local[0], fi.cam_local[1], fi.cam_local[2], fi.dist_scale, m, f);
 }
 
 }  // namespace nvgs
