@@ -271,15 +271,21 @@ def run_ours(args, rank, world):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.nvtx.range_push(label)   # lets ncu --nvtx-include select the timed frames
+        # per-frame events too (each call synchronises at its end, so they cost nothing extra)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
         e0.record(stream)
+        ev[0].record(stream)
         for k in range(K):
             _, st = r.render(frame(k), flags, out)
+            ev[k + 1].record(stream)
             stats.append(st)
         e1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
+        for k in range(K):
+            stats[k]["frame_ms"] = ev[k].elapsed_time(ev[k + 1])
         return e0.elapsed_time(e1), stats
 
     for k in range(args.warmup):
@@ -415,6 +421,10 @@ def run_ours(args, rank, world):
                    "logit_threshold": tau,
                    "threshold_calibration_min_psnr_db": calib,
                    "unculled_ms_per_frame": plain_ms,
+                   "culled_ms_median_p95": [float(np.median([x["frame_ms"] for x in st_culled])),
+                                            float(np.percentile([x["frame_ms"] for x in st_culled], 95))],
+                   "unculled_ms_median_p95": [float(np.median([x["frame_ms"] for x in st_plain])),
+                                              float(np.percentile([x["frame_ms"] for x in st_plain], 95))],
                    "speedup_culled_vs_unculled": plain_ms / value,
                    "psnr_culled_vs_unculled_db": min(psnrs) if psnrs else None,
                    "culled_fraction_of_in_frustum": float(np.mean(culled_frac)),
