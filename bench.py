@@ -203,6 +203,23 @@ def cpu_baseline_line(sc, cams, steps, warmup, n_rows=SAMPLE_ROWS):
 
 
 # ----------------------------------------------------------------------------- ours
+# ----------------------------------------------------------------------------- replicas (N > 1)
+def replica_frames(rank: int, world: int, steps: int, n_frames: int):
+    """Orbit frames rank `rank` renders: frame rank + k * world, k = 0 .. steps-1 (no exchange step:
+    every rank holds the whole scene and renders its own frames)."""
+    return [(rank + k * world) % n_frames for k in range(steps)]
+
+
+def job_ms_per_frame(rank_ms, steps: int, world: int, device=None):
+    """Whole-job time per frame: the slowest rank's time for its `steps` frames over all
+    steps * world frames (max over ranks through torch.distributed when world > 1)."""
+    import torch
+    t = torch.tensor(list(rank_ms), dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) / (steps * world) for x in t.tolist()]
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2511_19202_b300 import build as nvbuild
@@ -258,8 +275,10 @@ def run_ours(args, rank, world):
     culled = r.flags(use_mlp=1, mlp_gate=1, tile_size=tile, logit_threshold=tau)
     stream = r.stream
 
+    my_frames = replica_frames(rank, world, max(args.steps, args.warmup, 8), len(cams))
+
     def frame(k):
-        return cams[(rank + k * world) % len(cams)]
+        return cams[my_frames[k % len(my_frames)]]
 
     def timed(flags, K, profile, label):
         flags.profile = 1 if profile else 0
@@ -303,13 +322,8 @@ def run_ours(args, rank, world):
     ms_culled_prof, st_prof = timed(culled, args.steps, True, "nvgs_profiled_culled")
     kstats = N.nvgs_kernel_stats(r.ctx)
 
-    if world > 1:
-        t = torch.tensor([ms_culled, ms_plain], device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_culled, ms_plain = float(t[0]), float(t[1])
-    frames_total = args.steps * world
-    value = ms_culled / frames_total * 1.0 if world > 1 else ms_culled / args.steps
-    plain_ms = ms_plain / frames_total if world > 1 else ms_plain / args.steps
+    value, plain_ms = job_ms_per_frame([ms_culled, ms_plain], args.steps, world,
+                                       device=f"cuda:{dev}" if world > 1 else None)
 
     # e2e through the C ABI with a host image (device->host copy inside the timed region)
     host = torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True)
