@@ -41,10 +41,14 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", choices=["composed", "small", "large"], default="composed",
+    p.add_argument("--config", choices=["composed", "small", "large", "multiview", "backward"],
+                   default="composed",
                    help="composed: 16 x 500k assets, 64 instances, 1080p (the headline workload); "
                         "small: one 20k torus at 256^2; large: 8 x 1M assets, 200 instances "
-                        "(200M instanced Gaussians) at 3840x2160")
+                        "(200M instanced Gaussians) at 3840x2160; multiview: 256 views of mixed "
+                        "resolution through the sync-free batch and its CUDA graph, plus the "
+                        "autotuner; backward: forward + backward of a 1M-Gaussian SH-3 asset at "
+                        "1080p against a random target")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--mlp", choices=["trained", "random"], default="trained",
                    help="trained: per-asset GPU labels + Adam (Sec. 3.1-3.2) before timing")
@@ -463,6 +467,164 @@ def run_ours(args, rank, world):
     return out, sc, cams
 
 
+# ----------------------------------------------------------------------------- multiview (N3)
+def run_multiview(args):
+    """256 views with resolutions drawn from {720p, 1080p, 2160p} (seed 23) of a scene of 200
+    instances of four 100k-Gaussian assets, rendered one view per call (synchronous) and as
+    batches of 32 views through nvgs_render_batch, plain and replayed as a CUDA graph; the
+    autotuner runs on the first batch."""
+    import torch
+    import scenes
+    from paper_2511_19202_b300 import nvgs as N
+    from paper_2511_19202_b300.render import Renderer
+
+    rng = np.random.default_rng(23)
+    assets = [scenes.random_asset(k, 100_000, 3) for k in range(4)]
+    insts = []
+    for i in range(200):
+        a = int(rng.integers(0, 4))
+        R = scenes.synth._random_rotation(rng)
+        s = float(np.float32(rng.uniform(0.5, 2.0)))
+        xz = rng.uniform(-15.0, 15.0, 2)
+        insts.append(scenes.Instance(a, R.astype(np.float32), np.float32([xz[0], s, xz[1]]), s))
+    sc = scenes.Scene(assets, insts)
+    sizes = [(1280, 720), (1920, 1080), (3840, 2160)]
+    n_views = 256
+    cams = []
+    for v in range(n_views):
+        w, h = sizes[int(rng.integers(0, 3))]
+        ang = 2 * math.pi * v / n_views
+        eye = (22.0 * math.cos(ang), float(rng.uniform(3.0, 9.0)), 22.0 * math.sin(ang))
+        cams.append(scenes.look_at_camera(eye, (0.0, 0.0, 0.0), w, h, 50.0))
+    r = Renderer(0)
+    r.load_scene(sc, [scenes.mlp_weights(42 + k) for k in range(4)], N.NVGS_PREC_BF16)
+    fl = lambda: r.flags(use_mlp=1, mlp_gate=1, logit_threshold=-2.0)
+    outs = [torch.empty((c.height, c.width, 3), dtype=torch.float32, device="cuda") for c in cams]
+    # synchronous, one view per call
+    stats = []
+    for k in range(4):
+        r.render(cams[k], fl(), outs[k])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(n_views):
+        _, st = r.render(cams[k], fl(), outs[k])
+        stats.append(st)
+    e1.record()
+    torch.cuda.synchronize()
+    sync_ms = e0.elapsed_time(e1) / n_views
+    max_pairs = int(1.25 * max(st["n_pairs"] for st in stats))
+    B = 32
+    groups = [list(range(g, g + B)) for g in range(0, n_views, B)]
+    # every view once in batches of 32 (no host synchronisation inside a batch)
+    r.render_batch([cams[k] for k in groups[0]], fl(), out=[outs[k] for k in groups[0]], max_pairs=max_pairs)
+    same = all(bool(torch.equal(outs[k], r.render(cams[k], fl())[0])) for k in groups[0][:4])
+    torch.cuda.synchronize()
+    e0.record()
+    for g in groups:
+        r.render_batch([cams[k] for k in g], fl(), out=[outs[k] for k in g], max_pairs=max_pairs,
+                       want_stats=False)
+    e1.record()
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / n_views
+    # replay of one fixed group (what a graph is for: the same views' sizes every frame)
+    g0 = groups[0]
+    for _ in range(2):
+        r.render_batch([cams[k] for k in g0], fl(), out=[outs[k] for k in g0], max_pairs=max_pairs,
+                       use_graph=True, want_stats=False)
+    torch.cuda.synchronize()
+    e0.record()
+    reps = 8
+    for _ in range(reps):
+        r.render_batch([cams[k] for k in g0], fl(), out=[outs[k] for k in g0], max_pairs=max_pairs,
+                       use_graph=True, want_stats=False)
+    e1.record()
+    torch.cuda.synchronize()
+    replay_ms = e0.elapsed_time(e1) / (reps * B)
+    sync0 = 0.0
+    e0.record()
+    for k in g0:
+        r.render(cams[k], fl(), outs[k])
+    e1.record()
+    torch.cuda.synchronize()
+    sync0 = e0.elapsed_time(e1) / B
+    best, table = N.nvgs_autotune(r.ctx, [cams[k] for k in g0], fl(), [outs[k] for k in g0], 4 * max_pairs)
+    line = {"metric": "ms/view, a 32-view batch of mixed resolution (720p/1080p/2160p) replayed as one CUDA graph",
+            "value": replay_ms, "unit": "ms/view", "n_gpus": 1,
+            "steps": reps, "warmup": 2, "ms_per_step": replay_ms * B,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "4 assets x 100k Gaussians (SH 3), 200 instances, 256 views of "
+                                   "1280x720 / 1920x1080 / 3840x2160 (seed 23), random-weight BF16 MLP",
+                       "all_256_views_sync_ms_per_view": sync_ms,
+                       "all_256_views_batch32_ms_per_view": batch_ms,
+                       "images_equal_sync": same,
+                       "group_sync_ms_per_view": sync0,
+                       "group_graph_replay_ms_per_view": replay_ms,
+                       "autotune_best": {"tile_size": best.tile_size, "mlp_ctas_per_sm": best.mlp_ctas_per_sm,
+                                         "blend_split_len": best.blend_split_len},
+                       "autotune_candidates": table}}
+    r.close()
+    return line
+
+
+# ----------------------------------------------------------------------------- backward (N2)
+def run_backward(args):
+    """One 1M-Gaussian SH-3 asset (sphere) at 1920x1080; each step renders through the
+    autograd wrapper, takes the L2 loss against a U[0, 1] random target and back-propagates into
+    the asset's parameters (forward + nvgs_render_backward)."""
+    import torch
+    import scenes
+    from paper_2511_19202_b300.autograd import PARAM_NAMES, render_asset
+    from paper_2511_19202_b300.render import Renderer
+
+    a = scenes.sphere_asset(1_000_000, 31, sh_degree=3, radius=1.0)
+    sc = scenes.Scene([a], [scenes.Instance(0, np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 1.0)])
+    cam = scenes.look_at_camera((0.0, 0.6, 2.8), (0.0, 0.0, 0.0), 1920, 1080, 50.0)
+    r = Renderer(0)
+    r.load_scene(sc)
+    params = {k: torch.from_numpy(np.ascontiguousarray(getattr(a, k), np.float32)).cuda().requires_grad_(True)
+              for k in PARAM_NAMES}
+    target = torch.rand((1080, 1920, 3), device="cuda", generator=torch.Generator(device="cuda").manual_seed(5))
+
+    def step():
+        img = render_asset(r, 0, params, cam, r.flags(use_mlp=0))
+        loss = ((img - target) ** 2).mean()
+        for p in params.values():
+            p.grad = None
+        loss.backward()
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        loss = step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # forward alone, for the split
+    e0.record()
+    for _ in range(args.steps):
+        with torch.no_grad():
+            render_asset(r, 0, params, cam, r.flags(use_mlp=0))
+    e1.record()
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1) / args.steps
+    from paper_2511_19202_b300 import nvgs as N
+    N.nvgs_reset_kernel_stats(r.ctx)
+    line = {"metric": "ms per forward+backward step, 1M-Gaussian SH-3 asset at 1080p, L2 loss",
+            "value": ms, "unit": "ms/step", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sphere asset, 1M Gaussians, SH degree 3, 1920x1080, random U[0,1] target",
+                       "forward_ms": fwd, "backward_ms": ms - fwd, "loss": float(loss)}}
+    r.close()
+    return line
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -485,6 +647,10 @@ def main():
         print(json.dumps(line))
         return 0
 
+    if args.config in ("multiview", "backward"):
+        if rank == 0:
+            print(json.dumps(run_multiview(args) if args.config == "multiview" else run_backward(args)))
+        return 0
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
