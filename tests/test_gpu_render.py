@@ -60,6 +60,10 @@ def test_background_and_host_output(cfg1_setup):
     host = np.zeros((cam.height, cam.width, 3), np.float32)
     r.render_host(cam, r.flags(use_mlp=0, bg=bg), host)
     np.testing.assert_array_equal(dev, host.astype(np.float64))
+    # a page-locked host image (what the end-to-end timing uses) gives the same image
+    pinned = torch.full((cam.height, cam.width, 3), -1.0, dtype=torch.float32, pin_memory=True)
+    r.render_host(cam, r.flags(use_mlp=0, bg=bg), pinned)
+    np.testing.assert_array_equal(dev, pinned.numpy().astype(np.float64))
     ref = oracle.render(osc, cam, oracle_opts_for(dict(bg=bg)))
     compare_images(dev, ref["image"], ref["ambiguous"])
 
