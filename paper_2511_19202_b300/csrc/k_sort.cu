@@ -5,9 +5,10 @@
 // Radix sort, per 8-bit digit pass over tiles of 8192 pairs (512 threads x 16):
 //   1. k_rs_hist:    per-tile digit histogram, stored digit-major: hist[d * n_tiles + tile]
 //   2. exclusive scan of hist -> global start of every (digit, tile) bucket
-//   3. k_rs_scatter: stable rank of every pair inside its tile (warp match + per-warp running
-//      digit counters, each warp owning a contiguous 512-pair slice), a local counting sort in
-//      shared memory, then runs of equal digits written to consecutive global addresses.
+//   3. k_rs_scatter: stable rank of every pair inside its tile (digit peers from eight warp
+//      ballots + per-warp running digit counters, each warp owning a contiguous 512-pair slice),
+//      a local counting sort in shared memory, then runs of equal digits written to consecutive
+//      global addresses.
 #include <algorithm>
 
 #include "nvgs_internal.cuh"
@@ -155,6 +156,18 @@ constexpr int kRsItems = 16;
 constexpr int kRsTile = kRsThreads * kRsItems;  // 8192
 constexpr int kRsWarps = kRsThreads / 32;       // 16
 
+// Lanes of the warp whose 8-bit digit equals this lane's, from one ballot per bit (cheaper than
+// a warp match instruction); lanes with ok = false match only themselves.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool ok) {
+    uint32_t peers = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        const uint32_t m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? m : ~m;
+    }
+    return ok ? peers : 1u << (threadIdx.x & 31);
+}
+
 template <typename K>
 constexpr int rs_smem_bytes() { return kRsWarps * 256 * 4 + kRsTile * (int)sizeof(K) + kRsTile * 4 + 2 * 256 * 4; }
 
@@ -226,11 +239,14 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 2 : 1) k_rs_scatt
         const int p = warp * (kRsItems * 32) + r * 32 + lane;
         const bool ok = p < tile_n;
         const uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u + lane;  // unmatched
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t before = ok ? cnt[warp * 256 + d] : 0u;
-        __syncwarp();
-        if (ok && (peers & lt) == 0u) cnt[warp * 256 + d] = before + __popc(peers);
-        __syncwarp();
+        // the lowest lane of each digit group reserves the group's slots with one shared-memory
+        // atomic; a warp's atomics on a counter complete in program order, so the ranks keep the
+        // input order (stable) without a load / store round trip between the items
+        const uint32_t peers = digit_peers(d & 255u, ok);
+        const int leader = __ffs(peers) - 1;
+        uint32_t before = 0u;
+        if (ok && leader == lane) before = atomicAdd(&cnt[warp * 256 + d], (uint32_t)__popc(peers));
+        before = __shfl_sync(0xffffffffu, before, leader);
         pk[r] = (d << 16) | (before + __popc(peers & lt));
     }
     __syncthreads();
