@@ -188,10 +188,27 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ ke
     }
     for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) (&h[0][0])[k] = 0u;
     __syncthreads();
+    bool vec = false;
+    if constexpr (sizeof(K) == 4) vec = base + kRsTile <= n && ((uintptr_t)(keys + base) & 15u) == 0;
+    if (vec) {
+        // a full tile of 32-bit keys: four 16-byte loads per thread, all in flight at once
+        const uint4* k4 = reinterpret_cast<const uint4*>(keys + base);
+        uint4 v[kRsItems / 4];
+#pragma unroll
+        for (int j = 0; j < kRsItems / 4; j++) v[j] = k4[j * kRsThreads + threadIdx.x];
+#pragma unroll
+        for (int j = 0; j < kRsItems / 4; j++) {
+            atomicAdd(&h[warp][(v[j].x >> shift) & 255u], 1u);
+            atomicAdd(&h[warp][(v[j].y >> shift) & 255u], 1u);
+            atomicAdd(&h[warp][(v[j].z >> shift) & 255u], 1u);
+            atomicAdd(&h[warp][(v[j].w >> shift) & 255u], 1u);
+        }
+    } else {
 #pragma unroll 4
-    for (int j = 0; j < kRsItems; j++) {
-        const uint64_t i = base + (uint64_t)j * kRsThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & 255u], 1u);
+        for (int j = 0; j < kRsItems; j++) {
+            const uint64_t i = base + (uint64_t)j * kRsThreads + threadIdx.x;
+            if (i < n) atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & 255u], 1u);
+        }
     }
     __syncthreads();
     if (threadIdx.x < 256) {
