@@ -251,6 +251,11 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 2 : 1) k_rs_scatt
         const int p = warp * (kRsItems * 32) + r * 32 + lane;
         key[r] = p < tile_n ? keys_in[base + p] : (K)0;
     }
+    {   // the values are read only after the ranking: start their 128-byte lines towards L2 now
+        const int p = warp * (kRsItems * 32) + lane * 32;
+        if (lane < kRsItems && p < tile_n)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(vals_in + base + p));
+    }
 #pragma unroll
     for (int r = 0; r < kRsItems; r++) {
         const int p = warp * (kRsItems * 32) + r * 32 + lane;
