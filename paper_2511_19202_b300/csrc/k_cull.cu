@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(256) k_expand_chunks(const Chunk* __restrict__
     const uint32_t base = chunk_offsets[c];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
+    const int asset = out_mean ? fi[ch.inst].asset : 0;
 #pragma unroll
     for (int k = 0; k < 8; k++) {
         int w = warp * 8 + k;
@@ -182,8 +183,12 @@ __global__ void __launch_bounds__(256) k_expand_chunks(const Chunk* __restrict__
             uint32_t pos = base + s_pref[64 + w] + __popc(word & lt);
             const uint32_t g = (uint32_t)(ch.g0 + w * 32 + lane);
             out[pos] = make_uint2((uint32_t)ch.inst, g);
-            // the MLP reads the mean next to the entry instead of through instance -> asset
-            if (out_mean) out_mean[pos] = __ldg(&assets[fi[ch.inst].asset].mean_op[g]);
+            // the MLP reads the mean next to the entry instead of through instance -> asset, and
+            // the asset id in place of the opacity (which the MLP does not use)
+            if (out_mean) {
+                const float4 m = __ldg(&assets[asset].mean_op[g]);
+                out_mean[pos] = make_float4(m.x, m.y, m.z, __int_as_float(asset));
+            }
         }
     }
 }

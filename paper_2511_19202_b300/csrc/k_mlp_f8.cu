@@ -147,17 +147,26 @@ k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
     const uint32_t n_steps = (n + kRows - 1) / kRows;
     for (uint32_t step = blockIdx.x; step < n_steps && !abort; step += gridDim.x) {
         uint2 e[kHalves];
-        float4 m[kHalves];
+        float4 m[kHalves], ci[kHalves];
         int my_asset[kHalves];
-        bool pending[kHalves], keep[kHalves];
+        bool pending[kHalves], keep[kHalves], gated[kHalves];
         float logit[kHalves];
 #pragma unroll
         for (int h = 0; h < kHalves; h++) {
             const uint32_t i = step * kRows + h * 128 + tid;
             e[h] = make_uint2(0, 0);
             m[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (i < n) { e[h] = __ldg(&list[i]); m[h] = __ldg(&list_mean[i]); }
-            my_asset[h] = i < n ? fis[e[h].x].asset : INT_MAX;
+            ci[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+            gated[h] = false;
+            if (i < n) {
+                e[h] = __ldg(&list[i]);
+                m[h] = __ldg(&list_mean[i]);
+                // instance values the inputs need, loaded ahead of their use
+                const FrameInst& fr = fis[e[h].x];
+                ci[h] = make_float4(fr.cam_local[0], fr.cam_local[1], fr.cam_local[2], fr.dist_scale);
+                gated[h] = fr.gated != 0;
+            }
+            my_asset[h] = i < n ? __float_as_int(m[h].w) : INT_MAX;   // the list mean carries it
             pending[h] = i < n;
             keep[h] = false;
             logit[h] = 0.0f;
@@ -191,7 +200,7 @@ k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
             for (int h = 0; h < kHalves; h++) {
                 float f[32];
                 if (mine[h]) {
-                    mlp_features(a, fis[e[h].x], m[h], f);
+                    mlp_features(mlp_asset(a), ci[h].x, ci[h].y, ci[h].z, ci[h].w, m[h], f);
 #pragma unroll
                     for (int k = 0; k < 32; k++) f[k] *= kInScale;
                 } else {
@@ -245,7 +254,7 @@ k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
                         const float lg = epilogue_logit(t_lane + 64 * h, sVec[259], sVec + 128, sVec + 192, sVec[256]);
                         if (mine[h]) {
                             logit[h] = lg;
-                            keep[h] = fis[e[h].x].gated || (lg > threshold);
+                            keep[h] = gated[h] || (lg > threshold);
                             pending[h] = false;
                         }
                     }

@@ -174,9 +174,9 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
     }
     for (uint32_t step = blockIdx.x; step < n_steps && !abort; step += gridDim.x) {
         uint2 e[kHalves];
-        float4 m[kHalves];
+        float4 m[kHalves], ci[kHalves];
         int my_asset[kHalves];
-        bool pending[kHalves], keep[kHalves];
+        bool pending[kHalves], keep[kHalves], gated[kHalves];
         float logit[kHalves];
 #pragma unroll
         for (int h = 0; h < kHalves; h++) {
@@ -188,7 +188,16 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
                 e_next[h] = __ldg(&list[i_next]);
                 m_next[h] = __ldg(&list_mean[i_next]);
             }
-            my_asset[h] = i < n ? fis[e[h].x].asset : INT_MAX;
+            // the list's mean carries the row's asset id in w; the instance values the inputs
+            // need are loaded here, well ahead of their use after the asset pass
+            my_asset[h] = i < n ? __float_as_int(m[h].w) : INT_MAX;
+            ci[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+            gated[h] = false;
+            if (i < n) {
+                const FrameInst& fr = fis[e[h].x];
+                ci[h] = make_float4(fr.cam_local[0], fr.cam_local[1], fr.cam_local[2], fr.dist_scale);
+                gated[h] = fr.gated != 0;
+            }
             pending[h] = i < n;
             keep[h] = false;
             logit[h] = 0.0f;
@@ -227,7 +236,7 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
                 uint32_t p[16];
                 if (mine[h]) {
                     float f[32];
-                    mlp_features(a, fis[e[h].x], m[h], f);
+                    mlp_features(mlp_asset(a), ci[h].x, ci[h].y, ci[h].z, ci[h].w, m[h], f);
 #pragma unroll
                     for (int k = 0; k < 16; k++) p[k] = bf16x2(f[2 * k], f[2 * k + 1]);
                 } else {
@@ -283,7 +292,7 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
                         const float lg = __uint_as_float(r[0]) + __uint_as_float(r[1]);
                         if (mine[h]) {
                             logit[h] = lg;
-                            keep[h] = fis[e[h].x].gated || (lg > threshold);
+                            keep[h] = gated[h] || (lg > threshold);
                             pending[h] = false;
                         }
                     }
