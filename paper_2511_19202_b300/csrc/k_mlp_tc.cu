@@ -107,14 +107,14 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, uint8_t* sH, in
     }
 }
 
-// Issue one layer for one 128-row tile: K / 16 steps of A x B plus the bias step.
-__device__ __forceinline__ void issue_layer(uint32_t d, const uint8_t* sA, uint32_t sbo_a, int k_steps,
-                                            const uint8_t* sW, uint32_t sbo_w, const uint8_t* sBias,
-                                            const uint8_t* sOnes, uint32_t idesc_) {
+// Issue one layer for one 128-row tile: K / 16 steps of A x B plus the bias step.  Descriptors
+// are precomputed; consecutive K = 16 slices of a K-major tile are 256 bytes (16 in the
+// descriptor's address field) apart.
+__device__ __forceinline__ void issue_layer(uint32_t d, uint64_t da, int k_steps, uint64_t dw,
+                                            uint64_t dbias, uint64_t dones, uint32_t idesc_) {
 #pragma unroll 4
-    for (int k = 0; k < k_steps; k++)
-        mma_f16(d, sdesc(sA + 256 * k, kLbo, sbo_a), sdesc(sW + 256 * k, kLbo, sbo_w), idesc_, k > 0);
-    mma_f16(d, sdesc(sOnes, kLbo, kSboK16), sdesc(sBias, kLbo, kSboK16), idesc_, 1);
+    for (int k = 0; k < k_steps; k++) mma_f16(d, da + 16u * k, dw + 16u * k, idesc_, k > 0);
+    mma_f16(d, dones, dbias, idesc_, 1);
 }
 
 }  // namespace
@@ -153,6 +153,14 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
     const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
+    // operand descriptors of every MMA (fixed addresses; only thread 0 issues)
+    const uint64_t dA32[kHalves] = {sdesc(sm + kOffH, kLbo, kSboK32), sdesc(sm + kOffH + kHBytes, kLbo, kSboK32)};
+    const uint64_t dA64[kHalves] = {sdesc(sm + kOffH, kLbo, kSboK64), sdesc(sm + kOffH + kHBytes, kLbo, kSboK64)};
+    const uint64_t dW1 = sdesc(sm + kOffW1, kLbo, kSboK32), dW2 = sdesc(sm + kOffW2, kLbo, kSboK64);
+    const uint64_t dW3 = sdesc(sm + kOffW3, kLbo, kSboK64), dW4 = sdesc(sm + kOffW4, kLbo, kSboK64);
+    const uint64_t dB1 = sdesc(sm + kOffB1, kLbo, kSboK16), dB2 = sdesc(sm + kOffB2, kLbo, kSboK16);
+    const uint64_t dB3 = sdesc(sm + kOffB3, kLbo, kSboK16), dB4 = sdesc(sm + kOffB4, kLbo, kSboK16);
+    const uint64_t dOnes = sdesc(sm + kOffOnes, kLbo, kSboK16);
 
     uint32_t phase = 0;
     int loaded = -1;
@@ -260,16 +268,15 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
                     tc_fence_after();
 #pragma unroll
                     for (int h = 0; h < kHalves; h++) {
-                        const uint8_t* sH = sm + kOffH + h * kHBytes;
                         const uint32_t d = tmem + 64 * h;
                         if (layer == 0)
-                            issue_layer(d, sH, kSboK32, 2, sm + kOffW1, kSboK32, sm + kOffB1, sm + kOffOnes, kIdescN64);
-                        else if (layer < 3)
-                            issue_layer(d, sH, kSboK64, 4, sm + (layer == 1 ? kOffW2 : kOffW3), kSboK64,
-                                        sm + (layer == 1 ? kOffB2 : kOffB3), sm + kOffOnes, kIdescN64);
+                            issue_layer(d, dA32[h], 2, dW1, dB1, dOnes, kIdescN64);
+                        else if (layer == 1)
+                            issue_layer(d, dA64[h], 4, dW2, dB2, dOnes, kIdescN64);
+                        else if (layer == 2)
+                            issue_layer(d, dA64[h], 4, dW3, dB3, dOnes, kIdescN64);
                         else
-                            issue_layer(d, sH, kSboK64, 4, sm + kOffW4, kSboK64, sm + kOffB4, sm + kOffOnes,
-                                        kIdescN16);
+                            issue_layer(d, dA64[h], 4, dW4, dB4, dOnes, kIdescN16);
                     }
                     mma_commit(mbar);
                 }
