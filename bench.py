@@ -285,7 +285,7 @@ def run_ours(args, rank, world):
         return cams[my_frames[k % len(my_frames)]]
 
     def timed(flags, K, profile, label):
-        flags.profile = 1 if profile else 0
+        flags.profile = int(profile)
         out = torch.empty((H, W, 3), dtype=torch.float32, device=f"cuda:{dev}")
         stats = []
         if world > 1:
@@ -323,8 +323,13 @@ def run_ours(args, rank, world):
     # per-kernel device time (CUDA events around every launch) in a separate pass over the same
     # frames, so that the events do not perturb the timed passes
     N.nvgs_reset_kernel_stats(r.ctx)
-    ms_culled_prof, st_prof = timed(culled, args.steps, True, "nvgs_profiled_culled")
+    ms_culled_prof, st_prof = timed(culled, args.steps, 1, "nvgs_profiled_culled")
     kstats = N.nvgs_kernel_stats(r.ctx)
+    # the compositing's (pixel, fragment) evaluation counts of the same frames, from a third pass
+    # (counting runs an instrumented compositing kernel, so it stays out of the kernel times)
+    _, st_count = timed(culled, args.steps, 2, "nvgs_counted_culled")
+    for s_, c_ in zip(st_prof, st_count):
+        s_["blend_evaluations"] = c_["blend_evaluations"]
 
     value, plain_ms = job_ms_per_frame([ms_culled, ms_plain], args.steps, world,
                                        device=f"cuda:{dev}" if world > 1 else None)

@@ -101,7 +101,10 @@ typedef struct {
     float bg[3];                 /* background colour */
     int32_t tile_size;           /* 8, 16 or 32 */
     int32_t image_memory;        /* nvgs_memory of the output image */
-    int32_t profile;             /* 1: time each stage with CUDA events (nvgs_frame_stats) */
+    int32_t profile;             /* 1: time each stage and kernel with CUDA events
+                                    (nvgs_frame_stats, nvgs_kernel_stats); 2: the same and count
+                                    S6's (pixel, fragment) evaluations, which runs an instrumented
+                                    compositing kernel (so its times are not those of 1) */
     const float* logits_override;/* nullable DEVICE array of per-instanced-Gaussian logits used
                                     instead of the MLP (tests inject fixed decisions with it) */
     int32_t keep_outputs;        /* 1: keep final T and the last blended pair per pixel for
@@ -127,9 +130,9 @@ typedef struct {
     uint64_t n_pairs;            /* (tile, Gaussian) pairs sorted in S5 */
     uint32_t n_instances_visible;/* instances whose bounding sphere meets the frustum */
     uint32_t sort_passes;        /* radix passes run in S5 */
-    float stage_ms[NVGS_NUM_STAGES]; /* filled when flags.profile = 1 (synchronises) */
+    float stage_ms[NVGS_NUM_STAGES]; /* filled when flags.profile >= 1 (synchronises) */
     uint64_t kernel_launches;    /* kernels this frame enqueued */
-    uint64_t blend_evaluations;  /* (pixel, fragment) evaluations of S6, when flags.profile = 1 */
+    uint64_t blend_evaluations;  /* (pixel, fragment) evaluations of S6, when flags.profile = 2 */
 } nvgs_frame_stats;
 
 /* ------------------------------------------------------------------ context */

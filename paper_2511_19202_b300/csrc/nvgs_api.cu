@@ -152,6 +152,8 @@ nvgs_status validate_flags(nvgs_ctx* ctx, const nvgs_render_flags* f) {
         return fail(ctx, NVGS_ERR_INVALID_ARG, "blending constants out of range");
     if (f->mlp_ctas_per_sm < 0 || f->mlp_ctas_per_sm > 3)
         return fail(ctx, NVGS_ERR_INVALID_ARG, "mlp_ctas_per_sm must be 0..3");
+    if (f->profile < 0 || f->profile > 2)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "profile must be 0, 1 or 2");
     if (f->blend_split_len > 0 && f->blend_split_len < 256)
         return fail(ctx, NVGS_ERR_INVALID_ARG, "blend_split_len must be 0, negative or >= 256");
     if (f->image_memory != NVGS_MEM_HOST && f->image_memory != NVGS_MEM_DEVICE)
@@ -804,7 +806,7 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
         CK(ensure(ctx->split_scratch, blend_split_scratch_bytes(n_tiles, n_pairs, cp.tile_size, split_len)));
         CK(ensure(ctx->scratch, scan_scratch_bytes(n_tiles)));
     }
-    unsigned long long* evals = f->profile ? reinterpret_cast<unsigned long long*>(counters + 10) : nullptr;
+    unsigned long long* evals = f->profile >= 2 ? reinterpret_cast<unsigned long long*>(counters + 10) : nullptr;
     if (evals) CK(cudaMemsetAsync(evals, 0, 8, s));
     CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, cam_dev, img_dev, fT, nc, mark,
                     split_len, n_pairs, ctx->split_scratch.p, ctx->scratch.p, ctx->num_sms, evals, s,
@@ -842,9 +844,11 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
         stats->sort_passes = (uint32_t)passes;
         stats->kernel_launches = ctx->log.count;
         if (f->profile) {
-            uint64_t ev = 0;
-            memcpy(&ev, ctx->h_counters + 10, 8);
-            stats->blend_evaluations = ev;
+            if (f->profile >= 2) {
+                uint64_t ev = 0;
+                memcpy(&ev, ctx->h_counters + 10, 8);
+                stats->blend_evaluations = ev;
+            }
             for (int k = 0; k < NVGS_NUM_STAGES; k++) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, ctx->ev[k], ctx->ev[k + 1]);

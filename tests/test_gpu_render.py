@@ -68,6 +68,22 @@ def test_background_and_host_output(cfg1_setup):
     compare_images(dev, ref["image"], ref["ambiguous"])
 
 
+def test_profile_levels(cfg1_setup):
+    """profile = 1 times stages without counting; profile = 2 also counts the compositing's
+    (pixel, fragment) evaluations -- at least one per covered pixel -- and the image is the same."""
+    sc, cam, r, osc = cfg1_setup
+    a, s0 = r.render(cam, r.flags(use_mlp=0, profile=0))
+    a = a.clone()
+    b, s1 = r.render(cam, r.flags(use_mlp=0, profile=1))
+    b = b.clone()
+    c, s2 = r.render(cam, r.flags(use_mlp=0, profile=2))
+    assert torch.equal(a, b) and torch.equal(a, c)
+    assert s1["blend_evaluations"] == 0 and sum(s1["stage_ms"].values()) > 0
+    covered = int((c.sum(-1) > 0).sum())
+    assert s2["blend_evaluations"] >= covered > 0
+    assert s2["blend_evaluations"] <= s2["n_pairs"] * r.flags().tile_size ** 2
+
+
 def test_render_is_deterministic(cfg1_setup):
     sc, cam, r, osc = cfg1_setup
     a, _ = gpu_image(r, cam, use_mlp=0)
