@@ -6,8 +6,8 @@
 // two 128-row tiles that share every MMA round trip (thread r owns rows r and 128 + r):
 //   1. thread r builds the 32 inputs of row r (Eq. 2 distance, frequency encoding) and writes
 //      them as BF16 into the A tile in shared memory;
-//   2. thread 0 issues tcgen05.mma (M = 128, K = 16 per instruction) for the layer with the
-//      accumulator in TMEM and commits to an mbarrier;
+//   2. lane 0 of warp h issues tcgen05.mma (M = 128, K = 16 per instruction) for tile h's layer
+//      with the accumulator in TMEM and commits to the layer's mbarrier (two arrivals);
 //   3. after the mbarrier completes, each warp reads its 32 TMEM lanes (tcgen05.ld 32x32b),
 //      applies ReLU while converting to BF16 and writes the activations back to shared memory as
 //      the next layer's A operand.
@@ -137,7 +137,7 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(mbar, 1);
+        mbar_init(mbar, kHalves);   // one commit per half per layer
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // constant A tile of the bias steps: row r = (1, 1, 0, ..., 0); core-matrix chunk 0 of row r
@@ -153,9 +153,10 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
     const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
-    // operand descriptors of every MMA (fixed addresses; only thread 0 issues)
-    const uint64_t dA32[kHalves] = {sdesc(sm + kOffH, kLbo, kSboK32), sdesc(sm + kOffH + kHBytes, kLbo, kSboK32)};
-    const uint64_t dA64[kHalves] = {sdesc(sm + kOffH, kLbo, kSboK64), sdesc(sm + kOffH + kHBytes, kLbo, kSboK64)};
+    // operand descriptors of every MMA (fixed addresses); lane 0 of warp h issues half h
+    const int issue_h = warp & 1;
+    const uint64_t dA32 = sdesc(sm + kOffH + issue_h * kHBytes, kLbo, kSboK32);
+    const uint64_t dA64 = sdesc(sm + kOffH + issue_h * kHBytes, kLbo, kSboK64);
     const uint64_t dW1 = sdesc(sm + kOffW1, kLbo, kSboK32), dW2 = sdesc(sm + kOffW2, kLbo, kSboK64);
     const uint64_t dW3 = sdesc(sm + kOffW3, kLbo, kSboK64), dW4 = sdesc(sm + kOffW4, kLbo, kSboK64);
     const uint64_t dB1 = sdesc(sm + kOffB1, kLbo, kSboK16), dB2 = sdesc(sm + kOffB2, kLbo, kSboK16);
@@ -264,20 +265,19 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
             bool ok = true;
 #pragma unroll 1
             for (int layer = 0; layer < 4 && ok; layer++) {
-                if (tid == 0) {
+                // the two halves are issued by lane 0 of warps 0 and 1 concurrently (a single
+                // thread issues an MMA only every ~50 cycles), each committing its own MMAs
+                if (lane == 0 && warp < kHalves) {
                     tc_fence_after();
-#pragma unroll
-                    for (int h = 0; h < kHalves; h++) {
-                        const uint32_t d = tmem + 64 * h;
-                        if (layer == 0)
-                            issue_layer(d, dA32[h], 2, dW1, dB1, dOnes, kIdescN64);
-                        else if (layer == 1)
-                            issue_layer(d, dA64[h], 4, dW2, dB2, dOnes, kIdescN64);
-                        else if (layer == 2)
-                            issue_layer(d, dA64[h], 4, dW3, dB3, dOnes, kIdescN64);
-                        else
-                            issue_layer(d, dA64[h], 4, dW4, dB4, dOnes, kIdescN16);
-                    }
+                    const uint32_t d = tmem + 64 * issue_h;
+                    if (layer == 0)
+                        issue_layer(d, dA32, 2, dW1, dB1, dOnes, kIdescN64);
+                    else if (layer == 1)
+                        issue_layer(d, dA64, 4, dW2, dB2, dOnes, kIdescN64);
+                    else if (layer == 2)
+                        issue_layer(d, dA64, 4, dW3, dB3, dOnes, kIdescN64);
+                    else
+                        issue_layer(d, dA64, 4, dW4, dB4, dOnes, kIdescN16);
                     mma_commit(mbar);
                 }
                 const bool done = mbar_wait(mbar, phase);
