@@ -2,7 +2,7 @@
 // (tile, depth) keys).  Both are reduce-then-scan designs: no CTA ever waits on another, so
 // there is no inter-CTA spin of any kind.
 //
-// Radix sort, per 8-bit digit pass over tiles of 8192 pairs (512 threads x 16):
+// Radix sort, per 8-bit digit pass over tiles of 4096 pairs (256 threads x 16):
 //   1. k_rs_hist:    per-tile digit histogram, stored digit-major: hist[d * n_tiles + tile]
 //   2. exclusive scan of hist -> global start of every (digit, tile) bucket
 //   3. k_rs_scatter: stable rank of every pair inside its tile (digit peers from eight warp
@@ -151,10 +151,10 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, ui
 }
 
 // ================================================================== radix sort
-constexpr int kRsThreads = 512;
+constexpr int kRsThreads = 256;
 constexpr int kRsItems = 16;
-constexpr int kRsTile = kRsThreads * kRsItems;  // 8192
-constexpr int kRsWarps = kRsThreads / 32;       // 16
+constexpr int kRsTile = kRsThreads * kRsItems;  // 4096
+constexpr int kRsWarps = kRsThreads / 32;       // 8
 
 // Lanes of the warp whose 8-bit digit equals this lane's, from one ballot per bit (cheaper than
 // a warp match instruction); lanes with ok = false match only themselves.
@@ -220,14 +220,15 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ ke
 }
 
 // Registers hold the tile's keys and one packed (digit << 16 | rank-in-warp) word per item;
-// values are read only when they are placed in shared memory, so two CTAs fit on an SM.
+// values are read only when they are placed in shared memory, so four CTAs fit on an SM
+// (smaller, more numerous CTAs overlap their load, rank and write phases better).
 template <typename K>
-__global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 2 : 1) k_rs_scatter(
+__global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatter(
     const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, K* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, uint64_t n, const uint32_t* __restrict__ n_dev, int shift,
     uint32_t n_tiles, const uint32_t* __restrict__ hist_scan) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* cnt = (uint32_t*)smem;                                   // [16 warps][256]
+    uint32_t* cnt = (uint32_t*)smem;                                   // [8 warps][256]
     K* s_keys = (K*)(smem + kRsWarps * 256 * 4);
     uint32_t* s_vals = (uint32_t*)(smem + kRsWarps * 256 * 4 + kRsTile * sizeof(K));
     uint32_t* d_local = s_vals + kRsTile;                              // [256] tile-local start
