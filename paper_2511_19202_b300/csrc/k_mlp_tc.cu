@@ -18,7 +18,9 @@
 // so the accumulator already contains W h + b (to about 2^-16 of b).  The epilogue of a hidden
 // layer is thus tcgen05.ld -> cvt.rn.relu.bf16x2 -> st.shared.
 // Three CTAs share an SM (128 TMEM columns and 65 KB of shared memory each), so the epilogues of
-// some overlap the MMAs of others.
+// some overlap the MMAs of others.  Within a CTA, each thread builds the inputs of its rows of the
+// next step while the first layer's MMAs of the current step run (kept in registers as BF16
+// pairs; a row of another asset is built in its own pass as usual).
 //
 // Operand layout (both operands K-major, no swizzle): 8 x 16-byte "core matrices"; element
 // (row, k) of a tile with K columns sits at (row / 8) * SBO + (k / 8) * 128 + (row % 8) * 16
@@ -153,19 +155,13 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
     const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
-    // operand descriptors of every MMA (fixed addresses); lane 0 of warp h issues half h
-    const int issue_h = warp & 1;
-    const uint64_t dA32 = sdesc(sm + kOffH + issue_h * kHBytes, kLbo, kSboK32);
-    const uint64_t dA64 = sdesc(sm + kOffH + issue_h * kHBytes, kLbo, kSboK64);
-    const uint64_t dW1 = sdesc(sm + kOffW1, kLbo, kSboK32), dW2 = sdesc(sm + kOffW2, kLbo, kSboK64);
-    const uint64_t dW3 = sdesc(sm + kOffW3, kLbo, kSboK64), dW4 = sdesc(sm + kOffW4, kLbo, kSboK64);
-    const uint64_t dB1 = sdesc(sm + kOffB1, kLbo, kSboK16), dB2 = sdesc(sm + kOffB2, kLbo, kSboK16);
-    const uint64_t dB3 = sdesc(sm + kOffB3, kLbo, kSboK16), dB4 = sdesc(sm + kOffB4, kLbo, kSboK16);
-    const uint64_t dOnes = sdesc(sm + kOffOnes, kLbo, kSboK16);
+    const int issue_h = warp & 1;   // lane 0 of warp h issues tile h's MMAs
 
     uint32_t phase = 0;
     int loaded = -1;
     bool abort = false;
+    uint32_t pnext[kHalves][16];               // inputs of this thread's next-step rows, as BF16x2
+    int pnext_asset[kHalves] = {-1, -1};       // the asset they were built for (-1: none)
     const uint32_t n_steps = (n + kRows - 1) / kRows;
     // row inputs of the next step are loaded one step ahead, so their latency overlaps the
     // current step's tensor-core chain
@@ -211,6 +207,7 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
             keep[h] = false;
             logit[h] = 0.0f;
         }
+        bool pre_done = false;
         // rows of different assets (at instance boundaries) are evaluated in separate passes,
         // each with that asset's weights
         for (;;) {
@@ -243,7 +240,10 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
 #pragma unroll
             for (int h = 0; h < kHalves; h++) {
                 uint32_t p[16];
-                if (mine[h]) {
+                if (mine[h] && pnext_asset[h] == cur) {
+#pragma unroll
+                    for (int k = 0; k < 16; k++) p[k] = pnext[h][k];
+                } else if (mine[h]) {
                     float f[32];
                     mlp_features(mlp_asset(a), ci[h].x, ci[h].y, ci[h].z, ci[h].w, m[h], f);
 #pragma unroll
@@ -270,15 +270,42 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
                 if (lane == 0 && warp < kHalves) {
                     tc_fence_after();
                     const uint32_t d = tmem + 64 * issue_h;
+                    const uint8_t* sH = sm + kOffH + issue_h * kHBytes;
+                    const uint64_t dOnes = sdesc(sm + kOffOnes, kLbo, kSboK16);
                     if (layer == 0)
-                        issue_layer(d, dA32, 2, dW1, dB1, dOnes, kIdescN64);
+                        issue_layer(d, sdesc(sH, kLbo, kSboK32), 2, sdesc(sm + kOffW1, kLbo, kSboK32),
+                                    sdesc(sm + kOffB1, kLbo, kSboK16), dOnes, kIdescN64);
                     else if (layer == 1)
-                        issue_layer(d, dA64, 4, dW2, dB2, dOnes, kIdescN64);
+                        issue_layer(d, sdesc(sH, kLbo, kSboK64), 4, sdesc(sm + kOffW2, kLbo, kSboK64),
+                                    sdesc(sm + kOffB2, kLbo, kSboK16), dOnes, kIdescN64);
                     else if (layer == 2)
-                        issue_layer(d, dA64, 4, dW3, dB3, dOnes, kIdescN64);
+                        issue_layer(d, sdesc(sH, kLbo, kSboK64), 4, sdesc(sm + kOffW3, kLbo, kSboK64),
+                                    sdesc(sm + kOffB3, kLbo, kSboK16), dOnes, kIdescN64);
                     else
-                        issue_layer(d, dA64, 4, dW4, dB4, dOnes, kIdescN16);
+                        issue_layer(d, sdesc(sH, kLbo, kSboK64), 4, sdesc(sm + kOffW4, kLbo, kSboK64),
+                                    sdesc(sm + kOffB4, kLbo, kSboK16), dOnes, kIdescN16);
                     mma_commit(mbar);
+                }
+                // the inputs of this thread's rows of the CTA's next step are built during the first
+                // layer's round trip (when they belong to the asset of this pass), once every row of
+                // this thread in the current step has had its inputs written (this pass or earlier)
+                if (layer == 0 && !pre_done && (mine[0] || !pending[0]) && (mine[1] || !pending[1])) {
+                    pre_done = true;
+                    const MlpAsset ma = mlp_asset(a);
+#pragma unroll
+                    for (int h = 0; h < kHalves; h++) {
+                        const uint32_t i_next = (step + gridDim.x) * kRows + h * 128 + tid;
+                        pnext_asset[h] = -1;
+                        if (step + gridDim.x < n_steps && i_next < n && __float_as_int(m_next[h].w) == cur) {
+                            const FrameInst& fr = fis[e_next[h].x];
+                            float f[32];
+                            mlp_features(ma, fr.cam_local[0], fr.cam_local[1], fr.cam_local[2], fr.dist_scale,
+                                         m_next[h], f);
+#pragma unroll
+                            for (int k = 0; k < 16; k++) pnext[h][k] = bf16x2(f[2 * k], f[2 * k + 1]);
+                            pnext_asset[h] = cur;
+                        }
+                    }
                 }
                 const bool done = mbar_wait(mbar, phase);
                 if (__syncthreads_or(!done)) { ok = false; break; }

@@ -56,26 +56,32 @@ def test_bf16_logits_match_oracle_cfg1():
         r.close()
 
 
-def test_bf16_multi_asset_tiles():
-    """Three assets, nine instances: tiles straddle instance and asset boundaries."""
+@pytest.mark.parametrize("side,ctas_per_sm", [(3, 0), (6, 1)])
+def test_bf16_multi_asset_tiles(side, ctas_per_sm):
+    """Three assets, side^2 instances: tiles straddle instance and asset boundaries.  With 36
+    instances (~90k rows) and one CTA per SM every CTA walks several steps, so the inputs built
+    ahead for a CTA's next step meet asset changes too."""
     assets = [scenes.torus_asset(3001, seed=1, sh_degree=0), scenes.sphere_asset(2500, 2, sh_degree=0),
               scenes.box_asset(1999, 3, sh_degree=0)]
     rng = np.random.default_rng(5)
     insts = []
-    for k in range(9):
+    for k in range(side * side):
         q, rr = np.linalg.qr(rng.standard_normal((3, 3)))
         q = q * np.sign(np.diag(rr))
         if np.linalg.det(q) < 0:
             q[:, 0] *= -1
         insts.append(scenes.Instance(k % 3, q.astype(np.float32),
-                                     np.array([(k % 3 - 1) * 2.5, (k // 3 - 1) * 2.5, 0], np.float32),
+                                     np.array([(k % side - (side - 1) / 2) * 2.5,
+                                               (k // side - (side - 1) / 2) * 2.5, 0], np.float32),
                                      float(np.float32(rng.uniform(0.6, 1.2)))))
     sc = scenes.Scene(assets, insts)
-    cam = scenes.look_at_camera((0.5, 1.0, 9.0), (0, 0, 0), 320, 240, 60.0)
+    cam = scenes.look_at_camera((0.5, 1.0, 3.0 * side), (0, 0, 0), 320, 240, 60.0)
     ws = [_weights(100 + k) for k in range(3)]
     r = renderer_for(sc, ws, precision=BF16)
     try:
-        lg, kp, st = r.query_visibility(cam, r.flags(use_mlp=1, mlp_gate=0))
+        lg, kp, st = r.query_visibility(cam, r.flags(use_mlp=1, mlp_gate=0, mlp_ctas_per_sm=ctas_per_sm))
+        if side == 6:
+            assert st["n_in_frustum"] > 148 * 256 * 2   # several 256-row steps per CTA
         osc = oracle.OracleScene(sc)
         inside, _ = oracle.frustum(osc, cam)
         # oracle logits per asset's own weights (one instance at a time)
