@@ -141,8 +141,16 @@ cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const flo
                              uint32_t* overflow, uint32_t* keys, uint32_t* values, int num_sms,
                              cudaStream_t s, LaunchLog* log) {
     if (n == 0) return cudaSuccess;
+    // a grid-stride kernel with equal shares per CTA: exactly the CTAs that are resident at once
+    // (a fraction of a second wave would run alone at the end)
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_duplicate, 256, 0);
+        if (e != cudaSuccess) return e;
+        per_sm = std::max(per_sm, 1);
+    }
     const uint32_t warps = (n + 31) / 32;
-    const uint32_t grid = std::min<uint32_t>((warps + 7) / 8, (uint32_t)num_sms * 8);
+    const uint32_t grid = std::min<uint32_t>((warps + 7) / 8, (uint32_t)(num_sms * per_sm));
     NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<<<grid, 256, 0, s>>>(order, rects, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, keys, values));
     return cudaGetLastError();
 }
