@@ -13,7 +13,8 @@
 // CUDA cores.  Conversions saturate (cvt .satfinite), so a value past its bound clamps to 448.
 //
 // Structure as in the BF16 kernel: one warpgroup per CTA, two 128-row tiles per step sharing each
-// MMA round trip, bounded mbarrier waits, multi-asset passes.  Operands are K-major without
+// MMA round trip, list entries loaded a step ahead, the next step's inputs built during the first
+// layer's round trip, bounded mbarrier waits, multi-asset passes.  Operands are K-major without
 // swizzle; an 8-bit core matrix is 8 rows x 16 elements, element (row, k) of a K-column tile at
 // (row / 8) * SBO + (k / 16) * 128 + (row % 8) * 16 + (k % 16), SBO = 8 K bytes.
 #include <algorithm>
@@ -145,6 +146,21 @@ k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
     int loaded = -1;
     bool abort = false;
     const uint32_t n_steps = (n + kRows - 1) / kRows;
+    uint4 qnext[kHalves][2];                   // E4M3 inputs of this thread's next-step rows
+    int qnext_asset[kHalves] = {-1, -1};       // the asset they were built for (-1: none)
+    // row inputs of the next step are loaded one step ahead
+    uint2 e_next[kHalves];
+    float4 m_next[kHalves];
+#pragma unroll
+    for (int h = 0; h < kHalves; h++) {
+        const uint32_t i = blockIdx.x * kRows + h * 128 + tid;
+        e_next[h] = make_uint2(0, 0);
+        m_next[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (blockIdx.x < n_steps && i < n) {
+            e_next[h] = __ldg(&list[i]);
+            m_next[h] = __ldg(&list_mean[i]);
+        }
+    }
     for (uint32_t step = blockIdx.x; step < n_steps && !abort; step += gridDim.x) {
         uint2 e[kHalves];
         float4 m[kHalves], ci[kHalves];
@@ -154,14 +170,16 @@ k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
 #pragma unroll
         for (int h = 0; h < kHalves; h++) {
             const uint32_t i = step * kRows + h * 128 + tid;
-            e[h] = make_uint2(0, 0);
-            m[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+            e[h] = e_next[h];
+            m[h] = m_next[h];
+            const uint32_t i_next = (step + gridDim.x) * kRows + h * 128 + tid;
+            if (step + gridDim.x < n_steps && i_next < n) {
+                e_next[h] = __ldg(&list[i_next]);
+                m_next[h] = __ldg(&list_mean[i_next]);
+            }
             ci[h] = make_float4(0.f, 0.f, 0.f, 0.f);
             gated[h] = false;
-            if (i < n) {
-                e[h] = __ldg(&list[i]);
-                m[h] = __ldg(&list_mean[i]);
-                // instance values the inputs need, loaded ahead of their use
+            if (i < n) {   // instance values the inputs need, loaded ahead of their use
                 const FrameInst& fr = fis[e[h].x];
                 ci[h] = make_float4(fr.cam_local[0], fr.cam_local[1], fr.cam_local[2], fr.dist_scale);
                 gated[h] = fr.gated != 0;
@@ -171,6 +189,7 @@ k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
             keep[h] = false;
             logit[h] = 0.0f;
         }
+        bool pre_done = false;
         for (;;) {
             int cand = min(pending[0] ? my_asset[0] : INT_MAX, pending[1] ? my_asset[1] : INT_MAX);
             cand = __reduce_min_sync(0xffffffffu, cand);
@@ -198,6 +217,12 @@ k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
             // ---- inputs -> A (E4M3, scaled by 256), one row per half
 #pragma unroll
             for (int h = 0; h < kHalves; h++) {
+                uint8_t* sA = sm + kOffH + h * kHBytes;
+                if (mine[h] && qnext_asset[h] == cur) {   // built during the previous step
+                    st_chunk(sA, kSboK32, tid, 0, qnext[h][0]);
+                    st_chunk(sA, kSboK32, tid, 1, qnext[h][1]);
+                    continue;
+                }
                 float f[32];
                 if (mine[h]) {
                     mlp_features(mlp_asset(a), ci[h].x, ci[h].y, ci[h].z, ci[h].w, m[h], f);
@@ -207,7 +232,6 @@ k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
 #pragma unroll
                     for (int k = 0; k < 32; k++) f[k] = 0.0f;
                 }
-                uint8_t* sA = sm + kOffH + h * kHBytes;
                 st_chunk(sA, kSboK32, tid, 0, pack16(f));
                 st_chunk(sA, kSboK32, tid, 1, pack16(f + 16));
             }
@@ -235,6 +259,29 @@ k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
                         }
                     }
                     mma_commit(mbar);
+                }
+                // the inputs of this thread's rows of the CTA's next step are built during the first
+                // layer's round trip (when they belong to the asset of this pass), once every row of
+                // this thread in the current step has had its inputs written (this pass or earlier)
+                if (layer == 0 && !pre_done && (mine[0] || !pending[0]) && (mine[1] || !pending[1])) {
+                    pre_done = true;
+                    const MlpAsset ma = mlp_asset(a);
+#pragma unroll
+                    for (int h = 0; h < kHalves; h++) {
+                        const uint32_t i_next = (step + gridDim.x) * kRows + h * 128 + tid;
+                        qnext_asset[h] = -1;
+                        if (step + gridDim.x < n_steps && i_next < n && __float_as_int(m_next[h].w) == cur) {
+                            const FrameInst& fr = fis[e_next[h].x];
+                            float f[32];
+                            mlp_features(ma, fr.cam_local[0], fr.cam_local[1], fr.cam_local[2], fr.dist_scale,
+                                         m_next[h], f);
+#pragma unroll
+                            for (int k = 0; k < 32; k++) f[k] *= kInScale;
+                            qnext[h][0] = pack16(f);
+                            qnext[h][1] = pack16(f + 16);
+                            qnext_asset[h] = cur;
+                        }
+                    }
                 }
                 const bool done = mbar_wait(mbar, phase);
                 if (__syncthreads_or(!done)) { ok = false; break; }
