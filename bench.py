@@ -32,6 +32,64 @@ METRIC = "ms/frame 1080p composed scene, MLP-culled vs unculled; PSNR ≥45 dB v
 UNIT = "ms/frame"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
+# DRAM bytes per unit of work of the profiled kernels, from one ncu capture each, with the hash of
+# the sources the capture was made from (a kernel changed since then reports traffic null)
+TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "dram_traffic_per_unit.md")
+CSRC = os.path.join(ROOT, "paper_2511_19202_b300", "csrc")
+KERNEL_SOURCES = {
+    "k_mlp_tc": ["k_mlp_tc.cu", "mlp_common.cuh", "tc_common.cuh", "nvgs_internal.cuh"],
+    "k_mlp_f8": ["k_mlp_f8.cu", "mlp_common.cuh", "tc_common.cuh", "nvgs_internal.cuh"],
+    "k_blend<16>": ["k_blend.cu", "nvgs_internal.cuh"],
+    "k_rs_scatter<u32>": ["k_sort.cu", "nvgs_internal.cuh"],
+    "k_rs_hist<u32>": ["k_sort.cu", "nvgs_internal.cuh"],
+    "k_project": ["k_project.cu", "nvgs_internal.cuh"],
+    "k_duplicate": ["k_bin.cu", "nvgs_internal.cuh"],
+}
+
+
+def kernel_units(name, fr):
+    """Units of work of kernel `name` in one frame (its traffic is taken to scale with them)."""
+    if name in ("k_mlp_tc", "k_mlp_f8"):
+        return fr["n_mlp_queries"]
+    if name.startswith("k_blend") or name == "k_duplicate":
+        return fr["n_pairs"]
+    if name == "k_project":
+        return fr["n_survivors"]
+    if name.startswith("k_rs_"):                       # item-passes: 4 depth, the rest tile passes
+        dp = 4 if fr["n_survivors"] > 1 else 0
+        return dp * fr["n_survivors"] + max(0, fr["sort_passes"] - dp) * fr["n_pairs"]
+    return None
+
+
+def sources_hash(name):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(name, []):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic_per_launch(name, frames, launches):
+    """ncu DRAM bytes (read + write) per launch of `name` over `frames`, scaled from the captured
+    bytes per unit; None if the kernel has no capture or its sources changed since."""
+    if name not in KERNEL_SOURCES or not os.path.exists(TRAFFIC_TABLE):
+        return None
+    with open(TRAFFIC_TABLE) as f:
+        for line in f:
+            cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 4 and cells[0] == name:
+                try:
+                    per_unit = float(cells[2])
+                except ValueError:
+                    return None
+                if cells[3] != sources_hash(name):
+                    return None
+                units = [kernel_units(name, fr) for fr in frames]
+                if any(u is None for u in units):
+                    return None
+                return per_unit * float(sum(units)) / max(1, launches)
+    return None
 SAMPLE_ROWS = 8
 
 
@@ -41,9 +99,11 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", choices=["composed", "small", "large", "multiview", "backward"],
+    p.add_argument("--config", choices=["composed", "medium", "small", "large", "multiview", "backward"],
                    default="composed",
                    help="composed: 16 x 500k assets, 64 instances, 1080p (the headline workload); "
+                        "medium: the composed scene with 8 of its 64 instances (a few GB on the "
+                        "device: the case the kernel profiles capture); "
                         "small: one 20k torus at 256^2; large: 8 x 1M assets, 200 instances "
                         "(200M instanced Gaussians) at 3840x2160; multiview: 256 views of mixed "
                         "resolution through the sync-free batch and its CUDA graph, plus the "
@@ -70,6 +130,11 @@ def workload(config):
         cams = [scenes.config2_camera(f) for f in range(120)]
         desc = ("composed scene: 16 assets x 500k Gaussians (sphere/torus/box), 64 instances, "
                 "SH degree 3, 1920x1080, 16x16 tiles, 120-frame orbit")
+    elif config == "medium":
+        sc = scenes.config2_scene(n_instances=8)
+        cams = [scenes.config2_camera(f) for f in range(120)]
+        desc = ("composed scene, first 8 of its 64 instances (4M instanced Gaussians): 16 assets x "
+                "500k Gaussians, SH degree 3, 1920x1080, 16x16 tiles, 120-frame orbit")
     elif config == "large":
         sc = scenes.config5_scene()
         cams = [scenes.config5_camera(f) for f in range(120)]
@@ -370,7 +435,8 @@ def run_ours(args, rank, world):
     graph_plain, same_p = graph_time(mk_plain, 1, args.steps)
     graph_info = {"culled_ms_per_frame_graph": graph_culled, "unculled_ms_per_frame_graph": graph_plain,
                   "graph_images_equal_sync": same_c and same_p, "max_pairs": max_pairs}
-    if args.config != "large":   # eight 4K views or 8-pixel tiles would need tens of GB more pairs
+    if args.config == "composed":   # (large: eight 4K views or 8-pixel tiles would need tens of GB
+                                    # more pairs; medium: kept to the per-frame path it profiles)
         batch8_culled, same_b = graph_time(mk_culled, 8, max(8, args.steps))
         tune_cams = [cams[f] for f in (64, 72, 80, 88)] if len(cams) >= 120 else cams[:1]
         tune_out = [torch.empty((c.height, c.width, 3), dtype=torch.float32, device=f"cuda:{dev}")
@@ -420,7 +486,9 @@ def run_ours(args, rank, world):
         achieved = work / (tot_ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6400.0)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s"}
-    roof.update({"frac": achieved / peak, "traffic": None, "kernel": name,
+    roof.update({"frac": achieved / peak, "traffic": dram_traffic_per_launch(name, st_prof, n_launch),
+                 "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled by units of work)",
+                 "kernel": name,
                  "avg_launch_ms": avg_ms,
                  "peak_source": (peak_src if bound != "alu" else
                                  "derived: 148 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock"),
@@ -457,6 +525,9 @@ def run_ours(args, rank, world):
                    "mean_survivors": mean("n_survivors", st_culled),
                    "mean_pairs": mean("n_pairs", st_culled),
                    "mean_pairs_unculled": mean("n_pairs", st_plain),
+                   "first_timed_frames": [{k: int(fr[k]) for k in ("n_in_frustum", "n_mlp_queries",
+                                                                  "n_survivors", "n_pairs", "sort_passes")}
+                                          for fr in st_culled[:3]],
                    "gaussians_per_s": st_culled[0]["n_instanced"] / (value * 1e-3),
                    "kernels_ms_per_frame": kernels,
                    "sync_free": graph_info,
