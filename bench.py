@@ -34,7 +34,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
 # DRAM bytes per unit of work of the profiled kernels, from one ncu capture each, with the hash of
 # the sources the capture was made from (a kernel changed since then reports traffic null)
-TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "dram_traffic_per_unit.md")
+TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "dram_traffic_per_unit.txt")
 CSRC = os.path.join(ROOT, "paper_2511_19202_b300", "csrc")
 KERNEL_SOURCES = {
     "k_mlp_tc": ["k_mlp_tc.cu", "mlp_common.cuh", "tc_common.cuh", "nvgs_internal.cuh"],
