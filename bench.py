@@ -477,8 +477,13 @@ def run_ours(args, rank, world):
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s"}
     elif bound == "alu":
         achieved = work / (tot_ms * 1e-3) / 1e12
-        mhz = clk.get("sm_max_mhz") or 2032.0
-        peak = 148 * 128 * 2 * mhz * 1e6 / 1e12   # FP32 lanes x FMA x max SM clock
+        try:   # FP32 FMA throughput measured on this GPU now (independent FMA chains on every SM)
+            peak = N.nvgs_measure_fp32_fma(dev)
+            alu_src = "measured in this run: FP32 FMA throughput kernel (nvgs_measure_fp32_fma)"
+        except Exception:
+            mhz = clk.get("sm_max_mhz") or 2032.0
+            peak = 148 * 128 * 2 * mhz * 1e6 / 1e12   # FP32 lanes x FMA x max SM clock
+            alu_src = "derived: 148 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock"
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "evaluations_per_frame": float(np.mean([s_["blend_evaluations"] for s_ in st_prof])),
                 "flops_per_evaluation": BLEND_FLOPS_PER_EVAL}
@@ -490,8 +495,7 @@ def run_ours(args, rank, world):
                  "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled by units of work)",
                  "kernel": name,
                  "avg_launch_ms": avg_ms,
-                 "peak_source": (peak_src if bound != "alu" else
-                                 "derived: 148 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock"),
+                 "peak_source": (peak_src if bound != "alu" else alu_src),
                  "algorithmic_per_launch": per_launch})
     kernels = {k: {"launches": v[0], "ms_per_frame": v[1] / len(st_culled)}
                for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])}

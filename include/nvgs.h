@@ -387,6 +387,21 @@ nvgs_status nvgs_sort_pairs(nvgs_ctx* ctx, uint64_t* keys, uint32_t* values, int
 nvgs_status nvgs_sort_pairs_noalloc(uint64_t* keys, uint32_t* values, int64_t n, int key_bits,
                                     void* cuda_stream);
 
+/* Self-test of the failure path of the bounded device-side waits (a library service; the paper
+ * has no counterpart).  On `device`, one warp waits on an mbarrier that nothing arrives on, with
+ * the helper the tensor-core MLP kernels use for their mbarrier waits (bounded by an iteration
+ * count and by one second of the GPU's global timer).  Returns NVGS_OK if the wait gave up, the
+ * kernel recorded it and returned; seconds_waited (HOST, nullable) receives how long it waited.
+ * NVGS_ERR_INVALID_ARG for a bad device, NVGS_ERR_CUDA if a CUDA call failed or the wait did not
+ * give up.  Blocks the calling thread for about a second; no fault, trap or hang is involved. */
+nvgs_status nvgs_selftest_wait_timeout(int device, double* seconds_waited);
+
+/* Measured FP32 FMA throughput of `device` in TFLOP/s (HOST *tflops; a fused multiply-add counts
+ * as 2 flops): a kernel of independent FMA chains on every SM, timed with CUDA events after a
+ * warm-up launch (~20 ms).  The compositing kernel's ALU roofline is quoted against it.  Returns
+ * NVGS_ERR_INVALID_ARG for a bad device or NULL tflops, NVGS_ERR_CUDA if a CUDA call failed. */
+nvgs_status nvgs_measure_fp32_fma(int device, double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

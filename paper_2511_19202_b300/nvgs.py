@@ -122,7 +122,8 @@ EXPORTS = ("nvgs_create", "nvgs_destroy", "nvgs_last_error", "nvgs_get_stream", 
            "nvgs_sort_pairs_noalloc", "nvgs_label_visibility", "nvgs_train_init",
            "nvgs_train_visibility_step", "nvgs_train_get_weights", "nvgs_lr_schedule",
            "nvgs_get_asset_info", "nvgs_training_views", "nvgs_render_backward",
-           "nvgs_update_asset", "nvgs_render_batch", "nvgs_autotune", "nvgs_device_bytes")
+           "nvgs_update_asset", "nvgs_render_batch", "nvgs_autotune", "nvgs_device_bytes",
+           "nvgs_selftest_wait_timeout", "nvgs_measure_fp32_fma")
 NVGS_SORT_NOALLOC_MAX_PAIRS = 1 << 20
 
 
@@ -151,6 +152,8 @@ def _load():
     L.nvgs_kernel_stats.argtypes = [vp, vp, C.c_int, P(C.c_int)]
     L.nvgs_reset_kernel_stats.argtypes = [vp]
     L.nvgs_sort_pairs_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int, vp]
+    L.nvgs_selftest_wait_timeout.argtypes = [C.c_int, P(C.c_double)]
+    L.nvgs_measure_fp32_fma.argtypes = [C.c_int, P(C.c_double)]
     L.nvgs_label_visibility.argtypes = [vp, C.c_int, vp, C.c_int, C.c_int, P(RenderFlags), vp]
     L.nvgs_train_init.argtypes = [vp, C.c_int, vp, vp, C.c_int]
     L.nvgs_train_visibility_step.argtypes = [vp, C.c_int, P(TrainBatch), P(AdamCfg), P(C.c_float)]
@@ -333,6 +336,21 @@ def nvgs_sort_pairs_noalloc(keys, values, n: int, key_bits: int, stream=None) ->
     callers can test the capacity error."""
     s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
     return lib.nvgs_sort_pairs_noalloc(_ptr(keys), _ptr(values), int(n), int(key_bits), s)
+
+
+def nvgs_selftest_wait_timeout(device: int = 0):
+    """(status, seconds waited) of the bounded-wait self-test (NVGS_OK: the wait gave up as it
+    must, the kernel returned)."""
+    sec = C.c_double(0.0)
+    st = lib.nvgs_selftest_wait_timeout(int(device), C.byref(sec))
+    return st, sec.value
+
+
+def nvgs_measure_fp32_fma(device: int = 0) -> float:
+    """Measured FP32 FMA throughput of the device, TFLOP/s."""
+    t = C.c_double(0.0)
+    _check(None, lib.nvgs_measure_fp32_fma(int(device), C.byref(t)))
+    return t.value
 
 
 def _cam_array(cams):
