@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(128) k_project_bwd(const uint2* __restrict__ s
     const AssetDev& a = assets[fi.asset];
     const uint32_t g = e.y;
     const float4 m = a.mean_op[g];
-    const float4 ls = a.scale[g];
-    const float4 qr = a.quat[g];
+    const float4 ls = a.scale_quat[2 * (size_t)g];
+    const float4 qr = a.scale_quat[2 * (size_t)g + 1];
     // ---- forward recomputation (as in k_project)
     const float3 pc = cam_point(fi, m.x, m.y, m.z);
     const float x = pc.x, y = pc.y, z = pc.z;
@@ -332,25 +332,25 @@ size_t render_backward_scratch_bytes(uint64_t n_surv) { return (size_t)(n_surv *
 __global__ void k_pack_asset(uint32_t n, int K, int stride, const float* __restrict__ means,
                              const float* __restrict__ log_scales, const float* __restrict__ quats,
                              const float* __restrict__ opacity_logits, const float* __restrict__ sh,
-                             float4* __restrict__ mean_op, float4* __restrict__ scale,
-                             float4* __restrict__ quat, float* __restrict__ sh_out) {
+                             float4* __restrict__ mean_op, float4* __restrict__ scale_quat,
+                             float* __restrict__ sh_out) {
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     mean_op[g] = make_float4(means[3 * (size_t)g], means[3 * (size_t)g + 1], means[3 * (size_t)g + 2],
                              opacity_logits[g]);
-    scale[g] = make_float4(log_scales[3 * (size_t)g], log_scales[3 * (size_t)g + 1],
-                           log_scales[3 * (size_t)g + 2], 0.0f);
-    quat[g] = make_float4(quats[4 * (size_t)g], quats[4 * (size_t)g + 1], quats[4 * (size_t)g + 2],
-                          quats[4 * (size_t)g + 3]);
+    scale_quat[2 * (size_t)g] = make_float4(log_scales[3 * (size_t)g], log_scales[3 * (size_t)g + 1],
+                                            log_scales[3 * (size_t)g + 2], 0.0f);
+    scale_quat[2 * (size_t)g + 1] = make_float4(quats[4 * (size_t)g], quats[4 * (size_t)g + 1],
+                                                quats[4 * (size_t)g + 2], quats[4 * (size_t)g + 3]);
     for (int k = 0; k < 3 * K; k++) sh_out[(size_t)g * stride + k] = sh[(size_t)g * 3 * K + k];
 }
 
 cudaError_t launch_pack_asset(uint32_t n, int K, int stride, const float* means, const float* log_scales,
                               const float* quats, const float* opacity_logits, const float* sh,
-                              float4* mean_op, float4* scale, float4* quat, float* sh_out,
+                              float4* mean_op, float4* scale_quat, float* sh_out,
                               cudaStream_t s, LaunchLog* log) {
     if (n == 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_pack_asset", k_pack_asset<<<(n + 255) / 256, 256, 0, s>>>(n, K, stride, means, log_scales, quats, opacity_logits, sh, mean_op, scale, quat, sh_out));
+    NVGS_LAUNCH(log, s, "k_pack_asset", k_pack_asset<<<(n + 255) / 256, 256, 0, s>>>(n, K, stride, means, log_scales, quats, opacity_logits, sh, mean_op, scale_quat, sh_out));
     return cudaGetLastError();
 }
 

@@ -33,8 +33,8 @@ __global__ void __launch_bounds__(256, 4) k_project(const uint2* __restrict__ su
         const AssetDev& a = assets[fi.asset];
         const uint32_t g = e.y;
         const float4 m = __ldg(&a.mean_op[g]);
-        const float4 ls = __ldg(&a.scale[g]);
-        const float4 qr = __ldg(&a.quat[g]);
+        const float4 ls = __ldg(&a.scale_quat[2 * (size_t)g]);
+        const float4 qr = __ldg(&a.scale_quat[2 * (size_t)g + 1]);
 
         const float3 pc = cam_point(fi, m.x, m.y, m.z);
         const float x = pc.x, y = pc.y, z = pc.z;

@@ -23,7 +23,7 @@ struct DevBuf {
 };
 
 struct AssetStore {
-    DevBuf mean_op, scale, quat, sh, w_fp32, w_tc, w_f8;
+    DevBuf mean_op, scale_quat, sh, w_fp32, w_tc, w_f8;
     AssetDev dev{};
     int precision = -1;  // -1: no MLP
 };
@@ -446,7 +446,7 @@ extern "C" nvgs_status nvgs_destroy(nvgs_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     for (auto& a : ctx->assets) {
-        release(a.mean_op); release(a.scale); release(a.quat); release(a.sh);
+        release(a.mean_op); release(a.scale_quat); release(a.sh);
         release(a.w_fp32); release(a.w_tc); release(a.w_f8);
     }
     DevBuf* bufs[] = {&ctx->assets_dev, &ctx->inst_raw, &ctx->inst_offset, &ctx->chunks,
@@ -504,7 +504,7 @@ extern "C" nvgs_status nvgs_load_asset(nvgs_ctx* ctx, const nvgs_asset_desc* d, 
     };
     CK(fetch(mh, d->means)); CK(fetch(lh, d->log_scales)); CK(fetch(qh, d->quats));
     CK(fetch(oh, d->opacity_logits)); CK(fetch(sh, d->sh));
-    std::vector<float4> m4(n), s4(n), q4(n);
+    std::vector<float4> m4(n), sq4(2 * (size_t)n);
     std::vector<float> shp((size_t)n * stride, 0.0f);
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int64_t g = 0; g < n; g++) {
@@ -515,19 +515,18 @@ extern "C" nvgs_status nvgs_load_asset(nvgs_ctx* ctx, const nvgs_asset_desc* d, 
             hi[k] = std::max(hi[k], v);
         }
         m4[g] = make_float4(mh[3 * g], mh[3 * g + 1], mh[3 * g + 2], oh[g]);
-        s4[g] = make_float4(lh[3 * g], lh[3 * g + 1], lh[3 * g + 2], 0.0f);
-        q4[g] = make_float4(qh[4 * g], qh[4 * g + 1], qh[4 * g + 2], qh[4 * g + 3]);
+        sq4[2 * g] = make_float4(lh[3 * g], lh[3 * g + 1], lh[3 * g + 2], 0.0f);
+        sq4[2 * g + 1] = make_float4(qh[4 * g], qh[4 * g + 1], qh[4 * g + 2], qh[4 * g + 3]);
         memcpy(&shp[(size_t)g * stride], &sh[(size_t)g * 3 * K], 3 * K * sizeof(float));
     }
     AssetStore as;
-    CK(ensure(as.mean_op, n * 16)); CK(ensure(as.scale, n * 16)); CK(ensure(as.quat, n * 16));
+    CK(ensure(as.mean_op, n * 16)); CK(ensure(as.scale_quat, n * 32));
     CK(ensure(as.sh, (size_t)n * stride * 4));
     CK(cudaMemcpy(as.mean_op.p, m4.data(), n * 16, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(as.scale.p, s4.data(), n * 16, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(as.quat.p, q4.data(), n * 16, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(as.scale_quat.p, sq4.data(), n * 32, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(as.sh.p, shp.data(), (size_t)n * stride * 4, cudaMemcpyHostToDevice));
     AssetDev& a = as.dev;
-    a.mean_op = P<float4>(as.mean_op); a.scale = P<float4>(as.scale); a.quat = P<float4>(as.quat);
+    a.mean_op = P<float4>(as.mean_op); a.scale_quat = P<float4>(as.scale_quat);
     a.sh = P<float>(as.sh);
     a.w_fp32 = nullptr; a.w_tc = nullptr; a.w_f8 = nullptr;
     a.n = n; a.sh_degree = d->sh_degree; a.sh_stride = stride;
@@ -1293,7 +1292,7 @@ extern "C" nvgs_status nvgs_device_bytes(const nvgs_ctx* ctx, uint64_t* bytes) {
     if (!ctx || !bytes) return NVGS_ERR_INVALID_ARG;
     uint64_t t = 0;
     for (auto& a : ctx->assets)
-        for (const DevBuf* b : {&a.mean_op, &a.scale, &a.quat, &a.sh, &a.w_fp32, &a.w_tc, &a.w_f8}) t += b->cap;
+        for (const DevBuf* b : {&a.mean_op, &a.scale_quat, &a.sh, &a.w_fp32, &a.w_tc, &a.w_f8}) t += b->cap;
     const DevBuf* bufs[] = {&ctx->assets_dev, &ctx->inst_raw, &ctx->inst_offset, &ctx->chunks,
                             &ctx->frame_inst, &ctx->bits, &ctx->chunk_counts, &ctx->chunk_offsets,
                             &ctx->vis_list, &ctx->keep_bits, &ctx->logits_tmp, &ctx->block_counts,
@@ -1349,7 +1348,7 @@ extern "C" nvgs_status nvgs_update_asset(nvgs_ctx* ctx, int asset_id, const floa
     ctx->kept_frame = false;
     begin_frame_log_only(ctx);
     CK(launch_pack_asset((uint32_t)a.dev.n, K, a.dev.sh_stride, means, log_scales, quats, opacity_logits,
-                         sh, P<float4>(a.mean_op), P<float4>(a.scale), P<float4>(a.quat), P<float>(a.sh),
+                         sh, P<float4>(a.mean_op), P<float4>(a.scale_quat), P<float>(a.sh),
                          ctx->stream, &ctx->log));
     return NVGS_OK;
 }

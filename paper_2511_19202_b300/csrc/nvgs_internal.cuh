@@ -17,8 +17,8 @@ constexpr int kChunkWords = kChunk / 32;
 // One asset in device memory (structure of arrays of 16-byte vectors).
 struct AssetDev {
     const float4* mean_op;    // (x, y, z, opacity logit)
-    const float4* scale;      // (log sx, log sy, log sz, 0)
-    const float4* quat;       // (w, x, y, z)
+    const float4* scale_quat; // per Gaussian (log sx, log sy, log sz, 0) then (w, x, y, z): the
+                              // 32 bytes the projection reads together, one sector
     const float* sh;          // n * sh_stride floats, coefficient-major, RGB innermost
     const float* w_fp32;      // visibility MLP, kMlpWeights floats (nullptr: no MLP)
     const uint8_t* w_tc;      // BF16 operand tiles for the tcgen05 MLP (nullptr: none)
@@ -379,7 +379,7 @@ cudaError_t launch_render_backward(const uint32_t* ranges, const uint32_t* value
                                    cudaStream_t s, LaunchLog* log);
 cudaError_t launch_pack_asset(uint32_t n, int K, int stride, const float* means, const float* log_scales,
                               const float* quats, const float* opacity_logits, const float* sh,
-                              float4* mean_op, float4* scale, float4* quat, float* sh_out,
+                              float4* mean_op, float4* scale_quat, float* sh_out,
                               cudaStream_t s, LaunchLog* log);
 
 }  // namespace nvgs
