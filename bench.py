@@ -115,6 +115,9 @@ def parse():
     p.add_argument("--train-dirs", type=int, default=256)
     p.add_argument("--train-steps", type=int, default=1000)
     p.add_argument("--train-res", type=int, default=512)
+    p.add_argument("--radius-clip", type=float, default=0.0,
+                   help="radius clipping (Sec. 4.4) on the culled pass: drop splats whose 1-sigma "
+                        "ellipse is below this many px^2 (0: off; lossy, reported by the PSNR)")
     p.add_argument("--psnr-target", type=float, default=48.0,
                    help="calibration target (dB) for the logit threshold on held-out orbit frames")
     p.add_argument("--precision", choices=["bf16", "fp32", "fp8"], default="bf16",
@@ -341,7 +344,7 @@ def run_ours(args, rank, world):
             if min(ps) >= args.psnr_target:
                 tau = cand
                 break
-    culled = r.flags(use_mlp=1, mlp_gate=1, tile_size=tile, logit_threshold=tau)
+    culled = r.flags(use_mlp=1, mlp_gate=1, tile_size=tile, logit_threshold=tau, radius_clip_area=args.radius_clip)
     stream = r.stream
 
     my_frames = replica_frames(rank, world, max(args.steps, args.warmup, 8), len(cams))
@@ -401,7 +404,7 @@ def run_ours(args, rank, world):
 
     # e2e through the C ABI with a host image (device->host copy inside the timed region)
     host = torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True)
-    e2e_flags = r.flags(use_mlp=1, mlp_gate=1, tile_size=tile, logit_threshold=tau)
+    e2e_flags = r.flags(use_mlp=1, mlp_gate=1, tile_size=tile, logit_threshold=tau, radius_clip_area=args.radius_clip)
     t0 = time.perf_counter()
     for k in range(args.steps):
         r.render_host(frame(k), e2e_flags, host)
@@ -429,7 +432,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         return g0.elapsed_time(g1) / (calls * views_per_call), same
 
-    mk_culled = lambda: r.flags(use_mlp=1, mlp_gate=1, tile_size=tile, logit_threshold=tau)
+    mk_culled = lambda: r.flags(use_mlp=1, mlp_gate=1, tile_size=tile, logit_threshold=tau, radius_clip_area=args.radius_clip)
     mk_plain = lambda: r.flags(use_mlp=0, tile_size=tile)
     graph_culled, same_c = graph_time(mk_culled, 1, args.steps)
     graph_plain, same_p = graph_time(mk_plain, 1, args.steps)
@@ -513,7 +516,7 @@ def run_ours(args, rank, world):
                             "fp32": "FP32 CUDA cores"}[args.precision]),
                    "l2": "no flush: the assets (1.9 GB or more) and per-frame buffers exceed the 126 MB L2",
                    "mlp_training": train_info,
-                   "logit_threshold": tau,
+                   "logit_threshold": tau, "radius_clip_area": args.radius_clip,
                    "threshold_calibration_min_psnr_db": calib,
                    "unculled_ms_per_frame": plain_ms,
                    "culled_ms_median_p95": [float(np.median([x["frame_ms"] for x in st_culled])),

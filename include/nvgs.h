@@ -114,7 +114,11 @@ typedef struct {
                                     mean pairs per tile); < 0: never; else >= 256) */
     int32_t mlp_ctas_per_sm;     /* resident CTAs per SM of the tensor-core MLP (0: default 3;
                                     1..3) -- a tuning knob, results do not depend on it */
-    int32_t reserved[5];
+    float radius_clip_area;      /* radius clipping (Sec. 4.4), lossy: a splat whose 1-sigma
+                                    ellipse is smaller than this many px^2, i.e. whose
+                                    pi sqrt(det Sigma_2D) (dilation included) is below it, is not
+                                    binned.  0 (default): off.  >= 0 */
+    int32_t reserved[4];
 } nvgs_render_flags;
 
 #define NVGS_NUM_STAGES 8

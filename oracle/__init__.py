@@ -70,7 +70,8 @@ class OrOpts(C.Structure):
                 ("dilation", C.c_double), ("guard_band", C.c_double), ("bg", C.c_double * 3),
                 ("tile_size", C.c_int32), ("pad_", C.c_int32), ("eps_alpha", C.c_double),
                 ("eps_t", C.c_double), ("eps_depth", C.c_double), ("eps_frustum", C.c_double),
-                ("eps_px", C.c_double), ("swap_tol", C.c_double)]
+                ("eps_px", C.c_double), ("swap_tol", C.c_double),
+                ("radius_clip_area", C.c_double), ("eps_clip", C.c_double)]
 
 
 SPLAT_DTYPE = np.dtype([
@@ -132,8 +133,10 @@ def _ptr(a):
 # ----------------------------------------------------------------------------- options
 def opts(alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4, dilation=0.3, guard_band=1.3,
          bg=(0.0, 0.0, 0.0), tile_size=16, eps_alpha=2e-4, eps_t=2e-4, eps_depth=4e-7,
-         eps_frustum=1e-6, eps_px=1e-3, swap_tol=5e-4) -> OrOpts:
-    """Blending constants of Sec. 4.1 and the 3DGS conventions, plus ambiguity-band widths."""
+         eps_frustum=1e-6, eps_px=1e-3, swap_tol=5e-4, radius_clip_area=0.0,
+         eps_clip=1e-3) -> OrOpts:
+    """Blending constants of Sec. 4.1 and the 3DGS conventions, radius clipping (Sec. 4.4; 0:
+    off), plus ambiguity-band widths."""
     o = OrOpts()
     o.alpha_min, o.alpha_max, o.t_stop = alpha_min, alpha_max, t_stop
     o.dilation, o.guard_band = dilation, guard_band
@@ -141,6 +144,7 @@ def opts(alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4, dilation=0.3, guard
     o.tile_size = int(tile_size)
     o.eps_alpha, o.eps_t, o.eps_depth = eps_alpha, eps_t, eps_depth
     o.eps_frustum, o.eps_px, o.swap_tol = eps_frustum, eps_px, swap_tol
+    o.radius_clip_area, o.eps_clip = radius_clip_area, eps_clip
     return o
 
 

@@ -83,6 +83,9 @@ typedef struct {
     double eps_frustum;    /* |margin| <= eps_frustum * z */
     double eps_px;         /* support bounding box within eps_px pixels of a pixel/tile edge */
     double swap_tol;       /* a near-tie in depth only counts if swapping changes a channel by more */
+    double radius_clip_area; /* Sec. 4.4 radius clipping: drop a splat whose 1-sigma ellipse area
+                                pi sqrt(det Sigma_2D) is below this (px^2); 0: off */
+    double eps_clip;       /* |det - threshold| <= eps_clip * threshold: the clip decision is ambiguous */
 } or_opts;
 
 typedef struct {
@@ -444,11 +447,21 @@ static void project_one(const or_asset* a, const or_instance* in, const or_camer
     for (int k = 0; k < 3; k++) dir[k] /= nrm;
     sh_color(a, g, dir, sp->rgb);
 
+    /* radius clipping (Sec. 4.4): the 1-sigma ellipse {d : d^T Sigma_2D^-1 d <= 1} has area
+       pi sqrt(det Sigma_2D); below the given area the splat is dropped */
+    int clipped = 0;
+    if (o->radius_clip_area > 0.0) {
+        double thr = o->radius_clip_area / OR_PI;
+        thr *= thr;
+        clipped = det < thr;
+        if (fabs(det - thr) <= o->eps_clip * thr) amb = 1;
+    }
+
     /* exact support: {d : d^T conic d <= 2 ln(255 o)}; its bounding box */
     double kk = 2.0 * log(sp->opacity / o->alpha_min);
     if (fabs(sp->opacity - o->alpha_min) <= o->eps_alpha * o->alpha_min) amb = 1;
-    int valid = inside && keep && kk > 0.0;
-    if (kk > 0.0) {
+    int valid = inside && keep && kk > 0.0 && !clipped;
+    if (kk > 0.0 && !clipped) {
         sp->x_ext = sqrt(kk * ca);
         sp->y_ext = sqrt(kk * cc);
         double lo_x = sp->u - sp->x_ext - 0.5, hi_x = sp->u + sp->x_ext - 0.5;

@@ -79,8 +79,10 @@ __global__ void __launch_bounds__(256, 4) k_project(const uint2* __restrict__ su
         const float xe = sqrtf(kk * ca), ye = sqrtf(kk * cc);
         const float cA = cc / det, cB = -cb / det, cC = ca / det;   // conic, as stored
         const float kw = -0.5f * kk;                                  // stored ln(alpha_min / o)
-        // non-finite geometry (degenerate input) is never binned
-        if (kk > 0.0f && det > 0.0f && isfinite(u) && isfinite(v) && isfinite(xe) &&
+        // non-finite geometry (degenerate input) is never binned; neither is a splat that radius
+        // clipping (Sec. 4.4) drops by the determinant of its 2D covariance
+        const bool clipped = cam.clip_det > 0.0f && det < cam.clip_det;
+        if (kk > 0.0f && det > 0.0f && !clipped && isfinite(u) && isfinite(v) && isfinite(xe) &&
             isfinite(ye) && isfinite(det)) {
             float x0 = fmaxf(ceilf(u - xe - 0.5f), 0.0f);
             float x1 = fminf(floorf(u + xe - 0.5f), (float)(cam.W - 1));

@@ -152,6 +152,8 @@ nvgs_status validate_flags(nvgs_ctx* ctx, const nvgs_render_flags* f) {
         return fail(ctx, NVGS_ERR_INVALID_ARG, "blending constants out of range");
     if (f->mlp_ctas_per_sm < 0 || f->mlp_ctas_per_sm > 3)
         return fail(ctx, NVGS_ERR_INVALID_ARG, "mlp_ctas_per_sm must be 0..3");
+    if (!(f->radius_clip_area >= 0.0f) || !std::isfinite(f->radius_clip_area))
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "radius_clip_area must be a finite value >= 0");
     if (f->profile < 0 || f->profile > 2)
         return fail(ctx, NVGS_ERR_INVALID_ARG, "profile must be 0, 1 or 2");
     if (f->blend_split_len > 0 && f->blend_split_len < 256)
@@ -187,6 +189,9 @@ nvgs_status make_cam(nvgs_ctx* ctx, const nvgs_camera* c, const nvgs_render_flag
     p.tiles_x = (c->width + f->tile_size - 1) / f->tile_size;
     p.tiles_y = (c->height + f->tile_size - 1) / f->tile_size;
     p.mlp_gate = f->mlp_gate ? 1 : 0;
+    // the 1-sigma ellipse of Sigma_2D has area pi sqrt(det): area < A  <=>  det < (A / pi)^2
+    const double clip = (double)f->radius_clip_area / 3.14159265358979323846;
+    p.clip_det = (float)(clip * clip);
     *cp = p;
     return NVGS_OK;
 }

@@ -70,6 +70,7 @@ struct CamParams {
     float bg[3];
     int tile_size, tiles_x, tiles_y;
     int mlp_gate;             // 1: instances closer than d_min bypass the MLP
+    float clip_det;           // radius clipping: splats with det Sigma_2D below it are not binned (0: off)
 };
 
 // Real spherical harmonics up to degree 3 (the 3DGS sign convention), Y[(l+1)^2].

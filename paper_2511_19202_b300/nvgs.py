@@ -57,7 +57,8 @@ class RenderFlags(C.Structure):
                 ("tile_size", C.c_int32), ("image_memory", C.c_int32), ("profile", C.c_int32),
                 ("logits_override", C.c_void_p), ("keep_outputs", C.c_int32),
                 ("blend_split_len", C.c_int32), ("mlp_ctas_per_sm", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("radius_clip_area", C.c_float),
+                ("reserved", C.c_int32 * 4)]
 
 
 class FrameStats(C.Structure):

@@ -22,7 +22,8 @@ def gpu_image(r, cam, **flags):
 def oracle_opts_for(flags: dict, **eps):
     return oracle.opts(alpha_min=flags.get("alpha_min", 1 / 255), alpha_max=flags.get("alpha_max", 0.99),
                        t_stop=flags.get("t_stop", 1e-4), bg=flags.get("bg", (0, 0, 0)),
-                       tile_size=flags.get("tile_size", 16), **eps)
+                       tile_size=flags.get("tile_size", 16),
+                       radius_clip_area=flags.get("radius_clip_area", 0.0), **eps)
 
 
 def compare_images(gpu, ora, amb, tol=1e-3, max_amb_frac=0.02):

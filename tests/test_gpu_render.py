@@ -84,6 +84,25 @@ def test_profile_levels(cfg1_setup):
     assert s2["blend_evaluations"] <= s2["n_pairs"] * r.flags().tile_size ** 2
 
 
+def test_radius_clipping_matches_the_oracle(cfg1_setup):
+    """Sec. 4.4 radius clipping at the median 1-sigma area of the frame's splats: the image matches
+    the oracle with the same clipping (splats whose FP64 det lies within 1e-3 of the threshold are
+    ambiguous), about half the splats lose their tiles, and zero keeps the unclipped image."""
+    sc, cam, r, osc = cfg1_setup
+    sp = oracle.project(osc, cam)
+    cov = sp["cov"][sp["valid"] == 1]
+    thr = float(np.median(np.pi * np.sqrt(cov[:, 0] * cov[:, 2] - cov[:, 1] ** 2)))
+    fl = dict(bg=(0.05, 0.1, 0.2), radius_clip_area=thr)
+    img, st = gpu_image(r, cam, use_mlp=0, **fl)
+    base, st0 = gpu_image(r, cam, use_mlp=0, bg=(0.05, 0.1, 0.2))
+    off, _ = gpu_image(r, cam, use_mlp=0, bg=(0.05, 0.1, 0.2), radius_clip_area=0.0)
+    np.testing.assert_array_equal(off, base)
+    assert 0.3 * st0["n_pairs"] < st["n_pairs"] < 0.8 * st0["n_pairs"]
+    ref = oracle.render(osc, cam, oracle_opts_for(fl))
+    compare_images(img, ref["image"], ref["ambiguous"])
+    assert np.abs(img - base).max() > 1e-2                   # clipping changed the picture
+
+
 def test_render_is_deterministic(cfg1_setup):
     sc, cam, r, osc = cfg1_setup
     a, _ = gpu_image(r, cam, use_mlp=0)

@@ -296,3 +296,27 @@ def test_support_tile_list_of_a_circle_off_a_tile_corner():
     sp["u"], sp["v"] = 16.0, 16.0        # on the corner: all four tiles are reached
     sp["px_min"], sp["px_max"] = [[11, 11]], [[20, 20]]
     assert oracle.tile_lists(sp, cam, 16, mode="support")[0].tolist() == [0, 1, 4, 5]
+
+
+@pytest.mark.parametrize("side", [-1, 1])
+def test_radius_clipping_threshold_is_the_one_sigma_area(side):
+    """Sec. 4.4 radius clipping, pinned on one isotropic Gaussian on the optical axis: there
+    Sigma_2D = ((f sigma / z)^2 + 0.3) I, whose 1-sigma ellipse has area pi ((f sigma / z)^2 + 0.3).
+    A threshold 1 % above it drops the splat (the image is the background); 1 % below keeps the
+    unclipped image."""
+    cam = axis_camera(32, 32, fx=32.0, cx=16.5, cy=16.5)
+    sigma, z = math.exp(-2.5), 2.0
+    a = one_asset([[0.0, 0.0, z]], [[math.log(sigma)] * 3], None, [logit(0.8)],
+                  np.full((1, 1, 3), 0.6))
+    osc = oracle.OracleScene(scenes.Scene([a], [identity_instance()]))
+    s32 = math.exp(float(np.float32(math.log(sigma))))
+    area = math.pi * ((32.0 * s32 / z) ** 2 + 0.3)
+    bg = (0.1, 0.2, 0.3)
+    ref = oracle.render(osc, cam, oracle.opts(bg=bg))["image"]
+    got = oracle.render(osc, cam, oracle.opts(bg=bg, radius_clip_area=area * (1.0 + 0.01 * side)))["image"]
+    assert np.abs(ref - np.asarray(bg)).max() > 0.1          # the splat is visible unclipped
+    if side > 0:
+        np.testing.assert_array_equal(got, np.broadcast_to(np.asarray(bg), got.shape))
+    else:
+        np.testing.assert_array_equal(got, ref)
+
