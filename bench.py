@@ -115,6 +115,11 @@ def parse():
     p.add_argument("--train-dirs", type=int, default=256)
     p.add_argument("--train-steps", type=int, default=1000)
     p.add_argument("--train-res", type=int, default=512)
+    p.add_argument("--train-aux", type=int, default=0,
+                   help="auxiliary cone views per training view (Sec. 3.1; the paper's figures use 6)")
+    p.add_argument("--train-aux-angle", type=float, default=2.5, help="their cone half-angle, degrees")
+    p.add_argument("--train-offset", action="store_true",
+                   help="random asset offset in the training views (Sec. 3.1, 4.1)")
     p.add_argument("--radius-clip", type=float, default=0.0,
                    help="radius clipping (Sec. 4.4) on the culled pass: drop splats whose 1-sigma "
                         "ellipse is below this many px^2 (0: off; lossy, reported by the PSNR)")
@@ -313,9 +318,13 @@ def run_ours(args, rank, world):
         for k in ids:
             _, info = train_visibility(r.ctx, k, n_dirs=args.train_dirs, n_dist=3, res=args.train_res,
                                        steps=args.train_steps, batch=65536, precision=prec,
-                                       device=dev, log_every=args.train_steps)
+                                       device=dev, log_every=args.train_steps, n_aux=args.train_aux,
+                                       aux_angle_deg=args.train_aux_angle,
+                                       random_offset=args.train_offset)
             losses.append(info["losses"][-1][1])
         train_info = {"views_per_asset": 3 * args.train_dirs, "view_res": args.train_res,
+                      "aux_views_per_view": args.train_aux, "aux_angle_deg": args.train_aux_angle,
+                      "random_offset": bool(args.train_offset),
                       "steps": args.train_steps, "batch": 65536,
                       "final_loss_mean": float(np.mean(losses)),
                       "seconds_all_assets": time.perf_counter() - t0}

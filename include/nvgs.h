@@ -220,6 +220,27 @@ nvgs_status nvgs_get_asset_info(const nvgs_ctx* ctx, int asset_id, nvgs_asset_in
 nvgs_status nvgs_training_views(const nvgs_ctx* ctx, int asset_id, int n_dirs, int n_dist, int width,
                                 int height, nvgs_camera* out);
 
+/* Training views with the paper's robustness variants (Sec. 3.1, 4.1).  Main views as for
+ * nvgs_training_views, each followed by n_aux auxiliary views: cameras at the same distance whose
+ * directions lie on the cone of half-angle aux_angle around the main direction (equally spaced
+ * around it), looking at the box centre; nvgs_label_visibility with group = 1 + n_aux OR-s a main
+ * view with its auxiliary views.  random_offset = 1 shifts every main camera in its image plane
+ * so that the asset does not sit at the image centre: the shift is (a r + b d_n) s(d) d with
+ * (a, b) uniform in [-1, 1]^2 (SplitMix64 of seed and the view index), r / d_n the camera's right
+ * and down axes and s(d) growing linearly from 0 at d_min to d_min / d_max at d_max.  out: HOST
+ * array of n_dirs * n_dist * (1 + n_aux) cameras, main-view-major. */
+typedef struct {
+    int32_t n_dirs, n_dist;      /* Fibonacci directions, log-spaced distances per direction */
+    int32_t width, height;
+    int32_t n_aux;               /* auxiliary views per main view (0: none; the paper's figures: 6) */
+    float aux_angle;             /* cone half-angle, radians (> 0 when n_aux > 0) */
+    int32_t random_offset;       /* 0 / 1 */
+    int32_t pad_;
+    uint64_t seed;
+} nvgs_view_opts;
+nvgs_status nvgs_training_views_ex(const nvgs_ctx* ctx, int asset_id, const nvgs_view_opts* opts,
+                                   nvgs_camera* out);
+
 /* Starts training the MLP of `asset_id` (Sec. 3.2, 4.1): FP32 master weights from `w0` (HOST,
  * 10497 floats, the nvgs_set_mlp layout), zero Adam moments, and the n_views HOST cameras the
  * label rows refer to (one per label row; their centre and focal length give each sample's view

@@ -1050,6 +1050,90 @@ extern "C" nvgs_status nvgs_training_views(const nvgs_ctx* ctx, int asset_id, in
     return NVGS_OK;
 }
 
+namespace {
+// Camera at `eye` looking along f (unit): rows right, down, forward (right = f x up, with up = +y,
+// or +z when looking along y).
+void look_along(const double* eye, const double* f, int width, int height, double fx, nvgs_camera& c,
+                double* right = nullptr, double* down = nullptr) {
+    double r[3], dn[3];
+    double up[3] = {0.0, 1.0, 0.0};
+    if (std::fabs(f[1]) > 0.999) { up[1] = 0.0; up[2] = 1.0; }
+    r[0] = f[1] * up[2] - f[2] * up[1]; r[1] = f[2] * up[0] - f[0] * up[2]; r[2] = f[0] * up[1] - f[1] * up[0];
+    const double rn = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (int q = 0; q < 3; q++) r[q] /= rn;
+    dn[0] = f[1] * r[2] - f[2] * r[1]; dn[1] = f[2] * r[0] - f[0] * r[2]; dn[2] = f[0] * r[1] - f[1] * r[0];
+    const double* rows[3] = {r, dn, f};
+    for (int p = 0; p < 3; p++) {
+        for (int q = 0; q < 3; q++) c.R[3 * p + q] = (float)rows[p][q];
+        c.t[p] = (float)(-(rows[p][0] * eye[0] + rows[p][1] * eye[1] + rows[p][2] * eye[2]));
+    }
+    c.fx = c.fy = (float)fx;
+    c.cx = width / 2.0f;
+    c.cy = height / 2.0f;
+    c.width = width;
+    c.height = height;
+    c.z_near = 0.2f;
+    if (right) for (int q = 0; q < 3; q++) right[q] = r[q];
+    if (down) for (int q = 0; q < 3; q++) down[q] = dn[q];
+}
+
+// SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number generators", 2014).
+uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+double unit_uniform(uint64_t bits) { return (double)(bits >> 11) * (1.0 / 9007199254740992.0); }
+}  // namespace
+
+extern "C" nvgs_status nvgs_training_views_ex(const nvgs_ctx* ctx, int asset_id, const nvgs_view_opts* o,
+                                              nvgs_camera* out) {
+    if (!ctx || !o || !out || asset_id < 0 || asset_id >= (int)ctx->assets.size() || o->n_dirs < 1 ||
+        o->n_dist < 1 || o->width < 1 || o->height < 1 || o->n_aux < 0 || o->n_aux > 64 ||
+        (o->n_aux > 0 && !(o->aux_angle > 0.0f && o->aux_angle < 1.5f)))
+        return NVGS_ERR_INVALID_ARG;
+    const AssetDev& a = ctx->assets[asset_id].dev;
+    const double golden = M_PI * (3.0 - std::sqrt(5.0));
+    const double fx = (o->width / 2.0) * a.train_focal;   // (W/2) / tan(theta_t / 2)
+    const int group = 1 + o->n_aux;
+    for (int k = 0; k < o->n_dirs; k++) {
+        const double y = 1.0 - 2.0 * (k + 0.5) / o->n_dirs;
+        const double rad = std::sqrt(std::max(0.0, 1.0 - y * y));
+        const double ph = golden * k;
+        const double dir[3] = {rad * std::cos(ph), y, rad * std::sin(ph)};
+        for (int j = 0; j < o->n_dist; j++) {
+            const double u = o->n_dist > 1 ? (double)j / (o->n_dist - 1) : 0.0;
+            const double d = a.d_min * std::pow((double)a.d_max / a.d_min, u);
+            const int view = k * o->n_dist + j;
+            double eye[3], f[3], r[3], dn[3];
+            for (int q = 0; q < 3; q++) { eye[q] = a.bbox_c[q] + d * dir[q]; f[q] = -dir[q]; }
+            nvgs_camera& c = out[(size_t)view * group];
+            look_along(eye, f, o->width, o->height, fx, c, r, dn);
+            if (o->random_offset) {
+                // s(d): 0 at d_min, d_min / d_max at d_max, linear in d
+                const double t = a.d_max > a.d_min ? (d - a.d_min) / ((double)a.d_max - a.d_min) : 0.0;
+                const double s = t * (double)a.d_min / a.d_max;
+                const uint64_t h = splitmix64(o->seed ^ splitmix64((uint64_t)view));
+                const double oa = 2.0 * unit_uniform(h) - 1.0, ob = 2.0 * unit_uniform(splitmix64(h)) - 1.0;
+                for (int q = 0; q < 3; q++) eye[q] += (oa * r[q] + ob * dn[q]) * s * d;
+                look_along(eye, f, o->width, o->height, fx, c);
+            }
+            // auxiliary views: directions on the cone of half-angle aux_angle around dir, same distance
+            for (int m = 0; m < o->n_aux; m++) {
+                const double phi = 2.0 * M_PI * m / o->n_aux;
+                const double cb = std::cos((double)o->aux_angle), sb = std::sin((double)o->aux_angle);
+                double ad[3], aeye[3], af[3];
+                for (int q = 0; q < 3; q++) ad[q] = cb * dir[q] + sb * (std::cos(phi) * r[q] + std::sin(phi) * dn[q]);
+                const double an = std::sqrt(ad[0] * ad[0] + ad[1] * ad[1] + ad[2] * ad[2]);
+                for (int q = 0; q < 3; q++) { ad[q] /= an; aeye[q] = a.bbox_c[q] + d * ad[q]; af[q] = -ad[q]; }
+                look_along(aeye, af, o->width, o->height, fx, out[(size_t)view * group + 1 + m]);
+            }
+        }
+    }
+    return NVGS_OK;
+}
+
 extern "C" float nvgs_lr_schedule(int step, int total, float lr0, float lr1, float warmup_frac) {
     if (total <= 0) return lr0;
     const double tw = std::max(1.0, (double)warmup_frac * total);

@@ -107,6 +107,12 @@ class TuneResult(C.Structure):
                 ("ms_per_view", C.c_float)]
 
 
+class ViewOpts(C.Structure):
+    _fields_ = [("n_dirs", C.c_int32), ("n_dist", C.c_int32), ("width", C.c_int32), ("height", C.c_int32),
+                ("n_aux", C.c_int32), ("aux_angle", C.c_float), ("random_offset", C.c_int32),
+                ("pad_", C.c_int32), ("seed", C.c_uint64)]
+
+
 class AssetGrads(C.Structure):
     _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
                 ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
@@ -124,7 +130,7 @@ EXPORTS = ("nvgs_create", "nvgs_destroy", "nvgs_last_error", "nvgs_get_stream", 
            "nvgs_train_visibility_step", "nvgs_train_get_weights", "nvgs_lr_schedule",
            "nvgs_get_asset_info", "nvgs_training_views", "nvgs_render_backward",
            "nvgs_update_asset", "nvgs_render_batch", "nvgs_autotune", "nvgs_device_bytes",
-           "nvgs_selftest_wait_timeout", "nvgs_measure_fp32_fma")
+           "nvgs_selftest_wait_timeout", "nvgs_measure_fp32_fma", "nvgs_training_views_ex")
 NVGS_SORT_NOALLOC_MAX_PAIRS = 1 << 20
 
 
@@ -163,6 +169,7 @@ def _load():
     L.nvgs_lr_schedule.restype = C.c_float
     L.nvgs_get_asset_info.argtypes = [vp, C.c_int, P(AssetInfo)]
     L.nvgs_training_views.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+    L.nvgs_training_views_ex.argtypes = [vp, C.c_int, P(ViewOpts), vp]
     L.nvgs_render_backward.argtypes = [vp, vp, C.c_int, P(AssetGrads)]
     L.nvgs_device_bytes.argtypes = [vp, P(C.c_uint64)]
     L.nvgs_render_batch.argtypes = [vp, vp, C.c_int, vp, P(RenderFlags), P(BatchOpts), vp]
@@ -412,6 +419,17 @@ def nvgs_training_views(ctx, asset_id: int, n_dirs: int, n_dist: int, width: int
     arr = (Camera * (n_dirs * n_dist))()
     _check(ctx, lib.nvgs_training_views(ctx, int(asset_id), int(n_dirs), int(n_dist), int(width),
                                         int(height), C.cast(arr, C.c_void_p)))
+    return arr
+
+
+def nvgs_training_views_ex(ctx, asset_id: int, n_dirs: int, n_dist: int, width: int, height: int,
+                           n_aux: int = 0, aux_angle: float = 0.0, random_offset: bool = False,
+                           seed: int = 0):
+    """Main views, each followed by its n_aux auxiliary cone views (label with group = 1 + n_aux)."""
+    o = ViewOpts(int(n_dirs), int(n_dist), int(width), int(height), int(n_aux), float(aux_angle),
+                 1 if random_offset else 0, 0, int(seed) & 0xFFFFFFFFFFFFFFFF)
+    arr = (Camera * (n_dirs * n_dist * (1 + n_aux)))()
+    _check(ctx, lib.nvgs_training_views_ex(ctx, int(asset_id), C.byref(o), C.cast(arr, C.c_void_p)))
     return arr
 
 

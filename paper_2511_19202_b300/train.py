@@ -29,15 +29,23 @@ def init_weights(seed: int) -> np.ndarray:
 def train_visibility(ctx, asset_id: int, n_dirs: int = 512, n_dist: int = 3, res: int = 512,
                      steps: int = 1500, batch: int = 65536, lr0: float = 2e-3, lr1: float = 2e-4,
                      warmup: float = 0.2, seed: int = 0, precision: int = N.NVGS_PREC_BF16,
-                     tile: int = 16, device: int = 0, log_every: int = 0):
-    """Labels, trains and installs the visibility MLP of one asset.  Returns (weights, info)."""
+                     tile: int = 16, device: int = 0, log_every: int = 0, n_aux: int = 0,
+                     aux_angle_deg: float = 2.5, random_offset: bool = False):
+    """Labels, trains and installs the visibility MLP of one asset.  Returns (weights, info).
+    n_aux > 0 adds that many auxiliary cone views per main view (a Gaussian is labelled visible
+    if any of them blends it; Sec. 3.1); random_offset shifts the asset off the image centre
+    (Sec. 3.1, 4.1)."""
     t0 = time.perf_counter()
     info = N.nvgs_get_asset_info(ctx, asset_id)
-    views = N.nvgs_training_views(ctx, asset_id, n_dirs, n_dist, res, res)
+    group = 1 + int(n_aux)
+    all_views = N.nvgs_training_views_ex(ctx, asset_id, n_dirs, n_dist, res, res, n_aux=n_aux,
+                                         aux_angle=math.radians(aux_angle_deg), random_offset=random_offset,
+                                         seed=seed)
+    views = (N.Camera * (len(all_views) // group))(*[all_views[k] for k in range(0, len(all_views), group)])
     n = int(info.n)
     labels = torch.empty(len(views) * n, dtype=torch.uint8, device=f"cuda:{device}")
     flags = N.nvgs_default_flags(use_mlp=0, tile_size=tile)
-    N.nvgs_label_visibility(ctx, asset_id, views, flags, labels, group=1)
+    N.nvgs_label_visibility(ctx, asset_id, all_views, flags, labels, group=group)
     torch.cuda.synchronize(device)
     t_label = time.perf_counter() - t0
     visible_frac = float(labels.float().mean())

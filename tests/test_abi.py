@@ -45,7 +45,7 @@ def test_struct_layouts_match_the_c_compiler(N):
                "nvgs_kernel_stat": N.KernelStat, "nvgs_asset_info": N.AssetInfo,
                "nvgs_train_batch": N.TrainBatch, "nvgs_adam_cfg": N.AdamCfg,
                "nvgs_asset_grads": N.AssetGrads, "nvgs_batch_opts": N.BatchOpts,
-               "nvgs_tune_result": N.TuneResult}
+               "nvgs_tune_result": N.TuneResult, "nvgs_view_opts": N.ViewOpts}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void){']
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

@@ -109,3 +109,80 @@ def test_training_learns_back_face_occlusion():
         assert np.mean(recall) > 0.97 and np.mean(culled) > 0.05
     finally:
         r.close()
+
+
+def _centre(c):
+    R = np.asarray(c.R, np.float64).reshape(3, 3)
+    return -R.T @ np.asarray(c.t, np.float64), R
+
+
+def test_training_views_with_auxiliary_cones_and_offsets():
+    """Sec. 3.1 / 4.1 view variants: each main view is followed by n_aux cameras at the same
+    distance on the cone of the given half-angle around its direction, looking at the box centre;
+    the random offset moves a main camera only in its image plane, not at d_min, and by at most
+    sqrt(2) s(d) d with s growing linearly to d_min / d_max at d_max; without variants the main
+    views are those of nvgs_training_views."""
+    from paper_2511_19202_b300 import nvgs as N
+    sc = scenes.config1_scene(3000)
+    r = renderer_for(sc)
+    try:
+        info = N.nvgs_get_asset_info(r.ctx, 0)
+        bc = np.asarray(info.bbox_center, np.float64)
+        dmin, dmax = float(info.d_min), float(info.d_max)
+        plain = N.nvgs_training_views(r.ctx, 0, 8, 3, 64, 64)
+        same = N.nvgs_training_views_ex(r.ctx, 0, 8, 3, 64, 64)
+        for a, b in zip(plain, same):
+            assert list(a.R) == list(b.R) and list(a.t) == list(b.t)
+        ang = np.radians(2.5)
+        ex = N.nvgs_training_views_ex(r.ctx, 0, 8, 3, 64, 64, n_aux=6, aux_angle=ang, random_offset=True, seed=3)
+        assert len(ex) == 8 * 3 * 7
+        shifted = 0
+        for v in range(24):
+            main, base = ex[7 * v], plain[v]
+            cm, Rm = _centre(main)
+            cb, Rb = _centre(base)
+            np.testing.assert_allclose(Rm, Rb, atol=1e-6)          # same orientation
+            f = Rb[2]
+            d = float(np.linalg.norm(cb - bc))
+            off = cm - cb
+            assert abs(off @ f) < 1e-4 * d                          # in the image plane
+            s = (d - dmin) / (dmax - dmin) * dmin / dmax
+            assert np.linalg.norm(off) <= np.sqrt(2) * s * d * (1 + 1e-4) + 1e-5
+            if v % 3 == 0:
+                assert np.linalg.norm(off) < 1e-5 * d               # none at d_min
+            else:
+                shifted += np.linalg.norm(off) > 1e-3 * s * d
+            main_dir = (cb - bc) / d
+            for m in range(1, 7):
+                ca, Ra = _centre(ex[7 * v + m])
+                da = float(np.linalg.norm(ca - bc))
+                assert abs(da - d) < 1e-4 * d
+                cosang = float(((ca - bc) / da) @ main_dir)
+                assert abs(np.arccos(min(1.0, cosang)) - ang) < 1e-4
+                np.testing.assert_allclose(Ra[2], -(ca - bc) / da, atol=1e-5)   # looks at the centre
+        assert shifted >= 8
+    finally:
+        r.close()
+
+
+def test_auxiliary_views_only_add_visible_labels():
+    """A Gaussian is visible for a main view if the main view or any of its auxiliary views blends
+    it (Sec. 3.1): labels with the cones contain those of the main views alone, and add some."""
+    from paper_2511_19202_b300 import nvgs as N
+    sc = scenes.config1_scene(6000)
+    r = renderer_for(sc)
+    try:
+        n = sc.n_instanced
+        allv = N.nvgs_training_views_ex(r.ctx, 0, 6, 2, 128, 128, n_aux=6, aux_angle=np.radians(2.5))
+        mains = (N.Camera * 12)(*[allv[k] for k in range(0, len(allv), 7)])
+        fl = N.nvgs_default_flags(use_mlp=0)
+        lab_main = torch.zeros(12 * n, dtype=torch.uint8, device="cuda")
+        N.nvgs_label_visibility(r.ctx, 0, mains, fl, lab_main)
+        lab_aux = torch.zeros(12 * n, dtype=torch.uint8, device="cuda")
+        N.nvgs_label_visibility(r.ctx, 0, allv, fl, lab_aux, group=7)
+        a = lab_main.cpu().numpy().astype(bool)
+        b = lab_aux.cpu().numpy().astype(bool)
+        assert not (a & ~b).any()
+        assert b.sum() > a.sum()
+    finally:
+        r.close()
