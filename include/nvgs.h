@@ -272,6 +272,16 @@ nvgs_status nvgs_train_visibility_step(nvgs_ctx* ctx, int asset_id, const nvgs_t
 /* Copies the FP32 master weights (HOST, 10497 floats).  Pass them to nvgs_set_mlp to use them. */
 nvgs_status nvgs_train_get_weights(nvgs_ctx* ctx, int asset_id, float* w_out);
 
+/* Training checkpoint for resume: the FP32 master weights and both Adam moments of `asset_id`'s
+ * training state, as 3 x 10497 HOST floats in the order w, m, v (each in the nvgs_set_mlp layout).
+ * nvgs_train_load_state replaces them in a training state that nvgs_train_init created (with the
+ * same views).  Training is deterministic given (seed, step), so a run that saves after step k - 1
+ * and resumes at step k repeats the uninterrupted run bit for bit.  NVGS_ERR_INVALID_ARG if the
+ * asset has no training state or a pointer is NULL. */
+#define NVGS_TRAIN_STATE_FLOATS (3 * 10497)
+nvgs_status nvgs_train_save_state(nvgs_ctx* ctx, int asset_id, float* state_out);
+nvgs_status nvgs_train_load_state(nvgs_ctx* ctx, int asset_id, const float* state);
+
 /* Learning rate at `step` of `total` (Sec. 4.1): cosine warm-up from 0 to lr0 over the first
  * warmup_frac of the steps, then exponential decay to lr1 at the last step. */
 float nvgs_lr_schedule(int step, int total, float lr0, float lr1, float warmup_frac);

@@ -2,6 +2,7 @@
 // Sec. 3.3).  Host code here only validates arguments, sizes buffers and enqueues kernels; every
 // step of the pass itself runs in the kernels of the k_*.cu files.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -206,11 +207,23 @@ nvgs_status upload_assets(nvgs_ctx* ctx) {
     return NVGS_OK;
 }
 
+// Stage boundaries of a frame: CUDA events when profiling, and always an NVTX range per stage
+// (free unless a profiler is attached), so that tools can select S1-S6 by name.
+const char* const kStageNvtx[NVGS_NUM_STAGES] = {"nvgs setup", "nvgs S1 cull", "nvgs S2 mlp",
+                                                 "nvgs S3 compact", "nvgs S4 project", "nvgs S5 bin",
+                                                 "nvgs S5 sort", "nvgs S6 blend"};
 struct StageTimer {
     nvgs_ctx* ctx;
     bool on;
+    bool range_open = false;
     void mark(int k) {
         if (on) cudaEventRecord(ctx->ev[k], ctx->stream);
+        if (range_open) nvtxRangePop();
+        range_open = k >= 0 && k < NVGS_NUM_STAGES;
+        if (range_open) nvtxRangePushA(kStageNvtx[k]);
+    }
+    ~StageTimer() {
+        if (range_open) nvtxRangePop();
     }
 };
 
@@ -986,6 +999,34 @@ extern "C" nvgs_status nvgs_train_get_weights(nvgs_ctx* ctx, int asset_id, float
     CK(cudaSetDevice(ctx->device));
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemcpy(w_out, ctx->train[asset_id].w.p, kMlpWeights * 4, cudaMemcpyDeviceToHost));
+    return NVGS_OK;
+}
+
+static_assert(NVGS_TRAIN_STATE_FLOATS == 3 * kMlpWeights, "checkpoint size");
+
+extern "C" nvgs_status nvgs_train_save_state(nvgs_ctx* ctx, int asset_id, float* out) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (asset_id < 0 || asset_id >= (int)ctx->train.size() || !ctx->train[asset_id].n_views || !out)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "asset %d has no training state", asset_id);
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const auto& T = ctx->train[asset_id];
+    CK(cudaMemcpy(out, T.w.p, kMlpWeights * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out + kMlpWeights, T.m.p, kMlpWeights * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out + 2 * kMlpWeights, T.v.p, kMlpWeights * 4, cudaMemcpyDeviceToHost));
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_train_load_state(nvgs_ctx* ctx, int asset_id, const float* in) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    if (asset_id < 0 || asset_id >= (int)ctx->train.size() || !ctx->train[asset_id].n_views || !in)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "asset %d has no training state", asset_id);
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    auto& T = ctx->train[asset_id];
+    CK(cudaMemcpy(T.w.p, in, kMlpWeights * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(T.m.p, in + kMlpWeights, kMlpWeights * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(T.v.p, in + 2 * kMlpWeights, kMlpWeights * 4, cudaMemcpyHostToDevice));
     return NVGS_OK;
 }
 

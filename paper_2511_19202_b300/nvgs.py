@@ -130,7 +130,8 @@ EXPORTS = ("nvgs_create", "nvgs_destroy", "nvgs_last_error", "nvgs_get_stream", 
            "nvgs_train_visibility_step", "nvgs_train_get_weights", "nvgs_lr_schedule",
            "nvgs_get_asset_info", "nvgs_training_views", "nvgs_render_backward",
            "nvgs_update_asset", "nvgs_render_batch", "nvgs_autotune", "nvgs_device_bytes",
-           "nvgs_selftest_wait_timeout", "nvgs_measure_fp32_fma", "nvgs_training_views_ex")
+           "nvgs_selftest_wait_timeout", "nvgs_measure_fp32_fma", "nvgs_training_views_ex",
+           "nvgs_train_save_state", "nvgs_train_load_state")
 NVGS_SORT_NOALLOC_MAX_PAIRS = 1 << 20
 
 
@@ -170,6 +171,8 @@ def _load():
     L.nvgs_get_asset_info.argtypes = [vp, C.c_int, P(AssetInfo)]
     L.nvgs_training_views.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
     L.nvgs_training_views_ex.argtypes = [vp, C.c_int, P(ViewOpts), vp]
+    L.nvgs_train_save_state.argtypes = [vp, C.c_int, vp]
+    L.nvgs_train_load_state.argtypes = [vp, C.c_int, vp]
     L.nvgs_render_backward.argtypes = [vp, vp, C.c_int, P(AssetGrads)]
     L.nvgs_device_bytes.argtypes = [vp, P(C.c_uint64)]
     L.nvgs_render_batch.argtypes = [vp, vp, C.c_int, vp, P(RenderFlags), P(BatchOpts), vp]
@@ -420,6 +423,23 @@ def nvgs_training_views(ctx, asset_id: int, n_dirs: int, n_dist: int, width: int
     _check(ctx, lib.nvgs_training_views(ctx, int(asset_id), int(n_dirs), int(n_dist), int(width),
                                         int(height), C.cast(arr, C.c_void_p)))
     return arr
+
+
+NVGS_TRAIN_STATE_FLOATS = 3 * 10497
+
+
+def nvgs_train_save_state(ctx, asset_id: int) -> np.ndarray:
+    """Training checkpoint: FP32 master weights and Adam moments (w, m, v) as one float32 array."""
+    out = np.empty(NVGS_TRAIN_STATE_FLOATS, np.float32)
+    _check(ctx, lib.nvgs_train_save_state(ctx, int(asset_id), out.ctypes.data))
+    return out
+
+
+def nvgs_train_load_state(ctx, asset_id: int, state) -> None:
+    st = np.ascontiguousarray(state, dtype=np.float32)
+    if st.size != NVGS_TRAIN_STATE_FLOATS:
+        raise ValueError(f"state must hold {NVGS_TRAIN_STATE_FLOATS} floats")
+    _check(ctx, lib.nvgs_train_load_state(ctx, int(asset_id), st.ctypes.data))
 
 
 def nvgs_training_views_ex(ctx, asset_id: int, n_dirs: int, n_dist: int, width: int, height: int,

@@ -186,3 +186,37 @@ def test_auxiliary_views_only_add_visible_labels():
         assert b.sum() > a.sum()
     finally:
         r.close()
+
+
+def test_training_resumes_bit_for_bit_from_a_checkpoint():
+    """Checkpoint / resume: save the training state (master weights, Adam moments) after 20 steps,
+    run 20 more; a fresh state loaded from the checkpoint and run over the same 20 steps ends with
+    the same weights, bit for bit."""
+    from paper_2511_19202_b300 import nvgs as N
+    from paper_2511_19202_b300.train import init_weights
+    sc = scenes.config1_scene(6000)
+    r = renderer_for(sc)
+    try:
+        views = N.nvgs_training_views(r.ctx, 0, 12, 2, 96, 96)
+        n = sc.n_instanced
+        labels = torch.zeros(len(views) * n, dtype=torch.uint8, device="cuda")
+        N.nvgs_label_visibility(r.ctx, 0, views, N.nvgs_default_flags(use_mlp=0), labels)
+        w0 = init_weights(5)
+
+        def run(first, last):
+            for step in range(first, last):
+                N.nvgs_train_visibility_step(r.ctx, 0, labels, 4096, step, 1e-3, seed=9)
+
+        N.nvgs_train_init(r.ctx, 0, w0, views)
+        run(0, 20)
+        ckpt = N.nvgs_train_save_state(r.ctx, 0)
+        run(20, 40)
+        straight = N.nvgs_train_get_weights(r.ctx, 0)
+        N.nvgs_train_init(r.ctx, 0, w0, views)          # a fresh state ...
+        N.nvgs_train_load_state(r.ctx, 0, ckpt)           # ... resumed from the checkpoint
+        run(20, 40)
+        resumed = N.nvgs_train_get_weights(r.ctx, 0)
+        np.testing.assert_array_equal(N.flat_weights(straight), N.flat_weights(resumed))
+        assert not np.array_equal(N.flat_weights(straight), ckpt[:10497])   # it did train
+    finally:
+        r.close()
