@@ -437,6 +437,11 @@ nvgs_status nvgs_selftest_wait_timeout(int device, double* seconds_waited);
  * NVGS_ERR_INVALID_ARG for a bad device or NULL tflops, NVGS_ERR_CUDA if a CUDA call failed. */
 nvgs_status nvgs_measure_fp32_fma(int device, double* tflops);
 
+/* Host-side fault injection for tests: the library's next n device-buffer growths (in any
+ * context of the process) fail as if cudaMalloc had run out of memory, so the calls that need them
+ * return NVGS_ERR_OOM; n = 0 turns it off.  A context stays usable after such a failure. */
+void nvgs_debug_fail_allocs(int n);
+
 #ifdef __cplusplus
 }
 #endif

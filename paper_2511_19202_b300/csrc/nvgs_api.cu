@@ -5,6 +5,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -109,9 +110,15 @@ nvgs_status fail(nvgs_ctx* c, nvgs_status st, const char* fmt, ...) {
                         __LINE__);                                                            \
     } while (0)
 
+// Host-side fault injection for the tests: the next g_fail_allocs buffer growths fail as if
+// cudaMalloc had run out of memory (nvgs_debug_fail_allocs).
+std::atomic<int> g_fail_allocs{0};
+
 cudaError_t ensure(DevBuf& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.cap >= bytes) return cudaSuccess;
+    for (int left = g_fail_allocs.load(); left > 0;)
+        if (g_fail_allocs.compare_exchange_weak(left, left - 1)) return cudaErrorMemoryAllocation;
     if (b.p) {
         cudaError_t e = cudaFree(b.p);
         if (e != cudaSuccess) return e;
@@ -1529,3 +1536,5 @@ extern "C" nvgs_status nvgs_reset_kernel_stats(nvgs_ctx* ctx) {
     ctx->kms.clear();
     return NVGS_OK;
 }
+
+extern "C" void nvgs_debug_fail_allocs(int n) { g_fail_allocs.store(n > 0 ? n : 0); }

@@ -131,7 +131,7 @@ EXPORTS = ("nvgs_create", "nvgs_destroy", "nvgs_last_error", "nvgs_get_stream", 
            "nvgs_get_asset_info", "nvgs_training_views", "nvgs_render_backward",
            "nvgs_update_asset", "nvgs_render_batch", "nvgs_autotune", "nvgs_device_bytes",
            "nvgs_selftest_wait_timeout", "nvgs_measure_fp32_fma", "nvgs_training_views_ex",
-           "nvgs_train_save_state", "nvgs_train_load_state")
+           "nvgs_train_save_state", "nvgs_train_load_state", "nvgs_debug_fail_allocs")
 NVGS_SORT_NOALLOC_MAX_PAIRS = 1 << 20
 
 
@@ -172,6 +172,8 @@ def _load():
     L.nvgs_training_views.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
     L.nvgs_training_views_ex.argtypes = [vp, C.c_int, P(ViewOpts), vp]
     L.nvgs_train_save_state.argtypes = [vp, C.c_int, vp]
+    L.nvgs_debug_fail_allocs.argtypes = [C.c_int]
+    L.nvgs_debug_fail_allocs.restype = None
     L.nvgs_train_load_state.argtypes = [vp, C.c_int, vp]
     L.nvgs_render_backward.argtypes = [vp, vp, C.c_int, P(AssetGrads)]
     L.nvgs_device_bytes.argtypes = [vp, P(C.c_uint64)]
@@ -423,6 +425,11 @@ def nvgs_training_views(ctx, asset_id: int, n_dirs: int, n_dist: int, width: int
     _check(ctx, lib.nvgs_training_views(ctx, int(asset_id), int(n_dirs), int(n_dist), int(width),
                                         int(height), C.cast(arr, C.c_void_p)))
     return arr
+
+
+def nvgs_debug_fail_allocs(n: int) -> None:
+    """Test hook: the library's next n device-buffer growths fail as out-of-memory (0: off)."""
+    lib.nvgs_debug_fail_allocs(int(n))
 
 
 NVGS_TRAIN_STATE_FLOATS = 3 * 10497

@@ -36,3 +36,33 @@ def test_fp32_fma_throughput_is_measured():
     t = N.nvgs_measure_fp32_fma(0)
     print(f"FP32 FMA: {t:.1f} TFLOP/s")
     assert 5.0 < t < 200.0
+
+
+def test_failed_allocation_is_reported_and_the_context_recovers():
+    """Host-side fault injection: buffer growths fail as out-of-memory; the render that needs
+    them returns NVGS_ERR_OOM with a message, and once the fault is lifted the same context
+    renders the frame exactly as a fresh context does."""
+    from paper_2511_19202_b300 import nvgs as N
+    sc = scenes.tiny_scene(3000, 3, sh_degree=1)
+    small = scenes.look_at_camera((0.0, 0.5, 6.0), (0, 0, 0), 48, 32, 50.0)
+    big = scenes.look_at_camera((0.0, 0.3, 2.0), (0, 0, 0), 320, 240, 60.0)
+    r = renderer_for(sc)
+    try:
+        r.render(small, r.flags(use_mlp=0))
+        N.nvgs_debug_fail_allocs(1000)
+        try:
+            with pytest.raises(N.NvgsError) as e:
+                r.render(big, r.flags(use_mlp=0))
+            assert e.value.status == N.NVGS_ERR_OOM
+        finally:
+            N.nvgs_debug_fail_allocs(0)
+        img, _ = r.render(big, r.flags(use_mlp=0))
+        img = img.clone()
+    finally:
+        r.close()
+    r2 = renderer_for(sc)
+    try:
+        ref, _ = r2.render(big, r2.flags(use_mlp=0))
+        assert torch.equal(img, ref)
+    finally:
+        r2.close()
