@@ -3,8 +3,10 @@
 // there is no inter-CTA spin of any kind.
 //
 // Radix sort, per 8-bit digit pass over tiles of 4096 pairs (256 threads x 16):
-//   1. k_rs_hist:    per-tile digit histogram, stored digit-major: hist[d * n_tiles + tile]
-//   2. exclusive scan of hist -> global start of every (digit, tile) bucket
+//   1. k_rs_hist:        per-tile digit histogram, stored digit-major: hist[d * n_tiles + tile]
+//   2. k_rs_digit_scan:  one CTA per digit scans its row in place (start of every (digit, tile)
+//                        bucket among that digit's buckets) and writes the digit's total; the
+//                        scatter adds the exclusive prefix of the 256 totals
 //   3. k_rs_scatter: stable rank of every pair inside its tile (digit peers from eight warp
 //      ballots + per-warp running digit counters, each warp owning a contiguous 512-pair slice),
 //      a local counting sort in shared memory, then runs of equal digits written to consecutive
@@ -219,6 +221,33 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ ke
     }
 }
 
+// Row d of the digit-major histogram (n_tiles counts) -> its exclusive prefix, in place; the row's
+// total to totals[d].  One CTA per digit, 256 threads, 1024 counts per step (four per thread,
+// consecutive) with a running carry.
+__global__ void __launch_bounds__(256) k_rs_digit_scan(uint32_t* __restrict__ hist, uint32_t n_tiles,
+                                                       uint32_t* __restrict__ totals) {
+    __shared__ uint32_t s_warp[16];
+    uint32_t* row = hist + (uint64_t)blockIdx.x * n_tiles;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < n_tiles; base += 1024) {
+        const uint32_t i0 = base + 4 * threadIdx.x;
+        uint32_t v[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) v[k] = i0 + k < n_tiles ? row[i0 + k] : 0u;
+        const uint32_t sum = v[0] + v[1] + v[2] + v[3];
+        uint32_t tot;
+        uint32_t run = carry + block_exclusive_scan_256(sum, s_warp, &tot);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (i0 + k < n_tiles) row[i0 + k] = run;
+            run += v[k];
+        }
+        carry += tot;
+        __syncthreads();   // s_warp is reused by the next step's scan
+    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
 // Registers hold the tile's keys and one packed (digit << 16 | rank-in-warp) word per item;
 // values are read only when they are placed in shared memory, so four CTAs fit on an SM
 // (smaller, more numerous CTAs overlap their load, rank and write phases better).
@@ -226,7 +255,7 @@ template <typename K>
 __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatter(
     const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, K* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, uint64_t n, const uint32_t* __restrict__ n_dev, int shift,
-    uint32_t n_tiles, const uint32_t* __restrict__ hist_scan) {
+    uint32_t n_tiles, const uint32_t* __restrict__ hist_scan, const uint32_t* __restrict__ totals) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* cnt = (uint32_t*)smem;                                   // [8 warps][256]
     K* s_keys = (K*)(smem + kRsWarps * 256 * 4);
@@ -283,14 +312,16 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatt
             cnt[w * 256 + d] = run;
             run += c;
         }
-        d_local[d] = run;   // digit total for now
-        d_global[d] = hist_scan[(uint64_t)d * n_tiles + tile];
+        d_local[d] = run;        // this tile's digit total for now
+        d_global[d] = totals[d];  // the pass's digit total for now
     }
     __syncthreads();
-    if (threadIdx.x < 32) {  // exclusive scan of the 256 digit totals by one warp
+    // warps 0 and 1: exclusive scans of the tile's and of the pass's 256 digit totals
+    if (threadIdx.x < 64) {
+        uint32_t* a = threadIdx.x < 32 ? d_local : d_global;
         uint32_t v[8], s = 0;
 #pragma unroll
-        for (int k = 0; k < 8; k++) { v[k] = d_local[lane * 8 + k]; s += v[k]; }
+        for (int k = 0; k < 8; k++) { v[k] = a[lane * 8 + k]; s += v[k]; }
         uint32_t x = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -299,8 +330,11 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatt
         }
         uint32_t run = x - s;
 #pragma unroll
-        for (int k = 0; k < 8; k++) { d_local[lane * 8 + k] = run; run += v[k]; }
+        for (int k = 0; k < 8; k++) { a[lane * 8 + k] = run; run += v[k]; }
     }
+    __syncthreads();
+    // global start of this tile's bucket of digit d: digit d's start + its count in earlier tiles
+    if (threadIdx.x < 256) d_global[threadIdx.x] += hist_scan[(uint64_t)threadIdx.x * n_tiles + tile];
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRsItems; r++) {
@@ -330,7 +364,7 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatt
 size_t radix_scratch_bytes(uint64_t n) {
     const uint64_t tiles = (n + kRsTile - 1) / kRsTile;
     const uint64_t h = (256 * tiles * 4 + 255) / 256 * 256;
-    return (size_t)(2 * h + scan_scratch_bytes(256 * tiles));
+    return (size_t)(h + 256 * 4);
 }
 
 // n is the element count, or with n_dev the capacity (the count then lives on the device and
@@ -356,8 +390,7 @@ static cudaError_t radix_sort_impl(K* keys, uint32_t* values, K* keys_alt, uint3
     const uint64_t tiles = (n + kRsTile - 1) / kRsTile;
     const uint64_t h = (256 * tiles * 4 + 255) / 256 * 256;
     uint32_t* hist = (uint32_t*)scratch;
-    uint32_t* hist_scan = (uint32_t*)((char*)scratch + h);
-    void* scan_scratch = (char*)scratch + 2 * h;
+    uint32_t* totals = (uint32_t*)((char*)scratch + h);
     K* kin = keys;
     uint32_t* vin = values;
     K* kout = keys_alt;
@@ -373,9 +406,10 @@ static cudaError_t radix_sort_impl(K* keys, uint32_t* values, K* keys_alt, uint3
         NVGS_LAUNCH(log, s, hname, k_rs_hist<K><<<hgrid, kRsThreads, 0, s>>>(kin, n, n_dev, shift, (uint32_t)tiles, hist));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        e = exclusive_scan_u32(hist, hist_scan, 256 * tiles, nullptr, scan_scratch, s, log);
+        NVGS_LAUNCH(log, s, "k_rs_digit_scan", k_rs_digit_scan<<<256, 256, 0, s>>>(hist, (uint32_t)tiles, totals));
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        NVGS_LAUNCH(log, s, sname, k_rs_scatter<K><<<sgrid, kRsThreads, rs_smem_bytes<K>(), s>>>(kin, vin, kout, vout, n, n_dev, shift, (uint32_t)tiles, hist_scan));
+        NVGS_LAUNCH(log, s, sname, k_rs_scatter<K><<<sgrid, kRsThreads, rs_smem_bytes<K>(), s>>>(kin, vin, kout, vout, n, n_dev, shift, (uint32_t)tiles, hist, totals));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         K* tk = kin; kin = kout; kout = tk;
