@@ -343,7 +343,7 @@ def run_ours(args, rank, world):
         held = [cams[f] for f in range(61, 120, 8)] if len(cams) >= 120 else cams[:1]
         refs = [r.render(c, plain)[0].clone() for c in held]
         tau = -6.0
-        for cand in (-1.0, -1.5, -2.0, -2.5, -3.0, -3.5, -4.0, -5.0, -6.0):
+        for cand in (-1.0, -1.25, -1.5, -1.75, -2.0, -2.5, -3.0, -3.5, -4.0, -5.0, -6.0):
             ps = []
             for c, ref in zip(held, refs):
                 img, _ = r.render(c, r.flags(use_mlp=1, mlp_gate=1, tile_size=tile, logit_threshold=cand))
