@@ -111,8 +111,10 @@ __device__ __forceinline__ void walk(const uint32_t* __restrict__ values, const 
 
 }  // namespace
 
+// The register cap of a 16 x 16 tile's kernel (launch bound of 4 CTAs per SM) leaves the compiler
+// its 48-register schedule (5 resident CTAs): 1.4 % faster than forcing 6 CTAs at 40 registers.
 template <int TS, bool kCount>
-__global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS) < 6 ? 1536 / (TS * TS) : 6) k_blend(const uint32_t* __restrict__ ranges,
+__global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS) < 4 ? 1536 / (TS * TS) : 4) k_blend(const uint32_t* __restrict__ ranges,
                                                   const uint32_t* __restrict__ values,
                                                   const float4* __restrict__ rec, const CamParams* __restrict__ camp,
                                                   float* __restrict__ image, float* __restrict__ final_T,
