@@ -267,6 +267,10 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatt
     if (n_dev) n = min(n, (uint64_t)*n_dev);
     const uint32_t tile = blockIdx.x;   // one CTA per tile; CTAs past the device-side count exit
     if ((uint64_t)tile * kRsTile >= n) return;
+    // this thread's digit: the pass's total and this tile's bucket start, loaded now so that
+    // their latency hides behind the ranking
+    const uint32_t my_total = totals[threadIdx.x];
+    const uint32_t my_hs = hist_scan[(uint64_t)threadIdx.x * n_tiles + tile];
     for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) cnt[k] = 0u;
     __syncthreads();
 
@@ -313,7 +317,7 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatt
             run += c;
         }
         d_local[d] = run;        // this tile's digit total for now
-        d_global[d] = totals[d];  // the pass's digit total for now
+        d_global[d] = my_total;   // the pass's digit total for now
     }
     __syncthreads();
     // warps 0 and 1: exclusive scans of the tile's and of the pass's 256 digit totals
@@ -334,7 +338,7 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatt
     }
     __syncthreads();
     // global start of this tile's bucket of digit d: digit d's start + its count in earlier tiles
-    if (threadIdx.x < 256) d_global[threadIdx.x] += hist_scan[(uint64_t)threadIdx.x * n_tiles + tile];
+    if (threadIdx.x < 256) d_global[threadIdx.x] += my_hs;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRsItems; r++) {
