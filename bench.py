@@ -246,7 +246,9 @@ def kernel_frame_work(name, fr, sh_stride_floats, W, H, tile):
     if name in ("k_mlp_fp32", "k_mlp_tc"):
         return "flop", fr["n_mlp_queries"] * 20608
     if name == "k_expand_chunks":
-        return "hbm", nvis * 8 + fr["n_instanced"] / 8
+        # list entry; with the MLP on, also the mean read and its copy beside the entry
+        per = 8 + (32 if fr.get("n_mlp_queries") else 0)
+        return "hbm", nvis * per + fr["n_instanced"] / 8
     if name == "k_compact_list":
         return "hbm", nvis * 8 / 32 * 33 + ns * 8
     return "hbm", 0
