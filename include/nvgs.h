@@ -55,7 +55,7 @@ typedef enum { NVGS_PREC_FP32 = 0, NVGS_PREC_BF16 = 1, NVGS_PREC_FP8 = 2 } nvgs_
 
 typedef struct nvgs_ctx nvgs_ctx;
 
-/* One 3DGS asset (Sec. 3.3: "each unique asset is stored once").  Arrays are read during the
+/* One 3DGS asset (Sec. 3.3: every distinct asset is held once, however often it is placed).  Arrays are read during the
  * call and copied into the library's own layout. */
 typedef struct {
     int64_t n;                   /* Gaussians, >= 1 */
@@ -71,7 +71,8 @@ typedef struct {
     float p_near, p_far;         /* Eq. 1 coverage fractions; <= 0 selects 0.9 / 0.05 (Sec. 3.1) */
 } nvgs_asset_desc;
 
-/* A rigid, uniformly scaled placement of an asset (Sec. 3.3: "list of instance transforms"). */
+/* A rigid, uniformly scaled placement of an asset (Sec. 3.3: the scene is a list of such
+ * transforms over the stored assets). */
 typedef struct {
     int32_t asset_id;
     float R[9];                  /* row-major rotation */
@@ -263,8 +264,8 @@ typedef struct {
 } nvgs_adam_cfg;
 
 /* One Adam step on the class-balanced binary cross-entropy of B samples (a sample of class c
- * weighs B / (2 N_c), N_c = its class count in the batch; Sec. 4.1 "weights each occurrence by
- * its frequency in the batch").  loss_out (HOST, nullable) receives the batch loss; reading it
+ * weighs B / (2 N_c), N_c = its class count in the batch: the class-frequency weighting of
+ * Sec. 4.1).  loss_out (HOST, nullable) receives the batch loss; reading it
  * synchronises. */
 nvgs_status nvgs_train_visibility_step(nvgs_ctx* ctx, int asset_id, const nvgs_train_batch* batch,
                                        const nvgs_adam_cfg* adam, float* loss_out);

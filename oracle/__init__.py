@@ -102,6 +102,9 @@ def lib():
             L.or_mlp_forward.argtypes = [vp, C.c_int64, vp, vp]
             L.or_visibility.argtypes = [P(OrAsset), P(OrInstance), C.c_int, P(OrCamera), vp,
                                         C.c_int, vp, vp, vp]
+            L.or_visibility_at.restype = C.c_int
+            L.or_visibility_at.argtypes = [P(OrAsset), P(OrInstance), C.c_int, P(OrCamera), vp,
+                                           C.c_int, vp, C.c_int64, vp, vp, vp]
             L.or_sh_basis.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, vp]
             L.or_quat_to_rot.argtypes = [vp, vp]
             L.or_cov3d.argtypes = [vp, vp, vp]
@@ -230,6 +233,25 @@ def visibility(osc: OracleScene, cam, weights=None, gate=False, return_features=
     w = flat_weights(weights) if weights is not None else None
     lib().or_visibility(osc.assets, osc.instances, osc.n_inst, C.byref(camera(cam)), _ptr(w),
                         int(bool(gate)), _ptr(logits), _ptr(gated), _ptr(feats))
+    out = dict(logits=logits, gated=gated.astype(bool))
+    if return_features:
+        out["features"] = feats
+    return out
+
+
+def visibility_at(osc: OracleScene, cam, idx, weights=None, gate=False, return_features=False):
+    """visibility() at the instanced Gaussians `idx` (instance-major indices) only, each value
+    computed exactly as visibility() computes it."""
+    idx = np.ascontiguousarray(idx, np.int64)
+    n = idx.size
+    logits = np.zeros(n, np.float64)
+    gated = np.zeros(n, np.uint8)
+    feats = np.zeros((n, 32), np.float64) if return_features else None
+    w = flat_weights(weights) if weights is not None else None
+    rc = lib().or_visibility_at(osc.assets, osc.instances, osc.n_inst, C.byref(camera(cam)), _ptr(w),
+                                int(bool(gate)), _ptr(idx), n, _ptr(logits), _ptr(gated), _ptr(feats))
+    if rc != 0:
+        raise ValueError("visibility_at: index out of range or allocation failed")
     out = dict(logits=logits, gated=gated.astype(bool))
     if return_features:
         out["features"] = feats

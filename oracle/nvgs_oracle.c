@@ -305,6 +305,21 @@ void or_mlp_forward(const double* w, int64_t n, const double* feats, double* log
 /* Per instanced Gaussian: the MLP logit (NaN-free) and whether the instance bypasses the MLP
  * because its corrected centre distance is below d_min (Sec. 3.3 gating).  Features are
  * returned too when feats != NULL (32 per Gaussian). */
+/* Per instance: the camera centre in its local frame and whether it bypasses the MLP (Sec. 3.3:
+ * its bounding-box centre is closer than the asset's minimum distance, with the Eq. 2 focal
+ * correction). */
+static int instance_gate(const or_asset* a, const or_instance* in, const or_camera* cam, double f_r,
+                         int gate, double* cl) {
+    local_camera_center(cam, in, cl);
+    double bc[3], dd = 0.0;
+    for (int k = 0; k < 3; k++) {
+        bc[k] = 0.5 * (a->bbox_min[k] + a->bbox_max[k]);
+        dd += (bc[k] - cl[k]) * (bc[k] - cl[k]);
+    }
+    double d_centre = sqrt(dd) * (a->train_focal / f_r);
+    return gate && (d_centre < a->d_min);
+}
+
 void or_visibility(const or_asset* assets, const or_instance* inst, int n_inst,
                    const or_camera* cam, const double* weights, int gate, double* logits,
                    uint8_t* gated, double* feats) {
@@ -313,14 +328,7 @@ void or_visibility(const or_asset* assets, const or_instance* inst, int n_inst,
         const or_asset* a = &assets[inst[i].asset_id];
         int64_t off = instance_offset(assets, inst, i);
         double cl[3];
-        local_camera_center(cam, &inst[i], cl);
-        double bc[3], dd = 0.0;
-        for (int k = 0; k < 3; k++) {
-            bc[k] = 0.5 * (a->bbox_min[k] + a->bbox_max[k]);
-            dd += (bc[k] - cl[k]) * (bc[k] - cl[k]);
-        }
-        double d_centre = sqrt(dd) * (a->train_focal / f_r);
-        int bypass = gate && (d_centre < a->d_min);
+        int bypass = instance_gate(a, &inst[i], cam, f_r, gate, cl);
 #pragma omp parallel for schedule(static)
         for (int64_t g = 0; g < a->n; g++) {
             double f[32];
@@ -330,6 +338,40 @@ void or_visibility(const or_asset* assets, const or_instance* inst, int n_inst,
             if (gated) gated[off + g] = (uint8_t)bypass;
         }
     }
+}
+
+/* or_visibility at sampled instanced Gaussians: entry s of the outputs is Gaussian idx[s] of the
+ * instance-major order, computed exactly as or_visibility computes it (feats: 32 per entry,
+ * nullable).  For checks at scene sizes where evaluating every Gaussian in FP64 takes minutes.
+ * Returns 0, or -1 for an index outside [0, total) or a failed allocation. */
+int or_visibility_at(const or_asset* assets, const or_instance* inst, int n_inst,
+                     const or_camera* cam, const double* weights, int gate, const int64_t* idx,
+                     int64_t n_idx, double* logits, uint8_t* gated, double* feats) {
+    double f_r = render_focal(cam);
+    int64_t* offs = (int64_t*)malloc(((size_t)n_inst + 1) * sizeof *offs);
+    if (!offs) return -1;
+    offs[0] = 0;
+    for (int i = 0; i < n_inst; i++) offs[i + 1] = offs[i] + assets[inst[i].asset_id].n;
+    for (int64_t s = 0; s < n_idx; s++)
+        if (idx[s] < 0 || idx[s] >= offs[n_inst]) { free(offs); return -1; }
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < n_idx; s++) {
+        int lo = 0, hi = n_inst - 1;   /* last instance whose first index is <= idx[s] */
+        while (lo < hi) {
+            int mid = (lo + hi + 1) / 2;
+            if (offs[mid] <= idx[s]) lo = mid; else hi = mid - 1;
+        }
+        const or_asset* a = &assets[inst[lo].asset_id];
+        const int64_t g = idx[s] - offs[lo];
+        double cl[3], f[32];
+        int bypass = instance_gate(a, &inst[lo], cam, f_r, gate, cl);
+        or_mlp_features(a, &a->means[3 * g], cl, f_r, f);
+        if (feats) memcpy(&feats[32 * s], f, sizeof f);
+        logits[s] = weights ? or_mlp_forward_one(weights, f) : 0.0;
+        if (gated) gated[s] = (uint8_t)bypass;
+    }
+    free(offs);
+    return 0;
 }
 
 /* ------------------------------------------------------------------ O4: SH colour */
@@ -774,8 +816,8 @@ int or_pixel_weights(const or_splat* splats, int64_t n_splats, const or_camera* 
 /* Batch loss of the class-balanced binary cross-entropy and (if grad != NULL) its gradient with
  * respect to the flat weights.  Sample k is Gaussian sg[k] seen from training view sv[k]; views
  * holds, per view, the camera centre in the asset frame and its normalised focal length f_view.
- * A sample of class c weighs B / (2 N_c), N_c = the batch count of class c ("each occurrence
- * weighted by its frequency in the batch"); the loss is the weighted mean over the batch. */
+ * A sample of class c weighs B / (2 N_c), N_c = the batch count of class c (the class-frequency
+ * weighting of Sec. 4.1, read as class balancing); the loss is the weighted mean over the batch. */
 double or_train_loss_grad(const or_asset* a, const double* views, const uint8_t* labels,
                           int64_t n_gauss, const int32_t* sv, const int32_t* sg, int64_t B,
                           const double* w, double* grad) {

@@ -12,7 +12,7 @@
 // The CTA leaves the range as soon as every pixel has stopped (a block-wide vote per batch).
 // With `mark` set, every blended fragment also flags its survivor (the visibility labeller).
 //
-// Dense tiles (the supplement's "Gaussian/Asset Density": many Gaussians on few pixels balance
+// Dense tiles (the supplement's section on Gaussian and asset density: many Gaussians on few pixels balance
 // badly): k_blend walks at most `split_len` pairs of a tile.  If some pixel of a longer tile is
 // still unsaturated after them, its state (colour, T, count) is saved and the rest of the range
 // is cut into chunks of split_len that separate CTAs process in three steps --

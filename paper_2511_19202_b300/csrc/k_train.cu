@@ -10,8 +10,8 @@
 //                     writes its partial gradient (same flat layout as the weights) -- no atomics
 //                     on gradients, so a step is deterministic;
 //   k_train_adam      sums the partial gradients per weight and applies one Adam update.
-// "Weights each occurrence by its frequency in the batch" (Sec. 4.1) is read as class balancing:
-// a sample of class c weighs B / (2 N_c).
+// The loss weighting of Sec. 4.1 (each sample weighted by the frequency of its class in the
+// batch) is read as class balancing: a sample of class c weighs B / (2 N_c).
 #include "mlp_common.cuh"
 
 namespace nvgs {

@@ -64,3 +64,31 @@ def check_pruned_tile_lists(gpu_tiles, gpu_inst, gpu_g, support, rect, depth_of,
             assert ds[k + 1] >= ds[k] - eps * abs(ds[k]), f"tile {t}: order broken at {k}"
     count = lambda d: sum(len(v) for v in d.values())
     return count(G), count(S), count(R)
+
+
+def bf16_round(x):
+    """Round to nearest even to BF16 (as the kernel's cvt.rn and its weight packing do), as FP64."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32).astype(np.float64)
+
+
+def bf16_reference(w, feats):
+    """The BF16 tensor-core MLP's quantised arithmetic with exact accumulation: FP32 inputs,
+    weights and the ReLU'd hidden activations rounded to BF16; biases and the output weights as
+    BF16 high + low pairs.  Only the accumulation order and precision differ from the kernel."""
+    def pair(v):
+        v = np.ascontiguousarray(v, np.float32)
+        hi = bf16_round(v)
+        return hi + bf16_round(v - hi.astype(np.float32))
+    h = bf16_round(np.asarray(feats, np.float64).astype(np.float32))
+    for k in (1, 2, 3):
+        a = h @ bf16_round(w[f"W{k}"]).T + pair(w[f"b{k}"])
+        h = bf16_round(np.maximum(a, 0.0).astype(np.float32))
+    return h @ pair(np.ravel(w["W4"])) + pair(np.ravel(w["b4"]))[0]
+
+
+# BF16 decisions are compared outside a band of 1 % of the logit scale (p99 |logit|): inside it,
+# one BF16 rounding of an input or activation that falls the other way (FP32 features and FP32
+# accumulation on the GPU) can move the logit by a few 1e-3 of the scale.
+BF16_DECISION_BAND = 1e-2

@@ -1,12 +1,15 @@
 """GPU parity of the BF16 tensor-core visibility MLP (tcgen05) against the FP64 oracle: logits
-within the BF16 error budget, decisions agreeing on >= 99.9% of Gaussians with |logit| > 0.05,
-multi-asset tiles, and the culled image against the oracle render with the same decisions."""
+within the BF16 error budget, decisions agreeing on >= 99.9% of Gaussians with |logit| > 0.05;
+against the kernel's own quantised arithmetic on the oracle's inputs, logits within 1e-3 of the
+scale and decisions equal outside a 1% band; multi-asset tiles; and the culled image against the
+oracle render with the decisions taken in BF16 on the oracle's side."""
 import numpy as np
 import pytest
 
 import oracle
 import scenes
-from gpu_common import compare_images, gpu_image, oracle_opts_for, renderer_for
+from gpu_common import (BF16_DECISION_BAND, bf16_reference, bf16_round, compare_images, gpu_image,
+                        oracle_opts_for, renderer_for)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -54,6 +57,37 @@ def test_bf16_logits_match_oracle_cfg1():
         np.testing.assert_array_equal(kp, inside & (lg > 0))
     finally:
         r.close()
+
+
+def test_bf16_rounding_reference():
+    # exact values, ties to even (1 + 2^-8 down, 1 + 3 * 2^-8 up), a carry into the exponent
+    assert bf16_round([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -7 + 2.0 ** -9, -3.3,
+                       255.9]).tolist() == [1.0, 1.0, 1.015625, 1.0078125, -3.296875, 256.0]
+
+
+def test_bf16_logits_match_the_quantised_reference():
+    """The kernel's logits against its own quantised arithmetic (BF16 operands, exact sums) on
+    the oracle's FP64 inputs: the decision is taken in the kernel's precision on both sides."""
+    sc, cam = scenes.config1_scene(), scenes.config1_camera()
+    w = _weights(42)
+    r = renderer_for(sc, w, precision=BF16)
+    try:
+        lg, kp, _ = r.query_visibility(cam, r.flags(use_mlp=1, mlp_gate=0))
+        lg = lg.cpu().numpy().astype(np.float64)
+    finally:
+        r.close()
+    osc = oracle.OracleScene(sc)
+    inside, _ = oracle.frustum(osc, cam)
+    ref = bf16_reference(w, oracle.visibility(osc, cam, w, gate=False, return_features=True)["features"][inside])
+    scale = float(np.percentile(np.abs(ref), 99))
+    e = np.abs(lg[inside] - ref)
+    amb = np.abs(ref) <= BF16_DECISION_BAND * scale
+    print(f"bf16 vs quantised reference: p99 {np.percentile(e, 99):.3e} max {e.max():.3e} "
+          f"(scale {scale:.3f}), banded {amb.mean():.4f}")
+    assert np.percentile(e, 99) <= 1e-3 * scale
+    assert e.max() <= BF16_DECISION_BAND * scale
+    assert amb.mean() <= 0.05
+    np.testing.assert_array_equal((lg[inside] > 0)[~amb], (ref > 0)[~amb])
 
 
 @pytest.mark.parametrize("side,ctas_per_sm", [(3, 0), (6, 1)])
@@ -111,21 +145,27 @@ def test_bf16_culled_render_matches_oracle_with_same_decisions():
     r = renderer_for(sc, w, precision=BF16)
     try:
         lg, kp, _ = r.query_visibility(cam, r.flags(use_mlp=1, mlp_gate=0))
-        lg = lg.cpu().numpy().astype(np.float64)
+        kp = kp.cpu().numpy().astype(bool)
         img, st = gpu_image(r, cam, use_mlp=1, mlp_gate=0)
         osc = oracle.OracleScene(sc)
-        vis = oracle.visibility(osc, cam, w, gate=False)
+        vis = oracle.visibility(osc, cam, w, gate=False, return_features=True)
         inside, _ = oracle.frustum(osc, cam)
-        keep = inside & (vis["logits"] > 0)
-        # decisions inside the 0.05 band, or the (<= 0.1%) ones that disagree, are ambiguous
-        amb = inside & ((np.abs(vis["logits"]) <= 0.05) | ((lg > 0) != (vis["logits"] > 0)))
-        assert (amb & inside).sum() <= 0.03 * inside.sum()
-        assert 0.05 * inside.sum() < (keep.sum()) < 0.95 * inside.sum()
+        # the decisions in the kernel's precision (the BF16 quantised arithmetic on the oracle's
+        # FP64 inputs), banded where one rounding the other way could flip them
+        q = np.zeros(sc.n_instanced)
+        q[inside] = bf16_reference(w, vis["features"][inside])
+        band = BF16_DECISION_BAND * float(np.percentile(np.abs(q[inside]), 99))
+        keep = inside & (q > 0)
+        amb = inside & (np.abs(q) <= band)
+        assert amb.sum() <= 0.03 * inside.sum()
+        assert 0.05 * inside.sum() < keep.sum() < 0.95 * inside.sum()
+        np.testing.assert_array_equal(kp[inside & ~amb], keep[inside & ~amb])
         ref = oracle.render(osc, cam, oracle_opts_for({}), keep=keep.astype(np.uint8),
                             keep_amb=amb.astype(np.uint8))
-        # random weights put many logits near 0, where BF16 rounding may flip a decision; every
-        # pixel such a Gaussian touches is excluded (trained MLPs have bimodal logits)
-        compare_images(img, ref["image"], ref["ambiguous"], max_amb_frac=0.35)
+        # random weights with the output bias at the median logit put the bulk of the logits
+        # near 0: the 2 % of Gaussians in the band reach ~40 % of the pixels, which are excluded
+        # (trained MLPs have bimodal logits); the rest is compared at 1e-3
+        compare_images(img, ref["image"], ref["ambiguous"], max_amb_frac=0.45)
         assert st["n_mlp_queries"] == st["n_in_frustum"]
     finally:
         r.close()

@@ -111,6 +111,29 @@ def test_visibility_gate_uses_corrected_centre_distance():
         assert g.all() == bypass and g.any() == bypass      # d_t = z / s (f_t = f_r = 1)
 
 
+def test_visibility_at_equals_the_full_evaluation():
+    """The sampled entry point (used where a full FP64 evaluation of every Gaussian is too slow)
+    returns exactly what the full evaluation returns at those Gaussians, gate flags included."""
+    assets = [scenes.random_asset(k, 300 + 50 * k, sh_degree=0) for k in range(3)]
+    rng = np.random.default_rng(3)
+    insts = [scenes.Instance(k % 3, Rotation.random(random_state=k).as_matrix().astype(np.float32),
+                             rng.uniform(-2, 2, 3).astype(np.float32), float(rng.uniform(0.5, 2)))
+             for k in range(7)]
+    sc = scenes.Scene(assets, insts)
+    osc = oracle.OracleScene(sc, d_min=8.0, d_max=60.0)   # gates about half of the instances
+    cam = scenes.look_at_camera((0, 1, 9), (0, 0, 0), 96, 64, 50.0)
+    w = scenes.mlp_weights(5)
+    full = oracle.visibility(osc, cam, w, gate=True, return_features=True)
+    idx = np.concatenate([rng.integers(0, sc.n_instanced, 200), [0, sc.n_instanced - 1]])
+    got = oracle.visibility_at(osc, cam, idx, w, gate=True, return_features=True)
+    assert np.array_equal(got["logits"], full["logits"][idx])
+    assert np.array_equal(got["gated"], full["gated"][idx])
+    assert np.array_equal(got["features"], full["features"][idx])
+    assert full["gated"].any() and not full["gated"].all()
+    with pytest.raises(ValueError):
+        oracle.visibility_at(osc, cam, [sc.n_instanced], w)
+
+
 # ----------------------------------------------------------------------------- frustum (Sec. 3.3)
 def test_frustum_guard_band_and_near_plane():
     cam = axis_camera(32, 32, fx=40.0)                     # tan(half fov) = 16/40 = 0.4
