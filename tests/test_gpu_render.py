@@ -178,7 +178,7 @@ def test_fp32_mlp_logits_and_decisions_match_oracle():
         m = inside & np.isfinite(lg)
         assert m.sum() == inside.sum() > 0
         err = np.abs(lg[m] - vis["logits"][m])
-        scale = np.abs(vis["logits"][m]).max()
+        scale = np.abs(vis["logits"][inside]).max()
         assert err.max() <= 1e-4 * max(1.0, scale), err.max()
         big = np.abs(vis["logits"][m]) > 0.05
         agree = ((lg[m] > 0) == (vis["logits"][m] > 0))[big].mean()
@@ -186,11 +186,13 @@ def test_fp32_mlp_logits_and_decisions_match_oracle():
         # culled render with the MLP's own decisions, threshold at the median logit
         thr = float(np.float32(np.median(vis["logits"][inside])))
         img, st = gpu_image(r, cam, use_mlp=1, mlp_gate=0, logit_threshold=thr)
-        # decisions within 3x the measured FP32 logit error of the threshold may flip
-        keep, kamb = oracle.cull_decision(vis, inside, thr, band=3.0 * float(err.max()) + 1e-7)
+        # with |GPU - FP64 logit| <= tol (asserted above), only a decision within tol of the
+        # threshold can differ: those are banded (15 Gaussians here, reaching ~3.4 % of pixels)
+        tol = 1e-4 * max(1.0, scale)
+        keep, kamb = oracle.cull_decision(vis, inside, thr, band=tol)
         ref = oracle.render(osc, cam, oracle_opts_for({}), keep=keep.astype(np.uint8),
                             keep_amb=kamb.astype(np.uint8))
-        compare_images(img, ref["image"], ref["ambiguous"])
+        compare_images(img, ref["image"], ref["ambiguous"], max_amb_frac=0.05)
         assert st["n_survivors"] < st["n_in_frustum"]
     finally:
         r.close()

@@ -63,7 +63,9 @@ def test_train_step_matches_oracle_gradient():
         r.close()
     osc = oracle.OracleScene(sc)
     views = oracle.training_views_table(cams)
-    ref_loss, g = oracle.train_loss_grad(osc, 0, views, labels, sv, sg, w0.astype(np.float64))
+    w_or = oracle.flat_weights(w)                 # the oracle packs its own copy of the weights
+    np.testing.assert_array_equal(np.asarray(w0, np.float64), w_or)   # same layout on both sides
+    ref_loss, g = oracle.train_loss_grad(osc, 0, views, labels, sv, sg, w_or)
     assert loss == pytest.approx(ref_loss, rel=1e-4)
     step_gpu = w0.astype(np.float64) - w1
     step_ref = g / (1.0 + np.abs(g) / 1e6)
