@@ -109,6 +109,9 @@ def parse():
                         "resolution through the sync-free batch and its CUDA graph, plus the "
                         "autotuner; backward: forward + backward of a 1M-Gaussian SH-3 asset at "
                         "1080p against a random target")
+    p.add_argument("--instances", type=int, default=0,
+                   help="composed / medium: keep only the first N of the scene's 64 instances "
+                        "(0: the config's own count); sizes a profiling case between the two")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--mlp", choices=["trained", "random"], default="trained",
                    help="trained: per-asset GPU labels + Adam (Sec. 3.1-3.2) before timing")
@@ -131,9 +134,14 @@ def parse():
 
 
 # ----------------------------------------------------------------------------- workload
-def workload(config):
+def workload(config, n_instances=0):
     import scenes
-    if config == "composed":
+    if config in ("composed", "medium") and n_instances:
+        sc = scenes.config2_scene(n_instances=n_instances)
+        cams = [scenes.config2_camera(f) for f in range(120)]
+        desc = (f"composed scene, first {n_instances} of its 64 instances: 16 assets x 500k "
+                "Gaussians, SH degree 3, 1920x1080, 16x16 tiles, 120-frame orbit")
+    elif config == "composed":
         sc = scenes.config2_scene()
         cams = [scenes.config2_camera(f) for f in range(120)]
         desc = ("composed scene: 16 assets x 500k Gaussians (sphere/torus/box), 64 instances, "
@@ -308,7 +316,7 @@ def run_ours(args, rank, world):
 
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    sc, cams, weights, desc = workload(args.config)
+    sc, cams, weights, desc = workload(args.config, args.instances)
     r = Renderer(dev)
     prec = {"bf16": N.NVGS_PREC_BF16, "fp32": N.NVGS_PREC_FP32, "fp8": N.NVGS_PREC_FP8}[args.precision]
     train_info = None
@@ -449,8 +457,9 @@ def run_ours(args, rank, world):
     graph_plain, same_p = graph_time(mk_plain, 1, args.steps)
     graph_info = {"culled_ms_per_frame_graph": graph_culled, "unculled_ms_per_frame_graph": graph_plain,
                   "graph_images_equal_sync": same_c and same_p, "max_pairs": max_pairs}
-    if args.config == "composed":   # (large: eight 4K views or 8-pixel tiles would need tens of GB
-                                    # more pairs; medium: kept to the per-frame path it profiles)
+    if args.config == "composed" and not args.instances:
+        # (large: eight 4K views or 8-pixel tiles would need tens of GB more pairs; medium and
+        # instance subsets: kept to the per-frame path they profile)
         batch8_culled, same_b = graph_time(mk_culled, 8, max(8, args.steps))
         tune_cams = [cams[f] for f in (64, 72, 80, 88)] if len(cams) >= 120 else cams[:1]
         tune_out = [torch.empty((c.height, c.width, 3), dtype=torch.float32, device=f"cuda:{dev}")
@@ -726,7 +735,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        sc, cams, _, desc = workload(args.config)
+        sc, cams, _, desc = workload(args.config, args.instances)
         ms, cores, times = cpu_baseline_line(sc, cams, args.steps, args.warmup)
         sample = (f"per step: FP64 projection of all {sc.n_instanced} instanced Gaussians + exact "
                   f"compositing of {SAMPLE_ROWS} of {cams[0].height} rows of one orbit frame; "

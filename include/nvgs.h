@@ -318,7 +318,9 @@ typedef struct {
 /* cams: n_views cameras (host); images: n_views DEVICE pointers to H x W x 3 float32 (each the
  * size of its camera); flags as for nvgs_render except that image_memory must be DEVICE and
  * keep_outputs, profile and labelling are not available (NVGS_ERR_INVALID_ARG).  With
- * blend_split_len = 0 the split length is max(4096, 4 x max_pairs / tiles).  opts: nullable
+ * blend_split_len = 0 the split length is nvgs_render's automatic one, max(4096, 4 x (the view's
+ * pair count / tiles + 1)), computed on the device from the view's own count, so every view equals
+ * its synchronous render bit for bit.  opts: nullable
  * (defaults).  stats: NULL (the call returns without waiting for the GPU; capacity overflows are
  * then not reported) or n_views records, in which case the call waits for the batch and returns
  * NVGS_ERR_CAPACITY if some view needed more than max_pairs pairs (that view's image is

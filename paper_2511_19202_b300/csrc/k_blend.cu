@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS) < 4 ? 1536 / (TS * T
                                                   float* __restrict__ image, float* __restrict__ final_T,
                                                   int32_t* __restrict__ n_contrib,
                                                   uint8_t* __restrict__ mark, uint32_t split_len,
+                                                  const uint32_t* __restrict__ split_dev,
                                                   float4* __restrict__ state_tc,
                                                   int32_t* __restrict__ state_cnt,
                                                   uint32_t* __restrict__ alive,
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS) < 4 ? 1536 / (TS * T
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
     __shared__ float4 s_c[B];
+    if (split_dev) split_len = *split_dev;   // resolved on the device (sync-free batches)
     const int tile = blockIdx.x;
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     const bool longer = end - start > split_len;
@@ -160,10 +162,20 @@ __global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS) < 4 ? 1536 / (TS * T
 }
 
 // ------------------------------------------------------------------ dense tiles
+// The automatic split length from the frame's pair count on the device, with the integer rule the
+// synchronous path applies on the host: max(4096, 4 (n_pairs / n_tiles + 1)), capped at 2^31 - 1.
+__global__ void k_split_auto(const uint32_t* __restrict__ n_pairs, uint32_t n_tiles,
+                             uint32_t* __restrict__ split_len) {
+    const uint64_t a = max((uint64_t)4096, 4 * ((uint64_t)*n_pairs / n_tiles + 1));
+    *split_len = (uint32_t)min(a, (uint64_t)0x7fffffffu);
+}
+
 __global__ void k_split_count(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ alive,
-                              int n_tiles, uint32_t split_len, uint32_t* __restrict__ n_chunks) {
+                              int n_tiles, uint32_t split_len, const uint32_t* __restrict__ split_dev,
+                              uint32_t* __restrict__ n_chunks) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
+    if (split_dev) split_len = *split_dev;
     const uint32_t n = ranges[2 * t + 1] - ranges[2 * t];
     n_chunks[t] = (n > split_len && alive[t]) ? (n - split_len + split_len - 1) / split_len : 0u;
 }
@@ -189,6 +201,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __rest
                                                           const uint2* __restrict__ items,
                                                           const uint32_t* __restrict__ n_items,
                                                           uint32_t split_len,
+                                                          const uint32_t* __restrict__ split_dev,
                                                           const float4* __restrict__ state_tc,
                                                           float* __restrict__ Tch,
                                                           unsigned long long* __restrict__ evals_out) {
@@ -199,6 +212,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __rest
     __shared__ float4 s_c[B];
     // persistent: the grid is sized for the GPU, not for the worst-case item count
     const uint32_t n_it = *n_items;
+    if (split_dev) split_len = *split_dev;
     for (uint32_t item = blockIdx.x; item < n_it; item += gridDim.x) {
         const uint2 it = items[item];
         const int tile = (int)it.x;
@@ -223,6 +237,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
                                                           const uint2* __restrict__ items,
                                                           const uint32_t* __restrict__ n_items,
                                                           uint32_t split_len,
+                                                          const uint32_t* __restrict__ split_dev,
                                                           const float4* __restrict__ state_tc,
                                                           const float* __restrict__ Tch,
                                                           float4* __restrict__ part, int32_t* __restrict__ pcount,
@@ -234,6 +249,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
     __shared__ float4 s_b[B];
     __shared__ float4 s_c[B];
     const uint32_t n_it = *n_items;
+    if (split_dev) split_len = *split_dev;
     for (uint32_t item = blockIdx.x; item < n_it; item += gridDim.x) {
         const uint2 it = items[item];
         const int tile = (int)it.x;
@@ -312,14 +328,15 @@ template <int TS>
 static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, const float4* rec,
                             const CamParams& cam, const CamParams* cam_dev, float* image, float* final_T,
                             int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
-                            void* scratch, void* scan_scratch, int num_sms, unsigned long long* evals,
-                            cudaStream_t s, LaunchLog* log) {
+                            const uint32_t* auto_split_pairs, void* scratch, void* scan_scratch,
+                            int num_sms, unsigned long long* evals, cudaStream_t s, LaunchLog* log) {
     constexpr int B = TS * TS;
     const int n_tiles = cam.tiles_x * cam.tiles_y;
     const bool may_split = n_pairs > split_len;
     // carve the scratch; every section starts on a 256-byte boundary
     char* p = static_cast<char*>(scratch);
     uint32_t *n_chunks = nullptr, *first = nullptr, *n_items = nullptr, *alive = nullptr;
+    uint32_t* split_dev = nullptr;
     float4* state_tc = nullptr;
     int32_t* state_cnt = nullptr;
     uint2* items = nullptr;
@@ -332,6 +349,7 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
         first = n_chunks + n_tiles;
         alive = first + n_tiles;
         n_items = alive + n_tiles;
+        if (auto_split_pairs) split_dev = n_items + 1;   // inside the region's 64 spare bytes
         p += round256((uint64_t)n_tiles * 12 + 64);
         state_tc = reinterpret_cast<float4*>(p);
         p += round256((uint64_t)n_tiles * B * 16);
@@ -345,19 +363,24 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
         p += round256(max_items * B * 16);
         pcount = reinterpret_cast<int32_t*>(p);
     }
+    if (split_dev) {
+        NVGS_LAUNCH(log, s, "k_split_auto", k_split_auto<<<1, 1, 0, s>>>(auto_split_pairs, (uint32_t)n_tiles, split_dev));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     NVGS_LAUNCH(log, s, TS == 8 ? "k_blend<8>" : TS == 16 ? "k_blend<16>" : "k_blend<32>",
                 (evals ? k_blend<TS, true> : k_blend<TS, false>)<<<n_tiles, B, 0, s>>>(ranges, values, rec, cam_dev, image, final_T, n_contrib, mark,
-                                                  split_len, state_tc, state_cnt, alive, evals));
+                                                  split_len, split_dev, state_tc, state_cnt, alive, evals));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !may_split) return e;
-    NVGS_LAUNCH(log, s, "k_split_count", k_split_count<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, alive, n_tiles, split_len, n_chunks));
+    NVGS_LAUNCH(log, s, "k_split_count", k_split_count<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, alive, n_tiles, split_len, split_dev, n_chunks));
     e = exclusive_scan_u32(n_chunks, first, n_tiles, n_items, scan_scratch, s, log);
     if (e != cudaSuccess) return e;
     NVGS_LAUNCH(log, s, "k_split_fill", k_split_fill<<<(n_tiles + 255) / 256, 256, 0, s>>>(n_chunks, first, n_tiles, items));
     // persistent grids: enough CTAs to fill the GPU (the item count lives on the device)
     const unsigned pgrid = (unsigned)std::min<uint64_t>(max_items, (uint64_t)num_sms * (2048 / B));
-    NVGS_LAUNCH(log, s, "k_blend_split_T", (evals ? k_blend_split_T<TS, true> : k_blend_split_T<TS, false>)<<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, state_tc, Tch, evals));
-    NVGS_LAUNCH(log, s, "k_blend_split_C", (evals ? k_blend_split_C<TS, true> : k_blend_split_C<TS, false>)<<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, state_tc, Tch, part, pcount, mark, evals));
+    NVGS_LAUNCH(log, s, "k_blend_split_T", (evals ? k_blend_split_T<TS, true> : k_blend_split_T<TS, false>)<<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, split_dev, state_tc, Tch, evals));
+    NVGS_LAUNCH(log, s, "k_blend_split_C", (evals ? k_blend_split_C<TS, true> : k_blend_split_C<TS, false>)<<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, split_dev, state_tc, Tch, part, pcount, mark, evals));
     NVGS_LAUNCH(log, s, "k_blend_split_D", k_blend_split_D<TS><<<n_tiles, B, 0, s>>>(n_chunks, first, cam_dev, state_tc, state_cnt, part, pcount, image, final_T, n_contrib));
     return cudaGetLastError();
 }
@@ -365,14 +388,14 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
 cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const float4* rec,
                          const CamParams& cam, const CamParams* cam_dev, float* image, float* final_T,
                          int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
-                         void* scratch, void* scan_scratch, int num_sms, unsigned long long* evals,
-                         cudaStream_t s, LaunchLog* log) {
+                         const uint32_t* auto_split_pairs, void* scratch, void* scan_scratch,
+                         int num_sms, unsigned long long* evals, cudaStream_t s, LaunchLog* log) {
     const int n_tiles = cam.tiles_x * cam.tiles_y;
     if (n_tiles <= 0) return cudaSuccess;
     switch (cam.tile_size) {
-        case 8: return blend_ts<8>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, num_sms, evals, s, log);
-        case 16: return blend_ts<16>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, num_sms, evals, s, log);
-        case 32: return blend_ts<32>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, scratch, scan_scratch, num_sms, evals, s, log);
+        case 8: return blend_ts<8>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log);
+        case 16: return blend_ts<16>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log);
+        case 32: return blend_ts<32>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log);
         default: return cudaErrorInvalidValue;
     }
 }

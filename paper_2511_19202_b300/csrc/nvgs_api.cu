@@ -833,8 +833,8 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     unsigned long long* evals = f->profile >= 2 ? reinterpret_cast<unsigned long long*>(counters + 10) : nullptr;
     if (evals) CK(cudaMemsetAsync(evals, 0, 8, s));
     CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, cam_dev, img_dev, fT, nc, mark,
-                    split_len, n_pairs, ctx->split_scratch.p, ctx->scratch.p, ctx->num_sms, evals, s,
-                    &ctx->log));
+                    split_len, n_pairs, nullptr, ctx->split_scratch.p, ctx->scratch.p, ctx->num_sms, evals,
+                    s, &ctx->log));
     if (evals) CK(cudaMemcpyAsync(ctx->h_counters + 10, counters + 10, 8, cudaMemcpyDeviceToHost, s));
     if (labels_row) CK(launch_mark_labels(surv, n_surv, mark, labels_row, s, &ctx->log));
     tm.mark(NVGS_NUM_STAGES);
@@ -1247,18 +1247,19 @@ static nvgs_status enqueue_view_async(nvgs_ctx* ctx, const CamParams& cp, const 
     uint32_t* svals = in_alt ? P<uint32_t>(ctx->vals_alt) : P<uint32_t>(ctx->vals);
     CK(launch_tile_ranges(skeys, (uint32_t)pair_cap, counters + 2, (uint32_t)n_tiles, P<uint32_t>(ctx->ranges),
                           s, &ctx->log));
-    // S6
-    const uint64_t auto_len = std::max<uint64_t>(4096, 4 * (pair_cap / (uint64_t)n_tiles + 1));
+    // S6.  The automatic split length depends on the frame's pair count, which only the device
+    // knows here: it is resolved there with the synchronous path's rule (so both paths split the
+    // same tiles and give the same image), and the scratch is sized for its lower bound 4096.
+    const bool auto_split = f->blend_split_len == 0;
     const uint32_t split_len = f->blend_split_len < 0 ? 0xffffffffu
-                               : (f->blend_split_len == 0 ? (uint32_t)std::min<uint64_t>(auto_len, 0x7fffffffu)
-                                                          : (uint32_t)f->blend_split_len);
+                               : (auto_split ? 4096u : (uint32_t)f->blend_split_len);
     if (pair_cap > split_len) {
         CK(ensure(ctx->split_scratch, blend_split_scratch_bytes(n_tiles, pair_cap, cp.tile_size, split_len)));
         CK(ensure(ctx->scratch, scan_scratch_bytes(n_tiles)));
     }
     CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, cam_dev, image, nullptr, nullptr,
-                    nullptr, split_len, pair_cap, ctx->split_scratch.p, ctx->scratch.p, ctx->num_sms, nullptr, s,
-                    &ctx->log));
+                    nullptr, split_len, pair_cap, auto_split ? counters + 2 : nullptr, ctx->split_scratch.p,
+                    ctx->scratch.p, ctx->num_sms, nullptr, s, &ctx->log));
     // this view's counts
     CK(cudaMemcpyAsync(view_counts, counters, 3 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     return NVGS_OK;

@@ -332,13 +332,16 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, const uint32_t*
 // mark (nullable, per survivor): set to 1 when the survivor is blended at some pixel.  evals
 // (nullable, device): receives the number of (pixel, fragment) evaluations (profiling).
 // Tiles with more than split_len pairs take the chunked path; scratch must hold
-// blend_split_scratch_bytes(...), scan_scratch a scan of n_tiles values.
+// blend_split_scratch_bytes(...), scan_scratch a scan of n_tiles values.  auto_split_pairs
+// (device, nullable): the split length is the automatic one, computed on the device from this pair
+// count with the host's rule; split_len is then its lower bound 4096 (scratch sizing) and n_pairs
+// the pair capacity.
 size_t blend_split_scratch_bytes(int n_tiles, uint64_t n_pairs, int tile_size, uint32_t split_len);
 cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const float4* rec,
                          const CamParams& cam, const CamParams* cam_dev, float* image, float* final_T,
                          int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
-                         void* scratch, void* scan_scratch, int num_sms, unsigned long long* evals,
-                         cudaStream_t s, LaunchLog* log);
+                         const uint32_t* auto_split_pairs, void* scratch, void* scan_scratch,
+                         int num_sms, unsigned long long* evals, cudaStream_t s, LaunchLog* log);
 // labels[row * n_gauss + g] |= mark[s] for survivor s = (instance, g)
 cudaError_t launch_mark_labels(const uint2* surv, uint32_t n_surv, const uint8_t* mark,
                                uint8_t* labels_row, cudaStream_t s, LaunchLog* log);

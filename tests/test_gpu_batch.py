@@ -127,3 +127,29 @@ def test_autotuner_times_every_candidate_and_images_do_not_depend_on_the_choice(
             assert torch.equal(imgs[8][k], imgs[16][k]) and torch.equal(imgs[16][k], imgs[32][k])
     finally:
         r.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_automatic_split_equals_the_synchronous_render(use_graph):
+    """The automatic dense-tile split length depends on the frame's pair count.  The sync-free
+    batch knows only its pair capacity (here 3x the count), so it resolves the length on the
+    device from the count: it splits the same tiles as the synchronous render and the images are
+    equal bit for bit."""
+    sc = scenes.config1_scene(20000)
+    # the torus covers a few of the 64 tiles of a 128 x 128 view: those tiles hold many times
+    # the mean tile's pairs and more than the 4096-pair minimum
+    cam = scenes.look_at_camera((0.0, 0.0, 12.0), (0, 0, 0), 128, 128, 50.0)
+    r = renderer_for(sc)
+    try:
+        fl = lambda split: r.flags(use_mlp=0, blend_split_len=split)
+        auto, st = r.render(cam, fl(0))
+        auto = auto.clone()
+        never, _ = r.render(cam, fl(-1))
+        assert not torch.equal(auto, never), "no tile was split: the case does not exercise the path"
+        out = [torch.empty_like(auto)]
+        for _ in range(2):   # the second call replays the captured graph
+            r.render_batch([cam], fl(0), out=out, max_pairs=3 * st["n_pairs"], use_graph=use_graph)
+            torch.cuda.synchronize()
+            assert torch.equal(out[0], auto)
+    finally:
+        r.close()
