@@ -143,11 +143,16 @@ cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const flo
     if (n == 0) return cudaSuccess;
     // a grid-stride kernel with equal shares per CTA: exactly the CTAs that are resident at once
     // (a fraction of a second wave would run alone at the end)
-    static int per_sm = 0;
+    int dev = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static std::atomic<int> per_sm_cache[64];   // per device ordinal; 0 = not measured yet
+    if (dev >= 0 && dev < 64) per_sm = per_sm_cache[dev].load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_duplicate, 256, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_duplicate, 256, 0);
         if (e != cudaSuccess) return e;
         per_sm = std::max(per_sm, 1);
+        if (dev >= 0 && dev < 64) per_sm_cache[dev].store(per_sm, std::memory_order_relaxed);
     }
     const uint32_t warps = (n + 31) / 32;
     const uint32_t grid = std::min<uint32_t>((warps + 7) / 8, (uint32_t)(num_sms * per_sm));

@@ -417,11 +417,12 @@ cudaError_t launch_mlp_f8(const uint2* list, const float4* list_mean, uint32_t n
                           const FrameInst* fi, const AssetDev* assets, float threshold, uint32_t* keep_bits,
                           float* logits_out, uint32_t* err_flag, int num_sms, cudaStream_t s, LaunchLog* log) {
     if (n == 0) return cudaSuccess;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_f8, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    static std::atomic<uint64_t> attr_done{0};
+    {
+        cudaError_t e = once_per_device(attr_done, [] {
+            return cudaFuncSetAttribute(k_mlp_f8, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        });
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     const uint32_t steps = (n + kRows - 1) / kRows;
     const uint32_t grid = std::min<uint32_t>(steps, (uint32_t)num_sms * kCtasPerSm);

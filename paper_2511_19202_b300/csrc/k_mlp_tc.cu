@@ -424,11 +424,12 @@ cudaError_t launch_mlp_tc(const uint2* list, const float4* list_mean, uint32_t n
                           float threshold, uint32_t* keep_bits, float* logits_out, uint32_t* err_flag,
                           int num_sms, int ctas_per_sm, cudaStream_t s, LaunchLog* log) {
     if (n == 0) return cudaSuccess;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    static std::atomic<uint64_t> attr_done{0};
+    {
+        cudaError_t e = once_per_device(attr_done, [] {
+            return cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        });
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     const uint32_t steps = (n + kRows - 1) / kRows;
     const uint32_t per_sm = ctas_per_sm >= 1 && ctas_per_sm <= kCtasPerSm ? (uint32_t)ctas_per_sm

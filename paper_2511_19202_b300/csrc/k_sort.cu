@@ -384,12 +384,13 @@ static cudaError_t radix_sort_impl(K* keys, uint32_t* values, K* keys_alt, uint3
     if (passes_out) *passes_out = passes;
     if (result_in_alt) *result_in_alt = 0;
     if (passes == 0) return cudaSuccess;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_rs_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    static std::atomic<uint64_t> attr_done{0};
+    {
+        cudaError_t e = once_per_device(attr_done, [] {
+            return cudaFuncSetAttribute(k_rs_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              rs_smem_bytes<K>());
+        });
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     const uint64_t tiles = (n + kRsTile - 1) / kRsTile;
     const uint64_t h = (256 * tiles * 4 + 255) / 256 * 256;

@@ -315,11 +315,12 @@ cudaError_t launch_train_step(const AssetDev* asset_dev, uint32_t n_gauss, const
                               uint32_t* n_pos, float* loss_sum, float* partial, float* w, float* m,
                               float* v, float lr, float beta1, float beta2, float eps,
                               cudaStream_t s, LaunchLog* log) {
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_train_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    static std::atomic<uint64_t> attr_done{0};
+    {
+        cudaError_t e = once_per_device(attr_done, [] {
+            return cudaFuncSetAttribute(k_train_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        });
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     cudaError_t e = cudaMemsetAsync(n_pos, 0, 4, s);
     if (e != cudaSuccess) return e;

@@ -4,9 +4,27 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/nvgs.h"
 
 namespace nvgs {
+
+// Per-device once-only setup of a kernel (a function attribute belongs to the device it was set
+// on): `done` holds one bit per device ordinal below 64; a device at or above 64 repeats the setup
+// every time, which is correct, only slower.  Setting the same attribute twice is harmless, so
+// two host threads that race here both succeed.
+template <typename Setup>
+cudaError_t once_per_device(std::atomic<uint64_t>& done, Setup setup) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = setup();
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 constexpr int kMlpIn = 32;
 constexpr int kMlpHidden = 64;
