@@ -42,7 +42,7 @@ typedef enum {
     NVGS_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
     NVGS_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
     NVGS_ERR_CAPACITY = 5,     /* a fixed-capacity buffer would overflow */
-    NVGS_ERR_UNSUPPORTED = 6   /* valid request this build cannot serve */
+    NVGS_ERR_UNSUPPORTED = 6   /* a valid request the library does not implement */
 } nvgs_status;
 
 typedef enum { NVGS_MEM_HOST = 0, NVGS_MEM_DEVICE = 1 } nvgs_memory;
