@@ -159,13 +159,19 @@ constexpr int kRsTile = kRsThreads * kRsItems;  // 4096
 constexpr int kRsWarps = kRsThreads / 32;       // 8
 
 // Lanes of the warp whose 8-bit digit equals this lane's, from one ballot per bit (cheaper than
-// a warp match instruction); lanes with ok = false match only themselves.
-__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool ok) {
+// a warp match instruction); lanes with ok = false match only themselves.  `vary` (the same in
+// every thread) has a bit set for every digit bit that differs between some keys of the pass: a
+// bit that every key shares cannot separate two of them, so its ballot is skipped (the ranking is
+// bound by the integer ALU pipe, and e.g. 13-bit tile ids leave three bits of their second digit
+// constant).
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool ok, uint32_t vary) {
     uint32_t peers = __ballot_sync(0xffffffffu, ok);
 #pragma unroll
     for (int b = 0; b < 8; b++) {
-        const uint32_t m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-        peers &= ((d >> b) & 1u) ? m : ~m;
+        if (vary & (1u << b)) {
+            const uint32_t m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? m : ~m;
+        }
     }
     return ok ? peers : 1u << (threadIdx.x & 31);
 }
@@ -271,8 +277,23 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatt
     // their latency hides behind the ranking
     const uint32_t my_total = totals[threadIdx.x];
     const uint32_t my_hs = hist_scan[(uint64_t)threadIdx.x * n_tiles + tile];
+    // the digit bits that differ between keys of the pass: OR of the present digits (a pass total
+    // above 0) and OR of their complements, per warp here and over the CTA after the barrier
+    // (d_global is free until the bucket starts are written)
+    {
+        const uint32_t any1 = __reduce_or_sync(0xffffffffu, my_total ? threadIdx.x : 0u);
+        const uint32_t any0 = __reduce_or_sync(0xffffffffu, my_total ? (~threadIdx.x & 255u) : 0u);
+        if (lane == 0) { d_global[warp] = any1; d_global[kRsWarps + warp] = any0; }
+    }
     for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) cnt[k] = 0u;
     __syncthreads();
+    uint32_t vm;
+    {
+        uint32_t any1 = 0u, any0 = 0u;
+#pragma unroll
+        for (int w = 0; w < kRsWarps; w++) { any1 |= d_global[w]; any0 |= d_global[kRsWarps + w]; }
+        vm = any1 & any0;
+    }
 
     const uint64_t base = (uint64_t)tile * kRsTile;
     const uint64_t tile_n64 = n - base < (uint64_t)kRsTile ? n - base : (uint64_t)kRsTile;
@@ -298,7 +319,7 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatt
         // the lowest lane of each digit group reserves the group's slots with one shared-memory
         // atomic; a warp's atomics on a counter complete in program order, so the ranks keep the
         // input order (stable) without a load / store round trip between the items
-        const uint32_t peers = digit_peers(d & 255u, ok);
+        const uint32_t peers = digit_peers(d & 255u, ok, vm);
         const int leader = __ffs(peers) - 1;
         uint32_t before = 0u;
         if (ok && leader == lane) before = atomicAdd(&cnt[warp * 256 + d], (uint32_t)__popc(peers));
