@@ -402,8 +402,9 @@ nvgs_status nvgs_last_frame(const nvgs_ctx* ctx, nvgs_frame_view* out);
 
 /* ------------------------------------------------------------------ building blocks */
 /* Stable LSD radix sort of n (key, value) pairs on the low `key_bits` bits of the keys, in
- * place, on DEVICE arrays (the library's scratch is used for the ping-pong buffers).  The S5
- * sort of nvgs_render is this routine. */
+ * place, on DEVICE arrays (the library's scratch is used for the ping-pong buffers).  Bits at or
+ * above key_bits may be set; they do not influence the order.  The S5 sort of nvgs_render is this
+ * routine. */
 nvgs_status nvgs_sort_pairs(nvgs_ctx* ctx, uint64_t* keys, uint32_t* values, int64_t n,
                             int key_bits);
 
@@ -416,9 +417,13 @@ nvgs_status nvgs_sort_pairs(nvgs_ctx* ctx, uint64_t* keys, uint32_t* values, int
  *   keys, values : DEVICE arrays of n pairs, sorted in place (stable, low key_bits bits)
  *   n            : 0 .. NVGS_SORT_NOALLOC_MAX_PAIRS; larger n returns NVGS_ERR_CAPACITY and
  *                  enqueues nothing
- *   cuda_stream  : cudaStream_t to enqueue on (NULL = the legacy default stream)
+ *   cuda_stream  : cudaStream_t to enqueue on (NULL = the legacy default stream); it must
+ *                  belong to the current device, else NVGS_ERR_INVALID_ARG
+ * Keys may carry bits at or above key_bits; they do not influence the order.
  * The first call on a device looks up the scratch array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  All calls share
+ * with that device current; make that first call before any stream capture.  The address is kept
+ * for the life of the process, which assumes that every device keeps its primary context: do not
+ * call this entry point after cudaDeviceReset or under another driver-API context.  All calls share
  * the one array and leave their data in it; calls that overlap on the GPU race, so serialise
  * them.  Returns NVGS_ERR_INVALID_ARG for bad arguments and NVGS_ERR_CUDA if a launch fails. */
 #define NVGS_SORT_NOALLOC_MAX_PAIRS (1u << 20)

@@ -2,7 +2,8 @@
 // (tile, depth) keys).  Both are reduce-then-scan designs: no CTA ever waits on another, so
 // there is no inter-CTA spin of any kind.
 //
-// Radix sort, per 8-bit digit pass over tiles of 4096 pairs (256 threads x 16):
+// Radix sort, per digit pass (8 bits by default, 1..8 selectable) over tiles of 4096 pairs
+// (256 threads x 16):
 //   1. k_rs_hist:        per-tile digit histogram, stored digit-major: hist[d * n_tiles + tile]
 //   2. k_rs_digit_scan:  one CTA per digit scans its row in place (start of every (digit, tile)
 //                        bucket among that digit's buckets) and writes the digit's total; the
@@ -184,7 +185,8 @@ constexpr int rs_smem_bytes() { return kRsWarps * 256 * 4 + kRsTile * (int)sizeo
 template <typename K>
 __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ keys, uint64_t n,
                                                         const uint32_t* __restrict__ n_dev, int shift,
-                                                        uint32_t n_tiles, uint32_t* __restrict__ hist) {
+                                                        uint32_t mask, uint32_t n_tiles,
+                                                        uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[kRsWarps][256];
     if (n_dev) n = min(n, (uint64_t)*n_dev);
     const int warp = threadIdx.x >> 5;
@@ -206,16 +208,16 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ ke
         for (int j = 0; j < kRsItems / 4; j++) v[j] = k4[j * kRsThreads + threadIdx.x];
 #pragma unroll
         for (int j = 0; j < kRsItems / 4; j++) {
-            atomicAdd(&h[warp][(v[j].x >> shift) & 255u], 1u);
-            atomicAdd(&h[warp][(v[j].y >> shift) & 255u], 1u);
-            atomicAdd(&h[warp][(v[j].z >> shift) & 255u], 1u);
-            atomicAdd(&h[warp][(v[j].w >> shift) & 255u], 1u);
+            atomicAdd(&h[warp][(v[j].x >> shift) & mask], 1u);
+            atomicAdd(&h[warp][(v[j].y >> shift) & mask], 1u);
+            atomicAdd(&h[warp][(v[j].z >> shift) & mask], 1u);
+            atomicAdd(&h[warp][(v[j].w >> shift) & mask], 1u);
         }
     } else {
 #pragma unroll 4
         for (int j = 0; j < kRsItems; j++) {
             const uint64_t i = base + (uint64_t)j * kRsThreads + threadIdx.x;
-            if (i < n) atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & 255u], 1u);
+            if (i < n) atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & mask], 1u);
         }
     }
     __syncthreads();
@@ -261,7 +263,8 @@ template <typename K>
 __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatter(
     const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, K* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, uint64_t n, const uint32_t* __restrict__ n_dev, int shift,
-    uint32_t n_tiles, const uint32_t* __restrict__ hist_scan, const uint32_t* __restrict__ totals) {
+    uint32_t mask, uint32_t n_tiles, const uint32_t* __restrict__ hist_scan,
+    const uint32_t* __restrict__ totals) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* cnt = (uint32_t*)smem;                                   // [8 warps][256]
     K* s_keys = (K*)(smem + kRsWarps * 256 * 4);
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatt
     for (int r = 0; r < kRsItems; r++) {
         const int p = warp * (kRsItems * 32) + r * 32 + lane;
         const bool ok = p < tile_n;
-        const uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u + lane;  // unmatched
+        const uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & mask) : 256u + lane;  // unmatched
         // the lowest lane of each digit group reserves the group's slots with one shared-memory
         // atomic; a warp's atomics on a counter complete in program order, so the ranks keep the
         // input order (stable) without a load / store round trip between the items
@@ -378,7 +381,7 @@ __global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatt
         const int p = j * kRsThreads + threadIdx.x;
         if (p < tile_n) {
             const K k = s_keys[p];
-            const uint32_t d = (uint32_t)(k >> shift) & 255u;
+            const uint32_t d = (uint32_t)(k >> shift) & mask;
             const uint64_t g = (uint64_t)d_global[d] + (uint32_t)(p - d_local[d]);
             keys_out[g] = k;
             vals_out[g] = s_vals[p];
@@ -394,12 +397,15 @@ size_t radix_scratch_bytes(uint64_t n) {
 
 // n is the element count, or with n_dev the capacity (the count then lives on the device and
 // every kernel reads it; nothing here waits for it).
+// Digits are `digit_bits` wide (1..8); the last pass takes only the key bits that remain, so bits
+// at or above key_bits never influence the order.
 template <typename K>
 static cudaError_t radix_sort_impl(K* keys, uint32_t* values, K* keys_alt, uint32_t* values_alt,
                                    uint64_t n, int key_bits, void* scratch, cudaStream_t s,
                                    LaunchLog* log, int* passes_out, int copy_back, int* result_in_alt,
-                                   const uint32_t* n_dev) {
-    int passes = key_bits <= 0 ? 0 : (key_bits + 7) / 8;
+                                   const uint32_t* n_dev, int digit_bits = 8) {
+    if (digit_bits < 1 || digit_bits > 8) return cudaErrorInvalidValue;
+    int passes = key_bits <= 0 ? 0 : (key_bits + digit_bits - 1) / digit_bits;
     if (n <= 1 && !n_dev) passes = 0;
     if (n == 0) passes = 0;
     if (passes_out) *passes_out = passes;
@@ -428,14 +434,16 @@ static cudaError_t radix_sort_impl(K* keys, uint32_t* values, K* keys_alt, uint3
     const unsigned hgrid = (unsigned)tiles;
     const unsigned sgrid = (unsigned)tiles;
     for (int p = 0; p < passes; p++) {
-        const int shift = 8 * p;
-        NVGS_LAUNCH(log, s, hname, k_rs_hist<K><<<hgrid, kRsThreads, 0, s>>>(kin, n, n_dev, shift, (uint32_t)tiles, hist));
+        const int shift = digit_bits * p;
+        const int width = std::min(digit_bits, key_bits - shift);
+        const uint32_t mask = (1u << width) - 1u;
+        NVGS_LAUNCH(log, s, hname, k_rs_hist<K><<<hgrid, kRsThreads, 0, s>>>(kin, n, n_dev, shift, mask, (uint32_t)tiles, hist));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         NVGS_LAUNCH(log, s, "k_rs_digit_scan", k_rs_digit_scan<<<256, 256, 0, s>>>(hist, (uint32_t)tiles, totals));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        NVGS_LAUNCH(log, s, sname, k_rs_scatter<K><<<sgrid, kRsThreads, rs_smem_bytes<K>(), s>>>(kin, vin, kout, vout, n, n_dev, shift, (uint32_t)tiles, hist, totals));
+        NVGS_LAUNCH(log, s, sname, k_rs_scatter<K><<<sgrid, kRsThreads, rs_smem_bytes<K>(), s>>>(kin, vin, kout, vout, n, n_dev, shift, mask, (uint32_t)tiles, hist, totals));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         K* tk = kin; kin = kout; kout = tk;
@@ -465,9 +473,9 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* values,
 cudaError_t radix_sort_pairs_u32(uint32_t* keys, uint32_t* values, uint32_t* keys_alt,
                                  uint32_t* values_alt, uint64_t n, int key_bits, void* scratch,
                                  cudaStream_t s, LaunchLog* log, int* passes_out, int copy_back,
-                                 int* result_in_alt, const uint32_t* n_dev) {
+                                 int* result_in_alt, const uint32_t* n_dev, int digit_bits) {
     return radix_sort_impl<uint32_t>(keys, values, keys_alt, values_alt, n, key_bits, scratch, s, log,
-                                     passes_out, copy_back, result_in_alt, n_dev);
+                                     passes_out, copy_back, result_in_alt, n_dev, digit_bits);
 }
 
 }  // namespace nvgs

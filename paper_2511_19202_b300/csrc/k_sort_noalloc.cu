@@ -11,7 +11,12 @@
 // the library holds it until the process exits.  Host code cannot pass the symbol itself to a
 // kernel (in host code it names a host-side stand-in), so the first call on each device looks up
 // its device address with cudaGetSymbolAddress while that device is current, and later calls on
-// that device reuse it.  Make the first call on a device before any stream capture.
+// that device reuse it.  Make the first call on a device before any stream capture.  The cached
+// address assumes that each device keeps its primary CUDA context for the life of the process:
+// after cudaDeviceReset, or from a thread whose current context is another driver-API context
+// of the same device, the cached address no longer names the array, so do not call this entry
+// point there.  The stream must belong to the current device (checked: a stream of another
+// device returns NVGS_ERR_INVALID_ARG).
 //
 // Every call shares the one array, and the array keeps whatever the last call left in it.
 // Nothing in it has to start at zero: each radix pass writes every histogram entry, scan entry
@@ -61,6 +66,13 @@ extern "C" nvgs_status nvgs_sort_pairs_noalloc(uint64_t* keys, uint32_t* values,
     if (n > 0 && (!keys || !values)) return NVGS_ERR_INVALID_ARG;
     if (n <= 1 || key_bits == 0) return NVGS_OK;
     if (nvgs::radix_scratch_bytes((uint64_t)n) > kNoAllocRadix) return NVGS_ERR_CAPACITY;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NVGS_ERR_CUDA;
+    if (cuda_stream) {   // the scratch address is the current device's: the stream must match
+        int sdev = -1;
+        if (cudaStreamGetDevice((cudaStream_t)cuda_stream, &sdev) != cudaSuccess) return NVGS_ERR_INVALID_ARG;
+        if (sdev != dev) return NVGS_ERR_INVALID_ARG;
+    }
     void* base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return NVGS_ERR_CUDA;
     unsigned char* b = static_cast<unsigned char*>(base);

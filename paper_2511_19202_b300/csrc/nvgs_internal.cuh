@@ -374,7 +374,8 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, ui
                                void* scratch, cudaStream_t s, LaunchLog* log,
                                const uint32_t* n_dev = nullptr);
 
-// Stable LSD radix sort (8-bit digits) of n (key, value) pairs on bits [0, key_bits).
+// Stable LSD radix sort (8-bit digits) of n (key, value) pairs on bits [0, key_bits); key bits at
+// or above key_bits are ignored (they never change the order).
 // keys/values hold the input; the alt buffers must hold n entries each.  With copy_back the
 // result always lands in keys/values; otherwise *result_in_alt tells where it is.
 // Scratch: radix_scratch_bytes(n).
@@ -383,12 +384,13 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* values,
                              unsigned long long* keys_alt, uint32_t* values_alt, uint64_t n,
                              int key_bits, void* scratch, cudaStream_t s, LaunchLog* log,
                              int* passes_out, int copy_back, int* result_in_alt);
-// The same sort for 32-bit keys.
+// The same sort for 32-bit keys, with digits of digit_bits (1..8) bits.
 // With n_dev the element count is read on the device (n is the capacity).
 cudaError_t radix_sort_pairs_u32(uint32_t* keys, uint32_t* values, uint32_t* keys_alt,
                                  uint32_t* values_alt, uint64_t n, int key_bits, void* scratch,
                                  cudaStream_t s, LaunchLog* log, int* passes_out, int copy_back,
-                                 int* result_in_alt, const uint32_t* n_dev = nullptr);
+                                 int* result_in_alt, const uint32_t* n_dev = nullptr,
+                                 int digit_bits = 8);
 
 // N2: gradients of the render (k_backward.cu).  gsurv: render_backward_scratch_bytes(n_surv).
 size_t render_backward_scratch_bytes(uint64_t n_surv);

@@ -9,8 +9,8 @@ import pytest
 
 import oracle
 import scenes
-from gpu_common import (check_pruned_tile_lists, compare_images, gpu_image, oracle_opts_for,
-                        renderer_for)
+from gpu_common import (check_exact_tile_lists, check_pruned_tile_lists, compare_images, gpu_image,
+                        oracle_opts_for, renderer_for)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -137,7 +137,51 @@ def test_fixed_logits_culled_set_and_order_are_exact(cfg1_setup):
     assert set(np.nonzero(kp != keep)[0].tolist()) <= amb
 
 
-def test_tile_lists_are_exact(cfg1_setup):
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_tile_lists_are_exact(cfg1_setup, tile):
+    """S5 parity: every tile's list equals the oracle's FP64 list (the tiles of the splat's support
+    rectangle whose pixel-centre box meets its support ellipse), element for element and in blend
+    order (depth, instance, gaussian), outside the band of pairs a conservative FP32 binner may take
+    either way; per-tile counts and ranges of every tile equal the oracle's outside that band."""
+    sc, cam, r, osc = cfg1_setup
+    o = oracle_opts_for(dict(tile_size=tile))
+    _, st = gpu_image(r, cam, use_mlp=0, tile_size=tile)
+    lf = r.last_frame()
+    vals = lf["pair_values"].cpu().numpy().astype(np.int64)
+    surv = lf["survivors"].cpu().numpy()
+    rec = lf["records"].cpu().numpy().reshape(-1, 12)
+    gpu_tiles = lf["pair_keys"].cpu().numpy().astype(np.int64)
+    assert np.all(np.diff(gpu_tiles) >= 0)
+    sp = oracle.project(osc, cam, o)
+    ell = oracle.tile_lists_ellipse(sp, cam, tile)
+    drop = set(zip(sp["instance"][sp["ambiguous"] != 0].tolist(), sp["gaussian"][sp["ambiguous"] != 0].tolist()))
+    depth_of = dict(zip(zip(sp["instance"].tolist(), sp["gaussian"].tolist()), sp["depth"].tolist()))
+    n, n_band, n_drop = check_exact_tile_lists(gpu_tiles, surv[vals, 0], surv[vals, 1], rec[vals, 6],
+                                               ell, depth_of, drop)
+    print(f"tile {tile}: {n} pairs equal, {n_band} in the band, {n_drop} of dropped splats "
+          f"(gpu {len(gpu_tiles)} pairs)")
+    assert n > 10000 and n_band <= 1e-3 * n
+    # ranges of EVERY tile: [start, end) of its pairs in the sorted list; counts = oracle's counts
+    # up to the tile's band and dropped pairs
+    n_tiles = lf["tiles_x"] * lf["tiles_y"]
+    rng_ = lf["tile_ranges"].cpu().numpy().reshape(-1, 2)[:n_tiles]
+    cnt = np.bincount(gpu_tiles, minlength=n_tiles)
+    starts = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    occupied = cnt > 0
+    np.testing.assert_array_equal(rng_[occupied, 0], starts[occupied])
+    np.testing.assert_array_equal(rng_[occupied, 1], starts[occupied] + cnt[occupied])
+    assert np.all(rng_[~occupied, 0] == rng_[~occupied, 1])
+    et, ei, eg, ea = ell
+    band = set(zip(et[ea].tolist(), ei[ea].tolist(), eg[ea].tolist()))
+    sure_o = ~ea & np.array([(b, c) not in drop for b, c in zip(ei.tolist(), eg.tolist())], bool)
+    gi, gg = surv[vals, 0], surv[vals, 1]
+    sure_g = np.array([(b, c) not in drop and (t, b, c) not in band
+                       for t, b, c in zip(gpu_tiles.tolist(), gi.tolist(), gg.tolist())], bool)
+    np.testing.assert_array_equal(np.bincount(gpu_tiles[sure_g], minlength=n_tiles),
+                                  np.bincount(et[sure_o], minlength=n_tiles))
+
+
+def test_tile_lists_lie_between_support_and_rect_lists(cfg1_setup):
     """Every tile holding a pixel a splat can blend at lists it (front to back); pruned tiles are
     only ever tiles of its rectangle."""
     sc, cam, r, osc = cfg1_setup
@@ -147,7 +191,6 @@ def test_tile_lists_are_exact(cfg1_setup):
     vals = lf["pair_values"].cpu().numpy().astype(np.int64)
     surv = lf["survivors"].cpu().numpy()
     gpu_tiles = lf["pair_keys"].cpu().numpy().astype(np.int64)
-    assert np.all(np.diff(gpu_tiles) >= 0)
     sp = oracle.project(osc, cam, o)
     support = oracle.tile_lists(sp, cam, 16, mode="support")
     rect = oracle.tile_lists(sp, cam, 16, mode="rect")
@@ -157,11 +200,6 @@ def test_tile_lists_are_exact(cfg1_setup):
                                                    depth_of, drop)
     print(f"pairs: gpu {n_gpu}, support {n_sup}, rect {n_rect}")
     assert n_sup > 10000 and n_gpu < n_rect
-    # ranges cover exactly the sorted pairs of each tile
-    rng_ = lf["tile_ranges"].cpu().numpy()
-    for t in np.unique(gpu_tiles)[:50]:
-        idx = np.nonzero(gpu_tiles == t)[0]
-        assert rng_[t, 0] == idx[0] and rng_[t, 1] == idx[-1] + 1
 
 
 # ----------------------------------------------------------------------------- S2 (FP32)
@@ -282,6 +320,24 @@ def test_radix_sort_is_a_stable_sort(cfg1_setup, n, bits, spread):
     order = np.argsort(keys, kind="stable")
     np.testing.assert_array_equal(dk.cpu().numpy().view(np.uint64), keys[order])
     np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), vals[order])
+
+
+@pytest.mark.parametrize("n,bits", [(65_537, 13), (8193, 4), (100_003, 20), (5000, 1)])
+def test_radix_sort_ignores_key_bits_above_key_bits(cfg1_setup, n, bits):
+    """Keys with random bits set above key_bits: the result is the stable sort on the low key_bits
+    bits alone (the last digit pass is masked), the full keys carried along."""
+    sc, cam, r, osc = cfg1_setup
+    rng = np.random.default_rng(n + 7 * bits)
+    low = rng.integers(0, 1 << bits, n, dtype=np.uint64)
+    keys = low | (rng.integers(0, 1 << (63 - bits), n, dtype=np.uint64) << np.uint64(bits))
+    vals = np.arange(n, dtype=np.uint32)
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    dv = torch.from_numpy(vals.view(np.int32)).cuda()
+    r.sort_pairs(dk, dv, bits)
+    torch.cuda.synchronize()
+    order = np.argsort(low, kind="stable")
+    np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), vals[order])
+    np.testing.assert_array_equal(dk.cpu().numpy().view(np.uint64), keys[order])
 
 
 # ----------------------------------------------------------------------------- dense-tile split
