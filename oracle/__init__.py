@@ -15,6 +15,9 @@ restates:
 * ``project``                Sec. 3.3 -> original 3DGS preprocessing (EWA splat, SH colour)
 * ``composite``/``render``   Sec. 4.1 blending rules, exact per-pixel depth-sorted compositing
 * ``labels``                 Sec. 3.1 (contribution alpha * T; visible iff it blends)
+* ``tile_lists``/``tile_lists_ellipse``  Sec. 3.3 -> tiled rasterisation: per-tile lists in blend
+  order (support rectangle, exact pixel support, and the support ellipse met by each tile's
+  pixel-centre box, with the band a conservative binner may take either way)
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py`` against closed
 forms, invariants, brute force or independent library routines.
@@ -424,6 +427,85 @@ def tile_lists(splats: np.ndarray, cam, tile_size: int, mode: str = "rect", alph
         return tiles, inst, gs
     order = np.lexsort((gs, inst, depth, tiles))
     return tiles[order], inst[order], gs[order]
+
+
+def box_min_quadratic(a, b, c, x0, x1, y0, y1):
+    """min over the box [x0, x1] x [y0, y1] (offsets from the splat mean) of the positive-definite
+    form q(x, y) = a x^2 + 2 b x y + c y^2, element-wise over arrays.  Zero if the box holds the
+    origin; otherwise the minimum lies on an edge, where q is a parabola in the free coordinate
+    with its vertex at -b x / c (vertical edges) or -b y / a (horizontal edges), clamped."""
+    a, b, c, x0, x1, y0, y1 = np.broadcast_arrays(*(np.asarray(v, np.float64) for v in (a, b, c, x0, x1, y0, y1)))
+
+    def q(x, y):
+        return a * x * x + 2.0 * b * x * y + c * y * y
+
+    best = np.full(a.shape, np.inf)
+    for xe in (x0, x1):                       # vertical edges x = xe
+        y = np.clip(-b * xe / c, y0, y1)
+        best = np.minimum(best, q(xe, y))
+    for ye in (y0, y1):                       # horizontal edges y = ye
+        x = np.clip(-b * ye / a, x0, x1)
+        best = np.minimum(best, q(x, ye))
+    inside = (x0 <= 0.0) & (0.0 <= x1) & (y0 <= 0.0) & (0.0 <= y1)
+    return np.where(inside, 0.0, best)
+
+
+def tile_lists_ellipse(splats: np.ndarray, cam, tile_size: int, alpha_min=1.0 / 255.0,
+                       band_rel=1e-4, band_abs=1e-3, pad_abs=1e-3, pad_rel=1e-5):
+    """Tile lists of the pruned binning (R3: exact support, with tiles pruned to the support
+    ellipse), in FP64.  A splat of a tile rectangle with more than one tile is listed in tile T
+    iff its support ellipse {d : d^T conic d <= kk}, kk = 2 ln(opacity / alpha_min), meets the box
+    spanned by T's pixel centres [tx ts + 1/2, tx ts + ts - 1/2] x [ty ts + 1/2, ty ts + ts - 1/2]
+    (tiles past the image edge keep their full box); a one-tile rectangle is listed as is.
+
+    A conservative binner in lower precision widens the ellipse: its level by ``band_rel``
+    relative plus ``band_abs``, and its horizontal extent by ``pad_abs`` plus ``pad_rel`` of the
+    extent.  Pairs whose minimum of q over the tile box lies above kk but within that widening
+    (plus an FP32 coordinate allowance) may be listed or not: they are returned as ambiguous.
+
+    Returns (tiles, instances, gaussians, ambiguous): every listed or ambiguous pair, sorted by
+    tile, then blend order (depth, instance, gaussian); ``ambiguous`` marks the band pairs."""
+    tw = (int(cam.width) + tile_size - 1) // tile_size
+    v = splats[splats["valid"] != 0]
+    ts = float(tile_size)
+    out_t, out_i, out_g, out_d, out_a = [], [], [], [], []
+    for s in v:
+        tx0, ty0 = int(s["tile_min"][0]), int(s["tile_min"][1])
+        tx1, ty1 = int(s["tile_max"][0]), int(s["tile_max"][1])
+        if tx0 > tx1 or ty0 > ty1:
+            continue
+        txs, tys = np.meshgrid(np.arange(tx0, tx1 + 1), np.arange(ty0, ty1 + 1))
+        txs, tys = txs.ravel(), tys.ravel()
+        if txs.size == 1:
+            inn, amb = np.ones(1, bool), np.zeros(1, bool)
+        else:
+            a, b, c = (float(x) for x in s["conic"])
+            kk = 2.0 * math.log(float(s["opacity"]) / alpha_min)
+            m = box_min_quadratic(a, b, c, txs * ts + 0.5 - s["u"], txs * ts + ts - 0.5 - s["u"],
+                                  tys * ts + 0.5 - s["v"], tys * ts + ts - 0.5 - s["v"])
+            k_inf = kk * (1.0 + band_rel) + band_abs
+            # horizontal pad (extent <= sqrt(ca k_inf), ca = Sigma_2D[0,0] = c / det(conic)) and an
+            # FP32 coordinate allowance, converted to q: |grad q| <= 2 sqrt(max(a, c) q) per unit
+            det_c = a * c - b * b
+            ext = math.sqrt(max(c / det_c, 0.0) * k_inf)
+            p = pad_abs + 2.0 * pad_rel * ext + 1e-6 * (cam.width + cam.height) + 1e-4
+            amax = max(a, c)
+            k_hi = k_inf * (1.0 + 1e-5) + 2.0 * math.sqrt(amax * k_inf) * p + 2.0 * amax * p * p
+            inn = m <= kk
+            amb = (m > kk) & (m <= k_hi)
+        sel = inn | amb
+        n = int(sel.sum())
+        out_t.append(tys[sel] * tw + txs[sel])
+        out_i.append(np.full(n, s["instance"]))
+        out_g.append(np.full(n, s["gaussian"]))
+        out_d.append(np.full(n, s["depth"]))
+        out_a.append(amb[sel])
+    if not out_t:
+        e = np.zeros(0, np.int64)
+        return e, e, e, np.zeros(0, bool)
+    tiles, inst, gs, depth, amb = (np.concatenate(x) for x in (out_t, out_i, out_g, out_d, out_a))
+    order = np.lexsort((gs, inst, depth, tiles))
+    return tiles[order], inst[order], gs[order], amb[order]
 
 
 def training_views_table(cams, train_fov_x=None):

@@ -3,6 +3,7 @@ C ABI, and compare with the FP64 oracle on the same seeded inputs."""
 import numpy as np
 
 import oracle
+import scenes
 
 
 def renderer_for(scene, weights=None, precision=0, **kw):
@@ -66,6 +67,46 @@ def check_pruned_tile_lists(gpu_tiles, gpu_inst, gpu_g, support, rect, depth_of,
     return count(G), count(S), count(R)
 
 
+def check_exact_tile_lists(gpu_tiles, gpu_inst, gpu_g, gpu_depth, ell, depth_of, drop, eps=4e-7):
+    """Exact tile-list parity against the oracle's FP64 ellipse lists ``ell`` = (tiles, instances,
+    gaussians, ambiguous).  Splats in ``drop`` (ambiguous for another reason: frustum plane,
+    support-box edge, ...) and the oracle's band pairs are left out of both sides; the rest must
+    be equal per tile, element for element and in order, where two neighbours may only trade places
+    if their FP64 depths lie within ``eps`` (relative) of each other.  Among equal FP32 depths
+    (``gpu_depth``, the GPU's sort key) the GPU order must be (instance, gaussian) ascending.
+    Returns (compared pairs, band pairs, dropped pairs)."""
+    et, ei, eg, ea = ell
+    band = set(zip(et[ea].tolist(), ei[ea].tolist(), eg[ea].tolist()))
+
+    def lists(t, i, g, extra=None):
+        d = {}
+        for k, (a, b, c) in enumerate(zip(t.tolist(), i.tolist(), g.tolist())):
+            if (b, c) in drop or (a, b, c) in band:
+                continue
+            d.setdefault(a, []).append((b, c) if extra is None else (b, c, extra[k]))
+        return d
+    G = lists(gpu_tiles, gpu_inst, gpu_g, gpu_depth.tolist())
+    O = lists(et, ei, eg)
+    assert set(G) == set(O), f"tiles differ: {sorted(set(G) ^ set(O))[:10]}"
+    n = 0
+    for t in O:
+        g_seq = [(b, c) for b, c, _ in G[t]]
+        o_seq = O[t]
+        assert len(set(g_seq)) == len(g_seq), f"tile {t}: duplicate pair"
+        assert sorted(g_seq) == sorted(o_seq), (f"tile {t}: {len(set(g_seq) - set(o_seq))} extra, "
+                                               f"{len(set(o_seq) - set(g_seq))} missing")
+        for k, (x, y) in enumerate(zip(g_seq, o_seq)):
+            if x != y:
+                dx, dy = depth_of[x], depth_of[y]
+                assert abs(dx - dy) <= eps * max(abs(dx), abs(dy)), f"tile {t}: order differs at {k}"
+        for (b0, c0, z0), (b1, c1, z1) in zip(G[t][:-1], G[t][1:]):
+            if z0 == z1:
+                assert (b0, c0) < (b1, c1), f"tile {t}: equal depths out of (instance, gaussian) order"
+        n += len(o_seq)
+    n_drop = sum(1 for b, c in zip(ei.tolist(), eg.tolist()) if (b, c) in drop)
+    return n, len(band), n_drop
+
+
 def bf16_round(x):
     """Round to nearest even to BF16 (as the kernel's cvt.rn and its weight packing do), as FP64."""
     u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
@@ -92,3 +133,23 @@ def bf16_reference(w, feats):
 # one BF16 rounding of an input or activation that falls the other way (FP32 features and FP32
 # accumulation on the GPU) can move the logit by a few 1e-3 of the scale.
 BF16_DECISION_BAND = 1e-2
+
+
+def layered_case(width=320, height=240, n=20000):
+    """Three instances of the workload-1 torus in separate distance ranges, with weights whose
+    logit is 10 x (cut - normalised log distance) plus small random terms through every layer:
+    trained-like, bimodal decisions (the nearest instance kept, the others culled) with the cut
+    placed by the oracle's FP64 features in the middle of the gap between the first two ranges."""
+    sc, cam = scenes.layered_scene(n), scenes.layered_camera(width, height)
+    dist = dict(d_min=1.0, d_max=20.0)
+    osc = oracle.OracleScene(sc, **dist)
+    inside, _ = oracle.frustum(osc, cam)
+    u = np.zeros(32)
+    u[30] = -1.0
+    f = oracle.visibility(osc, cam, scenes.planar_mlp_weights(3, direction=u), gate=False,
+                          return_features=True)["features"][:, 30]
+    m = sc.assets[0].n
+    near, mid = f[:m][inside[:m]], f[m:2 * m][inside[m:2 * m]]
+    cut = 0.5 * (near.max() + mid.min())
+    w = scenes.planar_mlp_weights(3, direction=u, offset=10.0 * cut)
+    return sc, cam, dist, osc, inside, w

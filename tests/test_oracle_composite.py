@@ -298,6 +298,101 @@ def test_support_tile_list_of_a_circle_off_a_tile_corner():
     assert oracle.tile_lists(sp, cam, 16, mode="support")[0].tolist() == [0, 1, 4, 5]
 
 
+def test_box_min_quadratic_against_dense_sampling():
+    """The minimum of a positive-definite quadratic over a box: never above any sampled value, and
+    within the sampling's resolution of the densest sample (2001^2 points per box), for boxes that
+    hold the origin, sit beside it and lie diagonally off it; the box on the origin gives 0."""
+    rng = np.random.default_rng(3)
+    for k in range(40):
+        L = rng.normal(size=(2, 2)) + 0.3 * np.eye(2)
+        a, b, c = (L @ L.T)[0, 0], (L @ L.T)[0, 1], (L @ L.T)[1, 1]
+        x0, y0 = rng.uniform(-3, 3, 2)
+        x1, y1 = x0 + rng.uniform(0.1, 2), y0 + rng.uniform(0.1, 2)
+        m = float(oracle.box_min_quadratic(a, b, c, x0, x1, y0, y1))
+        xs, ys = np.meshgrid(np.linspace(x0, x1, 2001), np.linspace(y0, y1, 2001))
+        q = a * xs * xs + 2 * b * xs * ys + c * ys * ys
+        assert m <= q.min() + 1e-12
+        step = max(x1 - x0, y1 - y0) / 2000
+        grad = 2 * math.sqrt(max(a, c) * max(q.min(), 1e-12)) * step + 2 * max(a, c) * step ** 2
+        assert q.min() - m <= grad + 1e-12, (k, m, q.min())
+    assert oracle.box_min_quadratic(1.0, 0.2, 2.0, -1, 1, -0.5, 0.5) == 0.0
+
+
+def _circle_splat(u, v, radius, op=0.8, tile=((0, 0), (1, 1))):
+    """One valid circular splat whose support (alpha >= 1/255) has the given radius in pixels."""
+    sp = np.zeros(1, oracle.SPLAT_DTYPE)
+    kk = 2.0 * math.log(op / (1.0 / 255.0))
+    sigma2 = radius * radius / kk
+    sp["valid"], sp["u"], sp["v"], sp["opacity"], sp["depth"] = 1, u, v, op, 1.0
+    sp["conic"] = [[1.0 / sigma2, 0.0, 1.0 / sigma2]]
+    sp["tile_min"], sp["tile_max"] = [tile[0]], [tile[1]]
+    return sp
+
+
+def test_ellipse_tile_list_of_a_circle_closed_form():
+    """Closed form: a circle of radius 5 px at (20, 20) meets the pixel-centre boxes of tiles
+    (1, 0), (0, 1) and (1, 1) (distances 4.5, 4.5 and 0) but not tile (0, 0)'s box [0.5, 15.5]^2,
+    whose corner (15.5, 15.5) lies 6.364 px away; at radius 6.4, or 1e-7 px beyond the corner, it
+    reaches that corner; 1e-7 px short of it the pair falls in the band a conservative binner may
+    take either way, and 1 % short of it the pair is out.  A circle between the pixel centres of one tile row, x in [15.6, 15.9], never reaches
+    tile (1, 0)'s box (x >= 16.5) although its rectangle holds it."""
+    cam = axis_camera(64, 64, fx=64.0)
+    t, i, g, amb = oracle.tile_lists_ellipse(_circle_splat(20.0, 20.0, 5.0), cam, 16)
+    assert t.tolist() == [1, 4, 5] and not amb.any()
+    t, i, g, amb = oracle.tile_lists_ellipse(_circle_splat(20.0, 20.0, 6.4), cam, 16)
+    assert t.tolist() == [0, 1, 4, 5] and not amb.any()
+    d = math.hypot(4.5, 4.5)
+    t, i, g, amb = oracle.tile_lists_ellipse(_circle_splat(20.0, 20.0, d + 1e-7), cam, 16)
+    assert t.tolist() == [0, 1, 4, 5] and not amb.any()
+    t, i, g, amb = oracle.tile_lists_ellipse(_circle_splat(20.0, 20.0, d - 1e-7), cam, 16)
+    assert t.tolist() == [0, 1, 4, 5] and amb.tolist() == [True, False, False, False]
+    t, i, g, amb = oracle.tile_lists_ellipse(_circle_splat(20.0, 20.0, 0.99 * d), cam, 16)
+    assert t.tolist() == [1, 4, 5] and not amb.any()
+    t, i, g, amb = oracle.tile_lists_ellipse(_circle_splat(15.4, 8.0, 0.15, tile=((0, 0), (1, 0))), cam, 16)
+    assert t.tolist() == [0] and not amb.any()
+    # a one-tile rectangle is listed as it is
+    t, i, g, amb = oracle.tile_lists_ellipse(_circle_splat(15.75, 8.0, 0.15, tile=((1, 0), (1, 0))), cam, 16)
+    assert t.tolist() == [1]
+
+
+def test_ellipse_tile_lists_between_support_and_rect_lists(cfg1):
+    """On the workload-1 frame: support lists (tiles with a pixel centre the splat blends at)
+    <= ellipse lists (tiles whose pixel-centre box the support ellipse meets) <= rect lists, in
+    blend order; the band is a small fraction; each ellipse pair is confirmed by brute force (a
+    point of the tile's pixel-centre box on a 65 x 65 grid inside the support, or the box's nearest
+    grid point within the grid's resolution)."""
+    scene, cam = cfg1
+    osc = oracle.OracleScene(scene)
+    sp = oracle.project(osc, cam, oracle.opts(tile_size=16))
+    v = sp[sp["valid"] != 0][:400]
+    et, ei, eg, ea = oracle.tile_lists_ellipse(v, cam, 16)
+    st, si, sg = oracle.tile_lists(v, cam, 16, mode="support")
+    rt, ri, rg = oracle.tile_lists(v, cam, 16, mode="rect")
+    ell = set(zip(et[~ea].tolist(), eg[~ea].tolist()))
+    assert set(zip(st.tolist(), sg.tolist())) <= ell
+    assert set(zip(et.tolist(), eg.tolist())) <= set(zip(rt.tolist(), rg.tolist()))
+    assert len(ell) < len(rt) and ea.mean() < 1e-2
+    by_g = {int(s["gaussian"]): s for s in v}
+    tw = cam.width // 16
+    for t, gg, am in zip(et.tolist(), eg.tolist(), ea.tolist()):
+        s = by_g[gg]
+        if am or (s["tile_min"] == s["tile_max"]).all():
+            continue
+        tx, ty = t % tw, t // tw
+        xs, ys = np.meshgrid(np.linspace(tx * 16 + 0.5, tx * 16 + 15.5, 65) - s["u"],
+                             np.linspace(ty * 16 + 0.5, ty * 16 + 15.5, 65) - s["v"])
+        a, b, c = s["conic"]
+        q = a * xs * xs + 2 * b * xs * ys + c * ys * ys
+        kk = 2.0 * math.log(s["opacity"] * 255.0)
+        slack = 2 * math.sqrt(max(a, c) * kk) * (15.0 / 64) + 2 * max(a, c) * (15.0 / 64) ** 2
+        assert q.min() <= kk + slack, (t, gg)
+    # blend order inside each tile
+    depth = dict(zip(v["gaussian"].tolist(), v["depth"].tolist()))
+    d = np.array([depth[x] for x in eg.tolist()])
+    same = et[1:] == et[:-1]
+    assert np.all(d[1:][same] >= d[:-1][same])
+
+
 @pytest.mark.parametrize("side", [-1, 1])
 def test_radius_clipping_threshold_is_the_one_sigma_area(side):
     """Sec. 4.4 radius clipping, pinned on one isotropic Gaussian on the optical axis: there
