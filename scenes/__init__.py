@@ -17,8 +17,11 @@ from .synth import (  # noqa: F401
     box_asset,
     random_asset,
     mlp_weights,
+    planar_mlp_weights,
     config1_scene,
     config1_camera,
+    layered_scene,
+    layered_camera,
     config2_scene,
     config2_camera,
     config2_orbit,

@@ -205,7 +205,53 @@ def mlp_weights(seed: int = 42) -> dict:
     return w
 
 
+def planar_mlp_weights(seed: int = 7, gain: float = 10.0, noise: float = 0.05,
+                       offset: float = 0.0, direction=None) -> dict:
+    """Visibility-MLP weights whose logit is close to gain * (u . x) + offset, x the 32 inputs and
+    u = ``direction`` (default: a seeded unit vector over the first three inputs, the normalised
+    local position): hidden units 0 and 1 carry ReLU(u . x) and ReLU(-u . x) through the three
+    layers, the output takes their difference times gain, and every other weight is N(0, 1/fan_in)
+    scaled by ``noise``.  Like a trained network, the decisions are coherent in space (or in
+    distance) and few logits sit near the threshold."""
+    rng = np.random.default_rng(seed)
+    w = {}
+    for li, (fi, fo) in enumerate(MLP_LAYERS, start=1):
+        w[f"W{li}"] = (noise * rng.normal(0.0, 1.0 / math.sqrt(fi), (fo, fi))).astype(np.float32)
+        w[f"b{li}"] = np.zeros(fo, np.float32)
+    if direction is None:
+        n = rng.normal(size=3)
+        u = np.zeros(32)
+        u[0:3] = n / np.linalg.norm(n)
+    else:
+        u = np.asarray(direction, np.float64).reshape(32)
+    w["W1"][0:2, :] = 0.0
+    w["W1"][0, :] = u
+    w["W1"][1, :] = -u
+    for li in (2, 3):
+        w[f"W{li}"][0:2, :] = 0.0
+        w[f"W{li}"][0, 0] = 1.0
+        w[f"W{li}"][1, 1] = 1.0
+    w["W4"][0, 0] = gain
+    w["W4"][0, 1] = -gain
+    w["b4"][0] = offset
+    return w
+
+
 # ----------------------------------------------------------------------------- configs
+def layered_scene(n: int = 20000, spacing: float = 4.0, layers: int = 3) -> Scene:
+    """The workload-1 torus as ``layers`` identity-rotation instances spaced ``spacing`` apart
+    along -z and shifted sideways, so that each sits in its own range of camera distances (for
+    decisions that depend on the distance input); seen by ``layered_camera``."""
+    insts = [Instance(0, np.eye(3, dtype=np.float32),
+                      np.array([0.9 * ((k % 2) * 2 - 1) * (k > 0), 0.0, -spacing * k], np.float32), 1.0)
+             for k in range(layers)]
+    return Scene([torus_asset(n, seed=0, sh_degree=0)], insts)
+
+
+def layered_camera(width: int = 320, height: int = 240) -> Camera:
+    return look_at_camera((0.0, 1.5, 3.0), (0.0, 0.0, -4.0), width, height, 60.0)
+
+
 def _identity_instance(asset_id=0) -> Instance:
     return Instance(asset_id, np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 1.0)
 

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import scenes
-from gpu_common import renderer_for
+from gpu_common import compare_images, gpu_image, layered_case, oracle_opts_for, renderer_for
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -91,8 +91,11 @@ def test_fp8_logits_match_the_quantised_reference_and_the_oracle():
     e_o = np.abs(lg[inside] - vis["logits"][inside])
     big = np.abs(vis["logits"][inside]) > 0.1 * scale
     agree = float(((lg[inside] > 0) == (vis["logits"][inside] > 0))[big].mean())
+    big05 = np.abs(vis["logits"][inside]) > 0.05
+    agree05 = float(((lg[inside] > 0) == (vis["logits"][inside] > 0))[big05].mean())
     print(f"fp8: vs quantised reference p99 {np.percentile(e_q, 99):.3e} max {e_q.max():.3e}; "
-          f"vs FP64 p99 {np.percentile(e_o, 99):.3e} (scale {scale:.3f}); agree {agree:.4f}")
+          f"vs FP64 p99 {np.percentile(e_o, 99):.3e} (scale {scale:.3f}); agree {agree:.4f} "
+          f"beyond 10 % of the scale, {agree05:.4f} beyond |logit| 0.05 (random weights)")
     # (1) the documented quantised arithmetic, up to accumulation order and rare boundary flips
     assert np.percentile(e_q, 99) <= 2e-3 * scale
     assert (e_q > 2e-2 * scale).mean() <= 0.01
@@ -125,3 +128,33 @@ def test_fp8_culling_in_a_multi_asset_render():
         assert torch.equal(img, img2)
     finally:
         r.close()
+
+
+def test_fp8_culled_render_matches_oracle_on_bimodal_logits():
+    """Trained-like, bimodal logits (the layered torus case, a distance cut): FP8 decisions agree
+    with the FP64 oracle on every Gaussian with |logit| > 0.05, and the FP8-culled image matches
+    the oracle render with the oracle's decisions (the quantised reference's decisions agree)."""
+    sc, cam, dist, osc, inside, w = layered_case()
+    r = renderer_for(sc, w, precision=FP8, **dist)
+    try:
+        lg, kp, _ = r.query_visibility(cam, r.flags(use_mlp=1, mlp_gate=0))
+        lg = lg.cpu().numpy().astype(np.float64)
+        kp = kp.cpu().numpy().astype(bool)
+        img, st = gpu_image(r, cam, use_mlp=1, mlp_gate=0)
+    finally:
+        r.close()
+    vis = oracle.visibility(osc, cam, w, gate=False, return_features=True)
+    ora = vis["logits"]
+    big = inside & (np.abs(ora) > 0.05)
+    agree = float(((lg > 0) == (ora > 0))[big].mean())
+    q = f8_reference(w, vis["features"][inside])
+    print(f"fp8 bimodal: agreement {agree:.5f} on {big.sum()} Gaussians with |logit| > 0.05; "
+          f"quantised-reference decisions equal: {((q > 0) == (ora[inside] > 0)).mean():.5f}")
+    assert agree >= 0.999
+    keep = inside & (ora > 0)
+    np.testing.assert_array_equal(kp, inside & (lg > 0))
+    np.testing.assert_array_equal(kp[big], keep[big])
+    amb = inside & ~big
+    ref = oracle.render(osc, cam, oracle_opts_for({}), keep=keep.astype(np.uint8), keep_amb=amb.astype(np.uint8))
+    compare_images(img, ref["image"], ref["ambiguous"], max_amb_frac=0.02)
+    assert 0 < st["n_survivors"] < st["n_in_frustum"]
