@@ -113,8 +113,8 @@ typedef struct {
     int32_t blend_split_len;     /* tiles with more pairs are composited in chunks of this many
                                     pairs on separate CTAs (0: automatic, max(4096, 4 x the
                                     mean pairs per tile); < 0: never; else >= 256) */
-    int32_t mlp_ctas_per_sm;     /* resident CTAs per SM of the tensor-core MLP (0: default 3;
-                                    1..3) -- a tuning knob, results do not depend on it */
+    int32_t mlp_ctas_per_sm;     /* resident CTAs per SM of the BF16 tensor-core MLP (0: default
+                                    4; 1..4) -- a tuning knob, results do not depend on it */
     float radius_clip_area;      /* radius clipping (Sec. 4.4), lossy: a splat whose 1-sigma
                                     ellipse is smaller than this many px^2, i.e. whose
                                     pi sqrt(det Sigma_2D) (dilation included) is below it, is not
@@ -330,7 +330,7 @@ nvgs_status nvgs_render_batch(nvgs_ctx* ctx, const nvgs_camera* cams, int n_view
                               const nvgs_batch_opts* opts, nvgs_frame_stats* stats);
 
 /* Autotuner: times nvgs_render_batch of the given views under every candidate configuration --
- * tile size {8, 16, 32} x tensor-core MLP CTAs per SM {1, 2, 3} (when flags.use_mlp and every
+ * tile size {8, 16, 32} x tensor-core MLP CTAs per SM {1, 2, 3, 4} (when flags.use_mlp and every
  * MLP is BF16) x dense-tile split {automatic, never} -- and returns the fastest flags (all other
  * fields copied from `flags`).  Images do not depend on these choices.  Each candidate runs one
  * untimed batch and three timed ones (CUDA events on the context's stream); the call waits.

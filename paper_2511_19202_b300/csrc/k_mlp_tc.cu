@@ -2,33 +2,36 @@
 // NVGS Sec. 3.2, queried per in-frustum Gaussian as in Sec. 3.3) on the 5th-generation tensor
 // cores (tcgen05), BF16 operands with FP32 accumulation in tensor memory (TMEM).
 //
-// One CTA = one warpgroup (128 threads) walking 256-Gaussian steps of the in-frustum list, as
-// two 128-row tiles that share every MMA round trip (thread r owns rows r and 128 + r):
-//   1. thread r builds the 32 inputs of row r (Eq. 2 distance, frequency encoding) and writes
-//      them as BF16 into the A tile in shared memory;
-//   2. lane 0 of warp h issues tcgen05.mma (M = 128, K = 16 per instruction) for tile h's layer
-//      with the accumulator in TMEM and commits to the layer's mbarrier (two arrivals);
-//   3. after the mbarrier completes, each warp reads its 32 TMEM lanes (tcgen05.ld 32x32b),
-//      applies ReLU while converting to BF16 and writes the activations back to shared memory as
-//      the next layer's A operand.
-// All four layers run on the tensor cores, the output layer as an N = 16 MMA whose first two
-// columns hold w4 split into BF16 high and low parts (the logit is their sum).  Biases cost no
-// CUDA-core work: every layer ends with one more K = 16 MMA step of a constant A tile whose
-// first two columns are 1 against a B tile holding the bias split into BF16 high and low parts,
-// so the accumulator already contains W h + b (to about 2^-16 of b).  The epilogue of a hidden
-// layer is thus tcgen05.ld -> cvt.rn.relu.bf16x2 -> st.shared.
-// Three CTAs share an SM (128 TMEM columns and 65 KB of shared memory each), so the epilogues of
-// some overlap the MMAs of others.  Within a CTA, each thread builds the inputs of its rows of the
-// next step while the first layer's MMAs of the current step run (kept in registers as BF16
-// pairs; a row of another asset is built in its own pass as usual).
+// One CTA = one warpgroup (128 threads) walking a contiguous range of 128-Gaussian steps of the
+// in-frustum list (instance-major, so the asset -- and the weights in shared memory -- rarely
+// changes within a range); thread r owns row r (TMEM lane r).  Four CTAs share an SM, each with 128 TMEM columns:
+//   [0, 64)    D   FP32 accumulator of the current layer (N = 64)
+//   [64, 96)   H   the layer's ReLU'd activations as BF16 pairs: the next layer's A operand
+//   [96, 128)  IN  two 16-column buffers of BF16 inputs (this step's and the next step's)
+// Every activation operand lives in tensor memory (tcgen05.mma with A from TMEM), so an MMA reads
+// only its weight tile from shared memory, and a hidden epilogue is tcgen05.ld -> cvt.rn.relu.bf16x2
+// -> tcgen05.st, with no shared-memory store or proxy fence.  Per step:
+//   1. lane 0 of warp 0 issues the first layer (A = IN[b], K = 32) and commits to the mbarrier;
+//      meanwhile every thread builds its row of the NEXT step's inputs (Eq. 2 distance, frequency
+//      encoding) into IN[b ^ 1];
+//   2. per hidden layer: wait for the commit, epilogue into H, barrier, issue the next layer;
+//   3. the third layer's epilogue also evaluates the 64 -> 1 output layer on the CUDA cores
+//      (FP32 w4 and b4 on the BF16-rounded ReLU activations), so a step costs three MMA round
+//      trips: each round trip (issue, commit, mbarrier) has a fixed latency of several hundred
+//      cycles, which bounds the kernel more than the tensor work of its 64-wide layers.
+// The hidden biases cost no CUDA-core work: every layer ends with one more K = 16 MMA step of a constant A
+// tile (shared memory) whose first two columns are 1 against a B tile holding the bias split into
+// BF16 high and low parts, so the accumulator already contains W h + b (to about 2^-16 of b).
+// Rows of several assets in one step (at instance boundaries) run one pass per asset over the same
+// inputs, each with that asset's weights.
 //
-// Operand layout (both operands K-major, no swizzle): 8 x 16-byte "core matrices"; element
-// (row, k) of a tile with K columns sits at (row / 8) * SBO + (k / 8) * 128 + (row % 8) * 16
-// + (k % 8) * 2 with SBO = 16 * K bytes.  The weights are packed on the host into exactly this
-// byte layout (mlp_tc_pack_weights) and copied to shared memory with 16-byte loads.
+// Weight layout (B operands, K-major, no swizzle): 8 x 16-byte core matrices; element (n, k) of a
+// tile with K columns sits at (n / 8) * SBO + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2 with
+// SBO = 16 * K bytes.  The host packs the weights into exactly this byte layout
+// (mlp_tc_pack_weights); they are copied to shared memory with 16-byte loads.
 //
-// Every mbarrier wait is bounded; on a timeout the CTA sets the error flag, frees its TMEM and
-// returns.
+// Every mbarrier wait is bounded; on a timeout the CTA sets the error flag, waits (bounded) for its
+// MMAs in flight, frees its TMEM and returns.
 #include <climits>
 #include <cstring>
 
@@ -42,28 +45,25 @@ namespace {
 using namespace tc;
 
 constexpr int kThreads = 128;
-constexpr int kCtasPerSm = 3;
-constexpr int kHalves = 2;                 // each CTA carries two 128-row tiles through a layer
-constexpr int kRows = 128 * kHalves;       // rows per CTA step
-constexpr int kTmemCols = 64 * kHalves;
+constexpr int kCtasPerSm = 4;
+constexpr int kRows = 128;                 // rows per CTA step (one per thread)
+constexpr int kTmemCols = 128;
+constexpr uint32_t kColD = 0;
+constexpr uint32_t kColH = 64;
+constexpr uint32_t kColIn = 96;            // + 16 * buffer
 // shared-memory map (bytes); the weight blob [0, kBlobBytes) is packed on the host
 constexpr int kOffW1 = 0;            // 64 x 32 BF16
 constexpr int kOffW2 = 4096;         // 64 x 64 BF16
 constexpr int kOffW3 = 12288;        // 64 x 64 BF16
-constexpr int kOffW4 = 20480;        // 16 x 64 BF16: row 0 = w4 high part, row 1 = low part
-constexpr int kOffB1 = 22528;        // bias tiles, N x 16 BF16: column 0 = high, 1 = low part
-constexpr int kOffB2 = 24576;
-constexpr int kOffB3 = 26624;
-constexpr int kOffB4 = 28672;        // 16 x 16: row 0 = b4
-constexpr int kBlobBytes = 29184;
-constexpr int kOffOnes = kBlobBytes; // 128 x 16 BF16, columns 0 and 1 = 1 (written in the kernel)
-// Per half, the input tile A (128 x 32) overlays the first half of the hidden tile H (128 x 64):
-// layer 1's MMA has finished reading A before its epilogue writes H, and the next step's inputs
-// are written only after the output layer's MMA has finished reading H.
-constexpr int kOffH = kOffOnes + 4096;
-constexpr int kHBytes = 16384;
-constexpr int kOffMisc = kOffH + kHalves * kHBytes;
-constexpr int kSmemBytes = kOffMisc + 64;
+constexpr int kOffB1 = 20480;        // bias tiles, N x 16 BF16: column 0 = high, 1 = low part
+constexpr int kOffB2 = 22528;
+constexpr int kOffB3 = 24576;
+constexpr int kOffW4 = 26624;        // FP32 w4[64], then b4
+constexpr int kBlobBytes = 26896;
+constexpr int kOffOnes = (kBlobBytes + 1023) / 1024 * 1024;   // 128 x 16 BF16, columns 0 and 1 = 1
+                                                              // (written in the kernel)
+constexpr int kOffMisc = kOffOnes + 4096;
+constexpr int kSmemBytes = kOffMisc + 128;
 constexpr uint32_t kSboK16 = 256;    // 16 * 16
 constexpr uint32_t kSboK32 = 512;    // 16 * 32
 constexpr uint32_t kSboK64 = 1024;   // 16 * 64
@@ -73,9 +73,8 @@ constexpr uint32_t kLbo = 128;
 // N / 8 at bit 17, M / 16 at bit 24.
 constexpr uint32_t idesc(uint32_t n) { return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24); }
 constexpr uint32_t kIdescN64 = idesc(64);
-constexpr uint32_t kIdescN16 = idesc(16);
 
-// (lo, hi) -> BF16x2 with ReLU, lo in the low half (the lower address).
+// (lo, hi) -> BF16x2 with ReLU, lo in the low half (the lower k).
 __device__ __forceinline__ uint32_t bf16x2_relu(float lo, float hi) {
     uint32_t d;
     asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
@@ -91,32 +90,71 @@ __device__ __forceinline__ void st_chunk(uint8_t* tile, uint32_t sbo, int row, i
     *reinterpret_cast<uint4*>(tile + (row >> 3) * sbo + chunk * kLbo + (row & 7) * 16) = v;
 }
 
-// TMEM accumulator (this lane, 64 columns, bias included) -> ReLU -> BF16 row of the next A
-// operand.
-__device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, uint8_t* sH, int row) {
+// TMEM accumulator (this lane, 64 columns, bias included) -> ReLU -> BF16 pairs in H.
+__device__ __forceinline__ void epilogue_hidden(uint32_t t_lane) {
+    uint32_t r[64];
+    tmem_ld32_async(t_lane + kColD, r);
+    tmem_ld32_async(t_lane + kColD + 32, r + 32);
+    tmem_wait_ld64(r);
+    uint32_t p[32];
 #pragma unroll
-    for (int half = 0; half < 2; half++) {
-        uint32_t r[32];
-        tmem_ld32(t_lane + half * 32, r);
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            uint32_t p[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++)
-                p[q] = bf16x2_relu(__uint_as_float(r[c * 8 + 2 * q]), __uint_as_float(r[c * 8 + 2 * q + 1]));
-            st_chunk(sH, kSboK64, row, half * 4 + c, make_uint4(p[0], p[1], p[2], p[3]));
-        }
-    }
+    for (int q = 0; q < 32; q++) p[q] = bf16x2_relu(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+    tmem_st32(t_lane + kColH, p);
 }
 
-// Issue one layer for one 128-row tile: K / 16 steps of A x B plus the bias step.  Descriptors
-// are precomputed; consecutive K = 16 slices of a K-major tile are 256 bytes (16 in the
-// descriptor's address field) apart.
-__device__ __forceinline__ void issue_layer(uint32_t d, uint64_t da, int k_steps, uint64_t dw,
-                                            uint64_t dbias, uint64_t dones, uint32_t idesc_) {
+// Output layer on the CUDA cores: acc (64 FP32 columns, b3 included) -> ReLU and BF16 rounding
+// (the hidden activations' precision) -> dot with the FP32 w4 -> + b4.
+__device__ __forceinline__ float epilogue_output(uint32_t t_lane, const float* __restrict__ w4) {
+    uint32_t r[64];
+    tmem_ld32_async(t_lane + kColD, r);
+    tmem_ld32_async(t_lane + kColD + 32, r + 32);
+    tmem_wait_ld64(r);
+    float acc[4] = {w4[64], 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int q = 0; q < 32; q += 2) {
+        const float4 w = *reinterpret_cast<const float4*>(w4 + 2 * q);
+        const uint32_t p0 = bf16x2_relu(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+        const uint32_t p1 = bf16x2_relu(__uint_as_float(r[2 * q + 2]), __uint_as_float(r[2 * q + 3]));
+        acc[0] = fmaf(__uint_as_float(p0 << 16), w.x, acc[0]);
+        acc[1] = fmaf(__uint_as_float(p0 & 0xffff0000u), w.y, acc[1]);
+        acc[2] = fmaf(__uint_as_float(p1 << 16), w.z, acc[2]);
+        acc[3] = fmaf(__uint_as_float(p1 & 0xffff0000u), w.w, acc[3]);
+    }
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
+// This thread's row of inputs (32 features as 16 BF16 pairs) into its lane of an input buffer;
+// rows past the list get zeros (their outputs are never used).  Returns the row's instance gate
+// (Sec. 3.3: an instance nearer than d_min bypasses the MLP).
+__device__ __forceinline__ bool build_inputs(uint32_t t_in, bool valid, uint2 e, float4 m,
+                                             const FrameInst* __restrict__ fis,
+                                             const AssetDev* __restrict__ assets) {
+    uint32_t p[16];
+    bool gated = false;
+    if (valid) {
+        const FrameInst& fr = fis[e.x];
+        gated = fr.gated != 0;
+        const MlpAsset ma = mlp_asset(assets[__float_as_int(m.w)]);
+        float f[32];
+        mlp_features(ma, fr.cam_local[0], fr.cam_local[1], fr.cam_local[2], fr.dist_scale, m, f);
+#pragma unroll
+        for (int k = 0; k < 16; k++) p[k] = bf16x2(f[2 * k], f[2 * k + 1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; k++) p[k] = 0u;
+    }
+    tmem_st16(t_in, p);
+    return gated;
+}
+
+// One layer for the CTA's 128 rows (issued by one thread): K / 16 steps of A (TMEM) x W, then the
+// bias step (A = the ones tile in shared memory), committed to the mbarrier.
+__device__ __forceinline__ void issue_layer(uint32_t d, uint32_t a_tmem, int k_steps, uint64_t dw,
+                                            uint64_t dbias, uint64_t dones, uint32_t idesc_, uint64_t* mbar) {
 #pragma unroll 4
-    for (int k = 0; k < k_steps; k++) mma_f16(d, da + 16u * k, dw + 16u * k, idesc_, k > 0);
+    for (int k = 0; k < k_steps; k++) mma_f16_ts(d, a_tmem + 8u * k, dw + 16u * k, idesc_, k > 0);
     mma_f16(d, dones, dbias, idesc_, 1);
+    mma_commit(mbar);
 }
 
 }  // namespace
@@ -130,6 +168,8 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
     if (n_dev) n = min(n, *n_dev);   // device-side count (n is then the capacity)
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kOffMisc);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + kOffMisc + 8);
+    // reduction slots: per step parity [0,4) min and [4,8) max (so that a warp that runs ahead into
+    // the next step never overwrites a slot another warp has still to read), then [16,20) pass min
     int* s_red = reinterpret_cast<int*>(sm + kOffMisc + 16);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -139,7 +179,7 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(mbar, kHalves);   // one commit per half per layer
+        mbar_init(mbar, 1);   // one commit per layer
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // constant A tile of the bias steps: row r = (1, 1, 0, ..., 0); core-matrix chunk 0 of row r
@@ -155,199 +195,145 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
     const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
-    const int issue_h = warp & 1;   // lane 0 of warp h issues tile h's MMAs
 
     uint32_t phase = 0;
-    int loaded = -1;
+    int loaded = -1;              // asset whose weights are in shared memory
+    int known = -1;               // asset whose MLP presence is in has_mlp
+    bool has_mlp = false;
     bool abort = false;
-    uint32_t pnext[kHalves][16];               // inputs of this thread's next-step rows, as BF16x2
-    int pnext_asset[kHalves] = {-1, -1};       // the asset they were built for (-1: none)
+    uint32_t buf = 0;
     const uint32_t n_steps = (n + kRows - 1) / kRows;
-    // row inputs of the next step are loaded one step ahead, so their latency overlaps the
-    // current step's tensor-core chain
-    uint2 e_next[kHalves];
-    float4 m_next[kHalves];
-#pragma unroll
-    for (int h = 0; h < kHalves; h++) {
-        const uint32_t i = blockIdx.x * kRows + h * 128 + tid;
-        e_next[h] = make_uint2(0, 0);
-        m_next[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (blockIdx.x < n_steps && i < n) {
-            e_next[h] = __ldg(&list[i]);
-            m_next[h] = __ldg(&list_mean[i]);
-        }
+    // this CTA's contiguous range of steps [s_begin, s_end)
+    const uint32_t per_cta = (n_steps + gridDim.x - 1) / gridDim.x;
+    const uint32_t s_begin = min(n_steps, blockIdx.x * per_cta);
+    const uint32_t s_end = min(n_steps, s_begin + per_cta);
+    // this step's row; the first step's inputs are built here, every later step's during the
+    // previous step's first-layer round trip
+    uint2 e = make_uint2(0, 0);
+    float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool gated = false;
+    if (s_begin < s_end) {
+        const uint32_t i0 = s_begin * kRows + tid;
+        if (i0 < n) { e = __ldg(&list[i0]); m = __ldg(&list_mean[i0]); }
+        gated = build_inputs(t_lane + kColIn, i0 < n, e, m, fis, assets);
     }
-    for (uint32_t step = blockIdx.x; step < n_steps && !abort; step += gridDim.x) {
-        uint2 e[kHalves];
-        float4 m[kHalves], ci[kHalves];
-        int my_asset[kHalves];
-        bool pending[kHalves], keep[kHalves], gated[kHalves];
-        float logit[kHalves];
-#pragma unroll
-        for (int h = 0; h < kHalves; h++) {
-            const uint32_t i = step * kRows + h * 128 + tid;
-            e[h] = e_next[h];
-            m[h] = m_next[h];
-            const uint32_t i_next = (step + gridDim.x) * kRows + h * 128 + tid;
-            if (step + gridDim.x < n_steps && i_next < n) {
-                e_next[h] = __ldg(&list[i_next]);
-                m_next[h] = __ldg(&list_mean[i_next]);
-            }
-            // the list's mean carries the row's asset id in w; the instance values the inputs
-            // need are loaded here, well ahead of their use after the asset pass
-            my_asset[h] = i < n ? __float_as_int(m[h].w) : INT_MAX;
-            ci[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-            gated[h] = false;
-            if (i < n) {
-                const FrameInst& fr = fis[e[h].x];
-                ci[h] = make_float4(fr.cam_local[0], fr.cam_local[1], fr.cam_local[2], fr.dist_scale);
-                gated[h] = fr.gated != 0;
-            }
-            pending[h] = i < n;
-            keep[h] = false;
-            logit[h] = 0.0f;
-        }
-        bool pre_done = false;
-        // rows of different assets (at instance boundaries) are evaluated in separate passes,
-        // each with that asset's weights
-        for (;;) {
-            int cand = INT_MAX;
-#pragma unroll
-            for (int h = 0; h < kHalves; h++) cand = min(cand, pending[h] ? my_asset[h] : INT_MAX);
-            cand = __reduce_min_sync(0xffffffffu, cand);
-            if (lane == 0) s_red[warp] = cand;
-            __syncthreads();
-            const int cur = min(min(s_red[0], s_red[1]), min(s_red[2], s_red[3]));
-            __syncthreads();
-            if (cur == INT_MAX) break;
-            const AssetDev& a = assets[cur];
-            bool mine[kHalves];
-#pragma unroll
-            for (int h = 0; h < kHalves; h++) mine[h] = pending[h] && my_asset[h] == cur;
-            if (a.w_tc == nullptr) {   // asset without an MLP: rendered unculled
-#pragma unroll
-                for (int h = 0; h < kHalves; h++)
-                    if (mine[h]) { keep[h] = true; logit[h] = __int_as_float(0x7f800000); pending[h] = false; }
-                continue;
-            }
-            if (cur != loaded) {
-                const uint4* src = reinterpret_cast<const uint4*>(a.w_tc);
-                uint4* dst = reinterpret_cast<uint4*>(sm);
-                for (int k = tid; k < kBlobBytes / 16; k += kThreads) dst[k] = __ldg(&src[k]);
-                loaded = cur;
-            }
-            // ---- inputs -> A (BF16), one row per half
-#pragma unroll
-            for (int h = 0; h < kHalves; h++) {
-                uint32_t p[16];
-                if (mine[h] && pnext_asset[h] == cur) {
-#pragma unroll
-                    for (int k = 0; k < 16; k++) p[k] = pnext[h][k];
-                } else if (mine[h]) {
-                    float f[32];
-                    mlp_features(mlp_asset(a), ci[h].x, ci[h].y, ci[h].z, ci[h].w, m[h], f);
-#pragma unroll
-                    for (int k = 0; k < 16; k++) p[k] = bf16x2(f[2 * k], f[2 * k + 1]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 16; k++) p[k] = 0u;
-                }
-                uint8_t* sA = sm + kOffH + h * kHBytes;
-#pragma unroll
-                for (int c = 0; c < 4; c++)
-                    st_chunk(sA, kSboK32, tid, c, make_uint4(p[4 * c], p[4 * c + 1], p[4 * c + 2], p[4 * c + 3]));
-            }
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
+    const uint64_t dOnes = sdesc(sm + kOffOnes, kLbo, kSboK16);
+    const uint64_t dW1 = sdesc(sm + kOffW1, kLbo, kSboK32), dB1 = sdesc(sm + kOffB1, kLbo, kSboK16);
+    const uint64_t dW2 = sdesc(sm + kOffW2, kLbo, kSboK64), dB2 = sdesc(sm + kOffB2, kLbo, kSboK16);
+    const uint64_t dW3 = sdesc(sm + kOffW3, kLbo, kSboK64), dB3 = sdesc(sm + kOffB3, kLbo, kSboK16);
 
-            // ---- four tensor-core layers, both halves per round trip
-            bool ok = true;
-#pragma unroll 1
-            for (int layer = 0; layer < 4 && ok; layer++) {
-                // the two halves are issued by lane 0 of warps 0 and 1 concurrently (a single
-                // thread issues an MMA only every ~50 cycles), each committing its own MMAs
-                if (lane == 0 && warp < kHalves) {
-                    tc_fence_after();
-                    const uint32_t d = tmem + 64 * issue_h;
-                    const uint8_t* sH = sm + kOffH + issue_h * kHBytes;
-                    const uint64_t dOnes = sdesc(sm + kOffOnes, kLbo, kSboK16);
-                    if (layer == 0)
-                        issue_layer(d, sdesc(sH, kLbo, kSboK32), 2, sdesc(sm + kOffW1, kLbo, kSboK32),
-                                    sdesc(sm + kOffB1, kLbo, kSboK16), dOnes, kIdescN64);
-                    else if (layer == 1)
-                        issue_layer(d, sdesc(sH, kLbo, kSboK64), 4, sdesc(sm + kOffW2, kLbo, kSboK64),
-                                    sdesc(sm + kOffB2, kLbo, kSboK16), dOnes, kIdescN64);
-                    else if (layer == 2)
-                        issue_layer(d, sdesc(sH, kLbo, kSboK64), 4, sdesc(sm + kOffW3, kLbo, kSboK64),
-                                    sdesc(sm + kOffB3, kLbo, kSboK16), dOnes, kIdescN64);
-                    else
-                        issue_layer(d, sdesc(sH, kLbo, kSboK64), 4, sdesc(sm + kOffW4, kLbo, kSboK64),
-                                    sdesc(sm + kOffB4, kLbo, kSboK16), dOnes, kIdescN16);
-                    mma_commit(mbar);
-                }
-                // the inputs of this thread's rows of the CTA's next step are built during the first
-                // layer's round trip (when they belong to the asset of this pass), once every row of
-                // this thread in the current step has had its inputs written (this pass or earlier)
-                if (layer == 0 && !pre_done && (mine[0] || !pending[0]) && (mine[1] || !pending[1])) {
-                    pre_done = true;
-                    const MlpAsset ma = mlp_asset(a);
+    for (uint32_t step = s_begin; step < s_end && !abort; step++) {
+        const uint32_t i = step * kRows + tid;
+        const bool valid = i < n;
+        const uint32_t nstep = step + 1;
+        const uint32_t i_next = nstep * kRows + tid;
+        const bool has_next = nstep < s_end;
+        const bool next_valid = has_next && i_next < n;
+        uint2 e_n = make_uint2(0, 0);
+        float4 m_n = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (next_valid) { e_n = __ldg(&list[i_next]); m_n = __ldg(&list_mean[i_next]); }
+        // the list's mean carries the row's asset id in w
+        const int my_asset = valid ? __float_as_int(m.w) : INT_MAX;
+        bool gated_next = false;
+        // the CTA's smallest and largest asset of this step; the barrier also orders this step's
+        // input stores and the previous step's accumulator reads before the first MMA
+        {
+            const int amin = __reduce_min_sync(0xffffffffu, my_asset);
+            const int amax = __reduce_max_sync(0xffffffffu, valid ? my_asset : INT_MIN);
+            if (lane == 0) { s_red[8 * buf + warp] = amin; s_red[8 * buf + 4 + warp] = amax; }
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        const int* sr = s_red + 8 * buf;
+        const int step_min = min(min(sr[0], sr[1]), min(sr[2], sr[3]));
+        const int step_max = max(max(sr[4], sr[5]), max(sr[6], sr[7]));
+        bool pending = valid, keep = false, built_next = false;
+        float logit = 0.0f;
+        const uint32_t a_in = tmem + kColIn + 16u * buf;
+        int cur = step_min;
+        while (cur != INT_MAX) {
+            const bool mine = pending && my_asset == cur;
+            if (cur != known) { has_mlp = assets[cur].w_tc != nullptr; known = cur; }
+            if (!has_mlp) {   // asset without an MLP: rendered unculled
+                if (mine) { keep = true; logit = __int_as_float(0x7f800000); }
+            } else {
+                if (cur != loaded) {   // every MMA of earlier passes has completed (waited on)
+                    const uint4* src = reinterpret_cast<const uint4*>(assets[cur].w_tc);
+                    uint4* dst = reinterpret_cast<uint4*>(sm);
+                    // four loads in flight per thread before their stores
+                    for (int k0 = tid; k0 < kBlobBytes / 16; k0 += 4 * kThreads) {
+                        uint4 v[4];
 #pragma unroll
-                    for (int h = 0; h < kHalves; h++) {
-                        const uint32_t i_next = (step + gridDim.x) * kRows + h * 128 + tid;
-                        pnext_asset[h] = -1;
-                        if (step + gridDim.x < n_steps && i_next < n && __float_as_int(m_next[h].w) == cur) {
-                            const FrameInst& fr = fis[e_next[h].x];
-                            float f[32];
-                            mlp_features(ma, fr.cam_local[0], fr.cam_local[1], fr.cam_local[2], fr.dist_scale,
-                                         m_next[h], f);
+                        for (int j = 0; j < 4; j++)
+                            if (k0 + j * kThreads < kBlobBytes / 16) v[j] = __ldg(&src[k0 + j * kThreads]);
 #pragma unroll
-                            for (int k = 0; k < 16; k++) pnext[h][k] = bf16x2(f[2 * k], f[2 * k + 1]);
-                            pnext_asset[h] = cur;
-                        }
+                        for (int j = 0; j < 4; j++)
+                            if (k0 + j * kThreads < kBlobBytes / 16) dst[k0 + j * kThreads] = v[j];
                     }
-                }
-                const bool done = mbar_wait(mbar, phase);
-                if (__syncthreads_or(!done)) { ok = false; break; }
-                phase ^= 1u;
-                tc_fence_after();
-                if (layer < 3) {
-#pragma unroll
-                    for (int h = 0; h < kHalves; h++)
-                        epilogue_hidden(t_lane + 64 * h, sm + kOffH + h * kHBytes, tid);
                     fence_async_smem();
-                    tc_fence_before();
                     __syncthreads();
-                } else {
-#pragma unroll
-                    for (int h = 0; h < kHalves; h++) {
-                        uint32_t r[2];
-                        tmem_ld2(t_lane + 64 * h, r);
-                        const float lg = __uint_as_float(r[0]) + __uint_as_float(r[1]);
-                        if (mine[h]) {
-                            logit[h] = lg;
-                            keep[h] = gated[h] || (lg > threshold);
-                            pending[h] = false;
-                        }
+                    loaded = cur;
+                }
+                // ---- three layers, one round trip each; the output layer in the last epilogue
+                bool ok = true;
+#pragma unroll 1
+                for (int layer = 0; layer < 3; layer++) {
+                    if (tid == 0) {
+                        tc_fence_after();
+                        if (layer == 0) issue_layer(tmem + kColD, a_in, 2, dW1, dB1, dOnes, kIdescN64, mbar);
+                        else if (layer == 1) issue_layer(tmem + kColD, tmem + kColH, 4, dW2, dB2, dOnes, kIdescN64, mbar);
+                        else issue_layer(tmem + kColD, tmem + kColH, 4, dW3, dB3, dOnes, kIdescN64, mbar);
+                    }
+                    if (layer == 0 && !built_next) {   // overlaps the first layer's round trip
+                        if (has_next) gated_next = build_inputs(t_lane + kColIn + 16u * (buf ^ 1u), next_valid, e_n, m_n, fis, assets);
+                        built_next = true;
+                    }
+                    ok = mbar_wait(mbar, phase);
+                    phase ^= 1u;
+                    tc_fence_after();
+                    if (layer < 2) {
+                        if (ok) epilogue_hidden(t_lane);
+                        tmem_wait_st();
+                    } else if (ok) {
+                        const float lg = epilogue_output(t_lane, reinterpret_cast<const float*>(sm + kOffW4));
+                        if (mine) { logit = lg; keep = gated || (lg > threshold); }
                     }
                     tc_fence_before();
+                    if (__syncthreads_or(!ok)) { abort = true; break; }
                 }
+                if (abort) break;
             }
-            if (!ok) {
-                if (tid == 0) atomicExch(err_flag, 1u);
-                abort = true;
-                break;
+            if (mine) pending = false;
+            if (step_min == step_max) break;   // one asset in this step (the common case)
+            // next asset of this step: the smallest one still pending
+            {
+                const int cand = __reduce_min_sync(0xffffffffu, pending ? my_asset : INT_MAX);
+                if (lane == 0) s_red[16 + warp] = cand;
             }
+            __syncthreads();
+            cur = min(min(s_red[16], s_red[17]), min(s_red[18], s_red[19]));
+            __syncthreads();
         }
         if (abort) break;
-#pragma unroll
-        for (int h = 0; h < kHalves; h++) {
-            const uint32_t row0 = step * kRows + h * 128;
-            const uint32_t w = __ballot_sync(0xffffffffu, keep[h]);
-            if (lane == 0 && row0 + warp * 32 < n) keep_bits[(row0 >> 5) + warp] = w;
-            if (logits_out && row0 + tid < n) logits_out[row0 + tid] = logit[h];
-        }
+        if (!built_next && has_next) gated_next = build_inputs(t_lane + kColIn + 16u * (buf ^ 1u), next_valid, e_n, m_n, fis, assets);
+        const uint32_t row0 = step * kRows;
+        const uint32_t w = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0 && row0 + warp * 32 < n) keep_bits[(row0 >> 5) + warp] = w;
+        if (logits_out && valid) logits_out[i] = logit;
+        e = e_n;
+        m = m_n;
+        gated = gated_next;
+        buf ^= 1u;
     }
+    if (abort) {
+        if (tid == 0) atomicExch(err_flag, 1u);
+        // the MMAs of the layer whose wait gave up may still be running: wait for them (bounded)
+        // before the tensor memory is released
+        mbar_wait(mbar, phase ^ 1u);
+    }
+    tmem_wait_st();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -375,10 +361,9 @@ static float bf16_to_f32(uint16_t h) {
     return f;
 }
 
-// Packs W1 (64x32), W2, W3 (64x64) as BF16 core-matrix tiles (row = output neuron, K-major), w4
-// as rows 0 (high part) and 1 (low part) of a 16 x 64 tile, and every bias as an N x 16 tile
-// with the high part in column 0 and the low part (bias - high, rounded) in column 1, in the
-// shared-memory byte layout k_mlp_tc reads.
+// Packs W1 (64x32), W2, W3 (64x64) as BF16 core-matrix tiles (row = output neuron, K-major), every
+// hidden bias as a 64 x 16 tile with the high part in column 0 and the low part (bias - high,
+// rounded) in column 1, and w4, b4 as FP32, in the shared-memory byte layout k_mlp_tc reads.
 void mlp_tc_pack_weights(const float* w, uint8_t* out) {
     memset(out, 0, kBlobBytes);
     const float* W1 = w;
@@ -405,17 +390,13 @@ void mlp_tc_pack_weights(const float* w, uint8_t* out) {
     put(kOffW1, 32, 64, W1);
     put(kOffW2, 64, 64, W2);
     put(kOffW3, 64, 64, W3);
-    for (int k = 0; k < 64; k++) {   // w4: rows 0 and 1 of the 16 x 64 tile
-        const uint16_t hi = f32_to_bf16_rne(W4[k]);
-        put1(kOffW4, 64, 0, k, hi);
-        put1(kOffW4, 64, 1, k, f32_to_bf16_rne(W4[k] - bf16_to_f32(hi)));
-    }
     for (int nrow = 0; nrow < 64; nrow++) {
         split(kOffB1, 16, nrow, 0, b1[nrow]);
         split(kOffB2, 16, nrow, 0, b2[nrow]);
         split(kOffB3, 16, nrow, 0, b3[nrow]);
     }
-    split(kOffB4, 16, 0, 0, b4[0]);
+    memcpy(out + kOffW4, W4, 64 * sizeof(float));
+    memcpy(out + kOffW4 + 256, b4, sizeof(float));
 }
 
 cudaError_t launch_mlp_tc(const uint2* list, const float4* list_mean, uint32_t n, const uint32_t* n_dev,

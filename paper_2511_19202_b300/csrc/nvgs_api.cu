@@ -158,8 +158,8 @@ nvgs_status validate_flags(nvgs_ctx* ctx, const nvgs_render_flags* f) {
     if (!(f->alpha_min > 0.f && f->alpha_min < 1.f) || !(f->alpha_max > 0.f && f->alpha_max <= 1.f) ||
         !(f->t_stop >= 0.f && f->t_stop < 1.f) || !(f->dilation >= 0.f) || !(f->guard_band > 0.f))
         return fail(ctx, NVGS_ERR_INVALID_ARG, "blending constants out of range");
-    if (f->mlp_ctas_per_sm < 0 || f->mlp_ctas_per_sm > 3)
-        return fail(ctx, NVGS_ERR_INVALID_ARG, "mlp_ctas_per_sm must be 0..3");
+    if (f->mlp_ctas_per_sm < 0 || f->mlp_ctas_per_sm > 4)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "mlp_ctas_per_sm must be 0..4");
     if (!(f->radius_clip_area >= 0.0f) || !std::isfinite(f->radius_clip_area))
         return fail(ctx, NVGS_ERR_INVALID_ARG, "radius_clip_area must be a finite value >= 0");
     if (f->profile < 0 || f->profile > 2)
@@ -1381,7 +1381,7 @@ extern "C" nvgs_status nvgs_autotune(nvgs_ctx* ctx, const nvgs_camera* cams, int
     const bool tc = f->use_mlp && uses_tc_mlp(ctx, f);
     const int tiles[3] = {8, 16, 32};
     const int splits[2] = {0, -1};
-    const int n_ctas = tc ? 3 : 1;
+    const int n_ctas = tc ? 4 : 1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaSetDevice(ctx->device));
     CK(cudaEventCreate(&e0));
