@@ -62,7 +62,9 @@ constexpr int kOffW4 = 26624;        // FP32 w4[64], then b4
 constexpr int kBlobBytes = 26896;
 constexpr int kOffOnes = (kBlobBytes + 1023) / 1024 * 1024;   // 128 x 16 BF16, columns 0 and 1 = 1
                                                               // (written in the kernel)
-constexpr int kOffMisc = kOffOnes + 4096;
+constexpr int kOffRowM = kOffOnes + 4096;       // next step's mean per row (16 B)
+constexpr int kOffRowE = kOffRowM + kRows * 16;  // next step's list entry per row (8 B)
+constexpr int kOffMisc = kOffRowE + kRows * 8;
 constexpr int kSmemBytes = kOffMisc + 128;
 constexpr uint32_t kSboK16 = 256;    // 16 * 16
 constexpr uint32_t kSboK32 = 512;    // 16 * 32
@@ -90,38 +92,50 @@ __device__ __forceinline__ void st_chunk(uint8_t* tile, uint32_t sbo, int row, i
     *reinterpret_cast<uint4*>(tile + (row >> 3) * sbo + chunk * kLbo + (row & 7) * 16) = v;
 }
 
-// TMEM accumulator (this lane, 64 columns, bias included) -> ReLU -> BF16 pairs in H.
+// TMEM accumulator (this lane, 64 columns, bias included) -> ReLU -> BF16 pairs in H, in two
+// 32-column halves (fewer live registers).
 __device__ __forceinline__ void epilogue_hidden(uint32_t t_lane) {
-    uint32_t r[64];
-    tmem_ld32_async(t_lane + kColD, r);
-    tmem_ld32_async(t_lane + kColD + 32, r + 32);
-    tmem_wait_ld64(r);
-    uint32_t p[32];
 #pragma unroll
-    for (int q = 0; q < 32; q++) p[q] = bf16x2_relu(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
-    tmem_st32(t_lane + kColH, p);
+    for (int h = 0; h < 2; h++) {
+        uint32_t r[32];
+        tmem_ld32(t_lane + kColD + 32 * h, r);
+        uint32_t p[16];
+#pragma unroll
+        for (int q = 0; q < 16; q++) p[q] = bf16x2_relu(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+        tmem_st16(t_lane + kColH + 16 * h, p);
+    }
 }
 
 // Output layer on the CUDA cores: acc (64 FP32 columns, b3 included) -> ReLU and BF16 rounding
 // (the hidden activations' precision) -> dot with the FP32 w4 -> + b4.
 __device__ __forceinline__ float epilogue_output(uint32_t t_lane, const float* __restrict__ w4) {
-    uint32_t r[64];
-    tmem_ld32_async(t_lane + kColD, r);
-    tmem_ld32_async(t_lane + kColD + 32, r + 32);
-    tmem_wait_ld64(r);
     float acc[4] = {w4[64], 0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int q = 0; q < 32; q += 2) {
-        const float4 w = *reinterpret_cast<const float4*>(w4 + 2 * q);
-        const uint32_t p0 = bf16x2_relu(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
-        const uint32_t p1 = bf16x2_relu(__uint_as_float(r[2 * q + 2]), __uint_as_float(r[2 * q + 3]));
-        acc[0] = fmaf(__uint_as_float(p0 << 16), w.x, acc[0]);
-        acc[1] = fmaf(__uint_as_float(p0 & 0xffff0000u), w.y, acc[1]);
-        acc[2] = fmaf(__uint_as_float(p1 << 16), w.z, acc[2]);
-        acc[3] = fmaf(__uint_as_float(p1 & 0xffff0000u), w.w, acc[3]);
+    for (int h = 0; h < 2; h++) {
+        uint32_t r[32];
+        tmem_ld32(t_lane + kColD + 32 * h, r);
+#pragma unroll
+        for (int q = 0; q < 16; q += 2) {
+            const float4 w = *reinterpret_cast<const float4*>(w4 + 32 * h + 2 * q);
+            const uint32_t p0 = bf16x2_relu(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+            const uint32_t p1 = bf16x2_relu(__uint_as_float(r[2 * q + 2]), __uint_as_float(r[2 * q + 3]));
+            acc[0] = fmaf(__uint_as_float(p0 << 16), w.x, acc[0]);
+            acc[1] = fmaf(__uint_as_float(p0 & 0xffff0000u), w.y, acc[1]);
+            acc[2] = fmaf(__uint_as_float(p1 << 16), w.z, acc[2]);
+            acc[3] = fmaf(__uint_as_float(p1 & 0xffff0000u), w.w, acc[3]);
+        }
     }
     return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
+
+// Asynchronous copy of this thread's next list entry and mean into shared memory (they are read
+// only when the next step's inputs are built, so no register holds them meanwhile).
+__device__ __forceinline__ void prefetch_row(uint2* s_e, float4* s_m, const uint2* e, const float4* m) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(s_e)), "l"(e) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(s_m)), "l"(m) : "memory");
+}
+__device__ __forceinline__ void prefetch_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void prefetch_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // This thread's row of inputs (32 features as 16 BF16 pairs) into its lane of an input buffer;
 // rows past the list get zeros (their outputs are never used).  Returns the row's instance gate
@@ -145,6 +159,21 @@ __device__ __forceinline__ bool build_inputs(uint32_t t_in, bool valid, uint2 e,
     }
     tmem_st16(t_in, p);
     return gated;
+}
+
+// The next step's inputs from the row staged in shared memory; also returns that row's asset.
+__device__ __forceinline__ bool build_next(uint32_t t_in, bool valid, const uint2* s_e, const float4* s_m,
+                                           const FrameInst* __restrict__ fis,
+                                           const AssetDev* __restrict__ assets, int& asset) {
+    prefetch_wait();
+    uint2 e = make_uint2(0, 0);
+    float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+        e = *s_e;
+        m = *s_m;
+    }
+    asset = valid ? __float_as_int(m.w) : INT_MAX;
+    return build_inputs(t_in, valid, e, m, fis, assets);
 }
 
 // One layer for the CTA's 128 rows (issued by one thread): K / 16 steps of A (TMEM) x W, then the
@@ -207,15 +236,19 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
     const uint32_t per_cta = (n_steps + gridDim.x - 1) / gridDim.x;
     const uint32_t s_begin = min(n_steps, blockIdx.x * per_cta);
     const uint32_t s_end = min(n_steps, s_begin + per_cta);
-    // this step's row; the first step's inputs are built here, every later step's during the
-    // previous step's first-layer round trip
-    uint2 e = make_uint2(0, 0);
-    float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+    // the first step's inputs are built here, every later step's during the previous step's
+    // first-layer round trip (from the list entry and mean staged in shared memory)
+    uint2* s_e = reinterpret_cast<uint2*>(sm + kOffRowE) + tid;
+    float4* s_m = reinterpret_cast<float4*>(sm + kOffRowM) + tid;
+    int my_asset_next = INT_MAX;   // asset of this thread's row of the next step
     bool gated = false;
     if (s_begin < s_end) {
         const uint32_t i0 = s_begin * kRows + tid;
+        uint2 e = make_uint2(0, 0);
+        float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
         if (i0 < n) { e = __ldg(&list[i0]); m = __ldg(&list_mean[i0]); }
         gated = build_inputs(t_lane + kColIn, i0 < n, e, m, fis, assets);
+        my_asset_next = i0 < n ? __float_as_int(m.w) : INT_MAX;
     }
     const uint64_t dOnes = sdesc(sm + kOffOnes, kLbo, kSboK16);
     const uint64_t dW1 = sdesc(sm + kOffW1, kLbo, kSboK32), dB1 = sdesc(sm + kOffB1, kLbo, kSboK16);
@@ -229,11 +262,10 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
         const uint32_t i_next = nstep * kRows + tid;
         const bool has_next = nstep < s_end;
         const bool next_valid = has_next && i_next < n;
-        uint2 e_n = make_uint2(0, 0);
-        float4 m_n = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (next_valid) { e_n = __ldg(&list[i_next]); m_n = __ldg(&list_mean[i_next]); }
+        if (next_valid) prefetch_row(s_e, s_m, &list[i_next], &list_mean[i_next]);
+        prefetch_commit();
         // the list's mean carries the row's asset id in w
-        const int my_asset = valid ? __float_as_int(m.w) : INT_MAX;
+        const int my_asset = my_asset_next;
         bool gated_next = false;
         // the CTA's smallest and largest asset of this step; the barrier also orders this step's
         // input stores and the previous step's accumulator reads before the first MMA
@@ -287,7 +319,8 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
                         else issue_layer(tmem + kColD, tmem + kColH, 4, dW3, dB3, dOnes, kIdescN64, mbar);
                     }
                     if (layer == 0 && !built_next) {   // overlaps the first layer's round trip
-                        if (has_next) gated_next = build_inputs(t_lane + kColIn + 16u * (buf ^ 1u), next_valid, e_n, m_n, fis, assets);
+                        if (has_next) gated_next = build_next(t_lane + kColIn + 16u * (buf ^ 1u), next_valid, s_e, s_m,
+                                                              fis, assets, my_asset_next);
                         built_next = true;
                     }
                     ok = mbar_wait(mbar, phase);
@@ -317,13 +350,13 @@ k_mlp_tc(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
             __syncthreads();
         }
         if (abort) break;
-        if (!built_next && has_next) gated_next = build_inputs(t_lane + kColIn + 16u * (buf ^ 1u), next_valid, e_n, m_n, fis, assets);
+        if (!built_next && has_next) gated_next = build_next(t_lane + kColIn + 16u * (buf ^ 1u), next_valid, s_e, s_m,
+                                                             fis, assets, my_asset_next);
+        if (!has_next) my_asset_next = INT_MAX;
         const uint32_t row0 = step * kRows;
         const uint32_t w = __ballot_sync(0xffffffffu, keep);
         if (lane == 0 && row0 + warp * 32 < n) keep_bits[(row0 >> 5) + warp] = w;
         if (logits_out && valid) logits_out[i] = logit;
-        e = e_n;
-        m = m_n;
         gated = gated_next;
         buf ^= 1u;
     }

@@ -114,7 +114,7 @@ def test_autotuner_times_every_candidate_and_images_do_not_depend_on_the_choice(
         base = r.flags(use_mlp=1, mlp_gate=0)
         best, table = N.nvgs_autotune(r.ctx, cams, base, out)
         print(table)
-        assert len(table) == 3 * 3 * 2
+        assert len(table) == 3 * 4 * 2          # tiles x MLP CTAs per SM x split
         assert {t["tile_size"] for t in table} == {8, 16, 32}
         fastest = min(table, key=lambda t: t["ms_per_view"])
         assert best.tile_size == fastest["tile_size"] and best.mlp_ctas_per_sm == fastest["mlp_ctas_per_sm"]
