@@ -116,6 +116,9 @@ def parse():
     p.add_argument("--mlp", choices=["trained", "random"], default="trained",
                    help="trained: per-asset GPU labels + Adam (Sec. 3.1-3.2) before timing")
     p.add_argument("--train-dirs", type=int, default=256)
+    p.add_argument("--train-precision", choices=["bf16", "fp32"], default="bf16",
+                   help="arithmetic of the training steps' forward and backward: BF16 on the tcgen05 "
+                        "tensor cores or FP32 on the CUDA cores (FP32 master weights and Adam either way)")
     p.add_argument("--train-steps", type=int, default=1000)
     p.add_argument("--train-res", type=int, default=512)
     p.add_argument("--train-aux", type=int, default=0,
@@ -324,18 +327,24 @@ def run_ours(args, rank, world):
         from paper_2511_19202_b300.train import train_visibility
         ids = r.load_scene(sc)
         t0 = time.perf_counter()
-        losses = []
+        losses, label_s, train_s = [], 0.0, 0.0
+        tprec = N.NVGS_PREC_BF16 if args.train_precision == "bf16" else N.NVGS_PREC_FP32
         for k in ids:
             _, info = train_visibility(r.ctx, k, n_dirs=args.train_dirs, n_dist=3, res=args.train_res,
                                        steps=args.train_steps, batch=65536, precision=prec,
                                        device=dev, log_every=args.train_steps, n_aux=args.train_aux,
                                        aux_angle_deg=args.train_aux_angle,
-                                       random_offset=args.train_offset)
+                                       random_offset=args.train_offset, train_precision=tprec)
             losses.append(info["losses"][-1][1])
+            label_s += info["label_s"]
+            train_s += info["train_s"]
         train_info = {"views_per_asset": 3 * args.train_dirs, "view_res": args.train_res,
                       "aux_views_per_view": args.train_aux, "aux_angle_deg": args.train_aux_angle,
                       "random_offset": bool(args.train_offset),
                       "steps": args.train_steps, "batch": 65536,
+                      "train_precision": args.train_precision,
+                      "label_seconds": label_s, "train_seconds": train_s,
+                      "train_steps_per_s": len(ids) * args.train_steps / max(train_s, 1e-9),
                       "final_loss_mean": float(np.mean(losses)),
                       "seconds_all_assets": time.perf_counter() - t0}
     else:

@@ -252,7 +252,10 @@ nvgs_status nvgs_train_init(nvgs_ctx* ctx, int asset_id, const float* w0, const 
 typedef struct {
     const uint8_t* labels;       /* DEVICE, n_views x N bytes from nvgs_label_visibility */
     int32_t batch;               /* samples per step (B) */
-    int32_t pad_;
+    int32_t precision;           /* NVGS_PREC_FP32 (0): forward and backward in FP32 on the CUDA
+                                    cores; NVGS_PREC_BF16: BF16 operands with FP32 accumulation on
+                                    the tcgen05 tensor cores, blocks of 128 samples.  Master
+                                    weights, moments and the Adam update are FP32 either way */
     const int32_t* sample_view;  /* nullable DEVICE [B]: explicit (view, gaussian) samples; NULL */
     const int32_t* sample_gauss; /*   draws them on the device from seed and step (SplitMix64) */
     uint64_t seed;
@@ -266,7 +269,8 @@ typedef struct {
 /* One Adam step on the class-balanced binary cross-entropy of B samples (a sample of class c
  * weighs B / (2 N_c), N_c = its class count in the batch: the class-frequency weighting of
  * Sec. 4.1).  loss_out (HOST, nullable) receives the batch loss; reading it
- * synchronises. */
+ * synchronises, and then a BF16 step whose bounded tensor-core wait gave up returns
+ * NVGS_ERR_TIMEOUT (its update must be discarded: reload a checkpoint). */
 nvgs_status nvgs_train_visibility_step(nvgs_ctx* ctx, int asset_id, const nvgs_train_batch* batch,
                                        const nvgs_adam_cfg* adam, float* loss_out);
 

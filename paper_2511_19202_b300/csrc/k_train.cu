@@ -1,7 +1,8 @@
 // Visibility-MLP training (NVGS Sec. 3.2 and 4.1): class-balanced binary cross-entropy on
 // (Gaussian, view) samples labelled by the GPU labeller, Adam on FP32 master weights.
 //
-// One step = three kernels:
+// One step = three kernels (the forward/backward kernel in FP32 here, or in BF16 on the tensor cores
+// in k_train_tc.cu):
 //   k_train_sample    draws B (view, gaussian) samples with a counter-based hash (SplitMix64's
 //                     finaliser of seed, step, sample index) unless explicit samples are given,
 //                     and counts the positive labels of the batch;
@@ -313,8 +314,8 @@ cudaError_t launch_train_step(const AssetDev* asset_dev, uint32_t n_gauss, const
                               uint32_t n_views, const uint8_t* labels, uint32_t B, uint64_t seed,
                               uint32_t step, int32_t* sv, int32_t* sg, int explicit_samples,
                               uint32_t* n_pos, float* loss_sum, float* partial, float* w, float* m,
-                              float* v, float lr, float beta1, float beta2, float eps,
-                              cudaStream_t s, LaunchLog* log) {
+                              float* v, float lr, float beta1, float beta2, float eps, int bf16,
+                              uint32_t* err_flag, cudaStream_t s, LaunchLog* log) {
     static std::atomic<uint64_t> attr_done{0};
     {
         cudaError_t e = once_per_device(attr_done, [] {
@@ -327,8 +328,17 @@ cudaError_t launch_train_step(const AssetDev* asset_dev, uint32_t n_gauss, const
     e = cudaMemsetAsync(loss_sum, 0, 4, s);
     if (e != cudaSuccess) return e;
     NVGS_LAUNCH(log, s, "k_train_sample", k_train_sample<<<(B + 255) / 256, 256, 0, s>>>(B, seed, step, n_views, n_gauss, labels, sv, sg, explicit_samples, n_pos));
-    const int nb = (int)((B + kS - 1) / kS);
-    NVGS_LAUNCH(log, s, "k_train_fwd_bwd", k_train_fwd_bwd<<<nb, kT, kSmemBytes, s>>>(w, asset_dev, views, labels, sv, sg, B, n_gauss, n_pos, partial, loss_sum));
+    // partial gradients: one per block of 64 samples (FP32) or 128 samples (BF16 tensor cores)
+    int nb;
+    if (bf16) {
+        nb = (int)((B + 127) / 128);
+        e = launch_train_fwd_bwd_tc(w, asset_dev, views, labels, sv, sg, B, n_gauss, n_pos, partial, loss_sum,
+                                    err_flag, s, log);
+        if (e != cudaSuccess) return e;
+    } else {
+        nb = (int)((B + kS - 1) / kS);
+        NVGS_LAUNCH(log, s, "k_train_fwd_bwd", k_train_fwd_bwd<<<nb, kT, kSmemBytes, s>>>(w, asset_dev, views, labels, sv, sg, B, n_gauss, n_pos, partial, loss_sum));
+    }
     const double bc1 = 1.0 - pow((double)beta1, (double)step + 1.0);
     const double bc2 = 1.0 - pow((double)beta2, (double)step + 1.0);
     const int ng = (nb + kGroup - 1) / kGroup;

@@ -964,6 +964,8 @@ extern "C" nvgs_status nvgs_train_visibility_step(nvgs_ctx* ctx, int asset_id, c
         return fail(ctx, NVGS_ERR_INVALID_ARG, "asset %d has no training state (nvgs_train_init)", asset_id);
     if (!b || !adam || !b->labels || b->batch < 1 || (!b->sample_view) != (!b->sample_gauss))
         return fail(ctx, NVGS_ERR_INVALID_ARG, "bad batch");
+    if (b->precision != NVGS_PREC_FP32 && b->precision != NVGS_PREC_BF16)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "batch precision must be NVGS_PREC_FP32 or NVGS_PREC_BF16");
     if (!(adam->lr >= 0.f) || !(adam->beta1 >= 0.f && adam->beta1 < 1.f) ||
         !(adam->beta2 >= 0.f && adam->beta2 < 1.f) || !(adam->eps > 0.f) || adam->step < 0)
         return fail(ctx, NVGS_ERR_INVALID_ARG, "bad Adam configuration");
@@ -985,16 +987,20 @@ extern "C" nvgs_status nvgs_train_visibility_step(nvgs_ctx* ctx, int asset_id, c
     }
     uint32_t* counters = P<uint32_t>(ctx->counters);
     ctx->log.count = 0;
+    const bool tc = b->precision == NVGS_PREC_BF16;
+    if (tc) CK(cudaMemsetAsync(&counters[12], 0, 4, s));
     CK(launch_train_step(P<AssetDev>(ctx->assets_dev) + asset_id, (uint32_t)ctx->assets[asset_id].dev.n,
                          P<float4>(T.views), (uint32_t)T.n_views, b->labels, B, b->seed,
                          (uint32_t)adam->step, P<int32_t>(ctx->tr_sv), P<int32_t>(ctx->tr_sg), expl ? 1 : 0,
                          &counters[10], reinterpret_cast<float*>(&counters[11]), P<float>(ctx->tr_partial),
                          P<float>(T.w), P<float>(T.m), P<float>(T.v), adam->lr, adam->beta1, adam->beta2,
-                         adam->eps, s, &ctx->log));
+                         adam->eps, tc ? 1 : 0, &counters[12], s, &ctx->log));
     if (loss_out) {
-        CK(cudaMemcpyAsync(ctx->h_counters + 11, &counters[11], 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(ctx->h_counters + 11, &counters[11], 8, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         memcpy(loss_out, ctx->h_counters + 11, 4);
+        if (tc && ctx->h_counters[12])
+            return fail(ctx, NVGS_ERR_TIMEOUT, "tensor-core training step: a bounded mbarrier wait gave up");
     }
     return NVGS_OK;
 }

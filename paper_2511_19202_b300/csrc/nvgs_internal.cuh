@@ -302,13 +302,19 @@ size_t mlp_tc_weight_bytes();
 void mlp_tc_pack_weights(const float* w, uint8_t* out);
 
 // One training step of the visibility MLP (k_train.cu); partial needs train_partial_bytes(B).
+// bf16: forward and backward on the tcgen05 tensor cores (k_train_tc.cu) instead of FP32 CUDA
+// cores; err_flag receives 1 if a bounded tensor-core wait gave up.
 size_t train_partial_bytes(uint32_t B);
 cudaError_t launch_train_step(const AssetDev* asset_dev, uint32_t n_gauss, const float4* views,
                               uint32_t n_views, const uint8_t* labels, uint32_t B, uint64_t seed,
                               uint32_t step, int32_t* sv, int32_t* sg, int explicit_samples,
                               uint32_t* n_pos, float* loss_sum, float* partial, float* w, float* m,
-                              float* v, float lr, float beta1, float beta2, float eps,
-                              cudaStream_t s, LaunchLog* log);
+                              float* v, float lr, float beta1, float beta2, float eps, int bf16,
+                              uint32_t* err_flag, cudaStream_t s, LaunchLog* log);
+cudaError_t launch_train_fwd_bwd_tc(const float* w, const AssetDev* asset, const float4* views,
+                                    const uint8_t* labels, const int32_t* sv, const int32_t* sg, uint32_t B,
+                                    uint32_t n_gauss, const uint32_t* n_pos, float* partial, float* loss_sum,
+                                    uint32_t* err_flag, cudaStream_t s, LaunchLog* log);
 
 // Per-block popcounts of a bitmask over n items (blocks of kChunk items).
 cudaError_t launch_bit_counts(const uint32_t* bits, uint32_t n, const uint32_t* n_dev,

@@ -89,7 +89,7 @@ class AssetInfo(C.Structure):
 
 
 class TrainBatch(C.Structure):
-    _fields_ = [("labels", C.c_void_p), ("batch", C.c_int32), ("pad_", C.c_int32),
+    _fields_ = [("labels", C.c_void_p), ("batch", C.c_int32), ("precision", C.c_int32),
                 ("sample_view", C.c_void_p), ("sample_gauss", C.c_void_p), ("seed", C.c_uint64)]
 
 
@@ -389,10 +389,11 @@ def nvgs_train_init(ctx, asset_id: int, w0, views):
 
 def nvgs_train_visibility_step(ctx, asset_id: int, labels, batch: int, step: int, lr: float,
                                seed: int = 0, sample_view=None, sample_gauss=None,
-                               beta1=0.9, beta2=0.999, eps=1e-8, want_loss=False):
+                               beta1=0.9, beta2=0.999, eps=1e-8, want_loss=False, precision=0):
     b = TrainBatch()
     b.labels = _ptr(labels)
     b.batch = int(batch)
+    b.precision = int(precision)
     b.sample_view = _ptr(sample_view)
     b.sample_gauss = _ptr(sample_gauss)
     b.seed = int(seed)

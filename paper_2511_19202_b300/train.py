@@ -30,8 +30,12 @@ def train_visibility(ctx, asset_id: int, n_dirs: int = 512, n_dist: int = 3, res
                      steps: int = 1500, batch: int = 65536, lr0: float = 2e-3, lr1: float = 2e-4,
                      warmup: float = 0.2, seed: int = 0, precision: int = N.NVGS_PREC_BF16,
                      tile: int = 16, device: int = 0, log_every: int = 0, n_aux: int = 0,
-                     aux_angle_deg: float = 2.5, random_offset: bool = False):
+                     aux_angle_deg: float = 2.5, random_offset: bool = False,
+                     train_precision: int = N.NVGS_PREC_BF16):
     """Labels, trains and installs the visibility MLP of one asset.  Returns (weights, info).
+    train_precision: NVGS_PREC_BF16 runs each step's forward and backward in BF16 on the tensor
+    cores (FP32 master weights and Adam), NVGS_PREC_FP32 on the CUDA cores; ``precision`` is the
+    arithmetic the installed MLP is queried in.
     n_aux > 0 adds that many auxiliary cone views per main view (a Gaussian is labelled visible
     if any of them blends it; Sec. 3.1); random_offset shifts the asset off the image centre
     (Sec. 3.1, 4.1)."""
@@ -55,11 +59,13 @@ def train_visibility(ctx, asset_id: int, n_dirs: int = 512, n_dist: int = 3, res
         lr = N.nvgs_lr_schedule(step, steps, lr0, lr1, warmup)
         want = bool(log_every) and (step % log_every == 0 or step == steps - 1)
         loss = N.nvgs_train_visibility_step(ctx, asset_id, labels, batch, step, lr, seed=seed,
-                                            want_loss=want)
+                                            want_loss=want, precision=train_precision)
         if want:
             losses.append((step, loss))
     w = N.nvgs_train_get_weights(ctx, asset_id)
     N.nvgs_set_mlp(ctx, asset_id, w, precision)
     del labels
-    return w, {"label_s": t_label, "total_s": time.perf_counter() - t0, "views": len(views),
+    torch.cuda.synchronize(device)
+    return w, {"label_s": t_label, "train_s": time.perf_counter() - t0 - t_label,
+               "total_s": time.perf_counter() - t0, "views": len(views),
                "visible_fraction": visible_frac, "losses": losses}

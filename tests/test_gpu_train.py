@@ -75,6 +75,61 @@ def test_train_step_matches_oracle_gradient():
     assert err <= 1e-4 * scale + 2e-7
 
 
+@pytest.mark.parametrize("B", [1000, 4096])
+def test_bf16_train_step_matches_oracle_gradient(B):
+    """The BF16 tensor-core step (tcgen05 forward and backward, FP32 master weights): its gradient
+    against the FP64 oracle's.  BF16 keeps 8 significant bits (unit roundoff u = 2^-9 ~ 2e-3); each
+    GEMM rounds its operands once and accumulates in FP32, and the error compounds over the three
+    forward and three backward GEMMs, so each layer's gradient is held to a relative L2 error of
+    3e-2 and the loss to 1e-2.  The labels are structured (visible iff the mean's x > 0, like the
+    spatially coherent labels of an occluder): with random labels the class-balanced gradient is a
+    near-cancelling sum of +- terms and BF16 rounding of the terms dominates it, whatever the
+    kernel.  B = 1000 leaves a ragged last block of 104 samples."""
+    from paper_2511_19202_b300 import nvgs as N
+    sc = scenes.config1_scene(3000)
+    cams = [scenes.look_at_camera(3.0 * d, (0, 0, 0), 128, 128, 50.0) for d in scenes.fibonacci_directions(6)]
+    rng = np.random.default_rng(1 + B)
+    labels = np.tile((sc.assets[0].means[:, 0] > 0).astype(np.uint8), (6, 1))
+    sv = rng.integers(0, 6, B).astype(np.int32)
+    sg = rng.integers(0, 3000, B).astype(np.int32)
+    w = scenes.mlp_weights(3)
+    for k in range(1, 5):
+        w[f"b{k}"] = rng.normal(0, 0.2, w[f"b{k}"].shape).astype(np.float32)
+    w0 = N.flat_weights(w)
+    r = renderer_for(sc)
+    try:
+        N.nvgs_train_init(r.ctx, 0, w0, cams)
+        d_lab = torch.from_numpy(labels.ravel()).cuda()
+        loss = N.nvgs_train_visibility_step(r.ctx, 0, d_lab, B, 0, 1e6, sample_view=torch.from_numpy(sv).cuda(),
+                                            sample_gauss=torch.from_numpy(sg).cuda(), beta1=0.0, beta2=0.0,
+                                            eps=1e6, want_loss=True, precision=N.NVGS_PREC_BF16)
+        w1 = N.nvgs_train_get_weights(r.ctx, 0).astype(np.float64)
+    finally:
+        r.close()
+    osc = oracle.OracleScene(sc)
+    views = oracle.training_views_table(cams)
+    ref_loss, g = oracle.train_loss_grad(osc, 0, views, labels, sv, sg, oracle.flat_weights(w))
+    step_gpu = w0.astype(np.float64) - w1
+    step_ref = g / (1.0 + np.abs(g) / 1e6)
+    layers = {"W1": (0, 2048), "b1": (2048, 2112), "W2": (2112, 6208), "b2": (6208, 6272),
+              "W3": (6272, 10368), "b3": (10368, 10432), "W4": (10432, 10496), "b4": (10496, 10497)}
+    errs = {}
+    for name, (a, b) in layers.items():
+        ref = step_ref[a:b]
+        errs[name] = float(np.linalg.norm(step_gpu[a:b] - ref) / max(np.linalg.norm(ref), 1e-30))
+    print(f"bf16 train step B={B}: loss {loss:.6f} vs {ref_loss:.6f}; relative L2 error per layer "
+          + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    assert loss == pytest.approx(ref_loss, rel=1e-2)
+    for name, e in errs.items():
+        if name != "b4":
+            assert e <= 3e-2, (name, e)
+    # gb4 = sum of dL/dz: under class balancing the two classes' sums nearly cancel, so its error is
+    # bounded against the RMS entry of gW4 (the output layer's gradient scale) instead
+    a4, b4_ = layers["W4"]
+    rms_w4 = float(np.sqrt(np.mean(step_ref[a4:b4_] ** 2)))
+    assert abs(step_gpu[10496] - step_ref[10496]) <= 3e-2 * rms_w4
+
+
 def test_training_learns_back_face_occlusion():
     """A dense sphere hides its far side: after training on GPU labels, the MLP predicts fresh
     labels of held-out views clearly better than the majority class, and a conservative threshold
