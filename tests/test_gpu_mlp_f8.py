@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import scenes
-from gpu_common import compare_images, gpu_image, layered_case, oracle_opts_for, renderer_for
+from gpu_common import compare_images, e4m3, f8_reference, gpu_image, layered_case, oracle_opts_for, renderer_for
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -19,42 +19,6 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 FP8 = 2
-
-
-def e4m3(x):
-    """Round to the nearest E4M3 value (ties to even), saturating at +-448; subnormals 2^-9 apart."""
-    x = np.asarray(x, np.float64)
-    a = np.minimum(np.abs(x), 448.0)
-    out = np.zeros_like(a)
-    sub = a < 2.0 ** -6
-    out[sub] = np.rint(a[sub] / 2.0 ** -9) * 2.0 ** -9
-    nrm = ~sub & (a > 0)
-    e = np.floor(np.log2(a[nrm]))
-    q = 2.0 ** (e - 3)
-    out[nrm] = np.minimum(np.rint(a[nrm] / q) * q, 448.0)
-    return np.sign(x) * out
-
-
-def f8_reference(w, feats):
-    W1, b1 = w["W1"].astype(np.float64), w["b1"].astype(np.float64)
-    W2, b2 = w["W2"].astype(np.float64), w["b2"].astype(np.float64)
-    W3, b3 = w["W3"].astype(np.float64), w["b3"].astype(np.float64)
-    W4, b4 = w["W4"].astype(np.float64).ravel(), float(np.ravel(w["b4"])[0])
-    f32 = np.float32
-    sW = [np.abs(W).max() / 448.0 for W in (W1, W2, W3)]
-    B1 = (np.abs(W1).sum(1) + np.abs(b1)).max()
-    B2 = (np.abs(W2).sum(1) * B1 + np.abs(b2)).max()
-    sh1, sh2 = B1 / 448.0, B2 / 448.0
-    a1, a2, a3 = f32(sW[0] / 256.0 / sh1), f32(sh1 * sW[1] / sh2), f32(sh2 * sW[2])
-    be1, be2 = (b1 / sh1).astype(f32), (b2 / sh2).astype(f32)
-    qx = e4m3(256.0 * feats)
-    acc1 = (qx @ e4m3(W1 / sW[0]).T).astype(f32)
-    q1 = e4m3(np.maximum(acc1 * a1 + be1, 0).astype(f32))
-    acc2 = (q1 @ e4m3(W2 / sW[1]).T).astype(f32)
-    q2 = e4m3(np.maximum(acc2 * a2 + be2, 0).astype(f32))
-    acc3 = (q2 @ e4m3(W3 / sW[2]).T).astype(f32)
-    h3 = np.maximum(acc3 * a3 + b3.astype(f32), 0).astype(np.float64)
-    return h3 @ W4.astype(f32).astype(np.float64) + b4
 
 
 def test_e4m3_rounding_reference():
