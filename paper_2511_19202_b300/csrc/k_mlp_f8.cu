@@ -12,11 +12,18 @@
 // and the third layer's h3 = max(0, acc alpha_3 + b3) stays FP32 for the 64 -> 1 output on the
 // CUDA cores.  Conversions saturate (cvt .satfinite), so a value past its bound clamps to 448.
 //
-// Structure as in the BF16 kernel: one warpgroup per CTA, two 128-row tiles per step sharing each
-// MMA round trip, list entries loaded a step ahead, the next step's inputs built during the first
-// layer's round trip, bounded mbarrier waits, multi-asset passes.  Operands are K-major without
-// swizzle; an 8-bit core matrix is 8 rows x 16 elements, element (row, k) of a K-column tile at
-// (row / 8) * SBO + (k / 16) * 128 + (row % 8) * 16 + (k % 16), SBO = 8 K bytes.
+// Structure as in the BF16 kernel (k_mlp_tc.cu): four single-tile CTAs per SM, each walking a
+// contiguous range of 128-row steps with 128 TMEM columns --
+//   [0, 64)   D   FP32 accumulator
+//   [64, 80)  H   the hidden activations as E4M3 (4 per 32-bit column, the lower k in the low byte):
+//                 the next layer's A operand
+//   [80, 96)  IN  two 8-column buffers of E4M3 inputs (this step's and the next step's)
+// -- so an MMA reads only its weight tile from shared memory; a step is 1 + 2 + 2 MMAs in three round
+// trips; the next step's list rows are staged in shared memory by cp.async and its inputs built
+// during the first layer's round trip; rows of several assets run one pass per asset; every wait
+// is bounded.  Weight tiles are K-major without swizzle; an 8-bit core matrix is 8 rows x 16
+// elements, element (row, k) of a K-column tile at (row / 8) * SBO + (k / 16) * 128 + (row % 8) * 16
+// + (k % 16), SBO = 8 K bytes.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -33,9 +40,11 @@ using namespace tc;
 
 constexpr int kThreads = 128;
 constexpr int kCtasPerSm = 4;
-constexpr int kHalves = 2;
-constexpr int kRows = 128 * kHalves;
-constexpr int kTmemCols = 64 * kHalves;
+constexpr int kRows = 128;
+constexpr int kTmemCols = 128;
+constexpr uint32_t kColD = 0;
+constexpr uint32_t kColH = 64;
+constexpr uint32_t kColIn = 80;       // + 8 * buffer
 // blob (packed on the host): E4M3 weight tiles, then FP32 vectors
 constexpr int kOffW1 = 0;        // 64 x 32 E4M3 (SBO 256)
 constexpr int kOffW2 = 2048;     // 64 x 64 E4M3 (SBO 512)
@@ -43,10 +52,10 @@ constexpr int kOffW3 = 6144;
 constexpr int kOffVec = 10240;   // FP32: beta1[64] beta2[64] b3[64] w4[64] b4 alpha1 alpha2 alpha3
 constexpr int kVecFloats = 260;
 constexpr int kBlobBytes = kOffVec + kVecFloats * 4;   // 11280
-constexpr int kOffH = 11520;     // kHalves x (128 x 64 E4M3); the 128 x 32 input tile overlays it
-constexpr int kHBytes = 8192;
-constexpr int kOffMisc = kOffH + kHalves * kHBytes;
-constexpr int kSmemBytes = kOffMisc + 64;
+constexpr int kOffRowM = 11264 + 1024;                 // next step's mean per row (16 B)
+constexpr int kOffRowE = kOffRowM + kRows * 16;        // next step's list entry per row (8 B)
+constexpr int kOffMisc = kOffRowE + kRows * 8;
+constexpr int kSmemBytes = kOffMisc + 128;
 constexpr uint32_t kSboK32 = 256;
 constexpr uint32_t kSboK64 = 512;
 constexpr uint32_t kLbo = 128;
@@ -56,60 +65,109 @@ constexpr float kInScale = 256.0f;
 // N / 8 at bit 17, M / 16 at bit 24.
 constexpr uint32_t kIdesc = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
-// (lo, hi) -> two saturated E4M3 codes, lo in the low byte (the lower address).
+// (lo, hi) -> two saturated E4M3 codes, lo in the low byte (the lower k).
 __device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
     uint16_t d;
     asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
     return (uint32_t)d;
 }
-
-__device__ __forceinline__ void st_chunk(uint8_t* tile, uint32_t sbo, int row, int chunk, uint4 v) {
-    *reinterpret_cast<uint4*>(tile + (row >> 3) * sbo + chunk * kLbo + (row & 7) * 16) = v;
+__device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
+    return e4m3x2(a, b) | (e4m3x2(c, d) << 16);
 }
 
-// 16 consecutive values -> 16 E4M3 bytes
-__device__ __forceinline__ uint4 pack16(const float* v) {
-    uint32_t w[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++)
-        w[q] = e4m3x2(v[4 * q], v[4 * q + 1]) | (e4m3x2(v[4 * q + 2], v[4 * q + 3]) << 16);
-    return make_uint4(w[0], w[1], w[2], w[3]);
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+                   "r"(r[7])
+                 : "memory");
 }
 
-// hidden epilogue: q_h = E4M3_sat(max(0, acc alpha + beta)) into the next layer's A tile
-__device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, float alpha, const float* beta, uint8_t* sH,
-                                                int row) {
+__device__ __forceinline__ void mma_f8_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %3, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %4, p;\n\t}\n"
+        ::"r"(d_tmem), "r"(a_tmem), "l"(b), "r"(accumulate), "r"(kIdesc)
+        : "memory");
+}
+
+// hidden epilogue: q_h = E4M3_sat(max(0, acc alpha + beta)) into H, in two 32-column halves
+__device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, float alpha, const float* beta) {
 #pragma unroll
     for (int half = 0; half < 2; half++) {
         uint32_t r[32];
-        tmem_ld32(t_lane + half * 32, r);
+        tmem_ld32(t_lane + kColD + 32 * half, r);
+        uint32_t p[8];
 #pragma unroll
-        for (int c = 0; c < 2; c++) {
-            float v[16];
+        for (int q = 0; q < 8; q++) {
+            float v[4];
 #pragma unroll
-            for (int q = 0; q < 16; q++) {
-                const int col = half * 32 + c * 16 + q;
-                v[q] = fmaxf(fmaf(__uint_as_float(r[c * 16 + q]), alpha, beta[col]), 0.0f);
+            for (int e = 0; e < 4; e++) {
+                const int col = 32 * half + 4 * q + e;
+                v[e] = fmaxf(fmaf(__uint_as_float(r[4 * q + e]), alpha, beta[col]), 0.0f);
             }
-            st_chunk(sH, kSboK64, row, half * 2 + c, pack16(v));
+            p[q] = e4m3x4(v[0], v[1], v[2], v[3]);
         }
+        tmem_st8(t_lane + kColH + 8 * half, p);
     }
 }
 
 __device__ __forceinline__ float epilogue_logit(uint32_t t_lane, float alpha, const float* b3, const float* w4,
                                                 float b4) {
-    float lg = b4;
+    float lg[2] = {b4, 0.0f};
 #pragma unroll
     for (int half = 0; half < 2; half++) {
         uint32_t r[32];
-        tmem_ld32(t_lane + half * 32, r);
+        tmem_ld32(t_lane + kColD + 32 * half, r);
 #pragma unroll
         for (int k = 0; k < 32; k++) {
             const int col = half * 32 + k;
-            lg = fmaf(w4[col], fmaxf(fmaf(__uint_as_float(r[k]), alpha, b3[col]), 0.0f), lg);
+            lg[k & 1] = fmaf(w4[col], fmaxf(fmaf(__uint_as_float(r[k]), alpha, b3[col]), 0.0f), lg[k & 1]);
         }
     }
-    return lg;
+    return lg[0] + lg[1];
+}
+
+__device__ __forceinline__ void prefetch_row(uint2* s_e, float4* s_m, const uint2* e, const float4* m) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(s_e)), "l"(e) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(s_m)), "l"(m) : "memory");
+}
+__device__ __forceinline__ void prefetch_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void prefetch_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// This thread's row of E4M3 inputs into its lane of an input buffer (zeros past the list); returns
+// the row's instance gate.
+__device__ __forceinline__ bool build_inputs(uint32_t t_in, bool valid, uint2 e, float4 m,
+                                             const FrameInst* __restrict__ fis,
+                                             const AssetDev* __restrict__ assets) {
+    uint32_t p[8];
+    bool gated = false;
+    if (valid) {
+        const FrameInst& fr = fis[e.x];
+        gated = fr.gated != 0;
+        const MlpAsset ma = mlp_asset(assets[__float_as_int(m.w)]);
+        float f[32];
+        mlp_features(ma, fr.cam_local[0], fr.cam_local[1], fr.cam_local[2], fr.dist_scale, m, f);
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+            p[q] = e4m3x4(f[4 * q] * kInScale, f[4 * q + 1] * kInScale, f[4 * q + 2] * kInScale, f[4 * q + 3] * kInScale);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; q++) p[q] = 0u;
+    }
+    tmem_st8(t_in, p);
+    return gated;
+}
+
+__device__ __forceinline__ bool build_next(uint32_t t_in, bool valid, const uint2* s_e, const float4* s_m,
+                                           const FrameInst* __restrict__ fis,
+                                           const AssetDev* __restrict__ assets, int& asset) {
+    prefetch_wait();
+    uint2 e = make_uint2(0, 0);
+    float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) { e = *s_e; m = *s_m; }
+    asset = valid ? __float_as_int(m.w) : INT_MAX;
+    return build_inputs(t_in, valid, e, m, fis, assets);
 }
 
 }  // namespace
@@ -124,6 +182,7 @@ k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
     const float* sVec = reinterpret_cast<const float*>(sm + kOffVec);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kOffMisc);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + kOffMisc + 8);
+    // reduction slots: per step parity [0,4) min and [4,8) max, then [16,20) pass min
     int* s_red = reinterpret_cast<int*>(sm + kOffMisc + 16);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -141,188 +200,136 @@ k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
     const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint64_t dW1 = sdesc(sm + kOffW1, kLbo, kSboK32);
+    const uint64_t dW2 = sdesc(sm + kOffW2, kLbo, kSboK64);
+    const uint64_t dW3 = sdesc(sm + kOffW3, kLbo, kSboK64);
 
     uint32_t phase = 0;
-    int loaded = -1;
+    int loaded = -1, known = -1;
+    bool has_mlp = false;
     bool abort = false;
+    uint32_t buf = 0;
     const uint32_t n_steps = (n + kRows - 1) / kRows;
-    uint4 qnext[kHalves][2];                   // E4M3 inputs of this thread's next-step rows
-    int qnext_asset[kHalves] = {-1, -1};       // the asset they were built for (-1: none)
-    // row inputs of the next step are loaded one step ahead
-    uint2 e_next[kHalves];
-    float4 m_next[kHalves];
-#pragma unroll
-    for (int h = 0; h < kHalves; h++) {
-        const uint32_t i = blockIdx.x * kRows + h * 128 + tid;
-        e_next[h] = make_uint2(0, 0);
-        m_next[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (blockIdx.x < n_steps && i < n) {
-            e_next[h] = __ldg(&list[i]);
-            m_next[h] = __ldg(&list_mean[i]);
-        }
+    const uint32_t per_cta = (n_steps + gridDim.x - 1) / gridDim.x;
+    const uint32_t s_begin = min(n_steps, blockIdx.x * per_cta);
+    const uint32_t s_end = min(n_steps, s_begin + per_cta);
+    uint2* s_e = reinterpret_cast<uint2*>(sm + kOffRowE) + tid;
+    float4* s_m = reinterpret_cast<float4*>(sm + kOffRowM) + tid;
+    int my_asset_next = INT_MAX;
+    bool gated = false;
+    if (s_begin < s_end) {
+        const uint32_t i0 = s_begin * kRows + tid;
+        uint2 e = make_uint2(0, 0);
+        float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i0 < n) { e = __ldg(&list[i0]); m = __ldg(&list_mean[i0]); }
+        gated = build_inputs(t_lane + kColIn, i0 < n, e, m, fis, assets);
+        my_asset_next = i0 < n ? __float_as_int(m.w) : INT_MAX;
     }
-    for (uint32_t step = blockIdx.x; step < n_steps && !abort; step += gridDim.x) {
-        uint2 e[kHalves];
-        float4 m[kHalves], ci[kHalves];
-        int my_asset[kHalves];
-        bool pending[kHalves], keep[kHalves], gated[kHalves];
-        float logit[kHalves];
-#pragma unroll
-        for (int h = 0; h < kHalves; h++) {
-            const uint32_t i = step * kRows + h * 128 + tid;
-            e[h] = e_next[h];
-            m[h] = m_next[h];
-            const uint32_t i_next = (step + gridDim.x) * kRows + h * 128 + tid;
-            if (step + gridDim.x < n_steps && i_next < n) {
-                e_next[h] = __ldg(&list[i_next]);
-                m_next[h] = __ldg(&list_mean[i_next]);
-            }
-            ci[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-            gated[h] = false;
-            if (i < n) {   // instance values the inputs need, loaded ahead of their use
-                const FrameInst& fr = fis[e[h].x];
-                ci[h] = make_float4(fr.cam_local[0], fr.cam_local[1], fr.cam_local[2], fr.dist_scale);
-                gated[h] = fr.gated != 0;
-            }
-            my_asset[h] = i < n ? __float_as_int(m[h].w) : INT_MAX;   // the list mean carries it
-            pending[h] = i < n;
-            keep[h] = false;
-            logit[h] = 0.0f;
-        }
-        bool pre_done = false;
-        for (;;) {
-            int cand = min(pending[0] ? my_asset[0] : INT_MAX, pending[1] ? my_asset[1] : INT_MAX);
-            cand = __reduce_min_sync(0xffffffffu, cand);
-            if (lane == 0) s_red[warp] = cand;
-            __syncthreads();
-            const int cur = min(min(s_red[0], s_red[1]), min(s_red[2], s_red[3]));
-            __syncthreads();
-            if (cur == INT_MAX) break;
-            const AssetDev& a = assets[cur];
-            bool mine[kHalves];
-#pragma unroll
-            for (int h = 0; h < kHalves; h++) mine[h] = pending[h] && my_asset[h] == cur;
-            if (a.w_f8 == nullptr) {   // asset without an MLP: rendered unculled
-#pragma unroll
-                for (int h = 0; h < kHalves; h++)
-                    if (mine[h]) { keep[h] = true; logit[h] = __int_as_float(0x7f800000); pending[h] = false; }
-                continue;
-            }
-            if (cur != loaded) {
-                const uint4* src = reinterpret_cast<const uint4*>(a.w_f8);
-                uint4* dst = reinterpret_cast<uint4*>(sm);
-                for (int k = tid; k < kBlobBytes / 16; k += kThreads) dst[k] = __ldg(&src[k]);
-                loaded = cur;
-            }
-            // ---- inputs -> A (E4M3, scaled by 256), one row per half
-#pragma unroll
-            for (int h = 0; h < kHalves; h++) {
-                uint8_t* sA = sm + kOffH + h * kHBytes;
-                if (mine[h] && qnext_asset[h] == cur) {   // built during the previous step
-                    st_chunk(sA, kSboK32, tid, 0, qnext[h][0]);
-                    st_chunk(sA, kSboK32, tid, 1, qnext[h][1]);
-                    continue;
-                }
-                float f[32];
-                if (mine[h]) {
-                    mlp_features(mlp_asset(a), ci[h].x, ci[h].y, ci[h].z, ci[h].w, m[h], f);
-#pragma unroll
-                    for (int k = 0; k < 32; k++) f[k] *= kInScale;
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 32; k++) f[k] = 0.0f;
-                }
-                st_chunk(sA, kSboK32, tid, 0, pack16(f));
-                st_chunk(sA, kSboK32, tid, 1, pack16(f + 16));
-            }
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
 
-            bool ok = true;
-#pragma unroll 1
-            for (int layer = 0; layer < 3 && ok; layer++) {
-                if (tid == 0) {
-                    tc_fence_after();
-#pragma unroll
-                    for (int h = 0; h < kHalves; h++) {
-                        const uint8_t* sH = sm + kOffH + h * kHBytes;
-                        const uint32_t d = tmem + 64 * h;
-                        if (layer == 0) {
-                            mma_f8(d, sdesc(sH, kLbo, kSboK32), sdesc(sm + kOffW1, kLbo, kSboK32), kIdesc, 0);
-                        } else {
-                            const uint8_t* W = sm + (layer == 1 ? kOffW2 : kOffW3);
-#pragma unroll
-                            for (int k = 0; k < 2; k++)   // K = 64 in two K = 32 steps (256 bytes apart)
-                                mma_f8(d, sdesc(sH + 256 * k, kLbo, kSboK64), sdesc(W + 256 * k, kLbo, kSboK64),
-                                       kIdesc, k > 0);
-                        }
-                    }
-                    mma_commit(mbar);
-                }
-                // the inputs of this thread's rows of the CTA's next step are built during the first
-                // layer's round trip (when they belong to the asset of this pass), once every row of
-                // this thread in the current step has had its inputs written (this pass or earlier)
-                if (layer == 0 && !pre_done && (mine[0] || !pending[0]) && (mine[1] || !pending[1])) {
-                    pre_done = true;
-                    const MlpAsset ma = mlp_asset(a);
-#pragma unroll
-                    for (int h = 0; h < kHalves; h++) {
-                        const uint32_t i_next = (step + gridDim.x) * kRows + h * 128 + tid;
-                        qnext_asset[h] = -1;
-                        if (step + gridDim.x < n_steps && i_next < n && __float_as_int(m_next[h].w) == cur) {
-                            const FrameInst& fr = fis[e_next[h].x];
-                            float f[32];
-                            mlp_features(ma, fr.cam_local[0], fr.cam_local[1], fr.cam_local[2], fr.dist_scale,
-                                         m_next[h], f);
-#pragma unroll
-                            for (int k = 0; k < 32; k++) f[k] *= kInScale;
-                            qnext[h][0] = pack16(f);
-                            qnext[h][1] = pack16(f + 16);
-                            qnext_asset[h] = cur;
-                        }
-                    }
-                }
-                const bool done = mbar_wait(mbar, phase);
-                if (__syncthreads_or(!done)) { ok = false; break; }
-                phase ^= 1u;
-                tc_fence_after();
-                if (layer < 2) {
-#pragma unroll
-                    for (int h = 0; h < kHalves; h++)
-                        epilogue_hidden(t_lane + 64 * h, sVec[257 + layer], sVec + 64 * layer, sm + kOffH + h * kHBytes,
-                                        tid);
+    for (uint32_t step = s_begin; step < s_end && !abort; step++) {
+        const uint32_t i = step * kRows + tid;
+        const bool valid = i < n;
+        const uint32_t nstep = step + 1;
+        const uint32_t i_next = nstep * kRows + tid;
+        const bool has_next = nstep < s_end;
+        const bool next_valid = has_next && i_next < n;
+        if (next_valid) prefetch_row(s_e, s_m, &list[i_next], &list_mean[i_next]);
+        prefetch_commit();
+        const int my_asset = my_asset_next;
+        bool gated_next = false;
+        {
+            const int amin = __reduce_min_sync(0xffffffffu, my_asset);
+            const int amax = __reduce_max_sync(0xffffffffu, valid ? my_asset : INT_MIN);
+            if (lane == 0) { s_red[8 * buf + warp] = amin; s_red[8 * buf + 4 + warp] = amax; }
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        const int* sr = s_red + 8 * buf;
+        const int step_min = min(min(sr[0], sr[1]), min(sr[2], sr[3]));
+        const int step_max = max(max(sr[4], sr[5]), max(sr[6], sr[7]));
+        bool pending = valid, keep = false, built_next = false;
+        float logit = 0.0f;
+        const uint32_t a_in = tmem + kColIn + 8u * buf;
+        int cur = step_min;
+        while (cur != INT_MAX) {
+            const bool mine = pending && my_asset == cur;
+            if (cur != known) { has_mlp = assets[cur].w_f8 != nullptr; known = cur; }
+            if (!has_mlp) {   // asset without an MLP: rendered unculled
+                if (mine) { keep = true; logit = __int_as_float(0x7f800000); }
+            } else {
+                if (cur != loaded) {   // every MMA of earlier passes has completed (waited on)
+                    const uint4* src = reinterpret_cast<const uint4*>(assets[cur].w_f8);
+                    uint4* dst = reinterpret_cast<uint4*>(sm);
+                    for (int k = tid; k < kBlobBytes / 16; k += kThreads) dst[k] = __ldg(&src[k]);
                     fence_async_smem();
-                    tc_fence_before();
                     __syncthreads();
-                } else {
+                    loaded = cur;
+                }
+                bool ok = true;
+#pragma unroll 1
+                for (int layer = 0; layer < 3; layer++) {
+                    if (tid == 0) {
+                        tc_fence_after();
+                        if (layer == 0) {
+                            mma_f8_ts(tmem + kColD, a_in, dW1, 0);
+                        } else {
+                            const uint64_t dW = layer == 1 ? dW2 : dW3;
 #pragma unroll
-                    for (int h = 0; h < kHalves; h++) {
-                        const float lg = epilogue_logit(t_lane + 64 * h, sVec[259], sVec + 128, sVec + 192, sVec[256]);
-                        if (mine[h]) {
-                            logit[h] = lg;
-                            keep[h] = gated[h] || (lg > threshold);
-                            pending[h] = false;
+                            for (int k = 0; k < 2; k++)   // K = 64 in two K = 32 steps
+                                mma_f8_ts(tmem + kColD, tmem + kColH + 8u * k, dW + 16u * k, k > 0);
                         }
+                        mma_commit(mbar);
+                    }
+                    if (layer == 0 && !built_next) {   // overlaps the first layer's round trip
+                        if (has_next)
+                            gated_next = build_next(t_lane + kColIn + 8u * (buf ^ 1u), next_valid, s_e, s_m, fis,
+                                                    assets, my_asset_next);
+                        built_next = true;
+                    }
+                    ok = mbar_wait(mbar, phase);
+                    phase ^= 1u;
+                    tc_fence_after();
+                    if (layer < 2) {
+                        if (ok) epilogue_hidden(t_lane, sVec[257 + layer], sVec + 64 * layer);
+                        tmem_wait_st();
+                    } else if (ok) {
+                        const float lg = epilogue_logit(t_lane, sVec[259], sVec + 128, sVec + 192, sVec[256]);
+                        if (mine) { logit = lg; keep = gated || (lg > threshold); }
                     }
                     tc_fence_before();
+                    if (__syncthreads_or(!ok)) { abort = true; break; }
                 }
+                if (abort) break;
             }
-            if (!ok) {
-                if (tid == 0) atomicExch(err_flag, 1u);
-                abort = true;
-                break;
+            if (mine) pending = false;
+            if (step_min == step_max) break;
+            {
+                const int cand = __reduce_min_sync(0xffffffffu, pending ? my_asset : INT_MAX);
+                if (lane == 0) s_red[16 + warp] = cand;
             }
+            __syncthreads();
+            cur = min(min(s_red[16], s_red[17]), min(s_red[18], s_red[19]));
+            __syncthreads();
         }
         if (abort) break;
-#pragma unroll
-        for (int h = 0; h < kHalves; h++) {
-            const uint32_t row0 = step * kRows + h * 128;
-            const uint32_t w = __ballot_sync(0xffffffffu, keep[h]);
-            if (lane == 0 && row0 + warp * 32 < n) keep_bits[(row0 >> 5) + warp] = w;
-            if (logits_out && row0 + tid < n) logits_out[row0 + tid] = logit[h];
-        }
+        if (!built_next && has_next)
+            gated_next = build_next(t_lane + kColIn + 8u * (buf ^ 1u), next_valid, s_e, s_m, fis, assets,
+                                    my_asset_next);
+        if (!has_next) my_asset_next = INT_MAX;
+        const uint32_t row0 = step * kRows;
+        const uint32_t w = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0 && row0 + warp * 32 < n) keep_bits[(row0 >> 5) + warp] = w;
+        if (logits_out && valid) logits_out[i] = logit;
+        gated = gated_next;
+        buf ^= 1u;
     }
+    if (abort) {
+        if (tid == 0) atomicExch(err_flag, 1u);
+        mbar_wait(mbar, phase ^ 1u);   // the layer whose wait gave up may still run (bounded)
+    }
+    tmem_wait_st();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
