@@ -119,7 +119,9 @@ typedef struct {
                                     ellipse is smaller than this many px^2, i.e. whose
                                     pi sqrt(det Sigma_2D) (dilation included) is below it, is not
                                     binned.  0 (default): off.  >= 0 */
-    int32_t reserved[4];
+    int32_t sort_digit_bits;     /* digit width of the S5 radix sorts, 4..8 bits (0: default 8) --
+                                    a tuning knob, results do not depend on it */
+    int32_t reserved[3];
 } nvgs_render_flags;
 
 #define NVGS_NUM_STAGES 8
@@ -333,9 +335,42 @@ nvgs_status nvgs_render_batch(nvgs_ctx* ctx, const nvgs_camera* cams, int n_view
                               float* const* images, const nvgs_render_flags* flags,
                               const nvgs_batch_opts* opts, nvgs_frame_stats* stats);
 
+/* Batches of views that each render their own subset of the context's instances (Sec. 3.3 per
+ * view; the paper renders one view per frame).  All views of the batch run as one flattened
+ * frame: every (view, instance) pair is a frame instance with that view's transforms, the
+ * in-frustum and survivor lists hold the Gaussians of every view, tile ids are global (each view's
+ * tiles follow the previous view's), and every stage -- frustum, MLP, compaction, projection, both
+ * sorts, duplication, compositing -- is ONE launch for the whole batch.  Nothing waits for the GPU,
+ * so the batch can be captured into a CUDA graph (opts.use_graph, as for nvgs_render_batch: the
+ * first call renders and captures, later calls with the same views, instance sets, flags, options
+ * and images replay it with the new cameras).
+ *   cams    : n_views HOST cameras (1..4096), any sizes; the tile size is flags.tile_size for all
+ *   sets    : nullable HOST array of n_views instance sets; a NULL array or a set whose `instances`
+ *             is NULL renders every instance of the context in that view
+ *   images  : n_views DEVICE pointers to H x W x 3 float32 (each the size of its camera)
+ *   flags   : as for nvgs_render_batch, and no injected logits; with blend_split_len = 0 the split
+ *             length follows the automatic rule over the whole batch's pairs and tiles
+ *   opts    : nullable; max_pairs is the pair capacity of the whole batch (0: 8 x its instanced
+ *             Gaussians)
+ *   stats   : NULL (no wait) or ONE record with the batch's totals; then the call waits and returns
+ *             NVGS_ERR_CAPACITY (pairs beyond max_pairs: images incomplete) or NVGS_ERR_TIMEOUT (a
+ *             bounded tensor-core wait gave up).
+ * Each view's image equals nvgs_render of that view with the same instances, up to FP32 rounding of
+ * the dense-tile split (bit for bit with blend_split_len < 0).  At most 2^31 instanced Gaussians
+ * per batch (NVGS_ERR_CAPACITY). */
+typedef struct {
+    const int32_t* instances;    /* HOST: indices into the context's instances (nvgs_set_instances) */
+    int32_t count;               /* number of indices */
+    int32_t pad_;
+} nvgs_view_instances;
+nvgs_status nvgs_render_views(nvgs_ctx* ctx, const nvgs_camera* cams, const nvgs_view_instances* sets,
+                              int n_views, float* const* images, const nvgs_render_flags* flags,
+                              const nvgs_batch_opts* opts, nvgs_frame_stats* stats);
+
 /* Autotuner: times nvgs_render_batch of the given views under every candidate configuration --
  * tile size {8, 16, 32} x tensor-core MLP CTAs per SM {1, 2, 3, 4} (when flags.use_mlp and every
- * MLP is BF16) x dense-tile split {automatic, never} -- and returns the fastest flags (all other
+ * MLP is BF16) x dense-tile split {automatic, never} x radix digit width {8, 6, 4} bits -- and
+ * returns the fastest flags (all other
  * fields copied from `flags`).  Images do not depend on these choices.  Each candidate runs one
  * untimed batch and three timed ones (CUDA events on the context's stream); the call waits.
  * results (nullable, up to max_results entries) receives every candidate with its time per
@@ -344,6 +379,7 @@ nvgs_status nvgs_render_batch(nvgs_ctx* ctx, const nvgs_camera* cams, int n_view
 typedef struct {
     int32_t tile_size, mlp_ctas_per_sm, blend_split_len;
     float ms_per_view;
+    int32_t sort_digit_bits, pad_;
 } nvgs_tune_result;
 nvgs_status nvgs_autotune(nvgs_ctx* ctx, const nvgs_camera* cams, int n_views, float* const* images,
                           const nvgs_render_flags* flags, const nvgs_batch_opts* opts,

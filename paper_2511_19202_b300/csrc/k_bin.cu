@@ -50,6 +50,9 @@ __device__ __forceinline__ int warp_owner(uint32_t pre, uint32_t c) {
     return j;
 }
 
+// kMV (multi-view batches): the rect's w carries the survivor's view in its high 16 bits, and the
+// pair key is that view's tile_base plus its local tile id.
+template <bool kMV>
 __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ order,
                                                    const int4* __restrict__ rects,
                                                    const float4* __restrict__ rec,
@@ -72,10 +75,17 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
         uint32_t i = 0, rows = 0;
         int4 r = make_int4(0, 0, -1, -1);
         float u = 0.f, v = 0.f, A = 0.f, B = 0.f, C = 0.f, det = 0.f, kk = 0.f;
+        int tiles_x = cam.tiles_x, tile_base = 0;
         bool test = false;
         if (k < n) {
             i = order[k];
             r = rects[i];
+            if (kMV) {
+                const CamParams& cv = camp[r.w >> 16];
+                tiles_x = cv.tiles_x;
+                tile_base = cv.tile_base;
+                r.w &= 0xffff;
+            }
             if (r.x <= r.z && r.y <= r.w) {
                 rows = (uint32_t)(r.w - r.y + 1);
                 test = (r.z - r.x + 1) * (int)rows > 1;
@@ -102,9 +112,14 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
             const float Cj = __shfl_sync(0xffffffffu, C, j), dj = __shfl_sync(0xffffffffu, det, j);
             const float kj = __shfl_sync(0xffffffffu, kk, j);
             const bool tj = __shfl_sync(0xffffffffu, (int)test, j) != 0;
+            // the unit's view: its first global tile and tiles per row (every lane shuffles)
+            const int tbj = kMV ? __shfl_sync(0xffffffffu, tile_base, j) : 0;
+            const int txj = kMV ? __shfl_sync(0xffffffffu, tiles_x, j) : cam.tiles_x;
             int ty = 0, t0 = 1, t1 = 0;
+            int row0 = 0;   // global id of the first tile of the unit's tile row
             if (c < n_units) {
                 ty = ry + (int)(c - pj);
+                row0 = tbj + ty * txj;
                 if (tj) {
                     row_tile_span(splat_ellipse(uj, vj, Aj, Bj, Cj, dj, kj), ty, cam.tile_size, t0, t1);
                     t0 = max(t0, rx);
@@ -122,11 +137,11 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
                 const uint32_t p = p0 + lane;
                 const int q = warp_owner(cnt_pre, p);
                 const uint32_t pq = __shfl_sync(0xffffffffu, cnt_pre, q);
-                const int tq0 = __shfl_sync(0xffffffffu, t0, q), tyq = __shfl_sync(0xffffffffu, ty, q);
+                const int tq0 = __shfl_sync(0xffffffffu, t0, q), rq = __shfl_sync(0xffffffffu, row0, q);
                 const uint32_t iq = __shfl_sync(0xffffffffu, ij, q);
                 const uint32_t pos = out + p;
                 if (p < batch && pos < limit) {
-                    keys[pos] = (uint32_t)(tyq * cam.tiles_x + tq0 + (int)(p - pq));
+                    keys[pos] = (uint32_t)(rq + tq0 + (int)(p - pq));
                     values[pos] = iq;
                 }
             }
@@ -139,7 +154,7 @@ cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const flo
                              const uint32_t* offsets, uint32_t n, const uint32_t* n_dev,
                              const CamParams* cam_dev, const uint32_t* n_pairs, uint32_t pair_cap,
                              uint32_t* overflow, uint32_t* keys, uint32_t* values, int num_sms,
-                             cudaStream_t s, LaunchLog* log) {
+                             cudaStream_t s, LaunchLog* log, int multi_view) {
     if (n == 0) return cudaSuccess;
     // a grid-stride kernel with equal shares per CTA: exactly the CTAs that are resident at once
     // (a fraction of a second wave would run alone at the end)
@@ -149,14 +164,17 @@ cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const flo
     static std::atomic<int> per_sm_cache[64];   // per device ordinal; 0 = not measured yet
     if (dev >= 0 && dev < 64) per_sm = per_sm_cache[dev].load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_duplicate, 256, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_duplicate<false>, 256, 0);
         if (e != cudaSuccess) return e;
         per_sm = std::max(per_sm, 1);
         if (dev >= 0 && dev < 64) per_sm_cache[dev].store(per_sm, std::memory_order_relaxed);
     }
     const uint32_t warps = (n + 31) / 32;
     const uint32_t grid = std::min<uint32_t>((warps + 7) / 8, (uint32_t)(num_sms * per_sm));
-    NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<<<grid, 256, 0, s>>>(order, rects, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, keys, values));
+    if (multi_view)
+        NVGS_LAUNCH(log, s, "k_duplicate_views", k_duplicate<true><<<grid, 256, 0, s>>>(order, rects, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, keys, values));
+    else
+        NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<false><<<grid, 256, 0, s>>>(order, rects, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, keys, values));
     return cudaGetLastError();
 }
 

@@ -37,6 +37,17 @@ struct Frag {
     uint32_t evals = 0;   // (pixel, fragment) evaluations -- the compositing's unit of work
 };
 
+// View of global tile `tile` in a multi-view batch: the last view whose tile_base is <= tile (views
+// are numbered in tile order).  One view: 0.
+__device__ __forceinline__ int tile_view(const CamParams* __restrict__ camp, int n_views, int tile) {
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (camp[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Adds the block's evaluations to *out (profiling only; nullable).
 __device__ __forceinline__ void add_evals(unsigned long long* out, uint32_t evals) {
     if (!out) return;
@@ -124,17 +135,21 @@ __global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS) < 4 ? 1536 / (TS * T
                                                   float4* __restrict__ state_tc,
                                                   int32_t* __restrict__ state_cnt,
                                                   uint32_t* __restrict__ alive,
-                                                  unsigned long long* __restrict__ evals_out) {
-    const CamParams cam = *camp;
+                                                  unsigned long long* __restrict__ evals_out,
+                                                  int n_views, float* const* __restrict__ images) {
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
     __shared__ float4 s_c[B];
     if (split_dev) split_len = *split_dev;   // resolved on the device (sync-free batches)
     const int tile = blockIdx.x;
+    const int view = n_views > 1 ? tile_view(camp, n_views, tile) : 0;
+    const CamParams cam = camp[view];
+    if (images) image = images[view];
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     const bool longer = end - start > split_len;
-    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int lt = tile - cam.tile_base;   // the tile within its view
+    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
     const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
     const bool inside = px < cam.W && py < cam.H;
     Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, !inside};
@@ -204,8 +219,8 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __rest
                                                           const uint32_t* __restrict__ split_dev,
                                                           const float4* __restrict__ state_tc,
                                                           float* __restrict__ Tch,
-                                                          unsigned long long* __restrict__ evals_out) {
-    const CamParams cam = *camp;
+                                                          unsigned long long* __restrict__ evals_out,
+                                                          int n_views) {
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
@@ -218,7 +233,9 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __rest
         const int tile = (int)it.x;
         uint32_t start, end;
         chunk_range(ranges, it, split_len, start, end);
-        const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+        const CamParams cam = camp[n_views > 1 ? tile_view(camp, n_views, tile) : 0];
+        const int lt = tile - cam.tile_base;
+        const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
         const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
         const bool stopped = state_tc[(size_t)tile * B + threadIdx.x].w < 0.0f;
         Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, stopped || !(px < cam.W && py < cam.H)};
@@ -242,8 +259,8 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
                                                           const float* __restrict__ Tch,
                                                           float4* __restrict__ part, int32_t* __restrict__ pcount,
                                                           uint8_t* __restrict__ mark,
-                                                          unsigned long long* __restrict__ evals_out) {
-    const CamParams cam = *camp;
+                                                          unsigned long long* __restrict__ evals_out,
+                                                          int n_views) {
     constexpr int B = TS * TS;
     __shared__ float4 s_a[B];
     __shared__ float4 s_b[B];
@@ -255,7 +272,9 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
         const int tile = (int)it.x;
         uint32_t start, end;
         chunk_range(ranges, it, split_len, start, end);
-        const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+        const CamParams cam = camp[n_views > 1 ? tile_view(camp, n_views, tile) : 0];
+        const int lt = tile - cam.tile_base;
+        const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
         const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
         // transmittance entering this chunk: after k_blend's pairs, times the earlier chunks
         const float sw = state_tc[(size_t)tile * B + threadIdx.x].w;
@@ -281,13 +300,17 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_D(const uint32_t* __rest
                                                           const float4* __restrict__ part,
                                                           const int32_t* __restrict__ pcount,
                                                           float* __restrict__ image, float* __restrict__ final_T,
-                                                          int32_t* __restrict__ n_contrib) {
-    const CamParams cam = *camp;
+                                                          int32_t* __restrict__ n_contrib,
+                                                          int n_views, float* const* __restrict__ images) {
     constexpr int B = TS * TS;
     const int tile = blockIdx.x;
     const uint32_t nc = n_chunks[tile];
     if (nc == 0) return;
-    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int view = n_views > 1 ? tile_view(camp, n_views, tile) : 0;
+    const CamParams cam = camp[view];
+    if (images) image = images[view];
+    const int lt = tile - cam.tile_base;
+    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
     const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
     if (!(px < cam.W && py < cam.H)) return;
     const float4 st = state_tc[(size_t)tile * B + threadIdx.x];
@@ -329,9 +352,9 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
                             const CamParams& cam, const CamParams* cam_dev, float* image, float* final_T,
                             int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
                             const uint32_t* auto_split_pairs, void* scratch, void* scan_scratch,
-                            int num_sms, unsigned long long* evals, cudaStream_t s, LaunchLog* log) {
+                            int num_sms, unsigned long long* evals, cudaStream_t s, LaunchLog* log,
+                            int n_views, float* const* images, int n_tiles) {
     constexpr int B = TS * TS;
-    const int n_tiles = cam.tiles_x * cam.tiles_y;
     const bool may_split = n_pairs > split_len;
     // carve the scratch; every section starts on a 256-byte boundary
     char* p = static_cast<char*>(scratch);
@@ -370,7 +393,7 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
     }
     NVGS_LAUNCH(log, s, TS == 8 ? "k_blend<8>" : TS == 16 ? "k_blend<16>" : "k_blend<32>",
                 (evals ? k_blend<TS, true> : k_blend<TS, false>)<<<n_tiles, B, 0, s>>>(ranges, values, rec, cam_dev, image, final_T, n_contrib, mark,
-                                                  split_len, split_dev, state_tc, state_cnt, alive, evals));
+                                                  split_len, split_dev, state_tc, state_cnt, alive, evals, n_views, images));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !may_split) return e;
     NVGS_LAUNCH(log, s, "k_split_count", k_split_count<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, alive, n_tiles, split_len, split_dev, n_chunks));
@@ -379,9 +402,9 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
     NVGS_LAUNCH(log, s, "k_split_fill", k_split_fill<<<(n_tiles + 255) / 256, 256, 0, s>>>(n_chunks, first, n_tiles, items));
     // persistent grids: enough CTAs to fill the GPU (the item count lives on the device)
     const unsigned pgrid = (unsigned)std::min<uint64_t>(max_items, (uint64_t)num_sms * (2048 / B));
-    NVGS_LAUNCH(log, s, "k_blend_split_T", (evals ? k_blend_split_T<TS, true> : k_blend_split_T<TS, false>)<<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, split_dev, state_tc, Tch, evals));
-    NVGS_LAUNCH(log, s, "k_blend_split_C", (evals ? k_blend_split_C<TS, true> : k_blend_split_C<TS, false>)<<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, split_dev, state_tc, Tch, part, pcount, mark, evals));
-    NVGS_LAUNCH(log, s, "k_blend_split_D", k_blend_split_D<TS><<<n_tiles, B, 0, s>>>(n_chunks, first, cam_dev, state_tc, state_cnt, part, pcount, image, final_T, n_contrib));
+    NVGS_LAUNCH(log, s, "k_blend_split_T", (evals ? k_blend_split_T<TS, true> : k_blend_split_T<TS, false>)<<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, split_dev, state_tc, Tch, evals, n_views));
+    NVGS_LAUNCH(log, s, "k_blend_split_C", (evals ? k_blend_split_C<TS, true> : k_blend_split_C<TS, false>)<<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, split_dev, state_tc, Tch, part, pcount, mark, evals, n_views));
+    NVGS_LAUNCH(log, s, "k_blend_split_D", k_blend_split_D<TS><<<n_tiles, B, 0, s>>>(n_chunks, first, cam_dev, state_tc, state_cnt, part, pcount, image, final_T, n_contrib, n_views, images));
     return cudaGetLastError();
 }
 
@@ -389,13 +412,14 @@ cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const f
                          const CamParams& cam, const CamParams* cam_dev, float* image, float* final_T,
                          int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
                          const uint32_t* auto_split_pairs, void* scratch, void* scan_scratch,
-                         int num_sms, unsigned long long* evals, cudaStream_t s, LaunchLog* log) {
-    const int n_tiles = cam.tiles_x * cam.tiles_y;
+                         int num_sms, unsigned long long* evals, cudaStream_t s, LaunchLog* log,
+                         int n_views, float* const* images, int n_tiles_total) {
+    const int n_tiles = n_tiles_total > 0 ? n_tiles_total : cam.tiles_x * cam.tiles_y;
     if (n_tiles <= 0) return cudaSuccess;
     switch (cam.tile_size) {
-        case 8: return blend_ts<8>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log);
-        case 16: return blend_ts<16>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log);
-        case 32: return blend_ts<32>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log);
+        case 8: return blend_ts<8>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log, n_views, images, n_tiles);
+        case 16: return blend_ts<16>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log, n_views, images, n_tiles);
+        case 32: return blend_ts<32>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log, n_views, images, n_tiles);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -16,11 +16,13 @@ namespace nvgs {
 // FP32 so that the per-Gaussian camera-space position is three FMAs per coordinate.
 __global__ void k_instance_setup(const InstanceRaw* __restrict__ inst, int n_inst,
                                  const AssetDev* __restrict__ assets, const CamParams* __restrict__ camp,
-                                 FrameInst* __restrict__ out) {
-    const CamParams cam = *camp;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_inst) return;
-    InstanceRaw r = inst[i];
+                                 FrameInst* __restrict__ out, const int2* __restrict__ fi_map) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_inst) return;
+    // frame instance k: (view, instance) of a multi-view batch, or instance k of view 0
+    const int2 vi = fi_map ? fi_map[k] : make_int2(0, k);
+    const CamParams cam = camp[vi.x];
+    InstanceRaw r = inst[vi.y];
     const AssetDev& a = assets[r.asset];
     double Rc[9], Ri[9], W[9];
     for (int k = 0; k < 9; k++) { Rc[k] = cam.R[k]; Ri[k] = r.R[k]; }
@@ -67,13 +69,16 @@ __global__ void k_instance_setup(const InstanceRaw* __restrict__ inst, int n_ins
     f.gated = cam.mlp_gate && (sqrt(dd) * dist_scale) < (double)a.d_min;
     // assets without an MLP are rendered unculled (Fig. 4: mixed neural / plain assets)
     f.no_mlp = a.w_fp32 == nullptr;
-    out[i] = f;
+    f.view = vi.x;
+    out[k] = f;
 }
 
 cudaError_t launch_instance_setup(const InstanceRaw* inst, int n_inst, const AssetDev* assets,
-                                  const CamParams* cam_dev, FrameInst* out, cudaStream_t s, LaunchLog* log) {
-    if (n_inst <= 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_instance_setup", k_instance_setup<<<(n_inst + 127) / 128, 128, 0, s>>>(inst, n_inst, assets, cam_dev, out));
+                                  const CamParams* cam_dev, FrameInst* out, cudaStream_t s, LaunchLog* log,
+                                  const int2* fi_map, int n_fi) {
+    const int n = fi_map ? n_fi : n_inst;
+    if (n <= 0) return cudaSuccess;
+    NVGS_LAUNCH(log, s, "k_instance_setup", k_instance_setup<<<(n + 127) / 128, 128, 0, s>>>(inst, n, assets, cam_dev, out, fi_map));
     return cudaGetLastError();
 }
 
@@ -88,13 +93,13 @@ __global__ void __launch_bounds__(256) k_frustum(const Chunk* __restrict__ chunk
                                                  const AssetDev* __restrict__ assets, const CamParams* __restrict__ camp,
                                                  uint32_t* __restrict__ bits,
                                                  uint32_t* __restrict__ chunk_counts) {
-    const CamParams cam = *camp;
     __shared__ uint32_t warp_tot[8];
     const int c = blockIdx.x;
     const Chunk ch = chunks[c];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t* out = bits + (size_t)c * kChunkWords;
     const FrameInst& f = fi[ch.inst];
+    const CamParams cam = camp[f.view];
     uint32_t tot = 0;
     if (!f.visible) {
         if (threadIdx.x < kChunkWords) out[threadIdx.x] = 0u;

@@ -17,6 +17,9 @@
 
 namespace nvgs {
 
+// kMV (multi-view batches): each survivor takes its view's camera, and the rect's w carries the
+// view in its high 16 bits (tile rows stay below 2^16).
+template <bool kMV>
 __global__ void __launch_bounds__(256, 4) k_project(const uint2* __restrict__ surv, uint32_t n,
                                                  const uint32_t* __restrict__ n_dev,
                                                  const FrameInst* __restrict__ fis,
@@ -25,11 +28,12 @@ __global__ void __launch_bounds__(256, 4) k_project(const uint2* __restrict__ su
                                                  uint32_t* __restrict__ counts,
                                                  uint32_t* __restrict__ dkey,
                                                  uint32_t* __restrict__ didx) {
-    const CamParams cam = *camp;
+    const CamParams cam0 = *camp;
     if (n_dev) n = min(n, *n_dev);   // device-side count (n is then the capacity)
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint2 e = surv[i];
         const FrameInst& fi = fis[e.x];
+        const CamParams cam = kMV ? camp[fi.view] : cam0;
         const AssetDev& a = assets[fi.asset];
         const uint32_t g = e.y;
         const float4 m = __ldg(&a.mean_op[g]);
@@ -106,6 +110,7 @@ __global__ void __launch_bounds__(256, 4) k_project(const uint2* __restrict__ su
                 }
             }
         }
+        if (kMV) r.w |= fi.view << 16;
         rects[i] = r;
         counts[i] = cnt;
         dkey[i] = __float_as_uint(z);   // z > z_near > 0: the bit pattern orders like the value
@@ -145,11 +150,14 @@ __global__ void __launch_bounds__(256, 4) k_project(const uint2* __restrict__ su
 cudaError_t launch_project(const uint2* surv, uint32_t n, const uint32_t* n_dev, const FrameInst* fi,
                            const AssetDev* assets, const CamParams* cam_dev, float4* rec, int4* rects,
                            uint32_t* tile_counts, uint32_t* dkey, uint32_t* didx, int num_sms,
-                           cudaStream_t s, LaunchLog* log) {
+                           cudaStream_t s, LaunchLog* log, int multi_view) {
     if (n == 0) return cudaSuccess;
     // grid-stride over two waves of the four resident CTAs per SM
     const uint32_t grid = std::min<uint32_t>((n + 255) / 256, (uint32_t)num_sms * 4 * 2);
-    NVGS_LAUNCH(log, s, "k_project", k_project<<<grid, 256, 0, s>>>(surv, n, n_dev, fi, assets, cam_dev, rec, rects, tile_counts, dkey, didx));
+    if (multi_view)
+        NVGS_LAUNCH(log, s, "k_project_views", k_project<true><<<grid, 256, 0, s>>>(surv, n, n_dev, fi, assets, cam_dev, rec, rects, tile_counts, dkey, didx));
+    else
+        NVGS_LAUNCH(log, s, "k_project", k_project<false><<<grid, 256, 0, s>>>(surv, n, n_dev, fi, assets, cam_dev, rec, rects, tile_counts, dkey, didx));
     return cudaGetLastError();
 }
 

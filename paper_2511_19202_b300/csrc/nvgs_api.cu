@@ -82,6 +82,11 @@ struct nvgs_ctx {
     DevBuf view_stats;
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<uint8_t> graph_key;
+    // multi-view batches with per-view instance sets: (view, instance) map, chunk list, image
+    // pointers, and their cached graph
+    DevBuf mv_fimap, mv_chunks, mv_images;
+    cudaGraphExec_t mv_graph_exec = nullptr;
+    std::vector<uint8_t> mv_graph_key;
     LaunchLog log;
     // per-kernel device time accumulated over profiled frames
     std::vector<std::string> kname;
@@ -162,6 +167,8 @@ nvgs_status validate_flags(nvgs_ctx* ctx, const nvgs_render_flags* f) {
         return fail(ctx, NVGS_ERR_INVALID_ARG, "mlp_ctas_per_sm must be 0..4");
     if (!(f->radius_clip_area >= 0.0f) || !std::isfinite(f->radius_clip_area))
         return fail(ctx, NVGS_ERR_INVALID_ARG, "radius_clip_area must be a finite value >= 0");
+    if (f->sort_digit_bits != 0 && (f->sort_digit_bits < 4 || f->sort_digit_bits > 8))
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "sort_digit_bits must be 0 or 4..8");
     if (f->profile < 0 || f->profile > 2)
         return fail(ctx, NVGS_ERR_INVALID_ARG, "profile must be 0, 1 or 2");
     if (f->blend_split_len > 0 && f->blend_split_len < 256)
@@ -256,31 +263,44 @@ bool uses_tc_mlp(const nvgs_ctx* ctx, const nvgs_render_flags* f) { return tc_ml
 // device-count mode (`async`) nothing waits: every later kernel reads the count from the counters
 // and the instanced-Gaussian count is the capacity (the MLP's timeout flag is read at the end of
 // the batch).
+// The frame instances a cull covers: the context's instances under one camera, or (multi-view
+// batches) the (view, instance) pairs of fi_map with their chunk list.
+struct CullScope {
+    const Chunk* chunks;
+    int n_chunks;
+    int n_fi;
+    const int2* fi_map;   // nullable
+    uint64_t cap;         // instanced Gaussians over the frame instances
+};
+
 nvgs_status run_cull(nvgs_ctx* ctx, const CamParams* cam_dev, const nvgs_render_flags* f,
                      StageTimer& tm, uint32_t* n_vis_out, uint32_t* n_mlp_out, bool want_logits,
-                     bool compact, bool async = false) {
+                     bool compact, bool async = false, const CullScope* scope = nullptr) {
     cudaStream_t s = ctx->stream;
+    const CullScope sc = scope ? *scope
+                               : CullScope{P<Chunk>(ctx->chunks), ctx->n_chunks, (int)ctx->instances.size(),
+                                           nullptr, (uint64_t)ctx->n_instanced};
     const int n_inst = (int)ctx->instances.size();
     tm.mark(NVGS_STAGE_SETUP);
-    CK(ensure(ctx->frame_inst, n_inst * sizeof(FrameInst)));
+    CK(ensure(ctx->frame_inst, (size_t)sc.n_fi * sizeof(FrameInst)));
     CK(launch_instance_setup(P<InstanceRaw>(ctx->inst_raw), n_inst, P<AssetDev>(ctx->assets_dev), cam_dev,
-                             P<FrameInst>(ctx->frame_inst), s, &ctx->log));
+                             P<FrameInst>(ctx->frame_inst), s, &ctx->log, sc.fi_map, sc.n_fi));
     tm.mark(NVGS_STAGE_CULL);
-    const uint64_t cap = (uint64_t)ctx->n_instanced;
-    CK(ensure(ctx->bits, (size_t)ctx->n_chunks * kChunkWords * 4));
-    CK(ensure(ctx->chunk_counts, (size_t)ctx->n_chunks * 4));
-    CK(ensure(ctx->chunk_offsets, (size_t)ctx->n_chunks * 4));
+    const uint64_t cap = sc.cap;
+    CK(ensure(ctx->bits, (size_t)sc.n_chunks * kChunkWords * 4));
+    CK(ensure(ctx->chunk_counts, (size_t)sc.n_chunks * 4));
+    CK(ensure(ctx->chunk_offsets, (size_t)sc.n_chunks * 4));
     CK(ensure(ctx->vis_list, cap * sizeof(uint2)));
-    CK(ensure(ctx->scratch, std::max(scan_scratch_bytes(ctx->n_chunks), scan_scratch_bytes(cap / kChunk + 1))));
-    CK(launch_frustum(P<Chunk>(ctx->chunks), ctx->n_chunks, P<FrameInst>(ctx->frame_inst),
+    CK(ensure(ctx->scratch, std::max(scan_scratch_bytes(sc.n_chunks), scan_scratch_bytes(cap / kChunk + 1))));
+    CK(launch_frustum(sc.chunks, sc.n_chunks, P<FrameInst>(ctx->frame_inst),
                       P<AssetDev>(ctx->assets_dev), cam_dev, P<uint32_t>(ctx->bits),
                       P<uint32_t>(ctx->chunk_counts), s, &ctx->log));
     uint32_t* counters = P<uint32_t>(ctx->counters);
-    CK(exclusive_scan_u32(P<uint32_t>(ctx->chunk_counts), P<uint32_t>(ctx->chunk_offsets), ctx->n_chunks,
+    CK(exclusive_scan_u32(P<uint32_t>(ctx->chunk_counts), P<uint32_t>(ctx->chunk_offsets), sc.n_chunks,
                           &counters[0], ctx->scratch.p, s, &ctx->log));
     const bool tc_mlp = f->use_mlp && uses_tc_mlp(ctx, f);
     if (tc_mlp) CK(ensure(ctx->vis_mean, cap * 16 + 16));
-    CK(launch_expand_chunks(P<Chunk>(ctx->chunks), ctx->n_chunks, P<uint32_t>(ctx->bits),
+    CK(launch_expand_chunks(sc.chunks, sc.n_chunks, P<uint32_t>(ctx->bits),
                             P<uint32_t>(ctx->chunk_offsets), P<uint2>(ctx->vis_list),
                             P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev),
                             tc_mlp ? P<float4>(ctx->vis_mean) : nullptr, s, &ctx->log));
@@ -482,12 +502,14 @@ extern "C" nvgs_status nvgs_destroy(nvgs_ctx* ctx) {
                       &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
                       &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial,
                       &ctx->dkey, &ctx->didx, &ctx->dkey_alt, &ctx->didx_alt, &ctx->split_scratch,
-                      &ctx->vis_mean, &ctx->grad_surv, &ctx->cam_dev, &ctx->view_stats};
+                      &ctx->vis_mean, &ctx->grad_surv, &ctx->cam_dev, &ctx->view_stats,
+                      &ctx->mv_fimap, &ctx->mv_chunks, &ctx->mv_images};
     for (auto& t : ctx->train) { release(t.w); release(t.m); release(t.v); release(t.views); }
     for (DevBuf* b : bufs) release(*b);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     if (ctx->h_cam) cudaFreeHost(ctx->h_cam);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->mv_graph_exec) cudaGraphExecDestroy(ctx->mv_graph_exec);
     if (ctx->cam_ev) cudaEventDestroy(ctx->cam_ev);
     if (ctx->events_ready)
         for (auto& ev : ctx->ev) cudaEventDestroy(ev);
@@ -765,7 +787,7 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     int dpasses = 0, d_alt = 0;
     CK(radix_sort_pairs_u32(P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), P<uint32_t>(ctx->dkey_alt),
                             P<uint32_t>(ctx->didx_alt), n_surv, 32, ctx->scratch.p, s, &ctx->log,
-                            &dpasses, 0, &d_alt));
+                            &dpasses, 0, &d_alt, nullptr, f->sort_digit_bits ? f->sort_digit_bits : 8));
     const uint32_t* order = d_alt ? P<uint32_t>(ctx->didx_alt) : P<uint32_t>(ctx->didx);
     if (n_surv <= 1) order = P<uint32_t>(ctx->didx);
     CK(launch_gather_counts(order, P<uint32_t>(ctx->tile_counts), n_surv, nullptr, P<uint32_t>(ctx->tile_offsets),
@@ -790,7 +812,7 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     int passes = 0, in_alt = 0;
     CK(radix_sort_pairs_u32(P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), P<uint32_t>(ctx->keys_alt),
                             P<uint32_t>(ctx->vals_alt), n_pairs, tile_bits, ctx->scratch.p, s, &ctx->log,
-                            &passes, 0, &in_alt));
+                            &passes, 0, &in_alt, nullptr, f->sort_digit_bits ? f->sort_digit_bits : 8));
     uint32_t* skeys = in_alt ? P<uint32_t>(ctx->keys_alt) : P<uint32_t>(ctx->keys);
     uint32_t* svals = in_alt ? P<uint32_t>(ctx->vals_alt) : P<uint32_t>(ctx->vals);
     CK(launch_tile_ranges(skeys, n_pairs, nullptr, (uint32_t)n_tiles, P<uint32_t>(ctx->ranges), s, &ctx->log));
@@ -1229,7 +1251,7 @@ static nvgs_status enqueue_view_async(nvgs_ctx* ctx, const CamParams& cp, const 
     int dpasses = 0, d_alt = 0;
     CK(radix_sort_pairs_u32(P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), P<uint32_t>(ctx->dkey_alt),
                             P<uint32_t>(ctx->didx_alt), cap, 32, ctx->scratch.p, s, &ctx->log, &dpasses, 0,
-                            &d_alt, n_surv_dev));
+                            &d_alt, n_surv_dev, f->sort_digit_bits ? f->sort_digit_bits : 8));
     const uint32_t* order = d_alt ? P<uint32_t>(ctx->didx_alt) : P<uint32_t>(ctx->didx);
     CK(launch_gather_counts(order, P<uint32_t>(ctx->tile_counts), (uint32_t)cap, n_surv_dev,
                             P<uint32_t>(ctx->tile_offsets), ctx->num_sms, s, &ctx->log));
@@ -1248,7 +1270,7 @@ static nvgs_status enqueue_view_async(nvgs_ctx* ctx, const CamParams& cp, const 
     int passes = 0, in_alt = 0;
     CK(radix_sort_pairs_u32(P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), P<uint32_t>(ctx->keys_alt),
                             P<uint32_t>(ctx->vals_alt), pair_cap, tile_bits, ctx->scratch.p, s, &ctx->log,
-                            &passes, 0, &in_alt, counters + 2));
+                            &passes, 0, &in_alt, counters + 2, f->sort_digit_bits ? f->sort_digit_bits : 8));
     uint32_t* skeys = in_alt ? P<uint32_t>(ctx->keys_alt) : P<uint32_t>(ctx->keys);
     uint32_t* svals = in_alt ? P<uint32_t>(ctx->vals_alt) : P<uint32_t>(ctx->vals);
     CK(launch_tile_ranges(skeys, (uint32_t)pair_cap, counters + 2, (uint32_t)n_tiles, P<uint32_t>(ctx->ranges),
@@ -1375,6 +1397,212 @@ extern "C" nvgs_status nvgs_render_batch(nvgs_ctx* ctx, const nvgs_camera* cams,
     return NVGS_OK;
 }
 
+// ============================================================================ N3: views with own instance sets
+// All views of the batch as one flattened frame: frame instance k = (view, instance) with the
+// view's camera, the in-frustum and survivor lists of every view in one list, tile ids made global
+// by each view's tile_base (the depth sort of all survivors and the tile sort of all pairs then
+// give every tile its pairs front to back), and one launch per stage for the whole batch; nothing
+// waits for the GPU, so the batch can be captured into a CUDA graph.
+static nvgs_status enqueue_views(nvgs_ctx* ctx, const CullScope& scope, const CamParams& cp0, int n_views,
+                                 int n_tiles, const nvgs_render_flags* f, uint64_t pair_cap, int digit_bits) {
+    cudaStream_t s = ctx->stream;
+    const CamParams* cam_dev = P<CamParams>(ctx->cam_dev);
+    uint32_t* counters = P<uint32_t>(ctx->counters);
+    CK(cudaMemsetAsync(&counters[8], 0, 8, s));   // MLP timeout flag, pair overflow flag
+    StageTimer tm{ctx, false};
+    uint32_t n_vis = 0, n_mlp = 0;
+    nvgs_status st = run_cull(ctx, cam_dev, f, tm, &n_vis, &n_mlp, false, true, true, &scope);
+    if (st != NVGS_OK) return st;
+    const uint64_t cap = scope.cap;
+    const uint2* surv = f->use_mlp ? P<uint2>(ctx->surv) : P<uint2>(ctx->vis_list);
+    const uint32_t* n_surv_dev = f->use_mlp ? &counters[1] : &counters[0];
+    // S4
+    CK(ensure(ctx->rec, cap * 48 + 48));
+    CK(ensure(ctx->rects, cap * 16 + 16));
+    CK(ensure(ctx->tile_counts, cap * 4 + 16));
+    CK(ensure(ctx->tile_offsets, cap * 4 + 16));
+    CK(ensure(ctx->dkey, cap * 4 + 16));
+    CK(ensure(ctx->didx, cap * 4 + 16));
+    CK(ensure(ctx->dkey_alt, cap * 4 + 16));
+    CK(ensure(ctx->didx_alt, cap * 4 + 16));
+    CK(ensure(ctx->scratch, std::max({scan_scratch_bytes(scope.n_chunks), scan_scratch_bytes(cap + 1),
+                                      radix_scratch_bytes(cap), radix_scratch_bytes(pair_cap),
+                                      scan_scratch_bytes((uint64_t)n_tiles)})));
+    CK(launch_project(surv, (uint32_t)cap, n_surv_dev, P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev),
+                      cam_dev, P<float4>(ctx->rec), P<int4>(ctx->rects), P<uint32_t>(ctx->tile_counts),
+                      P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), ctx->num_sms, s, &ctx->log, 1));
+    // S5: every survivor of the batch by depth, the pairs in that order with global tile ids, the
+    // pairs by tile id
+    int dpasses = 0, d_alt = 0;
+    CK(radix_sort_pairs_u32(P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), P<uint32_t>(ctx->dkey_alt),
+                            P<uint32_t>(ctx->didx_alt), cap, 32, ctx->scratch.p, s, &ctx->log, &dpasses, 0,
+                            &d_alt, n_surv_dev, digit_bits));
+    const uint32_t* order = d_alt ? P<uint32_t>(ctx->didx_alt) : P<uint32_t>(ctx->didx);
+    CK(launch_gather_counts(order, P<uint32_t>(ctx->tile_counts), (uint32_t)cap, n_surv_dev,
+                            P<uint32_t>(ctx->tile_offsets), ctx->num_sms, s, &ctx->log));
+    CK(exclusive_scan_u32(P<uint32_t>(ctx->tile_offsets), P<uint32_t>(ctx->tile_offsets), cap, counters + 2,
+                          ctx->scratch.p, s, &ctx->log, n_surv_dev));
+    const int tile_bits = std::max(1, bit_width((uint64_t)n_tiles - 1));
+    CK(ensure(ctx->keys, (size_t)pair_cap * 4 + 16));
+    CK(ensure(ctx->vals, (size_t)pair_cap * 4 + 16));
+    CK(ensure(ctx->keys_alt, (size_t)pair_cap * 4 + 16));
+    CK(ensure(ctx->vals_alt, (size_t)pair_cap * 4 + 16));
+    CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
+    CK(launch_duplicate(order, P<int4>(ctx->rects), P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
+                        (uint32_t)cap, n_surv_dev, cam_dev, counters + 2, (uint32_t)pair_cap, counters + 9,
+                        P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), ctx->num_sms, s, &ctx->log, 1));
+    int passes = 0, in_alt = 0;
+    CK(radix_sort_pairs_u32(P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), P<uint32_t>(ctx->keys_alt),
+                            P<uint32_t>(ctx->vals_alt), pair_cap, tile_bits, ctx->scratch.p, s, &ctx->log,
+                            &passes, 0, &in_alt, counters + 2, digit_bits));
+    uint32_t* skeys = in_alt ? P<uint32_t>(ctx->keys_alt) : P<uint32_t>(ctx->keys);
+    uint32_t* svals = in_alt ? P<uint32_t>(ctx->vals_alt) : P<uint32_t>(ctx->vals);
+    CK(launch_tile_ranges(skeys, (uint32_t)pair_cap, counters + 2, (uint32_t)n_tiles, P<uint32_t>(ctx->ranges),
+                          s, &ctx->log));
+    // S6 over the tiles of every view; the automatic split length takes the batch's pair count and
+    // tile count (the rule of nvgs_render over the whole batch)
+    const bool auto_split = f->blend_split_len == 0;
+    const uint32_t split_len = f->blend_split_len < 0 ? 0xffffffffu
+                               : (auto_split ? 4096u : (uint32_t)f->blend_split_len);
+    if (pair_cap > split_len)
+        CK(ensure(ctx->split_scratch, blend_split_scratch_bytes(n_tiles, pair_cap, cp0.tile_size, split_len)));
+    CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp0, cam_dev, nullptr, nullptr, nullptr,
+                    nullptr, split_len, pair_cap, auto_split ? counters + 2 : nullptr, ctx->split_scratch.p,
+                    ctx->scratch.p, ctx->num_sms, nullptr, s, &ctx->log, n_views, P<float*>(ctx->mv_images),
+                    n_tiles));
+    // batch counts (in frustum, survivors, pairs) and the flags, for the stats
+    CK(cudaMemcpyAsync(P<uint32_t>(ctx->view_stats), counters, 3 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(P<uint32_t>(ctx->view_stats) + 4, &counters[8], 8, cudaMemcpyDeviceToDevice, s));
+    return NVGS_OK;
+}
+
+extern "C" nvgs_status nvgs_render_views(nvgs_ctx* ctx, const nvgs_camera* cams,
+                                         const nvgs_view_instances* sets, int n_views, float* const* images,
+                                         const nvgs_render_flags* f, const nvgs_batch_opts* opts,
+                                         nvgs_frame_stats* stats) {
+    if (!ctx) return NVGS_ERR_INVALID_ARG;
+    nvgs_status st = validate_flags(ctx, f);
+    if (st != NVGS_OK) return st;
+    if (!cams || !images || n_views < 1 || n_views > 4096)
+        return fail(ctx, NVGS_ERR_INVALID_ARG, "need 1..4096 cameras and image pointers");
+    if (f->image_memory != NVGS_MEM_DEVICE || f->keep_outputs || f->profile || f->logits_override)
+        return fail(ctx, NVGS_ERR_INVALID_ARG,
+                    "views need device images, no kept outputs, no profiling, no injected logits");
+    for (int v = 0; v < n_views; v++)
+        if (!images[v]) return fail(ctx, NVGS_ERR_INVALID_ARG, "image %d is NULL", v);
+    nvgs_batch_opts o{};
+    if (opts) o = *opts;
+    if (o.max_pairs < 0) return fail(ctx, NVGS_ERR_INVALID_ARG, "max_pairs must be >= 0");
+    CK(cudaSetDevice(ctx->device));
+    if ((st = check_scene(ctx)) != NVGS_OK) return st;
+    const int n_inst = (int)ctx->instances.size();
+    // frame instances (view, instance) and their chunks; cameras with their global tile bases
+    std::vector<int2> fimap;
+    std::vector<Chunk> chunks;
+    std::vector<CamParams> cps(n_views);
+    uint64_t total = 0;
+    int n_tiles = 0;
+    for (int v = 0; v < n_views; v++) {
+        if ((st = make_cam(ctx, &cams[v], f, &cps[v])) != NVGS_OK) return st;
+        cps[v].tile_base = n_tiles;
+        n_tiles += cps[v].tiles_x * cps[v].tiles_y;
+        const bool all = !sets || !sets[v].instances;
+        const int count = all ? n_inst : sets[v].count;
+        if (count < 0) return fail(ctx, NVGS_ERR_INVALID_ARG, "view %d: negative instance count", v);
+        for (int j = 0; j < count; j++) {
+            const int i = all ? j : sets[v].instances[j];
+            if (i < 0 || i >= n_inst)
+                return fail(ctx, NVGS_ERR_INVALID_ARG, "view %d: instance %d out of range", v, i);
+            const int fi = (int)fimap.size();
+            fimap.push_back(make_int2(v, i));
+            const int64_t n = ctx->assets[ctx->instances[i].asset_id].dev.n;
+            for (int64_t g0 = 0; g0 < n; g0 += kChunk)
+                chunks.push_back(Chunk{fi, (int)g0, (int)std::min<int64_t>(kChunk, n - g0), 0});
+            total += (uint64_t)n;
+        }
+        if (n_tiles > (1 << 26)) return fail(ctx, NVGS_ERR_CAPACITY, "more than 2^26 tiles in the batch");
+    }
+    if (fimap.empty()) return fail(ctx, NVGS_ERR_INVALID_ARG, "no instance in any view");
+    if (total >= ((uint64_t)1 << 31))
+        return fail(ctx, NVGS_ERR_CAPACITY, "a batch takes at most 2^31 instanced Gaussians (has %llu)",
+                    (unsigned long long)total);
+    const uint64_t pair_cap = std::min<uint64_t>(o.max_pairs > 0 ? (uint64_t)o.max_pairs : 8ull * total,
+                                                 0xffffffffull - 16);
+    const int digit_bits = f->sort_digit_bits ? f->sort_digit_bits : 8;
+    begin_frame(ctx, false);
+    ctx->kept_frame = false;
+    cudaStream_t s = ctx->stream;
+    CK(ensure(ctx->view_stats, 32));
+    // graph key: cameras' sizes, the instance sets, flags, options and image pointers
+    std::vector<uint8_t> key;
+    auto put = [&](const void* p, size_t n) { key.insert(key.end(), (const uint8_t*)p, (const uint8_t*)p + n); };
+    put(&n_views, sizeof n_views);
+    for (auto& c : cps) { put(&c.W, sizeof c.W); put(&c.H, sizeof c.H); }
+    put(fimap.data(), fimap.size() * sizeof(int2));
+    put(f, sizeof *f);
+    put(&o, sizeof o);
+    put(&pair_cap, sizeof pair_cap);
+    for (int v = 0; v < n_views; v++) put(&images[v], sizeof(float*));
+    const bool replay = o.use_graph && ctx->mv_graph_exec && key == ctx->mv_graph_key;
+    if (replay) {
+        if (ctx->cam_ev_pending) CK(cudaEventSynchronize(ctx->cam_ev));
+        memcpy(ctx->h_cam, cps.data(), cps.size() * sizeof(CamParams));
+        CK(cudaGraphLaunch(ctx->mv_graph_exec, s));
+        CK(cudaEventRecord(ctx->cam_ev, s));
+        ctx->cam_ev_pending = true;
+    } else {
+        CK(ensure(ctx->mv_fimap, fimap.size() * sizeof(int2)));
+        CK(ensure(ctx->mv_chunks, chunks.size() * sizeof(Chunk)));
+        CK(ensure(ctx->mv_images, (size_t)n_views * sizeof(float*)));
+        CK(cudaMemcpyAsync(ctx->mv_fimap.p, fimap.data(), fimap.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->mv_chunks.p, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->mv_images.p, images, (size_t)n_views * sizeof(float*), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));   // the host vectors go out of scope
+        if ((st = upload_cams(ctx, cps.data(), n_views)) != NVGS_OK) return st;
+        const CullScope scope{P<Chunk>(ctx->mv_chunks), (int)chunks.size(), (int)fimap.size(), P<int2>(ctx->mv_fimap),
+                              total};
+        if ((st = enqueue_views(ctx, scope, cps[0], n_views, n_tiles, f, pair_cap, digit_bits)) != NVGS_OK) return st;
+        if (o.use_graph) {
+            CK(cudaStreamSynchronize(s));
+            if (ctx->mv_graph_exec) { cudaGraphExecDestroy(ctx->mv_graph_exec); ctx->mv_graph_exec = nullptr; }
+            ctx->mv_graph_key.clear();
+            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            cudaError_t ce = cudaMemcpyAsync(ctx->cam_dev.p, ctx->h_cam, cps.size() * sizeof(CamParams),
+                                             cudaMemcpyHostToDevice, s);
+            nvgs_status cs = ce == cudaSuccess
+                                 ? enqueue_views(ctx, scope, cps[0], n_views, n_tiles, f, pair_cap, digit_bits)
+                                 : fail(ctx, NVGS_ERR_CUDA, "capture: %s", cudaGetErrorString(ce));
+            cudaGraph_t g = nullptr;
+            cudaError_t ee = cudaStreamEndCapture(s, &g);
+            if (cs != NVGS_OK) { if (g) cudaGraphDestroy(g); return cs; }
+            if (ee != cudaSuccess) return fail(ctx, NVGS_ERR_CUDA, "capture: %s", cudaGetErrorString(ee));
+            cudaError_t ie = cudaGraphInstantiate(&ctx->mv_graph_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) {
+                ctx->mv_graph_exec = nullptr;
+                return fail(ctx, NVGS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+            }
+            ctx->mv_graph_key = key;
+        }
+    }
+    if (!stats) return NVGS_OK;
+    uint32_t h[8] = {};
+    CK(cudaMemcpyAsync(h, ctx->view_stats.p, sizeof h, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    memset(stats, 0, sizeof *stats);
+    stats->n_instanced = total;
+    stats->n_in_frustum = h[0];
+    stats->n_mlp_queries = f->use_mlp ? h[0] : 0;
+    stats->n_survivors = f->use_mlp ? h[1] : h[0];
+    stats->n_pairs = h[2];
+    stats->kernel_launches = ctx->log.count;
+    if (h[4]) return fail(ctx, NVGS_ERR_TIMEOUT, "tensor-core MLP: a bounded mbarrier wait gave up");
+    if (h[5])
+        return fail(ctx, NVGS_ERR_CAPACITY, "the batch needed more than max_pairs = %llu pairs",
+                    (unsigned long long)pair_cap);
+    return NVGS_OK;
+}
+
 extern "C" nvgs_status nvgs_autotune(nvgs_ctx* ctx, const nvgs_camera* cams, int n_views,
                                      float* const* images, const nvgs_render_flags* f,
                                      const nvgs_batch_opts* opts, nvgs_render_flags* best,
@@ -1387,6 +1615,7 @@ extern "C" nvgs_status nvgs_autotune(nvgs_ctx* ctx, const nvgs_camera* cams, int
     const bool tc = f->use_mlp && uses_tc_mlp(ctx, f);
     const int tiles[3] = {8, 16, 32};
     const int splits[2] = {0, -1};
+    const int digits[3] = {8, 6, 4};
     const int n_ctas = tc ? 4 : 1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaSetDevice(ctx->device));
@@ -1397,16 +1626,19 @@ extern "C" nvgs_status nvgs_autotune(nvgs_ctx* ctx, const nvgs_camera* cams, int
     nvgs_status st = NVGS_OK;
     for (int ti = 0; ti < 3 && st == NVGS_OK; ti++)
         for (int ci = 0; ci < n_ctas && st == NVGS_OK; ci++)
-            for (int si = 0; si < 2 && st == NVGS_OK; si++) {
+            for (int si = 0; si < 2 && st == NVGS_OK; si++)
+            for (int di = 0; di < 3 && st == NVGS_OK; di++) {
                 nvgs_render_flags c = *f;
                 c.tile_size = tiles[ti];
                 c.mlp_ctas_per_sm = tc ? ci + 1 : f->mlp_ctas_per_sm;
                 c.blend_split_len = splits[si];
+                c.sort_digit_bits = digits[di];
                 std::vector<nvgs_frame_stats> stv(n_views);
                 st = nvgs_render_batch(ctx, cams, n_views, images, &c, &o, stv.data());   // warm-up
                 if (st == NVGS_ERR_CAPACITY) {   // needs more pairs than max_pairs: not a candidate
                     if (results && count < max_results)
-                        results[count] = nvgs_tune_result{c.tile_size, c.mlp_ctas_per_sm, c.blend_split_len, INFINITY};
+                        results[count] = nvgs_tune_result{c.tile_size, c.mlp_ctas_per_sm, c.blend_split_len, INFINITY,
+                                                          c.sort_digit_bits, 0};
                     count++;
                     st = NVGS_OK;
                     continue;
@@ -1422,7 +1654,8 @@ extern "C" nvgs_status nvgs_autotune(nvgs_ctx* ctx, const nvgs_camera* cams, int
                 cudaEventElapsedTime(&ms, e0, e1);
                 ms /= 3.0f * (float)n_views;
                 if (results && count < max_results)
-                    results[count] = nvgs_tune_result{c.tile_size, c.mlp_ctas_per_sm, c.blend_split_len, ms};
+                    results[count] = nvgs_tune_result{c.tile_size, c.mlp_ctas_per_sm, c.blend_split_len, ms,
+                                                      c.sort_digit_bits, 0};
                 count++;
                 if (ms < best_ms) { best_ms = ms; *best = c; }
             }

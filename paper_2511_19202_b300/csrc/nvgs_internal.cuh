@@ -65,6 +65,7 @@ struct FrameInst {
     int visible;              // bounding sphere meets the guard-band frustum
     int gated;                // instance closer than d_min: bypass the MLP (Sec. 3.3)
     int no_mlp;               // the asset has no visibility MLP: rendered unculled
+    int view;                 // the view (camera) of this frame instance in a multi-view batch
 };
 
 // Camera-space position of a local mean: the small terms M mu first, the instance offset b last,
@@ -89,6 +90,7 @@ struct CamParams {
     int tile_size, tiles_x, tiles_y;
     int mlp_gate;             // 1: instances closer than d_min bypass the MLP
     float clip_det;           // radius clipping: splats with det Sigma_2D below it are not binned (0: off)
+    int tile_base;            // first global tile id of this view (multi-view batches; 0 otherwise)
 };
 
 // Real spherical harmonics up to degree 3 (the 3DGS sign convention), Y[(l+1)^2].
@@ -259,8 +261,11 @@ struct LaunchLog {
 
 // ------------------------------------------------------------------ launchers (stream-ordered)
 // Each returns cudaGetLastError() after its launches and logs them in *log.
+// fi_map (nullable, device, n_fi entries): frame instance k = (view, instance) of a multi-view
+// batch, with that view's camera cam_dev[view]; without it frame instance k = instance k, view 0.
 cudaError_t launch_instance_setup(const InstanceRaw* inst, int n_inst, const AssetDev* assets,
-                                  const CamParams* cam_dev, FrameInst* out, cudaStream_t s, LaunchLog* log);
+                                  const CamParams* cam_dev, FrameInst* out, cudaStream_t s, LaunchLog* log,
+                                  const int2* fi_map = nullptr, int n_fi = 0);
 
 cudaError_t launch_frustum(const Chunk* chunks, int n_chunks, const FrameInst* fi,
                            const AssetDev* assets, const CamParams* cam_dev, uint32_t* bits,
@@ -331,11 +336,12 @@ cudaError_t launch_scatter_visibility(const uint2* list, uint32_t n, const uint3
                                       cudaStream_t s, LaunchLog* log);
 
 // S4: records, tile rects and counts; dkey / didx receive the depth sort keys (IEEE bits of
-// the camera-space z) and the survivor indices 0..n-1.
+// the camera-space z) and the survivor indices 0..n-1.  multi_view: each survivor's camera is
+// cam_dev[its frame instance's view], and the rect's w holds the last tile row | view << 16.
 cudaError_t launch_project(const uint2* surv, uint32_t n, const uint32_t* n_dev, const FrameInst* fi,
                            const AssetDev* assets, const CamParams* cam_dev, float4* rec, int4* rects,
                            uint32_t* tile_counts, uint32_t* dkey, uint32_t* didx, int num_sms,
-                           cudaStream_t s, LaunchLog* log);
+                           cudaStream_t s, LaunchLog* log, int multi_view = 0);
 
 // S5 (k_bin.cu)
 cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* counts, uint32_t n,
@@ -344,11 +350,13 @@ cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* counts, 
 // Pairs of the survivors in depth order: the tiles of each rectangle that row_tile_span keeps,
 // as the projection counted them.  n_pairs (device) is the total; writes stop at pair_cap, and
 // overflow (device, nullable) is set when the total exceeds it.
+// multi_view: tile ids are global (the view's tile_base + its local tile id), the view taken
+// from the rect (as launch_project writes it in multi-view mode).
 cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const float4* rec,
                              const uint32_t* offsets, uint32_t n, const uint32_t* n_dev,
                              const CamParams* cam_dev, const uint32_t* n_pairs, uint32_t pair_cap,
                              uint32_t* overflow, uint32_t* keys, uint32_t* values, int num_sms,
-                             cudaStream_t s, LaunchLog* log);
+                             cudaStream_t s, LaunchLog* log, int multi_view = 0);
 cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, const uint32_t* n_dev, uint32_t n_tiles,
                                uint32_t* ranges, cudaStream_t s, LaunchLog* log);
 
@@ -361,11 +369,16 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, const uint32_t*
 // count with the host's rule; split_len is then its lower bound 4096 (scratch sizing) and n_pairs
 // the pair capacity.
 size_t blend_split_scratch_bytes(int n_tiles, uint64_t n_pairs, int tile_size, uint32_t split_len);
+// Multi-view batches (n_views > 1 or images != nullptr): the tiles of all views are global ids
+// (cam_dev[v].tile_base), n_tiles_total of them; a tile's view is found from the tile bases and
+// it is written to images[view] (a DEVICE array of n_views image pointers); final_T, n_contrib
+// and mark must then be null.
 cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const float4* rec,
                          const CamParams& cam, const CamParams* cam_dev, float* image, float* final_T,
                          int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
                          const uint32_t* auto_split_pairs, void* scratch, void* scan_scratch,
-                         int num_sms, unsigned long long* evals, cudaStream_t s, LaunchLog* log);
+                         int num_sms, unsigned long long* evals, cudaStream_t s, LaunchLog* log,
+                         int n_views = 1, float* const* images = nullptr, int n_tiles_total = 0);
 // labels[row * n_gauss + g] |= mark[s] for survivor s = (instance, g)
 cudaError_t launch_mark_labels(const uint2* surv, uint32_t n_surv, const uint8_t* mark,
                                uint8_t* labels_row, cudaStream_t s, LaunchLog* log);

@@ -57,8 +57,8 @@ class RenderFlags(C.Structure):
                 ("tile_size", C.c_int32), ("image_memory", C.c_int32), ("profile", C.c_int32),
                 ("logits_override", C.c_void_p), ("keep_outputs", C.c_int32),
                 ("blend_split_len", C.c_int32), ("mlp_ctas_per_sm", C.c_int32),
-                ("radius_clip_area", C.c_float),
-                ("reserved", C.c_int32 * 4)]
+                ("radius_clip_area", C.c_float), ("sort_digit_bits", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class FrameStats(C.Structure):
@@ -104,7 +104,7 @@ class BatchOpts(C.Structure):
 
 class TuneResult(C.Structure):
     _fields_ = [("tile_size", C.c_int32), ("mlp_ctas_per_sm", C.c_int32), ("blend_split_len", C.c_int32),
-                ("ms_per_view", C.c_float)]
+                ("ms_per_view", C.c_float), ("sort_digit_bits", C.c_int32), ("pad_", C.c_int32)]
 
 
 class ViewOpts(C.Structure):
@@ -129,7 +129,7 @@ EXPORTS = ("nvgs_create", "nvgs_destroy", "nvgs_last_error", "nvgs_get_stream", 
            "nvgs_sort_pairs_noalloc", "nvgs_label_visibility", "nvgs_train_init",
            "nvgs_train_visibility_step", "nvgs_train_get_weights", "nvgs_lr_schedule",
            "nvgs_get_asset_info", "nvgs_training_views", "nvgs_render_backward",
-           "nvgs_update_asset", "nvgs_render_batch", "nvgs_autotune", "nvgs_device_bytes",
+           "nvgs_update_asset", "nvgs_render_batch", "nvgs_render_views", "nvgs_autotune", "nvgs_device_bytes",
            "nvgs_selftest_wait_timeout", "nvgs_measure_fp32_fma", "nvgs_training_views_ex",
            "nvgs_train_save_state", "nvgs_train_load_state", "nvgs_debug_fail_allocs")
 NVGS_SORT_NOALLOC_MAX_PAIRS = 1 << 20
@@ -178,6 +178,7 @@ def _load():
     L.nvgs_render_backward.argtypes = [vp, vp, C.c_int, P(AssetGrads)]
     L.nvgs_device_bytes.argtypes = [vp, P(C.c_uint64)]
     L.nvgs_render_batch.argtypes = [vp, vp, C.c_int, vp, P(RenderFlags), P(BatchOpts), vp]
+    L.nvgs_render_views.argtypes = [vp, vp, vp, C.c_int, vp, P(RenderFlags), P(BatchOpts), vp]
     L.nvgs_autotune.argtypes = [vp, vp, C.c_int, vp, P(RenderFlags), P(BatchOpts), P(RenderFlags), vp, C.c_int,
                                 P(C.c_int)]
     L.nvgs_update_asset.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
@@ -488,20 +489,50 @@ def nvgs_render_batch(ctx, cams, flags: RenderFlags, images, max_pairs: int = 0,
 
 
 def nvgs_autotune(ctx, cams, flags: RenderFlags, images, max_pairs: int = 0):
-    """(best flags, [ {tile_size, mlp_ctas_per_sm, blend_split_len, ms_per_view} ... ])."""
+    """(best flags, [ {tile_size, mlp_ctas_per_sm, blend_split_len, sort_digit_bits, ms_per_view}
+    ... ])."""
     n = len(cams)
     arr = (Camera * n)(*[camera(c) for c in cams])
     ptrs = (C.c_void_p * n)(*[_ptr(im) for im in images])
     o = BatchOpts(int(max_pairs), 0)
     best = RenderFlags()
-    res = (TuneResult * 64)()
+    cap = 256
+    res = (TuneResult * cap)()
     cnt = C.c_int(0)
     _check(ctx, lib.nvgs_autotune(ctx, C.cast(arr, C.c_void_p), n, C.cast(ptrs, C.c_void_p), C.byref(flags),
-                                  C.byref(o), C.byref(best), C.cast(res, C.c_void_p), 64, C.byref(cnt)))
+                                  C.byref(o), C.byref(best), C.cast(res, C.c_void_p), cap, C.byref(cnt)))
     table = [dict(tile_size=res[k].tile_size, mlp_ctas_per_sm=res[k].mlp_ctas_per_sm,
-                  blend_split_len=res[k].blend_split_len, ms_per_view=res[k].ms_per_view)
-             for k in range(min(cnt.value, 64))]
+                  blend_split_len=res[k].blend_split_len, sort_digit_bits=res[k].sort_digit_bits,
+                  ms_per_view=res[k].ms_per_view)
+             for k in range(min(cnt.value, cap))]
     return best, table
+
+
+class ViewInstances(C.Structure):
+    _fields_ = [("instances", C.c_void_p), ("count", C.c_int32), ("pad_", C.c_int32)]
+
+
+def nvgs_render_views(ctx, cams, instance_sets, flags: RenderFlags, images, max_pairs: int = 0,
+                      use_graph: bool = False, want_stats: bool = True):
+    """Views with their own instance subsets (None: every instance), one launch per stage for the
+    whole batch; returns the batch's totals (or None without stats)."""
+    n = len(cams)
+    arr = (Camera * n)(*[camera(c) for c in cams])
+    ptrs = (C.c_void_p * n)(*[_ptr(im) for im in images])
+    keep = []
+    sets = (ViewInstances * n)()
+    for k, idx in enumerate(instance_sets if instance_sets is not None else [None] * n):
+        if idx is not None:
+            a = np.ascontiguousarray(idx, np.int32)
+            keep.append(a)
+            sets[k].instances = a.ctypes.data
+            sets[k].count = a.size
+    o = BatchOpts(int(max_pairs), 1 if use_graph else 0)
+    st = FrameStats() if want_stats else None
+    _check(ctx, lib.nvgs_render_views(ctx, C.cast(arr, C.c_void_p), C.cast(sets, C.c_void_p), n,
+                                      C.cast(ptrs, C.c_void_p), C.byref(flags), C.byref(o),
+                                      C.byref(st) if st is not None else None))
+    return st.as_dict() if st is not None else None
 
 
 def nvgs_device_bytes(ctx) -> int:

@@ -72,6 +72,17 @@ class Renderer:
         st = N.nvgs_render(self.ctx, cam, flags, out)
         return out, st.as_dict()
 
+    def render_views(self, cams, instance_sets=None, flags: N.RenderFlags | None = None, out=None,
+                     max_pairs: int = 0, use_graph: bool = False, want_stats: bool = True):
+        """Views with their own instance subsets (lists of indices into the scene's instances;
+        None: all), one launch per stage for the whole batch (optionally replayed as a CUDA
+        graph).  Returns (images, batch totals)."""
+        flags = flags or self.flags()
+        if out is None:
+            out = [torch.empty((c.height, c.width, 3), dtype=torch.float32, device=self.device) for c in cams]
+        st = N.nvgs_render_views(self.ctx, cams, instance_sets, flags, out, max_pairs, use_graph, want_stats)
+        return out, st
+
     def render_batch(self, cams, flags: N.RenderFlags | None = None, out=None, max_pairs: int = 0,
                      use_graph: bool = False, want_stats: bool = True):
         """Several views in one sync-free call (optionally replayed as a CUDA graph)."""

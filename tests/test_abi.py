@@ -45,7 +45,8 @@ def test_struct_layouts_match_the_c_compiler(N):
                "nvgs_kernel_stat": N.KernelStat, "nvgs_asset_info": N.AssetInfo,
                "nvgs_train_batch": N.TrainBatch, "nvgs_adam_cfg": N.AdamCfg,
                "nvgs_asset_grads": N.AssetGrads, "nvgs_batch_opts": N.BatchOpts,
-               "nvgs_tune_result": N.TuneResult, "nvgs_view_opts": N.ViewOpts}
+               "nvgs_tune_result": N.TuneResult, "nvgs_view_opts": N.ViewOpts,
+               "nvgs_view_instances": N.ViewInstances}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void){']
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -87,3 +88,4 @@ def test_create_fails_cleanly_on_a_bad_device(N):
     assert N.lib.nvgs_render_backward(None, None, 0, C.byref(g)) == N.NVGS_ERR_INVALID_ARG
     assert N.lib.nvgs_update_asset(None, 0, None, None, None, None, None) == N.NVGS_ERR_INVALID_ARG
     assert N.lib.nvgs_render_batch(None, None, 0, None, None, None, None) == N.NVGS_ERR_INVALID_ARG
+    assert N.lib.nvgs_render_views(None, None, None, 0, None, None, None, None) == N.NVGS_ERR_INVALID_ARG

@@ -114,7 +114,7 @@ def test_autotuner_times_every_candidate_and_images_do_not_depend_on_the_choice(
         base = r.flags(use_mlp=1, mlp_gate=0)
         best, table = N.nvgs_autotune(r.ctx, cams, base, out)
         print(table)
-        assert len(table) == 3 * 4 * 2          # tiles x MLP CTAs per SM x split
+        assert len(table) == 3 * 4 * 2 * 3      # tiles x MLP CTAs per SM x split x radix digit width
         assert {t["tile_size"] for t in table} == {8, 16, 32}
         fastest = min(table, key=lambda t: t["ms_per_view"])
         assert best.tile_size == fastest["tile_size"] and best.mlp_ctas_per_sm == fastest["mlp_ctas_per_sm"]
@@ -151,5 +151,133 @@ def test_automatic_split_equals_the_synchronous_render(use_graph):
             r.render_batch([cam], fl(0), out=out, max_pairs=3 * st["n_pairs"], use_graph=use_graph)
             torch.cuda.synchronize()
             assert torch.equal(out[0], auto)
+    finally:
+        r.close()
+
+
+# ----------------------------------------------------------------------------- views with own instance sets
+def _pool_scene(n_instances=12, n=3000):
+    """Three small assets (torus, sphere, box; SH degree 1) as n_instances rigid instances spread on a
+    plane: the pool every view draws its own instance subset from."""
+    assets = [scenes.torus_asset(n, seed=1, sh_degree=1), scenes.sphere_asset(n, 2, sh_degree=1),
+              scenes.box_asset(n, 3, sh_degree=1)]
+    rng = np.random.default_rng(31)
+    insts = []
+    for k in range(n_instances):
+        q, rr = np.linalg.qr(rng.standard_normal((3, 3)))
+        q = q * np.sign(np.diag(rr))
+        if np.linalg.det(q) < 0:
+            q[:, 0] *= -1
+        t = np.array([rng.uniform(-3, 3), rng.uniform(-0.5, 0.5), rng.uniform(-3, 3)], np.float32)
+        insts.append(scenes.Instance(k % 3, q.astype(np.float32), t, float(np.float32(rng.uniform(0.5, 1.2)))))
+    return scenes.Scene(assets, insts)
+
+
+def _view_sets(n_instances, n_views, seed=5):
+    """Uneven instance subsets (2 .. all of the pool, shuffled order) and mixed camera sizes."""
+    rng = np.random.default_rng(seed)
+    sizes = [(256, 144), (320, 180), (97, 61), (200, 200), (128, 96), (61, 97)]
+    sets, cams = [], []
+    for v in range(n_views):
+        k = int(rng.integers(2, n_instances + 1))
+        sets.append(np.sort(rng.choice(n_instances, k, replace=False)).astype(np.int32))
+        ang = rng.uniform(0, 2 * np.pi)
+        eye = (8.0 * np.cos(ang), rng.uniform(1.0, 4.0), 8.0 * np.sin(ang))
+        cams.append(scenes.look_at_camera(eye, (0, 0, 0), *sizes[v % len(sizes)], 55.0))
+    return sets, cams
+
+
+def _subset_render(r, sc, subset, cam, fl):
+    r.set_instances([sc.instances[i] for i in subset])
+    img, st = r.render(cam, fl)
+    return img.clone(), st
+
+
+@pytest.mark.parametrize("use_mlp", [0, 1])
+def test_views_with_own_instance_sets_equal_their_single_view_renders(use_mlp):
+    """nvgs_render_views: every view, with its own uneven instance subset and size, equals the
+    synchronous render of that view over exactly those instances bit for bit (no dense-tile split),
+    the batch's totals are the views' sums, and the BF16 MLP path culls in both."""
+    from paper_2511_19202_b300 import nvgs as N
+    sc = _pool_scene()
+    ws = [scenes.mlp_weights(60 + k) for k in range(3)]
+    r = renderer_for(sc, ws, precision=N.NVGS_PREC_BF16)
+    try:
+        sets, cams = _view_sets(len(sc.instances), 7)
+        fl = dict(use_mlp=use_mlp, mlp_gate=0, bg=(0.05, 0.1, 0.2), blend_split_len=-1)
+        imgs, tot = r.render_views(cams, [s.tolist() for s in sets], r.flags(**fl))
+        imgs = [im.clone() for im in imgs]
+        sums = dict(n_in_frustum=0, n_survivors=0, n_pairs=0)
+        for v, (subset, cam) in enumerate(zip(sets, cams)):
+            ref, st = _subset_render(r, sc, subset, cam, r.flags(**fl))
+            assert torch.equal(imgs[v], ref), f"view {v}: max diff {float((imgs[v] - ref).abs().max()):.3e}"
+            for k in sums:
+                sums[k] += st[k]
+        for k in sums:
+            assert tot[k] == sums[k], (k, tot[k], sums[k])
+        assert tot["n_pairs"] > 0
+        if use_mlp:
+            assert 0 < tot["n_survivors"] < tot["n_in_frustum"]
+    finally:
+        r.close()
+
+
+def test_views_match_the_oracle():
+    """Two views of one batch against the FP64 oracle over their own instance subsets: a small one
+    and a ragged one (97 x 61, tiles cut at both edges), unculled, 1e-3 max-abs outside the band."""
+    import oracle
+    from gpu_common import compare_images, oracle_opts_for
+    sc = _pool_scene()
+    r = renderer_for(sc)
+    try:
+        sets, cams = _view_sets(len(sc.instances), 6, seed=9)
+        fl = dict(use_mlp=0, bg=(0.05, 0.1, 0.2))
+        imgs, tot = r.render_views(cams, [s.tolist() for s in sets], r.flags(**fl))
+        for v in (2, 5):   # 97 x 61 and 61 x 97
+            sub = scenes.Scene(sc.assets, [sc.instances[i] for i in sets[v]])
+            ref = oracle.render(oracle.OracleScene(sub), cams[v], oracle_opts_for(fl))
+            err, n_amb = compare_images(imgs[v].cpu().numpy().astype(np.float64), ref["image"], ref["ambiguous"])
+            print(f"view {v} ({cams[v].width}x{cams[v].height}, {len(sets[v])} instances): max err {err:.2e}, "
+                  f"{n_amb} ambiguous pixels")
+    finally:
+        r.close()
+
+
+def test_views_graph_replay_with_new_cameras():
+    """The batch captured into a CUDA graph replays with new cameras (same sizes, instance sets and
+    images) and equals a plain call with those cameras; automatic dense-tile split on."""
+    sc = _pool_scene()
+    r = renderer_for(sc)
+    try:
+        sets, cams = _view_sets(len(sc.instances), 5, seed=3)
+        sets2, cams2 = _view_sets(len(sc.instances), 5, seed=4)
+        fl = r.flags(use_mlp=0)
+        lists = [s.tolist() for s in sets]
+        out = [torch.zeros((c.height, c.width, 3), device="cuda") for c in cams]
+        r.render_views(cams, lists, fl, out=out, use_graph=True)          # render + capture
+        cams_b = [scenes.look_at_camera(-np.asarray(c2.R).T @ np.asarray(c2.t), (0, 0, 0), c.width, c.height, 55.0)
+                  for c, c2 in zip(cams, cams2)]
+        r.render_views(cams_b, lists, fl, out=out, use_graph=True)        # replay
+        torch.cuda.synchronize()
+        replay = [o.clone() for o in out]
+        plain, _ = r.render_views(cams_b, lists, fl)
+        for a, b in zip(replay, plain):
+            assert torch.equal(a, b)
+    finally:
+        r.close()
+
+
+def test_views_reject_bad_sets():
+    from paper_2511_19202_b300 import nvgs as N
+    sc = _pool_scene(4)
+    r = renderer_for(sc)
+    try:
+        cam = scenes.look_at_camera((0, 2, 8), (0, 0, 0), 64, 64, 55.0)
+        with pytest.raises(N.NvgsError):
+            r.render_views([cam], [[0, 7]], r.flags(use_mlp=0))            # instance out of range
+        with pytest.raises(N.NvgsError):
+            r.render_views([cam], [[0]], r.flags(use_mlp=0, keep_outputs=1))
+        img, tot = r.render_views([cam, cam], [[], None], r.flags(use_mlp=0))   # an empty view is fine
+        assert tot["n_instanced"] == 4 * 3000
     finally:
         r.close()
