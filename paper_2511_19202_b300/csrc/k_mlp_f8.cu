@@ -65,10 +65,16 @@ constexpr float kInScale = 256.0f;
 // N / 8 at bit 17, M / 16 at bit 24.
 constexpr uint32_t kIdesc = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
-// (lo, hi) -> two saturated E4M3 codes, lo in the low byte (the lower k).
+// (lo, hi) -> two saturated E4M3 codes, lo in the low byte (the lower k); the _relu form clamps
+// negative values to 0 in the same conversion.
 __device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
     uint16_t d;
     asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+    return (uint32_t)d;
+}
+__device__ __forceinline__ uint32_t e4m3x2_relu(float lo, float hi) {
+    uint16_t d;
+    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
     return (uint32_t)d;
 }
 __device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
@@ -91,7 +97,8 @@ __device__ __forceinline__ void mma_f8_ts(uint32_t d_tmem, uint32_t a_tmem, uint
         : "memory");
 }
 
-// hidden epilogue: q_h = E4M3_sat(max(0, acc alpha + beta)) into H, in two 32-column halves
+// hidden epilogue: q_h = E4M3_sat(max(0, acc alpha + beta)) into H, in two 32-column halves (the
+// ReLU inside the saturating conversion, beta read four at a time)
 __device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, float alpha, const float* beta) {
 #pragma unroll
     for (int half = 0; half < 2; half++) {
@@ -100,13 +107,12 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, float alpha, co
         uint32_t p[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) {
-            float v[4];
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const int col = 32 * half + 4 * q + e;
-                v[e] = fmaxf(fmaf(__uint_as_float(r[4 * q + e]), alpha, beta[col]), 0.0f);
-            }
-            p[q] = e4m3x4(v[0], v[1], v[2], v[3]);
+            const float4 b = *reinterpret_cast<const float4*>(beta + 32 * half + 4 * q);
+            const float v0 = fmaf(__uint_as_float(r[4 * q]), alpha, b.x);
+            const float v1 = fmaf(__uint_as_float(r[4 * q + 1]), alpha, b.y);
+            const float v2 = fmaf(__uint_as_float(r[4 * q + 2]), alpha, b.z);
+            const float v3 = fmaf(__uint_as_float(r[4 * q + 3]), alpha, b.w);
+            p[q] = e4m3x2_relu(v0, v1) | (e4m3x2_relu(v2, v3) << 16);
         }
         tmem_st8(t_lane + kColH + 8 * half, p);
     }
@@ -114,18 +120,22 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, float alpha, co
 
 __device__ __forceinline__ float epilogue_logit(uint32_t t_lane, float alpha, const float* b3, const float* w4,
                                                 float b4) {
-    float lg[2] = {b4, 0.0f};
+    float lg[4] = {b4, 0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int half = 0; half < 2; half++) {
         uint32_t r[32];
         tmem_ld32(t_lane + kColD + 32 * half, r);
 #pragma unroll
-        for (int k = 0; k < 32; k++) {
-            const int col = half * 32 + k;
-            lg[k & 1] = fmaf(w4[col], fmaxf(fmaf(__uint_as_float(r[k]), alpha, b3[col]), 0.0f), lg[k & 1]);
+        for (int q = 0; q < 8; q++) {
+            const float4 b = *reinterpret_cast<const float4*>(b3 + 32 * half + 4 * q);
+            const float4 w = *reinterpret_cast<const float4*>(w4 + 32 * half + 4 * q);
+            lg[0] = fmaf(w.x, fmaxf(fmaf(__uint_as_float(r[4 * q]), alpha, b.x), 0.0f), lg[0]);
+            lg[1] = fmaf(w.y, fmaxf(fmaf(__uint_as_float(r[4 * q + 1]), alpha, b.y), 0.0f), lg[1]);
+            lg[2] = fmaf(w.z, fmaxf(fmaf(__uint_as_float(r[4 * q + 2]), alpha, b.z), 0.0f), lg[2]);
+            lg[3] = fmaf(w.w, fmaxf(fmaf(__uint_as_float(r[4 * q + 3]), alpha, b.w), 0.0f), lg[3]);
         }
     }
-    return lg[0] + lg[1];
+    return (lg[0] + lg[1]) + (lg[2] + lg[3]);
 }
 
 __device__ __forceinline__ void prefetch_row(uint2* s_e, float4* s_m, const uint2* e, const float4* m) {
