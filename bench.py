@@ -426,6 +426,7 @@ def run_ours(args, rank, world):
     _, st_count = timed(culled, args.steps, 2, "nvgs_counted_culled")
     for s_, c_ in zip(st_prof, st_count):
         s_["blend_evaluations"] = c_["blend_evaluations"]
+        s_["blend_composited"] = c_["blend_composited"]
 
     value, plain_ms = job_ms_per_frame([ms_culled, ms_plain], args.steps, world,
                                        device=f"cuda:{dev}" if world > 1 else None)
@@ -518,6 +519,7 @@ def run_ours(args, rank, world):
             alu_src = "derived: 148 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock"
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "evaluations_per_frame": float(np.mean([s_["blend_evaluations"] for s_ in st_prof])),
+                "composited_per_frame": float(np.mean([s_["blend_composited"] for s_ in st_prof])),
                 "flops_per_evaluation": BLEND_FLOPS_PER_EVAL}
     else:
         achieved = work / (tot_ms * 1e-3) / 1e9

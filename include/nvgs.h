@@ -139,7 +139,10 @@ typedef struct {
     uint32_t sort_passes;        /* radix passes run in S5 */
     float stage_ms[NVGS_NUM_STAGES]; /* filled when flags.profile >= 1 (synchronises) */
     uint64_t kernel_launches;    /* kernels this frame enqueued */
-    uint64_t blend_evaluations;  /* (pixel, fragment) evaluations of S6, when flags.profile = 2 */
+    uint64_t blend_evaluations;  /* (pixel, fragment) evaluations of S6 up to each pixel's stop,
+                                    when flags.profile = 2 */
+    uint64_t blend_composited;   /* of those, the fragments composited (alpha >= alpha_min, not
+                                    stopped), when flags.profile = 2 */
 } nvgs_frame_stats;
 
 /* ------------------------------------------------------------------ context */

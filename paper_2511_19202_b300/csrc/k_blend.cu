@@ -2,15 +2,20 @@
 // rasteriser).
 //
 // One CTA per TS x TS tile, one thread per pixel.  The tile's Gaussians (a contiguous range of
-// the sorted pairs) are staged through shared memory in batches of TS*TS records, gathered by
+// the sorted pairs) are staged through shared memory in batches of up to 256 records, gathered by
 // survivor index; every thread then walks the batch for its pixel:
 //   power = -1/2 (A dx^2 + C dy^2) - B dx dy      (conic [[A, B], [B, C]], pixel centre - mean)
 //   skip if power > 0;  alpha = min(alpha_max, opacity e^power);  skip if alpha < alpha_min;
 //   stop (without blending) if T (1 - alpha) < t_stop;  C += alpha T rgb;  T *= 1 - alpha.
-// A fragment whose exponent is below ln(alpha_min / opacity) minus a margin of 1e-4 is skipped
-// before the exponential: with that margin the skip never changes an alpha decision.
+// The walk takes two fragments per step: the batch is staged as pairs of records side by side, so
+// that the exponents, the opacity products and 1 - alpha of both come from packed FP32x2
+// instructions (Blackwell's paired FP32 pipe), and the step has no branch per fragment (a
+// rejected fragment gets alpha 0, which leaves C and T unchanged bit for bit).  Every rounding
+// step is the scalar rule's, lane by lane, so the image is the same as a one-fragment walk's.
 // The CTA leaves the range as soon as every pixel has stopped (a block-wide vote per batch).
-// With `mark` set, every blended fragment also flags its survivor (the visibility labeller).
+// With `mark` set, every blended fragment also flags its survivor (the visibility labeller);
+// the kernels that track the last blended pair and the marks (kAux) are separate instances, so
+// that an ordinary frame does not carry that bookkeeping.
 //
 // Dense tiles (the supplement's section on Gaussian and asset density: many Gaussians on few pixels balance
 // badly): k_blend walks at most `split_len` pairs of a tile.  If some pixel of a longer tile is
@@ -32,9 +37,12 @@ namespace {
 
 struct Frag {
     float T, C0, C1, C2;
-    uint32_t last;   // global index + 1 of the last pair blended at the pixel (0: none)
+    uint32_t last;       // global index + 1 of the last pair blended at the pixel (0: none)
     bool done;
-    uint32_t evals = 0;   // (pixel, fragment) evaluations -- the compositing's unit of work
+    uint32_t walked;     // (pixel, fragment) evaluations up to the stop -- the compositing's unit
+    uint32_t blended;    // of those, the fragments composited
+    __device__ Frag(float T_, bool done_)
+        : T(T_), C0(0.f), C1(0.f), C2(0.f), last(0), done(done_), walked(0), blended(0) {}
 };
 
 // View of global tile `tile` in a multi-view batch: the last view whose tile_base is <= tile (views
@@ -48,84 +56,166 @@ __device__ __forceinline__ int tile_view(const CamParams* __restrict__ camp, int
     return lo;
 }
 
-// Adds the block's evaluations to *out (profiling only; nullable).
-__device__ __forceinline__ void add_evals(unsigned long long* out, uint32_t evals) {
+// Adds the block's evaluations and composited fragments to out[0], out[1] (profiling; nullable).
+__device__ __forceinline__ void add_evals(unsigned long long* out, const Frag& f) {
     if (!out) return;
-    unsigned long long v = evals;
+    unsigned long long v = f.walked, e = f.blended;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+    }
+    if ((threadIdx.x & 31) == 0 && v) {
+        atomicAdd(out, v);
+        atomicAdd(out + 1, e);
+    }
 }
 
+// A batch of up to 256 staged fragments, stored in pairs (fragments 2p and 2p + 1 side by side) so
+// that every pixel evaluates two fragments per step with packed FP32x2 arithmetic.
 template <int TS>
-__device__ __forceinline__ void stage(const uint32_t* __restrict__ values, const float4* __restrict__ rec,
-                                      uint32_t k, uint32_t end, float4* s_a, float4* s_b, float4* s_c) {
+struct Smem {
+    static constexpr int NB = TS * TS < 256 ? TS * TS : 256;   // fragments a batch (even)
+    static constexpr int NP = NB / 2;
+    float4 uv[NP];   // (-u, -u', -v, -v'): the mean, negated
+    float4 ab[NP];   // (kA, kA', kB, kB')
+    float4 co[NP];   // (kC, kC', opacity, opacity')
+    float4 rg[NP];   // (r, r', g, g')
+    float2 bl[NP];   // (b, b')
+};
+
+// Thread t stages fragment k = base + t (gathered by its survivor index) into slot (t / 2, t % 2);
+// past the range it stages a fragment of zero opacity, which no pixel composites (the padding of
+// an odd last pair).
+template <int TS>
+__device__ __forceinline__ void stage(Smem<TS>& sm, const uint32_t* __restrict__ values,
+                                      const float4* __restrict__ rec, uint32_t k, uint32_t end) {
+    const int t = threadIdx.x;
+    if (t >= Smem<TS>::NB) return;
+    const int p = t >> 1, h = t & 1;
+    float* uv = reinterpret_cast<float*>(&sm.uv[p]);
+    float* ab = reinterpret_cast<float*>(&sm.ab[p]);
+    float* co = reinterpret_cast<float*>(&sm.co[p]);
+    float* rg = reinterpret_cast<float*>(&sm.rg[p]);
+    float* bl = reinterpret_cast<float*>(&sm.bl[p]);
     if (k < end) {
         const size_t idx = 3 * (size_t)values[k];
         float4 sa, sb;
         stage_splat(__ldg(&rec[idx]), __ldg(&rec[idx + 1]), sa, sb);
-        s_a[threadIdx.x] = sa;
-        s_b[threadIdx.x] = sb;
-        s_c[threadIdx.x] = __ldg(&rec[idx + 2]);
+        const float4 c = __ldg(&rec[idx + 2]);
+        uv[h] = -sa.x; uv[2 + h] = -sa.y;
+        ab[h] = sa.z;  ab[2 + h] = sa.w;
+        co[h] = sb.x;  co[2 + h] = sb.y;
+        rg[h] = c.x;   rg[2 + h] = c.y;
+        bl[h] = c.z;
+    } else {   // zero opacity: alpha 0 < alpha_min everywhere
+        uv[h] = 0.f; uv[2 + h] = 0.f;
+        ab[h] = 0.f; ab[2 + h] = 0.f;
+        co[h] = 0.f; co[2 + h] = 0.f;
+        rg[h] = 0.f; rg[2 + h] = 0.f;
+        bl[h] = 0.f;
     }
 }
 
-// Blend records [base, base + nb) (staged in shared memory) into one pixel.  transmittance_only:
-// no stop rule, no colour -- only the product of (1 - alpha).
-template <bool kTransmittanceOnly, bool kCount>
-__device__ __forceinline__ void blend_batch(const float4* s_a, const float4* s_b, const float4* s_c,
-                                            int nb, float fx, float fy, const CamParams& cam, Frag& f,
+// Blend staged fragments [base, base + nb) into one pixel, two per step, in straight-line code
+// (no branch per fragment: a rejected fragment gets alpha 0).  Per fragment, in list order,
+// exactly the scalar rules with the same FP32 operations lane by lane: the exponent p2, skip if
+// p2 > 0; alpha = min(alpha_max, opacity 2^p2), skip if alpha < alpha_min (this also covers the
+// ln(alpha_min / opacity) pre-test, whose 1e-4 margin lies far outside ex2's error); stop
+// without blending if T (1 - alpha) < t_stop; else C += alpha T rgb, T *= 1 - alpha.  The second
+// fragment of a pair sees the T the first one left.  transmittance_only: no stop rule before the
+// update and no colour -- the product of (1 - alpha), ending once it is below t_stop.  kAux:
+// also track the last blended pair and flag blended survivors in `mark`.
+template <int TS, bool kTransmittanceOnly, bool kAux, bool kCount>
+__device__ __forceinline__ void blend_batch(const Smem<TS>& sm, int nb, float fx, float fy,
+                                            const CamParams& cam, Frag& f,
                                             const uint32_t* __restrict__ values, uint32_t base,
                                             uint8_t* __restrict__ mark) {
-    for (int j = 0; j < nb && !f.done; j++) {
-        if (kCount) f.evals++;
-        const float4 a = s_a[j];
-        const float dx = fx - a.x, dy = fy - a.y;
-        const float4 b = s_b[j];
-        const float p2 = splat_exponent2(a, b, dx, dy);
-        if (p2 > 0.0f || p2 < b.z) continue;
-        const float alpha = fminf(cam.alpha_max, __fmul_rn(b.y, ex2_approx(p2)));
-        if (alpha < cam.alpha_min) continue;
-        const float nt = f.T * (1.0f - alpha);
+    const float2 FX = make_float2(fx, fx), FY = make_float2(fy, fy);
+    const float2 ONE = make_float2(1.0f, 1.0f), MINUS = make_float2(-1.0f, -1.0f);
+    const int np = (nb + 1) >> 1;
+    for (int p = 0; p < np && !f.done; p++) {
+        const float4 uv = sm.uv[p];
+        const float4 ab = sm.ab[p];
+        const float4 co = sm.co[p];
+        const float2 dx = __fadd2_rn(FX, make_float2(uv.x, uv.y));
+        const float2 dy = __fadd2_rn(FY, make_float2(uv.z, uv.w));
+        const float2 t = __ffma2_rn(make_float2(ab.x, ab.y), dx, __fmul2_rn(make_float2(ab.z, ab.w), dy));
+        const float2 p2 = __ffma2_rn(dx, t, __fmul2_rn(__fmul2_rn(make_float2(co.x, co.y), dy), dy));
+        const float2 og = __fmul2_rn(make_float2(co.z, co.w), make_float2(ex2_approx(p2.x), ex2_approx(p2.y)));
+        const float2 al = make_float2(fminf(cam.alpha_max, og.x), fminf(cam.alpha_max, og.y));
+        const bool okx = !(p2.x > 0.0f) && al.x >= cam.alpha_min;
+        const bool oky = !(p2.y > 0.0f) && al.y >= cam.alpha_min;
+        const float2 om = __ffma2_rn(MINUS, al, ONE);   // 1 - alpha, exactly as the scalar rule
         if (kTransmittanceOnly) {
-            f.T = nt;
-            if (nt < cam.t_stop) f.done = true;   // every later chunk is dead already
+            const float Tx = okx ? f.T * om.x : f.T;
+            const bool dx_ = okx && Tx < cam.t_stop;
+            const float Ty = (!dx_ && oky) ? Tx * om.y : Tx;
+            if (kCount) {
+                f.walked += dx_ ? 1 : min(2, nb - 2 * p);
+                f.blended += (int)okx + (int)(!dx_ && oky);
+            }
+            f.done = dx_ || (oky && Ty < cam.t_stop);
+            f.T = Ty;
             continue;
         }
-        if (nt < cam.t_stop) { f.done = true; break; }
-        const float4 c = s_c[j];
-        const float w = alpha * f.T;
-        if (mark) mark[values[base + j]] = 1;   // contribution alpha * T > 0 (Sec. 3.1)
-        f.C0 = fmaf(w, c.x, f.C0);
-        f.C1 = fmaf(w, c.y, f.C1);
-        f.C2 = fmaf(w, c.z, f.C2);
-        f.T = nt;
-        f.last = base + j + 1;
+        const float ntx = f.T * om.x;
+        const bool stopx = okx && ntx < cam.t_stop;
+        const bool blx = okx && !stopx;
+        const float Tx = blx ? ntx : f.T;
+        const float nty = Tx * om.y;
+        const bool stopy = !stopx && oky && nty < cam.t_stop;
+        const bool bly = !stopx && oky && !stopy;
+        const float Ty = bly ? nty : Tx;
+        const float4 rg = sm.rg[p];
+        const float2 bl = sm.bl[p];
+        const float2 w = __fmul2_rn(make_float2(blx ? al.x : 0.0f, bly ? al.y : 0.0f), make_float2(f.T, Tx));
+        // in list order, as the scalar rule (an unblended fragment adds 0 x rgb: C is unchanged)
+        f.C0 = fmaf(w.y, rg.y, fmaf(w.x, rg.x, f.C0));
+        f.C1 = fmaf(w.y, rg.w, fmaf(w.x, rg.z, f.C1));
+        f.C2 = fmaf(w.y, bl.y, fmaf(w.x, bl.x, f.C2));
+        if (kAux) {
+            if (mark) {   // contribution alpha * T > 0 (Sec. 3.1)
+                if (blx) mark[values[base + 2 * p]] = 1;
+                if (bly) mark[values[base + 2 * p + 1]] = 1;
+            }
+            f.last = bly ? base + 2 * p + 2 : (blx ? base + 2 * p + 1 : f.last);
+        }
+        if (kCount) {
+            f.walked += stopx ? 1 : min(2, nb - 2 * p);
+            f.blended += (int)blx + (int)bly;
+        }
+        f.T = Ty;
+        f.done = stopx || stopy;
     }
 }
 
-// Walk pairs [start, end) for this thread's pixel with the usual batching and block-wide exit.
-template <int TS, bool kTransmittanceOnly, bool kCount>
+// Walk pairs [start, end) for this thread's pixel in staged batches, with a block-wide exit vote
+// per batch.
+template <int TS, bool kTransmittanceOnly, bool kAux, bool kCount>
 __device__ __forceinline__ void walk(const uint32_t* __restrict__ values, const float4* __restrict__ rec,
                                      uint32_t start, uint32_t end, float fx, float fy,
-                                     const CamParams& cam, Frag& f, uint8_t* __restrict__ mark,
-                                     float4* s_a, float4* s_b, float4* s_c) {
-    constexpr int B = TS * TS;
-    for (uint32_t base = start; base < end; base += B) {
-        if (__syncthreads_count(f.done) == B) break;   // also: previous batch fully consumed
-        stage<TS>(values, rec, base + threadIdx.x, end, s_a, s_b, s_c);
+                                     const CamParams& cam, Frag& f, uint8_t* __restrict__ mark, Smem<TS>& sm) {
+    constexpr int B = TS * TS, NB = Smem<TS>::NB;
+    for (uint32_t base = start; base < end; base += NB) {
+        if (__syncthreads_count(f.done) == B) break;   // also: the previous batch is consumed
+        stage<TS>(sm, values, rec, base + threadIdx.x, end);
         __syncthreads();
-        const int nb = (int)min((uint32_t)B, end - base);
-        blend_batch<kTransmittanceOnly, kCount>(s_a, s_b, s_c, nb, fx, fy, cam, f, values, base, mark);
+        const int nb = (int)min((uint32_t)NB, end - base);
+        blend_batch<TS, kTransmittanceOnly, kAux, kCount>(sm, nb, fx, fy, cam, f, values, base, mark);
     }
 }
 
 }  // namespace
 
-// The register cap of a 16 x 16 tile's kernel (launch bound of 4 CTAs per SM) leaves the compiler
-// its 48-register schedule (5 resident CTAs): 1.4 % faster than forcing 6 CTAs at 40 registers.
-template <int TS, bool kCount>
-__global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS) < 4 ? 1536 / (TS * TS) : 4) k_blend(const uint32_t* __restrict__ ranges,
+// CTAs per SM the compositing kernels are compiled for: 4 at 16 x 16 (up to 64 registers a
+// thread), which holds the paired evaluation without spills (at 5, 48 registers spill and the
+// kernel is slower).
+template <int TS>
+constexpr int blend_min_blocks() { return 1536 / (TS * TS) < 4 ? 1536 / (TS * TS) : 4; }
+
+template <int TS, bool kAux, bool kCount>
+__global__ void __launch_bounds__(TS * TS, blend_min_blocks<TS>()) k_blend(const uint32_t* __restrict__ ranges,
                                                   const uint32_t* __restrict__ values,
                                                   const float4* __restrict__ rec, const CamParams* __restrict__ camp,
                                                   float* __restrict__ image, float* __restrict__ final_T,
@@ -138,9 +228,7 @@ __global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS) < 4 ? 1536 / (TS * T
                                                   unsigned long long* __restrict__ evals_out,
                                                   int n_views, float* const* __restrict__ images) {
     constexpr int B = TS * TS;
-    __shared__ float4 s_a[B];
-    __shared__ float4 s_b[B];
-    __shared__ float4 s_c[B];
+    __shared__ Smem<TS> sm;
     if (split_dev) split_len = *split_dev;   // resolved on the device (sync-free batches)
     const int tile = blockIdx.x;
     const int view = n_views > 1 ? tile_view(camp, n_views, tile) : 0;
@@ -152,10 +240,10 @@ __global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS) < 4 ? 1536 / (TS * T
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
     const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
     const bool inside = px < cam.W && py < cam.H;
-    Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, !inside};
-    walk<TS, false, kCount>(values, rec, start, longer ? start + split_len : end, (float)px + 0.5f,
-                    (float)py + 0.5f, cam, f, mark, s_a, s_b, s_c);
-    if (kCount) add_evals(evals_out, f.evals);
+    Frag f(1.0f, !inside);
+    walk<TS, false, kAux, kCount>(values, rec, start, longer ? start + split_len : end, (float)px + 0.5f,
+                            (float)py + 0.5f, cam, f, mark, sm);
+    if (kCount) add_evals(evals_out, f);
     if (longer) {
         const bool all_done = __syncthreads_count(f.done) == B;
         if (threadIdx.x == 0) alive[tile] = all_done ? 0u : 1u;
@@ -210,7 +298,7 @@ __device__ __forceinline__ void chunk_range(const uint32_t* __restrict__ ranges,
 }
 
 template <int TS, bool kCount>
-__global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __restrict__ ranges,
+__global__ void __launch_bounds__(TS * TS, blend_min_blocks<TS>()) k_blend_split_T(const uint32_t* __restrict__ ranges,
                                                           const uint32_t* __restrict__ values,
                                                           const float4* __restrict__ rec, const CamParams* __restrict__ camp,
                                                           const uint2* __restrict__ items,
@@ -222,9 +310,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __rest
                                                           unsigned long long* __restrict__ evals_out,
                                                           int n_views) {
     constexpr int B = TS * TS;
-    __shared__ float4 s_a[B];
-    __shared__ float4 s_b[B];
-    __shared__ float4 s_c[B];
+    __shared__ Smem<TS> sm;
     // persistent: the grid is sized for the GPU, not for the worst-case item count
     const uint32_t n_it = *n_items;
     if (split_dev) split_len = *split_dev;
@@ -238,17 +324,17 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_T(const uint32_t* __rest
         const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
         const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
         const bool stopped = state_tc[(size_t)tile * B + threadIdx.x].w < 0.0f;
-        Frag f{1.0f, 0.0f, 0.0f, 0.0f, 0, stopped || !(px < cam.W && py < cam.H)};
+        Frag f(1.0f, stopped || !(px < cam.W && py < cam.H));
         __syncthreads();   // the previous item's last batch is fully consumed
-        walk<TS, true, kCount>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, nullptr, s_a, s_b,
-                               s_c);
+        walk<TS, true, false, kCount>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, nullptr,
+                                      sm);
         Tch[(size_t)item * B + threadIdx.x] = f.T;
-        if (kCount) add_evals(evals_out, f.evals);
+        if (kCount) add_evals(evals_out, f);
     }
 }
 
-template <int TS, bool kCount>
-__global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __restrict__ ranges,
+template <int TS, bool kAux, bool kCount>
+__global__ void __launch_bounds__(TS * TS, blend_min_blocks<TS>()) k_blend_split_C(const uint32_t* __restrict__ ranges,
                                                           const uint32_t* __restrict__ values,
                                                           const float4* __restrict__ rec, const CamParams* __restrict__ camp,
                                                           const uint2* __restrict__ items,
@@ -262,9 +348,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
                                                           unsigned long long* __restrict__ evals_out,
                                                           int n_views) {
     constexpr int B = TS * TS;
-    __shared__ float4 s_a[B];
-    __shared__ float4 s_b[B];
-    __shared__ float4 s_c[B];
+    __shared__ Smem<TS> sm;
     const uint32_t n_it = *n_items;
     if (split_dev) split_len = *split_dev;
     for (uint32_t item = blockIdx.x; item < n_it; item += gridDim.x) {
@@ -281,14 +365,14 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_C(const uint32_t* __rest
         float T_in = sw < 0.0f ? 0.0f : sw;
         for (uint32_t c = 0; c < it.y; c++) T_in *= Tch[(size_t)(item - it.y + c) * B + threadIdx.x];
         const bool dead = sw < 0.0f || T_in < cam.t_stop;
-        Frag f{T_in, 0.0f, 0.0f, 0.0f, 0, dead || !(px < cam.W && py < cam.H)};
+        Frag f(T_in, dead || !(px < cam.W && py < cam.H));
         __syncthreads();   // the previous item's last batch is fully consumed
-        walk<TS, false, kCount>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, mark, s_a, s_b,
-                                s_c);
+        walk<TS, false, kAux, kCount>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, mark,
+                                      sm);
         // w < 0 marks "stopped inside this chunk or before"
         part[(size_t)item * B + threadIdx.x] = make_float4(f.C0, f.C1, f.C2, (f.done || dead) ? -f.T - 1.0f : f.T);
         pcount[(size_t)item * B + threadIdx.x] = (int32_t)f.last;
-        if (kCount) add_evals(evals_out, f.evals);
+        if (kCount) add_evals(evals_out, f);
     }
 }
 
@@ -356,6 +440,7 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
                             int n_views, float* const* images, int n_tiles) {
     constexpr int B = TS * TS;
     const bool may_split = n_pairs > split_len;
+    const bool aux = n_contrib || mark;   // the last blended pair per pixel, blended survivors
     // carve the scratch; every section starts on a 256-byte boundary
     char* p = static_cast<char*>(scratch);
     uint32_t *n_chunks = nullptr, *first = nullptr, *n_items = nullptr, *alive = nullptr;
@@ -392,7 +477,7 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
         if (e != cudaSuccess) return e;
     }
     NVGS_LAUNCH(log, s, TS == 8 ? "k_blend<8>" : TS == 16 ? "k_blend<16>" : "k_blend<32>",
-                (evals ? k_blend<TS, true> : k_blend<TS, false>)<<<n_tiles, B, 0, s>>>(ranges, values, rec, cam_dev, image, final_T, n_contrib, mark,
+                (evals ? k_blend<TS, true, true> : aux ? k_blend<TS, true, false> : k_blend<TS, false, false>)<<<n_tiles, B, 0, s>>>(ranges, values, rec, cam_dev, image, final_T, n_contrib, mark,
                                                   split_len, split_dev, state_tc, state_cnt, alive, evals, n_views, images));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !may_split) return e;
@@ -403,7 +488,7 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
     // persistent grids: enough CTAs to fill the GPU (the item count lives on the device)
     const unsigned pgrid = (unsigned)std::min<uint64_t>(max_items, (uint64_t)num_sms * (2048 / B));
     NVGS_LAUNCH(log, s, "k_blend_split_T", (evals ? k_blend_split_T<TS, true> : k_blend_split_T<TS, false>)<<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, split_dev, state_tc, Tch, evals, n_views));
-    NVGS_LAUNCH(log, s, "k_blend_split_C", (evals ? k_blend_split_C<TS, true> : k_blend_split_C<TS, false>)<<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, split_dev, state_tc, Tch, part, pcount, mark, evals, n_views));
+    NVGS_LAUNCH(log, s, "k_blend_split_C", (evals ? k_blend_split_C<TS, true, true> : aux ? k_blend_split_C<TS, true, false> : k_blend_split_C<TS, false, false>)<<<pgrid, B, 0, s>>>(ranges, values, rec, cam_dev, items, n_items, split_len, split_dev, state_tc, Tch, part, pcount, mark, evals, n_views));
     NVGS_LAUNCH(log, s, "k_blend_split_D", k_blend_split_D<TS><<<n_tiles, B, 0, s>>>(n_chunks, first, cam_dev, state_tc, state_cnt, part, pcount, image, final_T, n_contrib, n_views, images));
     return cudaGetLastError();
 }

@@ -477,8 +477,8 @@ extern "C" nvgs_status nvgs_create(nvgs_ctx** out, int device, void* cuda_stream
         }
         ctx->own_stream = true;
     }
-    if (ensure(ctx->counters, 64) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_counters, 64) != cudaSuccess) {
+    if (ensure(ctx->counters, 128) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_counters, 128) != cudaSuccess) {
         delete ctx;
         return NVGS_ERR_OOM;
     }
@@ -852,12 +852,13 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
         CK(ensure(ctx->split_scratch, blend_split_scratch_bytes(n_tiles, n_pairs, cp.tile_size, split_len)));
         CK(ensure(ctx->scratch, scan_scratch_bytes(n_tiles)));
     }
-    unsigned long long* evals = f->profile >= 2 ? reinterpret_cast<unsigned long long*>(counters + 10) : nullptr;
-    if (evals) CK(cudaMemsetAsync(evals, 0, 8, s));
+    // profile 2: S6's (pixel, fragment) evaluations and composited fragments in counters[16..19]
+    unsigned long long* evals = f->profile >= 2 ? reinterpret_cast<unsigned long long*>(counters + 16) : nullptr;
+    if (evals) CK(cudaMemsetAsync(evals, 0, 16, s));
     CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, cam_dev, img_dev, fT, nc, mark,
                     split_len, n_pairs, nullptr, ctx->split_scratch.p, ctx->scratch.p, ctx->num_sms, evals,
                     s, &ctx->log));
-    if (evals) CK(cudaMemcpyAsync(ctx->h_counters + 10, counters + 10, 8, cudaMemcpyDeviceToHost, s));
+    if (evals) CK(cudaMemcpyAsync(ctx->h_counters + 16, counters + 16, 16, cudaMemcpyDeviceToHost, s));
     if (labels_row) CK(launch_mark_labels(surv, n_surv, mark, labels_row, s, &ctx->log));
     tm.mark(NVGS_NUM_STAGES);
     if (f->image_memory == NVGS_MEM_HOST)
@@ -891,9 +892,10 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
         stats->kernel_launches = ctx->log.count;
         if (f->profile) {
             if (f->profile >= 2) {
-                uint64_t ev = 0;
-                memcpy(&ev, ctx->h_counters + 10, 8);
-                stats->blend_evaluations = ev;
+                uint64_t ev[2] = {0, 0};
+                memcpy(ev, ctx->h_counters + 16, 16);
+                stats->blend_evaluations = ev[0];
+                stats->blend_composited = ev[1];
             }
             for (int k = 0; k < NVGS_NUM_STAGES; k++) {
                 float ms = 0.f;

@@ -66,7 +66,8 @@ class FrameStats(C.Structure):
                 ("n_mlp_queries", C.c_uint64), ("n_survivors", C.c_uint64),
                 ("n_pairs", C.c_uint64), ("n_instances_visible", C.c_uint32),
                 ("sort_passes", C.c_uint32), ("stage_ms", C.c_float * NVGS_NUM_STAGES),
-                ("kernel_launches", C.c_uint64), ("blend_evaluations", C.c_uint64)]
+                ("kernel_launches", C.c_uint64), ("blend_evaluations", C.c_uint64),
+                ("blend_composited", C.c_uint64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "stage_ms"}

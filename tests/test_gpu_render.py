@@ -82,6 +82,44 @@ def test_profile_levels(cfg1_setup):
     covered = int((c.sum(-1) > 0).sum())
     assert s2["blend_evaluations"] >= covered > 0
     assert s2["blend_evaluations"] <= s2["n_pairs"] * r.flags().tile_size ** 2
+    # at least one composited fragment per covered pixel, at most one per evaluation
+    assert covered <= s2["blend_composited"] <= s2["blend_evaluations"]
+    print(f"evaluations {s2['blend_evaluations']}, composited {s2['blend_composited']}")
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_isolated_needles_lose_no_fragment(tile):
+    """Sparse splats of every orientation with axis ratios up to 1:80 and opacities from 0.005 to
+    0.99, SH colour near 1: most pixels see a few splats at T near 1, so a fragment that the paired
+    compositing dropped, doubled or took out of order (odd list lengths, the padding fragment, a
+    pair's second fragment after the first one stopped) would move a pixel by at least alpha_min x
+    colour (> 3e-3), three times the tolerance."""
+    from helpers import axis_camera, one_asset
+    rng = np.random.default_rng(11)
+    n, W, H, fx = 1500, 256, 192, 200.0
+    z = rng.uniform(2.0, 6.0, n)
+    u, v = rng.uniform(-20, W + 20, n), rng.uniform(-20, H + 20, n)
+    means = np.stack([(u - W / 2) * z / fx, (v - H / 2) * z / fx, z], 1)
+    s_major = rng.uniform(-4.0, -1.5, n)
+    ratio = np.exp(rng.uniform(0.0, math.log(80.0), n))
+    log_scales = np.stack([s_major, s_major - np.log(ratio), s_major - np.log(ratio) - 0.5], 1)
+    quats = rng.normal(size=(n, 4))
+    op = rng.uniform(0.005, 0.99, n)
+    a = one_asset(means, log_scales, quats / np.linalg.norm(quats, axis=1, keepdims=True),
+                  np.log(op / (1 - op)), np.full((n, 1, 3), 1.75))
+    sc = scenes.Scene([a], [scenes.Instance(0, np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 1.0)])
+    cam = axis_camera(W, H, fx=fx)
+    r = renderer_for(sc)
+    try:
+        img, st = gpu_image(r, cam, use_mlp=0, tile_size=tile, profile=2)
+        ref = oracle.render(oracle.OracleScene(sc), cam, oracle_opts_for(dict(tile_size=tile)))
+        err, n_amb = compare_images(img, ref["image"], ref["ambiguous"])
+        covered = int((img.sum(-1) > 0).sum())
+        assert covered > 0.3 * W * H
+        print(f"needles tile {tile}: max err {err:.2e}, {n_amb} ambiguous px; evaluations "
+              f"{st['blend_evaluations']}, composited {st['blend_composited']}")
+    finally:
+        r.close()
 
 
 def test_radius_clipping_matches_the_oracle(cfg1_setup):
