@@ -84,14 +84,12 @@ struct Smem {
     float2 bl[NP];   // (b, b')
 };
 
-// Thread t stages fragment k = base + t (gathered by its survivor index) into slot (t / 2, t % 2);
+// Stages fragment k = base + t of a batch (gathered by its survivor index) into slot (t / 2, t % 2);
 // past the range it stages a fragment of zero opacity, which no pixel composites (the padding of
 // an odd last pair).
 template <int TS>
 __device__ __forceinline__ void stage(Smem<TS>& sm, const uint32_t* __restrict__ values,
-                                      const float4* __restrict__ rec, uint32_t k, uint32_t end) {
-    const int t = threadIdx.x;
-    if (t >= Smem<TS>::NB) return;
+                                      const float4* __restrict__ rec, int t, uint32_t k, uint32_t end) {
     const int p = t >> 1, h = t & 1;
     float* uv = reinterpret_cast<float*>(&sm.uv[p]);
     float* ab = reinterpret_cast<float*>(&sm.ab[p]);
@@ -144,36 +142,34 @@ __device__ __forceinline__ void blend_batch(const Smem<TS>& sm, int nb, float fx
         const float2 p2 = __ffma2_rn(dx, t, __fmul2_rn(__fmul2_rn(make_float2(co.x, co.y), dy), dy));
         const float2 og = __fmul2_rn(make_float2(co.z, co.w), make_float2(ex2_approx(p2.x), ex2_approx(p2.y)));
         const float2 al = make_float2(fminf(cam.alpha_max, og.x), fminf(cam.alpha_max, og.y));
-        const bool okx = !(p2.x > 0.0f) && al.x >= cam.alpha_min;
-        const bool oky = !(p2.y > 0.0f) && al.y >= cam.alpha_min;
-        const float2 om = __ffma2_rn(MINUS, al, ONE);   // 1 - alpha, exactly as the scalar rule
-        if (kTransmittanceOnly) {
-            const float Tx = okx ? f.T * om.x : f.T;
-            const bool dx_ = okx && Tx < cam.t_stop;
-            const float Ty = (!dx_ && oky) ? Tx * om.y : Tx;
+        // alpha of a fragment that passes the tests, else 0 (a passing alpha is >= alpha_min > 0)
+        const float ax = (!(p2.x > 0.0f) && al.x >= cam.alpha_min) ? al.x : 0.0f;
+        const float ay = (!(p2.y > 0.0f) && al.y >= cam.alpha_min) ? al.y : 0.0f;
+        const float2 om = __ffma2_rn(MINUS, make_float2(ax, ay), ONE);   // 1 - alpha, as the scalar rule
+        // T after each (T >= t_stop on entry, and a skipped fragment leaves it as it is): the
+        // first stops iff T (1 - a1) < t_stop, the pair stops (at the first or the second) iff
+        // T (1 - a1) (1 - a2) < t_stop
+        const float ntx = f.T * om.x;
+        const float nty = ntx * om.y;
+        const bool sx = ntx < cam.t_stop, sy = nty < cam.t_stop;
+        if (kTransmittanceOnly) {   // the stopping factor is applied, then the product ends
             if (kCount) {
-                f.walked += dx_ ? 1 : min(2, nb - 2 * p);
-                f.blended += (int)okx + (int)(!dx_ && oky);
+                f.walked += sx ? 1 : min(2, nb - 2 * p);
+                f.blended += (int)(ax > 0.0f) + (int)(!sx && ay > 0.0f);
             }
-            f.done = dx_ || (oky && Ty < cam.t_stop);
-            f.T = Ty;
+            f.T = sx ? ntx : nty;
+            f.done = sy;
             continue;
         }
-        const float ntx = f.T * om.x;
-        const bool stopx = okx && ntx < cam.t_stop;
-        const bool blx = okx && !stopx;
-        const float Tx = blx ? ntx : f.T;
-        const float nty = Tx * om.y;
-        const bool stopy = !stopx && oky && nty < cam.t_stop;
-        const bool bly = !stopx && oky && !stopy;
-        const float Ty = bly ? nty : Tx;
         const float4 rg = sm.rg[p];
         const float2 bl = sm.bl[p];
-        const float2 w = __fmul2_rn(make_float2(blx ? al.x : 0.0f, bly ? al.y : 0.0f), make_float2(f.T, Tx));
+        const float2 w0 = __fmul2_rn(make_float2(ax, ay), make_float2(f.T, ntx));
+        const float wx = sx ? 0.0f : w0.x, wy = sy ? 0.0f : w0.y;   // a stopping fragment is not blended
         // in list order, as the scalar rule (an unblended fragment adds 0 x rgb: C is unchanged)
-        f.C0 = fmaf(w.y, rg.y, fmaf(w.x, rg.x, f.C0));
-        f.C1 = fmaf(w.y, rg.w, fmaf(w.x, rg.z, f.C1));
-        f.C2 = fmaf(w.y, bl.y, fmaf(w.x, bl.x, f.C2));
+        f.C0 = fmaf(wy, rg.y, fmaf(wx, rg.x, f.C0));
+        f.C1 = fmaf(wy, rg.w, fmaf(wx, rg.z, f.C1));
+        f.C2 = fmaf(wy, bl.y, fmaf(wx, bl.x, f.C2));
+        const bool blx = !sx && ax > 0.0f, bly = !sy && ay > 0.0f;
         if (kAux) {
             if (mark) {   // contribution alpha * T > 0 (Sec. 3.1)
                 if (blx) mark[values[base + 2 * p]] = 1;
@@ -182,24 +178,25 @@ __device__ __forceinline__ void blend_batch(const Smem<TS>& sm, int nb, float fx
             f.last = bly ? base + 2 * p + 2 : (blx ? base + 2 * p + 1 : f.last);
         }
         if (kCount) {
-            f.walked += stopx ? 1 : min(2, nb - 2 * p);
+            f.walked += sx ? 1 : min(2, nb - 2 * p);
             f.blended += (int)blx + (int)bly;
         }
-        f.T = Ty;
-        f.done = stopx || stopy;
+        f.T = sy ? (sx ? f.T : ntx) : nty;
+        f.done = sy;
     }
 }
 
-// Walk pairs [start, end) for this thread's pixel in staged batches, with a block-wide exit vote
-// per batch.
-template <int TS, bool kTransmittanceOnly, bool kAux, bool kCount>
+// Walk pairs [start, end) for this thread's pixel in staged batches (the CTA's kThreads threads
+// stage them together), with a block-wide exit vote per batch.
+template <int TS, int kThreads, bool kTransmittanceOnly, bool kAux, bool kCount>
 __device__ __forceinline__ void walk(const uint32_t* __restrict__ values, const float4* __restrict__ rec,
                                      uint32_t start, uint32_t end, float fx, float fy,
                                      const CamParams& cam, Frag& f, uint8_t* __restrict__ mark, Smem<TS>& sm) {
-    constexpr int B = TS * TS, NB = Smem<TS>::NB;
+    constexpr int NB = Smem<TS>::NB;
     for (uint32_t base = start; base < end; base += NB) {
-        if (__syncthreads_count(f.done) == B) break;   // also: the previous batch is consumed
-        stage<TS>(sm, values, rec, base + threadIdx.x, end);
+        if (__syncthreads_count(f.done) == kThreads) break;   // also: the previous batch is consumed
+#pragma unroll
+        for (int t = threadIdx.x; t < NB; t += kThreads) stage<TS>(sm, values, rec, t, base + t, end);
         __syncthreads();
         const int nb = (int)min((uint32_t)NB, end - base);
         blend_batch<TS, kTransmittanceOnly, kAux, kCount>(sm, nb, fx, fy, cam, f, values, base, mark);
@@ -214,8 +211,15 @@ __device__ __forceinline__ void walk(const uint32_t* __restrict__ values, const 
 template <int TS>
 constexpr int blend_min_blocks() { return 1536 / (TS * TS) < 4 ? 1536 / (TS * TS) : 4; }
 
+// CTAs that share one tile in k_blend, each compositing TS / parts full rows of it (all of them
+// stage the tile's whole list): a CTA ends with the last of its own pixels, so that a tile whose
+// rows saturate at different depths frees part of its SM early.
+template <int TS>
+constexpr int blend_parts() { return 1; }
+constexpr int kMaxBlendParts = 4;
+
 template <int TS, bool kAux, bool kCount>
-__global__ void __launch_bounds__(TS * TS, blend_min_blocks<TS>()) k_blend(const uint32_t* __restrict__ ranges,
+__global__ void __launch_bounds__(TS * TS / blend_parts<TS>(), 4 * blend_parts<TS>()) k_blend(const uint32_t* __restrict__ ranges,
                                                   const uint32_t* __restrict__ values,
                                                   const float4* __restrict__ rec, const CamParams* __restrict__ camp,
                                                   float* __restrict__ image, float* __restrict__ final_T,
@@ -227,10 +231,11 @@ __global__ void __launch_bounds__(TS * TS, blend_min_blocks<TS>()) k_blend(const
                                                   uint32_t* __restrict__ alive,
                                                   unsigned long long* __restrict__ evals_out,
                                                   int n_views, float* const* __restrict__ images) {
-    constexpr int B = TS * TS;
+    constexpr int B = TS * TS, P = blend_parts<TS>(), kThreads = B / P;
     __shared__ Smem<TS> sm;
     if (split_dev) split_len = *split_dev;   // resolved on the device (sync-free batches)
-    const int tile = blockIdx.x;
+    const int tile = blockIdx.x / P, part = blockIdx.x % P;
+    const int li = part * kThreads + threadIdx.x;   // the pixel within the tile
     const int view = n_views > 1 ? tile_view(camp, n_views, tile) : 0;
     const CamParams cam = camp[view];
     if (images) image = images[view];
@@ -238,19 +243,18 @@ __global__ void __launch_bounds__(TS * TS, blend_min_blocks<TS>()) k_blend(const
     const bool longer = end - start > split_len;
     const int lt = tile - cam.tile_base;   // the tile within its view
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
+    const int px = tx * TS + (li % TS), py = ty * TS + (li / TS);
     const bool inside = px < cam.W && py < cam.H;
     Frag f(1.0f, !inside);
-    walk<TS, false, kAux, kCount>(values, rec, start, longer ? start + split_len : end, (float)px + 0.5f,
+    walk<TS, kThreads, false, kAux, kCount>(values, rec, start, longer ? start + split_len : end, (float)px + 0.5f,
                             (float)py + 0.5f, cam, f, mark, sm);
     if (kCount) add_evals(evals_out, f);
     if (longer) {
-        const bool all_done = __syncthreads_count(f.done) == B;
-        if (threadIdx.x == 0) alive[tile] = all_done ? 0u : 1u;
-        if (!all_done) {   // the chunked kernels finish this tile
-            state_tc[(size_t)tile * B + threadIdx.x] =
-                make_float4(f.C0, f.C1, f.C2, f.done ? -f.T - 1.0f : f.T);
-            state_cnt[(size_t)tile * B + threadIdx.x] = (int32_t)f.last;
+        const bool all_done = __syncthreads_count(f.done) == kThreads;
+        if (threadIdx.x == 0) alive[(size_t)tile * kMaxBlendParts + part] = all_done ? 0u : 1u;
+        if (!all_done) {   // the chunked kernels finish this part of the tile
+            state_tc[(size_t)tile * B + li] = make_float4(f.C0, f.C1, f.C2, f.done ? -f.T - 1.0f : f.T);
+            state_cnt[(size_t)tile * B + li] = (int32_t)f.last;
             return;
         }
     }
@@ -274,13 +278,15 @@ __global__ void k_split_auto(const uint32_t* __restrict__ n_pairs, uint32_t n_ti
 }
 
 __global__ void k_split_count(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ alive,
-                              int n_tiles, uint32_t split_len, const uint32_t* __restrict__ split_dev,
+                              int parts, int n_tiles, uint32_t split_len, const uint32_t* __restrict__ split_dev,
                               uint32_t* __restrict__ n_chunks) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
     if (split_dev) split_len = *split_dev;
     const uint32_t n = ranges[2 * t + 1] - ranges[2 * t];
-    n_chunks[t] = (n > split_len && alive[t]) ? (n - split_len + split_len - 1) / split_len : 0u;
+    bool any = false;   // some part of the tile is still unsaturated
+    for (int q = 0; q < parts; q++) any = any || alive[(size_t)t * kMaxBlendParts + q] != 0u;
+    n_chunks[t] = (n > split_len && any) ? (n - split_len + split_len - 1) / split_len : 0u;
 }
 
 __global__ void k_split_fill(const uint32_t* __restrict__ n_chunks, const uint32_t* __restrict__ first,
@@ -326,7 +332,7 @@ __global__ void __launch_bounds__(TS * TS, blend_min_blocks<TS>()) k_blend_split
         const bool stopped = state_tc[(size_t)tile * B + threadIdx.x].w < 0.0f;
         Frag f(1.0f, stopped || !(px < cam.W && py < cam.H));
         __syncthreads();   // the previous item's last batch is fully consumed
-        walk<TS, true, false, kCount>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, nullptr,
+        walk<TS, TS * TS, true, false, kCount>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, nullptr,
                                       sm);
         Tch[(size_t)item * B + threadIdx.x] = f.T;
         if (kCount) add_evals(evals_out, f);
@@ -367,7 +373,7 @@ __global__ void __launch_bounds__(TS * TS, blend_min_blocks<TS>()) k_blend_split
         const bool dead = sw < 0.0f || T_in < cam.t_stop;
         Frag f(T_in, dead || !(px < cam.W && py < cam.H));
         __syncthreads();   // the previous item's last batch is fully consumed
-        walk<TS, false, kAux, kCount>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, mark,
+        walk<TS, TS * TS, false, kAux, kCount>(values, rec, start, end, (float)px + 0.5f, (float)py + 0.5f, cam, f, mark,
                                       sm);
         // w < 0 marks "stopped inside this chunk or before"
         part[(size_t)item * B + threadIdx.x] = make_float4(f.C0, f.C1, f.C2, (f.done || dead) ? -f.T - 1.0f : f.T);
@@ -426,7 +432,7 @@ static inline uint64_t round256(uint64_t b) { return (b + 255) / 256 * 256; }
 size_t blend_split_scratch_bytes(int n_tiles, uint64_t n_pairs, int tile_size, uint32_t split_len) {
     const uint64_t items = n_pairs / split_len + 2;
     const uint64_t B = (uint64_t)tile_size * tile_size;
-    return (size_t)(round256((uint64_t)n_tiles * 12 + 64) + round256((uint64_t)n_tiles * B * 16) +
+    return (size_t)(round256((uint64_t)n_tiles * (8 + 4 * kMaxBlendParts) + 64) + round256((uint64_t)n_tiles * B * 16) +
                     round256((uint64_t)n_tiles * B * 4) + round256(items * 8) + round256(items * B * 4) +
                     round256(items * B * 16) + round256(items * B * 4));
 }
@@ -455,10 +461,10 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
     if (may_split) {
         n_chunks = reinterpret_cast<uint32_t*>(p);
         first = n_chunks + n_tiles;
-        alive = first + n_tiles;
-        n_items = alive + n_tiles;
+        alive = first + n_tiles;   // per tile, one flag per part
+        n_items = alive + (size_t)n_tiles * kMaxBlendParts;
         if (auto_split_pairs) split_dev = n_items + 1;   // inside the region's 64 spare bytes
-        p += round256((uint64_t)n_tiles * 12 + 64);
+        p += round256((uint64_t)n_tiles * (8 + 4 * kMaxBlendParts) + 64);
         state_tc = reinterpret_cast<float4*>(p);
         p += round256((uint64_t)n_tiles * B * 16);
         state_cnt = reinterpret_cast<int32_t*>(p);
@@ -477,11 +483,11 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
         if (e != cudaSuccess) return e;
     }
     NVGS_LAUNCH(log, s, TS == 8 ? "k_blend<8>" : TS == 16 ? "k_blend<16>" : "k_blend<32>",
-                (evals ? k_blend<TS, true, true> : aux ? k_blend<TS, true, false> : k_blend<TS, false, false>)<<<n_tiles, B, 0, s>>>(ranges, values, rec, cam_dev, image, final_T, n_contrib, mark,
+                (evals ? k_blend<TS, true, true> : aux ? k_blend<TS, true, false> : k_blend<TS, false, false>)<<<n_tiles * blend_parts<TS>(), B / blend_parts<TS>(), 0, s>>>(ranges, values, rec, cam_dev, image, final_T, n_contrib, mark,
                                                   split_len, split_dev, state_tc, state_cnt, alive, evals, n_views, images));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !may_split) return e;
-    NVGS_LAUNCH(log, s, "k_split_count", k_split_count<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, alive, n_tiles, split_len, split_dev, n_chunks));
+    NVGS_LAUNCH(log, s, "k_split_count", k_split_count<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, alive, blend_parts<TS>(), n_tiles, split_len, split_dev, n_chunks));
     e = exclusive_scan_u32(n_chunks, first, n_tiles, n_items, scan_scratch, s, log);
     if (e != cudaSuccess) return e;
     NVGS_LAUNCH(log, s, "k_split_fill", k_split_fill<<<(n_tiles + 255) / 256, 256, 0, s>>>(n_chunks, first, n_tiles, items));
