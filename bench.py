@@ -236,20 +236,23 @@ def kernel_frame_work(name, fr, sh_stride_floats, W, H, tile):
     dpasses = 4 if ns > 1 else 0                       # survivors: 32-bit depth keys
     tpasses = max(0, fr["sort_passes"] - dpasses)      # pairs: tile-id keys
     if name == "k_project":
-        return "hbm", ns * (8 + 16 + 16 + 16 + 4 * sh_stride_floats + 48 + 16 + 4 + 8)
+        # list entry, mean, scale, quaternion, SH read; 64-byte record, count, depth key + index
+        return "hbm", ns * (8 + 16 + 16 + 16 + 4 * sh_stride_floats + 64 + 4 + 8)
     if name.startswith("k_blend"):
         # ALU-bound: FP32 work of the (pixel, fragment) evaluations (profiled frames count them):
         # offsets 2, exponent 9 (3 mul + 2 FMA + 2 mul... with FMA as 2), exp2 argument 1 + ex2 1,
         # alpha 2 = 15 flops up to the alpha test
         if fr.get("blend_evaluations"):
             return "alu", fr["blend_evaluations"] * BLEND_FLOPS_PER_EVAL
-        return "hbm", npairs * (4 + 48) + W * H * 12 + n_tiles * 8
+        return "hbm", npairs * (4 + 48) + W * H * 12 + n_tiles * 8   # value + 48 record bytes
     if name == "k_rs_scatter<u32>":                    # read and write key + value per pass
         return "hbm", 16 * (dpasses * ns + tpasses * npairs)
     if name == "k_rs_hist<u32>":
         return "hbm", 4 * (dpasses * ns + tpasses * npairs)
     if name == "k_duplicate":
-        return "hbm", ns * (4 + 16 + 4) + npairs * 8
+        # depth order, the record's rectangle and splat fields (48 of its 64 bytes), offset;
+        # key + value per pair
+        return "hbm", ns * (4 + 48 + 4) + npairs * 8
     if name == "k_tile_ranges":
         return "hbm", n_tiles * 8
     if name == "k_frustum":

@@ -429,9 +429,10 @@ nvgs_status nvgs_device_bytes(const nvgs_ctx* ctx, uint64_t* bytes);
  * (S4), sorted pair values and per-tile ranges (S5). */
 typedef struct {
     const uint32_t* survivors;   /* 2 x n_survivors: (instance, gaussian) */
-    const float* records;        /* 12 x n_survivors: u, v, conic a, b, c, opacity, depth,
-                                    ln(alpha_min / opacity), r, g, b, det Sigma_2D */
-    const int32_t* tile_rects;   /* 4 x n_survivors: tile x0, y0, x1, y1 (inclusive) */
+    const float* records;        /* 16 x n_survivors: u, v, conic a, b, c, opacity, det Sigma_2D,
+                                    ln(alpha_min / opacity), r, g, b, depth, then the tile
+                                    rectangle x0, y0, x1, y1 (inclusive) as int32 bits */
+    const int32_t* tile_rects;   /* the rectangles inside the records: 4 int32 every 16 */
     const uint32_t* pair_values; /* n_pairs survivor indices in (tile, depth) order */
     const uint32_t* pair_keys;   /* n_pairs tile ids of those pairs (non-decreasing) */
     const uint32_t* tile_ranges; /* 2 x n_tiles: [start, end) into pair_values */

@@ -69,9 +69,9 @@ __global__ void __launch_bounds__(TS* TS) k_blend_bwd(const uint32_t* __restrict
         if (k < hi) {
             const uint32_t id = values[k];
             s_id[threadIdx.x] = id;
-            s_a[threadIdx.x] = __ldg(&rec[3 * (size_t)id]);
-            s_b[threadIdx.x] = __ldg(&rec[3 * (size_t)id + 1]);
-            s_c[threadIdx.x] = __ldg(&rec[3 * (size_t)id + 2]);
+            s_a[threadIdx.x] = __ldg(&rec[kRecF4 * (size_t)id]);
+            s_b[threadIdx.x] = __ldg(&rec[kRecF4 * (size_t)id + 1]);
+            s_c[threadIdx.x] = __ldg(&rec[kRecF4 * (size_t)id + 2]);
         }
         __syncthreads();
         for (int j = (int)(hi - lo) - 1; j >= 0; j--) {

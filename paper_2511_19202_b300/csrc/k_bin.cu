@@ -54,7 +54,6 @@ __device__ __forceinline__ int warp_owner(uint32_t pre, uint32_t c) {
 // pair key is that view's tile_base plus its local tile id.
 template <bool kMV>
 __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ order,
-                                                   const int4* __restrict__ rects,
                                                    const float4* __restrict__ rec,
                                                    const uint32_t* __restrict__ offsets, uint32_t n,
                                                    const uint32_t* __restrict__ n_dev,
@@ -79,7 +78,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
         bool test = false;
         if (k < n) {
             i = order[k];
-            r = rects[i];
+            r = rec_rect(rec, i);
             if (kMV) {
                 const CamParams& cv = camp[r.w >> 16];
                 tiles_x = cv.tiles_x;
@@ -90,10 +89,10 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
                 rows = (uint32_t)(r.w - r.y + 1);
                 test = (r.z - r.x + 1) * (int)rows > 1;
                 if (test) {
-                    const float4 a = rec[3 * (size_t)i];
-                    const float4 b = rec[3 * (size_t)i + 1];
+                    const float4 a = __ldg(&rec[kRecF4 * (size_t)i]);
+                    const float4 b = __ldg(&rec[kRecF4 * (size_t)i + 1]);
                     u = a.x; v = a.y; A = a.z; B = a.w; C = b.x; kk = -2.0f * b.w;
-                    det = rec[3 * (size_t)i + 2].w;
+                    det = b.z;
                 }
             }
         }
@@ -150,7 +149,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
     }
 }
 
-cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const float4* rec,
+cudaError_t launch_duplicate(const uint32_t* order, const float4* rec,
                              const uint32_t* offsets, uint32_t n, const uint32_t* n_dev,
                              const CamParams* cam_dev, const uint32_t* n_pairs, uint32_t pair_cap,
                              uint32_t* overflow, uint32_t* keys, uint32_t* values, int num_sms,
@@ -172,9 +171,9 @@ cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const flo
     const uint32_t warps = (n + 31) / 32;
     const uint32_t grid = std::min<uint32_t>((warps + 7) / 8, (uint32_t)(num_sms * per_sm));
     if (multi_view)
-        NVGS_LAUNCH(log, s, "k_duplicate_views", k_duplicate<true><<<grid, 256, 0, s>>>(order, rects, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, keys, values));
+        NVGS_LAUNCH(log, s, "k_duplicate_views", k_duplicate<true><<<grid, 256, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, keys, values));
     else
-        NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<false><<<grid, 256, 0, s>>>(order, rects, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, keys, values));
+        NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<false><<<grid, 256, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, keys, values));
     return cudaGetLastError();
 }
 

@@ -97,7 +97,7 @@ __device__ __forceinline__ void stage(Smem<TS>& sm, const uint32_t* __restrict__
     float* rg = reinterpret_cast<float*>(&sm.rg[p]);
     float* bl = reinterpret_cast<float*>(&sm.bl[p]);
     if (k < end) {
-        const size_t idx = 3 * (size_t)values[k];
+        const size_t idx = kRecF4 * (size_t)values[k];
         float4 sa, sb;
         stage_splat(__ldg(&rec[idx]), __ldg(&rec[idx + 1]), sa, sb);
         const float4 c = __ldg(&rec[idx + 2]);

@@ -2,8 +2,9 @@
 // (NVGS Sec. 3.3 hands the survivors to the original 3DGS tiled pipeline).
 //
 // One thread per survivor.  Per survivor it reads 16 B mean/opacity + 16 B log-scale + 16 B
-// quaternion + 16..192 B of SH (all 16-byte vector loads) and writes one 48-byte record, a
-// 16-byte tile rectangle and a 4-byte tile count.
+// quaternion + 16..192 B of SH (all 16-byte vector loads) and writes one 64-byte record (the
+// splat with its 16-byte tile rectangle, one aligned 64-byte access for the depth-ordered
+// gathers of the binning and the compositing), a 4-byte tile count and the depth sort's key.
 //
 // Conventions (3DGS):  Sigma = R(q) diag(e^{2 ls}) R(q)^T;  Sigma_cam = s^2 W Sigma W^T with
 // W = R_cam R_inst;  J is the pinhole Jacobian at the mean with x/z, y/z clamped to the guard
@@ -24,7 +25,7 @@ __global__ void __launch_bounds__(256, 4) k_project(const uint2* __restrict__ su
                                                  const uint32_t* __restrict__ n_dev,
                                                  const FrameInst* __restrict__ fis,
                                                  const AssetDev* __restrict__ assets, const CamParams* __restrict__ camp,
-                                                 float4* __restrict__ rec, int4* __restrict__ rects,
+                                                 float4* __restrict__ rec,
                                                  uint32_t* __restrict__ counts,
                                                  uint32_t* __restrict__ dkey,
                                                  uint32_t* __restrict__ didx) {
@@ -111,13 +112,15 @@ __global__ void __launch_bounds__(256, 4) k_project(const uint2* __restrict__ su
             }
         }
         if (kMV) r.w |= fi.view << 16;
-        rects[i] = r;
         counts[i] = cnt;
         dkey[i] = __float_as_uint(z);   // z > z_near > 0: the bit pattern orders like the value
         didx[i] = i;
-        rec[3 * (size_t)i] = make_float4(u, v, cA, cB);
+        float4* out = rec + kRecF4 * (size_t)i;
+        out[0] = make_float4(u, v, cA, cB);
+        // z: det Sigma_2D (the binning's row spans recover Sigma_2D from it and the conic);
         // w: ln(alpha_min / opacity), the exponent below which a fragment cannot reach alpha_min
-        rec[3 * (size_t)i + 1] = make_float4(cC, op, z, kw);
+        out[1] = make_float4(cC, op, det, kw);
+        reinterpret_cast<int4*>(out)[3] = r;
 
         // colour at the local-frame direction from the camera to the mean; the coefficients are
         // streamed 16 bytes at a time (coefficient j / 3, channel j % 3 of float j)
@@ -141,23 +144,21 @@ __global__ void __launch_bounds__(256, 4) k_project(const uint2* __restrict__ su
                 }
             }
         }
-        // w: det Sigma_2D (the binning's row spans recover Sigma_2D from it and the conic)
-        rec[3 * (size_t)i + 2] = make_float4(fmaxf(col[0], 0.0f), fmaxf(col[1], 0.0f),
-                                             fmaxf(col[2], 0.0f), det);
+        out[2] = make_float4(fmaxf(col[0], 0.0f), fmaxf(col[1], 0.0f), fmaxf(col[2], 0.0f), z);
     }
 }
 
 cudaError_t launch_project(const uint2* surv, uint32_t n, const uint32_t* n_dev, const FrameInst* fi,
-                           const AssetDev* assets, const CamParams* cam_dev, float4* rec, int4* rects,
+                           const AssetDev* assets, const CamParams* cam_dev, float4* rec,
                            uint32_t* tile_counts, uint32_t* dkey, uint32_t* didx, int num_sms,
                            cudaStream_t s, LaunchLog* log, int multi_view) {
     if (n == 0) return cudaSuccess;
     // grid-stride over two waves of the four resident CTAs per SM
     const uint32_t grid = std::min<uint32_t>((n + 255) / 256, (uint32_t)num_sms * 4 * 2);
     if (multi_view)
-        NVGS_LAUNCH(log, s, "k_project_views", k_project<true><<<grid, 256, 0, s>>>(surv, n, n_dev, fi, assets, cam_dev, rec, rects, tile_counts, dkey, didx));
+        NVGS_LAUNCH(log, s, "k_project_views", k_project<true><<<grid, 256, 0, s>>>(surv, n, n_dev, fi, assets, cam_dev, rec, tile_counts, dkey, didx));
     else
-        NVGS_LAUNCH(log, s, "k_project", k_project<false><<<grid, 256, 0, s>>>(surv, n, n_dev, fi, assets, cam_dev, rec, rects, tile_counts, dkey, didx));
+        NVGS_LAUNCH(log, s, "k_project", k_project<false><<<grid, 256, 0, s>>>(surv, n, n_dev, fi, assets, cam_dev, rec, tile_counts, dkey, didx));
     return cudaGetLastError();
 }
 

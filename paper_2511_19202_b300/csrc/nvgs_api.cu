@@ -51,7 +51,7 @@ struct nvgs_ctx {
 
     // per-frame buffers
     DevBuf frame_inst, bits, chunk_counts, chunk_offsets, vis_list, keep_bits, logits_tmp,
-        block_counts, block_offsets, surv, rec, rects, tile_counts, tile_offsets, keys, vals,
+        block_counts, block_offsets, surv, rec, tile_counts, tile_offsets, keys, vals,
         keys_alt, vals_alt, ranges, scratch, counters, image_tmp, final_T, n_contrib, mark, dkey,
         didx, dkey_alt, didx_alt, split_scratch, vis_mean, grad_surv;
     // visibility-MLP training state, per asset (FP32 master weights, Adam moments, views)
@@ -497,7 +497,7 @@ extern "C" nvgs_status nvgs_destroy(nvgs_ctx* ctx) {
     DevBuf* bufs[] = {&ctx->assets_dev, &ctx->inst_raw, &ctx->inst_offset, &ctx->chunks,
                       &ctx->frame_inst, &ctx->bits, &ctx->chunk_counts, &ctx->chunk_offsets,
                       &ctx->vis_list, &ctx->keep_bits, &ctx->logits_tmp, &ctx->block_counts,
-                      &ctx->block_offsets, &ctx->surv, &ctx->rec, &ctx->rects, &ctx->tile_counts,
+                      &ctx->block_offsets, &ctx->surv, &ctx->rec, &ctx->tile_counts,
                       &ctx->tile_offsets, &ctx->keys, &ctx->vals, &ctx->keys_alt, &ctx->vals_alt,
                       &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
                       &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial,
@@ -768,8 +768,7 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     // ---- S4
     tm.mark(NVGS_STAGE_PROJECT);
     const uint64_t cap = (uint64_t)ctx->n_instanced;
-    CK(ensure(ctx->rec, cap * 48 + 48));
-    CK(ensure(ctx->rects, cap * 16 + 16));
+    CK(ensure(ctx->rec, cap * 64 + 64));
     CK(ensure(ctx->tile_counts, cap * 4 + 16));
     CK(ensure(ctx->tile_offsets, cap * 4 + 16));
     CK(ensure(ctx->dkey, cap * 4 + 16));
@@ -779,7 +778,7 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     CK(ensure(ctx->scratch, std::max({scan_scratch_bytes(ctx->n_chunks), scan_scratch_bytes(cap + 1),
                                       radix_scratch_bytes(n_surv)})));
     CK(launch_project(surv, n_surv, nullptr, P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev), cam_dev,
-                      P<float4>(ctx->rec), P<int4>(ctx->rects), P<uint32_t>(ctx->tile_counts),
+                      P<float4>(ctx->rec), P<uint32_t>(ctx->tile_counts),
                       P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), ctx->num_sms, s, &ctx->log));
 
     // ---- S5: survivors by depth, pairs in that order, pairs by tile, tile ranges
@@ -805,7 +804,7 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     CK(ensure(ctx->vals_alt, (size_t)n_pairs * 4 + 16));
     CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
     if (radix_scratch_bytes(n_pairs) > ctx->scratch.cap) CK(ensure(ctx->scratch, radix_scratch_bytes(n_pairs)));
-    CK(launch_duplicate(order, P<int4>(ctx->rects), P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
+    CK(launch_duplicate(order, P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
                         n_surv, nullptr, cam_dev, counters + 2, n_pairs, nullptr, P<uint32_t>(ctx->keys),
                         P<uint32_t>(ctx->vals), ctx->num_sms, s, &ctx->log));
     tm.mark(NVGS_STAGE_SORT);
@@ -869,7 +868,7 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     nvgs_frame_view& L = ctx->last;
     L.survivors = reinterpret_cast<const uint32_t*>(surv);
     L.records = P<float>(ctx->rec);
-    L.tile_rects = P<int32_t>(ctx->rects);
+    L.tile_rects = P<int32_t>(ctx->rec) + 12;   // inside the records, 16 int32 apart
     L.pair_values = svals;
     L.pair_keys = skeys;
     L.tile_ranges = P<uint32_t>(ctx->ranges);
@@ -1236,8 +1235,7 @@ static nvgs_status enqueue_view_async(nvgs_ctx* ctx, const CamParams& cp, const 
     const uint2* surv = f->use_mlp ? P<uint2>(ctx->surv) : P<uint2>(ctx->vis_list);
     const uint32_t* n_surv_dev = f->use_mlp ? &counters[1] : &counters[0];
     // S4
-    CK(ensure(ctx->rec, cap * 48 + 48));
-    CK(ensure(ctx->rects, cap * 16 + 16));
+    CK(ensure(ctx->rec, cap * 64 + 64));
     CK(ensure(ctx->tile_counts, cap * 4 + 16));
     CK(ensure(ctx->tile_offsets, cap * 4 + 16));
     CK(ensure(ctx->dkey, cap * 4 + 16));
@@ -1247,7 +1245,7 @@ static nvgs_status enqueue_view_async(nvgs_ctx* ctx, const CamParams& cp, const 
     CK(ensure(ctx->scratch, std::max({scan_scratch_bytes(ctx->n_chunks), scan_scratch_bytes(cap + 1),
                                       radix_scratch_bytes(cap), radix_scratch_bytes(pair_cap)})));
     CK(launch_project(surv, (uint32_t)cap, n_surv_dev, P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev),
-                      cam_dev, P<float4>(ctx->rec), P<int4>(ctx->rects), P<uint32_t>(ctx->tile_counts),
+                      cam_dev, P<float4>(ctx->rec), P<uint32_t>(ctx->tile_counts),
                       P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), ctx->num_sms, s, &ctx->log));
     // S5
     int dpasses = 0, d_alt = 0;
@@ -1266,7 +1264,7 @@ static nvgs_status enqueue_view_async(nvgs_ctx* ctx, const CamParams& cp, const 
     CK(ensure(ctx->keys_alt, (size_t)pair_cap * 4 + 16));
     CK(ensure(ctx->vals_alt, (size_t)pair_cap * 4 + 16));
     CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
-    CK(launch_duplicate(order, P<int4>(ctx->rects), P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
+    CK(launch_duplicate(order, P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
                         (uint32_t)cap, n_surv_dev, cam_dev, counters + 2, (uint32_t)pair_cap, counters + 9,
                         P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), ctx->num_sms, s, &ctx->log));
     int passes = 0, in_alt = 0;
@@ -1419,8 +1417,7 @@ static nvgs_status enqueue_views(nvgs_ctx* ctx, const CullScope& scope, const Ca
     const uint2* surv = f->use_mlp ? P<uint2>(ctx->surv) : P<uint2>(ctx->vis_list);
     const uint32_t* n_surv_dev = f->use_mlp ? &counters[1] : &counters[0];
     // S4
-    CK(ensure(ctx->rec, cap * 48 + 48));
-    CK(ensure(ctx->rects, cap * 16 + 16));
+    CK(ensure(ctx->rec, cap * 64 + 64));
     CK(ensure(ctx->tile_counts, cap * 4 + 16));
     CK(ensure(ctx->tile_offsets, cap * 4 + 16));
     CK(ensure(ctx->dkey, cap * 4 + 16));
@@ -1431,7 +1428,7 @@ static nvgs_status enqueue_views(nvgs_ctx* ctx, const CullScope& scope, const Ca
                                       radix_scratch_bytes(cap), radix_scratch_bytes(pair_cap),
                                       scan_scratch_bytes((uint64_t)n_tiles)})));
     CK(launch_project(surv, (uint32_t)cap, n_surv_dev, P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev),
-                      cam_dev, P<float4>(ctx->rec), P<int4>(ctx->rects), P<uint32_t>(ctx->tile_counts),
+                      cam_dev, P<float4>(ctx->rec), P<uint32_t>(ctx->tile_counts),
                       P<uint32_t>(ctx->dkey), P<uint32_t>(ctx->didx), ctx->num_sms, s, &ctx->log, 1));
     // S5: every survivor of the batch by depth, the pairs in that order with global tile ids, the
     // pairs by tile id
@@ -1450,7 +1447,7 @@ static nvgs_status enqueue_views(nvgs_ctx* ctx, const CullScope& scope, const Ca
     CK(ensure(ctx->keys_alt, (size_t)pair_cap * 4 + 16));
     CK(ensure(ctx->vals_alt, (size_t)pair_cap * 4 + 16));
     CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
-    CK(launch_duplicate(order, P<int4>(ctx->rects), P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
+    CK(launch_duplicate(order, P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
                         (uint32_t)cap, n_surv_dev, cam_dev, counters + 2, (uint32_t)pair_cap, counters + 9,
                         P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), ctx->num_sms, s, &ctx->log, 1));
     int passes = 0, in_alt = 0;
@@ -1675,7 +1672,7 @@ extern "C" nvgs_status nvgs_device_bytes(const nvgs_ctx* ctx, uint64_t* bytes) {
     const DevBuf* bufs[] = {&ctx->assets_dev, &ctx->inst_raw, &ctx->inst_offset, &ctx->chunks,
                             &ctx->frame_inst, &ctx->bits, &ctx->chunk_counts, &ctx->chunk_offsets,
                             &ctx->vis_list, &ctx->keep_bits, &ctx->logits_tmp, &ctx->block_counts,
-                            &ctx->block_offsets, &ctx->surv, &ctx->rec, &ctx->rects, &ctx->tile_counts,
+                            &ctx->block_offsets, &ctx->surv, &ctx->rec, &ctx->tile_counts,
                             &ctx->tile_offsets, &ctx->keys, &ctx->vals, &ctx->keys_alt, &ctx->vals_alt,
                             &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
                             &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial,

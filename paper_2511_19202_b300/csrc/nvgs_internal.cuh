@@ -335,11 +335,22 @@ cudaError_t launch_scatter_visibility(const uint2* list, uint32_t n, const uint3
                                       const FrameInst* fi, float* out_logits, uint8_t* out_keep,
                                       cudaStream_t s, LaunchLog* log);
 
-// S4: records, tile rects and counts; dkey / didx receive the depth sort keys (IEEE bits of
-// the camera-space z) and the survivor indices 0..n-1.  multi_view: each survivor's camera is
-// cam_dev[its frame instance's view], and the rect's w holds the last tile row | view << 16.
+// Projected splat record: kRecF4 float4 = 64 bytes per survivor, so that one aligned 64-byte
+// access fetches all of it (the binning and the compositing gather records in depth order):
+//   [0] u, v, conic A, conic B
+//   [1] conic C, opacity, det Sigma_2D, ln(alpha_min / opacity)
+//   [2] r, g, b, camera-space depth
+//   [3] tile rectangle x0, y0, x1, y1 (inclusive; int bits; multi-view: w | view << 16)
+constexpr int kRecF4 = 4;
+__device__ __forceinline__ int4 rec_rect(const float4* __restrict__ rec, size_t i) {
+    return __ldg(reinterpret_cast<const int4*>(rec) + kRecF4 * i + 3);
+}
+
+// S4: records (with their tile rects) and tile counts; dkey / didx receive the depth sort keys
+// (IEEE bits of the camera-space z) and the survivor indices 0..n-1.  multi_view: each survivor's
+// camera is cam_dev[its frame instance's view], and the rect's w holds the last tile row | view << 16.
 cudaError_t launch_project(const uint2* surv, uint32_t n, const uint32_t* n_dev, const FrameInst* fi,
-                           const AssetDev* assets, const CamParams* cam_dev, float4* rec, int4* rects,
+                           const AssetDev* assets, const CamParams* cam_dev, float4* rec,
                            uint32_t* tile_counts, uint32_t* dkey, uint32_t* didx, int num_sms,
                            cudaStream_t s, LaunchLog* log, int multi_view = 0);
 
@@ -352,7 +363,7 @@ cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* counts, 
 // overflow (device, nullable) is set when the total exceeds it.
 // multi_view: tile ids are global (the view's tile_base + its local tile id), the view taken
 // from the rect (as launch_project writes it in multi-view mode).
-cudaError_t launch_duplicate(const uint32_t* order, const int4* rects, const float4* rec,
+cudaError_t launch_duplicate(const uint32_t* order, const float4* rec,
                              const uint32_t* offsets, uint32_t n, const uint32_t* n_dev,
                              const CamParams* cam_dev, const uint32_t* n_pairs, uint32_t pair_cap,
                              uint32_t* overflow, uint32_t* keys, uint32_t* values, int num_sms,

@@ -121,10 +121,11 @@ class Renderer:
             self.stream.synchronize()
             return torch.as_tensor(view, device=self.device).clone()
 
+        rec = grab(v.records, 16 * ns, torch.float32).view(-1, 16)
         out = dict(
             survivors=grab(v.survivors, 2 * ns, torch.int32).view(-1, 2),
-            records=grab(v.records, 12 * ns, torch.float32).view(-1, 12),
-            tile_rects=grab(v.tile_rects, 4 * ns, torch.int32).view(-1, 4),
+            records=rec,
+            tile_rects=rec[:, 12:].contiguous().view(torch.int32),   # stored inside the records
             pair_values=grab(v.pair_values, npairs, torch.int32),
             pair_keys=grab(v.pair_keys, npairs, torch.int32),
             tile_ranges=grab(v.tile_ranges, 2 * n_tiles, torch.int32).view(-1, 2),

@@ -187,14 +187,14 @@ def test_tile_lists_are_exact(cfg1_setup, tile):
     lf = r.last_frame()
     vals = lf["pair_values"].cpu().numpy().astype(np.int64)
     surv = lf["survivors"].cpu().numpy()
-    rec = lf["records"].cpu().numpy().reshape(-1, 12)
+    rec = lf["records"].cpu().numpy().reshape(-1, 16)
     gpu_tiles = lf["pair_keys"].cpu().numpy().astype(np.int64)
     assert np.all(np.diff(gpu_tiles) >= 0)
     sp = oracle.project(osc, cam, o)
     ell = oracle.tile_lists_ellipse(sp, cam, tile)
     drop = set(zip(sp["instance"][sp["ambiguous"] != 0].tolist(), sp["gaussian"][sp["ambiguous"] != 0].tolist()))
     depth_of = dict(zip(zip(sp["instance"].tolist(), sp["gaussian"].tolist()), sp["depth"].tolist()))
-    n, n_band, n_drop = check_exact_tile_lists(gpu_tiles, surv[vals, 0], surv[vals, 1], rec[vals, 6],
+    n, n_band, n_drop = check_exact_tile_lists(gpu_tiles, surv[vals, 0], surv[vals, 1], rec[vals, 11],
                                                ell, depth_of, drop)
     print(f"tile {tile}: {n} pairs equal, {n_band} in the band, {n_drop} of dropped splats "
           f"(gpu {len(gpu_tiles)} pairs)")
