@@ -566,9 +566,11 @@ def run_ours(args, rank, world):
                    "mean_survivors": mean("n_survivors", st_culled),
                    "mean_pairs": mean("n_pairs", st_culled),
                    "mean_pairs_unculled": mean("n_pairs", st_plain),
-                   "first_timed_frames": [{k: int(fr[k]) for k in ("n_in_frustum", "n_mlp_queries",
-                                                                  "n_survivors", "n_pairs", "sort_passes")}
-                                          for fr in st_culled[:3]],
+                   "first_timed_frames": [dict({k: int(fr[k]) for k in ("n_in_frustum", "n_mlp_queries",
+                                                                       "n_survivors", "n_pairs", "sort_passes")},
+                                               blend_evaluations=int(fc["blend_evaluations"]),
+                                               blend_composited=int(fc["blend_composited"]))
+                                          for fr, fc in zip(st_culled[:3], st_count[:3])],
                    "gaussians_per_s": st_culled[0]["n_instanced"] / (value * 1e-3),
                    "kernels_ms_per_frame": kernels,
                    "sync_free": graph_info,
