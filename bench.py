@@ -42,13 +42,17 @@ KERNEL_SOURCES = {
     "k_blend<16>": ["k_blend.cu", "nvgs_internal.cuh"],
     "k_rs_scatter<u32>": ["k_sort.cu", "nvgs_internal.cuh"],
     "k_rs_hist<u32>": ["k_sort.cu", "nvgs_internal.cuh"],
+    "k_rs_scatter<u16>": ["k_sort.cu", "nvgs_internal.cuh"],
+    "k_rs_hist<u16>": ["k_sort.cu", "nvgs_internal.cuh"],
     "k_project": ["k_project.cu", "nvgs_internal.cuh"],
     "k_duplicate": ["k_bin.cu", "nvgs_internal.cuh"],
 }
 
 
-def kernel_units(name, fr):
-    """Units of work of kernel `name` in one frame (its traffic is taken to scale with them)."""
+def kernel_units(name, fr, tile16=True):
+    """Units of work of kernel `name` in one frame (its traffic is taken to scale with them).
+    tile16: the frame's tile ids are sorted as 16-bit keys (at most 65536 tiles), so the tile
+    passes run in the <u16> radix kernels and the depth passes alone in the <u32> ones."""
     if name in ("k_mlp_tc", "k_mlp_f8"):
         return fr["n_mlp_queries"]
     if name.startswith("k_blend") or name == "k_duplicate":
@@ -57,7 +61,10 @@ def kernel_units(name, fr):
         return fr["n_survivors"]
     if name.startswith("k_rs_"):                       # item-passes: 4 depth, the rest tile passes
         dp = 4 if fr["n_survivors"] > 1 else 0
-        return dp * fr["n_survivors"] + max(0, fr["sort_passes"] - dp) * fr["n_pairs"]
+        tile_items = max(0, fr["sort_passes"] - dp) * fr["n_pairs"]
+        if name.endswith("<u16>"):
+            return tile_items
+        return dp * fr["n_survivors"] + (0 if tile16 else tile_items)
     return None
 
 
@@ -245,14 +252,19 @@ def kernel_frame_work(name, fr, sh_stride_floats, W, H, tile):
         if fr.get("blend_evaluations"):
             return "alu", fr["blend_evaluations"] * BLEND_FLOPS_PER_EVAL
         return "hbm", npairs * (4 + 48) + W * H * 12 + n_tiles * 8   # value + 48 record bytes
+    tile16 = n_tiles <= 65536                           # tile ids sorted as 16-bit keys
     if name == "k_rs_scatter<u32>":                    # read and write key + value per pass
-        return "hbm", 16 * (dpasses * ns + tpasses * npairs)
+        return "hbm", 16 * (dpasses * ns + (0 if tile16 else tpasses * npairs))
     if name == "k_rs_hist<u32>":
-        return "hbm", 4 * (dpasses * ns + tpasses * npairs)
+        return "hbm", 4 * (dpasses * ns + (0 if tile16 else tpasses * npairs))
+    if name == "k_rs_scatter<u16>":
+        return "hbm", 12 * tpasses * npairs
+    if name == "k_rs_hist<u16>":
+        return "hbm", 2 * tpasses * npairs
     if name == "k_duplicate":
         # depth order, the record's rectangle and splat fields (48 of its 64 bytes), offset;
         # key + value per pair
-        return "hbm", ns * (4 + 48 + 4) + npairs * 8
+        return "hbm", ns * (4 + 48 + 4) + npairs * (6 if n_tiles <= 65536 else 8)
     if name == "k_tile_ranges":
         return "hbm", n_tiles * 8
     if name == "k_frustum":

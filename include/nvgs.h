@@ -434,13 +434,15 @@ typedef struct {
                                     rectangle x0, y0, x1, y1 (inclusive) as int32 bits */
     const int32_t* tile_rects;   /* the rectangles inside the records: 4 int32 every 16 */
     const uint32_t* pair_values; /* n_pairs survivor indices in (tile, depth) order */
-    const uint32_t* pair_keys;   /* n_pairs tile ids of those pairs (non-decreasing) */
+    const void* pair_keys;       /* n_pairs tile ids of those pairs (non-decreasing), uint16 when
+                                    pair_key_bytes = 2 (frames of at most 65536 tiles), else uint32 */
     const uint32_t* tile_ranges; /* 2 x n_tiles: [start, end) into pair_values */
     const float* final_T;        /* W x H, when flags.keep_outputs */
     const int32_t* n_contrib;    /* W x H, when flags.keep_outputs: 1 + index (into the sorted
                                     pairs) of the last fragment blended at the pixel, 0 if none */
     uint64_t n_survivors, n_pairs;
     int32_t tiles_x, tiles_y, tile_size, depth_bits; /* depth_bits: 0 (pair_keys hold tile ids) */
+    int32_t pair_key_bytes, pad_;
 } nvgs_frame_view;
 nvgs_status nvgs_last_frame(const nvgs_ctx* ctx, nvgs_frame_view* out);
 

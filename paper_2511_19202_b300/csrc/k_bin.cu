@@ -51,15 +51,16 @@ __device__ __forceinline__ int warp_owner(uint32_t pre, uint32_t c) {
 }
 
 // kMV (multi-view batches): the rect's w carries the survivor's view in its high 16 bits, and the
-// pair key is that view's tile_base plus its local tile id.
-template <bool kMV>
+// pair key is that view's tile_base plus its local tile id.  KT: the key type (16-bit tile ids
+// when the frame or batch has at most 65536 tiles).
+template <bool kMV, typename KT>
 __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ order,
                                                    const float4* __restrict__ rec,
                                                    const uint32_t* __restrict__ offsets, uint32_t n,
                                                    const uint32_t* __restrict__ n_dev,
                                                    const CamParams* __restrict__ camp, const uint32_t* __restrict__ n_pairs,
                                                    uint32_t pair_cap, uint32_t* __restrict__ overflow,
-                                                   uint32_t* __restrict__ keys,
+                                                   KT* __restrict__ keys,
                                                    uint32_t* __restrict__ values) {
     const CamParams cam = *camp;
     if (n_dev) n = min(n, *n_dev);
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
                 const uint32_t iq = __shfl_sync(0xffffffffu, ij, q);
                 const uint32_t pos = out + p;
                 if (p < batch && pos < limit) {
-                    keys[pos] = (uint32_t)(rq + tq0 + (int)(p - pq));
+                    keys[pos] = (KT)(rq + tq0 + (int)(p - pq));
                     values[pos] = iq;
                 }
             }
@@ -152,8 +153,9 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
 cudaError_t launch_duplicate(const uint32_t* order, const float4* rec,
                              const uint32_t* offsets, uint32_t n, const uint32_t* n_dev,
                              const CamParams* cam_dev, const uint32_t* n_pairs, uint32_t pair_cap,
-                             uint32_t* overflow, uint32_t* keys, uint32_t* values, int num_sms,
+                             uint32_t* overflow, void* keys, int key_bytes, uint32_t* values, int num_sms,
                              cudaStream_t s, LaunchLog* log, int multi_view) {
+    if (key_bytes != 2 && key_bytes != 4) return cudaErrorInvalidValue;
     if (n == 0) return cudaSuccess;
     // a grid-stride kernel with equal shares per CTA: exactly the CTAs that are resident at once
     // (a fraction of a second wave would run alone at the end)
@@ -163,46 +165,59 @@ cudaError_t launch_duplicate(const uint32_t* order, const float4* rec,
     static std::atomic<int> per_sm_cache[64];   // per device ordinal; 0 = not measured yet
     if (dev >= 0 && dev < 64) per_sm = per_sm_cache[dev].load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_duplicate<false>, 256, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_duplicate<false, uint32_t>, 256, 0);
         if (e != cudaSuccess) return e;
         per_sm = std::max(per_sm, 1);
         if (dev >= 0 && dev < 64) per_sm_cache[dev].store(per_sm, std::memory_order_relaxed);
     }
     const uint32_t warps = (n + 31) / 32;
     const uint32_t grid = std::min<uint32_t>((warps + 7) / 8, (uint32_t)(num_sms * per_sm));
-    if (multi_view)
-        NVGS_LAUNCH(log, s, "k_duplicate_views", k_duplicate<true><<<grid, 256, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, keys, values));
+    uint16_t* k16 = static_cast<uint16_t*>(keys);
+    uint32_t* k32 = static_cast<uint32_t*>(keys);
+    if (multi_view && key_bytes == 2)
+        NVGS_LAUNCH(log, s, "k_duplicate_views", k_duplicate<true, uint16_t><<<grid, 256, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, k16, values));
+    else if (multi_view)
+        NVGS_LAUNCH(log, s, "k_duplicate_views", k_duplicate<true, uint32_t><<<grid, 256, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, k32, values));
+    else if (key_bytes == 2)
+        NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<false, uint16_t><<<grid, 256, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, k16, values));
     else
-        NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<false><<<grid, 256, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, keys, values));
+        NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<false, uint32_t><<<grid, 256, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, k32, values));
     return cudaGetLastError();
 }
 
 // ranges[2t] / ranges[2t+1] = first / one-past-last index of tile t in the sorted keys: one
 // thread per tile, two binary searches (lower bounds of t and t + 1) instead of a pass over the
 // pairs.
-__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ a, uint32_t n, uint32_t v) {
+template <typename KT>
+__device__ __forceinline__ uint32_t lower_bound_key(const KT* __restrict__ a, uint32_t n, uint32_t v) {
     uint32_t lo = 0, hi = n;
     while (lo < hi) {
         const uint32_t mid = lo + ((hi - lo) >> 1);
-        if (__ldg(&a[mid]) < v) lo = mid + 1; else hi = mid;
+        if ((uint32_t)__ldg(&a[mid]) < v) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
 
-__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ keys, uint32_t n,
+template <typename KT>
+__global__ void __launch_bounds__(256) k_tile_ranges(const KT* __restrict__ keys, uint32_t n,
                                                      const uint32_t* __restrict__ n_dev,
                                                      uint32_t n_tiles, uint32_t* __restrict__ ranges) {
     if (n_dev) n = min(n, *n_dev);
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
-    ranges[2 * t] = lower_bound_u32(keys, n, t);
-    ranges[2 * t + 1] = lower_bound_u32(keys, n, t + 1);
+    ranges[2 * t] = lower_bound_key(keys, n, t);
+    ranges[2 * t + 1] = lower_bound_key(keys, n, t + 1);
 }
 
-cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, const uint32_t* n_dev, uint32_t n_tiles,
-                               uint32_t* ranges, cudaStream_t s, LaunchLog* log) {
+cudaError_t launch_tile_ranges(const void* keys, int key_bytes, uint32_t n, const uint32_t* n_dev,
+                               uint32_t n_tiles, uint32_t* ranges, cudaStream_t s, LaunchLog* log) {
     if (n_tiles == 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_tile_ranges", k_tile_ranges<<<(n_tiles + 255) / 256, 256, 0, s>>>(keys, n, n_dev, n_tiles, ranges));
+    if (key_bytes == 2)
+        NVGS_LAUNCH(log, s, "k_tile_ranges", k_tile_ranges<uint16_t><<<(n_tiles + 255) / 256, 256, 0, s>>>(static_cast<const uint16_t*>(keys), n, n_dev, n_tiles, ranges));
+    else if (key_bytes == 4)
+        NVGS_LAUNCH(log, s, "k_tile_ranges", k_tile_ranges<uint32_t><<<(n_tiles + 255) / 256, 256, 0, s>>>(static_cast<const uint32_t*>(keys), n, n_dev, n_tiles, ranges));
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -198,22 +198,45 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ ke
     }
     for (int k = threadIdx.x; k < kRsWarps * 256; k += kRsThreads) (&h[0][0])[k] = 0u;
     __syncthreads();
-    bool vec = false;
-    if constexpr (sizeof(K) == 4) vec = base + kRsTile <= n && ((uintptr_t)(keys + base) & 15u) == 0;
-    if (vec) {
-        // a full tile of 32-bit keys: four 16-byte loads per thread, all in flight at once
-        const uint4* k4 = reinterpret_cast<const uint4*>(keys + base);
-        uint4 v[kRsItems / 4];
+    const bool vec = sizeof(K) <= 4 && base + kRsTile <= n && ((uintptr_t)(keys + base) & 15u) == 0;
+    bool counted = false;
+    if constexpr (sizeof(K) == 2) {
+        if (vec) {
+            // a full tile of 16-bit keys: two 16-byte loads (eight keys each) per thread
+            const uint4* k4 = reinterpret_cast<const uint4*>(keys + base);
+            uint4 v[kRsItems / 8];
 #pragma unroll
-        for (int j = 0; j < kRsItems / 4; j++) v[j] = k4[j * kRsThreads + threadIdx.x];
+            for (int j = 0; j < kRsItems / 8; j++) v[j] = k4[j * kRsThreads + threadIdx.x];
 #pragma unroll
-        for (int j = 0; j < kRsItems / 4; j++) {
-            atomicAdd(&h[warp][(v[j].x >> shift) & mask], 1u);
-            atomicAdd(&h[warp][(v[j].y >> shift) & mask], 1u);
-            atomicAdd(&h[warp][(v[j].z >> shift) & mask], 1u);
-            atomicAdd(&h[warp][(v[j].w >> shift) & mask], 1u);
+            for (int j = 0; j < kRsItems / 8; j++) {
+                const uint32_t w[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    atomicAdd(&h[warp][((w[q] & 0xffffu) >> shift) & mask], 1u);
+                    atomicAdd(&h[warp][((w[q] >> 16) >> shift) & mask], 1u);
+                }
+            }
+            counted = true;
         }
-    } else {
+    }
+    if constexpr (sizeof(K) == 4) {
+        if (vec) {
+            // a full tile of 32-bit keys: four 16-byte loads per thread, all in flight at once
+            const uint4* k4 = reinterpret_cast<const uint4*>(keys + base);
+            uint4 v[kRsItems / 4];
+#pragma unroll
+            for (int j = 0; j < kRsItems / 4; j++) v[j] = k4[j * kRsThreads + threadIdx.x];
+#pragma unroll
+            for (int j = 0; j < kRsItems / 4; j++) {
+                atomicAdd(&h[warp][(v[j].x >> shift) & mask], 1u);
+                atomicAdd(&h[warp][(v[j].y >> shift) & mask], 1u);
+                atomicAdd(&h[warp][(v[j].z >> shift) & mask], 1u);
+                atomicAdd(&h[warp][(v[j].w >> shift) & mask], 1u);
+            }
+            counted = true;
+        }
+    }
+    if (!counted) {
 #pragma unroll 4
         for (int j = 0; j < kRsItems; j++) {
             const uint64_t i = base + (uint64_t)j * kRsThreads + threadIdx.x;
@@ -260,7 +283,7 @@ __global__ void __launch_bounds__(256) k_rs_digit_scan(uint32_t* __restrict__ hi
 // values are read only when they are placed in shared memory, so four CTAs fit on an SM
 // (smaller, more numerous CTAs overlap their load, rank and write phases better).
 template <typename K>
-__global__ void __launch_bounds__(kRsThreads, sizeof(K) == 4 ? 4 : 2) k_rs_scatter(
+__global__ void __launch_bounds__(kRsThreads, sizeof(K) <= 4 ? 4 : 2) k_rs_scatter(
     const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, K* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, uint64_t n, const uint32_t* __restrict__ n_dev, int shift,
     uint32_t mask, uint32_t n_tiles, const uint32_t* __restrict__ hist_scan,
@@ -427,8 +450,8 @@ static cudaError_t radix_sort_impl(K* keys, uint32_t* values, K* keys_alt, uint3
     uint32_t* vin = values;
     K* kout = keys_alt;
     uint32_t* vout = values_alt;
-    const char* hname = sizeof(K) == 8 ? "k_rs_hist<u64>" : "k_rs_hist<u32>";
-    const char* sname = sizeof(K) == 8 ? "k_rs_scatter<u64>" : "k_rs_scatter<u32>";
+    const char* hname = sizeof(K) == 8 ? "k_rs_hist<u64>" : sizeof(K) == 4 ? "k_rs_hist<u32>" : "k_rs_hist<u16>";
+    const char* sname = sizeof(K) == 8 ? "k_rs_scatter<u64>" : sizeof(K) == 4 ? "k_rs_scatter<u32>" : "k_rs_scatter<u16>";
     // one CTA per tile; with a device-side count the CTAs past it exit at once (the histogram
     // ones after writing zero counts)
     const unsigned hgrid = (unsigned)tiles;
@@ -475,6 +498,15 @@ cudaError_t radix_sort_pairs_u32(uint32_t* keys, uint32_t* values, uint32_t* key
                                  cudaStream_t s, LaunchLog* log, int* passes_out, int copy_back,
                                  int* result_in_alt, const uint32_t* n_dev, int digit_bits) {
     return radix_sort_impl<uint32_t>(keys, values, keys_alt, values_alt, n, key_bits, scratch, s, log,
+                                     passes_out, copy_back, result_in_alt, n_dev, digit_bits);
+}
+
+cudaError_t radix_sort_pairs_u16(uint16_t* keys, uint32_t* values, uint16_t* keys_alt,
+                                 uint32_t* values_alt, uint64_t n, int key_bits, void* scratch,
+                                 cudaStream_t s, LaunchLog* log, int* passes_out, int copy_back,
+                                 int* result_in_alt, const uint32_t* n_dev, int digit_bits) {
+    if (key_bits > 16) return cudaErrorInvalidValue;
+    return radix_sort_impl<uint16_t>(keys, values, keys_alt, values_alt, n, key_bits, scratch, s, log,
                                      passes_out, copy_back, result_in_alt, n_dev, digit_bits);
 }
 

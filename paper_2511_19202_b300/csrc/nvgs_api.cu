@@ -733,6 +733,51 @@ extern "C" nvgs_status nvgs_query_visibility(nvgs_ctx* ctx, const nvgs_camera* c
 
 // The whole pass for one camera.  labels_row (nullable, device, one byte per Gaussian of the
 // scene's single instance) receives 1 for every Gaussian blended at some pixel (the labeller).
+// S5 after the depth order: the survivors' pairs in that order (k_duplicate), sorted stably by tile
+// id, and each tile's range.  Tile ids are 16-bit when the frame (or batch) has at most 65536
+// tiles (12 instead of 16 bytes of key + value traffic per pair and radix pass).  n / n_dev: the
+// survivor count (host, or a capacity with the count on the device); pair_cap: the pairs' count
+// (synchronous path) or capacity; n_pairs_dev: the pair total on the device; sort_n_dev: null
+// when pair_cap is the exact count, else n_pairs_dev.
+struct SortedPairs {
+    void* keys = nullptr;
+    int key_bytes = 4;
+    uint32_t* vals = nullptr;
+    int passes = 0;
+};
+static nvgs_status bin_and_sort(nvgs_ctx* ctx, const uint32_t* order, uint32_t n, const uint32_t* n_dev,
+                                const CamParams* cam_dev, const uint32_t* n_pairs_dev, uint64_t pair_cap,
+                                uint32_t* overflow, const uint32_t* sort_n_dev, int n_tiles, int digit_bits,
+                                int multi_view, cudaStream_t s, SortedPairs& out, StageTimer* tm = nullptr) {
+    const int tile_bits = std::max(1, bit_width((uint64_t)n_tiles - 1));
+    const int kb = n_tiles <= 65536 ? 2 : 4;
+    CK(ensure(ctx->keys, (size_t)pair_cap * 4 + 16));
+    CK(ensure(ctx->vals, (size_t)pair_cap * 4 + 16));
+    CK(ensure(ctx->keys_alt, (size_t)pair_cap * 4 + 16));
+    CK(ensure(ctx->vals_alt, (size_t)pair_cap * 4 + 16));
+    CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
+    if (radix_scratch_bytes(pair_cap) > ctx->scratch.cap) CK(ensure(ctx->scratch, radix_scratch_bytes(pair_cap)));
+    CK(launch_duplicate(order, P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets), n, n_dev, cam_dev,
+                        n_pairs_dev, (uint32_t)pair_cap, overflow, ctx->keys.p, kb, P<uint32_t>(ctx->vals),
+                        ctx->num_sms, s, &ctx->log, multi_view));
+    if (tm) tm->mark(NVGS_STAGE_SORT);
+    int in_alt = 0;
+    if (kb == 2)
+        CK(radix_sort_pairs_u16(P<uint16_t>(ctx->keys), P<uint32_t>(ctx->vals), P<uint16_t>(ctx->keys_alt),
+                                P<uint32_t>(ctx->vals_alt), pair_cap, tile_bits, ctx->scratch.p, s, &ctx->log,
+                                &out.passes, 0, &in_alt, sort_n_dev, digit_bits));
+    else
+        CK(radix_sort_pairs_u32(P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), P<uint32_t>(ctx->keys_alt),
+                                P<uint32_t>(ctx->vals_alt), pair_cap, tile_bits, ctx->scratch.p, s, &ctx->log,
+                                &out.passes, 0, &in_alt, sort_n_dev, digit_bits));
+    out.keys = in_alt ? ctx->keys_alt.p : ctx->keys.p;
+    out.vals = in_alt ? P<uint32_t>(ctx->vals_alt) : P<uint32_t>(ctx->vals);
+    out.key_bytes = kb;
+    CK(launch_tile_ranges(out.keys, kb, (uint32_t)pair_cap, sort_n_dev, (uint32_t)n_tiles,
+                          P<uint32_t>(ctx->ranges), s, &ctx->log));
+    return NVGS_OK;
+}
+
 static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_render_flags* f,
                              float* image, nvgs_frame_stats* stats, uint8_t* labels_row) {
     if (!ctx) return NVGS_ERR_INVALID_ARG;
@@ -797,25 +842,15 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     CK(cudaStreamSynchronize(s));
     const uint32_t n_pairs = n_surv ? ctx->h_counters[2] : 0u;
     const int n_tiles = cp.tiles_x * cp.tiles_y;
-    const int tile_bits = std::max(1, bit_width((uint64_t)n_tiles - 1));
-    CK(ensure(ctx->keys, (size_t)n_pairs * 4 + 16));
-    CK(ensure(ctx->vals, (size_t)n_pairs * 4 + 16));
-    CK(ensure(ctx->keys_alt, (size_t)n_pairs * 4 + 16));
-    CK(ensure(ctx->vals_alt, (size_t)n_pairs * 4 + 16));
-    CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
-    if (radix_scratch_bytes(n_pairs) > ctx->scratch.cap) CK(ensure(ctx->scratch, radix_scratch_bytes(n_pairs)));
-    CK(launch_duplicate(order, P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
-                        n_surv, nullptr, cam_dev, counters + 2, n_pairs, nullptr, P<uint32_t>(ctx->keys),
-                        P<uint32_t>(ctx->vals), ctx->num_sms, s, &ctx->log));
-    tm.mark(NVGS_STAGE_SORT);
-    int passes = 0, in_alt = 0;
-    CK(radix_sort_pairs_u32(P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), P<uint32_t>(ctx->keys_alt),
-                            P<uint32_t>(ctx->vals_alt), n_pairs, tile_bits, ctx->scratch.p, s, &ctx->log,
-                            &passes, 0, &in_alt, nullptr, f->sort_digit_bits ? f->sort_digit_bits : 8));
-    uint32_t* skeys = in_alt ? P<uint32_t>(ctx->keys_alt) : P<uint32_t>(ctx->keys);
-    uint32_t* svals = in_alt ? P<uint32_t>(ctx->vals_alt) : P<uint32_t>(ctx->vals);
-    CK(launch_tile_ranges(skeys, n_pairs, nullptr, (uint32_t)n_tiles, P<uint32_t>(ctx->ranges), s, &ctx->log));
-    passes += dpasses;
+    SortedPairs sp;
+    {
+        const nvgs_status st = bin_and_sort(ctx, order, n_surv, nullptr, cam_dev, counters + 2, n_pairs, nullptr,
+                                            nullptr, n_tiles, f->sort_digit_bits ? f->sort_digit_bits : 8, 0, s, sp,
+                                            &tm);
+        if (st != NVGS_OK) return st;
+    }
+    uint32_t* svals = sp.vals;
+    int passes = sp.passes + dpasses;
     const int depth_bits = 0;
 
     // ---- S6
@@ -870,7 +905,8 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     L.records = P<float>(ctx->rec);
     L.tile_rects = P<int32_t>(ctx->rec) + 12;   // inside the records, 16 int32 apart
     L.pair_values = svals;
-    L.pair_keys = skeys;
+    L.pair_keys = sp.keys;
+    L.pair_key_bytes = sp.key_bytes;
     L.tile_ranges = P<uint32_t>(ctx->ranges);
     L.final_T = fT;
     L.n_contrib = nc;
@@ -1258,23 +1294,14 @@ static nvgs_status enqueue_view_async(nvgs_ctx* ctx, const CamParams& cp, const 
     CK(exclusive_scan_u32(P<uint32_t>(ctx->tile_offsets), P<uint32_t>(ctx->tile_offsets), cap, counters + 2,
                           ctx->scratch.p, s, &ctx->log, n_surv_dev));
     const int n_tiles = cp.tiles_x * cp.tiles_y;
-    const int tile_bits = std::max(1, bit_width((uint64_t)n_tiles - 1));
-    CK(ensure(ctx->keys, (size_t)pair_cap * 4 + 16));
-    CK(ensure(ctx->vals, (size_t)pair_cap * 4 + 16));
-    CK(ensure(ctx->keys_alt, (size_t)pair_cap * 4 + 16));
-    CK(ensure(ctx->vals_alt, (size_t)pair_cap * 4 + 16));
-    CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
-    CK(launch_duplicate(order, P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
-                        (uint32_t)cap, n_surv_dev, cam_dev, counters + 2, (uint32_t)pair_cap, counters + 9,
-                        P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), ctx->num_sms, s, &ctx->log));
-    int passes = 0, in_alt = 0;
-    CK(radix_sort_pairs_u32(P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), P<uint32_t>(ctx->keys_alt),
-                            P<uint32_t>(ctx->vals_alt), pair_cap, tile_bits, ctx->scratch.p, s, &ctx->log,
-                            &passes, 0, &in_alt, counters + 2, f->sort_digit_bits ? f->sort_digit_bits : 8));
-    uint32_t* skeys = in_alt ? P<uint32_t>(ctx->keys_alt) : P<uint32_t>(ctx->keys);
-    uint32_t* svals = in_alt ? P<uint32_t>(ctx->vals_alt) : P<uint32_t>(ctx->vals);
-    CK(launch_tile_ranges(skeys, (uint32_t)pair_cap, counters + 2, (uint32_t)n_tiles, P<uint32_t>(ctx->ranges),
-                          s, &ctx->log));
+    SortedPairs sp;
+    {
+        const nvgs_status st = bin_and_sort(ctx, order, (uint32_t)cap, n_surv_dev, cam_dev, counters + 2, pair_cap,
+                                            counters + 9, counters + 2, n_tiles,
+                                            f->sort_digit_bits ? f->sort_digit_bits : 8, 0, s, sp);
+        if (st != NVGS_OK) return st;
+    }
+    uint32_t* svals = sp.vals;
     // S6.  The automatic split length depends on the frame's pair count, which only the device
     // knows here: it is resolved there with the synchronous path's rule (so both paths split the
     // same tiles and give the same image), and the scratch is sized for its lower bound 4096.
@@ -1441,23 +1468,13 @@ static nvgs_status enqueue_views(nvgs_ctx* ctx, const CullScope& scope, const Ca
                             P<uint32_t>(ctx->tile_offsets), ctx->num_sms, s, &ctx->log));
     CK(exclusive_scan_u32(P<uint32_t>(ctx->tile_offsets), P<uint32_t>(ctx->tile_offsets), cap, counters + 2,
                           ctx->scratch.p, s, &ctx->log, n_surv_dev));
-    const int tile_bits = std::max(1, bit_width((uint64_t)n_tiles - 1));
-    CK(ensure(ctx->keys, (size_t)pair_cap * 4 + 16));
-    CK(ensure(ctx->vals, (size_t)pair_cap * 4 + 16));
-    CK(ensure(ctx->keys_alt, (size_t)pair_cap * 4 + 16));
-    CK(ensure(ctx->vals_alt, (size_t)pair_cap * 4 + 16));
-    CK(ensure(ctx->ranges, (size_t)n_tiles * 8));
-    CK(launch_duplicate(order, P<float4>(ctx->rec), P<uint32_t>(ctx->tile_offsets),
-                        (uint32_t)cap, n_surv_dev, cam_dev, counters + 2, (uint32_t)pair_cap, counters + 9,
-                        P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), ctx->num_sms, s, &ctx->log, 1));
-    int passes = 0, in_alt = 0;
-    CK(radix_sort_pairs_u32(P<uint32_t>(ctx->keys), P<uint32_t>(ctx->vals), P<uint32_t>(ctx->keys_alt),
-                            P<uint32_t>(ctx->vals_alt), pair_cap, tile_bits, ctx->scratch.p, s, &ctx->log,
-                            &passes, 0, &in_alt, counters + 2, digit_bits));
-    uint32_t* skeys = in_alt ? P<uint32_t>(ctx->keys_alt) : P<uint32_t>(ctx->keys);
-    uint32_t* svals = in_alt ? P<uint32_t>(ctx->vals_alt) : P<uint32_t>(ctx->vals);
-    CK(launch_tile_ranges(skeys, (uint32_t)pair_cap, counters + 2, (uint32_t)n_tiles, P<uint32_t>(ctx->ranges),
-                          s, &ctx->log));
+    SortedPairs sp;
+    {
+        const nvgs_status st = bin_and_sort(ctx, order, (uint32_t)cap, n_surv_dev, cam_dev, counters + 2, pair_cap,
+                                            counters + 9, counters + 2, n_tiles, digit_bits, 1, s, sp);
+        if (st != NVGS_OK) return st;
+    }
+    uint32_t* svals = sp.vals;
     // S6 over the tiles of every view; the automatic split length takes the batch's pair count and
     // tile count (the rule of nvgs_render over the whole batch)
     const bool auto_split = f->blend_split_len == 0;

@@ -362,14 +362,16 @@ cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* counts, 
 // as the projection counted them.  n_pairs (device) is the total; writes stop at pair_cap, and
 // overflow (device, nullable) is set when the total exceeds it.
 // multi_view: tile ids are global (the view's tile_base + its local tile id), the view taken
-// from the rect (as launch_project writes it in multi-view mode).
+// from the rect (as launch_project writes it in multi-view mode).  keys: key_bytes 2 (uint16 tile
+// ids, at most 65536 tiles) or 4 (uint32).
 cudaError_t launch_duplicate(const uint32_t* order, const float4* rec,
                              const uint32_t* offsets, uint32_t n, const uint32_t* n_dev,
                              const CamParams* cam_dev, const uint32_t* n_pairs, uint32_t pair_cap,
-                             uint32_t* overflow, uint32_t* keys, uint32_t* values, int num_sms,
+                             uint32_t* overflow, void* keys, int key_bytes, uint32_t* values, int num_sms,
                              cudaStream_t s, LaunchLog* log, int multi_view = 0);
-cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n, const uint32_t* n_dev, uint32_t n_tiles,
-                               uint32_t* ranges, cudaStream_t s, LaunchLog* log);
+// keys: the sorted tile ids, key_bytes 2 (uint16) or 4 (uint32).
+cudaError_t launch_tile_ranges(const void* keys, int key_bytes, uint32_t n, const uint32_t* n_dev,
+                               uint32_t n_tiles, uint32_t* ranges, cudaStream_t s, LaunchLog* log);
 
 // S6
 // mark (nullable, per survivor): set to 1 when the survivor is blended at some pixel.  evals
@@ -417,6 +419,13 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* values,
 // The same sort for 32-bit keys, with digits of digit_bits (1..8) bits.
 // With n_dev the element count is read on the device (n is the capacity).
 cudaError_t radix_sort_pairs_u32(uint32_t* keys, uint32_t* values, uint32_t* keys_alt,
+                                 uint32_t* values_alt, uint64_t n, int key_bits, void* scratch,
+                                 cudaStream_t s, LaunchLog* log, int* passes_out, int copy_back,
+                                 int* result_in_alt, const uint32_t* n_dev = nullptr,
+                                 int digit_bits = 8);
+// The same sort for 16-bit keys (key_bits <= 16): the S5 tile sort when the frame (or batch) has
+// at most 65536 tiles, at 12 instead of 16 bytes of key + value traffic per element and pass.
+cudaError_t radix_sort_pairs_u16(uint16_t* keys, uint32_t* values, uint16_t* keys_alt,
                                  uint32_t* values_alt, uint64_t n, int key_bits, void* scratch,
                                  cudaStream_t s, LaunchLog* log, int* passes_out, int copy_back,
                                  int* result_in_alt, const uint32_t* n_dev = nullptr,

@@ -80,7 +80,8 @@ class FrameView(C.Structure):
                 ("pair_values", C.c_void_p), ("pair_keys", C.c_void_p), ("tile_ranges", C.c_void_p),
                 ("final_T", C.c_void_p), ("n_contrib", C.c_void_p), ("n_survivors", C.c_uint64),
                 ("n_pairs", C.c_uint64), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
-                ("tile_size", C.c_int32), ("depth_bits", C.c_int32)]
+                ("tile_size", C.c_int32), ("depth_bits", C.c_int32), ("pair_key_bytes", C.c_int32),
+                ("pad_", C.c_int32)]
 
 
 class AssetInfo(C.Structure):

@@ -116,7 +116,7 @@ class Renderer:
         def grab(ptr, count, dtype):
             if not count or not ptr:
                 return torch.empty(count, dtype=dtype, device=self.device)
-            typestr = {torch.int32: "<i4", torch.float32: "<f4", torch.int64: "<i8"}[dtype]
+            typestr = {torch.int32: "<i4", torch.float32: "<f4", torch.int64: "<i8", torch.int16: "<i2"}[dtype]
             view = _DeviceArray(ptr, count, typestr)
             self.stream.synchronize()
             return torch.as_tensor(view, device=self.device).clone()
@@ -127,7 +127,9 @@ class Renderer:
             records=rec,
             tile_rects=rec[:, 12:].contiguous().view(torch.int32),   # stored inside the records
             pair_values=grab(v.pair_values, npairs, torch.int32),
-            pair_keys=grab(v.pair_keys, npairs, torch.int32),
+            # 16-bit tile ids come back as int32 (ids below 65536: read as unsigned)
+            pair_keys=(grab(v.pair_keys, npairs, torch.int16).to(torch.int32) & 0xffff
+                       if v.pair_key_bytes == 2 else grab(v.pair_keys, npairs, torch.int32)),
             tile_ranges=grab(v.tile_ranges, 2 * n_tiles, torch.int32).view(-1, 2),
             tiles_x=int(v.tiles_x), tiles_y=int(v.tiles_y), tile_size=int(v.tile_size),
             depth_bits=int(v.depth_bits))
