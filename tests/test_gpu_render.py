@@ -53,6 +53,28 @@ def test_tile_size_does_not_change_the_image(cfg1_setup):
     np.testing.assert_array_equal(imgs[1], imgs[2])
 
 
+def test_tile_id_width_does_not_change_the_image():
+    """More than 65536 tiles (2080 x 2080 at 8 px: 67,600) sort 32-bit tile ids, fewer (16 px:
+    16,900) 16-bit ones; the tile size never changes the image, so both must agree bit for bit, and
+    the 8 px frame's tile lists must be sorted and cover every pair."""
+    sc = scenes.config1_scene()
+    cam = scenes.config1_camera(2080, 2080)
+    r = renderer_for(sc)
+    try:
+        a, sa = gpu_image(r, cam, use_mlp=0, tile_size=8, keep_outputs=1)
+        lf = r.last_frame()
+        keys = lf["pair_keys"].cpu().numpy().astype(np.int64)
+        ranges = lf["tile_ranges"].cpu().numpy().astype(np.int64)
+        assert lf["tiles_x"] * lf["tiles_y"] == 260 * 260 > 65536
+        assert keys.size == sa["n_pairs"] > 0 and np.all(np.diff(keys) >= 0) and keys[-1] < 260 * 260
+        np.testing.assert_array_equal(np.diff(ranges, axis=1)[:, 0], np.bincount(keys, minlength=260 * 260))
+        b, sb = gpu_image(r, cam, use_mlp=0, tile_size=16)
+        np.testing.assert_array_equal(a, b)
+        print(f"8 px: {sa['n_pairs']} pairs over {260 * 260} tiles; 16 px: {sb['n_pairs']} pairs")
+    finally:
+        r.close()
+
+
 def test_background_and_host_output(cfg1_setup):
     sc, cam, r, osc = cfg1_setup
     bg = (0.2, 0.5, 0.9)
