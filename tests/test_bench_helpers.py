@@ -16,8 +16,12 @@ def test_kernel_units():
     assert bench.kernel_units("k_mlp_tc", FRAME) == 900
     assert bench.kernel_units("k_blend<16>", FRAME) == 5000
     assert bench.kernel_units("k_project", FRAME) == 600
-    # four 8-bit passes over the survivors' depth keys, the rest over the pairs' tile keys
-    assert bench.kernel_units("k_rs_scatter<u32>", FRAME) == 4 * 600 + 2 * 5000
+    # four 8-bit passes over the survivors' depth keys (32-bit), the rest over the pairs' tile keys
+    # (16-bit up to 65536 tiles, else 32-bit in the same kernels as the depth passes)
+    assert bench.kernel_units("k_rs_scatter<u32>", FRAME) == 4 * 600
+    assert bench.kernel_units("k_rs_scatter<u16>", FRAME) == 2 * 5000
+    assert bench.kernel_units("k_rs_hist<u16>", FRAME) == 2 * 5000
+    assert bench.kernel_units("k_rs_scatter<u32>", FRAME, tile16=False) == 4 * 600 + 2 * 5000
     assert bench.kernel_units("k_frustum", FRAME) is None
 
 
