@@ -90,6 +90,21 @@ def test_background_and_host_output(cfg1_setup):
     compare_images(dev, ref["image"], ref["ambiguous"])
 
 
+@pytest.mark.parametrize("size,tile,split", [((1000, 562), 16, 0), ((333, 301), 8, 0), ((640, 480), 16, 600),
+                                             ((640, 480), 32, -1)])
+def test_host_output_equals_device_output(cfg1_setup, size, tile, split):
+    """A host image (page-locked or pageable) equals the device image bit for bit, over ragged
+    image sizes, tile sizes and dense-tile splitting."""
+    sc, _, r, _ = cfg1_setup
+    cam = scenes.config1_camera(*size)
+    flags = dict(use_mlp=0, tile_size=tile, blend_split_len=split, bg=(0.1, 0.2, 0.3))
+    dev, st = gpu_image(r, cam, **flags)
+    for pinned in (True, False):
+        host = torch.full((cam.height, cam.width, 3), -1.0, dtype=torch.float32, pin_memory=pinned)
+        r.render_host(cam, r.flags(**flags), host)
+        np.testing.assert_array_equal(dev, host.numpy().astype(np.float64))
+
+
 def test_profile_levels(cfg1_setup):
     """profile = 1 times stages without counting; profile = 2 also counts the compositing's
     (pixel, fragment) evaluations -- at least one per covered pixel -- and the image is the same."""
