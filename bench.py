@@ -122,7 +122,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--mlp", choices=["trained", "random"], default="trained",
                    help="trained: per-asset GPU labels + Adam (Sec. 3.1-3.2) before timing")
-    p.add_argument("--train-dirs", type=int, default=256)
+    p.add_argument("--train-dirs", type=int, default=512)
     p.add_argument("--train-precision", choices=["bf16", "fp32"], default="bf16",
                    help="arithmetic of the training steps' forward and backward: BF16 on the tcgen05 "
                         "tensor cores or FP32 on the CUDA cores (FP32 master weights and Adam either way)")
