@@ -39,7 +39,12 @@ cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* counts, 
 // 32 at a time: each lane finds its unit's survivor by a binary search over the lanes' row
 // prefix sums and computes the row's kept tile span once (as the projection counted it); a
 // second walk over the batch's pairs writes them, each lane finding its unit by a binary search
-// over the span prefix -- balanced whatever the rectangle sizes, and coalesced.
+// over the span prefix -- balanced whatever the rectangle sizes, and coalesced.  The survivors'
+// ellipse terms (computed once per survivor) and the batch's units are staged in shared memory
+// rather than shuffled field by field.  (Letting each lane write a small rectangle's pairs itself,
+// without the walk, measured slower: its divergent loops leave most lanes idle.)
+constexpr int kDupWarps = 8;
+
 __device__ __forceinline__ int warp_owner(uint32_t pre, uint32_t c) {
     int j = 0;
 #pragma unroll
@@ -54,17 +59,27 @@ __device__ __forceinline__ int warp_owner(uint32_t pre, uint32_t c) {
 // pair key is that view's tile_base plus its local tile id.  KT: the key type (16-bit tile ids
 // when the frame or batch has at most 65536 tiles).
 template <bool kMV, typename KT>
-__global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ order,
-                                                   const float4* __restrict__ rec,
-                                                   const uint32_t* __restrict__ offsets, uint32_t n,
-                                                   const uint32_t* __restrict__ n_dev,
-                                                   const CamParams* __restrict__ camp, const uint32_t* __restrict__ n_pairs,
-                                                   uint32_t pair_cap, uint32_t* __restrict__ overflow,
-                                                   KT* __restrict__ keys,
-                                                   uint32_t* __restrict__ values) {
+__global__ void __launch_bounds__(kDupWarps * 32) k_duplicate(const uint32_t* __restrict__ order,
+                                                              const float4* __restrict__ rec,
+                                                              const uint32_t* __restrict__ offsets, uint32_t n,
+                                                              const uint32_t* __restrict__ n_dev,
+                                                              const CamParams* __restrict__ camp,
+                                                              const uint32_t* __restrict__ n_pairs,
+                                                              uint32_t pair_cap, uint32_t* __restrict__ overflow,
+                                                              KT* __restrict__ keys,
+                                                              uint32_t* __restrict__ values) {
+    // the warp's survivors: ellipse (u, v, cb, rcc), (det, ck, ymax or -1 for a whole rectangle
+    // row, yr), rectangle (x0, x1, y0 - row prefix, index), its view's (tiles per row, first
+    // tile); and a batch's units (first key - span prefix, index)
+    __shared__ float4 s_e0[kDupWarps][32], s_e1[kDupWarps][32];
+    __shared__ int4 s_r[kDupWarps][32];
+    __shared__ int2 s_x[kMV ? kDupWarps : 1][32];
+    __shared__ uint2 s_u[kDupWarps][32];
     const CamParams cam = *camp;
+    const int ts = cam.tile_size;
+    const float rts = 1.0f / (float)ts;
     if (n_dev) n = min(n, *n_dev);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const uint32_t n_pairs_all = *n_pairs;
     const uint32_t limit = min(n_pairs_all, pair_cap);
     if (n_pairs_all > pair_cap && blockIdx.x == 0 && threadIdx.x == 0 && overflow) *overflow = 1u;
@@ -72,13 +87,14 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
     for (uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; warp * 32u < n; warp += n_warps) {
         const uint32_t k = warp * 32u + lane;
         // this lane's survivor
-        uint32_t i = 0, rows = 0;
+        uint32_t i = 0, rows = 0, off = 0;
         int4 r = make_int4(0, 0, -1, -1);
-        float u = 0.f, v = 0.f, A = 0.f, B = 0.f, C = 0.f, det = 0.f, kk = 0.f;
         int tiles_x = cam.tiles_x, tile_base = 0;
         bool test = false;
+        SplatEllipse el{};
         if (k < n) {
             i = order[k];
+            off = offsets[k];
             r = rec_rect(rec, i);
             if (kMV) {
                 const CamParams& cv = camp[r.w >> 16];
@@ -92,57 +108,61 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
                 if (test) {
                     const float4 a = __ldg(&rec[kRecF4 * (size_t)i]);
                     const float4 b = __ldg(&rec[kRecF4 * (size_t)i + 1]);
-                    u = a.x; v = a.y; A = a.z; B = a.w; C = b.x; kk = -2.0f * b.w;
-                    det = b.z;
+                    el = splat_ellipse(a.x, a.y, a.z, a.w, b.x, b.z, -2.0f * b.w);
                 }
             }
         }
         uint32_t row_pre;
         const uint32_t n_units = warp_prefix(rows, row_pre);
-        uint32_t out = __shfl_sync(0xffffffffu, k < n ? offsets[k] : 0u, 0);
+        __syncwarp();   // the previous iteration's walk has read the staging arrays
+        s_e0[wi][lane] = make_float4(el.u, el.v, el.cb, el.rcc);
+        s_e1[wi][lane] = make_float4(el.det, el.ck, test ? el.ymax : -1.0f, el.yr);
+        s_r[wi][lane] = make_int4(r.x, r.z, r.y - (int)row_pre, (int)i);
+        if (kMV) s_x[wi][lane] = make_int2(tiles_x, tile_base);
+        __syncwarp();
+        uint32_t out = __shfl_sync(0xffffffffu, off, 0);
         for (uint32_t c0 = 0; c0 < n_units; c0 += 32) {
             // ---- unit (survivor j, tile row ty): its kept span [t0, t1]
             const uint32_t c = c0 + lane;
             const int j = warp_owner(row_pre, c);
-            const uint32_t pj = __shfl_sync(0xffffffffu, row_pre, j);
-            const int rx = __shfl_sync(0xffffffffu, r.x, j), rz = __shfl_sync(0xffffffffu, r.z, j);
-            const int ry = __shfl_sync(0xffffffffu, r.y, j);
-            const float uj = __shfl_sync(0xffffffffu, u, j), vj = __shfl_sync(0xffffffffu, v, j);
-            const float Aj = __shfl_sync(0xffffffffu, A, j), Bj = __shfl_sync(0xffffffffu, B, j);
-            const float Cj = __shfl_sync(0xffffffffu, C, j), dj = __shfl_sync(0xffffffffu, det, j);
-            const float kj = __shfl_sync(0xffffffffu, kk, j);
-            const bool tj = __shfl_sync(0xffffffffu, (int)test, j) != 0;
-            // the unit's view: its first global tile and tiles per row (every lane shuffles)
-            const int tbj = kMV ? __shfl_sync(0xffffffffu, tile_base, j) : 0;
-            const int txj = kMV ? __shfl_sync(0xffffffffu, tiles_x, j) : cam.tiles_x;
-            int ty = 0, t0 = 1, t1 = 0;
-            int row0 = 0;   // global id of the first tile of the unit's tile row
+            const int4 sr = s_r[wi][j];
+            int t0 = 1, t1 = 0, row0 = 0;
             if (c < n_units) {
-                ty = ry + (int)(c - pj);
-                row0 = tbj + ty * txj;
-                if (tj) {
-                    row_tile_span(splat_ellipse(uj, vj, Aj, Bj, Cj, dj, kj), ty, cam.tile_size, t0, t1);
-                    t0 = max(t0, rx);
-                    t1 = min(t1, rz);
+                const int ty = sr.z + (int)c;
+                if (kMV) {
+                    const int2 sx = s_x[kMV ? wi : 0][j];
+                    row0 = sx.y + ty * sx.x;
                 } else {
-                    t0 = rx; t1 = rz;
+                    row0 = ty * cam.tiles_x;
+                }
+                const float4 e1 = s_e1[wi][j];
+                if (e1.z >= 0.0f) {
+                    const float4 e0 = s_e0[wi][j];
+                    SplatEllipse ej;
+                    ej.u = e0.x; ej.v = e0.y; ej.cb = e0.z; ej.rcc = e0.w;
+                    ej.det = e1.x; ej.ck = e1.y; ej.ymax = e1.z; ej.yr = e1.w;
+                    row_tile_span(ej, ty, ts, rts, t0, t1);
+                    t0 = max(t0, sr.x);
+                    t1 = min(t1, sr.y);
+                } else {
+                    t0 = sr.x; t1 = sr.y;
                 }
             }
             const uint32_t cnt = t0 <= t1 ? (uint32_t)(t1 - t0 + 1) : 0u;
             uint32_t cnt_pre;
             const uint32_t batch = warp_prefix(cnt, cnt_pre);
-            const uint32_t ij = __shfl_sync(0xffffffffu, i, j);
+            __syncwarp();   // the previous batch's pairs have read s_u
+            s_u[wi][lane] = make_uint2((uint32_t)(row0 + t0) - cnt_pre, (uint32_t)sr.w);
+            __syncwarp();
             // ---- the batch's pairs, 32 at a time
             for (uint32_t p0 = 0; p0 < batch; p0 += 32) {
                 const uint32_t p = p0 + lane;
                 const int q = warp_owner(cnt_pre, p);
-                const uint32_t pq = __shfl_sync(0xffffffffu, cnt_pre, q);
-                const int tq0 = __shfl_sync(0xffffffffu, t0, q), rq = __shfl_sync(0xffffffffu, row0, q);
-                const uint32_t iq = __shfl_sync(0xffffffffu, ij, q);
+                const uint2 uq = s_u[wi][q];
                 const uint32_t pos = out + p;
                 if (p < batch && pos < limit) {
-                    keys[pos] = (KT)(rq + tq0 + (int)(p - pq));
-                    values[pos] = iq;
+                    keys[pos] = (KT)(uq.x + p);
+                    values[pos] = uq.y;
                 }
             }
             out += batch;
@@ -165,23 +185,23 @@ cudaError_t launch_duplicate(const uint32_t* order, const float4* rec,
     static std::atomic<int> per_sm_cache[64];   // per device ordinal; 0 = not measured yet
     if (dev >= 0 && dev < 64) per_sm = per_sm_cache[dev].load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_duplicate<false, uint32_t>, 256, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_duplicate<false, uint32_t>, kDupWarps * 32, 0);
         if (e != cudaSuccess) return e;
         per_sm = std::max(per_sm, 1);
         if (dev >= 0 && dev < 64) per_sm_cache[dev].store(per_sm, std::memory_order_relaxed);
     }
     const uint32_t warps = (n + 31) / 32;
-    const uint32_t grid = std::min<uint32_t>((warps + 7) / 8, (uint32_t)(num_sms * per_sm));
+    const uint32_t grid = std::min<uint32_t>((warps + kDupWarps - 1) / kDupWarps, (uint32_t)(num_sms * per_sm));
     uint16_t* k16 = static_cast<uint16_t*>(keys);
     uint32_t* k32 = static_cast<uint32_t*>(keys);
     if (multi_view && key_bytes == 2)
-        NVGS_LAUNCH(log, s, "k_duplicate_views", k_duplicate<true, uint16_t><<<grid, 256, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, k16, values));
+        NVGS_LAUNCH(log, s, "k_duplicate_views", k_duplicate<true, uint16_t><<<grid, kDupWarps * 32, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, k16, values));
     else if (multi_view)
-        NVGS_LAUNCH(log, s, "k_duplicate_views", k_duplicate<true, uint32_t><<<grid, 256, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, k32, values));
+        NVGS_LAUNCH(log, s, "k_duplicate_views", k_duplicate<true, uint32_t><<<grid, kDupWarps * 32, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, k32, values));
     else if (key_bytes == 2)
-        NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<false, uint16_t><<<grid, 256, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, k16, values));
+        NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<false, uint16_t><<<grid, kDupWarps * 32, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, k16, values));
     else
-        NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<false, uint32_t><<<grid, 256, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, k32, values));
+        NVGS_LAUNCH(log, s, "k_duplicate", k_duplicate<false, uint32_t><<<grid, kDupWarps * 32, 0, s>>>(order, rec, offsets, n, n_dev, cam_dev, n_pairs, pair_cap, overflow, k32, values));
     return cudaGetLastError();
 }
 

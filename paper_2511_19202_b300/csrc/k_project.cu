@@ -110,10 +110,11 @@ __global__ void __launch_bounds__(256, 2) k_project(const uint2* __restrict__ su
                 if (cnt > 1) {
                     // row by row, from the values the record stores (as k_duplicate reads them)
                     const SplatEllipse el = splat_ellipse(u, v, cA, cB, cC, det, -2.0f * kw);
+                    const float rts = 1.0f / (float)ts;
                     cnt = 0;
                     for (int ty = r.y; ty <= r.w; ty++) {
                         int t0, t1;
-                        row_tile_span(el, ty, ts, t0, t1);
+                        row_tile_span(el, ty, ts, rts, t0, t1);
                         t0 = max(t0, r.x);
                         t1 = min(t1, r.z);
                         if (t0 <= t1) cnt += (uint32_t)(t1 - t0 + 1);

@@ -153,51 +153,69 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // (Sigma_2D = [[ca, cb], [cb, cc]], det its determinant); x_right is concave with its maximum at
 // the ellipse's rightmost point y = cb x_max / ca, x_max = sqrt(ca kk), so its maximum over the
 // band is at that y clamped to the band (and symmetrically for x_left).  The projection counts
-// with this function and the duplication writes with it, on the same stored record values
-// (conic and det), with every rounding step explicit, so both agree.  It is conservative: kk is
-// inflated by 1e-4 relative plus 1e-3 and the interval widened by 1e-3 px plus 1e-5 relative --
-// more than the compositing's exponent pre-test margin -- so a pruned tile holds no pixel the
-// compositing could blend.
+// with these functions and the duplication writes with them, on the same stored record values
+// (conic and det), with every rounding step explicit, so both agree bit for bit.  It is
+// conservative: kk is inflated by 1e-4 relative plus 1e-3 and the interval widened by 1e-3 px
+// plus 1e-5 relative -- more than the compositing's exponent pre-test margin, and far more than
+// the ~1e-7 relative error of the hardware's approximate square root, reciprocal and division
+// used for the extents and of the division by cc (a product with its reciprocal) -- so a pruned
+// tile holds no pixel the compositing could blend.  The per-splat part (splat_ellipse) is
+// computed once per splat, the per-row part (row_tile_span) per tile row.
 struct SplatEllipse {
     float u, v;          // mean (pixels)
-    float ca, cb, cc;    // Sigma_2D recovered from the stored conic and det
-    float det, kq;       // det Sigma_2D, inflated support level
-    float xmax, ymax, yr;
+    float cb, rcc;       // Sigma_2D[0][1], 1 / Sigma_2D[1][1] (rounded)
+    float det, ck;       // det Sigma_2D, cc kq (kq: the inflated support level)
+    float ymax, yr;      // vertical half-extent sqrt(cc kq); y of the rightmost point
 };
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 __device__ __forceinline__ SplatEllipse splat_ellipse(float u, float v, float A, float B, float C, float det,
                                                       float kk) {
     SplatEllipse e;
     e.u = u; e.v = v;
-    e.ca = __fmul_rn(C, det);
+    const float ca = __fmul_rn(C, det);
     e.cb = __fmul_rn(-B, det);
-    e.cc = __fmul_rn(A, det);
+    const float cc = __fmul_rn(A, det);
     e.det = det;
-    e.kq = __fadd_rn(__fmul_rn(kk, 1.0001f), 1e-3f);
-    e.xmax = __fsqrt_rn(__fmul_rn(e.ca, e.kq));
-    e.ymax = __fsqrt_rn(__fmul_rn(e.cc, e.kq));
-    e.yr = __fdiv_rn(__fmul_rn(e.cb, e.xmax), e.ca);
+    const float kq = __fadd_rn(__fmul_rn(kk, 1.0001f), 1e-3f);
+    const float xmax = sqrt_approx(__fmul_rn(ca, kq));
+    e.ck = __fmul_rn(cc, kq);
+    e.ymax = sqrt_approx(e.ck);
+    e.yr = __fmul_rn(__fmul_rn(e.cb, xmax), rcp_approx(ca));
+    e.rcc = rcp_approx(cc);
     return e;
 }
 
-// Tile columns [t0, t1] of tile row ty that the ellipse reaches (t0 > t1: none).
-__device__ __forceinline__ void row_tile_span(const SplatEllipse& e, int ty, int ts, int& t0, int& t1) {
+// Tile columns [t0, t1] of tile row ty that the ellipse reaches (t0 > t1: none).  ts is the tile
+// size (8, 16 or 32) and rts = 1 / ts, exact for these powers of two.
+__device__ __forceinline__ void row_tile_span(const SplatEllipse& e, int ty, int ts, float rts, int& t0, int& t1) {
     const float y0 = __fsub_rn(__fadd_rn((float)(ty * ts), 0.5f), e.v);
     const float y1 = __fsub_rn(__fadd_rn((float)((ty + 1) * ts), -0.5f), e.v);
     const float ya = fmaxf(y0, -e.ymax), yb = fminf(y1, e.ymax);
     if (!(ya <= yb)) { t0 = 1; t1 = 0; return; }
     const float ys = fminf(yb, fmaxf(ya, e.yr));     // band point of the rightmost x
     const float yl = fminf(yb, fmaxf(ya, -e.yr));    // band point of the leftmost x
-    const float hr = __fsqrt_rn(fmaxf(0.0f, __fmul_rn(e.det, __fsub_rn(__fmul_rn(e.cc, e.kq), __fmul_rn(ys, ys)))));
-    const float hl = __fsqrt_rn(fmaxf(0.0f, __fmul_rn(e.det, __fsub_rn(__fmul_rn(e.cc, e.kq), __fmul_rn(yl, yl)))));
-    float xr = __fdiv_rn(__fadd_rn(__fmul_rn(e.cb, ys), hr), e.cc);
-    float xl = __fdiv_rn(__fsub_rn(__fmul_rn(e.cb, yl), hl), e.cc);
+    const float hr = sqrt_approx(fmaxf(0.0f, __fmul_rn(e.det, __fsub_rn(e.ck, __fmul_rn(ys, ys)))));
+    const float hl = sqrt_approx(fmaxf(0.0f, __fmul_rn(e.det, __fsub_rn(e.ck, __fmul_rn(yl, yl)))));
+    float xr = __fmul_rn(__fadd_rn(__fmul_rn(e.cb, ys), hr), e.rcc);
+    float xl = __fmul_rn(__fsub_rn(__fmul_rn(e.cb, yl), hl), e.rcc);
     const float pad = __fadd_rn(1e-3f, __fmul_rn(1e-5f, __fadd_rn(fabsf(xl), fabsf(xr))));
     xr = __fadd_rn(__fadd_rn(xr, pad), e.u);    // absolute pixel coordinates
     xl = __fsub_rn(__fadd_rn(xl, e.u), pad);
     // tile tx's pixel centres span [tx ts + 0.5, tx ts + ts - 0.5]
-    t1 = (int)floorf(__fdiv_rn(__fsub_rn(xr, 0.5f), (float)ts));
-    t0 = (int)ceilf(__fdiv_rn(__fadd_rn(xl, 0.5f - (float)ts), (float)ts));
+    t1 = (int)floorf(__fmul_rn(__fsub_rn(xr, 0.5f), rts));
+    t0 = (int)ceilf(__fmul_rn(__fadd_rn(xl, 0.5f - (float)ts), rts));
 }
 
 // Exclusive warp prefix of one value per lane; returns the warp total.
