@@ -190,9 +190,12 @@ nvgs_status nvgs_query_visibility(nvgs_ctx* ctx, const nvgs_camera* cam,
                                   const nvgs_render_flags* flags, float* logits,
                                   uint8_t* keep, nvgs_frame_stats* stats);
 
-/* The whole pass S1-S6 for one camera into `image` (H x W x 3 float32 in flags.image_memory;
- * a HOST image is copied back inside the call).  stats (HOST, nullable) is filled after the
- * call synchronises. */
+/* The whole pass S1-S6 for one camera into `image` (H x W x 3 float32 in flags.image_memory).
+ * A HOST image that is page-locked and mapped for the device (cudaHostAlloc, or a pinned torch
+ * tensor) is written directly by the compositing kernels, overlapping the transfer with the
+ * compositing; a pageable HOST image is copied back from a device buffer.  Either way it is
+ * complete when the call returns.  stats (HOST, nullable) is filled after the call
+ * synchronises. */
 nvgs_status nvgs_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_render_flags* flags,
                         float* image, nvgs_frame_stats* stats);
 

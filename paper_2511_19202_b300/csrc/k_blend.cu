@@ -84,6 +84,30 @@ struct Smem {
     float2 bl[NP];   // (b, b')
 };
 
+// The compositing kernels' shared memory: the staged batches while walking, then the tile's final
+// colours for the image write.
+template <int TS>
+union BlendShared {
+    Smem<TS> st;
+    float rgb[3 * TS * TS];
+};
+
+// Writes a block of `rows` tile rows, whose colours are in rgb (3 floats per pixel, row-major,
+// TS pixels a row), to the image rows y0.. at columns x0..: consecutive threads store consecutive
+// floats of an image row, so each tile row leaves as one contiguous run (192 bytes at 16 x 16)
+// rather than as three 12-byte-strided stores per pixel -- what keeps a page-locked host image
+// written over the host link at full width.  Pixels outside the image are skipped.  Call after
+// a barrier that follows the rgb stores.
+template <int TS, int kThreads>
+__device__ __forceinline__ void store_rows_rgb(const float* rgb, int rows, float* __restrict__ image,
+                                               const CamParams& cam, int x0, int y0) {
+    const int run = 3 * min(TS, cam.W - x0);
+    for (int q = threadIdx.x; q < 3 * TS * rows; q += kThreads) {
+        const int r = q / (3 * TS), c = q - r * (3 * TS);
+        if (y0 + r < cam.H && c < run) image[((size_t)(y0 + r) * cam.W + x0) * 3 + c] = rgb[q];
+    }
+}
+
 // Stages fragment k = base + t of a batch (gathered by its survivor index) into slot (t / 2, t % 2);
 // past the range it stages a fragment of zero opacity, which no pixel composites (the padding of
 // an odd last pair).
@@ -232,7 +256,8 @@ __global__ void __launch_bounds__(TS * TS / blend_parts<TS>(), 4 * blend_parts<T
                                                   unsigned long long* __restrict__ evals_out,
                                                   int n_views, float* const* __restrict__ images) {
     constexpr int B = TS * TS, P = blend_parts<TS>(), kThreads = B / P;
-    __shared__ Smem<TS> sm;
+    __shared__ BlendShared<TS> sh;
+    Smem<TS>& sm = sh.st;
     if (split_dev) split_len = *split_dev;   // resolved on the device (sync-free batches)
     const int tile = blockIdx.x / P, part = blockIdx.x % P;
     const int li = part * kThreads + threadIdx.x;   // the pixel within the tile
@@ -258,14 +283,17 @@ __global__ void __launch_bounds__(TS * TS / blend_parts<TS>(), 4 * blend_parts<T
             return;
         }
     }
+    __syncthreads();   // every thread is past the last staged batch: sh.rgb may overwrite it
+    sh.rgb[3 * threadIdx.x] = fmaf(f.T, cam.bg[0], f.C0);
+    sh.rgb[3 * threadIdx.x + 1] = fmaf(f.T, cam.bg[1], f.C1);
+    sh.rgb[3 * threadIdx.x + 2] = fmaf(f.T, cam.bg[2], f.C2);
     if (inside) {
         const size_t p = (size_t)py * cam.W + px;
-        image[3 * p] = fmaf(f.T, cam.bg[0], f.C0);
-        image[3 * p + 1] = fmaf(f.T, cam.bg[1], f.C1);
-        image[3 * p + 2] = fmaf(f.T, cam.bg[2], f.C2);
         if (final_T) final_T[p] = f.T;
         if (n_contrib) n_contrib[p] = (int32_t)f.last;
     }
+    __syncthreads();
+    store_rows_rgb<TS, kThreads>(sh.rgb, kThreads / TS, image, cam, tx * TS, ty * TS + part * (kThreads / TS));
 }
 
 // ------------------------------------------------------------------ dense tiles
@@ -393,6 +421,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_D(const uint32_t* __rest
                                                           int32_t* __restrict__ n_contrib,
                                                           int n_views, float* const* __restrict__ images) {
     constexpr int B = TS * TS;
+    __shared__ float rgb[3 * B];
     const int tile = blockIdx.x;
     const uint32_t nc = n_chunks[tile];
     if (nc == 0) return;
@@ -402,7 +431,6 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_D(const uint32_t* __rest
     const int lt = tile - cam.tile_base;
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
     const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
-    if (!(px < cam.W && py < cam.H)) return;
     const float4 st = state_tc[(size_t)tile * B + threadIdx.x];
     float C0 = st.x, C1 = st.y, C2 = st.z, T;
     int32_t last = state_cnt[(size_t)tile * B + threadIdx.x];
@@ -419,12 +447,16 @@ __global__ void __launch_bounds__(TS* TS) k_blend_split_D(const uint32_t* __rest
             T = v.w;
         }
     }
-    const size_t p = (size_t)py * cam.W + px;
-    image[3 * p] = fmaf(T, cam.bg[0], C0);
-    image[3 * p + 1] = fmaf(T, cam.bg[1], C1);
-    image[3 * p + 2] = fmaf(T, cam.bg[2], C2);
-    if (final_T) final_T[p] = T;
-    if (n_contrib) n_contrib[p] = last;
+    rgb[3 * threadIdx.x] = fmaf(T, cam.bg[0], C0);
+    rgb[3 * threadIdx.x + 1] = fmaf(T, cam.bg[1], C1);
+    rgb[3 * threadIdx.x + 2] = fmaf(T, cam.bg[2], C2);
+    if (px < cam.W && py < cam.H) {
+        const size_t p = (size_t)py * cam.W + px;
+        if (final_T) final_T[p] = T;
+        if (n_contrib) n_contrib[p] = last;
+    }
+    __syncthreads();
+    store_rows_rgb<TS, B>(rgb, TS, image, cam, tx * TS, ty * TS);
 }
 
 static inline uint64_t round256(uint64_t b) { return (b + 255) / 256 * 256; }

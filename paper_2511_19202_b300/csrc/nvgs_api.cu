@@ -857,9 +857,21 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     tm.mark(NVGS_STAGE_BLEND);
     const size_t npx = (size_t)cp.W * cp.H;
     float* img_dev = image;
+    bool copy_back = false;
     if (f->image_memory == NVGS_MEM_HOST) {
-        CK(ensure(ctx->image_tmp, npx * 12));
-        img_dev = P<float>(ctx->image_tmp);
+        // a page-locked host image that the device can address is written by the compositing
+        // kernels themselves (the transfer overlaps the compositing); a pageable one goes
+        // through a device buffer and one copy after the last kernel
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, image) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer) {
+            img_dev = static_cast<float*>(pa.devicePointer);
+        } else {
+            (void)cudaGetLastError();
+            CK(ensure(ctx->image_tmp, npx * 12));
+            img_dev = P<float>(ctx->image_tmp);
+            copy_back = true;
+        }
     }
     float* fT = nullptr;
     int32_t* nc = nullptr;
@@ -895,8 +907,7 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     if (evals) CK(cudaMemcpyAsync(ctx->h_counters + 16, counters + 16, 16, cudaMemcpyDeviceToHost, s));
     if (labels_row) CK(launch_mark_labels(surv, n_surv, mark, labels_row, s, &ctx->log));
     tm.mark(NVGS_NUM_STAGES);
-    if (f->image_memory == NVGS_MEM_HOST)
-        CK(cudaMemcpyAsync(image, img_dev, npx * 12, cudaMemcpyDeviceToHost, s));
+    if (copy_back) CK(cudaMemcpyAsync(image, img_dev, npx * 12, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     end_frame(ctx);
 
