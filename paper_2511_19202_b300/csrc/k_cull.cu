@@ -167,10 +167,7 @@ __device__ __forceinline__ void chunk_word_prefix(const uint32_t* __restrict__ w
 __global__ void __launch_bounds__(256) k_expand_chunks(const Chunk* __restrict__ chunks,
                                                        const uint32_t* __restrict__ bits,
                                                        const uint32_t* __restrict__ chunk_offsets,
-                                                       uint2* __restrict__ out,
-                                                       const FrameInst* __restrict__ fi,
-                                                       const AssetDev* __restrict__ assets,
-                                                       float4* __restrict__ out_mean) {
+                                                       uint2* __restrict__ out) {
     __shared__ uint32_t s_word[64];
     __shared__ uint32_t s_pref[128];
     const int c = blockIdx.x;
@@ -179,7 +176,6 @@ __global__ void __launch_bounds__(256) k_expand_chunks(const Chunk* __restrict__
     const uint32_t base = chunk_offsets[c];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    const int asset = out_mean ? fi[ch.inst].asset : 0;
 #pragma unroll
     for (int k = 0; k < 8; k++) {
         int w = warp * 8 + k;
@@ -188,22 +184,15 @@ __global__ void __launch_bounds__(256) k_expand_chunks(const Chunk* __restrict__
             uint32_t pos = base + s_pref[64 + w] + __popc(word & lt);
             const uint32_t g = (uint32_t)(ch.g0 + w * 32 + lane);
             out[pos] = make_uint2((uint32_t)ch.inst, g);
-            // the MLP reads the mean next to the entry instead of through instance -> asset, and
-            // the asset id in place of the opacity (which the MLP does not use)
-            if (out_mean) {
-                const float4 m = __ldg(&assets[asset].mean_op[g]);
-                out_mean[pos] = make_float4(m.x, m.y, m.z, __int_as_float(asset));
-            }
         }
     }
 }
 
 cudaError_t launch_expand_chunks(const Chunk* chunks, int n_chunks, const uint32_t* bits,
-                                 const uint32_t* chunk_offsets, uint2* out, const FrameInst* fi,
-                                 const AssetDev* assets, float4* out_mean, cudaStream_t s,
+                                 const uint32_t* chunk_offsets, uint2* out, cudaStream_t s,
                                  LaunchLog* log) {
     if (n_chunks <= 0) return cudaSuccess;
-    NVGS_LAUNCH(log, s, "k_expand_chunks", k_expand_chunks<<<n_chunks, 256, 0, s>>>(chunks, bits, chunk_offsets, out, fi, assets, out_mean));
+    NVGS_LAUNCH(log, s, "k_expand_chunks", k_expand_chunks<<<n_chunks, 256, 0, s>>>(chunks, bits, chunk_offsets, out));
     return cudaGetLastError();
 }
 

@@ -138,8 +138,7 @@ __device__ __forceinline__ float epilogue_logit(uint32_t t_lane, float alpha, co
     return (lg[0] + lg[1]) + (lg[2] + lg[3]);
 }
 
-__device__ __forceinline__ void prefetch_row(uint2* s_e, float4* s_m, const uint2* e, const float4* m) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(s_e)), "l"(e) : "memory");
+__device__ __forceinline__ void prefetch_mean(float4* s_m, const float4* m) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(s_m)), "l"(m) : "memory");
 }
 __device__ __forceinline__ void prefetch_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -147,7 +146,7 @@ __device__ __forceinline__ void prefetch_wait() { asm volatile("cp.async.wait_gr
 
 // This thread's row of E4M3 inputs into its lane of an input buffer (zeros past the list); returns
 // the row's instance gate.
-__device__ __forceinline__ bool build_inputs(uint32_t t_in, bool valid, uint2 e, float4 m,
+__device__ __forceinline__ bool build_inputs(uint32_t t_in, bool valid, uint2 e, float4 m, int asset,
                                              const FrameInst* __restrict__ fis,
                                              const AssetDev* __restrict__ assets) {
     uint32_t p[8];
@@ -155,7 +154,7 @@ __device__ __forceinline__ bool build_inputs(uint32_t t_in, bool valid, uint2 e,
     if (valid) {
         const FrameInst& fr = fis[e.x];
         gated = fr.gated != 0;
-        const MlpAsset ma = mlp_asset(assets[__float_as_int(m.w)]);
+        const MlpAsset ma = mlp_asset(assets[asset]);
         float f[32];
         mlp_features(ma, fr.cam_local[0], fr.cam_local[1], fr.cam_local[2], fr.dist_scale, m, f);
 #pragma unroll
@@ -175,15 +174,19 @@ __device__ __forceinline__ bool build_next(uint32_t t_in, bool valid, const uint
     prefetch_wait();
     uint2 e = make_uint2(0, 0);
     float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid) { e = *s_e; m = *s_m; }
-    asset = valid ? __float_as_int(m.w) : INT_MAX;
-    return build_inputs(t_in, valid, e, m, fis, assets);
+    asset = INT_MAX;
+    if (valid) {
+        e = *s_e;
+        m = *s_m;
+        asset = fis[e.x].asset;
+    }
+    return build_inputs(t_in, valid, e, m, asset, fis, assets);
 }
 
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
-k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, uint32_t n,
+k_mlp_f8(const uint2* __restrict__ list, uint32_t n,
          const uint32_t* __restrict__ n_dev, const FrameInst* __restrict__ fis,
          const AssetDev* __restrict__ assets, float threshold, uint32_t* __restrict__ keep_bits,
          float* __restrict__ logits_out, uint32_t* __restrict__ err_flag) {
@@ -231,10 +234,19 @@ k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
         const uint32_t i0 = s_begin * kRows + tid;
         uint2 e = make_uint2(0, 0);
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i0 < n) { e = __ldg(&list[i0]); m = __ldg(&list_mean[i0]); }
-        gated = build_inputs(t_lane + kColIn, i0 < n, e, m, fis, assets);
-        my_asset_next = i0 < n ? __float_as_int(m.w) : INT_MAX;
+        int a0 = INT_MAX;
+        if (i0 < n) {
+            e = __ldg(&list[i0]);
+            a0 = fis[e.x].asset;
+            m = __ldg(&assets[a0].mean_op[e.y]);
+        }
+        gated = build_inputs(t_lane + kColIn, i0 < n, e, m, a0, fis, assets);
+        my_asset_next = a0;
     }
+    // this thread's entry of the step after the current one: entries are loaded two steps ahead,
+    // means one step ahead (addressed through the entry's instance and asset)
+    uint2 e_ahead = make_uint2(0u, 0u);
+    if (s_begin + 1 < s_end && (s_begin + 1) * kRows + tid < n) e_ahead = __ldg(&list[(s_begin + 1) * kRows + tid]);
 
     for (uint32_t step = s_begin; step < s_end && !abort; step++) {
         const uint32_t i = step * kRows + tid;
@@ -243,8 +255,15 @@ k_mlp_f8(const uint2* __restrict__ list, const float4* __restrict__ list_mean, u
         const uint32_t i_next = nstep * kRows + tid;
         const bool has_next = nstep < s_end;
         const bool next_valid = has_next && i_next < n;
-        if (next_valid) prefetch_row(s_e, s_m, &list[i_next], &list_mean[i_next]);
+        if (next_valid) {
+            *s_e = e_ahead;
+            prefetch_mean(s_m, assets[fis[e_ahead.x].asset].mean_op + e_ahead.y);
+        }
         prefetch_commit();
+        {
+            const uint32_t i_next2 = (nstep + 1) * kRows + tid;
+            e_ahead = (nstep + 1 < s_end && i_next2 < n) ? __ldg(&list[i_next2]) : make_uint2(0u, 0u);
+        }
         const int my_asset = my_asset_next;
         bool gated_next = false;
         {
@@ -430,7 +449,7 @@ void mlp_f8_pack_weights(const float* w, uint8_t* out, float* scales_out) {
     }
 }
 
-cudaError_t launch_mlp_f8(const uint2* list, const float4* list_mean, uint32_t n, const uint32_t* n_dev,
+cudaError_t launch_mlp_f8(const uint2* list, uint32_t n, const uint32_t* n_dev,
                           const FrameInst* fi, const AssetDev* assets, float threshold, uint32_t* keep_bits,
                           float* logits_out, uint32_t* err_flag, int num_sms, cudaStream_t s, LaunchLog* log) {
     if (n == 0) return cudaSuccess;
@@ -443,7 +462,7 @@ cudaError_t launch_mlp_f8(const uint2* list, const float4* list_mean, uint32_t n
     }
     const uint32_t steps = (n + kRows - 1) / kRows;
     const uint32_t grid = std::min<uint32_t>(steps, (uint32_t)num_sms * kCtasPerSm);
-    NVGS_LAUNCH(log, s, "k_mlp_f8", k_mlp_f8<<<grid, kThreads, kSmemBytes, s>>>(list, list_mean, n, n_dev, fi, assets, threshold, keep_bits, logits_out, err_flag));
+    NVGS_LAUNCH(log, s, "k_mlp_f8", k_mlp_f8<<<grid, kThreads, kSmemBytes, s>>>(list, n, n_dev, fi, assets, threshold, keep_bits, logits_out, err_flag));
     return cudaGetLastError();
 }
 

@@ -53,7 +53,7 @@ struct nvgs_ctx {
     DevBuf frame_inst, bits, chunk_counts, chunk_offsets, vis_list, keep_bits, logits_tmp,
         block_counts, block_offsets, surv, rec, tile_counts, tile_offsets, keys, vals,
         keys_alt, vals_alt, ranges, scratch, counters, image_tmp, final_T, n_contrib, mark, dkey,
-        didx, dkey_alt, didx_alt, split_scratch, vis_mean, grad_surv;
+        didx, dkey_alt, didx_alt, split_scratch, grad_surv;
     // visibility-MLP training state, per asset (FP32 master weights, Adam moments, views)
     struct Train {
         DevBuf w, m, v, views;
@@ -299,11 +299,8 @@ nvgs_status run_cull(nvgs_ctx* ctx, const CamParams* cam_dev, const nvgs_render_
     CK(exclusive_scan_u32(P<uint32_t>(ctx->chunk_counts), P<uint32_t>(ctx->chunk_offsets), sc.n_chunks,
                           &counters[0], ctx->scratch.p, s, &ctx->log));
     const bool tc_mlp = f->use_mlp && uses_tc_mlp(ctx, f);
-    if (tc_mlp) CK(ensure(ctx->vis_mean, cap * 16 + 16));
     CK(launch_expand_chunks(sc.chunks, sc.n_chunks, P<uint32_t>(ctx->bits),
-                            P<uint32_t>(ctx->chunk_offsets), P<uint2>(ctx->vis_list),
-                            P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev),
-                            tc_mlp ? P<float4>(ctx->vis_mean) : nullptr, s, &ctx->log));
+                            P<uint32_t>(ctx->chunk_offsets), P<uint2>(ctx->vis_list), s, &ctx->log));
     uint32_t n_vis_cap = (uint32_t)cap;
     const uint32_t* n_vis_dev = &counters[0];
     if (!async) {
@@ -324,12 +321,12 @@ nvgs_status run_cull(nvgs_ctx* ctx, const CamParams* cam_dev, const nvgs_render_
     if (tc_mlp) {
         if (!async) CK(cudaMemsetAsync(&counters[8], 0, 4, s));
         if (tc_mlp_precision(ctx, f) == NVGS_PREC_FP8)
-            CK(launch_mlp_f8(P<uint2>(ctx->vis_list), P<float4>(ctx->vis_mean), n_vis_cap, n_vis_dev,
+            CK(launch_mlp_f8(P<uint2>(ctx->vis_list), n_vis_cap, n_vis_dev,
                              P<FrameInst>(ctx->frame_inst), P<AssetDev>(ctx->assets_dev), f->logit_threshold,
                              P<uint32_t>(ctx->keep_bits), want_logits ? P<float>(ctx->logits_tmp) : nullptr,
                              &counters[8], ctx->num_sms, s, &ctx->log));
         else
-            CK(launch_mlp_tc(P<uint2>(ctx->vis_list), P<float4>(ctx->vis_mean), n_vis_cap, n_vis_dev,
+            CK(launch_mlp_tc(P<uint2>(ctx->vis_list), n_vis_cap, n_vis_dev,
                              P<FrameInst>(ctx->frame_inst),
                              P<AssetDev>(ctx->assets_dev), f->logit_threshold, P<uint32_t>(ctx->keep_bits),
                              want_logits ? P<float>(ctx->logits_tmp) : nullptr, &counters[8],
@@ -502,7 +499,7 @@ extern "C" nvgs_status nvgs_destroy(nvgs_ctx* ctx) {
                       &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
                       &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial,
                       &ctx->dkey, &ctx->didx, &ctx->dkey_alt, &ctx->didx_alt, &ctx->split_scratch,
-                      &ctx->vis_mean, &ctx->grad_surv, &ctx->cam_dev, &ctx->view_stats,
+                      &ctx->grad_surv, &ctx->cam_dev, &ctx->view_stats,
                       &ctx->mv_fimap, &ctx->mv_chunks, &ctx->mv_images};
     for (auto& t : ctx->train) { release(t.w); release(t.m); release(t.v); release(t.views); }
     for (DevBuf* b : bufs) release(*b);
@@ -1705,7 +1702,7 @@ extern "C" nvgs_status nvgs_device_bytes(const nvgs_ctx* ctx, uint64_t* bytes) {
                             &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
                             &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial,
                             &ctx->dkey, &ctx->didx, &ctx->dkey_alt, &ctx->didx_alt, &ctx->split_scratch,
-                            &ctx->vis_mean, &ctx->grad_surv, &ctx->cam_dev, &ctx->view_stats};
+                            &ctx->grad_surv, &ctx->cam_dev, &ctx->view_stats};
     for (const DevBuf* b : bufs) t += b->cap;
     for (auto& tr : ctx->train) t += tr.w.cap + tr.m.cap + tr.v.cap + tr.views.cap;
     *bytes = t;

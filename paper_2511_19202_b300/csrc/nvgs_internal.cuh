@@ -289,12 +289,9 @@ cudaError_t launch_frustum(const Chunk* chunks, int n_chunks, const FrameInst* f
                            const AssetDev* assets, const CamParams* cam_dev, uint32_t* bits,
                            uint32_t* chunk_counts, cudaStream_t s, LaunchLog* log);
 
-// Writes (instance, gaussian) of every set bit, in bit order, at out[chunk_offsets[c] + rank],
-// and (out_mean nullable) the Gaussian's local mean with its asset id (int bits) in w at the same
-// position.
+// Writes (instance, gaussian) of every set bit, in bit order, at out[chunk_offsets[c] + rank].
 cudaError_t launch_expand_chunks(const Chunk* chunks, int n_chunks, const uint32_t* bits,
-                                 const uint32_t* chunk_offsets, uint2* out, const FrameInst* fi,
-                                 const AssetDev* assets, float4* out_mean, cudaStream_t s,
+                                 const uint32_t* chunk_offsets, uint2* out, cudaStream_t s,
                                  LaunchLog* log);
 
 // S2: keep bits over a list of (instance, gaussian) entries.
@@ -308,13 +305,12 @@ cudaError_t launch_mlp_fp32(const uint2* list, uint32_t n, const uint32_t* n_dev
 // per-tensor scales s_W1, s_W2, s_W3, s_h1, s_h2).
 size_t mlp_f8_weight_bytes();
 void mlp_f8_pack_weights(const float* w, uint8_t* out, float* scales_out);
-// list_mean as for launch_mlp_tc.
-cudaError_t launch_mlp_f8(const uint2* list, const float4* list_mean, uint32_t n, const uint32_t* n_dev,
+cudaError_t launch_mlp_f8(const uint2* list, uint32_t n, const uint32_t* n_dev,
                           const FrameInst* fi, const AssetDev* assets, float threshold, uint32_t* keep_bits,
                           float* logits_out, uint32_t* err_flag, int num_sms, cudaStream_t s, LaunchLog* log);
-// list_mean: per entry (local mean, asset id as int bits), as launch_expand_chunks writes it.
-// err_flag (device) is set to 1 if a bounded wait on the tensor-core pipeline gave up.
-cudaError_t launch_mlp_tc(const uint2* list, const float4* list_mean, uint32_t n, const uint32_t* n_dev,
+// The rows' means are read through each entry's instance and asset.  err_flag (device) is set to 1
+// if a bounded wait on the tensor-core pipeline gave up.
+cudaError_t launch_mlp_tc(const uint2* list, uint32_t n, const uint32_t* n_dev,
                           const FrameInst* fi,
                           const AssetDev* assets, float threshold, uint32_t* keep_bits,
                           float* logits_out, uint32_t* err_flag, int num_sms, int ctas_per_sm,
