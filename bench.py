@@ -97,6 +97,26 @@ def dram_traffic_per_launch(name, frames, launches):
                     return None
                 return per_unit * float(sum(units)) / max(1, launches)
     return None
+ISSUE_TABLE = os.path.join(ROOT, "profiles", "issue_per_unit.txt")
+
+
+def issue_per_unit(name):
+    """ncu warp instructions per unit of work of `name` (smsp__inst_executed.sum over the captured
+    launch's units), or None if the kernel has no capture or its sources changed since."""
+    if name not in KERNEL_SOURCES or not os.path.exists(ISSUE_TABLE):
+        return None
+    with open(ISSUE_TABLE) as f:
+        for line in f:
+            cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 4 and cells[0] == name:
+                try:
+                    per_unit = float(cells[2])
+                except ValueError:
+                    return None
+                return per_unit if cells[3] == sources_hash(name) else None
+    return None
+
+
 SAMPLE_ROWS = 8
 
 
@@ -532,10 +552,25 @@ def run_ours(args, rank, world):
             mhz = clk.get("sm_max_mhz") or 2032.0
             peak = 148 * 128 * 2 * mhz * 1e6 / 1e12   # FP32 lanes x FMA x max SM clock
             alu_src = "derived: 148 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock"
+        evals = float(np.mean([s_["blend_evaluations"] for s_ in st_prof]))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "evaluations_per_frame": float(np.mean([s_["blend_evaluations"] for s_ in st_prof])),
+                "evaluations_per_frame": evals,
                 "composited_per_frame": float(np.mean([s_["blend_composited"] for s_ in st_prof])),
                 "flops_per_evaluation": BLEND_FLOPS_PER_EVAL}
+        # the issue-slot view of the same launches: warp instructions per evaluation from the
+        # committed ncu capture x evaluations per launch / launch time, against 4 warp
+        # instructions per clock per SM at the SM clock sampled under load
+        ipe = issue_per_unit(name)
+        if ipe is not None:
+            n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+            mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2032.0
+            issued = ipe * evals * len(st_prof) / max(1, n_launch) / (avg_ms * 1e-3)
+            issue_peak = 4.0 * n_sm * mhz * 1e6
+            roof["issue"] = {"warp_instructions_per_evaluation": ipe, "achieved": issued / 1e9,
+                             "peak": issue_peak / 1e9, "unit": "G warp instructions/s",
+                             "frac": issued / issue_peak,
+                             "source": "profiles/issue_per_unit.txt (ncu smsp__inst_executed.sum); "
+                                       "peak: 4 per clock per SM at the sampled SM clock"}
     else:
         achieved = work / (tot_ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6400.0)

@@ -1,5 +1,6 @@
 """Host logic of bench.py that needs no GPU: the units a kernel's DRAM traffic scales with, and
-the profile table of DRAM bytes per unit (read only while the kernel's sources are unchanged)."""
+the profile tables of DRAM bytes and warp instructions per unit (read only while the kernel's
+sources are unchanged)."""
 import os
 import sys
 
@@ -40,3 +41,16 @@ def test_traffic_table_scaling_and_staleness(tmp_path, monkeypatch):
     assert bench.dram_traffic_per_launch("k_blend<16>", [FRAME], 1) is None
     assert bench.dram_traffic_per_launch("k_frustum", [FRAME], 1) is None
 
+
+
+def test_issue_table_is_read_only_while_sources_match(tmp_path, monkeypatch):
+    h = bench.sources_hash("k_blend<16>")
+    table = tmp_path / "i.txt"
+    table.write_text("| kernel | unit | warp instructions per unit | hash |\n|---|---|---:|---|\n"
+                     f"| `k_blend<16>` | evaluation | 1.085 | `{h}` |\n"
+                     "| `k_project` | survivor | 40.0 | `0000000000000000` |\n")
+    monkeypatch.setattr(bench, "ISSUE_TABLE", str(table))
+    assert bench.issue_per_unit("k_blend<16>") == pytest.approx(1.085)
+    assert bench.issue_per_unit("k_project") is None     # stale hash
+    assert bench.issue_per_unit("k_mlp_tc") is None      # no row
+    assert bench.issue_per_unit("k_frustum") is None     # no sources list
