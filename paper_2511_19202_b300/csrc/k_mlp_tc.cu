@@ -16,7 +16,7 @@
 //      encoding) into IN[b ^ 1];
 //   2. per hidden layer: wait for the commit, epilogue into H, barrier, issue the next layer;
 //   3. the third layer's epilogue also evaluates the 64 -> 1 output layer on the CUDA cores
-//      (FP32 w4 and b4 on the BF16-rounded ReLU activations), so a step costs three MMA round
+//      (FP32 w4 and b4 on the FP32 ReLU activations), so a step costs three MMA round
 //      trips: each round trip (issue, commit, mbarrier) has a fixed latency of several hundred
 //      cycles, which bounds the kernel more than the tensor work of its 64-wide layers.
 // The hidden biases cost no CUDA-core work: every layer ends with one more K = 16 MMA step of a constant A
@@ -106,26 +106,25 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t t_lane) {
     }
 }
 
-// Output layer on the CUDA cores: acc (64 FP32 columns, b3 included) -> ReLU and BF16 rounding
-// (the hidden activations' precision) -> dot with the FP32 w4 -> + b4.
+// Output layer on the CUDA cores: acc (64 FP32 columns, b3 included) -> ReLU -> dot with the FP32
+// w4 (packed FP32x2 FMAs over neighbouring columns) -> + b4.  The third layer's activations stay
+// in FP32 here: only the hidden activations that feed a tensor-core layer are rounded to BF16.
 __device__ __forceinline__ float epilogue_output(uint32_t t_lane, const float* __restrict__ w4) {
-    float acc[4] = {w4[64], 0.0f, 0.0f, 0.0f};
+    float2 a01 = make_float2(w4[64], 0.0f), a23 = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         uint32_t r[32];
         tmem_ld32(t_lane + kColD + 32 * h, r);
 #pragma unroll
-        for (int q = 0; q < 16; q += 2) {
-            const float4 w = *reinterpret_cast<const float4*>(w4 + 32 * h + 2 * q);
-            const uint32_t p0 = bf16x2_relu(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
-            const uint32_t p1 = bf16x2_relu(__uint_as_float(r[2 * q + 2]), __uint_as_float(r[2 * q + 3]));
-            acc[0] = fmaf(__uint_as_float(p0 << 16), w.x, acc[0]);
-            acc[1] = fmaf(__uint_as_float(p0 & 0xffff0000u), w.y, acc[1]);
-            acc[2] = fmaf(__uint_as_float(p1 << 16), w.z, acc[2]);
-            acc[3] = fmaf(__uint_as_float(p1 & 0xffff0000u), w.w, acc[3]);
+        for (int q = 0; q < 32; q += 4) {
+            const float4 w = *reinterpret_cast<const float4*>(w4 + 32 * h + q);
+            a01 = __ffma2_rn(make_float2(fmaxf(__uint_as_float(r[q]), 0.0f), fmaxf(__uint_as_float(r[q + 1]), 0.0f)),
+                             make_float2(w.x, w.y), a01);
+            a23 = __ffma2_rn(make_float2(fmaxf(__uint_as_float(r[q + 2]), 0.0f), fmaxf(__uint_as_float(r[q + 3]), 0.0f)),
+                             make_float2(w.z, w.w), a23);
         }
     }
-    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    return (a01.x + a01.y) + (a23.x + a23.y);
 }
 
 // Asynchronous copy of this thread's next list entry and mean into shared memory (they are read

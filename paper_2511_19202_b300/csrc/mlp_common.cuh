@@ -49,7 +49,8 @@ __device__ __forceinline__ void mlp_features(const MlpAsset& a, float clx, float
     f[27] = dx * inv;
     f[28] = dy * inv;
     f[29] = dz * inv;
-    float dn = fmaf(2.0f * (logf(dist * dist_scale) - a.log_dmin), a.inv_log_range, -1.0f);
+    // the hardware log2 (about 1e-7 relative; the feature is rounded to BF16 or kept in FP32)
+    float dn = fmaf(2.0f * (__logf(dist * dist_scale) - a.log_dmin), a.inv_log_range, -1.0f);
     f[30] = fminf(1.0f, fmaxf(-1.0f, dn));
     f[31] = 0.0f;
 }

@@ -116,9 +116,9 @@ def bf16_round(x):
 
 def bf16_reference(w, feats):
     """The BF16 tensor-core MLP's quantised arithmetic with exact accumulation: FP32 inputs,
-    weights and the ReLU'd hidden activations rounded to BF16; the hidden biases as BF16 high +
-    low pairs; the output layer in FP32 (w4, b4) on the BF16-rounded third-layer activations.
-    Only the accumulation order and precision differ from the kernel."""
+    weights and the ReLU'd activations that feed a tensor-core layer rounded to BF16; the hidden
+    biases as BF16 high + low pairs; the output layer in FP32 (w4, b4) on the third layer's FP32
+    ReLU activations.  Only the accumulation order and precision differ from the kernel."""
     def pair(v):
         v = np.ascontiguousarray(v, np.float32)
         hi = bf16_round(v)
@@ -126,7 +126,9 @@ def bf16_reference(w, feats):
     h = bf16_round(np.asarray(feats, np.float64).astype(np.float32))
     for k in (1, 2, 3):
         a = h @ bf16_round(w[f"W{k}"]).T + pair(w[f"b{k}"])
-        h = bf16_round(np.maximum(a, 0.0).astype(np.float32))
+        h = np.maximum(a, 0.0)
+        if k < 3:
+            h = bf16_round(h.astype(np.float32))
     return h @ np.ravel(w["W4"]).astype(np.float32).astype(np.float64) + float(np.float32(np.ravel(w["b4"])[0]))
 
 
