@@ -108,11 +108,12 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, float alpha, co
 #pragma unroll
         for (int q = 0; q < 8; q++) {
             const float4 b = *reinterpret_cast<const float4*>(beta + 32 * half + 4 * q);
-            const float v0 = fmaf(__uint_as_float(r[4 * q]), alpha, b.x);
-            const float v1 = fmaf(__uint_as_float(r[4 * q + 1]), alpha, b.y);
-            const float v2 = fmaf(__uint_as_float(r[4 * q + 2]), alpha, b.z);
-            const float v3 = fmaf(__uint_as_float(r[4 * q + 3]), alpha, b.w);
-            p[q] = e4m3x2_relu(v0, v1) | (e4m3x2_relu(v2, v3) << 16);
+            // the same FMAs lane by lane as packed FP32x2 instructions
+            const float2 v01 = __ffma2_rn(make_float2(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1])),
+                                          make_float2(alpha, alpha), make_float2(b.x, b.y));
+            const float2 v23 = __ffma2_rn(make_float2(__uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3])),
+                                          make_float2(alpha, alpha), make_float2(b.z, b.w));
+            p[q] = e4m3x2_relu(v01.x, v01.y) | (e4m3x2_relu(v23.x, v23.y) << 16);
         }
         tmem_st8(t_lane + kColH + 8 * half, p);
     }
@@ -120,7 +121,9 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t t_lane, float alpha, co
 
 __device__ __forceinline__ float epilogue_logit(uint32_t t_lane, float alpha, const float* b3, const float* w4,
                                                 float b4) {
-    float lg[4] = {b4, 0.0f, 0.0f, 0.0f};
+    // four partial sums, (0, 1) and (2, 3) packed: the same FMAs lane by lane as FP32x2 instructions
+    float2 l01 = make_float2(b4, 0.0f), l23 = make_float2(0.0f, 0.0f);
+    const float2 al = make_float2(alpha, alpha);
 #pragma unroll
     for (int half = 0; half < 2; half++) {
         uint32_t r[32];
@@ -129,13 +132,15 @@ __device__ __forceinline__ float epilogue_logit(uint32_t t_lane, float alpha, co
         for (int q = 0; q < 8; q++) {
             const float4 b = *reinterpret_cast<const float4*>(b3 + 32 * half + 4 * q);
             const float4 w = *reinterpret_cast<const float4*>(w4 + 32 * half + 4 * q);
-            lg[0] = fmaf(w.x, fmaxf(fmaf(__uint_as_float(r[4 * q]), alpha, b.x), 0.0f), lg[0]);
-            lg[1] = fmaf(w.y, fmaxf(fmaf(__uint_as_float(r[4 * q + 1]), alpha, b.y), 0.0f), lg[1]);
-            lg[2] = fmaf(w.z, fmaxf(fmaf(__uint_as_float(r[4 * q + 2]), alpha, b.z), 0.0f), lg[2]);
-            lg[3] = fmaf(w.w, fmaxf(fmaf(__uint_as_float(r[4 * q + 3]), alpha, b.w), 0.0f), lg[3]);
+            const float2 v01 = __ffma2_rn(make_float2(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1])), al,
+                                          make_float2(b.x, b.y));
+            const float2 v23 = __ffma2_rn(make_float2(__uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3])), al,
+                                          make_float2(b.z, b.w));
+            l01 = __ffma2_rn(make_float2(w.x, w.y), make_float2(fmaxf(v01.x, 0.0f), fmaxf(v01.y, 0.0f)), l01);
+            l23 = __ffma2_rn(make_float2(w.z, w.w), make_float2(fmaxf(v23.x, 0.0f), fmaxf(v23.y, 0.0f)), l23);
         }
     }
-    return (lg[0] + lg[1]) + (lg[2] + lg[3]);
+    return (l01.x + l01.y) + (l23.x + l23.y);
 }
 
 __device__ __forceinline__ void prefetch_mean(float4* s_m, const float4* m) {
