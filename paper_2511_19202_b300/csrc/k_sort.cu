@@ -253,28 +253,47 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const K* __restrict__ ke
 }
 
 // Row d of the digit-major histogram (n_tiles counts) -> its exclusive prefix, in place; the row's
-// total to totals[d].  One CTA per digit, 256 threads, 1024 counts per step (four per thread,
-// consecutive) with a running carry.
-__global__ void __launch_bounds__(256) k_rs_digit_scan(uint32_t* __restrict__ hist, uint32_t n_tiles,
-                                                       uint32_t* __restrict__ totals) {
-    __shared__ uint32_t s_warp[16];
+// total to totals[d].  One CTA of 1024 threads per digit, 4096 counts per step (four per thread,
+// consecutive) with a running carry: a 1080p frame's 17k tiles of pairs take five steps.
+constexpr int kDigitScanThreads = 1024;
+__global__ void __launch_bounds__(kDigitScanThreads) k_rs_digit_scan(uint32_t* __restrict__ hist, uint32_t n_tiles,
+                                                                     uint32_t* __restrict__ totals) {
+    __shared__ uint32_t s_warp[2][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t* row = hist + (uint64_t)blockIdx.x * n_tiles;
     uint32_t carry = 0;
-    for (uint32_t base = 0; base < n_tiles; base += 1024) {
+    int par = 0;
+    for (uint32_t base = 0; base < n_tiles; base += 4 * kDigitScanThreads, par ^= 1) {
         const uint32_t i0 = base + 4 * threadIdx.x;
         uint32_t v[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) v[k] = i0 + k < n_tiles ? row[i0 + k] : 0u;
         const uint32_t sum = v[0] + v[1] + v[2] + v[3];
-        uint32_t tot;
-        uint32_t run = carry + block_exclusive_scan_256(sum, s_warp, &tot);
+        // inclusive scan within the warp, then over the 32 warp totals (slots alternate between
+        // steps so that one barrier a step suffices)
+        uint32_t x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane == 31) s_warp[par][warp] = x;
+        __syncthreads();
+        uint32_t wt = s_warp[par][lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, wt, o);
+            if (lane >= o) wt += t;
+        }
+        const uint32_t warp_excl = __shfl_sync(0xffffffffu, wt, (warp + 31) & 31) * (warp > 0);
+        const uint32_t total = __shfl_sync(0xffffffffu, wt, 31);
+        uint32_t run = carry + warp_excl + x - sum;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             if (i0 + k < n_tiles) row[i0 + k] = run;
             run += v[k];
         }
-        carry += tot;
-        __syncthreads();   // s_warp is reused by the next step's scan
+        carry += total;
     }
     if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
@@ -463,7 +482,7 @@ static cudaError_t radix_sort_impl(K* keys, uint32_t* values, K* keys_alt, uint3
         NVGS_LAUNCH(log, s, hname, k_rs_hist<K><<<hgrid, kRsThreads, 0, s>>>(kin, n, n_dev, shift, mask, (uint32_t)tiles, hist));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        NVGS_LAUNCH(log, s, "k_rs_digit_scan", k_rs_digit_scan<<<256, 256, 0, s>>>(hist, (uint32_t)tiles, totals));
+        NVGS_LAUNCH(log, s, "k_rs_digit_scan", k_rs_digit_scan<<<256, kDigitScanThreads, 0, s>>>(hist, (uint32_t)tiles, totals));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         NVGS_LAUNCH(log, s, sname, k_rs_scatter<K><<<sgrid, kRsThreads, rs_smem_bytes<K>(), s>>>(kin, vin, kout, vout, n, n_dev, shift, mask, (uint32_t)tiles, hist, totals));
