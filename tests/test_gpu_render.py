@@ -374,10 +374,12 @@ def test_invalid_arguments_are_rejected(cfg1_setup):
 
 
 # ----------------------------------------------------------------------------- radix sort
+# (20M elements: 4883 radix tiles, more than one step of the digit-row scan, with a ragged last step)
 @pytest.mark.parametrize("n,bits,spread", [(0, 8, 0), (1, 8, 0), (2, 3, 2), (1000, 7, 100),
                                            (8191, 13, 1 << 13), (8192, 45, 1 << 45),
                                            (8193, 16, 5), (100_003, 40, 1 << 40),
-                                           (1_000_003, 64, 0), (777_777, 20, 3)])
+                                           (1_000_003, 64, 0), (777_777, 20, 3),
+                                           (20_000_003, 16, 1 << 16)])
 def test_radix_sort_is_a_stable_sort(cfg1_setup, n, bits, spread):
     sc, cam, r, osc = cfg1_setup
     rng = np.random.default_rng(n + bits)
