@@ -127,8 +127,9 @@ __device__ __forceinline__ float epilogue_output(uint32_t t_lane, const float* _
     return (a01.x + a01.y) + (a23.x + a23.y);
 }
 
-// Asynchronous copy of this thread's next list entry and mean into shared memory (they are read
-// only when the next step's inputs are built, so no register holds them meanwhile).
+// Asynchronous copy of the mean of this thread's next row into shared memory (read only when the
+// next step's inputs are built, so no register holds it meanwhile; the row's list entry is stored
+// beside it with a plain store).
 __device__ __forceinline__ void prefetch_mean(float4* s_m, const float4* m) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(s_m)), "l"(m) : "memory");
 }
@@ -279,7 +280,6 @@ k_mlp_tc(const uint2* __restrict__ list, uint32_t n,
             const uint32_t i_next2 = (nstep + 1) * kRows + tid;
             e_ahead = (nstep + 1 < s_end && i_next2 < n) ? __ldg(&list[i_next2]) : make_uint2(0u, 0u);
         }
-        // the list's mean carries the row's asset id in w
         const int my_asset = my_asset_next;
         bool gated_next = false;
         // the CTA's smallest and largest asset of this step; the barrier also orders this step's
