@@ -67,7 +67,6 @@ __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
     return d;
 }
-__device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
 // Byte offset of element (r, k) in a K-major core-matrix tile with K columns.
 __device__ __forceinline__ uint32_t tile_off(int r, int k, int K) {
@@ -267,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_train_fwd_bwd_tc(
         sync_operands();
         ok = run([&] { gemm(tmem + kColZ, sm + kOffH2, 64, sm + kOffW3, 64, 4, 64, mbar); });
     }
-    // ---- Z3, H3 (BF16-rounded as in inference), logit, loss, dL/dz, G3 = dz w4 [Z3 > 0]
+    // ---- Z3, H3 (FP32, as the inference's output layer takes it), logit, loss, dL/dz, G3 = dz w4 [Z3 > 0]
     float dz = 0.0f, loss = 0.0f;
     if (ok) {
         load64(tmem + kColZ + lane_off, z);
@@ -276,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_train_fwd_bwd_tc(
         for (int q = 0; q < 64; q++) {
             z[q] += sb3[q];
             if (z[q] > 0.0f) m3[q >> 5] |= 1u << (q & 31);
-            z[q] = bf16_to_f32(bf16(fmaxf(z[q], 0.0f)));
+            z[q] = fmaxf(z[q], 0.0f);
             lg = fmaf(sw4[q], z[q], lg);
         }
         const uint32_t np = *n_pos;
