@@ -856,12 +856,12 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     float* img_dev = image;
     bool copy_back = false;
     if (f->image_memory == NVGS_MEM_HOST) {
-        // a page-locked host image that the device can address is written by the compositing
-        // kernels themselves (the transfer overlaps the compositing); a pageable one goes
-        // through a device buffer and one copy after the last kernel
+        // a page-locked host image that the device can address (and whose floats are aligned) is
+        // written by the compositing kernels themselves (the transfer overlaps the compositing);
+        // any other goes through a device buffer and one copy after the last kernel
         cudaPointerAttributes pa{};
-        if (cudaPointerGetAttributes(&pa, image) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
-            pa.devicePointer) {
+        if (((uintptr_t)image & 3u) == 0 && cudaPointerGetAttributes(&pa, image) == cudaSuccess &&
+            pa.type == cudaMemoryTypeHost && pa.devicePointer && ((uintptr_t)pa.devicePointer & 3u) == 0) {
             img_dev = static_cast<float*>(pa.devicePointer);
         } else {
             (void)cudaGetLastError();
