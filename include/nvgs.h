@@ -318,8 +318,10 @@ nvgs_status nvgs_reset_kernel_stats(nvgs_ctx* ctx);
  * the stream.  The whole batch can therefore be captured into a CUDA graph: with use_graph = 1
  * the first call renders the batch and captures it; later calls with the same number of views,
  * the same view sizes, flags and options replay the graph with the new cameras (one graph launch
- * per batch).  The paper runs one view per frame (Sec. 3.3); batching serves multi-view use such
- * as training-view rendering or several cameras per frame. */
+ * per batch).  A call after the assets, MLPs or instances changed, or after any call of the
+ * library (re)allocated a buffer, captures anew instead of replaying (a graph holds the scene's
+ * lists and raw buffer addresses).  The paper runs one view per frame (Sec. 3.3); batching serves
+ * multi-view use such as training-view rendering or several cameras per frame. */
 typedef struct {
     int64_t max_pairs;           /* capacity of (tile, Gaussian) pairs per view; 0: 8 x the
                                     instanced Gaussians */

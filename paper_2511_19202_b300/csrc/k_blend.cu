@@ -254,12 +254,13 @@ __global__ void __launch_bounds__(TS * TS / blend_parts<TS>(), 4 * blend_parts<T
                                                   int32_t* __restrict__ state_cnt,
                                                   uint32_t* __restrict__ alive,
                                                   unsigned long long* __restrict__ evals_out,
-                                                  int n_views, float* const* __restrict__ images) {
+                                                  int n_views, float* const* __restrict__ images,
+                                                  const uint32_t* __restrict__ tile_order) {
     constexpr int B = TS * TS, P = blend_parts<TS>(), kThreads = B / P;
     __shared__ BlendShared<TS> sh;
     Smem<TS>& sm = sh.st;
     if (split_dev) split_len = *split_dev;   // resolved on the device (sync-free batches)
-    const int tile = blockIdx.x / P, part = blockIdx.x % P;
+    const int tile = tile_order ? (int)tile_order[blockIdx.x / P] : (int)(blockIdx.x / P), part = blockIdx.x % P;
     const int li = part * kThreads + threadIdx.x;   // the pixel within the tile
     const int view = n_views > 1 ? tile_view(camp, n_views, tile) : 0;
     const CamParams cam = camp[view];
@@ -469,13 +470,37 @@ size_t blend_split_scratch_bytes(int n_tiles, uint64_t n_pairs, int tile_size, u
                     round256(items * B * 16) + round256(items * B * 4));
 }
 
+// The tiles in descending classes of their work, min(pair count, split length) rounded down to a
+// power of two (the order inside a class is whatever the shared-memory atomics give: a tile's
+// result does not depend on when its CTA runs).  One CTA.
+__global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ ranges, int n_tiles,
+                                                     uint32_t split_len, const uint32_t* __restrict__ split_dev,
+                                                     uint32_t* __restrict__ order) {
+    __shared__ uint32_t slot[33];
+    if (split_dev) split_len = *split_dev;
+    if (threadIdx.x < 33) slot[threadIdx.x] = 0u;
+    __syncthreads();
+    auto cls = [&](int t) {
+        const uint32_t w = min(ranges[2 * t + 1] - ranges[2 * t], split_len);
+        return w ? 32 - __clz(w) : 0;   // 0 (empty) .. 32
+    };
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) atomicAdd(&slot[cls(t)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {   // class starts, the heaviest class first
+        uint32_t run = 0;
+        for (int c = 32; c >= 0; c--) { const uint32_t k = slot[c]; slot[c] = run; run += k; }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) order[atomicAdd(&slot[cls(t)], 1u)] = (uint32_t)t;
+}
+
 template <int TS>
 static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, const float4* rec,
                             const CamParams& cam, const CamParams* cam_dev, float* image, float* final_T,
                             int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
                             const uint32_t* auto_split_pairs, void* scratch, void* scan_scratch,
                             int num_sms, unsigned long long* evals, cudaStream_t s, LaunchLog* log,
-                            int n_views, float* const* images, int n_tiles) {
+                            int n_views, float* const* images, int n_tiles, uint32_t* tile_order) {
     constexpr int B = TS * TS;
     const bool may_split = n_pairs > split_len;
     const bool aux = n_contrib || mark;   // the last blended pair per pixel, blended survivors
@@ -514,9 +539,15 @@ static cudaError_t blend_ts(const uint32_t* ranges, const uint32_t* values, cons
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (tile_order) {
+        NVGS_LAUNCH(log, s, "k_tile_order", k_tile_order<<<1, 1024, 0, s>>>(ranges, n_tiles, split_len, split_dev, tile_order));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     NVGS_LAUNCH(log, s, TS == 8 ? "k_blend<8>" : TS == 16 ? "k_blend<16>" : "k_blend<32>",
                 (evals ? k_blend<TS, true, true> : aux ? k_blend<TS, true, false> : k_blend<TS, false, false>)<<<n_tiles * blend_parts<TS>(), B / blend_parts<TS>(), 0, s>>>(ranges, values, rec, cam_dev, image, final_T, n_contrib, mark,
-                                                  split_len, split_dev, state_tc, state_cnt, alive, evals, n_views, images));
+                                                  split_len, split_dev, state_tc, state_cnt, alive, evals, n_views, images,
+                                                  tile_order));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !may_split) return e;
     NVGS_LAUNCH(log, s, "k_split_count", k_split_count<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, alive, blend_parts<TS>(), n_tiles, split_len, split_dev, n_chunks));
@@ -536,13 +567,13 @@ cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const f
                          int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
                          const uint32_t* auto_split_pairs, void* scratch, void* scan_scratch,
                          int num_sms, unsigned long long* evals, cudaStream_t s, LaunchLog* log,
-                         int n_views, float* const* images, int n_tiles_total) {
+                         int n_views, float* const* images, int n_tiles_total, uint32_t* tile_order) {
     const int n_tiles = n_tiles_total > 0 ? n_tiles_total : cam.tiles_x * cam.tiles_y;
     if (n_tiles <= 0) return cudaSuccess;
     switch (cam.tile_size) {
-        case 8: return blend_ts<8>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log, n_views, images, n_tiles);
-        case 16: return blend_ts<16>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log, n_views, images, n_tiles);
-        case 32: return blend_ts<32>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log, n_views, images, n_tiles);
+        case 8: return blend_ts<8>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log, n_views, images, n_tiles, tile_order);
+        case 16: return blend_ts<16>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log, n_views, images, n_tiles, tile_order);
+        case 32: return blend_ts<32>(ranges, values, rec, cam, cam_dev, image, final_T, n_contrib, mark, split_len, n_pairs, auto_split_pairs, scratch, scan_scratch, num_sms, evals, s, log, n_views, images, n_tiles, tile_order);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -42,6 +42,7 @@ struct nvgs_ctx {
     std::vector<AssetStore> assets;
     DevBuf assets_dev;
     bool assets_dirty = true;
+    uint64_t scene_gen = 0;   // bumped by every change of assets, MLPs or instances (graph keys)
 
     std::vector<nvgs_instance> instances;
     std::vector<int64_t> inst_offset_h;
@@ -53,7 +54,7 @@ struct nvgs_ctx {
     DevBuf frame_inst, bits, chunk_counts, chunk_offsets, vis_list, keep_bits, logits_tmp,
         block_counts, block_offsets, surv, rec, tile_counts, tile_offsets, keys, vals,
         keys_alt, vals_alt, ranges, scratch, counters, image_tmp, final_T, n_contrib, mark, dkey,
-        didx, dkey_alt, didx_alt, split_scratch, grad_surv;
+        didx, dkey_alt, didx_alt, split_scratch, grad_surv, tile_order;
     // visibility-MLP training state, per asset (FP32 master weights, Adam moments, views)
     struct Train {
         DevBuf w, m, v, views;
@@ -118,6 +119,9 @@ nvgs_status fail(nvgs_ctx* c, nvgs_status st, const char* fmt, ...) {
 // Host-side fault injection for the tests: the next g_fail_allocs buffer growths fail as if
 // cudaMalloc had run out of memory (nvgs_debug_fail_allocs).
 std::atomic<int> g_fail_allocs{0};
+// Bumped by every device or staging allocation: a captured graph holds raw buffer addresses, so
+// its key carries this count and any (re)allocation since the capture forces a new capture.
+std::atomic<uint64_t> g_alloc_gen{0};
 
 cudaError_t ensure(DevBuf& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -138,6 +142,7 @@ cudaError_t ensure(DevBuf& b, size_t bytes) {
         return e;
     }
     b.cap = want;
+    g_alloc_gen.fetch_add(1);
     return cudaSuccess;
 }
 
@@ -402,6 +407,16 @@ void end_frame(nvgs_ctx* ctx) {
     L.n = 0;
 }
 
+// A graph key with the allocation count and the context's scene generation appended: a graph
+// captured before a buffer was reallocated, or before the assets, MLPs or instances changed, never
+// matches again.
+static std::vector<uint8_t> graph_stamp(const nvgs_ctx* ctx, std::vector<uint8_t> key) {
+    const uint64_t a = g_alloc_gen.load(), g = ctx->scene_gen;
+    key.insert(key.end(), (const uint8_t*)&a, (const uint8_t*)&a + sizeof a);
+    key.insert(key.end(), (const uint8_t*)&g, (const uint8_t*)&g + sizeof g);
+    return key;
+}
+
 // Stage n camera records and copy them to ctx->cam_dev on the stream (the staging buffer is
 // reused only after the previous copy has completed).
 nvgs_status upload_cams(nvgs_ctx* ctx, const CamParams* cps, int n) {
@@ -413,6 +428,7 @@ nvgs_status upload_cams(nvgs_ctx* ctx, const CamParams* cps, int n) {
         const int cap = std::max(n, 64);
         CK(cudaMallocHost(&ctx->h_cam, (size_t)cap * sizeof(CamParams)));
         ctx->h_cam_cap = cap;
+        g_alloc_gen.fetch_add(1);
         CK(ensure(ctx->cam_dev, (size_t)cap * sizeof(CamParams)));
     }
     if (!ctx->cam_ev) CK(cudaEventCreateWithFlags(&ctx->cam_ev, cudaEventDisableTiming));
@@ -499,7 +515,7 @@ extern "C" nvgs_status nvgs_destroy(nvgs_ctx* ctx) {
                       &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
                       &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial,
                       &ctx->dkey, &ctx->didx, &ctx->dkey_alt, &ctx->didx_alt, &ctx->split_scratch,
-                      &ctx->grad_surv, &ctx->cam_dev, &ctx->view_stats,
+                      &ctx->grad_surv, &ctx->tile_order, &ctx->cam_dev, &ctx->view_stats,
                       &ctx->mv_fimap, &ctx->mv_chunks, &ctx->mv_images};
     for (auto& t : ctx->train) { release(t.w); release(t.m); release(t.v); release(t.views); }
     for (DevBuf* b : bufs) release(*b);
@@ -596,6 +612,7 @@ extern "C" nvgs_status nvgs_load_asset(nvgs_ctx* ctx, const nvgs_asset_desc* d, 
     a.train_focal = (float)(1.0 / std::tan(th / 2.0));
     ctx->assets.push_back(as);
     ctx->assets_dirty = true;
+    ctx->scene_gen++;
     *asset_id = (int)ctx->assets.size() - 1;
     return NVGS_OK;
 }
@@ -633,6 +650,7 @@ extern "C" nvgs_status nvgs_set_mlp(nvgs_ctx* ctx, int asset_id, const float* w,
         as.precision = NVGS_PREC_FP8;
     }
     ctx->assets_dirty = true;
+    ctx->scene_gen++;
     return NVGS_OK;
 }
 
@@ -675,6 +693,7 @@ extern "C" nvgs_status nvgs_set_instances(nvgs_ctx* ctx, const nvgs_instance* in
     ctx->inst_offset_h = off;
     ctx->n_chunks = (int)chunks.size();
     ctx->n_instanced = total;
+    ctx->scene_gen++;
     return NVGS_OK;
 }
 
@@ -898,9 +917,10 @@ static nvgs_status do_render(nvgs_ctx* ctx, const nvgs_camera* cam, const nvgs_r
     // profile 2: S6's (pixel, fragment) evaluations and composited fragments in counters[16..19]
     unsigned long long* evals = f->profile >= 2 ? reinterpret_cast<unsigned long long*>(counters + 16) : nullptr;
     if (evals) CK(cudaMemsetAsync(evals, 0, 16, s));
+    CK(ensure(ctx->tile_order, (size_t)n_tiles * 4 + 16));
     CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, cam_dev, img_dev, fT, nc, mark,
                     split_len, n_pairs, nullptr, ctx->split_scratch.p, ctx->scratch.p, ctx->num_sms, evals,
-                    s, &ctx->log));
+                    s, &ctx->log, 1, nullptr, 0, P<uint32_t>(ctx->tile_order)));
     if (evals) CK(cudaMemcpyAsync(ctx->h_counters + 16, counters + 16, 16, cudaMemcpyDeviceToHost, s));
     if (labels_row) CK(launch_mark_labels(surv, n_surv, mark, labels_row, s, &ctx->log));
     tm.mark(NVGS_NUM_STAGES);
@@ -988,7 +1008,7 @@ extern "C" nvgs_status nvgs_label_visibility(nvgs_ctx* ctx, int asset_id, const 
                        labels + (size_t)(v / group) * n);
     }
     nvgs_status st2 = saved.empty() ? NVGS_OK : nvgs_set_instances(ctx, saved.data(), (int)saved.size());
-    if (saved.empty()) { ctx->instances.clear(); ctx->n_instanced = 0; ctx->n_chunks = 0; }
+    if (saved.empty()) { ctx->instances.clear(); ctx->n_instanced = 0; ctx->n_chunks = 0; ctx->scene_gen++; }
     return st != NVGS_OK ? st : st2;
 }
 
@@ -1320,9 +1340,10 @@ static nvgs_status enqueue_view_async(nvgs_ctx* ctx, const CamParams& cp, const 
         CK(ensure(ctx->split_scratch, blend_split_scratch_bytes(n_tiles, pair_cap, cp.tile_size, split_len)));
         CK(ensure(ctx->scratch, scan_scratch_bytes(n_tiles)));
     }
+    CK(ensure(ctx->tile_order, (size_t)n_tiles * 4 + 16));
     CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp, cam_dev, image, nullptr, nullptr,
                     nullptr, split_len, pair_cap, auto_split ? counters + 2 : nullptr, ctx->split_scratch.p,
-                    ctx->scratch.p, ctx->num_sms, nullptr, s, &ctx->log));
+                    ctx->scratch.p, ctx->num_sms, nullptr, s, &ctx->log, 1, nullptr, 0, P<uint32_t>(ctx->tile_order)));
     // this view's counts
     CK(cudaMemcpyAsync(view_counts, counters, 3 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     return NVGS_OK;
@@ -1379,7 +1400,8 @@ extern "C" nvgs_status nvgs_render_batch(nvgs_ctx* ctx, const nvgs_camera* cams,
     put(&o, sizeof o);
     put(&pair_cap, sizeof pair_cap);
     for (int v = 0; v < n_views; v++) put(&images[v], sizeof(float*));
-    const bool replay = o.use_graph && ctx->graph_exec && key == ctx->graph_key;
+    const std::vector<uint8_t> key_now = graph_stamp(ctx, key);
+    const bool replay = o.use_graph && ctx->graph_exec && key_now == ctx->graph_key;
     if (replay) {
         // the graph's first node copies the staged cameras; restage them once the last copy is done
         if (ctx->cam_ev_pending) CK(cudaEventSynchronize(ctx->cam_ev));
@@ -1410,7 +1432,7 @@ extern "C" nvgs_status nvgs_render_batch(nvgs_ctx* ctx, const nvgs_camera* cams,
                 ctx->graph_exec = nullptr;
                 return fail(ctx, NVGS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ie));
             }
-            ctx->graph_key = key;
+            ctx->graph_key = graph_stamp(ctx, key);   // the buffers as captured
         }
     }
     if (!stats) return NVGS_OK;
@@ -1490,10 +1512,16 @@ static nvgs_status enqueue_views(nvgs_ctx* ctx, const CullScope& scope, const Ca
                                : (auto_split ? 4096u : (uint32_t)f->blend_split_len);
     if (pair_cap > split_len)
         CK(ensure(ctx->split_scratch, blend_split_scratch_bytes(n_tiles, pair_cap, cp0.tile_size, split_len)));
+    // longest tiles first, while one CTA orders them quickly (a batch of up to 256K tiles)
+    uint32_t* tile_order = nullptr;
+    if (n_tiles <= (1 << 18)) {
+        CK(ensure(ctx->tile_order, (size_t)n_tiles * 4 + 16));
+        tile_order = P<uint32_t>(ctx->tile_order);
+    }
     CK(launch_blend(P<uint32_t>(ctx->ranges), svals, P<float4>(ctx->rec), cp0, cam_dev, nullptr, nullptr, nullptr,
                     nullptr, split_len, pair_cap, auto_split ? counters + 2 : nullptr, ctx->split_scratch.p,
                     ctx->scratch.p, ctx->num_sms, nullptr, s, &ctx->log, n_views, P<float*>(ctx->mv_images),
-                    n_tiles));
+                    n_tiles, tile_order));
     // batch counts (in frustum, survivors, pairs) and the flags, for the stats
     CK(cudaMemcpyAsync(P<uint32_t>(ctx->view_stats), counters, 3 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(P<uint32_t>(ctx->view_stats) + 4, &counters[8], 8, cudaMemcpyDeviceToDevice, s));
@@ -1567,7 +1595,8 @@ extern "C" nvgs_status nvgs_render_views(nvgs_ctx* ctx, const nvgs_camera* cams,
     put(&o, sizeof o);
     put(&pair_cap, sizeof pair_cap);
     for (int v = 0; v < n_views; v++) put(&images[v], sizeof(float*));
-    const bool replay = o.use_graph && ctx->mv_graph_exec && key == ctx->mv_graph_key;
+    const std::vector<uint8_t> key_now = graph_stamp(ctx, key);
+    const bool replay = o.use_graph && ctx->mv_graph_exec && key_now == ctx->mv_graph_key;
     if (replay) {
         if (ctx->cam_ev_pending) CK(cudaEventSynchronize(ctx->cam_ev));
         memcpy(ctx->h_cam, cps.data(), cps.size() * sizeof(CamParams));
@@ -1606,7 +1635,7 @@ extern "C" nvgs_status nvgs_render_views(nvgs_ctx* ctx, const nvgs_camera* cams,
                 ctx->mv_graph_exec = nullptr;
                 return fail(ctx, NVGS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ie));
             }
-            ctx->mv_graph_key = key;
+            ctx->mv_graph_key = graph_stamp(ctx, key);   // the buffers as captured
         }
     }
     if (!stats) return NVGS_OK;
@@ -1702,7 +1731,7 @@ extern "C" nvgs_status nvgs_device_bytes(const nvgs_ctx* ctx, uint64_t* bytes) {
                             &ctx->ranges, &ctx->scratch, &ctx->counters, &ctx->image_tmp, &ctx->final_T,
                             &ctx->n_contrib, &ctx->mark, &ctx->tr_sv, &ctx->tr_sg, &ctx->tr_partial,
                             &ctx->dkey, &ctx->didx, &ctx->dkey_alt, &ctx->didx_alt, &ctx->split_scratch,
-                            &ctx->grad_surv, &ctx->cam_dev, &ctx->view_stats};
+                            &ctx->grad_surv, &ctx->tile_order, &ctx->cam_dev, &ctx->view_stats};
     for (const DevBuf* b : bufs) t += b->cap;
     for (auto& tr : ctx->train) t += tr.w.cap + tr.m.cap + tr.v.cap + tr.views.cap;
     *bytes = t;

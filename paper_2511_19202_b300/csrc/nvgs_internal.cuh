@@ -405,7 +405,11 @@ cudaError_t launch_blend(const uint32_t* ranges, const uint32_t* values, const f
                          int32_t* n_contrib, uint8_t* mark, uint32_t split_len, uint64_t n_pairs,
                          const uint32_t* auto_split_pairs, void* scratch, void* scan_scratch,
                          int num_sms, unsigned long long* evals, cudaStream_t s, LaunchLog* log,
-                         int n_views = 1, float* const* images = nullptr, int n_tiles_total = 0);
+                         int n_views = 1, float* const* images = nullptr, int n_tiles_total = 0,
+                         uint32_t* tile_order = nullptr);
+// tile_order (device, nullable; n_tiles entries of scratch): the compositing CTAs then take the
+// tiles longest list first (pair counts capped at the split length, in power-of-two classes), so
+// that the longest tiles do not start in the grid's last wave.
 // labels[row * n_gauss + g] |= mark[s] for survivor s = (instance, g)
 cudaError_t launch_mark_labels(const uint2* surv, uint32_t n_surv, const uint8_t* mark,
                                uint8_t* labels_row, cudaStream_t s, LaunchLog* log);

@@ -75,6 +75,38 @@ def test_graph_replays_with_new_cameras():
         r.close()
 
 
+def test_graph_is_recaptured_after_the_scene_or_a_buffer_changes():
+    """A captured graph holds the scene's instance list and raw buffer addresses: after the
+    instances change, or after another call grew (reallocated) a buffer, the next call with the
+    same key must not replay the old graph -- its images equal the synchronous render of the
+    scene as it is now."""
+    sc = scenes.tiny_scene(3000, 4, spread=0.6, log_scale_mean=-3.0, sh_degree=2, n_instances=3)
+    r = renderer_for(sc)
+    try:
+        fl = r.flags(use_mlp=0)
+        cams = _cams(0)
+        out = [torch.zeros((c.height, c.width, 3), device="cuda") for c in cams]
+
+        def check():
+            ref = _sync_images(r, cams, fl)
+            r.render_batch(cams, r.flags(use_mlp=0), out=out, use_graph=True)   # replay or recapture
+            torch.cuda.synchronize()
+            for (a, _), b in zip(ref, out):
+                assert torch.equal(a, b)
+
+        r.render_batch(cams, r.flags(use_mlp=0), out=out, use_graph=True)   # render + capture
+        check()
+        r.set_instances(sc.instances[:2])                                    # fewer instances
+        check()
+        r.set_instances(sc.instances)
+        check()
+        big = scenes.look_at_camera((0.0, 0.0, 3.0), (0, 0, 0), 1600, 1200, 400.0)
+        r.render(big, fl)                                                    # grows per-frame buffers
+        check()
+    finally:
+        r.close()
+
+
 def test_pair_capacity_overflow_is_reported():
     from paper_2511_19202_b300 import nvgs as N
     sc = scenes.config1_scene(20000)
