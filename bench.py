@@ -407,7 +407,33 @@ def run_ours(args, rank, world):
             if min(ps) >= args.psnr_target:
                 tau = cand
                 break
-    culled = r.flags(use_mlp=1, mlp_gate=1, tile_size=tile, logit_threshold=tau, radius_clip_area=args.radius_clip)
+    # dense-tile split (flags.blend_split_len): automatic or never, whichever renders held-out
+    # orbit frames faster, separately for the culled and the unculled pass (with the compositing's
+    # longest-first tile order the split's extra launches can cost more than cutting up the long
+    # tiles saves); both modes render the whole image
+    held_t = [cams[f] for f in range(61, 120, 16)] if len(cams) >= 120 else cams[:1]
+
+    def pick_split(**kw):
+        times = {}
+        for mode in (0, -1):
+            fl_ = r.flags(tile_size=tile, blend_split_len=mode, **kw)
+            r.render(held_t[0], fl_)
+            e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0_.record(r.stream)
+            for c_ in held_t:
+                r.render(c_, fl_)
+            e1_.record(r.stream)
+            torch.cuda.synchronize()
+            times["automatic" if mode == 0 else "never"] = e0_.elapsed_time(e1_) / len(held_t)
+        best = min(times, key=times.get)
+        return (0 if best == "automatic" else -1), {"chosen": best, "held_out_ms_per_frame": times}
+
+    split_c, split_info_c = pick_split(use_mlp=1, mlp_gate=1, logit_threshold=tau, radius_clip_area=args.radius_clip)
+    split_p, split_info_p = pick_split(use_mlp=0)
+    plain = r.flags(use_mlp=0, tile_size=tile, blend_split_len=split_p)
+    culled = r.flags(use_mlp=1, mlp_gate=1, tile_size=tile, logit_threshold=tau, radius_clip_area=args.radius_clip,
+                     blend_split_len=split_c)
     stream = r.stream
 
     my_frames = replica_frames(rank, world, max(args.steps, args.warmup, 8), len(cams))
@@ -468,7 +494,8 @@ def run_ours(args, rank, world):
 
     # e2e through the C ABI with a host image (device->host copy inside the timed region)
     host = torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True)
-    e2e_flags = r.flags(use_mlp=1, mlp_gate=1, tile_size=tile, logit_threshold=tau, radius_clip_area=args.radius_clip)
+    e2e_flags = r.flags(use_mlp=1, mlp_gate=1, tile_size=tile, logit_threshold=tau, radius_clip_area=args.radius_clip,
+                        blend_split_len=split_c)
     t0 = time.perf_counter()
     for k in range(args.steps):
         r.render_host(frame(k), e2e_flags, host)
@@ -598,6 +625,7 @@ def run_ours(args, rank, world):
                    "l2": "no flush: the assets (1.9 GB or more) and per-frame buffers exceed the 126 MB L2",
                    "mlp_training": train_info,
                    "logit_threshold": tau, "radius_clip_area": args.radius_clip,
+                   "blend_split": {"culled": split_info_c, "unculled": split_info_p},
                    "threshold_calibration_min_psnr_db": calib,
                    "unculled_ms_per_frame": plain_ms,
                    "culled_ms_median_p95": [float(np.median([x["frame_ms"] for x in st_culled])),
