@@ -436,7 +436,9 @@ typedef struct {
     const uint32_t* survivors;   /* 2 x n_survivors: (instance, gaussian) */
     const float* records;        /* 16 x n_survivors: u, v, conic a, b, c, opacity, det Sigma_2D,
                                     ln(alpha_min / opacity), r, g, b, depth, then the tile
-                                    rectangle x0, y0, x1, y1 (inclusive) as int32 bits */
+                                    rectangle x0, y0, x1, y1 (inclusive) as int32 bits; a
+                                    survivor without tiles has only its (empty: 1, 1, 0, 0)
+                                    rectangle written */
     const int32_t* tile_rects;   /* the rectangles inside the records: 4 int32 every 16 */
     const uint32_t* pair_values; /* n_pairs survivor indices in (tile, depth) order */
     const void* pair_keys;       /* n_pairs tile ids of those pairs (non-decreasing), uint16 when

@@ -44,12 +44,11 @@ __global__ void __launch_bounds__(256, 2) k_project(const uint2* __restrict__ su
         const float4 m = __ldg(&a.mean_op[g]);
         const float4 ls = __ldg(&a.scale_quat[2 * (size_t)g]);
         const float4 qr = __ldg(&a.scale_quat[2 * (size_t)g + 1]);
-        // the SH coefficients (16 bytes at a time: coefficient j / 3, channel j % 3 of float j)
+        // the SH coefficients (16 bytes at a time: coefficient j / 3, channel j % 3 of float j),
+        // loaded only for a splat whose support box meets the image (below)
         const int n_floats = 3 * (a.sh_degree + 1) * (a.sh_degree + 1);
         const float4* __restrict__ shp = reinterpret_cast<const float4*>(a.sh + (size_t)g * a.sh_stride);
         float4 shv[12];
-#pragma unroll
-        for (int q = 0; q < 12; q++) shv[q] = 4 * q < n_floats ? __ldg(&shp[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
 
         const float3 pc = cam_point(fi, m.x, m.y, m.z);
         const float x = pc.x, y = pc.y, z = pc.z;
@@ -104,6 +103,10 @@ __global__ void __launch_bounds__(256, 2) k_project(const uint2* __restrict__ su
             float y0 = fmaxf(ceilf(v - ye - 0.5f), 0.0f);
             float y1 = fminf(floorf(v + ye - 0.5f), (float)(cam.H - 1));
             if (x0 <= x1 && y0 <= y1) {
+                // the colour's inputs, in flight while the tile rows are counted
+#pragma unroll
+                for (int q = 0; q < 12; q++)
+                    shv[q] = 4 * q < n_floats ? __ldg(&shp[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
                 const int ts = cam.tile_size;
                 r = make_int4((int)x0 / ts, (int)y0 / ts, (int)x1 / ts, (int)y1 / ts);
                 cnt = (uint32_t)((r.z - r.x + 1) * (r.w - r.y + 1));
@@ -122,16 +125,21 @@ __global__ void __launch_bounds__(256, 2) k_project(const uint2* __restrict__ su
                 }
             }
         }
+        // a splat without tiles (its support box outside the image -- the guard band keeps ~15-20 %
+        // of the survivors there -- or every row pruned) gets an empty rectangle and nothing else:
+        // no pair ever reads the rest of its record, so neither its colour nor its SH are fetched
+        if (cnt == 0) r = make_int4(1, 1, 0, 0);
         if (kMV) r.w |= fi.view << 16;
         counts[i] = cnt;
         dkey[i] = __float_as_uint(z);   // z > z_near > 0: the bit pattern orders like the value
         didx[i] = i;
         float4* out = rec + kRecF4 * (size_t)i;
+        reinterpret_cast<int4*>(out)[3] = r;
+        if (cnt == 0) continue;
         out[0] = make_float4(u, v, cA, cB);
         // z: det Sigma_2D (the binning's row spans recover Sigma_2D from it and the conic);
         // w: ln(alpha_min / opacity), the exponent below which a fragment cannot reach alpha_min
         out[1] = make_float4(cC, op, det, kw);
-        reinterpret_cast<int4*>(out)[3] = r;
 
         // colour at the local-frame direction from the camera to the mean
         float dx = m.x - fi.cam_local[0], dy = m.y - fi.cam_local[1], dz = m.z - fi.cam_local[2];
