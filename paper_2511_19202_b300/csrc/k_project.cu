@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(256, 2) k_project(const uint2* __restrict__ su
         const float4 ls = __ldg(&a.scale_quat[2 * (size_t)g]);
         const float4 qr = __ldg(&a.scale_quat[2 * (size_t)g + 1]);
         // the SH coefficients (16 bytes at a time: coefficient j / 3, channel j % 3 of float j),
-        // loaded only for a splat whose support box meets the image (below)
+        // fetched only for a splat that can reach the image: early on a cheap conservative bound
+        // (below), else once its support box is known to meet the image
         const int n_floats = 3 * (a.sh_degree + 1) * (a.sh_degree + 1);
         const float4* __restrict__ shp = reinterpret_cast<const float4*>(a.sh + (size_t)g * a.sh_stride);
         float4 shv[12];
@@ -55,6 +56,21 @@ __global__ void __launch_bounds__(256, 2) k_project(const uint2* __restrict__ su
         const float iz = 1.0f / z;
         const float tx = fminf(cam.lim_x, fmaxf(-cam.lim_x, x * iz));
         const float ty = fminf(cam.lim_y, fmaxf(-cam.lim_y, y * iz));
+        // a cheap bound on the support's pixel radius: the largest 3D scale through the Jacobian's
+        // Frobenius norm at the clamped ray, the level 2 ln(1 / alpha_min) at full opacity, the
+        // dilation; a splat certainly outside the image fetches no SH here
+        bool sh_loaded = false;
+        {
+            const float smax = fi.s * expf(fmaxf(ls.x, fmaxf(ls.y, ls.z)));
+            const float rad = 3.4f * (fmaxf(cam.fx, cam.fy) * iz * sqrtf(2.0f + tx * tx + ty * ty) * smax + 0.6f) + 2.0f;
+            const float uc = fmaf(cam.fx, x * iz, cam.cx), vc = fmaf(cam.fy, y * iz, cam.cy);
+            if (uc + rad >= -0.5f && uc - rad <= (float)cam.W && vc + rad >= -0.5f && vc - rad <= (float)cam.H) {
+#pragma unroll
+                for (int q = 0; q < 12; q++)
+                    shv[q] = 4 * q < n_floats ? __ldg(&shp[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                sh_loaded = true;
+            }
+        }
         // A = J W (2 x 3)
         const float jx = cam.fx * iz, jy = cam.fy * iz;
         float A0[3], A1[3];
@@ -103,10 +119,12 @@ __global__ void __launch_bounds__(256, 2) k_project(const uint2* __restrict__ su
             float y0 = fmaxf(ceilf(v - ye - 0.5f), 0.0f);
             float y1 = fminf(floorf(v + ye - 0.5f), (float)(cam.H - 1));
             if (x0 <= x1 && y0 <= y1) {
-                // the colour's inputs, in flight while the tile rows are counted
+                // the colour's inputs (if the bound above did not already fetch them)
+                if (!sh_loaded) {
 #pragma unroll
-                for (int q = 0; q < 12; q++)
-                    shv[q] = 4 * q < n_floats ? __ldg(&shp[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int q = 0; q < 12; q++)
+                        shv[q] = 4 * q < n_floats ? __ldg(&shp[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 const int ts = cam.tile_size;
                 r = make_int4((int)x0 / ts, (int)y0 / ts, (int)x1 / ts, (int)y1 / ts);
                 cnt = (uint32_t)((r.z - r.x + 1) * (r.w - r.y + 1));
