@@ -834,7 +834,7 @@ def run_backward(args):
             "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "sphere asset, 1M Gaussians, SH degree 3, 1920x1080, random U[0,1] target",
-                       "forward_ms": fwd, "backward_ms": ms - fwd, "loss": float(loss)}}
+                       "forward_ms": fwd, "backward_ms": ms - fwd, "loss": float(loss.detach())}}
     r.close()
     return line
 
